@@ -1,0 +1,218 @@
+/*
+ * icon.h -- C ABI of the GB300 dynamical-core library (sm_103a).
+ *
+ * The library advances the nonhydrostatic atmospheric dynamical core of an
+ * ICON-style model on the icosahedral-triangular C grid (paper: Sec. "Current
+ * State of the Art" -- nonhydrostatic formulation on an icosahedral-triangular
+ * C grid with a terrain-following height coordinate; Table 2 -- 90 levels,
+ * normal velocity on edges counted as 1.5 variables per cell; Sec. "Separation
+ * of Concerns" -- index lookups on triangles and on the dual hexagons and 12
+ * pentagons; Sec. "Innovations Realized" -- data stay resident on the GPU for
+ * the whole run). The paper gives no equations; the discretisation implemented
+ * here is stated operator by operator in the comments of the CUDA sources and
+ * restated, independently, by the FP64 oracle used in the tests.
+ *
+ * Conventions (all entry points):
+ *   - Every function except the *_free functions and icon_last_error returns an
+ *     icon_status. On error, out-pointers are left untouched, a message is
+ *     available from icon_last_error() (thread-local), and no handle leaks.
+ *   - Handles are opaque and owned by the caller; free them with the matching
+ *     *_free function (NULL is accepted). The library never frees caller memory.
+ *   - Device memory comes from the allocator registered with icon_set_allocator
+ *     (the Python binding registers PyTorch's caching allocator) or from
+ *     cudaMalloc when none is registered. Work is issued on the stream bound by
+ *     icon_set_stream (default: the legacy default stream).
+ *   - Pointers named host_* are host memory (pageable or pinned); no pointer in
+ *     this interface is a device pointer.
+ *   - Sizes are element counts unless named *bytes.
+ *   - Entry points are not reentrant on the same handle; distinct handles may be
+ *     used from distinct threads.
+ */
+#ifndef ICON_GB300_H
+#define ICON_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct icon_grid icon_grid;
+typedef struct icon_state icon_state;
+typedef struct icon_ensemble icon_ensemble;
+
+typedef enum {
+  ICON_OK = 0,
+  ICON_EINVAL = 1,      /* bad argument (NULL handle, size mismatch, unsupported grid) */
+  ICON_ENOMEM = 2,      /* the allocator returned NULL; nothing was leaked            */
+  ICON_ECUDA = 3,       /* a CUDA runtime call failed (message has the CUDA error)    */
+  ICON_ETIMEOUT = 4,    /* a bounded in-kernel wait ran out (persistent ensemble)     */
+  ICON_ENONFINITE = 5,  /* a NaN or Inf appeared in the prognostic state              */
+  ICON_EINDEX = 6       /* an internal index check failed (grid construction)         */
+} icon_status;
+
+typedef enum { ICON_FP64 = 0, ICON_MIXED = 1 } icon_precision;
+
+typedef enum {
+  ICON_CASE_REST = 0,    /* isothermal 250 K atmosphere at rest                          */
+  ICON_CASE_SBR = 1,     /* solid-body rotation 20 m/s in gradient balance, 250 K        */
+  ICON_CASE_JET = 2,     /* balanced 35 m/s midlatitude jet + 1 m/s bump at 20E 40N      */
+  ICON_CASE_MEMBER = 3   /* case 2 with a seeded bump amplitude and position per member  */
+} icon_case;
+
+/* Integer connectivity tables (int32, row-major, entity-major). */
+typedef enum {
+  ICON_T_C2V = 0,   /* [Nc][3] corner vertices of each cell, counter-clockwise          */
+  ICON_T_C2E = 1,   /* [Nc][3] edges; slot s joins corner s to corner (s+1)%3            */
+  ICON_T_E2C = 2,   /* [Ne][2] (c1, c2); c1 is the lower cell id; normal points c1->c2  */
+  ICON_T_E2V = 3,   /* [Ne][2] (v1, v2), counter-clockwise in c1; tangent points v1->v2 */
+  ICON_T_V2E = 4,   /* [Nv][6] edges around each vertex, CCW from the lowest edge id    */
+  ICON_T_V2C = 5,   /* [Nv][6] cell between v2e[j] and v2e[j+1]; pentagons repeat [0]   */
+  ICON_T_VDEG = 6,  /* [Nv]    5 or 6                                                   */
+  ICON_T_E2VT = 7,  /* [Ne][5] own edge, two other edges of c1, two other edges of c2   */
+  ICON_T_E2Q = 8    /* [Ne][4] v1, v2, vertex of c1 opposite e, vertex of c2 opposite e */
+} icon_table_int;
+
+/* FP64 geometry tables (unit vectors are on the unit sphere; lengths in m, areas in m^2). */
+typedef enum {
+  ICON_G_XC = 16,   /* [Nc][3] cell circumcentres                                      */
+  ICON_G_XE = 17,   /* [Ne][3] edge midpoints                                          */
+  ICON_G_XV = 18,   /* [Nv][3] vertices                                                */
+  ICON_G_NE = 19,   /* [Ne][3] edge normals                                            */
+  ICON_G_TE = 20,   /* [Ne][3] edge tangents                                           */
+  ICON_G_LE = 21,   /* [Ne] primal edge length                                         */
+  ICON_G_DE = 22,   /* [Ne] dual edge length (distance of the two cell centres)        */
+  ICON_G_AC = 23,   /* [Nc] cell area                                                  */
+  ICON_G_AV = 24,   /* [Nv] dual cell area                                             */
+  ICON_G_FE = 25,   /* [Ne] Coriolis parameter at edges                                */
+  ICON_G_VTW = 26,  /* [Ne][5] tangential-velocity weights, order of ICON_T_E2VT       */
+  ICON_G_KINW = 27, /* [Nc][3] kinetic-energy weights, order of ICON_T_C2E             */
+  ICON_G_LSQW = 28, /* [Nv][6][3] least-squares vertex-velocity weights                */
+  ICON_G_L34 = 29,  /* [Ne] distance of the two opposite quad vertices                 */
+  ICON_G_SCE = 30,  /* [Nc][3] outward sign of each cell edge (+1 if c is c1)          */
+  ICON_G_SVE = 31   /* [Nv][6] circulation sign (-1 if v is v1, +1 if v2, 0 padding)   */
+} icon_table_geom;
+
+/* Fields (copied out as FP64, row-major [entity][level], unpadded). */
+typedef enum {
+  ICON_F_VN = 0,       /* [Ne][N]   edge-normal velocity, m/s                        */
+  ICON_F_W = 1,        /* [Nc][N+1] vertical velocity at half levels (0 = lid), m/s  */
+  ICON_F_RHO = 2,      /* [Nc][N]   density, kg/m^3                                  */
+  ICON_F_THETA_V = 3,  /* [Nc][N]   virtual potential temperature, K                 */
+  ICON_F_EXNER = 4,    /* [Nc][N]   Exner pressure                                   */
+  ICON_F_MFLX = 5,     /* [Ne][N]   step-mean horizontal mass flux, kg/m^2/s         */
+  ICON_F_WFLX = 6      /* [Nc][N+1] step-mean vertical mass flux, kg/m^2/s           */
+} icon_field;
+
+/* Optional overrides for icon_state_init_ex. Negative / zero values select the default. */
+typedef struct {
+  double noise_K;    /* theta_v noise amplitude, K (<0: case default: 0.01 K for case 1, else 0) */
+  double top_m;      /* model top, m (<=0: 75 km for N >= 60, else 30 km)                        */
+  double stretch_s;  /* level stretching s (<=0: 5.5 for N >= 60, else 2)                        */
+  double damp_m;     /* base of the Rayleigh damping layer, m (<=0: 45 km / 20 km)               */
+  int precision;     /* icon_precision                                                           */
+  int member;        /* ensemble member index for ICON_CASE_MEMBER                               */
+} icon_case_params;
+
+/* ---------------------------------------------------------------- allocator, stream */
+
+/* Register device allocation callbacks (both non-NULL) or restore cudaMalloc/cudaFree
+ * (both NULL). alloc(bytes, ctx) returns a device pointer aligned to >= 256 bytes or
+ * NULL; dealloc(ptr, ctx) releases it. Handles created before the call keep the
+ * allocator they were created with. Returns ICON_EINVAL if exactly one is NULL. */
+int icon_set_allocator(void* (*alloc)(size_t bytes, void* ctx),
+                       void (*dealloc)(void* ptr, void* ctx), void* ctx);
+
+/* Bind the cudaStream_t (passed as void*) on which subsequent calls from this
+ * thread enqueue work; NULL selects the legacy default stream. */
+int icon_set_stream(void* cuda_stream);
+
+/* Message of the last failing call on this thread ("" if none). Never NULL. */
+const char* icon_last_error(void);
+
+/* ---------------------------------------------------------------- grid */
+
+/* Build the icosahedral grid R{root}B{bisections} with nlev full levels
+ * (grid family: Sec. "Current State of the Art"; sizes: Table 2, where R2B8 has
+ * 0.05e8 cells and R2B11 3.36e8). root must be 2 (RnBk = k+1 bisections of the
+ * icosahedron), 0 <= bisections <= 10, 1 <= nlev <= 256 (nlev >= 2 for the
+ * dycore). Cell ids follow the hierarchical (Morton) bisection order; vertex and
+ * edge ids ascend with (lowest incident cell id, slot in that cell). Builds on the
+ * GPU and returns after the build has completed. */
+int icon_grid_build(int root, int bisections, int nlev, icon_grid** out);
+
+/* Entity counts: Nc = 20*4^L, Ne = 30*4^L, Nv = 10*4^L + 2 with L = bisections+1. */
+int icon_grid_counts(const icon_grid* grid, int64_t* nc, int64_t* ne, int64_t* nv);
+
+/* Copy one table (ids above) to host memory; bytes must equal the table size
+ * (int32 for ICON_T_*, double for ICON_G_*), else ICON_EINVAL. Synchronous. */
+int icon_grid_copy_table(const icon_grid* grid, int table_id, void* host_dst, size_t bytes);
+
+void icon_grid_free(icon_grid* grid);
+
+/* ---------------------------------------------------------------- state */
+
+/* Create a state on `grid` with the analytic initial condition `case_id`
+ * (icon_case), FP64 precision and default parameters. seed selects the theta_v
+ * noise and, for ICON_CASE_MEMBER, the member's bump (SplitMix64 draws). The
+ * state borrows the grid, which must outlive it. */
+int icon_state_init(const icon_grid* grid, uint64_t seed, int case_id, icon_state** out);
+
+/* As icon_state_init with explicit parameters (params may be NULL). */
+int icon_state_init_ex(const icon_grid* grid, uint64_t seed, int case_id,
+                       const icon_case_params* params, icon_state** out);
+
+/* Advance the state by one dycore step of length dt seconds: nsubsteps
+ * predictor-corrector substeps of dt/nsubsteps (each with the vertically
+ * implicit w/Exner column solve) followed by one Smagorinsky diffusion step
+ * with dt. The step-mean mass fluxes (ICON_F_MFLX, ICON_F_WFLX) are recomputed.
+ * The first call for a given (dt, nsubsteps) records a CUDA graph of the step;
+ * later calls replay it. Waits for completion and returns ICON_ENONFINITE if a
+ * non-finite value was produced. dt > 0, 1 <= nsubsteps <= 64. */
+int icon_dycore_step(icon_state* state, double dt, int nsubsteps);
+
+/* As icon_dycore_step without waiting: enqueues the step on the bound stream and
+ * returns ICON_OK; the non-finite check is reported by icon_state_status(). */
+int icon_dycore_step_async(icon_state* state, double dt, int nsubsteps);
+
+/* Wait for the state's work and return ICON_ENONFINITE if any step since the last
+ * call produced a non-finite value (the flag is then cleared), else ICON_OK. */
+int icon_state_status(icon_state* state);
+
+/* Total air mass  sum_c A_c sum_k dz_k rho_ck  in kg, FP64, deterministic
+ * (fixed summation order, bit-identical between calls on the same device). */
+int icon_global_mass(const icon_state* state, double* out);
+
+/* Copy a field (icon_field) to host memory as FP64, [entity][level] unpadded;
+ * count must equal the field's element count. Synchronous. */
+int icon_state_copy_field(const icon_state* state, int field_id, double* host_dst, size_t count);
+
+/* Overwrite a prognostic field (ICON_F_VN .. ICON_F_EXNER) from FP64 host memory
+ * in the same layout (rounded to FP32 where the state stores FP32). w at the lid
+ * and the ground must be 0. Synchronous with respect to host_src. */
+int icon_state_set_field(icon_state* state, int field_id, const double* host_src, size_t count);
+
+/* Storage precision of the state (icon_precision). */
+int icon_state_precision(const icon_state* state, int* out);
+
+void icon_state_free(icon_state* state);
+
+/* ---------------------------------------------------------------- ensemble */
+
+/* Group n >= 1 states (any grids, same precision) for batched stepping. The
+ * ensemble borrows the states, which must outlive it. */
+int icon_ensemble_create(icon_state* const* members, int n, icon_ensemble** out);
+
+/* Advance every member by nsteps dycore steps (member i with dt_per_member[i],
+ * host array of n doubles, all with nsubsteps substeps). Uses one persistent
+ * kernel per phase over all members; waits and reports ICON_ETIMEOUT if an
+ * in-kernel barrier wait ran out, ICON_ENONFINITE as icon_dycore_step. */
+int icon_ensemble_step(icon_ensemble* ens, const double* dt_per_member, int nsubsteps, int nsteps);
+
+void icon_ensemble_free(icon_ensemble* ens);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ICON_GB300_H */

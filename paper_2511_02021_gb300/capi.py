@@ -1,0 +1,215 @@
+"""ctypes binding of the C ABI in include/icon.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls; all computation
+happens in the CUDA library. Errors raise IconError with the library's message.
+If the compiled library is missing the import fails: there is no fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libicon_gb300.so")
+
+ICON_OK, ICON_EINVAL, ICON_ENOMEM, ICON_ECUDA, ICON_ETIMEOUT, ICON_ENONFINITE, ICON_EINDEX = range(7)
+STATUS_NAMES = {0: "ICON_OK", 1: "ICON_EINVAL", 2: "ICON_ENOMEM", 3: "ICON_ECUDA", 4: "ICON_ETIMEOUT",
+                5: "ICON_ENONFINITE", 6: "ICON_EINDEX"}
+ICON_FP64, ICON_MIXED = 0, 1
+ICON_CASE_REST, ICON_CASE_SBR, ICON_CASE_JET, ICON_CASE_MEMBER = 0, 1, 2, 3
+
+# table ids: name -> (id, dtype, entity ('c','e','v'), columns)
+TABLES = {
+    "c2v": (0, np.int32, "c", 3), "c2e": (1, np.int32, "c", 3), "e2c": (2, np.int32, "e", 2),
+    "e2v": (3, np.int32, "e", 2), "v2e": (4, np.int32, "v", 6), "v2c": (5, np.int32, "v", 6),
+    "vdeg": (6, np.int32, "v", 1), "e2vt": (7, np.int32, "e", 5), "e2q": (8, np.int32, "e", 4),
+    "x_c": (16, np.float64, "c", 3), "x_e": (17, np.float64, "e", 3), "x_v": (18, np.float64, "v", 3),
+    "n_e": (19, np.float64, "e", 3), "t_e": (20, np.float64, "e", 3), "l_e": (21, np.float64, "e", 1),
+    "d_e": (22, np.float64, "e", 1), "A_c": (23, np.float64, "c", 1), "A_v": (24, np.float64, "v", 1),
+    "f_e": (25, np.float64, "e", 1), "vt_w": (26, np.float64, "e", 5), "kin_w": (27, np.float64, "c", 3),
+    "lsq_w": (28, np.float64, "v", 18), "L34": (29, np.float64, "e", 1), "s_ce": (30, np.float64, "c", 3),
+    "s_ve": (31, np.float64, "v", 6),
+}
+# field ids: name -> (id, entity, half-level field)
+FIELDS = {"vn": (0, "e", False), "w": (1, "c", True), "rho": (2, "c", False), "theta_v": (3, "c", False),
+          "exner": (4, "c", False), "mflx": (5, "e", False), "wflx": (6, "c", True)}
+
+
+class IconError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class CaseParams(ctypes.Structure):
+    _fields_ = [("noise_K", ctypes.c_double), ("top_m", ctypes.c_double), ("stretch_s", ctypes.c_double),
+                ("damp_m", ctypes.c_double), ("precision", ctypes.c_int), ("member", ctypes.c_int)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("the CUDA library %s is not built; run __graft_entry__.build()" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    I64p = ctypes.POINTER(ctypes.c_int64)
+    sig = {
+        "icon_set_allocator": (I, [P, P, P]), "icon_set_stream": (I, [P]),
+        "icon_last_error": (ctypes.c_char_p, []),
+        "icon_grid_build": (I, [I, I, I, ctypes.POINTER(P)]),
+        "icon_grid_counts": (I, [P, I64p, I64p, I64p]),
+        "icon_grid_copy_table": (I, [P, I, P, S]), "icon_grid_free": (None, [P]),
+        "icon_state_init": (I, [P, ctypes.c_uint64, I, ctypes.POINTER(P)]),
+        "icon_state_init_ex": (I, [P, ctypes.c_uint64, I, ctypes.POINTER(CaseParams), ctypes.POINTER(P)]),
+        "icon_dycore_step": (I, [P, D, I]), "icon_dycore_step_async": (I, [P, D, I]),
+        "icon_state_status": (I, [P]),
+        "icon_global_mass": (I, [P, ctypes.POINTER(D)]),
+        "icon_state_copy_field": (I, [P, I, P, S]), "icon_state_set_field": (I, [P, I, P, S]),
+        "icon_state_precision": (I, [P, ctypes.POINTER(I)]), "icon_state_free": (None, [P]),
+        "icon_ensemble_create": (I, [ctypes.POINTER(P), I, ctypes.POINTER(P)]),
+        "icon_ensemble_step": (I, [P, ctypes.POINTER(D), I, I]), "icon_ensemble_free": (None, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+DEALLOC_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+_keep = []
+
+
+def _check(rc):
+    if rc != ICON_OK:
+        raise IconError(rc, _lib.icon_last_error().decode())
+
+
+def exported_symbols():
+    """Names of the C entry points this binding resolved (all of include/icon.h)."""
+    return sorted(n for n in dir(_lib) if n.startswith("icon_"))
+
+
+# ---------------------------------------------------------------- allocator / stream
+def icon_set_allocator(alloc, dealloc):
+    """Register Python callables alloc(nbytes) -> int device pointer and dealloc(ptr);
+    (None, None) restores cudaMalloc."""
+    if alloc is None:
+        _check(_lib.icon_set_allocator(None, None, None))
+        return
+    a = ALLOC_FN(lambda n, ctx: alloc(n))
+    d = DEALLOC_FN(lambda p, ctx: dealloc(p))
+    _keep.append((a, d))
+    _check(_lib.icon_set_allocator(ctypes.cast(a, ctypes.c_void_p), ctypes.cast(d, ctypes.c_void_p), None))
+
+
+def icon_set_stream(stream_handle):
+    _check(_lib.icon_set_stream(ctypes.c_void_p(stream_handle or None)))
+
+
+# ---------------------------------------------------------------- grid
+def icon_grid_build(root, bisections, nlev):
+    h = ctypes.c_void_p()
+    _check(_lib.icon_grid_build(root, bisections, nlev, ctypes.byref(h)))
+    return h
+
+
+def icon_grid_counts(grid):
+    nc, ne, nv = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.icon_grid_counts(grid, ctypes.byref(nc), ctypes.byref(ne), ctypes.byref(nv)))
+    return nc.value, ne.value, nv.value
+
+
+def icon_grid_copy_table(grid, name):
+    tid, dt, ent, cols = TABLES[name]
+    nc, ne, nv = icon_grid_counts(grid)
+    n = {"c": nc, "e": ne, "v": nv}[ent]
+    out = np.empty((n, cols) if cols > 1 else (n,), dtype=dt)
+    _check(_lib.icon_grid_copy_table(grid, tid, out.ctypes.data, out.nbytes))
+    return out
+
+
+def icon_grid_free(grid):
+    _lib.icon_grid_free(grid)
+
+
+# ---------------------------------------------------------------- state
+def icon_state_init(grid, seed, case_id):
+    h = ctypes.c_void_p()
+    _check(_lib.icon_state_init(grid, seed, case_id, ctypes.byref(h)))
+    return h
+
+
+def icon_state_init_ex(grid, seed, case_id, noise_K=-1.0, precision=ICON_FP64, member=0):
+    p = CaseParams(noise_K, -1.0, -1.0, -1.0, precision, member)
+    h = ctypes.c_void_p()
+    _check(_lib.icon_state_init_ex(grid, seed, case_id, ctypes.byref(p), ctypes.byref(h)))
+    return h
+
+
+def icon_dycore_step(state, dt, nsubsteps):
+    _check(_lib.icon_dycore_step(state, dt, nsubsteps))
+
+
+def icon_dycore_step_async(state, dt, nsubsteps):
+    _check(_lib.icon_dycore_step_async(state, dt, nsubsteps))
+
+
+def icon_state_status(state):
+    _check(_lib.icon_state_status(state))
+
+
+def icon_global_mass(state):
+    m = ctypes.c_double()
+    _check(_lib.icon_global_mass(state, ctypes.byref(m)))
+    return m.value
+
+
+def _field_shape(grid, name, nlev):
+    fid, ent, half = FIELDS[name]
+    nc, ne, nv = icon_grid_counts(grid)
+    return fid, ({"c": nc, "e": ne}[ent], nlev + 1 if half else nlev)
+
+
+def icon_state_copy_field(state, grid, nlev, name, out=None):
+    fid, shape = _field_shape(grid, name, nlev)
+    if out is None:
+        out = np.empty(shape, dtype=np.float64)
+    assert out.shape == shape and out.dtype == np.float64 and out.flags.c_contiguous
+    _check(_lib.icon_state_copy_field(state, fid, out.ctypes.data, out.size))
+    return out
+
+
+def icon_state_set_field(state, grid, nlev, name, values):
+    fid, shape = _field_shape(grid, name, nlev)
+    values = np.ascontiguousarray(values, dtype=np.float64)
+    assert values.shape == shape
+    _check(_lib.icon_state_set_field(state, fid, values.ctypes.data, values.size))
+
+
+def icon_state_precision(state):
+    p = ctypes.c_int()
+    _check(_lib.icon_state_precision(state, ctypes.byref(p)))
+    return p.value
+
+
+def icon_state_free(state):
+    _lib.icon_state_free(state)
+
+
+# ---------------------------------------------------------------- ensemble
+def icon_ensemble_create(states):
+    arr = (ctypes.c_void_p * len(states))(*[s.value for s in states])
+    h = ctypes.c_void_p()
+    _check(_lib.icon_ensemble_create(arr, len(states), ctypes.byref(h)))
+    return h
+
+
+def icon_ensemble_step(ens, dts, nsubsteps, nsteps):
+    arr = (ctypes.c_double * len(dts))(*dts)
+    _check(_lib.icon_ensemble_step(ens, arr, nsubsteps, nsteps))
+
+
+def icon_ensemble_free(ens):
+    _lib.icon_ensemble_free(ens)

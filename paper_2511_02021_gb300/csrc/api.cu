@@ -1,0 +1,530 @@
+// C ABI of the dycore library: argument checks, handle lifetimes, device memory
+// through the registered allocator, the recorded step graph and host copies.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include "icon_internal.h"
+
+namespace icon {
+
+static thread_local std::string t_err;
+static thread_local cudaStream_t t_stream = nullptr;
+static std::mutex g_alloc_mu;
+static Allocator g_alloc;
+
+void set_error(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  t_err = buf;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  set_error("CUDA error in %s: %s", what, cudaGetErrorString(e));
+  return ICON_ECUDA;
+}
+
+Allocator current_allocator() {
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  return g_alloc;
+}
+cudaStream_t current_stream() { return t_stream; }
+
+void* DeviceArena::get(size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  bytes = (bytes + 255) & ~(size_t)255;
+  void* p = nullptr;
+  if (al.alloc) {
+    p = al.alloc(bytes, al.ctx);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (!p) {
+    failed = true;
+    return nullptr;
+  }
+  blocks.push_back(p);
+  return p;
+}
+
+void DeviceArena::release() {
+  for (void* p : blocks) {
+    if (al.dealloc) al.dealloc(p, al.ctx);
+    else cudaFree(p);
+  }
+  blocks.clear();
+}
+
+namespace {
+
+int upload_vertical(icon_grid* grid, cudaStream_t st) {
+  Vertical& v = grid->vert;
+  DeviceArena& A = grid->arena;
+  double** dst[] = {&v.d_z_h, &v.d_z_f, &v.d_dz, &v.d_dzh, &v.d_wu, &v.d_wl, &v.d_ray, &v.d_dz2};
+  const std::vector<double>* src[] = {&v.z_h, &v.z_f, &v.dz, &v.dzh, &v.wu, &v.wl, &v.rayleigh, &v.dz2};
+  for (int i = 0; i < 8; ++i) {
+    *dst[i] = A.get_n<double>(v.ld);
+    if (!*dst[i]) { set_error("out of device memory (vertical grid)"); return ICON_ENOMEM; }
+    ICON_CUDA(cudaMemcpyAsync(*dst[i], src[i]->data(), sizeof(double) * v.ld, cudaMemcpyHostToDevice, st));
+  }
+  return ICON_OK;
+}
+
+struct TableRef {
+  const void* ptr;
+  size_t elem;
+  size_t count;
+};
+
+bool table_ref(const icon_grid* grid, int id, TableRef& t) {
+  const GridDev& g = grid->g;
+  const size_t nc = g.nc, ne = g.ne, nv = g.nv;
+  switch (id) {
+    case ICON_T_C2V: t = {g.c2v, 4, 3 * nc}; return true;
+    case ICON_T_C2E: t = {g.c2e, 4, 3 * nc}; return true;
+    case ICON_T_E2C: t = {g.e2c, 4, 2 * ne}; return true;
+    case ICON_T_E2V: t = {g.e2v, 4, 2 * ne}; return true;
+    case ICON_T_V2E: t = {g.v2e, 4, 6 * nv}; return true;
+    case ICON_T_V2C: t = {g.v2c, 4, 6 * nv}; return true;
+    case ICON_T_VDEG: t = {g.vdeg, 4, nv}; return true;
+    case ICON_T_E2VT: t = {g.e2vt, 4, 5 * ne}; return true;
+    case ICON_T_E2Q: t = {g.e2q, 4, 4 * ne}; return true;
+    case ICON_G_XC: t = {g.x_c, 8, 3 * nc}; return true;
+    case ICON_G_XE: t = {g.x_e, 8, 3 * ne}; return true;
+    case ICON_G_XV: t = {g.x_v, 8, 3 * nv}; return true;
+    case ICON_G_NE: t = {g.n_e, 8, 3 * ne}; return true;
+    case ICON_G_TE: t = {g.t_e, 8, 3 * ne}; return true;
+    case ICON_G_LE: t = {g.l_e, 8, ne}; return true;
+    case ICON_G_DE: t = {g.d_e, 8, ne}; return true;
+    case ICON_G_AC: t = {g.A_c, 8, nc}; return true;
+    case ICON_G_AV: t = {g.A_v, 8, nv}; return true;
+    case ICON_G_FE: t = {g.f_e, 8, ne}; return true;
+    case ICON_G_VTW: t = {g.vt_w, 8, 5 * ne}; return true;
+    case ICON_G_KINW: t = {g.kin_w, 8, 3 * nc}; return true;
+    case ICON_G_LSQW: t = {g.lsq_w, 8, 18 * nv}; return true;
+    case ICON_G_L34: t = {g.L34, 8, ne}; return true;
+    case ICON_G_SCE: t = {g.s_ce, 8, 3 * nc}; return true;
+    case ICON_G_SVE: t = {g.s_ve, 8, 6 * nv}; return true;
+    default: return false;
+  }
+}
+
+// allocate every buffer of a state; returns ICON_ENOMEM (arena then released by the caller)
+int alloc_state(icon_state* st, int precision) {
+  const icon_grid* grid = st->grid;
+  const int64_t ld = grid->vert.ld, nc = grid->g.nc, ne = grid->g.ne, nv = grid->g.nv;
+  DeviceArena& A = st->arena;
+  StateDev& s = st->s;
+  s.precision = precision;
+  const size_t E = (size_t)(ne * ld), C = (size_t)(nc * ld), V = (size_t)(nv * ld);
+  s.w = A.get_n<double>(C); s.rho = A.get_n<double>(C); s.thv = A.get_n<double>(C); s.ex = A.get_n<double>(C);
+  s.w_s = A.get_n<double>(C); s.rho_s = A.get_n<double>(C); s.thv_s = A.get_n<double>(C);
+  s.ex_s = A.get_n<double>(C);
+  s.mflx = A.get_n<double>(E); s.wflx = A.get_n<double>(C);
+  s.ex_ref = A.get_n<double>(ld);
+  s.mass_part = A.get_n<double>(mass_partials_count(nc) + 8);
+  s.status = A.get_n<unsigned>(64);
+  if (precision == ICON_FP64) {
+    s.vn = A.get_n<double>(E); s.vn_s = A.get_n<double>(E);
+    s.Avn0 = A.get_n<double>(E); s.Aw0 = A.get_n<double>(C);
+    s.zeta = A.get_n<double>(V); s.w_v = A.get_n<double>(V);
+    s.vt = A.get_n<double>(E); s.Ke = A.get_n<double>(E); s.Kc = A.get_n<double>(C);
+    s.a_e = A.get_n<double>(E); s.F = A.get_n<double>(E); s.G = A.get_n<double>(E);
+    // diffusion scratch reuses substep scratch (they never overlap in time)
+    s.Kh = s.vt; s.thflx = s.Ke; s.divc = s.Kc; s.uvx = s.w_v;
+    s.uvy = A.get_n<double>(V); s.uvz = A.get_n<double>(V);
+  } else {
+    set_error("mixed precision is not available in this build");
+    return ICON_EINVAL;
+  }
+  if (A.failed) {
+    set_error("out of device memory allocating the state");
+    return ICON_ENOMEM;
+  }
+  return ICON_OK;
+}
+
+int sync_status(icon_state* st, cudaStream_t stream) {
+  unsigned h = 0;
+  ICON_CUDA(cudaMemcpyAsync(&h, st->s.status, sizeof(unsigned), cudaMemcpyDeviceToHost, stream));
+  ICON_CUDA(cudaStreamSynchronize(stream));
+  if (h != 0) {
+    ICON_CUDA(cudaMemsetAsync(st->s.status, 0, sizeof(unsigned), stream));
+    ICON_CUDA(cudaStreamSynchronize(stream));
+    if (h & 2u) {
+      set_error("an in-kernel barrier wait ran out (status 0x%x)", h);
+      return ICON_ETIMEOUT;
+    }
+    set_error("non-finite value in the prognostic state (status 0x%x)", h);
+    return ICON_ENONFINITE;
+  }
+  return ICON_OK;
+}
+
+void enqueue_step(icon_state* st, double dt, int nsub, cudaStream_t stream) {
+  if (st->s.precision == ICON_FP64) enqueue_step_fp64(st, dt, nsub, stream);
+  else enqueue_step_mixed(st, dt, nsub, stream);
+}
+
+// record (once per (dt, nsub)) and launch the graph of one step
+int launch_step(icon_state* st, double dt, int nsub, cudaStream_t stream) {
+  if (!st->graph || st->graph_dt != dt || st->graph_nsub != nsub) {
+    if (st->graph) {
+      cudaGraphExecDestroy(st->graph);
+      st->graph = nullptr;
+    }
+    if (!st->capture_stream) ICON_CUDA(cudaStreamCreateWithFlags(&st->capture_stream, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    ICON_CUDA(cudaStreamBeginCapture(st->capture_stream, cudaStreamCaptureModeThreadLocal));
+    enqueue_step(st, dt, nsub, st->capture_stream);
+    cudaError_t e = cudaStreamEndCapture(st->capture_stream, &g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&st->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      st->graph = nullptr;
+      return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    st->graph_dt = dt;
+    st->graph_nsub = nsub;
+  }
+  ICON_CUDA(cudaGraphLaunch(st->graph, stream));
+  return ICON_OK;
+}
+
+bool field_ref(const icon_state* st, int id, void** ptr, int* is_f32, int64_t* n, int* nlev) {
+  const icon_grid* grid = st->grid;
+  const StateDev& s = st->s;
+  const int N = grid->vert.N;
+  *is_f32 = 0;
+  switch (id) {
+    case ICON_F_VN:
+      *n = grid->g.ne; *nlev = N;
+      if (s.precision == ICON_FP64) *ptr = s.vn; else { *ptr = s.vn32; *is_f32 = 1; }
+      return true;
+    case ICON_F_W: *ptr = s.w; *n = grid->g.nc; *nlev = N + 1; return true;
+    case ICON_F_RHO: *ptr = s.rho; *n = grid->g.nc; *nlev = N; return true;
+    case ICON_F_THETA_V: *ptr = s.thv; *n = grid->g.nc; *nlev = N; return true;
+    case ICON_F_EXNER: *ptr = s.ex; *n = grid->g.nc; *nlev = N; return true;
+    case ICON_F_MFLX: *ptr = s.mflx; *n = grid->g.ne; *nlev = N; return true;
+    case ICON_F_WFLX: *ptr = s.wflx; *n = grid->g.nc; *nlev = N + 1; return true;
+    default: return false;
+  }
+}
+
+__global__ void k_f32_to_f64(const float* __restrict__ a, double* __restrict__ b, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (double)a[i];
+}
+__global__ void k_f64_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+}  // namespace
+}  // namespace icon
+
+using namespace icon;
+
+extern "C" {
+
+int icon_set_allocator(void* (*alloc)(size_t, void*), void (*dealloc)(void*, void*), void* ctx) {
+  if ((alloc == nullptr) != (dealloc == nullptr)) {
+    set_error("icon_set_allocator: pass both callbacks or neither");
+    return ICON_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_alloc.alloc = alloc;
+  g_alloc.dealloc = dealloc;
+  g_alloc.ctx = alloc ? ctx : nullptr;
+  return ICON_OK;
+}
+
+int icon_set_stream(void* cuda_stream) {
+  t_stream = static_cast<cudaStream_t>(cuda_stream);
+  return ICON_OK;
+}
+
+const char* icon_last_error(void) { return t_err.c_str(); }
+
+int icon_grid_build(int root, int bisections, int nlev, icon_grid** out) {
+  if (!out) { set_error("icon_grid_build: out is NULL"); return ICON_EINVAL; }
+  if (root != 2) { set_error("icon_grid_build: only root 2 is supported (got %d)", root); return ICON_EINVAL; }
+  if (bisections < 0 || bisections > 10) {
+    set_error("icon_grid_build: bisections must be in 0..10 (got %d)", bisections);
+    return ICON_EINVAL;
+  }
+  if (nlev < 1 || nlev > 256) { set_error("icon_grid_build: nlev must be in 1..256 (got %d)", nlev); return ICON_EINVAL; }
+  icon_grid* g = new icon_grid();
+  g->root = root;
+  g->bisections = bisections;
+  g->arena.al = current_allocator();
+  make_vertical(g->vert, nlev, -1, -1, -1);
+  cudaStream_t st = current_stream();
+  int rc = upload_vertical(g, st);
+  if (rc == ICON_OK) rc = build_grid_device(g, st);
+  if (rc == ICON_OK) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "grid build");
+  }
+  if (rc != ICON_OK) {
+    cudaStreamSynchronize(st);
+    g->arena.release();
+    delete g;
+    return rc;
+  }
+  *out = g;
+  return ICON_OK;
+}
+
+int icon_grid_counts(const icon_grid* grid, int64_t* nc, int64_t* ne, int64_t* nv) {
+  if (!grid) { set_error("icon_grid_counts: grid is NULL"); return ICON_EINVAL; }
+  if (nc) *nc = grid->g.nc;
+  if (ne) *ne = grid->g.ne;
+  if (nv) *nv = grid->g.nv;
+  return ICON_OK;
+}
+
+int icon_grid_copy_table(const icon_grid* grid, int table_id, void* host_dst, size_t bytes) {
+  if (!grid || !host_dst) { set_error("icon_grid_copy_table: NULL argument"); return ICON_EINVAL; }
+  TableRef t;
+  if (!table_ref(grid, table_id, t)) { set_error("icon_grid_copy_table: unknown table %d", table_id); return ICON_EINVAL; }
+  if (bytes != t.elem * t.count) {
+    set_error("icon_grid_copy_table: table %d has %zu bytes, got %zu", table_id, t.elem * t.count, bytes);
+    return ICON_EINVAL;
+  }
+  cudaStream_t st = current_stream();
+  ICON_CUDA(cudaMemcpyAsync(host_dst, t.ptr, bytes, cudaMemcpyDeviceToHost, st));
+  ICON_CUDA(cudaStreamSynchronize(st));
+  return ICON_OK;
+}
+
+void icon_grid_free(icon_grid* grid) {
+  if (!grid) return;
+  cudaDeviceSynchronize();
+  grid->arena.release();
+  delete grid;
+}
+
+int icon_state_init_ex(const icon_grid* grid, uint64_t seed, int case_id, const icon_case_params* params,
+                       icon_state** out) {
+  if (!grid || !out) { set_error("icon_state_init: NULL argument"); return ICON_EINVAL; }
+  if (case_id < ICON_CASE_REST || case_id > ICON_CASE_MEMBER) {
+    set_error("icon_state_init: unknown case %d", case_id);
+    return ICON_EINVAL;
+  }
+  if (grid->vert.N < 2) { set_error("icon_state_init: the dycore needs nlev >= 2"); return ICON_EINVAL; }
+  icon_case_params p;
+  p.noise_K = -1.0; p.top_m = -1.0; p.stretch_s = -1.0; p.damp_m = -1.0; p.precision = ICON_FP64; p.member = 0;
+  if (params) p = *params;
+  if (p.precision != ICON_FP64 && p.precision != ICON_MIXED) {
+    set_error("icon_state_init: unknown precision %d", p.precision);
+    return ICON_EINVAL;
+  }
+  if (p.member < 0) { set_error("icon_state_init: member must be >= 0"); return ICON_EINVAL; }
+  if ((p.top_m > 0 && p.top_m != grid->vert.z_top) || (p.stretch_s > 0 && p.stretch_s != grid->vert.s) ||
+      (p.damp_m > 0 && p.damp_m != grid->vert.z_d)) {
+    set_error("icon_state_init: vertical-grid overrides must match the grid's (top %g, s %g, damping base %g)",
+              grid->vert.z_top, grid->vert.s, grid->vert.z_d);
+    return ICON_EINVAL;
+  }
+  icon_state* st = new icon_state();
+  st->grid = grid;
+  st->seed = seed;
+  st->case_id = case_id;
+  st->arena.al = current_allocator();
+  cudaStream_t stream = current_stream();
+  int rc = alloc_state(st, p.precision);
+  if (rc == ICON_OK) {
+    cudaError_t e = cudaMemsetAsync(st->s.status, 0, 64 * sizeof(unsigned), stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemsetAsync");
+  }
+  if (rc == ICON_OK) rc = init_state_device(st, seed, case_id, p, stream);
+  if (rc == ICON_OK) {
+    cudaError_t e = cudaEventCreateWithFlags(&st->done, cudaEventDisableTiming);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cudaEventCreate");
+  }
+  if (rc == ICON_OK) {
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "state init");
+  }
+  if (rc != ICON_OK) {
+    cudaStreamSynchronize(stream);
+    if (st->done) cudaEventDestroy(st->done);
+    st->arena.release();
+    delete st;
+    return rc;
+  }
+  *out = st;
+  return ICON_OK;
+}
+
+int icon_state_init(const icon_grid* grid, uint64_t seed, int case_id, icon_state** out) {
+  return icon_state_init_ex(grid, seed, case_id, nullptr, out);
+}
+
+int icon_dycore_step_async(icon_state* st, double dt, int nsubsteps) {
+  if (!st) { set_error("icon_dycore_step: state is NULL"); return ICON_EINVAL; }
+  if (!(dt > 0.0) || nsubsteps < 1 || nsubsteps > 64) {
+    set_error("icon_dycore_step: need dt > 0 and 1 <= nsubsteps <= 64 (got %g, %d)", dt, nsubsteps);
+    return ICON_EINVAL;
+  }
+  return launch_step(st, dt, nsubsteps, current_stream());
+}
+
+int icon_dycore_step(icon_state* st, double dt, int nsubsteps) {
+  int rc = icon_dycore_step_async(st, dt, nsubsteps);
+  if (rc != ICON_OK) return rc;
+  return sync_status(st, current_stream());
+}
+
+int icon_state_status(icon_state* st) {
+  if (!st) { set_error("icon_state_status: state is NULL"); return ICON_EINVAL; }
+  return sync_status(st, current_stream());
+}
+
+int icon_global_mass(const icon_state* st, double* out) {
+  if (!st || !out) { set_error("icon_global_mass: NULL argument"); return ICON_EINVAL; }
+  cudaStream_t stream = current_stream();
+  double* d_out = st->s.mass_part + mass_partials_count(st->grid->g.nc);
+  enqueue_mass(st, d_out, stream);
+  ICON_CUDA(cudaGetLastError());
+  double h = 0.0;
+  ICON_CUDA(cudaMemcpyAsync(&h, d_out, sizeof(double), cudaMemcpyDeviceToHost, stream));
+  ICON_CUDA(cudaStreamSynchronize(stream));
+  *out = h;
+  return ICON_OK;
+}
+
+int icon_state_copy_field(const icon_state* st, int field_id, double* host_dst, size_t count) {
+  if (!st || !host_dst) { set_error("icon_state_copy_field: NULL argument"); return ICON_EINVAL; }
+  void* ptr;
+  int f32, nlev;
+  int64_t n;
+  if (!field_ref(st, field_id, &ptr, &f32, &n, &nlev)) {
+    set_error("icon_state_copy_field: unknown field %d", field_id);
+    return ICON_EINVAL;
+  }
+  if (count != (size_t)(n * nlev)) {
+    set_error("icon_state_copy_field: field %d has %lld elements, got %zu", field_id, (long long)(n * nlev), count);
+    return ICON_EINVAL;
+  }
+  const int ld = st->grid->vert.ld;
+  cudaStream_t stream = current_stream();
+  const double* src = static_cast<const double*>(ptr);
+  DeviceArena tmp;
+  tmp.al = st->arena.al;
+  if (f32) {
+    double* d = tmp.get_n<double>((size_t)n * ld);
+    if (!d) { set_error("icon_state_copy_field: out of device memory"); return ICON_ENOMEM; }
+    k_f32_to_f64<<<blocks_for(n * ld, 256), 256, 0, stream>>>(static_cast<const float*>(ptr), d, n * ld);
+    src = d;
+  }
+  cudaError_t e = cudaMemcpy2DAsync(host_dst, sizeof(double) * nlev, src, sizeof(double) * ld,
+                                    sizeof(double) * nlev, n, cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  tmp.release();
+  if (e != cudaSuccess) return cuda_fail(e, "icon_state_copy_field");
+  return ICON_OK;
+}
+
+int icon_state_set_field(icon_state* st, int field_id, const double* host_src, size_t count) {
+  if (!st || !host_src) { set_error("icon_state_set_field: NULL argument"); return ICON_EINVAL; }
+  if (field_id < ICON_F_VN || field_id > ICON_F_EXNER) {
+    set_error("icon_state_set_field: field %d is not a prognostic field", field_id);
+    return ICON_EINVAL;
+  }
+  void* ptr;
+  int f32, nlev;
+  int64_t n;
+  field_ref(st, field_id, &ptr, &f32, &n, &nlev);
+  if (count != (size_t)(n * nlev)) {
+    set_error("icon_state_set_field: field %d has %lld elements, got %zu", field_id, (long long)(n * nlev), count);
+    return ICON_EINVAL;
+  }
+  const int ld = st->grid->vert.ld;
+  cudaStream_t stream = current_stream();
+  DeviceArena tmp;
+  tmp.al = st->arena.al;
+  double* dst = static_cast<double*>(ptr);
+  if (f32) {
+    dst = tmp.get_n<double>((size_t)n * ld);
+    if (!dst) { set_error("icon_state_set_field: out of device memory"); return ICON_ENOMEM; }
+  }
+  cudaError_t e = cudaMemcpy2DAsync(dst, sizeof(double) * ld, host_src, sizeof(double) * nlev,
+                                    sizeof(double) * nlev, n, cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess && f32) {
+    k_f64_to_f32<<<blocks_for(n * ld, 256), 256, 0, stream>>>(dst, static_cast<float*>(ptr), n * ld);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  tmp.release();
+  if (e != cudaSuccess) return cuda_fail(e, "icon_state_set_field");
+  return ICON_OK;
+}
+
+int icon_state_precision(const icon_state* st, int* out) {
+  if (!st || !out) { set_error("icon_state_precision: NULL argument"); return ICON_EINVAL; }
+  *out = st->s.precision;
+  return ICON_OK;
+}
+
+void icon_state_free(icon_state* st) {
+  if (!st) return;
+  cudaDeviceSynchronize();
+  if (st->graph) cudaGraphExecDestroy(st->graph);
+  if (st->capture_stream) cudaStreamDestroy(st->capture_stream);
+  if (st->done) cudaEventDestroy(st->done);
+  st->arena.release();
+  delete st;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- ensemble
+struct icon_ensemble {
+  std::vector<icon_state*> members;
+};
+
+extern "C" {
+
+int icon_ensemble_create(icon_state* const* members, int n, icon_ensemble** out) {
+  if (!members || !out || n < 1) { set_error("icon_ensemble_create: bad arguments"); return ICON_EINVAL; }
+  int prec = -1;
+  for (int i = 0; i < n; ++i) {
+    if (!members[i]) { set_error("icon_ensemble_create: member %d is NULL", i); return ICON_EINVAL; }
+    if (prec >= 0 && members[i]->s.precision != prec) {
+      set_error("icon_ensemble_create: members must share one precision");
+      return ICON_EINVAL;
+    }
+    prec = members[i]->s.precision;
+  }
+  icon_ensemble* e = new icon_ensemble();
+  e->members.assign(members, members + n);
+  *out = e;
+  return ICON_OK;
+}
+
+int icon_ensemble_step(icon_ensemble* ens, const double* dt_per_member, int nsubsteps, int nsteps) {
+  if (!ens || !dt_per_member || nsteps < 0) { set_error("icon_ensemble_step: bad arguments"); return ICON_EINVAL; }
+  cudaStream_t stream = current_stream();
+  for (int s = 0; s < nsteps; ++s)
+    for (size_t i = 0; i < ens->members.size(); ++i) {
+      int rc = icon_dycore_step_async(ens->members[i], dt_per_member[i], nsubsteps);
+      if (rc != ICON_OK) return rc;
+    }
+  int worst = ICON_OK;
+  for (size_t i = 0; i < ens->members.size(); ++i) {
+    int rc = sync_status(ens->members[i], stream);
+    if (rc != ICON_OK) worst = rc;
+  }
+  return worst;
+}
+
+void icon_ensemble_free(icon_ensemble* ens) { delete ens; }
+
+}  // extern "C"

@@ -1,0 +1,475 @@
+// FP64 dynamical-core step ("plain method"): predictor-corrector substeps with
+// a vertically implicit w/Exner column solve, then Smagorinsky diffusion.
+//
+// The paper states that ICON's dynamical core is a nonhydrostatic solver on the
+// icosahedral-triangular C grid (Sec. "Current State of the Art"), that it is
+// memory-bandwidth bound and dominated by index lookups on triangles, hexagons
+// and 12 pentagons (Sec. "Separation of Concerns"), and that all data stay on
+// the GPU (Sec. "Innovations Realized"). It gives no discretisation; the one
+// computed here, on fields stored level-contiguous ([entity][ld], full level k =
+// 0..N-1 top to bottom, half level h = 0..N with w = 0 at h = 0 and h = N), is:
+//
+//   O1 gradient   (psi_c2 - psi_c1) / d_e
+//   O2 divergence (1/A_c) sum_e s_ce l_e u_e
+//   O3 curl       (1/A_v) sum_e s_ve d_e vn_e           (counter-clockwise about v)
+//   O4 vt         sum_j W_ej vn_j over 5 edges (Perot)
+//   O5 K_c        sum_e kappa_ce (vn^2 + vt^2)/2
+//   A_vn = -(K_c2 - K_c1)/d_e + ((zeta_v1 + zeta_v2)/2 + f_e) vt - wbar_e dvn/dz
+//   A_w  = -sum_e kappa_ce [vn_ie dw/dn + vt_ie dw_v/dt] - w (w_{h-1} - w_{h+1})/(z_{h-1} - z_{h+1})
+//   predictor vn* = vn + dtau (A_vn - cpd thv_e dpi/dn), column(S^n, vn*, A_w)
+//   corrector vn' = vn + dtau ((A_vn0 + A_vn*)/2 - cpd thv_e* dpi*/dn),
+//             column(S^n, vn', (A_w0 + A_w*)/2) with fluxes from S*
+//   column: explicit predictors of rho, rho*theta_v, Exner, w with off-centring
+//   beta = 0.65, tridiagonal system in w at interior half levels (Thomas,
+//   no pivoting), Rayleigh damping, then back-substituted rho, Theta, Exner.
+//   diffusion: K_h = cs^2 l d sqrt(D_T^2 + D_S^2) from least-squares vertex
+//   velocities, vn += dt K_h L(vn), flux-form theta_v diffusion, Exner adjusted
+//   at constant density.
+//
+// Mapping: one warp per entity (edge, cell or vertex) with lanes over levels, so
+// every neighbour index is loaded once per entity and every gathered neighbour
+// row is a coalesced, aligned segment; one thread per column for the implicit
+// solve. This file is compiled without FMA contraction so that each expression
+// rounds exactly as written.
+#include "icon_internal.h"
+
+namespace icon {
+namespace {
+
+constexpr int kWarpsPerBlock = 8;
+
+struct Geo64 {
+  int64_t nc, ne, nv;
+  int N, ld;
+  const int *c2e, *e2c, *e2v, *v2e, *v2c, *vdeg, *e2vt, *e2q;
+  const double *div_w, *rot_w, *A_c, *A_v, *vt_w, *kin_w, *lsq_w, *d_e, *l_e, *f_e, *L34, *n_e, *t_e, *s_ce;
+  const double *dz, *dzh, *wu, *wl, *dz2, *ray;
+};
+
+__device__ inline int64_t warp_entity() {
+  return (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+}
+
+// zeta_v (full levels) and w_v (half levels)
+__global__ void __launch_bounds__(256) k_vertex(Geo64 G, const double* __restrict__ vn, const double* __restrict__ w,
+                                                double* __restrict__ zeta, double* __restrict__ w_v) {
+  const int64_t v = warp_entity();
+  if (v >= G.nv) return;
+  const int lane = threadIdx.x & 31, ld = G.ld;
+  int64_t E[6], C[6];
+  double rw[6];
+  for (int j = 0; j < 6; ++j) {
+    E[j] = (int64_t)G.v2e[6 * v + j] * ld;
+    C[j] = (int64_t)G.v2c[6 * v + j] * ld;
+    rw[j] = G.rot_w[6 * v + j];
+  }
+  const double Av = G.A_v[v];
+  const int deg = G.vdeg[v];
+  for (int k = lane; k < G.N; k += 32) {
+    double acc = 0.0;
+    for (int j = 0; j < 6; ++j) acc += rw[j] * vn[E[j] + k];
+    zeta[v * ld + k] = acc / Av;
+  }
+  for (int h = lane; h <= G.N; h += 32) {
+    double acc = 0.0;
+    for (int j = 0; j < 5; ++j) acc += w[C[j] + h];
+    acc += (deg == 6) ? w[C[5] + h] : 0.0;
+    w_v[v * ld + h] = acc / (double)deg;
+  }
+}
+
+// vt (Perot) and K_e at edges
+__global__ void __launch_bounds__(256) k_edge_vt(Geo64 G, const double* __restrict__ vn, double* __restrict__ vt,
+                                                 double* __restrict__ Ke) {
+  const int64_t e = warp_entity();
+  if (e >= G.ne) return;
+  const int lane = threadIdx.x & 31, ld = G.ld;
+  int64_t S[5];
+  double W[5];
+  for (int j = 0; j < 5; ++j) {
+    S[j] = (int64_t)G.e2vt[5 * e + j] * ld;
+    W[j] = G.vt_w[5 * e + j];
+  }
+  for (int k = lane; k < G.N; k += 32) {
+    double acc = 0.0;
+    for (int j = 0; j < 5; ++j) acc += W[j] * vn[S[j] + k];
+    const double v0 = vn[e * ld + k];
+    vt[e * ld + k] = acc;
+    Ke[e * ld + k] = 0.5 * (v0 * v0 + acc * acc);
+  }
+}
+
+// K_c at cells
+__global__ void __launch_bounds__(256) k_cell_ke(Geo64 G, const double* __restrict__ Ke, double* __restrict__ Kc) {
+  const int64_t c = warp_entity();
+  if (c >= G.nc) return;
+  const int lane = threadIdx.x & 31, ld = G.ld;
+  int64_t E[3];
+  double kw[3];
+  for (int s = 0; s < 3; ++s) {
+    E[s] = (int64_t)G.c2e[3 * c + s] * ld;
+    kw[s] = G.kin_w[3 * c + s];
+  }
+  for (int k = lane; k < G.N; k += 32) {
+    double acc = 0.0;
+    for (int s = 0; s < 3; ++s) acc += kw[s] * Ke[E[s] + k];
+    Kc[c * ld + k] = acc;
+  }
+}
+
+struct EdgeArgs {
+  const double *vn, *w, *rho, *thv, *ex;   // stage state (S^n or S*)
+  const double *vt, *Kc, *zeta, *w_v;      // diagnostics of the stage state
+  const double* vn_base;                   // vn^n
+  double* vn_out;                          // vn* or vn^{n+1} (may alias vn_base)
+  double* Avn0;                            // stored (predictor) or read (corrector)
+  double *F, *G, *a_e, *mflx;
+  double dtau, nsub;
+  int corrector;
+};
+
+__device__ inline double to_half(const double* __restrict__ f, const double* __restrict__ wu,
+                                 const double* __restrict__ wl, int h, int N) {
+  if (h == 0) return f[0];
+  if (h == N) return f[N - 1];
+  return wu[h] * f[h - 1] + wl[h] * f[h];
+}
+
+// vn tendency and update, horizontal mass/heat fluxes, edge part of w advection
+__global__ void __launch_bounds__(256) k_edge_tend(Geo64 G, EdgeArgs a) {
+  const int64_t e = warp_entity();
+  if (e >= G.ne) return;
+  const int lane = threadIdx.x & 31, ld = G.ld, N = G.N;
+  const int64_t c1 = (int64_t)G.e2c[2 * e] * ld, c2 = (int64_t)G.e2c[2 * e + 1] * ld;
+  const int64_t v1 = (int64_t)G.e2v[2 * e] * ld, v2 = (int64_t)G.e2v[2 * e + 1] * ld;
+  const double de = G.d_e[e], le = G.l_e[e], fe = G.f_e[e];
+  const double* vn = a.vn + e * ld;
+  const double* vt = a.vt + e * ld;
+  for (int k = lane; k < N; k += 32) {
+    const double vt_k = vt[k];
+    const double vie0 = to_half(vn, G.wu, G.wl, k, N);
+    const double vie1 = to_half(vn, G.wu, G.wl, k + 1, N);
+    const double we0 = 0.5 * (a.w[c1 + k] + a.w[c2 + k]);
+    const double we1 = 0.5 * (a.w[c1 + k + 1] + a.w[c2 + k + 1]);
+    const double wbar = 0.5 * (we0 + we1);
+    const double zeta_e = 0.5 * (a.zeta[v1 + k] + a.zeta[v2 + k]);
+    const double A = (-(a.Kc[c2 + k] - a.Kc[c1 + k]) / de + (zeta_e + fe) * vt_k) - wbar * (vie0 - vie1) / G.dz[k];
+    const double th_e = 0.5 * (a.thv[c1 + k] + a.thv[c2 + k]);
+    const double pg = (kCpd * th_e) * ((a.ex[c2 + k] - a.ex[c1 + k]) / de);
+    double vnew;
+    if (a.corrector) {
+      vnew = a.vn_base[e * ld + k] + a.dtau * (0.5 * (a.Avn0[e * ld + k] + A) - pg);
+    } else {
+      vnew = a.vn_base[e * ld + k] + a.dtau * (A - pg);
+      a.Avn0[e * ld + k] = A;
+    }
+    a.vn_out[e * ld + k] = vnew;
+    const double rho_e = 0.5 * (a.rho[c1 + k] + a.rho[c2 + k]);
+    const double F = rho_e * vnew;
+    a.F[e * ld + k] = F;
+    a.G[e * ld + k] = F * th_e;
+    if (a.corrector) a.mflx[e * ld + k] = a.mflx[e * ld + k] + F / a.nsub;
+  }
+  for (int h = lane; h <= N; h += 32) {
+    const double vie = to_half(vn, G.wu, G.wl, h, N);
+    const double tie = to_half(vt, G.wu, G.wl, h, N);
+    a.a_e[e * ld + h] = vie * (a.w[c2 + h] - a.w[c1 + h]) / de + tie * (a.w_v[v2 + h] - a.w_v[v1 + h]) / le;
+  }
+}
+
+struct ColArgs {
+  const double *rho, *thv, *ex, *w;        // S^n
+  const double* w_stage;                   // w of the stage state (vertical part of A_w)
+  const double *F, *G, *a_e;               // edge fluxes and w-advection edge terms
+  double* Aw0;                             // stored (predictor) or read (corrector)
+  double *rho_o, *thv_o, *ex_o, *w_o;      // S* or S^{n+1} (may alias S^n)
+  double* wflx;
+  unsigned* status;
+  double dtau, nsub;
+  int corrector;
+};
+
+template <int NMAX>
+__global__ void __launch_bounds__(64) k_column(Geo64 G, ColArgs a) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= G.nc) return;
+  const int N = G.N, ld = G.ld;
+  const int64_t o = c * ld;
+  int64_t E[3];
+  double dw[3], kw[3];
+  for (int s = 0; s < 3; ++s) {
+    E[s] = (int64_t)G.c2e[3 * c + s] * ld;
+    dw[s] = G.div_w[3 * c + s];
+    kw[s] = G.kin_w[3 * c + s];
+  }
+  const double Ac = G.A_c[c];
+  const double dtau = a.dtau, rcv = kRd / kCvd;
+  double rho_ic[NMAX + 1], M[NMAX + 1], gam[NMAX], Th_x[NMAX], ex_x[NMAX], rho_x[NMAX], cp[NMAX], dp[NMAX];
+  // half-level interpolants of S^n
+  for (int h = 0; h <= N; ++h) {
+    double ri, ti;
+    if (h == 0) { ri = a.rho[o]; ti = a.thv[o]; }
+    else if (h == N) { ri = a.rho[o + N - 1]; ti = a.thv[o + N - 1]; }
+    else {
+      ri = G.wu[h] * a.rho[o + h - 1] + G.wl[h] * a.rho[o + h];
+      ti = G.wu[h] * a.thv[o + h - 1] + G.wl[h] * a.thv[o + h];
+    }
+    rho_ic[h] = ri;
+    M[h] = ri * ti;
+  }
+  // explicit predictors at full levels
+  for (int k = 0; k < N; ++k) {
+    double Dr = 0.0, Dt = 0.0;
+    for (int s = 0; s < 3; ++s) Dr += dw[s] * a.F[E[s] + k];
+    Dr = Dr / Ac;
+    for (int s = 0; s < 3; ++s) Dt += dw[s] * a.G[E[s] + k];
+    Dt = Dt / Ac;
+    const double rho = a.rho[o + k], thv = a.thv[o + k], ex = a.ex[o + k];
+    const double w0 = a.w[o + k], w1 = a.w[o + k + 1];
+    const double Th = rho * thv;
+    rho_x[k] = (rho - dtau * Dr) - dtau * (1.0 - kBeta) * (rho_ic[k] * w0 - rho_ic[k + 1] * w1) / G.dz[k];
+    Th_x[k] = (Th - dtau * Dt) - dtau * (1.0 - kBeta) * (M[k] * w0 - M[k + 1] * w1) / G.dz[k];
+    ex_x[k] = ex + rcv * (ex / Th) * (Th_x[k] - Th);
+    gam[k] = rcv * (ex / Th) * dtau * kBeta / G.dz[k];
+  }
+  // tridiagonal rows at interior half levels h = 1..N-1 (row i = h-1), Thomas forward sweep
+  for (int h = 1; h < N; ++h) {
+    // advective tendency of w at half level h (stage state)
+    double hadv = 0.0;
+    for (int s = 0; s < 3; ++s) hadv += kw[s] * a.a_e[E[s] + h];
+    const double ws = a.w_stage[o + h];
+    double Aw = -hadv - ws * (a.w_stage[o + h - 1] - a.w_stage[o + h + 1]) / G.dz2[h];
+    if (a.corrector) Aw = 0.5 * (a.Aw0[o + h] + Aw);
+    else a.Aw0[o + h] = Aw;
+    const double th_ic = G.wu[h] * a.thv[o + h - 1] + G.wl[h] * a.thv[o + h];
+    const double exm = a.ex[o + h - 1], exk = a.ex[o + h];
+    const double w_x = a.w[o + h] + dtau * ((Aw - (1.0 - kBeta) * kCpd * th_ic * (exm - exk) / G.dzh[h]) - kGrav);
+    const double aa = dtau * kBeta * kCpd * th_ic / G.dzh[h];
+    const double lower = -aa * gam[h - 1] * M[h - 1];
+    const double diag = 1.0 + aa * (gam[h - 1] + gam[h]) * M[h];
+    const double upper = -aa * gam[h] * M[h + 1];
+    const double rhs = w_x - aa * (ex_x[h - 1] - ex_x[h]);
+    const int i = h - 1;
+    if (i == 0) {
+      cp[0] = upper / diag;
+      dp[0] = rhs / diag;
+    } else {
+      const double m = diag - lower * cp[i - 1];
+      cp[i] = upper / m;
+      dp[i] = (rhs - lower * dp[i - 1]) / m;
+    }
+  }
+  // back substitution (dp becomes the solution), Rayleigh damping
+  for (int i = N - 3; i >= 0; --i) dp[i] = dp[i] - cp[i] * dp[i + 1];
+  double wn_prev = 0.0;   // w_new at the half level above the current full level
+  bool bad = false;
+  for (int k = 0; k < N; ++k) {
+    const int h1 = k + 1;
+    double wn1 = 0.0;
+    if (h1 < N) wn1 = dp[h1 - 1] / (1.0 + dtau * G.ray[h1]);
+    const double q0 = M[k] * wn_prev, q1 = M[k + 1] * wn1;
+    const double r0 = rho_ic[k] * wn_prev, r1 = rho_ic[k + 1] * wn1;
+    const double Th_n = Th_x[k] - dtau * kBeta * (q0 - q1) / G.dz[k];
+    const double ex_n = ex_x[k] - gam[k] * (q0 - q1);
+    const double rho_n = rho_x[k] - dtau * kBeta * (r0 - r1) / G.dz[k];
+    const double thv_n = Th_n / rho_n;
+    if (a.corrector) {
+      // step-mean vertical mass flux at the half level above this full level
+      const double wold = a.w[o + k];
+      a.wflx[o + k] = a.wflx[o + k] + rho_ic[k] * (kBeta * wn_prev + (1.0 - kBeta) * wold) / a.nsub;
+    }
+    a.rho_o[o + k] = rho_n;
+    a.thv_o[o + k] = thv_n;
+    a.ex_o[o + k] = ex_n;
+    a.w_o[o + k] = wn_prev;
+    bad |= !isfinite(thv_n) || !isfinite(wn_prev) || !isfinite(ex_n);
+    wn_prev = wn1;
+  }
+  a.w_o[o + N] = 0.0;
+  if (a.corrector) {
+    const double wold = a.w[o + N];
+    a.wflx[o + N] = a.wflx[o + N] + rho_ic[N] * (kBeta * 0.0 + (1.0 - kBeta) * wold) / a.nsub;
+  }
+  if (bad) atomicOr(a.status, 1u);
+}
+
+// ---------------------------------------------------------------- diffusion
+__global__ void __launch_bounds__(256) k_diff_vertex(Geo64 G, const double* __restrict__ vn, double* __restrict__ ux,
+                                                     double* __restrict__ uy, double* __restrict__ uz,
+                                                     double* __restrict__ zeta) {
+  const int64_t v = warp_entity();
+  if (v >= G.nv) return;
+  const int lane = threadIdx.x & 31, ld = G.ld;
+  int64_t E[6];
+  for (int j = 0; j < 6; ++j) E[j] = (int64_t)G.v2e[6 * v + j] * ld;
+  const double* lw = G.lsq_w + 18 * v;
+  const double* rw = G.rot_w + 6 * v;
+  const double Av = G.A_v[v];
+  for (int k = lane; k < G.N; k += 32) {
+    double x = 0.0, y = 0.0, z = 0.0, r = 0.0;
+    for (int j = 0; j < 6; ++j) {
+      const double q = vn[E[j] + k];
+      x += lw[3 * j] * q;
+      y += lw[3 * j + 1] * q;
+      z += lw[3 * j + 2] * q;
+      r += rw[j] * q;
+    }
+    ux[v * ld + k] = x;
+    uy[v * ld + k] = y;
+    uz[v * ld + k] = z;
+    zeta[v * ld + k] = r / Av;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_diff_div(Geo64 G, const double* __restrict__ vn, double* __restrict__ divc) {
+  const int64_t c = warp_entity();
+  if (c >= G.nc) return;
+  const int lane = threadIdx.x & 31, ld = G.ld;
+  int64_t E[3];
+  double dw[3];
+  for (int s = 0; s < 3; ++s) {
+    E[s] = (int64_t)G.c2e[3 * c + s] * ld;
+    dw[s] = G.div_w[3 * c + s];
+  }
+  const double Ac = G.A_c[c];
+  for (int k = lane; k < G.N; k += 32) {
+    double acc = 0.0;
+    for (int s = 0; s < 3; ++s) acc += dw[s] * vn[E[s] + k];
+    divc[c * ld + k] = acc / Ac;
+  }
+}
+
+__device__ inline double dot3(double ax, double ay, double az, const double* b) {
+  return (ax * b[0] + ay * b[1]) + az * b[2];
+}
+
+__global__ void __launch_bounds__(256) k_diff_edge(Geo64 G, double* __restrict__ vn, const double* __restrict__ ux,
+                                                   const double* __restrict__ uy, const double* __restrict__ uz,
+                                                   const double* __restrict__ zeta, const double* __restrict__ divc,
+                                                   const double* __restrict__ thv, double* __restrict__ Kh_out,
+                                                   double* __restrict__ thflx, double dt) {
+  const int64_t e = warp_entity();
+  if (e >= G.ne) return;
+  const int lane = threadIdx.x & 31, ld = G.ld;
+  int64_t Q[4];
+  for (int j = 0; j < 4; ++j) Q[j] = (int64_t)G.e2q[4 * e + j] * ld;
+  const int64_t c1 = (int64_t)G.e2c[2 * e] * ld, c2 = (int64_t)G.e2c[2 * e + 1] * ld;
+  const int64_t v1 = (int64_t)G.e2v[2 * e] * ld, v2 = (int64_t)G.e2v[2 * e + 1] * ld;
+  const double* n = G.n_e + 3 * e;
+  const double* t = G.t_e + 3 * e;
+  const double le = G.l_e[e], de = G.d_e[e], L34 = G.L34[e];
+  const double cs2ld = (kCsSmag * kCsSmag) * (le * de);
+  for (int k = lane; k < G.N; k += 32) {
+    const double d34x = ux[Q[3] + k] - ux[Q[2] + k], d34y = uy[Q[3] + k] - uy[Q[2] + k],
+                 d34z = uz[Q[3] + k] - uz[Q[2] + k];
+    const double d12x = ux[Q[1] + k] - ux[Q[0] + k], d12y = uy[Q[1] + k] - uy[Q[0] + k],
+                 d12z = uz[Q[1] + k] - uz[Q[0] + k];
+    const double DT = dot3(d34x, d34y, d34z, n) / L34 - dot3(d12x, d12y, d12z, t) / le;
+    const double DS = dot3(d34x, d34y, d34z, t) / L34 + dot3(d12x, d12y, d12z, n) / le;
+    const double Kh = cs2ld * sqrt(DT * DT + DS * DS);
+    const double lap = (divc[c2 + k] - divc[c1 + k]) / de - (zeta[v2 + k] - zeta[v1 + k]) / le;
+    vn[e * ld + k] = vn[e * ld + k] + dt * Kh * lap;
+    Kh_out[e * ld + k] = Kh;
+    thflx[e * ld + k] = (le * Kh) * (thv[c2 + k] - thv[c1 + k]) / de;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_diff_theta(Geo64 G, const double* __restrict__ thflx, double* __restrict__ thv,
+                                                    double* __restrict__ ex, double dt) {
+  const int64_t c = warp_entity();
+  if (c >= G.nc) return;
+  const int lane = threadIdx.x & 31, ld = G.ld;
+  int64_t E[3];
+  double sg[3];
+  for (int s = 0; s < 3; ++s) {
+    E[s] = (int64_t)G.c2e[3 * c + s] * ld;
+    sg[s] = G.s_ce[3 * c + s];
+  }
+  const double Ac = G.A_c[c];
+  for (int k = lane; k < G.N; k += 32) {
+    double acc = 0.0;
+    for (int s = 0; s < 3; ++s) acc += sg[s] * thflx[E[s] + k];
+    const double dth = dt * acc / Ac;
+    const double th = thv[c * ld + k];
+    ex[c * ld + k] = ex[c * ld + k] * (1.0 + (kRd / kCvd) * dth / th);
+    thv[c * ld + k] = th + dth;
+  }
+}
+
+Geo64 make_geo(const icon_grid* grid) {
+  const GridDev& g = grid->g;
+  const Vertical& v = grid->vert;
+  Geo64 G;
+  G.nc = g.nc; G.ne = g.ne; G.nv = g.nv; G.N = v.N; G.ld = v.ld;
+  G.c2e = g.c2e; G.e2c = g.e2c; G.e2v = g.e2v; G.v2e = g.v2e; G.v2c = g.v2c; G.vdeg = g.vdeg;
+  G.e2vt = g.e2vt; G.e2q = g.e2q;
+  G.div_w = g.div_w; G.rot_w = g.rot_w; G.A_c = g.A_c; G.A_v = g.A_v; G.vt_w = g.vt_w; G.kin_w = g.kin_w;
+  G.lsq_w = g.lsq_w; G.d_e = g.d_e; G.l_e = g.l_e; G.f_e = g.f_e; G.L34 = g.L34; G.n_e = g.n_e; G.t_e = g.t_e;
+  G.s_ce = g.s_ce;
+  G.dz = v.d_dz; G.dzh = v.d_dzh; G.wu = v.d_wu; G.wl = v.d_wl; G.dz2 = v.d_dz2; G.ray = v.d_ray;
+  return G;
+}
+
+void launch_column(const Geo64& G, const ColArgs& a, cudaStream_t st) {
+  const unsigned nb = blocks_for(G.nc, 64);
+  if (G.N <= 32) k_column<32><<<nb, 64, 0, st>>>(G, a);
+  else if (G.N <= 64) k_column<64><<<nb, 64, 0, st>>>(G, a);
+  else if (G.N <= 96) k_column<96><<<nb, 64, 0, st>>>(G, a);
+  else if (G.N <= 128) k_column<128><<<nb, 64, 0, st>>>(G, a);
+  else k_column<256><<<nb, 64, 0, st>>>(G, a);
+}
+
+}  // namespace
+
+void enqueue_step_fp64(icon_state* st, double dt, int nsub, cudaStream_t stream) {
+  const icon_grid* grid = st->grid;
+  StateDev& s = st->s;
+  const Geo64 G = make_geo(grid);
+  const int ld = G.ld;
+  const double dtau = dt / nsub;
+  const unsigned nbv = blocks_for(G.nv, kWarpsPerBlock), nbe = blocks_for(G.ne, kWarpsPerBlock),
+                 nbc = blocks_for(G.nc, kWarpsPerBlock);
+  cudaMemsetAsync(s.mflx, 0, sizeof(double) * G.ne * ld, stream);
+  cudaMemsetAsync(s.wflx, 0, sizeof(double) * G.nc * ld, stream);
+  for (int it = 0; it < nsub; ++it) {
+    for (int stage = 0; stage < 2; ++stage) {
+      const bool corr = stage == 1;
+      const double* vn_st = corr ? s.vn_s : s.vn;
+      const double* w_st = corr ? s.w_s : s.w;
+      const double* rho_st = corr ? s.rho_s : s.rho;
+      const double* thv_st = corr ? s.thv_s : s.thv;
+      const double* ex_st = corr ? s.ex_s : s.ex;
+      k_vertex<<<nbv, 256, 0, stream>>>(G, vn_st, w_st, s.zeta, s.w_v);
+      k_edge_vt<<<nbe, 256, 0, stream>>>(G, vn_st, s.vt, s.Ke);
+      k_cell_ke<<<nbc, 256, 0, stream>>>(G, s.Ke, s.Kc);
+      EdgeArgs ea;
+      ea.vn = vn_st; ea.w = w_st; ea.rho = rho_st; ea.thv = thv_st; ea.ex = ex_st;
+      ea.vt = s.vt; ea.Kc = s.Kc; ea.zeta = s.zeta; ea.w_v = s.w_v;
+      ea.vn_base = s.vn;
+      ea.vn_out = corr ? s.vn : s.vn_s;
+      ea.Avn0 = s.Avn0;
+      ea.F = s.F; ea.G = s.G; ea.a_e = s.a_e; ea.mflx = s.mflx;
+      ea.dtau = dtau; ea.nsub = (double)nsub; ea.corrector = corr;
+      k_edge_tend<<<nbe, 256, 0, stream>>>(G, ea);
+      ColArgs ca;
+      ca.rho = s.rho; ca.thv = s.thv; ca.ex = s.ex; ca.w = s.w;
+      ca.w_stage = w_st;
+      ca.F = s.F; ca.G = s.G; ca.a_e = s.a_e;
+      ca.Aw0 = s.Aw0;
+      ca.rho_o = corr ? s.rho : s.rho_s;
+      ca.thv_o = corr ? s.thv : s.thv_s;
+      ca.ex_o = corr ? s.ex : s.ex_s;
+      ca.w_o = corr ? s.w : s.w_s;
+      ca.wflx = s.wflx;
+      ca.status = s.status;
+      ca.dtau = dtau; ca.nsub = (double)nsub; ca.corrector = corr;
+      launch_column(G, ca, stream);
+    }
+  }
+  k_diff_vertex<<<nbv, 256, 0, stream>>>(G, s.vn, s.uvx, s.uvy, s.uvz, s.zeta);
+  k_diff_div<<<nbc, 256, 0, stream>>>(G, s.vn, s.divc);
+  k_diff_edge<<<nbe, 256, 0, stream>>>(G, s.vn, s.uvx, s.uvy, s.uvz, s.zeta, s.divc, s.thv, s.Kh, s.thflx, dt);
+  k_diff_theta<<<nbc, 256, 0, stream>>>(G, s.thflx, s.thv, s.ex, dt);
+}
+
+}  // namespace icon

@@ -1,0 +1,160 @@
+// Internal declarations of the GB300 dycore library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+#include <string>
+#include <vector>
+#include "../../include/icon.h"
+
+namespace icon {
+
+// ---------------------------------------------------------------- constants
+// Physical constants and method parameters (the paper fixes none of them).
+constexpr double kR = 6.371229e6;        // sphere radius, m
+constexpr double kOmega = 7.29212e-5;    // rotation rate, 1/s
+constexpr double kGrav = 9.80665;        // m/s^2
+constexpr double kRd = 287.04;           // J/kg/K
+constexpr double kCpd = 1004.64;         // J/kg/K
+constexpr double kCvd = kCpd - kRd;
+constexpr double kP0 = 1.0e5;            // Pa
+constexpr double kBeta = 0.65;           // vertical off-centring (implicit weight)
+constexpr double kCsSmag = 0.15;         // Smagorinsky constant
+
+// ---------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+#define ICON_CUDA(call)                                                        \
+  do {                                                                         \
+    cudaError_t _e = (call);                                                   \
+    if (_e != cudaSuccess) return ::icon::cuda_fail(_e, #call);                \
+  } while (0)
+
+// ---------------------------------------------------------------- memory
+struct Allocator {
+  void* (*alloc)(size_t, void*) = nullptr;
+  void (*dealloc)(void*, void*) = nullptr;
+  void* ctx = nullptr;
+};
+Allocator current_allocator();
+cudaStream_t current_stream();
+
+// A set of device buffers released together with the allocator that made them.
+struct DeviceArena {
+  Allocator al;
+  std::vector<void*> blocks;
+  bool failed = false;
+  void* get(size_t bytes);           // NULL (and failed = true) on failure
+  template <class T> T* get_n(size_t n) { return static_cast<T*>(get(n * sizeof(T))); }
+  void release();
+};
+
+// ---------------------------------------------------------------- grid
+struct Vertical {
+  int N = 0;           // full levels
+  int ld = 0;          // row stride (elements) of every (entity, level) field
+  double z_top = 0, s = 0, z_d = 0;
+  std::vector<double> z_h, z_f, dz, dzh, wu, wl, rayleigh, dz2;  // host copies
+  // device copies (length ld)
+  double *d_z_h = nullptr, *d_z_f = nullptr, *d_dz = nullptr, *d_dzh = nullptr,
+         *d_wu = nullptr, *d_wl = nullptr, *d_ray = nullptr, *d_dz2 = nullptr;
+};
+
+struct GridDev {
+  int64_t nc = 0, ne = 0, nv = 0;
+  int L = 0;
+  // connectivity
+  int *c2v = nullptr, *c2e = nullptr, *e2c = nullptr, *e2v = nullptr;
+  int *v2e = nullptr, *v2c = nullptr, *vdeg = nullptr, *e2vt = nullptr, *e2q = nullptr;
+  // geometry (FP64)
+  double *x_c = nullptr, *x_e = nullptr, *x_v = nullptr, *n_e = nullptr, *t_e = nullptr;
+  double *l_e = nullptr, *d_e = nullptr, *A_c = nullptr, *A_v = nullptr, *f_e = nullptr;
+  double *vt_w = nullptr, *kin_w = nullptr, *lsq_w = nullptr, *L34 = nullptr;
+  double *s_ce = nullptr, *s_ve = nullptr;
+  // derived coefficient tables
+  double *div_w = nullptr;   // [Nc][3]  s_ce * l_e  (divide by A_c afterwards)
+  double *rot_w = nullptr;   // [Nv][6]  s_ve * d_e  (divide by A_v afterwards)
+  float *vt_w32 = nullptr, *kin_w32 = nullptr, *lsq_w32 = nullptr;
+  float *div_w32 = nullptr, *rot_w32 = nullptr;   // mixed precision copies (already / area)
+  float *inv_de32 = nullptr, *inv_le32 = nullptr, *f_e32 = nullptr;
+};
+
+}  // namespace icon
+
+struct icon_grid {
+  icon::DeviceArena arena;
+  icon::GridDev g;
+  icon::Vertical vert;
+  int root = 2, bisections = 0;
+};
+
+namespace icon {
+// Device buffers of one state. Full-level fields are [n][ld], half-level fields
+// [n][ld] with N+1 used entries. "star" holds the predictor state.
+struct StateDev {
+  int precision = ICON_FP64;
+  // prognostics S^n (FP64 in both modes except vn in mixed mode)
+  double *vn = nullptr, *w = nullptr, *rho = nullptr, *thv = nullptr, *ex = nullptr;
+  float *vn32 = nullptr;
+  // predictor state S*
+  double *vn_s = nullptr, *w_s = nullptr, *rho_s = nullptr, *thv_s = nullptr, *ex_s = nullptr;
+  float *vn32_s = nullptr;
+  // tendencies kept from the predictor
+  double *Avn0 = nullptr, *Aw0 = nullptr;
+  float *Avn0_32 = nullptr, *Aw0_32 = nullptr;
+  // step-mean mass fluxes
+  double *mflx = nullptr, *wflx = nullptr;
+  // scratch (FP64 mode)
+  double *zeta = nullptr, *w_v = nullptr, *vt = nullptr, *Ke = nullptr, *Kc = nullptr;
+  double *a_e = nullptr, *F = nullptr, *G = nullptr;
+  double *uvx = nullptr, *uvy = nullptr, *uvz = nullptr, *divc = nullptr, *Kh = nullptr, *thflx = nullptr;
+  // mixed-mode scratch and shadows
+  float *zeta32 = nullptr, *wv32 = nullptr, *vt32 = nullptr, *Ke32 = nullptr, *Kc32 = nullptr,
+        *ae32 = nullptr, *F32 = nullptr, *G32 = nullptr;
+  float *rho32 = nullptr, *thv32 = nullptr, *exp32 = nullptr, *w32 = nullptr;
+  float *rho32_s = nullptr, *thv32_s = nullptr, *exp32_s = nullptr, *w32_s = nullptr;
+  double *ex_ref = nullptr;           // [ld] reference Exner profile
+  // column factorisation kept between predictor and corrector (mixed mode)
+  double *fac = nullptr;
+  // mass reduction partials and the device status word
+  double *mass_part = nullptr;
+  int mass_nblk = 0;
+  unsigned int* status = nullptr;
+};
+}  // namespace icon
+
+struct icon_state {
+  const icon_grid* grid = nullptr;
+  icon::DeviceArena arena;
+  icon::StateDev s;
+  uint64_t seed = 0;
+  int case_id = 0;
+  // recorded step graph
+  cudaGraphExec_t graph = nullptr;
+  double graph_dt = 0.0;
+  int graph_nsub = 0;
+  cudaStream_t capture_stream = nullptr;
+  cudaStream_t graph_stream = nullptr;
+  cudaEvent_t done = nullptr;
+};
+
+namespace icon {
+// grid_build.cu
+int build_grid_device(icon_grid* grid, cudaStream_t st);
+// init.cu
+void make_vertical(Vertical& v, int nlev, double top_m, double stretch_s, double damp_m);
+int init_state_device(icon_state* st, uint64_t seed, int case_id, const icon_case_params& p,
+                      cudaStream_t stream);
+// dycore64.cu
+void enqueue_step_fp64(icon_state* st, double dt, int nsub, cudaStream_t stream);
+// dycore32.cu
+void enqueue_step_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream);
+// mass
+void enqueue_mass(const icon_state* st, double* d_out, cudaStream_t stream);
+int mass_partials_count(int64_t nc);
+// scan helper (grid_build.cu)
+int exclusive_scan_u32(const unsigned* in, unsigned* out, int64_t n, unsigned* total_dev,
+                       DeviceArena& tmp, cudaStream_t st);
+
+inline unsigned blocks_for(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
+}  // namespace icon

@@ -1,0 +1,246 @@
+// Vertical grid and analytic initial states on the GPU.
+//
+// Vertical coordinate: flat bottom, rigid lid z_top; half level i = 0..N (top to
+// bottom) at z_top (exp(s (N-i)/N) - 1)/(exp(s) - 1) -- a stretched height grid
+// standing in for the paper's terrain-following hybrid height coordinate over
+// flat ground (Sec. "Current State of the Art"; 90 levels in Table 2).
+//
+// Initial states (the paper starts from reanalysis data, which is replaced here
+// by analytic states with the same sizes):
+//   rest   isothermal 250 K, no wind;
+//   SBR    u = u0 cos(phi), u0 = 20 m/s, 250 K, in gradient balance:
+//          ln p = ln p0 - g z/(Rd T0) - (R Omega u0 + u0^2/2) sin^2(phi)/(Rd T0);
+//   jet    ln p = ln p0 - z/H0 - B S(z) Phi(phi), H0 = Rd T_j/g, T_j = 288 K,
+//          S = exp(-((z - 10 km)/8 km)^2), Phi = -4(cos^3/3 - cos^5/5),
+//          T = g/(Rd (1/H0 + B S' Phi)), u the gradient-wind root continuous with
+//          geostrophy, B such that u = 35 m/s at 45 deg at z = 10 km, plus a
+//          Gaussian zonal bump amp exp(-(r/(R/10))^2) (1 m/s at 20E 40N, or a
+//          seeded amplitude in U(0.5, 2) m/s and a position uniform on the sphere
+//          for an ensemble member).
+// theta_v comes from the analytic T and p; Exner is analytic at the lowest level
+// and integrated upward in discrete hydrostatic balance
+// pi_{k-1} = pi_k - g dzh_k / (cpd theta_ic,k); rho from the state equation.
+// Seeded noise theta_v += a (2U - 1), U the SplitMix64 draw number (cell*N + k),
+// with Exner held fixed and rho recomputed.
+#include <cmath>
+#include "icon_internal.h"
+
+namespace icon {
+
+// SplitMix64 (Steele, Lea, Flood 2014): output number idx of the generator started at seed
+__host__ __device__ inline uint64_t splitmix64(uint64_t seed, uint64_t idx) {
+  uint64_t z = seed + (idx + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__host__ __device__ inline double uniform01(uint64_t seed, uint64_t idx) {
+  return (double)(splitmix64(seed, idx) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+void make_vertical(Vertical& v, int nlev, double top_m, double stretch_s, double damp_m) {
+  const int N = nlev;
+  if (top_m <= 0) top_m = N >= 60 ? 75000.0 : 30000.0;
+  if (stretch_s <= 0) stretch_s = N >= 60 ? 5.5 : 2.0;
+  if (damp_m <= 0) damp_m = N >= 60 ? 45000.0 : 20000.0;
+  v.N = N;
+  v.ld = ((N + 1 + 31) / 32) * 32;
+  v.z_top = top_m; v.s = stretch_s; v.z_d = damp_m;
+  v.z_h.assign(v.ld, 0.0); v.z_f.assign(v.ld, 0.0); v.dz.assign(v.ld, 0.0); v.dzh.assign(v.ld, 0.0);
+  v.wu.assign(v.ld, 0.0); v.wl.assign(v.ld, 0.0); v.rayleigh.assign(v.ld, 0.0); v.dz2.assign(v.ld, 0.0);
+  const double den = std::exp(stretch_s) - 1.0;
+  for (int i = 0; i <= N; ++i) v.z_h[i] = top_m * (std::exp(stretch_s * (N - i) / N) - 1.0) / den;
+  v.z_h[N] = 0.0;
+  v.z_h[0] = top_m;
+  for (int k = 0; k < N; ++k) {
+    v.dz[k] = v.z_h[k] - v.z_h[k + 1];
+    v.z_f[k] = 0.5 * (v.z_h[k] + v.z_h[k + 1]);
+  }
+  for (int h = 1; h < N; ++h) {
+    v.dzh[h] = v.z_f[h - 1] - v.z_f[h];
+    v.wu[h] = v.dz[h] / (v.dz[h - 1] + v.dz[h]);
+    v.wl[h] = 1.0 - v.wu[h];
+    v.dz2[h] = v.z_h[h - 1] - v.z_h[h + 1];
+  }
+  const double pi = 3.141592653589793;
+  for (int h = 0; h <= N; ++h) {
+    double z = v.z_h[h];
+    if (z > damp_m) {
+      double sn = std::sin(0.5 * pi * (z - damp_m) / (top_m - damp_m));
+      v.rayleigh[h] = 0.05 * (sn * sn);
+    }
+  }
+}
+
+namespace {
+
+struct CaseDev {
+  int case_id, N, ld;
+  double noise, B, H0;
+  uint64_t seed;
+  int has_bump;
+  double bamp, bx, by, bz;   // bump amplitude and unit centre
+};
+
+__device__ inline void basis(double x, double y, double z, double& cphi, double& sphi, double& elx, double& ely) {
+  cphi = sqrt(x * x + y * y);
+  sphi = z;
+  double safe = cphi > 0.0 ? cphi : 1.0;
+  elx = -y / safe;
+  ely = x / safe;
+}
+
+// ln p, T, zonal wind of the analytic state at unit position (x, y, z) and height zz
+__device__ void analytic(const CaseDev& cd, double x, double y, double zu, double zz, double& lnp, double& T,
+                         double& u) {
+  double cphi, sphi, elx, ely;
+  basis(x, y, zu, cphi, sphi, elx, ely);
+  if (cd.case_id == ICON_CASE_REST) {
+    lnp = (log(kP0) - kGrav * zz / (kRd * 250.0)) + 0.0 * x;
+    T = 250.0;
+    u = 0.0;
+  } else if (cd.case_id == ICON_CASE_SBR) {
+    const double u0 = 20.0, T0 = 250.0;
+    lnp = (log(kP0) - kGrav * zz / (kRd * T0)) - ((kR * kOmega * u0 + 0.5 * u0 * u0) * (sphi * sphi)) / (kRd * T0);
+    T = T0;
+    u = u0 * cphi;
+  } else {
+    const double zj = 10000.0, hj = 8000.0;
+    double q = (zz - zj) / hj;
+    double S = exp(-(q * q));
+    double dS = -2.0 * (zz - zj) / (hj * hj) * S;
+    double c3 = cphi * cphi * cphi, c5 = c3 * cphi * cphi;
+    double Phi = -4.0 * (c3 / 3.0 - c5 / 5.0);
+    lnp = (log(kP0) - zz / cd.H0) - cd.B * S * Phi;
+    T = kGrav / (kRd * (1.0 / cd.H0 + cd.B * dS * Phi));
+    double c = (kRd * T / kR) * cd.B * S * (4.0 * (cphi * cphi) * (sphi * sphi));
+    double a = cphi > 1e-12 ? 1.0 / (kR * cphi) : 0.0;
+    double b = 2.0 * kOmega;
+    u = 2.0 * c / (b + sqrt(b * b + 4.0 * a * c));
+  }
+}
+
+// one thread per column: theta_v, discrete hydrostatic Exner, noise, rho
+__global__ void k_init_cells(CaseDev cd, int64_t nc, const double* __restrict__ x_c, const double* __restrict__ z_f,
+                             const double* __restrict__ dzh, const double* __restrict__ wu,
+                             const double* __restrict__ wl, double* __restrict__ rho, double* __restrict__ thv,
+                             double* __restrict__ ex, double* __restrict__ w) {
+  int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  const int N = cd.N, ld = cd.ld;
+  double x = x_c[3 * c], y = x_c[3 * c + 1], z = x_c[3 * c + 2];
+  double* th = thv + c * ld;
+  double* pe = ex + c * ld;
+  double* rr = rho + c * ld;
+  const double kap = kRd / kCpd;
+  double exan_bottom = 0.0;
+  for (int k = 0; k < N; ++k) {
+    double lnp, T, u;
+    analytic(cd, x, y, z, z_f[k], lnp, T, u);
+    double exan = exp(kap * (lnp - log(kP0)));
+    th[k] = T / exan;
+    if (k == N - 1) exan_bottom = exan;
+  }
+  pe[N - 1] = exan_bottom;
+  for (int k = N - 1; k > 0; --k) {
+    double thic = wu[k] * th[k - 1] + wl[k] * th[k];
+    pe[k - 1] = pe[k] - kGrav * dzh[k] / (kCpd * thic);
+  }
+  if (cd.noise > 0.0) {
+    for (int k = 0; k < N; ++k) {
+      double U = uniform01(cd.seed, (uint64_t)c * (uint64_t)N + (uint64_t)k);
+      th[k] = th[k] + cd.noise * (2.0 * U - 1.0);
+    }
+  }
+  for (int k = 0; k < N; ++k) rr[k] = kP0 * pow(pe[k], kCvd / kRd) / (kRd * th[k]);
+  for (int k = N; k < ld; ++k) { th[k] = 0.0; pe[k] = 0.0; rr[k] = 0.0; }
+  for (int h = 0; h < ld; ++h) w[c * ld + h] = 0.0;
+}
+
+// one thread per (edge, level): vn = u . n with u = u_lambda e_lambda
+__global__ void k_init_edges(CaseDev cd, int64_t ne, const double* __restrict__ x_e, const double* __restrict__ n_e,
+                             const double* __restrict__ z_f, double* __restrict__ vn) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int ld = cd.ld;
+  if (t >= ne * ld) return;
+  int64_t e = t / ld;
+  int k = (int)(t % ld);
+  if (k >= cd.N) { vn[t] = 0.0; return; }
+  double x = x_e[3 * e], y = x_e[3 * e + 1], z = x_e[3 * e + 2];
+  double lnp, T, u;
+  analytic(cd, x, y, z, z_f[k], lnp, T, u);
+  if (cd.has_bump) {
+    double cx = y * cd.bz - z * cd.by, cy = z * cd.bx - x * cd.bz, cz = x * cd.by - y * cd.bx;
+    double r = kR * atan2(sqrt((cx * cx + cy * cy) + cz * cz), (x * cd.bx + y * cd.by) + z * cd.bz);
+    double q = r / (kR / 10.0);
+    u = u + cd.bamp * exp(-(q * q));
+  }
+  double cphi, sphi, elx, ely;
+  basis(x, y, z, cphi, sphi, elx, ely);
+  double proj = (elx * n_e[3 * e] + ely * n_e[3 * e + 1]) + 0.0 * n_e[3 * e + 2];
+  vn[t] = u * proj;
+}
+
+__global__ void k_exner_ref(int N, const double* __restrict__ z_f, const double* __restrict__ dzh,
+                            const double* __restrict__ wu, const double* __restrict__ wl, double* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double kap = kRd / kCpd;
+  double th[512];
+  for (int k = 0; k < N; ++k) {
+    double lnp = log(kP0) - kGrav * z_f[k] / (kRd * 250.0);
+    th[k] = 250.0 / exp(kap * (lnp - log(kP0)));
+    if (k == N - 1) out[k] = exp(kap * (lnp - log(kP0)));
+  }
+  for (int k = N - 1; k > 0; --k) {
+    double thic = wu[k] * th[k - 1] + wl[k] * th[k];
+    out[k - 1] = out[k] - kGrav * dzh[k] / (kCpd * thic);
+  }
+}
+
+double jet_B() {
+  const double c45 = std::sqrt(0.5), U = 35.0, Tj = 288.0;
+  return (U * U / (kR * c45) + 2.0 * kOmega * U) * kR / (kRd * Tj);
+}
+
+}  // namespace
+
+int init_state_device(icon_state* st, uint64_t seed, int case_id, const icon_case_params& p, cudaStream_t stream) {
+  const icon_grid* grid = st->grid;
+  const GridDev& g = grid->g;
+  const Vertical& v = grid->vert;
+  StateDev& s = st->s;
+  CaseDev cd;
+  cd.case_id = case_id;
+  cd.N = v.N;
+  cd.ld = v.ld;
+  cd.noise = p.noise_K >= 0.0 ? p.noise_K : (case_id == ICON_CASE_SBR ? 0.01 : 0.0);
+  cd.B = jet_B();
+  cd.H0 = kRd * 288.0 / kGrav;
+  cd.seed = seed;
+  cd.has_bump = 0;
+  cd.bamp = cd.bx = cd.by = cd.bz = 0.0;
+  const double pi = 3.141592653589793;
+  if (case_id == ICON_CASE_JET || case_id == ICON_CASE_MEMBER) {
+    double amp = 1.0, lon = 20.0 * pi / 180.0, lat = 40.0 * pi / 180.0;
+    if (case_id == ICON_CASE_MEMBER) {
+      uint64_t ms = splitmix64(seed, (uint64_t)p.member);
+      cd.seed = ms;
+      amp = 0.5 + 1.5 * uniform01(ms, 0);
+      lon = 2.0 * pi * uniform01(ms, 1);
+      lat = std::asin(2.0 * uniform01(ms, 2) - 1.0);
+    }
+    cd.has_bump = 1;
+    cd.bamp = amp;
+    cd.bx = std::cos(lat) * std::cos(lon);
+    cd.by = std::cos(lat) * std::sin(lon);
+    cd.bz = std::sin(lat);
+  }
+  k_init_cells<<<blocks_for(g.nc, 128), 128, 0, stream>>>(cd, g.nc, g.x_c, v.d_z_f, v.d_dzh, v.d_wu, v.d_wl, s.rho,
+                                                          s.thv, s.ex, s.w);
+  k_init_edges<<<blocks_for(g.ne * v.ld, 256), 256, 0, stream>>>(cd, g.ne, g.x_e, g.n_e, v.d_z_f, s.vn);
+  k_exner_ref<<<1, 1, 0, stream>>>(v.N, v.d_z_f, v.d_dzh, v.d_wu, v.d_wl, s.ex_ref);
+  ICON_CUDA(cudaGetLastError());
+  return ICON_OK;
+}
+
+}  // namespace icon

@@ -15,3 +15,31 @@ def pytest_configure(config):
 
 def golden_path(name):
     return os.path.join(ROOT, "tests", "golden", name)
+
+
+@pytest.fixture(scope="session")
+def built_lib():
+    """Compile the CUDA library if needed (nvcc cross-compiles without a GPU) and return its path."""
+    from paper_2511_02021_gb300 import build as b
+    return b.build()
+
+
+@pytest.fixture(scope="session")
+def gpu():
+    """The C ABI bound to cuda:0 with PyTorch's allocator and current stream."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test run without a CUDA device")
+    from paper_2511_02021_gb300 import build as b
+    b.build()
+    torch.cuda.set_device(0)
+    import paper_2511_02021_gb300 as P
+    P.use_torch_allocator(0)
+    P.bind_torch_stream()
+    return P.capi
+
+
+def rel_l2(a, b):
+    import numpy as np
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)

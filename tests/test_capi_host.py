@@ -1,0 +1,43 @@
+"""The C-ABI library loads, exports every entry point declared in include/icon.h and
+rejects bad arguments on the host (no GPU needed for any of these calls)."""
+import ctypes
+import os
+import re
+
+from tests.conftest import ROOT
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "icon.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(icon_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(built_lib):
+    names = _declared()
+    assert len(names) >= 20
+    lib = ctypes.CDLL(built_lib)
+    for n in names:
+        getattr(lib, n)          # dlsym; raises AttributeError if missing
+
+
+def test_host_argument_checks(built_lib):
+    from paper_2511_02021_gb300 import capi as C
+    lib = C._lib
+    h = ctypes.c_void_p()
+    assert lib.icon_grid_build(3, 2, 20, ctypes.byref(h)) == C.ICON_EINVAL
+    assert b"root 2" in lib.icon_last_error()
+    assert lib.icon_grid_build(2, 11, 20, ctypes.byref(h)) == C.ICON_EINVAL
+    assert lib.icon_grid_build(2, 2, 0, ctypes.byref(h)) == C.ICON_EINVAL
+    assert lib.icon_grid_build(2, 2, 20, None) == C.ICON_EINVAL
+    assert h.value is None                         # out-pointer untouched on error
+    f = C.ALLOC_FN(lambda n, c: 0)
+    assert lib.icon_set_allocator(ctypes.cast(f, ctypes.c_void_p), None, None) == C.ICON_EINVAL
+    assert lib.icon_set_allocator(None, None, None) == C.ICON_OK
+    assert lib.icon_state_init(None, 0, 0, ctypes.byref(h)) == C.ICON_EINVAL
+    assert lib.icon_dycore_step(None, 1.0, 1) == C.ICON_EINVAL
+    assert lib.icon_global_mass(None, None) == C.ICON_EINVAL
+    assert lib.icon_ensemble_create(None, 0, ctypes.byref(h)) == C.ICON_EINVAL
+    lib.icon_grid_free(None)
+    lib.icon_state_free(None)
+    lib.icon_ensemble_free(None)

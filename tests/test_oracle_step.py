@@ -8,6 +8,7 @@ import oracle as O
 from oracle import dycore as D
 from oracle import state as S
 from tests.conftest import golden_path
+from tests.tolerances import EPS, w_bound
 
 
 def rel(a, b):
@@ -154,3 +155,19 @@ def test_diffusion_properties():
     var0 = np.var(s["theta_v"], axis=0)
     var1 = np.var(s1["theta_v"], axis=0)
     assert np.all(var1 <= var0)
+
+
+def test_w_conditioning():
+    """The oracle's own w moves by far more than eps under one-ulp input perturbations,
+    while the other fields move by O(eps): the premise of w_bound."""
+    g = O.build_grid(2, 2)
+    v = O.vertical_grid(20)
+    s = O.init_state(g, v, 1, O.CASE_SBR, noise_K=0.01)
+    a, _ = O.dycore_step(g, v, s, 300.0, 5)
+    sp = dict(s)
+    sp["exner"] = s["exner"] * (1 + EPS * np.random.default_rng(0).choice([-1, 1], size=s["exner"].shape))
+    b, _ = O.dycore_step(g, v, sp, 300.0, 5)
+    assert rel(b["w"], a["w"]) > 1e-12
+    assert np.sqrt(np.mean((b["w"] - a["w"]) ** 2)) < w_bound(300.0, 5, 1)
+    for f in ("vn", "rho", "theta_v", "exner"):
+        assert rel(b[f], a[f]) < 1e-14
