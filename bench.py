@@ -1,0 +1,320 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the dynamical-core hot path on one GB300 (or N replicas).
+
+One benchmark step = one dycore step (nsub predictor-corrector substeps with the
+vertically implicit column solve, then Smagorinsky diffusion) followed by the
+global mass integral, on a synthetic analytic state resident in HBM. Metric:
+cell-level updates per second = cells x levels x substeps / time.
+
+Default workload: the R2B6 grid (327,680 cells, 491,520 edges) with 90 levels on
+a stretched height coordinate to 75 km, FP64, balanced 35 m/s jet with a 1 m/s
+Gaussian bump, dt = 90 s in 5 substeps, 10 steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+                  [--workload r2b6-fp64|r2b8-mixed|r2b9-mixed]
+
+Under torchrun (N > 1) every rank advances its own replica (no data exchange:
+"scaling": "weak"); rank 0 prints the JSON line with the max time over ranks.
+--impl reference times the FP64 CPU oracle on the host cores instead (rank 0 only).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2511_02021_gb300 import workloads as WL  # noqa: E402
+
+METRIC = "cell-level updates/s per dycore substep, % HBM roofline; mixed vs FP64"
+UNIT = "cell-level updates/s"
+WORKLOADS = {"r2b6-fp64": WL.R2B6_JET, "r2b8-mixed": WL.R2B8_JET_MIXED, "r2b9-mixed": WL.R2B9_JET_MIXED}
+PROG = ("vn", "w", "rho", "theta_v", "exner")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+# FP64 arithmetic-instruction rate of the GB300 measured with an FMA/ADD throughput
+# probe on this pool (505 G instr/s; NVIDIA's nominal 1.25 TFLOP/s FMA is 625 G instr/s
+# at 2.07 GHz). Used as the peak of kernels bound by FP64 arithmetic.
+FP64_INSTR_PEAK = 505e9
+
+
+def counts(wl):
+    L = wl.bisections + 1
+    nc, ne, nv = 20 * 4 ** L, 30 * 4 ** L, 10 * 4 ** L + 2
+    return nc, ne, nv
+
+
+def kernel_model(kind, wl):
+    """(algorithmic bytes, FP64 arithmetic ops) of ONE launch of a kernel kind, averaged
+    over predictor and corrector launches: every input and output array element read
+    or written once (8 B in FP64), and the FP64 operations of the expressions as
+    written (a division counted as one operation)."""
+    nc, ne, nv = counts(wl)
+    N = wl.nlev
+    H = N + 1
+    b = 8.0
+    table = {
+        "vertex_curl_wmean": (b * (ne * N + nc * H + nv * N + nv * H), nv * N * 13 + nv * H * 6),
+        "edge_vt_ke": (b * 3 * ne * N, ne * N * 14),
+        "cell_ke": (b * (ne + nc) * N, nc * N * 6),
+        "edge_tendency_flux": (b * (ne * N * 6.5 + nc * N * 4 + nv * N + nc * H + nv * H + ne * H),
+                               ne * N * 30 + ne * H * 10),
+        "column_solve": (b * (nc * N * 8 + ne * N * 2 + ne * H + nc * H * 2.5), nc * N * 120),
+        "diff_vertex": (b * (ne * N + 4 * nv * N), nv * N * 25),
+        "diff_div": (b * (ne + nc) * N, nc * N * 7),
+        "diff_edge": (b * (ne * N * 4 + nv * N * 5 + nc * N * 2), ne * N * 45),
+        "diff_theta": (b * (ne * N + 4 * nc * N), nc * N * 12),
+        "global_mass": (b * nc * N, nc * N * 2),
+    }
+    return table.get(kind)
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.f = open(self.path, "w")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- reference arm (oracle on host cores)
+def oracle_sample(wl):
+    """Time the oracle on one substep (predictor + corrector) of the workload, init excluded.
+    Returns (cell-level updates/s, seconds, description)."""
+    import oracle as O
+    from oracle import dycore as OD
+    g = O.build_grid(2, wl.bisections)
+    v = O.vertical_grid(wl.nlev)
+    s = O.init_state(g, v, wl.seed, wl.case, noise_K=(wl.noise_K if wl.noise_K >= 0 else None))
+    acc = {"mflx": np.zeros((g.ne, v.N)), "wflx": np.zeros((g.nc, v.N + 1))}
+    t0 = time.perf_counter()
+    OD.substep(g, v, s, wl.dt / wl.nsub, wl.nsub, acc)
+    el = time.perf_counter() - t0
+    return g.nc * v.N / el, el, "one substep of %s (init excluded)" % wl.name
+
+
+def run_reference(args, wl, rank):
+    if rank != 0:
+        return
+    # the oracle is plain numpy: its array operations run on one host core
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, el, desc = oracle_sample(wl)
+        if i >= args.warmup:
+            vals.append(el)
+    t = sum(vals) / len(vals)
+    nc, _, _ = counts(wl)
+    value = nc * wl.nlev / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "cells": nc, "levels": wl.nlev, "dt": wl.dt, "nsub": wl.nsub,
+                       "sample": "each step = one substep of the workload"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gpu(args, wl, rank, world, local_rank):
+    import torch
+    torch.cuda.set_device(local_rank)
+    from paper_2511_02021_gb300 import build as B
+    B.build()
+    import paper_2511_02021_gb300 as P
+    from paper_2511_02021_gb300 import capi as C
+    P.use_torch_allocator(local_rank)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    P.bind_torch_stream(stream)
+    dist = world > 1
+    if dist:
+        import torch.distributed as td
+
+    nc, ne, nv = counts(wl)
+    N = wl.nlev
+    grid = C.icon_grid_build(2, wl.bisections, N)
+    st = C.icon_state_init_ex(grid, wl.seed + rank, wl.case, noise_K=wl.noise_K, precision=wl.precision)
+    m0 = C.icon_global_mass(st)
+    for _ in range(args.warmup):
+        C.icon_dycore_step(st, wl.dt, wl.nsub)
+    kernels_per_step = C.icon_state_step_kernels(st, wl.dt, wl.nsub) + 2      # + the mass integral
+    mass_host = torch.empty(1, dtype=torch.float64, pin_memory=True)
+
+    clocks = ClockSampler(local_rank) if rank == 0 else None
+    time.sleep(0.4)
+    if dist:
+        td.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        C.icon_dycore_step_async(st, wl.dt, wl.nsub)
+        C.icon_global_mass_async(st, mass_host.data_ptr())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        td.barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop() if clocks else None
+    C.icon_state_status(st)                                   # raises on non-finite values
+    m1 = float(mass_host[0])
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        td.all_reduce(t, op=td.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * nc * N * wl.nsub * args.steps / (ms * 1e-3)
+
+    # per-kernel durations, measured live with CUDA events around every launch
+    kms, kn = None, None
+    for _ in range(2):
+        kms, kn = C.icon_dycore_step_profile(st, wl.dt, wl.nsub, kms, kn)
+    hbm_peak, peak_src = peaks()
+    rows = []
+    for k in range(C.ICON_KIND_COUNT):
+        if kn[k] == 0:
+            continue
+        name = C.icon_kernel_kind_name(k)
+        avg = kms[k] / kn[k]
+        model = kernel_model(name, wl)
+        gbs = model[0] / (avg * 1e-3) / 1e9 if model else None
+        fops = model[1] / (avg * 1e-3) if model else None
+        rows.append((kms[k] / 2, name, avg, int(kn[k] // 2), gbs, fops))
+    rows.sort(reverse=True)
+    top = rows[0]
+    hbm_frac = top[4] / hbm_peak if top[4] else None
+    alu_frac = top[5] / FP64_INSTR_PEAK if top[5] else None
+    if alu_frac is not None and hbm_frac is not None and alu_frac > hbm_frac:
+        roof = {"kernel": top[1], "bound": "alu", "achieved": top[5] / 1e9, "peak": FP64_INSTR_PEAK / 1e9,
+                "unit": "GFLOP/s (FP64)", "frac": alu_frac, "traffic": None,
+                "hbm": {"achieved": top[4], "peak": hbm_peak, "unit": "GB/s", "frac": hbm_frac,
+                        "peak_source": peak_src},
+                "launch_ms": top[2], "launches_per_step": top[3]}
+    else:
+        roof = {"kernel": top[1], "bound": "hbm", "achieved": top[4], "peak": hbm_peak, "unit": "GB/s",
+                "frac": hbm_frac, "traffic": None, "peak_source": peak_src, "launch_ms": top[2],
+                "launches_per_step": top[3]}
+    breakdown = {r[1]: {"ms_per_step": round(r[0], 4), "share": round(r[0] / sum(x[0] for x in rows), 4)}
+                 for r in rows}
+
+    # end to end through the C ABI with host buffers: h2d of the prognostic state,
+    # the step, the mass integral and d2h of the updated state, every step
+    host = {}
+    for f in PROG:
+        shape = (ne if f == "vn" else nc, N + 1 if f == "w" else N)
+        host[f] = torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+        C.icon_state_copy_field(st, grid, N, f, host[f])
+    h2d = sum(a.nbytes for a in host.values())
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for f in PROG:
+            C.icon_state_set_field(st, grid, N, f, host[f])
+        C.icon_dycore_step(st, wl.dt, wl.nsub)
+        C.icon_global_mass(st)
+        for f in PROG:
+            C.icon_state_copy_field(st, grid, N, f, host[f])
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": nc * N * wl.nsub / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": h2d + 8}
+
+    C.icon_state_free(st)
+    C.icon_grid_free(grid)
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        v, el, desc = oracle_sample(wl)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc, "seconds": el}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if wl.precision == 0 else "f32+f64",
+            "data": "synthetic (analytic balanced jet, resident in HBM)",
+            "config": {"workload": wl.name, "grid": "R2B%d" % wl.bisections, "cells": nc, "edges": ne,
+                       "levels": N, "dt": wl.dt, "nsub": wl.nsub, "precision": "fp64" if wl.precision == 0
+                       else "mixed", "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (state %.2f GB)" % ((ne * N + 4 * nc * N) * 8 / 1e9)},
+            "gpu_launches": kernels_per_step * args.steps, "roofline": roof, "kernels": breakdown,
+            "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
+            "mass_rel_drift": abs(m1 - m0) / m0}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="r2b6-fp64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, wl, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as td
+        torch.cuda.set_device(local_rank)
+        td.init_process_group("nccl")
+    run_gpu(args, wl, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as td
+        td.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

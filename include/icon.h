@@ -184,6 +184,12 @@ int icon_state_status(icon_state* state);
  * (fixed summation order, bit-identical between calls on the same device). */
 int icon_global_mass(const icon_state* state, double* out);
 
+/* As icon_global_mass without waiting: enqueues the reduction and an asynchronous
+ * copy of the result into host_out (8 bytes; pinned host memory for a truly
+ * asynchronous copy). The value is valid after the bound stream has been
+ * synchronised. */
+int icon_global_mass_async(const icon_state* state, double* host_out);
+
 /* Copy a field (icon_field) to host memory as FP64, [entity][level] unpadded;
  * count must equal the field's element count. Synchronous. */
 int icon_state_copy_field(const icon_state* state, int field_id, double* host_dst, size_t count);
@@ -192,6 +198,21 @@ int icon_state_copy_field(const icon_state* state, int field_id, double* host_ds
  * in the same layout (rounded to FP32 where the state stores FP32). w at the lid
  * and the ground must be 0. Synchronous with respect to host_src. */
 int icon_state_set_field(icon_state* state, int field_id, const double* host_src, size_t count);
+
+/* Number of kernel launches in the recorded graph of one step with the given
+ * (dt, nsubsteps) (records it if needed; no work is enqueued). */
+int icon_state_step_kernels(icon_state* state, double dt, int nsubsteps, int* out);
+
+/* Run one step eagerly (not from the graph) with a CUDA event pair around every
+ * kernel launch and add each launch's duration (ms) to ms_per_kind[kind] and 1 to
+ * launches_per_kind[kind] (host arrays of ICON_KIND_COUNT entries, accumulated,
+ * not cleared). The state advances exactly as with icon_dycore_step. Waits. */
+int icon_dycore_step_profile(icon_state* state, double dt, int nsubsteps, double* ms_per_kind,
+                             int* launches_per_kind);
+
+/* Name of kernel kind i (0 <= i < ICON_KIND_COUNT), or NULL. */
+const char* icon_kernel_kind_name(int kind);
+#define ICON_KIND_COUNT 24
 
 /* Storage precision of the state (icon_precision). */
 int icon_state_precision(const icon_state* state, int* out);

@@ -62,7 +62,10 @@ def _load():
         "icon_state_init_ex": (I, [P, ctypes.c_uint64, I, ctypes.POINTER(CaseParams), ctypes.POINTER(P)]),
         "icon_dycore_step": (I, [P, D, I]), "icon_dycore_step_async": (I, [P, D, I]),
         "icon_state_status": (I, [P]),
-        "icon_global_mass": (I, [P, ctypes.POINTER(D)]),
+        "icon_global_mass": (I, [P, ctypes.POINTER(D)]), "icon_global_mass_async": (I, [P, P]),
+        "icon_state_step_kernels": (I, [P, D, I, ctypes.POINTER(I)]),
+        "icon_dycore_step_profile": (I, [P, D, I, ctypes.POINTER(D), ctypes.POINTER(I)]),
+        "icon_kernel_kind_name": (ctypes.c_char_p, [I]),
         "icon_state_copy_field": (I, [P, I, P, S]), "icon_state_set_field": (I, [P, I, P, S]),
         "icon_state_precision": (I, [P, ctypes.POINTER(I)]), "icon_state_free": (None, [P]),
         "icon_ensemble_create": (I, [ctypes.POINTER(P), I, ctypes.POINTER(P)]),
@@ -164,6 +167,36 @@ def icon_global_mass(state):
     m = ctypes.c_double()
     _check(_lib.icon_global_mass(state, ctypes.byref(m)))
     return m.value
+
+
+def icon_global_mass_async(state, host_ptr):
+    """Enqueue the mass integral; the result lands in the 8-byte host buffer at host_ptr."""
+    _check(_lib.icon_global_mass_async(state, ctypes.c_void_p(host_ptr)))
+
+
+def icon_state_step_kernels(state, dt, nsubsteps):
+    n = ctypes.c_int()
+    _check(_lib.icon_state_step_kernels(state, dt, nsubsteps, ctypes.byref(n)))
+    return n.value
+
+
+ICON_KIND_COUNT = 24
+
+
+def icon_dycore_step_profile(state, dt, nsubsteps, ms=None, launches=None):
+    """One eager step with CUDA events around every launch; returns the accumulated
+    (ms per kind, launches per kind) arrays."""
+    if ms is None:
+        ms = np.zeros(ICON_KIND_COUNT)
+        launches = np.zeros(ICON_KIND_COUNT, dtype=np.int32)
+    _check(_lib.icon_dycore_step_profile(state, dt, nsubsteps, ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         launches.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+    return ms, launches
+
+
+def icon_kernel_kind_name(kind):
+    n = _lib.icon_kernel_kind_name(kind)
+    return n.decode() if n else None
 
 
 def _field_shape(grid, name, nlev):

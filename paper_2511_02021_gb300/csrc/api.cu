@@ -27,6 +27,40 @@ int cuda_fail(cudaError_t e, const char* what) {
   return ICON_ECUDA;
 }
 
+// ---------------------------------------------------------------- profiling
+struct Prof {
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> kind;
+  int open = -1;
+  bool failed = false;
+};
+static thread_local Prof* t_prof = nullptr;
+
+void prof_begin(cudaStream_t st, int kind) {
+  Prof* p = t_prof;
+  if (!p || p->failed) return;
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) { p->failed = true; return; }
+  p->ev.push_back(a);
+  p->ev.push_back(b);
+  p->kind.push_back(kind);
+  p->open = (int)p->kind.size() - 1;
+  cudaEventRecord(a, st);
+}
+
+void prof_end(cudaStream_t st) {
+  Prof* p = t_prof;
+  if (!p || p->failed || p->open < 0) return;
+  cudaEventRecord(p->ev[2 * p->open + 1], st);
+  p->open = -1;
+}
+
+static const char* kKindNames[K_KIND_COUNT] = {
+    "vertex_curl_wmean", "edge_vt_ke", "cell_ke", "edge_tendency_flux", "column_solve",
+    "diff_vertex", "diff_div", "diff_edge", "diff_theta", "global_mass",
+    "mx_vertex", "mx_edge_diag", "mx_cell_ke", "mx_edge_tendency_flux", "mx_column_solve", "mx_column_prep",
+    "mx_diff_vertex", "mx_diff_edge", "mx_diff_theta", "ensemble_persistent"};
+
 Allocator current_allocator() {
   std::lock_guard<std::mutex> lk(g_alloc_mu);
   return g_alloc;
@@ -170,28 +204,46 @@ void enqueue_step(icon_state* st, double dt, int nsub, cudaStream_t stream) {
   else enqueue_step_mixed(st, dt, nsub, stream);
 }
 
-// record (once per (dt, nsub)) and launch the graph of one step
-int launch_step(icon_state* st, double dt, int nsub, cudaStream_t stream) {
-  if (!st->graph || st->graph_dt != dt || st->graph_nsub != nsub) {
-    if (st->graph) {
-      cudaGraphExecDestroy(st->graph);
-      st->graph = nullptr;
-    }
-    if (!st->capture_stream) ICON_CUDA(cudaStreamCreateWithFlags(&st->capture_stream, cudaStreamNonBlocking));
-    cudaGraph_t g = nullptr;
-    ICON_CUDA(cudaStreamBeginCapture(st->capture_stream, cudaStreamCaptureModeThreadLocal));
-    enqueue_step(st, dt, nsub, st->capture_stream);
-    cudaError_t e = cudaStreamEndCapture(st->capture_stream, &g);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&st->graph, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) {
-      st->graph = nullptr;
-      return cuda_fail(e, "cudaGraphInstantiate");
-    }
-    st->graph_dt = dt;
-    st->graph_nsub = nsub;
+// record the graph of one step for (dt, nsub) unless it is already recorded
+int record_graph(icon_state* st, double dt, int nsub) {
+  if (st->graph && st->graph_dt == dt && st->graph_nsub == nsub) return ICON_OK;
+  if (st->graph) {
+    cudaGraphExecDestroy(st->graph);
+    st->graph = nullptr;
   }
+  if (!st->capture_stream) ICON_CUDA(cudaStreamCreateWithFlags(&st->capture_stream, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  ICON_CUDA(cudaStreamBeginCapture(st->capture_stream, cudaStreamCaptureModeThreadLocal));
+  Prof* saved = t_prof;
+  t_prof = nullptr;
+  enqueue_step(st, dt, nsub, st->capture_stream);
+  t_prof = saved;
+  cudaError_t e = cudaStreamEndCapture(st->capture_stream, &g);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  size_t nn = 0;
+  cudaGraphGetNodes(g, nullptr, &nn);
+  std::vector<cudaGraphNode_t> nodes(nn);
+  if (nn) cudaGraphGetNodes(g, nodes.data(), &nn);
+  int nk = 0;
+  for (size_t i = 0; i < nn; ++i) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++nk;
+  }
+  e = cudaGraphInstantiate(&st->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    st->graph = nullptr;
+    return cuda_fail(e, "cudaGraphInstantiate");
+  }
+  st->graph_dt = dt;
+  st->graph_nsub = nsub;
+  st->graph_kernels = nk;
+  return ICON_OK;
+}
+
+int launch_step(icon_state* st, double dt, int nsub, cudaStream_t stream) {
+  int rc = record_graph(st, dt, nsub);
+  if (rc != ICON_OK) return rc;
   ICON_CUDA(cudaGraphLaunch(st->graph, stream));
   return ICON_OK;
 }
@@ -398,6 +450,59 @@ int icon_global_mass(const icon_state* st, double* out) {
   ICON_CUDA(cudaStreamSynchronize(stream));
   *out = h;
   return ICON_OK;
+}
+
+int icon_global_mass_async(const icon_state* st, double* host_out) {
+  if (!st || !host_out) { set_error("icon_global_mass_async: NULL argument"); return ICON_EINVAL; }
+  cudaStream_t stream = current_stream();
+  double* d_out = st->s.mass_part + mass_partials_count(st->grid->g.nc);
+  enqueue_mass(st, d_out, stream);
+  ICON_CUDA(cudaGetLastError());
+  ICON_CUDA(cudaMemcpyAsync(host_out, d_out, sizeof(double), cudaMemcpyDeviceToHost, stream));
+  return ICON_OK;
+}
+
+int icon_state_step_kernels(icon_state* st, double dt, int nsubsteps, int* out) {
+  if (!st || !out) { set_error("icon_state_step_kernels: NULL argument"); return ICON_EINVAL; }
+  if (!(dt > 0.0) || nsubsteps < 1 || nsubsteps > 64) {
+    set_error("icon_state_step_kernels: need dt > 0 and 1 <= nsubsteps <= 64");
+    return ICON_EINVAL;
+  }
+  int rc = record_graph(st, dt, nsubsteps);
+  if (rc != ICON_OK) return rc;
+  *out = st->graph_kernels;
+  return ICON_OK;
+}
+
+int icon_dycore_step_profile(icon_state* st, double dt, int nsubsteps, double* ms_per_kind, int* launches_per_kind) {
+  if (!st || !ms_per_kind || !launches_per_kind) { set_error("icon_dycore_step_profile: NULL argument"); return ICON_EINVAL; }
+  if (!(dt > 0.0) || nsubsteps < 1 || nsubsteps > 64) { set_error("icon_dycore_step_profile: bad dt/nsubsteps"); return ICON_EINVAL; }
+  cudaStream_t stream = current_stream();
+  Prof prof;
+  t_prof = &prof;
+  enqueue_step(st, dt, nsubsteps, stream);
+  t_prof = nullptr;
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  int rc = ICON_OK;
+  if (e != cudaSuccess) rc = cuda_fail(e, "icon_dycore_step_profile");
+  if (rc == ICON_OK && prof.failed) { set_error("icon_dycore_step_profile: event creation failed"); rc = ICON_ECUDA; }
+  if (rc == ICON_OK) {
+    for (size_t i = 0; i < prof.kind.size(); ++i) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, prof.ev[2 * i], prof.ev[2 * i + 1]);
+      ms_per_kind[prof.kind[i]] += ms;
+      launches_per_kind[prof.kind[i]] += 1;
+    }
+  }
+  for (cudaEvent_t ev : prof.ev) cudaEventDestroy(ev);
+  if (rc != ICON_OK) return rc;
+  return sync_status(st, stream);
+}
+
+const char* icon_kernel_kind_name(int kind) {
+  if (kind < 0 || kind >= K_KIND_COUNT) return nullptr;
+  return kKindNames[kind];
 }
 
 int icon_state_copy_field(const icon_state* st, int field_id, double* host_dst, size_t count) {

@@ -439,9 +439,15 @@ void enqueue_step_fp64(icon_state* st, double dt, int nsub, cudaStream_t stream)
       const double* rho_st = corr ? s.rho_s : s.rho;
       const double* thv_st = corr ? s.thv_s : s.thv;
       const double* ex_st = corr ? s.ex_s : s.ex;
+      prof_begin(stream, K_VERTEX);
       k_vertex<<<nbv, 256, 0, stream>>>(G, vn_st, w_st, s.zeta, s.w_v);
+      prof_end(stream);
+      prof_begin(stream, K_EDGE_VT);
       k_edge_vt<<<nbe, 256, 0, stream>>>(G, vn_st, s.vt, s.Ke);
+      prof_end(stream);
+      prof_begin(stream, K_CELL_KE);
       k_cell_ke<<<nbc, 256, 0, stream>>>(G, s.Ke, s.Kc);
+      prof_end(stream);
       EdgeArgs ea;
       ea.vn = vn_st; ea.w = w_st; ea.rho = rho_st; ea.thv = thv_st; ea.ex = ex_st;
       ea.vt = s.vt; ea.Kc = s.Kc; ea.zeta = s.zeta; ea.w_v = s.w_v;
@@ -450,7 +456,9 @@ void enqueue_step_fp64(icon_state* st, double dt, int nsub, cudaStream_t stream)
       ea.Avn0 = s.Avn0;
       ea.F = s.F; ea.G = s.G; ea.a_e = s.a_e; ea.mflx = s.mflx;
       ea.dtau = dtau; ea.nsub = (double)nsub; ea.corrector = corr;
+      prof_begin(stream, K_EDGE_TEND);
       k_edge_tend<<<nbe, 256, 0, stream>>>(G, ea);
+      prof_end(stream);
       ColArgs ca;
       ca.rho = s.rho; ca.thv = s.thv; ca.ex = s.ex; ca.w = s.w;
       ca.w_stage = w_st;
@@ -463,13 +471,23 @@ void enqueue_step_fp64(icon_state* st, double dt, int nsub, cudaStream_t stream)
       ca.wflx = s.wflx;
       ca.status = s.status;
       ca.dtau = dtau; ca.nsub = (double)nsub; ca.corrector = corr;
+      prof_begin(stream, K_COLUMN);
       launch_column(G, ca, stream);
+      prof_end(stream);
     }
   }
+  prof_begin(stream, K_DIFF_VERTEX);
   k_diff_vertex<<<nbv, 256, 0, stream>>>(G, s.vn, s.uvx, s.uvy, s.uvz, s.zeta);
+  prof_end(stream);
+  prof_begin(stream, K_DIFF_DIV);
   k_diff_div<<<nbc, 256, 0, stream>>>(G, s.vn, s.divc);
+  prof_end(stream);
+  prof_begin(stream, K_DIFF_EDGE);
   k_diff_edge<<<nbe, 256, 0, stream>>>(G, s.vn, s.uvx, s.uvy, s.uvz, s.zeta, s.divc, s.thv, s.Kh, s.thflx, dt);
+  prof_end(stream);
+  prof_begin(stream, K_DIFF_THETA);
   k_diff_theta<<<nbc, 256, 0, stream>>>(G, s.thflx, s.thv, s.ex, dt);
+  prof_end(stream);
 }
 
 }  // namespace icon

@@ -30,6 +30,18 @@ int cuda_fail(cudaError_t e, const char* what);
     if (_e != cudaSuccess) return ::icon::cuda_fail(_e, #call);                \
   } while (0)
 
+// ---------------------------------------------------------------- kernel kinds and profiling
+enum KernelKind {
+  K_VERTEX = 0, K_EDGE_VT, K_CELL_KE, K_EDGE_TEND, K_COLUMN,
+  K_DIFF_VERTEX, K_DIFF_DIV, K_DIFF_EDGE, K_DIFF_THETA, K_MASS,
+  K_MX_VERTEX, K_MX_EDGE, K_MX_CELL_KE, K_MX_EDGE_TEND, K_MX_COLUMN, K_MX_COLUMN_PREP,
+  K_MX_DIFF_VERTEX, K_MX_DIFF_EDGE, K_MX_DIFF_THETA, K_ENSEMBLE, K_KIND_COUNT
+};
+static_assert(K_KIND_COUNT <= ICON_KIND_COUNT, "kind table");
+// When a profile is active on this thread, every launch is bracketed by events.
+void prof_begin(cudaStream_t st, int kind);
+void prof_end(cudaStream_t st);
+
 // ---------------------------------------------------------------- memory
 struct Allocator {
   void* (*alloc)(size_t, void*) = nullptr;
@@ -133,6 +145,7 @@ struct icon_state {
   cudaGraphExec_t graph = nullptr;
   double graph_dt = 0.0;
   int graph_nsub = 0;
+  int graph_kernels = 0;
   cudaStream_t capture_stream = nullptr;
   cudaStream_t graph_stream = nullptr;
   cudaEvent_t done = nullptr;

@@ -56,9 +56,11 @@ int mass_partials_count(int64_t) { return kMassBlocks; }
 
 void enqueue_mass(const icon_state* st, double* d_out, cudaStream_t stream) {
   const icon_grid* grid = st->grid;
+  prof_begin(stream, K_MASS);
   k_mass_partial<<<kMassBlocks, kMassThreads, 0, stream>>>(grid->g.nc, grid->vert.N, grid->vert.ld, st->s.rho,
                                                            grid->vert.d_dz, grid->g.A_c, st->s.mass_part);
   k_mass_final<<<1, 1024, 0, stream>>>(st->s.mass_part, kMassBlocks, d_out);
+  prof_end(stream);
 }
 
 }  // namespace icon
