@@ -22,8 +22,8 @@
  *     (the Python binding registers PyTorch's caching allocator) or from
  *     cudaMalloc when none is registered. Work is issued on the stream bound by
  *     icon_set_stream (default: the legacy default stream).
- *   - Pointers named host_* are host memory (pageable or pinned); no pointer in
- *     this interface is a device pointer.
+ *   - Pointers named host_* are host memory (pageable or pinned); pointers named
+ *     dev_* are device memory; no other pointer argument is a device pointer.
  *   - Sizes are element counts unless named *bytes.
  *   - Entry points are not reentrant on the same handle; distinct handles may be
  *     used from distinct threads.
@@ -189,6 +189,32 @@ int icon_global_mass(const icon_state* state, double* out);
  * asynchronous copy). The value is valid after the bound stream has been
  * synchronised. */
 int icon_global_mass_async(const icon_state* state, double* host_out);
+
+/* Global air mass of a caller-owned density array, with no device allocation.
+ *
+ * The paper has no counterpart to this entry point. It exists for callers that
+ * cannot allocate device memory when they need the integral: a component
+ * embedded in a host model whose device memory belongs to that model's pool
+ * allocator, or a latency-bound loop that forbids allocations after start-up.
+ *
+ * dev_rho is DEVICE memory holding the density of every cell of `grid`, row c at
+ * dev_rho + c*ld, levels 0..N-1 used (ld >= N). The result, in kg, is written to
+ * *host_out; the call waits for it. The geometry (cell areas, layer thickness)
+ * comes from the grid. Same integral as icon_global_mass, summed per block of
+ * 1024 cells in a fixed order (deterministic; it may differ from icon_global_mass
+ * in the last bits because the grouping of the sum differs).
+ *
+ * Scratch: the partial sums live in one fixed array inside the library
+ * (16384 partials, 128 KiB), which every GPU that loads the library holds until
+ * the process exits. Hence at most 16,777,216 cells (R2B8 fits, R2B9 does not);
+ * larger grids, ld < N, NULL pointers or more than 64 devices give ICON_EINVAL
+ * with a message. Nothing is allocated and no allocating library routine is
+ * called. The first call on a device looks up the array's device address (with
+ * that device current); make that first call before any stream capture. Every
+ * call on a device shares the array and overwrites it (each call rewrites every
+ * partial it reads), so calls that overlap on the GPU, for instance from two
+ * host threads or on two streams, race and must be serialised by the caller. */
+int icon_global_mass_noalloc(const icon_grid* grid, const double* dev_rho, int ld, double* host_out);
 
 /* Copy a field (icon_field) to host memory as FP64, [entity][level] unpadded;
  * count must equal the field's element count. Synchronous. */

@@ -66,6 +66,7 @@ def _load():
         "icon_state_step_kernels": (I, [P, D, I, ctypes.POINTER(I)]),
         "icon_dycore_step_profile": (I, [P, D, I, ctypes.POINTER(D), ctypes.POINTER(I)]),
         "icon_kernel_kind_name": (ctypes.c_char_p, [I]),
+        "icon_global_mass_noalloc": (I, [P, P, I, ctypes.POINTER(D)]),
         "icon_state_copy_field": (I, [P, I, P, S]), "icon_state_set_field": (I, [P, I, P, S]),
         "icon_state_precision": (I, [P, ctypes.POINTER(I)]), "icon_state_free": (None, [P]),
         "icon_ensemble_create": (I, [ctypes.POINTER(P), I, ctypes.POINTER(P)]),
@@ -172,6 +173,13 @@ def icon_global_mass(state):
 def icon_global_mass_async(state, host_ptr):
     """Enqueue the mass integral; the result lands in the 8-byte host buffer at host_ptr."""
     _check(_lib.icon_global_mass_async(state, ctypes.c_void_p(host_ptr)))
+
+
+def icon_global_mass_noalloc(grid, dev_rho_ptr, ld):
+    """Mass of a caller-owned device density array [Nc][ld] without any device allocation."""
+    m = ctypes.c_double()
+    _check(_lib.icon_global_mass_noalloc(grid, ctypes.c_void_p(dev_rho_ptr), ld, ctypes.byref(m)))
+    return m.value
 
 
 def icon_state_step_kernels(state, dt, nsubsteps):

@@ -5,6 +5,7 @@
 // reduces its warps in a fixed order into one partial, and a single block sums
 // the partials in a fixed tree. Repeated calls on the same device give
 // bit-identical results.
+#include <mutex>
 #include "icon_internal.h"
 
 namespace icon {
@@ -64,3 +65,101 @@ void enqueue_mass(const icon_state* st, double* d_out, cudaStream_t stream) {
 }
 
 }  // namespace icon
+
+// ---------------------------------------------------------------- allocation-free variant
+//
+// Some callers cannot allocate device memory at all when they need the mass
+// integral: a component embedded in a host model whose device memory is owned by
+// that model's pool allocator, or a latency-bound loop that forbids allocations
+// after start-up. For them icon_global_mass_noalloc reduces a caller-owned density
+// array with its partial sums in the fixed device array below, which every GPU
+// that loads this library holds until the process exits.
+namespace icon {
+namespace {
+
+constexpr int kNoAllocCellsPerBlock = 1024;
+constexpr int kNoAllocMaxPartials = 16384;                       // 128 KiB of partial sums
+constexpr int64_t kNoAllocMaxCells = (int64_t)kNoAllocCellsPerBlock * kNoAllocMaxPartials;
+constexpr int kNoAllocMaxDevices = 64;
+
+// partial sums [0, nblk) and the result [kNoAllocMaxPartials]; shared by every call
+static __device__ __align__(256) double g_mass_scratch[kNoAllocMaxPartials + 1];
+
+// block b sums the cells [b * 1024, (b + 1) * 1024) in a fixed order
+__global__ void __launch_bounds__(kMassThreads) k_mass_partial_blocked(int64_t nc, int N, int ld,
+                                                                       const double* __restrict__ rho,
+                                                                       const double* __restrict__ dz,
+                                                                       const double* __restrict__ A_c,
+                                                                       double* __restrict__ part) {
+  __shared__ double ws[kMassThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t c0 = (int64_t)blockIdx.x * kNoAllocCellsPerBlock;
+  const int64_t c1 = c0 + kNoAllocCellsPerBlock < nc ? c0 + kNoAllocCellsPerBlock : nc;
+  double acc = 0.0;
+  for (int64_t c = c0 + wid; c < c1; c += kMassThreads / 32) {
+    double col = 0.0;
+    for (int k = lane; k < N; k += 32) col += rho[c * ld + k] * dz[k];
+    for (int o = 16; o > 0; o >>= 1) col += __shfl_xor_sync(0xffffffffu, col, o);
+    acc += A_c[c] * col;
+  }
+  if (lane == 0) ws[wid] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < kMassThreads / 32; ++i) s += ws[i];
+    part[blockIdx.x] = s;
+  }
+}
+
+std::once_flag g_noalloc_once[kNoAllocMaxDevices];
+double* g_noalloc_ptr[kNoAllocMaxDevices];
+cudaError_t g_noalloc_err[kNoAllocMaxDevices];
+
+}  // namespace
+}  // namespace icon
+
+extern "C" int icon_global_mass_noalloc(const icon_grid* grid, const double* dev_rho, int ld, double* host_out) {
+  using namespace icon;
+  if (!grid || !dev_rho || !host_out) {
+    set_error("icon_global_mass_noalloc: NULL argument");
+    return ICON_EINVAL;
+  }
+  const int N = grid->vert.N;
+  const int64_t nc = grid->g.nc;
+  if (ld < N) {
+    set_error("icon_global_mass_noalloc: row stride %d is smaller than the %d levels", ld, N);
+    return ICON_EINVAL;
+  }
+  if (nc > kNoAllocMaxCells) {
+    set_error("icon_global_mass_noalloc: %lld cells exceed the maximum of %lld (fixed scratch of %d partial "
+              "sums of %d cells each); use icon_global_mass", (long long)nc, (long long)kNoAllocMaxCells,
+              kNoAllocMaxPartials, kNoAllocCellsPerBlock);
+    return ICON_EINVAL;
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kNoAllocMaxDevices) {
+    set_error("icon_global_mass_noalloc: device %d is beyond the %d supported devices", dev, kNoAllocMaxDevices);
+    return ICON_EINVAL;
+  }
+  // once per device, with that device current: the device address of the scratch array
+  std::call_once(g_noalloc_once[dev], [dev]() {
+    g_noalloc_err[dev] = cudaGetSymbolAddress((void**)&g_noalloc_ptr[dev], g_mass_scratch);
+  });
+  if (g_noalloc_err[dev] != cudaSuccess) return cuda_fail(g_noalloc_err[dev], "cudaGetSymbolAddress");
+  double* scratch = g_noalloc_ptr[dev];
+  const int nblk = (int)((nc + kNoAllocCellsPerBlock - 1) / kNoAllocCellsPerBlock);
+  cudaStream_t stream = current_stream();
+  k_mass_partial_blocked<<<nblk, kMassThreads, 0, stream>>>(nc, N, ld, dev_rho, grid->vert.d_dz, grid->g.A_c,
+                                                            scratch);
+  k_mass_final<<<1, 1024, 0, stream>>>(scratch, nblk, scratch + kNoAllocMaxPartials);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "icon_global_mass_noalloc launch");
+  double h = 0.0;
+  e = cudaMemcpyAsync(&h, scratch + kNoAllocMaxPartials, sizeof(double), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return cuda_fail(e, "icon_global_mass_noalloc");
+  *host_out = h;
+  return ICON_OK;
+}
