@@ -51,6 +51,11 @@ def peaks():
 # probe on this pool (505 G instr/s; NVIDIA's nominal 1.25 TFLOP/s FMA is 625 G instr/s
 # at 2.07 GHz). Used as the peak of kernels bound by FP64 arithmetic.
 FP64_INSTR_PEAK = 505e9
+# FP64 arithmetic operations per cell-level of one mixed column-solve launch (predictor and
+# corrector averaged), counted from the kernel source: interpolation 6, explicit predictors
+# and flux sums 17, w predictor and tridiagonal row 16, Thomas sweeps with one reciprocal
+# (counted as 1) 6, updates 14, conversions to and from FP32 10.
+MX_COLUMN_FP64_OPS = 69
 
 
 def counts(wl):
@@ -80,6 +85,16 @@ def kernel_model(kind, wl):
         "diff_edge": (b * (ne * N * 4 + nv * N * 5 + nc * N * 2), ne * N * 45),
         "diff_theta": (b * (ne * N + 4 * nc * N), nc * N * 12),
         "global_mass": (b * nc * N, nc * N * 2),
+        # mixed precision: FP32 stencil arrays (4 B), FP64 level-major prognostics (8 B)
+        "mx_vertex": (4.0 * (ne * N + nc * H + nv * N + nv * H), 0),
+        "mx_edge_diag": (4.0 * 3 * ne * N, 0),
+        "mx_cell_ke": (4.0 * (ne + nc) * N, 0),
+        "mx_edge_tendency_flux": (4.0 * (ne * N * 6.5 + ne * H + nc * N * 4 + nv * N + nc * H + nv * H)
+                                  + 8.0 * ne * N, ne * N * 1.0),
+        "mx_column_solve": (nc * N * 98.0, nc * N * MX_COLUMN_FP64_OPS),
+        "mx_diff_vertex": (4.0 * (2 * ne * N + 4 * nv * N + nc * N), 0),
+        "mx_diff_edge": (4.0 * (ne * N * 4 + nv * N * 3 + nc * N * 2), 0),
+        "mx_diff_theta": (4.0 * ne * N + 40.0 * nc * N, nc * N * 6),
     }
     return table.get(kind)
 
@@ -126,19 +141,25 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- reference arm (oracle on host cores)
-def oracle_sample(wl):
-    """Time the oracle on one substep (predictor + corrector) of the workload, init excluded.
-    Returns (cell-level updates/s, seconds, description)."""
-    import oracle as O
-    from oracle import dycore as OD
-    g = O.build_grid(2, wl.bisections)
-    v = O.vertical_grid(wl.nlev)
-    s = O.init_state(g, v, wl.seed, wl.case, noise_K=(wl.noise_K if wl.noise_K >= 0 else None))
-    acc = {"mflx": np.zeros((g.ne, v.N)), "wflx": np.zeros((g.nc, v.N + 1))}
-    t0 = time.perf_counter()
-    OD.substep(g, v, s, wl.dt / wl.nsub, wl.nsub, acc)
-    el = time.perf_counter() - t0
-    return g.nc * v.N / el, el, "one substep of %s (init excluded)" % wl.name
+class OracleSampler:
+    """The oracle on the workload's grid and initial state (built once, untimed); each
+    sample times one substep (predictor + corrector) continuing from the last one."""
+
+    def __init__(self, wl):
+        import oracle as O
+        from oracle import dycore as OD
+        self.OD, self.wl = OD, wl
+        self.g = O.build_grid(2, wl.bisections)
+        self.v = O.vertical_grid(wl.nlev)
+        self.s = O.init_state(self.g, self.v, wl.seed, wl.case, noise_K=(wl.noise_K if wl.noise_K >= 0 else None))
+
+    def sample(self):
+        g, v, wl = self.g, self.v, self.wl
+        acc = {"mflx": np.zeros((g.ne, v.N)), "wflx": np.zeros((g.nc, v.N + 1))}
+        t0 = time.perf_counter()
+        self.s = self.OD.substep(g, v, self.s, wl.dt / wl.nsub, wl.nsub, acc)
+        el = time.perf_counter() - t0
+        return g.nc * v.N / el, el, "one substep (predictor + corrector) of %s, init excluded" % wl.name
 
 
 def run_reference(args, wl, rank):
@@ -146,8 +167,9 @@ def run_reference(args, wl, rank):
         return
     # the oracle is plain numpy: its array operations run on one host core
     vals = []
+    smp = OracleSampler(wl)
     for i in range(args.warmup + args.steps):
-        v, el, desc = oracle_sample(wl)
+        v, el, desc = smp.sample()
         if i >= args.warmup:
             vals.append(el)
     t = sum(vals) / len(vals)
@@ -182,68 +204,100 @@ def run_gpu(args, wl, rank, world, local_rank):
     nc, ne, nv = counts(wl)
     N = wl.nlev
     grid = C.icon_grid_build(2, wl.bisections, N)
-    st = C.icon_state_init_ex(grid, wl.seed + rank, wl.case, noise_K=wl.noise_K, precision=wl.precision)
-    m0 = C.icon_global_mass(st)
-    for _ in range(args.warmup):
-        C.icon_dycore_step(st, wl.dt, wl.nsub)
-    kernels_per_step = C.icon_state_step_kernels(st, wl.dt, wl.nsub) + 2      # + the mass integral
-    mass_host = torch.empty(1, dtype=torch.float64, pin_memory=True)
-
-    clocks = ClockSampler(local_rank) if rank == 0 else None
-    time.sleep(0.4)
-    if dist:
-        td.barrier()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        C.icon_dycore_step_async(st, wl.dt, wl.nsub)
-        C.icon_global_mass_async(st, mass_host.data_ptr())
-    e1.record(stream)
-    torch.cuda.synchronize()
-    if dist:
-        td.barrier()
-    ms = e0.elapsed_time(e1)
-    clk = clocks.stop() if clocks else None
-    C.icon_state_status(st)                                   # raises on non-finite values
-    m1 = float(mass_host[0])
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        td.all_reduce(t, op=td.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * nc * N * wl.nsub * args.steps / (ms * 1e-3)
-
-    # per-kernel durations, measured live with CUDA events around every launch
-    kms, kn = None, None
-    for _ in range(2):
-        kms, kn = C.icon_dycore_step_profile(st, wl.dt, wl.nsub, kms, kn)
     hbm_peak, peak_src = peaks()
-    rows = []
-    for k in range(C.ICON_KIND_COUNT):
-        if kn[k] == 0:
-            continue
-        name = C.icon_kernel_kind_name(k)
-        avg = kms[k] / kn[k]
-        model = kernel_model(name, wl)
-        gbs = model[0] / (avg * 1e-3) / 1e9 if model else None
-        fops = model[1] / (avg * 1e-3) if model else None
-        rows.append((kms[k] / 2, name, avg, int(kn[k] // 2), gbs, fops))
-    rows.sort(reverse=True)
-    top = rows[0]
-    hbm_frac = top[4] / hbm_peak if top[4] else None
-    alu_frac = top[5] / FP64_INSTR_PEAK if top[5] else None
-    if alu_frac is not None and hbm_frac is not None and alu_frac > hbm_frac:
-        roof = {"kernel": top[1], "bound": "alu", "achieved": top[5] / 1e9, "peak": FP64_INSTR_PEAK / 1e9,
-                "unit": "GFLOP/s (FP64)", "frac": alu_frac, "traffic": None,
-                "hbm": {"achieved": top[4], "peak": hbm_peak, "unit": "GB/s", "frac": hbm_frac,
-                        "peak_source": peak_src},
-                "launch_ms": top[2], "launches_per_step": top[3]}
-    else:
-        roof = {"kernel": top[1], "bound": "hbm", "achieved": top[4], "peak": hbm_peak, "unit": "GB/s",
-                "frac": hbm_frac, "traffic": None, "peak_source": peak_src, "launch_ms": top[2],
-                "launches_per_step": top[3]}
-    breakdown = {r[1]: {"ms_per_step": round(r[0], 4), "share": round(r[0] / sum(x[0] for x in rows), 4)}
-                 for r in rows}
+
+    def measure(precision, sample_clocks):
+        """Time K steps (+ mass) of one precision; returns the state and the measurements."""
+        st = C.icon_state_init_ex(grid, wl.seed + rank, wl.case, noise_K=wl.noise_K, precision=precision)
+        m0 = C.icon_global_mass(st)
+        for _ in range(args.warmup):
+            C.icon_dycore_step(st, wl.dt, wl.nsub)
+        kps = C.icon_state_step_kernels(st, wl.dt, wl.nsub) + 2      # + the mass integral
+        mass_host = torch.empty(1, dtype=torch.float64, pin_memory=True)
+        clocks = ClockSampler(local_rank) if (rank == 0 and sample_clocks) else None
+        time.sleep(0.4)
+        if dist:
+            td.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            C.icon_dycore_step_async(st, wl.dt, wl.nsub)
+            C.icon_global_mass_async(st, mass_host.data_ptr())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            td.barrier()
+        ms = e0.elapsed_time(e1)
+        clk = clocks.stop() if clocks else None
+        C.icon_state_status(st)                               # raises on non-finite values
+        m1 = float(mass_host[0])
+        if dist:
+            t = torch.tensor([ms], device="cuda")
+            td.all_reduce(t, op=td.ReduceOp.MAX)
+            ms = float(t.item())
+        value = world * nc * N * wl.nsub * args.steps / (ms * 1e-3)
+        # per-kernel durations, measured live with CUDA events around every launch
+        kms, kn = None, None
+        for _ in range(2):
+            kms, kn = C.icon_dycore_step_profile(st, wl.dt, wl.nsub, kms, kn)
+        rows = []
+        for k in range(C.ICON_KIND_COUNT):
+            if kn[k] == 0:
+                continue
+            name = C.icon_kernel_kind_name(k)
+            avg = kms[k] / kn[k]
+            model = kernel_model(name, wl)
+            gbs = model[0] / (avg * 1e-3) / 1e9 if model else None
+            fops = model[1] / (avg * 1e-3) if model else None
+            rows.append((kms[k] / 2, name, avg, int(kn[k] // 2), gbs, fops))
+        rows.sort(reverse=True)
+        top = rows[0]
+        hbm_frac = top[4] / hbm_peak if top[4] else None
+        alu_frac = top[5] / FP64_INSTR_PEAK if top[5] else None
+        if alu_frac is not None and hbm_frac is not None and alu_frac > hbm_frac:
+            roof = {"kernel": top[1], "bound": "alu", "achieved": top[5] / 1e9, "peak": FP64_INSTR_PEAK / 1e9,
+                    "unit": "GFLOP/s (FP64)", "frac": alu_frac, "traffic": None,
+                    "hbm": {"achieved": top[4], "peak": hbm_peak, "unit": "GB/s", "frac": hbm_frac,
+                            "peak_source": peak_src},
+                    "launch_ms": top[2], "launches_per_step": top[3]}
+        else:
+            roof = {"kernel": top[1], "bound": "hbm", "achieved": top[4], "peak": hbm_peak, "unit": "GB/s",
+                    "frac": hbm_frac, "traffic": None, "peak_source": peak_src, "launch_ms": top[2],
+                    "launches_per_step": top[3],
+                    "fp64": {"achieved": (top[5] or 0) / 1e9, "peak": FP64_INSTR_PEAK / 1e9,
+                             "unit": "GFLOP/s", "frac": alu_frac}}
+        tot = sum(x[0] for x in rows)
+        breakdown = {r[1]: {"ms_per_step": round(r[0], 4), "share": round(r[0] / tot, 4)} for r in rows}
+        return st, {"value": value, "ms": ms, "kps": kps, "roof": roof, "breakdown": breakdown, "clocks": clk,
+                    "mass_rel_drift": abs(m1 - m0) / m0}
+
+    st, res = measure(wl.precision, True)
+    value, ms, roof, breakdown, clk = res["value"], res["ms"], res["roof"], res["breakdown"], res["clocks"]
+    kernels_per_step = res["kps"]
+
+    # mixed vs FP64 on the same workload: throughput, and the error of one mixed step
+    other = None
+    if wl.precision == 0 and not args.no_mixed:
+        st_m, res_m = measure(1, False)
+        C.icon_state_free(st_m)
+        a = C.icon_state_init_ex(grid, 77, wl.case, noise_K=wl.noise_K, precision=0)
+        b = C.icon_state_init_ex(grid, 77, wl.case, noise_K=wl.noise_K, precision=1)
+        C.icon_dycore_step(a, wl.dt, wl.nsub)
+        C.icon_dycore_step(b, wl.dt, wl.nsub)
+        err = {}
+        for f in ("vn", "rho", "theta_v", "exner", "w"):
+            x = C.icon_state_copy_field(a, grid, N, f)
+            y = C.icon_state_copy_field(b, grid, N, f)
+            err[f] = float(np.linalg.norm(y - x) / np.linalg.norm(x))
+        C.icon_state_free(a)
+        C.icon_state_free(b)
+        other = {"precision": "mixed (FP32 stencils, FP64 column solve and prognostics)",
+                 "value": res_m["value"], "unit": UNIT, "ms_per_step": res_m["ms"] / args.steps,
+                 "speedup_vs_fp64": res_m["value"] / value, "rel_l2_vs_fp64_after_1_step": err,
+                 "mass_rel_drift": res_m["mass_rel_drift"], "roofline": res_m["roof"],
+                 "kernels": res_m["breakdown"], "gpu_launches": res_m["kps"] * args.steps}
+    m_drift = res["mass_rel_drift"]
 
     # end to end through the C ABI with host buffers: h2d of the prognostic state,
     # the step, the mass integral and d2h of the updated state, every step
@@ -273,7 +327,7 @@ def run_gpu(args, wl, rank, world, local_rank):
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        v, el, desc = oracle_sample(wl)
+        v, el, desc = OracleSampler(wl).sample()
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc, "seconds": el}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -284,8 +338,7 @@ def run_gpu(args, wl, rank, world, local_rank):
                        else "mixed", "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (state %.2f GB)" % ((ne * N + 4 * nc * N) * 8 / 1e9)},
             "gpu_launches": kernels_per_step * args.steps, "roofline": roof, "kernels": breakdown,
-            "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
-            "mass_rel_drift": abs(m1 - m0) / m0}
+            "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "mass_rel_drift": m_drift, "mixed": other}
     print(json.dumps(line), flush=True)
 
 
@@ -297,6 +350,7 @@ def main():
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="r2b6-fp64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision variant of an FP64 workload")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -105,6 +105,21 @@ int upload_vertical(icon_grid* grid, cudaStream_t st) {
     if (!*dst[i]) { set_error("out of device memory (vertical grid)"); return ICON_ENOMEM; }
     ICON_CUDA(cudaMemcpyAsync(*dst[i], src[i]->data(), sizeof(double) * v.ld, cudaMemcpyHostToDevice, st));
   }
+  // FP32 copies for the mixed-precision stencils (kept in the grid, copied synchronously below)
+  v.h_f32.assign(4 * (size_t)v.ld, 0.0f);
+  for (int k = 0; k < v.N; ++k) v.h_f32[k] = (float)(1.0 / v.dz[k]);
+  for (int h = 0; h <= v.N; ++h) {
+    v.h_f32[v.ld + h] = (float)v.wu[h];
+    v.h_f32[2 * v.ld + h] = (float)v.wl[h];
+    v.h_f32[3 * v.ld + h] = (h > 0 && h < v.N) ? (float)(1.0 / v.dz2[h]) : 0.0f;
+  }
+  float* f = A.get_n<float>(4 * (size_t)v.ld);
+  if (!f) { set_error("out of device memory (vertical grid)"); return ICON_ENOMEM; }
+  ICON_CUDA(cudaMemcpyAsync(f, v.h_f32.data(), sizeof(float) * 4 * v.ld, cudaMemcpyHostToDevice, st));
+  v.d_inv_dz32 = f;
+  v.d_wu32 = f + v.ld;
+  v.d_wl32 = f + 2 * v.ld;
+  v.d_inv_dz2_32 = f + 3 * v.ld;
   return ICON_OK;
 }
 
@@ -155,14 +170,16 @@ int alloc_state(icon_state* st, int precision) {
   StateDev& s = st->s;
   s.precision = precision;
   const size_t E = (size_t)(ne * ld), C = (size_t)(nc * ld), V = (size_t)(nv * ld);
-  s.w = A.get_n<double>(C); s.rho = A.get_n<double>(C); s.thv = A.get_n<double>(C); s.ex = A.get_n<double>(C);
-  s.w_s = A.get_n<double>(C); s.rho_s = A.get_n<double>(C); s.thv_s = A.get_n<double>(C);
-  s.ex_s = A.get_n<double>(C);
-  s.mflx = A.get_n<double>(E); s.wflx = A.get_n<double>(C);
+  const size_t ld0 = (size_t)grid->vert.N;
+  s.mflx = A.get_n<double>(E);
   s.ex_ref = A.get_n<double>(ld);
   s.mass_part = A.get_n<double>(mass_partials_count(nc) + 8);
   s.status = A.get_n<unsigned>(64);
   if (precision == ICON_FP64) {
+    s.w = A.get_n<double>(C); s.rho = A.get_n<double>(C); s.thv = A.get_n<double>(C); s.ex = A.get_n<double>(C);
+    s.w_s = A.get_n<double>(C); s.rho_s = A.get_n<double>(C); s.thv_s = A.get_n<double>(C);
+    s.ex_s = A.get_n<double>(C);
+    s.wflx = A.get_n<double>(C);
     s.vn = A.get_n<double>(E); s.vn_s = A.get_n<double>(E);
     s.Avn0 = A.get_n<double>(E); s.Aw0 = A.get_n<double>(C);
     s.zeta = A.get_n<double>(V); s.w_v = A.get_n<double>(V);
@@ -172,8 +189,20 @@ int alloc_state(icon_state* st, int precision) {
     s.Kh = s.vt; s.thflx = s.Ke; s.divc = s.Kc; s.uvx = s.w_v;
     s.uvy = A.get_n<double>(V); s.uvz = A.get_n<double>(V);
   } else {
-    set_error("mixed precision is not available in this build");
-    return ICON_EINVAL;
+    // FP64 prognostics level-major [k][Nc]; everything the stencils touch is FP32 [entity][ld]
+    s.level_major = true;
+    s.w = A.get_n<double>(nc * (ld0 + 1)); s.rho = A.get_n<double>(nc * ld0);
+    s.thv = A.get_n<double>(nc * ld0); s.ex = A.get_n<double>(nc * ld0);
+    s.wflx = A.get_n<double>(nc * (ld0 + 1));
+    s.vn32 = A.get_n<float>(E); s.vn32_s = A.get_n<float>(E); s.Avn0_32 = A.get_n<float>(E);
+    s.vt32 = A.get_n<float>(E); s.Ke32 = A.get_n<float>(E); s.F32 = A.get_n<float>(E);
+    s.G32 = A.get_n<float>(E); s.ae32 = A.get_n<float>(E);
+    s.rho32 = A.get_n<float>(C); s.thv32 = A.get_n<float>(C); s.exp32 = A.get_n<float>(C); s.w32 = A.get_n<float>(C);
+    s.rho32_s = A.get_n<float>(C); s.thv32_s = A.get_n<float>(C); s.exp32_s = A.get_n<float>(C);
+    s.w32_s = A.get_n<float>(C); s.Kc32 = A.get_n<float>(C);
+    s.Aw0_32 = A.get_n<float>(nc * (ld0 + 1));
+    s.zeta32 = A.get_n<float>(V); s.wv32 = A.get_n<float>(V);
+    s.uvx32 = A.get_n<float>(V); s.uvy32 = A.get_n<float>(V); s.uvz32 = A.get_n<float>(V);
   }
   if (A.failed) {
     set_error("out of device memory allocating the state");
@@ -248,11 +277,12 @@ int launch_step(icon_state* st, double dt, int nsub, cudaStream_t stream) {
   return ICON_OK;
 }
 
-bool field_ref(const icon_state* st, int id, void** ptr, int* is_f32, int64_t* n, int* nlev) {
+bool field_ref(const icon_state* st, int id, void** ptr, int* is_f32, int64_t* n, int* nlev, int* lm) {
   const icon_grid* grid = st->grid;
   const StateDev& s = st->s;
   const int N = grid->vert.N;
   *is_f32 = 0;
+  *lm = (s.level_major && id != ICON_F_VN && id != ICON_F_MFLX) ? 1 : 0;
   switch (id) {
     case ICON_F_VN:
       *n = grid->g.ne; *nlev = N;
@@ -275,6 +305,19 @@ __global__ void k_f32_to_f64(const float* __restrict__ a, double* __restrict__ b
 __global__ void k_f64_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) b[i] = (float)a[i];
+}
+// level-major [k][n] <-> row-major [n][ld] for the first nlev levels
+__global__ void k_lm_to_rm(const double* __restrict__ a, double* __restrict__ b, int64_t n, int nlev, int ld) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * nlev) return;
+  int64_t k = t / n, i = t % n;
+  b[i * ld + k] = a[t];
+}
+__global__ void k_rm_to_lm(const double* __restrict__ b, double* __restrict__ a, int64_t n, int nlev, int ld) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * nlev) return;
+  int64_t k = t / n, i = t % n;
+  a[t] = b[i * ld + k];
 }
 
 }  // namespace
@@ -508,9 +551,9 @@ const char* icon_kernel_kind_name(int kind) {
 int icon_state_copy_field(const icon_state* st, int field_id, double* host_dst, size_t count) {
   if (!st || !host_dst) { set_error("icon_state_copy_field: NULL argument"); return ICON_EINVAL; }
   void* ptr;
-  int f32, nlev;
+  int f32, nlev, lm;
   int64_t n;
-  if (!field_ref(st, field_id, &ptr, &f32, &n, &nlev)) {
+  if (!field_ref(st, field_id, &ptr, &f32, &n, &nlev, &lm)) {
     set_error("icon_state_copy_field: unknown field %d", field_id);
     return ICON_EINVAL;
   }
@@ -523,10 +566,11 @@ int icon_state_copy_field(const icon_state* st, int field_id, double* host_dst, 
   const double* src = static_cast<const double*>(ptr);
   DeviceArena tmp;
   tmp.al = st->arena.al;
-  if (f32) {
+  if (f32 || lm) {
     double* d = tmp.get_n<double>((size_t)n * ld);
     if (!d) { set_error("icon_state_copy_field: out of device memory"); return ICON_ENOMEM; }
-    k_f32_to_f64<<<blocks_for(n * ld, 256), 256, 0, stream>>>(static_cast<const float*>(ptr), d, n * ld);
+    if (f32) k_f32_to_f64<<<blocks_for(n * ld, 256), 256, 0, stream>>>(static_cast<const float*>(ptr), d, n * ld);
+    else k_lm_to_rm<<<blocks_for(n * nlev, 256), 256, 0, stream>>>(static_cast<const double*>(ptr), d, n, nlev, ld);
     src = d;
   }
   cudaError_t e = cudaMemcpy2DAsync(host_dst, sizeof(double) * nlev, src, sizeof(double) * ld,
@@ -544,9 +588,9 @@ int icon_state_set_field(icon_state* st, int field_id, const double* host_src, s
     return ICON_EINVAL;
   }
   void* ptr;
-  int f32, nlev;
+  int f32, nlev, lm;
   int64_t n;
-  field_ref(st, field_id, &ptr, &f32, &n, &nlev);
+  field_ref(st, field_id, &ptr, &f32, &n, &nlev, &lm);
   if (count != (size_t)(n * nlev)) {
     set_error("icon_state_set_field: field %d has %lld elements, got %zu", field_id, (long long)(n * nlev), count);
     return ICON_EINVAL;
@@ -556,7 +600,7 @@ int icon_state_set_field(icon_state* st, int field_id, const double* host_src, s
   DeviceArena tmp;
   tmp.al = st->arena.al;
   double* dst = static_cast<double*>(ptr);
-  if (f32) {
+  if (f32 || lm) {
     dst = tmp.get_n<double>((size_t)n * ld);
     if (!dst) { set_error("icon_state_set_field: out of device memory"); return ICON_ENOMEM; }
   }
@@ -564,6 +608,11 @@ int icon_state_set_field(icon_state* st, int field_id, const double* host_src, s
                                     sizeof(double) * nlev, n, cudaMemcpyHostToDevice, stream);
   if (e == cudaSuccess && f32) {
     k_f64_to_f32<<<blocks_for(n * ld, 256), 256, 0, stream>>>(dst, static_cast<float*>(ptr), n * ld);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && lm) {
+    k_rm_to_lm<<<blocks_for(n * nlev, 256), 256, 0, stream>>>(dst, static_cast<double*>(ptr), n, nlev, ld);
+    mixed_refresh_shadows(st, stream);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);

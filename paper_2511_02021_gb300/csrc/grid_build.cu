@@ -407,16 +407,22 @@ __global__ void k_mixed_tables(int64_t nc, int64_t ne, int64_t nv, const double*
                                const double* __restrict__ A_v, const double* __restrict__ vt_w,
                                const double* __restrict__ kin_w, const double* __restrict__ lsq_w,
                                const double* __restrict__ d_e, const double* __restrict__ l_e,
-                               const double* __restrict__ f_e, float* __restrict__ div32,
+                               const double* __restrict__ f_e, const double* __restrict__ n_e,
+                               const double* __restrict__ t_e, const double* __restrict__ L34,
+                               const double* __restrict__ s_ce, float* __restrict__ div32,
                                float* __restrict__ rot32, float* __restrict__ vt32, float* __restrict__ kin32,
                                float* __restrict__ lsq32, float* __restrict__ ide32, float* __restrict__ ile32,
-                               float* __restrict__ fe32) {
+                               float* __restrict__ fe32, float* __restrict__ le32, float* __restrict__ ne32,
+                               float* __restrict__ te32, float* __restrict__ i34_32, float* __restrict__ sce32,
+                               double* __restrict__ invAc) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < nc) {
     for (int s = 0; s < 3; ++s) {
       div32[3 * i + s] = (float)(div_w[3 * i + s] / A_c[i]);
       kin32[3 * i + s] = (float)kin_w[3 * i + s];
+      sce32[3 * i + s] = (float)s_ce[3 * i + s];
     }
+    invAc[i] = 1.0 / A_c[i];
   }
   if (i < nv) {
     for (int j = 0; j < 6; ++j) rot32[6 * i + j] = (float)(rot_w[6 * i + j] / A_v[i]);
@@ -427,6 +433,12 @@ __global__ void k_mixed_tables(int64_t nc, int64_t ne, int64_t nv, const double*
     ide32[i] = (float)(1.0 / d_e[i]);
     ile32[i] = (float)(1.0 / l_e[i]);
     fe32[i] = (float)f_e[i];
+    le32[i] = (float)l_e[i];
+    i34_32[i] = (float)(1.0 / L34[i]);
+    for (int j = 0; j < 3; ++j) {
+      ne32[3 * i + j] = (float)n_e[3 * i + j];
+      te32[3 * i + j] = (float)t_e[3 * i + j];
+    }
   }
 }
 
@@ -514,6 +526,8 @@ int build_grid_device(icon_grid* grid, cudaStream_t st) {
   g.vt_w32 = A.get_n<float>(5 * ne); g.kin_w32 = A.get_n<float>(3 * nc); g.lsq_w32 = A.get_n<float>(18 * nv);
   g.div_w32 = A.get_n<float>(3 * nc); g.rot_w32 = A.get_n<float>(6 * nv);
   g.inv_de32 = A.get_n<float>(ne); g.inv_le32 = A.get_n<float>(ne); g.f_e32 = A.get_n<float>(ne);
+  g.l_e32 = A.get_n<float>(ne); g.n_e32 = A.get_n<float>(3 * ne); g.t_e32 = A.get_n<float>(3 * ne);
+  g.L34inv32 = A.get_n<float>(ne); g.s_ce32 = A.get_n<float>(3 * nc); g.inv_Ac = A.get_n<double>(nc);
   double* corner_pos = T.get_n<double>(9 * nc);
   unsigned* cv = T.get_n<unsigned>(n3);
   unsigned* ce = T.get_n<unsigned>(n3);
@@ -556,9 +570,10 @@ int build_grid_device(icon_grid* grid, cudaStream_t st) {
                                                 g.e2vt, g.vt_w);
   int64_t nmax = nc > ne ? (nc > nv ? nc : nv) : (ne > nv ? ne : nv);
   k_mixed_tables<<<blocks_for(nmax, TB), TB, 0, st>>>(nc, ne, nv, g.div_w, g.A_c, g.rot_w, g.A_v, g.vt_w,
-                                                       g.kin_w, g.lsq_w, g.d_e, g.l_e, g.f_e, g.div_w32,
-                                                       g.rot_w32, g.vt_w32, g.kin_w32, g.lsq_w32, g.inv_de32,
-                                                       g.inv_le32, g.f_e32);
+                                                       g.kin_w, g.lsq_w, g.d_e, g.l_e, g.f_e, g.n_e, g.t_e,
+                                                       g.L34, g.s_ce, g.div_w32, g.rot_w32, g.vt_w32, g.kin_w32,
+                                                       g.lsq_w32, g.inv_de32, g.inv_le32, g.f_e32, g.l_e32,
+                                                       g.n_e32, g.t_e32, g.L34inv32, g.s_ce32, g.inv_Ac);
   ICON_CUDA(cudaGetLastError());
   unsigned host_u[4];
   ICON_CUDA(cudaMemcpyAsync(host_u, dev_u, sizeof(host_u), cudaMemcpyDeviceToHost, st));

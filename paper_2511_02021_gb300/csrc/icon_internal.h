@@ -67,9 +67,11 @@ struct Vertical {
   int ld = 0;          // row stride (elements) of every (entity, level) field
   double z_top = 0, s = 0, z_d = 0;
   std::vector<double> z_h, z_f, dz, dzh, wu, wl, rayleigh, dz2;  // host copies
+  std::vector<float> h_f32;                                       // host staging of the FP32 tables
   // device copies (length ld)
   double *d_z_h = nullptr, *d_z_f = nullptr, *d_dz = nullptr, *d_dzh = nullptr,
          *d_wu = nullptr, *d_wl = nullptr, *d_ray = nullptr, *d_dz2 = nullptr;
+  float *d_inv_dz32 = nullptr, *d_wu32 = nullptr, *d_wl32 = nullptr, *d_inv_dz2_32 = nullptr;
 };
 
 struct GridDev {
@@ -89,6 +91,8 @@ struct GridDev {
   float *vt_w32 = nullptr, *kin_w32 = nullptr, *lsq_w32 = nullptr;
   float *div_w32 = nullptr, *rot_w32 = nullptr;   // mixed precision copies (already / area)
   float *inv_de32 = nullptr, *inv_le32 = nullptr, *f_e32 = nullptr;
+  float *l_e32 = nullptr, *n_e32 = nullptr, *t_e32 = nullptr, *L34inv32 = nullptr, *s_ce32 = nullptr;
+  double* inv_Ac = nullptr;  // 1 / A_c
 };
 
 }  // namespace icon
@@ -125,6 +129,9 @@ struct StateDev {
         *ae32 = nullptr, *F32 = nullptr, *G32 = nullptr;
   float *rho32 = nullptr, *thv32 = nullptr, *exp32 = nullptr, *w32 = nullptr;
   float *rho32_s = nullptr, *thv32_s = nullptr, *exp32_s = nullptr, *w32_s = nullptr;
+  float *uvx32 = nullptr, *uvy32 = nullptr, *uvz32 = nullptr;
+  // mixed mode stores rho, theta_v, Exner, w and wflx level-major ([k][Nc])
+  bool level_major = false;
   double *ex_ref = nullptr;           // [ld] reference Exner profile
   // column factorisation kept between predictor and corrector (mixed mode)
   double *fac = nullptr;
@@ -162,6 +169,10 @@ int init_state_device(icon_state* st, uint64_t seed, int case_id, const icon_cas
 void enqueue_step_fp64(icon_state* st, double dt, int nsub, cudaStream_t stream);
 // dycore32.cu
 void enqueue_step_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream);
+// mixed-mode state from FP64 fields in [entity][ld] layout (init.cu)
+void mixed_from_fp64(icon_state* st, const double* vn, const double* w, const double* rho, const double* thv,
+                     const double* ex, cudaStream_t stream);
+void mixed_refresh_shadows(icon_state* st, cudaStream_t stream);
 // mass
 void enqueue_mass(const icon_state* st, double* d_out, cudaStream_t stream);
 int mass_partials_count(int64_t nc);

@@ -202,7 +202,82 @@ double jet_B() {
   return (U * U / (kR * c45) + 2.0 * kOmega * U) * kR / (kRd * Tj);
 }
 
+// FP64 fields in [entity][ld] layout -> mixed-mode storage: FP64 level-major
+// prognostics, FP32 vn and FP32 shadows of S^n
+__global__ void k_mixed_cells(int64_t nc, int N, int ld, const double* __restrict__ w, const double* __restrict__ rho,
+                              const double* __restrict__ thv, const double* __restrict__ ex,
+                              const double* __restrict__ ex_ref, double* __restrict__ w_lm,
+                              double* __restrict__ rho_lm, double* __restrict__ thv_lm, double* __restrict__ ex_lm,
+                              float* __restrict__ w32, float* __restrict__ rho32, float* __restrict__ thv32,
+                              float* __restrict__ exp32) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nc * ld) return;
+  const int64_t c = t / ld;
+  const int k = (int)(t % ld);
+  if (k <= N) {
+    w_lm[(int64_t)k * nc + c] = w[t];
+    w32[t] = (float)w[t];
+  } else {
+    w32[t] = 0.0f;
+  }
+  if (k < N) {
+    rho_lm[(int64_t)k * nc + c] = rho[t];
+    thv_lm[(int64_t)k * nc + c] = thv[t];
+    ex_lm[(int64_t)k * nc + c] = ex[t];
+    rho32[t] = (float)rho[t];
+    thv32[t] = (float)thv[t];
+    exp32[t] = (float)(ex[t] - ex_ref[k]);
+  } else {
+    rho32[t] = 0.0f;
+    thv32[t] = 0.0f;
+    exp32[t] = 0.0f;
+  }
+}
+
+__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+// shadows of S^n from the level-major FP64 prognostics
+__global__ void k_mixed_shadows(int64_t nc, int N, int ld, const double* __restrict__ w_lm,
+                                const double* __restrict__ rho_lm, const double* __restrict__ thv_lm,
+                                const double* __restrict__ ex_lm, const double* __restrict__ ex_ref,
+                                float* __restrict__ w32, float* __restrict__ rho32, float* __restrict__ thv32,
+                                float* __restrict__ exp32) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nc * ld) return;
+  const int64_t c = t / ld;
+  const int k = (int)(t % ld);
+  w32[t] = k <= N ? (float)w_lm[(int64_t)k * nc + c] : 0.0f;
+  if (k < N) {
+    rho32[t] = (float)rho_lm[(int64_t)k * nc + c];
+    thv32[t] = (float)thv_lm[(int64_t)k * nc + c];
+    exp32[t] = (float)(ex_lm[(int64_t)k * nc + c] - ex_ref[k]);
+  }
+}
+
 }  // namespace
+
+void mixed_from_fp64(icon_state* st, const double* vn, const double* w, const double* rho, const double* thv,
+                     const double* ex, cudaStream_t stream) {
+  const GridDev& g = st->grid->g;
+  const Vertical& v = st->grid->vert;
+  StateDev& s = st->s;
+  const int64_t ncl = g.nc * v.ld, nel = g.ne * v.ld;
+  k_to_f32<<<blocks_for(nel, 256), 256, 0, stream>>>(vn, s.vn32, nel);
+  k_mixed_cells<<<blocks_for(ncl, 256), 256, 0, stream>>>(g.nc, v.N, v.ld, w, rho, thv, ex, s.ex_ref, s.w, s.rho,
+                                                          s.thv, s.ex, s.w32, s.rho32, s.thv32, s.exp32);
+}
+
+void mixed_refresh_shadows(icon_state* st, cudaStream_t stream) {
+  const GridDev& g = st->grid->g;
+  const Vertical& v = st->grid->vert;
+  StateDev& s = st->s;
+  const int64_t ncl = g.nc * v.ld;
+  k_mixed_shadows<<<blocks_for(ncl, 256), 256, 0, stream>>>(g.nc, v.N, v.ld, s.w, s.rho, s.thv, s.ex, s.ex_ref,
+                                                            s.w32, s.rho32, s.thv32, s.exp32);
+}
 
 int init_state_device(icon_state* st, uint64_t seed, int case_id, const icon_case_params& p, cudaStream_t stream) {
   const icon_grid* grid = st->grid;
@@ -235,11 +310,33 @@ int init_state_device(icon_state* st, uint64_t seed, int case_id, const icon_cas
     cd.by = std::cos(lat) * std::sin(lon);
     cd.bz = std::sin(lat);
   }
-  k_init_cells<<<blocks_for(g.nc, 128), 128, 0, stream>>>(cd, g.nc, g.x_c, v.d_z_f, v.d_dzh, v.d_wu, v.d_wl, s.rho,
-                                                          s.thv, s.ex, s.w);
-  k_init_edges<<<blocks_for(g.ne * v.ld, 256), 256, 0, stream>>>(cd, g.ne, g.x_e, g.n_e, v.d_z_f, s.vn);
   k_exner_ref<<<1, 1, 0, stream>>>(v.N, v.d_z_f, v.d_dzh, v.d_wu, v.d_wl, s.ex_ref);
-  ICON_CUDA(cudaGetLastError());
+  if (s.precision == ICON_FP64) {
+    k_init_cells<<<blocks_for(g.nc, 128), 128, 0, stream>>>(cd, g.nc, g.x_c, v.d_z_f, v.d_dzh, v.d_wu, v.d_wl,
+                                                            s.rho, s.thv, s.ex, s.w);
+    k_init_edges<<<blocks_for(g.ne * v.ld, 256), 256, 0, stream>>>(cd, g.ne, g.x_e, g.n_e, v.d_z_f, s.vn);
+    ICON_CUDA(cudaGetLastError());
+    return ICON_OK;
+  }
+  // mixed: the same FP64 initial state in temporaries, then the mixed-mode storage
+  DeviceArena T;
+  T.al = st->arena.al;
+  const size_t C = (size_t)(g.nc * v.ld), E = (size_t)(g.ne * v.ld);
+  double *rho = T.get_n<double>(C), *thv = T.get_n<double>(C), *ex = T.get_n<double>(C), *w = T.get_n<double>(C);
+  double* vn = T.get_n<double>(E);
+  if (T.failed) {
+    T.release();
+    set_error("out of device memory for the initial state");
+    return ICON_ENOMEM;
+  }
+  k_init_cells<<<blocks_for(g.nc, 128), 128, 0, stream>>>(cd, g.nc, g.x_c, v.d_z_f, v.d_dzh, v.d_wu, v.d_wl, rho,
+                                                          thv, ex, w);
+  k_init_edges<<<blocks_for(g.ne * v.ld, 256), 256, 0, stream>>>(cd, g.ne, g.x_e, g.n_e, v.d_z_f, vn);
+  mixed_from_fp64(st, vn, w, rho, thv, ex, stream);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  T.release();
+  if (e != cudaSuccess) return cuda_fail(e, "mixed initial state");
   return ICON_OK;
 }
 

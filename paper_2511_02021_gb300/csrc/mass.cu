@@ -38,6 +38,28 @@ __global__ void __launch_bounds__(kMassThreads) k_mass_partial(int64_t nc, int N
   }
 }
 
+// level-major density [k][Nc]: one thread per column, same fixed assignment and tree
+__global__ void __launch_bounds__(kMassThreads) k_mass_partial_lm(int64_t nc, int N, const double* __restrict__ rho,
+                                                                  const double* __restrict__ dz,
+                                                                  const double* __restrict__ A_c,
+                                                                  double* __restrict__ part) {
+  __shared__ double ws[kMassThreads];
+  const int64_t nthr = (int64_t)gridDim.x * kMassThreads;
+  double acc = 0.0;
+  for (int64_t c = (int64_t)blockIdx.x * kMassThreads + threadIdx.x; c < nc; c += nthr) {
+    double col = 0.0;
+    for (int k = 0; k < N; ++k) col += rho[(int64_t)k * nc + c] * dz[k];
+    acc += A_c[c] * col;
+  }
+  ws[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = kMassThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) ws[threadIdx.x] += ws[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = ws[0];
+}
+
 __global__ void __launch_bounds__(1024) k_mass_final(const double* __restrict__ part, int n, double* __restrict__ out) {
   __shared__ double sh[1024];
   double s = 0.0;
@@ -58,8 +80,12 @@ int mass_partials_count(int64_t) { return kMassBlocks; }
 void enqueue_mass(const icon_state* st, double* d_out, cudaStream_t stream) {
   const icon_grid* grid = st->grid;
   prof_begin(stream, K_MASS);
-  k_mass_partial<<<kMassBlocks, kMassThreads, 0, stream>>>(grid->g.nc, grid->vert.N, grid->vert.ld, st->s.rho,
-                                                           grid->vert.d_dz, grid->g.A_c, st->s.mass_part);
+  if (st->s.level_major)
+    k_mass_partial_lm<<<kMassBlocks, kMassThreads, 0, stream>>>(grid->g.nc, grid->vert.N, st->s.rho, grid->vert.d_dz,
+                                                                grid->g.A_c, st->s.mass_part);
+  else
+    k_mass_partial<<<kMassBlocks, kMassThreads, 0, stream>>>(grid->g.nc, grid->vert.N, grid->vert.ld, st->s.rho,
+                                                             grid->vert.d_dz, grid->g.A_c, st->s.mass_part);
   k_mass_final<<<1, 1024, 0, stream>>>(st->s.mass_part, kMassBlocks, d_out);
   prof_end(stream);
 }
