@@ -236,7 +236,9 @@ int icon_state_step_kernels(icon_state* state, double dt, int nsubsteps, int* ou
 int icon_dycore_step_profile(icon_state* state, double dt, int nsubsteps, double* ms_per_kind,
                              int* launches_per_kind);
 
-/* Name of kernel kind i (0 <= i < ICON_KIND_COUNT), or NULL. */
+/* Name of kernel kind i (0 <= i < ICON_KIND_COUNT), or NULL. Mixed-precision
+ * stencil kinds: 10 vertex, 11 edge diagnostics, 12 cell kinetic energy,
+ * 13 edge tendency, 16 diffusion vertex/divergence. */
 const char* icon_kernel_kind_name(int kind);
 #define ICON_KIND_COUNT 24
 
@@ -247,15 +249,35 @@ void icon_state_free(icon_state* state);
 
 /* ---------------------------------------------------------------- ensemble */
 
-/* Group n >= 1 states (any grids, same precision) for batched stepping. The
- * ensemble borrows the states, which must outlive it. */
+/* Stencil tile of a kernel kind (ICON_KIND_* below) of a mixed-precision state:
+ * lanes per entity (32 = one entity per warp, 16 = two) and threads per block. The
+ * autotuner picks them on the first step (timing every candidate on the state's
+ * data; cached per grid size, level count and GPU, and in the file named by the
+ * environment variable ICON_TUNE_CACHE if set). set_tiling forces a tile
+ * (lanes 0 restores automatic choice); results do not depend on the tile. */
+int icon_state_tiling(const icon_state* state, int kind, int* lanes, int* block);
+int icon_state_set_tiling(icon_state* state, int kind, int lanes, int block);
+
+/* Group 1 <= n <= 64 distinct mixed-precision states (grids of any size, one
+ * level count <= 96) for batched stepping (the paper runs ensemble members,
+ * Sec. "Implications"). The ensemble borrows the states, which must outlive it. */
 int icon_ensemble_create(icon_state* const* members, int n, icon_ensemble** out);
 
 /* Advance every member by nsteps dycore steps (member i with dt_per_member[i],
- * host array of n doubles, all with nsubsteps substeps). Uses one persistent
- * kernel per phase over all members; waits and reports ICON_ETIMEOUT if an
- * in-kernel barrier wait ran out, ICON_ENONFINITE as icon_dycore_step. */
+ * host array of n doubles, all with nsubsteps substeps) in ONE persistent
+ * cooperative launch per step for all members: every phase of the step is a work
+ * list over (member, entity) separated by a bounded grid barrier. The launch is
+ * recorded in a CUDA graph per (dt_per_member, nsubsteps). Waits; returns
+ * ICON_ETIMEOUT if a barrier wait ran out (the kernel then returns early and the
+ * members' states are not valid), ICON_ENONFINITE as icon_dycore_step. */
 int icon_ensemble_step(icon_ensemble* ens, const double* dt_per_member, int nsubsteps, int nsteps);
+
+/* Ensemble options: ICON_ENS_SPIN_LIMIT = spins (about 0.1 us each) before a grid
+ * barrier wait gives up (default 2^24); ICON_ENS_TEST_SKIP_BARRIER = 1 makes block
+ * 0 skip its first barrier arrival so that the others' waits run out (fault test). */
+#define ICON_ENS_SPIN_LIMIT 1
+#define ICON_ENS_TEST_SKIP_BARRIER 2
+int icon_ensemble_set_option(icon_ensemble* ens, int option, long long value);
 
 void icon_ensemble_free(icon_ensemble* ens);
 

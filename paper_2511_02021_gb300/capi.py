@@ -71,6 +71,9 @@ def _load():
         "icon_state_precision": (I, [P, ctypes.POINTER(I)]), "icon_state_free": (None, [P]),
         "icon_ensemble_create": (I, [ctypes.POINTER(P), I, ctypes.POINTER(P)]),
         "icon_ensemble_step": (I, [P, ctypes.POINTER(D), I, I]), "icon_ensemble_free": (None, [P]),
+        "icon_ensemble_set_option": (I, [P, I, ctypes.c_longlong]),
+        "icon_state_tiling": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "icon_state_set_tiling": (I, [P, I, I, I]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -250,6 +253,25 @@ def icon_ensemble_create(states):
 def icon_ensemble_step(ens, dts, nsubsteps, nsteps):
     arr = (ctypes.c_double * len(dts))(*dts)
     _check(_lib.icon_ensemble_step(ens, arr, nsubsteps, nsteps))
+
+
+ICON_ENS_SPIN_LIMIT, ICON_ENS_TEST_SKIP_BARRIER = 1, 2
+# mixed-precision stencil kinds that take a tile
+KIND_MX_VERTEX, KIND_MX_EDGE, KIND_MX_CELL_KE, KIND_MX_EDGE_TEND, KIND_MX_DIFF_VERTEX = 10, 11, 12, 13, 16
+
+
+def icon_ensemble_set_option(ens, option, value):
+    _check(_lib.icon_ensemble_set_option(ens, option, value))
+
+
+def icon_state_tiling(state, kind):
+    lanes, block = ctypes.c_int(), ctypes.c_int()
+    _check(_lib.icon_state_tiling(state, kind, ctypes.byref(lanes), ctypes.byref(block)))
+    return lanes.value, block.value
+
+
+def icon_state_set_tiling(state, kind, lanes, block):
+    _check(_lib.icon_state_set_tiling(state, kind, lanes, block))
 
 
 def icon_ensemble_free(ens):

@@ -203,6 +203,7 @@ int alloc_state(icon_state* st, int precision) {
     s.Aw0_32 = A.get_n<float>(nc * (ld0 + 1));
     s.zeta32 = A.get_n<float>(V); s.wv32 = A.get_n<float>(V);
     s.uvx32 = A.get_n<float>(V); s.uvy32 = A.get_n<float>(V); s.uvz32 = A.get_n<float>(V);
+    s.colconst = A.get_n<double>(8 * (size_t)ld);
   }
   if (A.failed) {
     set_error("out of device memory allocating the state");
@@ -236,6 +237,12 @@ void enqueue_step(icon_state* st, double dt, int nsub, cudaStream_t stream) {
 // record the graph of one step for (dt, nsub) unless it is already recorded
 int record_graph(icon_state* st, double dt, int nsub) {
   if (st->graph && st->graph_dt == dt && st->graph_nsub == nsub) return ICON_OK;
+  if (st->s.precision == ICON_MIXED && !st->tuned) {
+    cudaStream_t ts = current_stream();
+    autotune_mixed(st, dt, nsub, ts);
+    ICON_CUDA(cudaGetLastError());
+    ICON_CUDA(cudaStreamSynchronize(ts));
+  }
   if (st->graph) {
     cudaGraphExecDestroy(st->graph);
     st->graph = nullptr;
@@ -621,6 +628,32 @@ int icon_state_set_field(icon_state* st, int field_id, const double* host_src, s
   return ICON_OK;
 }
 
+int icon_state_tiling(const icon_state* st, int kind, int* lanes, int* block) {
+  if (!st || !lanes || !block || kind < 0 || kind >= ICON_KIND_COUNT) {
+    set_error("icon_state_tiling: bad argument");
+    return ICON_EINVAL;
+  }
+  *lanes = st->tile[kind].lanes;
+  *block = st->tile[kind].block;
+  return ICON_OK;
+}
+
+int icon_state_set_tiling(icon_state* st, int kind, int lanes, int block) {
+  if (!st || kind < 0 || kind >= ICON_KIND_COUNT) { set_error("icon_state_set_tiling: bad argument"); return ICON_EINVAL; }
+  if (lanes != 0 && ((lanes != 16 && lanes != 32) || (block != 128 && block != 256 && block != 512))) {
+    set_error("icon_state_set_tiling: lanes must be 16 or 32 and block 128, 256 or 512");
+    return ICON_EINVAL;
+  }
+  st->tile[kind] = TileChoice{lanes, lanes ? block : 0};
+  st->tile_forced[kind] = lanes != 0;
+  if (lanes == 0) st->tuned = false;
+  if (st->graph) {
+    cudaGraphExecDestroy(st->graph);
+    st->graph = nullptr;
+  }
+  return ICON_OK;
+}
+
 int icon_state_precision(const icon_state* st, int* out) {
   if (!st || !out) { set_error("icon_state_precision: NULL argument"); return ICON_EINVAL; }
   *out = st->s.precision;
@@ -642,43 +675,114 @@ void icon_state_free(icon_state* st) {
 // ---------------------------------------------------------------- ensemble
 struct icon_ensemble {
   std::vector<icon_state*> members;
+  icon::EnsembleDev E;
+  std::vector<double> dts;
+  int nsub = 0;
+  bool prepared = false;
+  cudaGraphExec_t graph = nullptr;
+  cudaStream_t capture_stream = nullptr;
 };
 
 extern "C" {
 
 int icon_ensemble_create(icon_state* const* members, int n, icon_ensemble** out) {
-  if (!members || !out || n < 1) { set_error("icon_ensemble_create: bad arguments"); return ICON_EINVAL; }
-  int prec = -1;
+  if (!members || !out || n < 1 || n > 64) { set_error("icon_ensemble_create: need 1..64 members"); return ICON_EINVAL; }
   for (int i = 0; i < n; ++i) {
     if (!members[i]) { set_error("icon_ensemble_create: member %d is NULL", i); return ICON_EINVAL; }
-    if (prec >= 0 && members[i]->s.precision != prec) {
-      set_error("icon_ensemble_create: members must share one precision");
+    if (members[i]->s.precision != ICON_MIXED) {
+      set_error("icon_ensemble_create: members must be mixed-precision states");
       return ICON_EINVAL;
     }
-    prec = members[i]->s.precision;
+    if (members[i]->grid->vert.N != members[0]->grid->vert.N || members[i]->grid->vert.N > 96) {
+      set_error("icon_ensemble_create: members must share one level count of at most 96");
+      return ICON_EINVAL;
+    }
+    for (int j = 0; j < i; ++j)
+      if (members[j] == members[i]) { set_error("icon_ensemble_create: member %d repeats member %d", i, j); return ICON_EINVAL; }
   }
   icon_ensemble* e = new icon_ensemble();
   e->members.assign(members, members + n);
+  e->E.arena.al = current_allocator();
   *out = e;
   return ICON_OK;
 }
 
+int icon_ensemble_set_option(icon_ensemble* ens, int option, long long value) {
+  if (!ens) { set_error("icon_ensemble_set_option: ensemble is NULL"); return ICON_EINVAL; }
+  if (option == ICON_ENS_SPIN_LIMIT && value > 0) ens->E.spin_limit = value;
+  else if (option == ICON_ENS_TEST_SKIP_BARRIER && (value == 0 || value == 1)) ens->E.test_skip_barrier = (int)value;
+  else { set_error("icon_ensemble_set_option: bad option %d or value %lld", option, value); return ICON_EINVAL; }
+  if (ens->graph) {
+    cudaGraphExecDestroy(ens->graph);
+    ens->graph = nullptr;
+  }
+  return ICON_OK;
+}
+
 int icon_ensemble_step(icon_ensemble* ens, const double* dt_per_member, int nsubsteps, int nsteps) {
-  if (!ens || !dt_per_member || nsteps < 0) { set_error("icon_ensemble_step: bad arguments"); return ICON_EINVAL; }
+  if (!ens || !dt_per_member || nsteps < 0 || nsubsteps < 1 || nsubsteps > 64) {
+    set_error("icon_ensemble_step: bad arguments");
+    return ICON_EINVAL;
+  }
+  const int n = (int)ens->members.size();
+  for (int i = 0; i < n; ++i)
+    if (!(dt_per_member[i] > 0.0)) { set_error("icon_ensemble_step: dt of member %d must be > 0", i); return ICON_EINVAL; }
   cudaStream_t stream = current_stream();
-  for (int s = 0; s < nsteps; ++s)
-    for (size_t i = 0; i < ens->members.size(); ++i) {
-      int rc = icon_dycore_step_async(ens->members[i], dt_per_member[i], nsubsteps);
-      if (rc != ICON_OK) return rc;
+  std::vector<double> dts(dt_per_member, dt_per_member + n);
+  if (!ens->prepared || dts != ens->dts || nsubsteps != ens->nsub) {
+    int rc = ensemble_prepare(ens->E, ens->members.data(), n, dts.data(), nsubsteps);
+    if (rc != ICON_OK) return rc;
+    ens->prepared = true;
+    ens->dts = dts;
+    ens->nsub = nsubsteps;
+    if (ens->graph) {
+      cudaGraphExecDestroy(ens->graph);
+      ens->graph = nullptr;
     }
+  }
+  if (!ens->graph) {
+    // one step: reset the barrier words, then the cooperative persistent launch
+    if (!ens->capture_stream) ICON_CUDA(cudaStreamCreateWithFlags(&ens->capture_stream, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    ICON_CUDA(cudaStreamBeginCapture(ens->capture_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaMemsetAsync(ens->E.bar, 0, 8 * sizeof(unsigned), ens->capture_stream);
+    int rc = e == cudaSuccess ? ensemble_launch(ens->E, ens->capture_stream) : cuda_fail(e, "cudaMemsetAsync");
+    cudaError_t e2 = cudaStreamEndCapture(ens->capture_stream, &g);
+    if (rc != ICON_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture (ensemble)");
+    e = cudaGraphInstantiate(&ens->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { ens->graph = nullptr; return cuda_fail(e, "cudaGraphInstantiate (ensemble)"); }
+  }
+  ICON_CUDA(cudaMemsetAsync(ens->E.bar + 8, 0, sizeof(unsigned), stream));
+  for (int s = 0; s < nsteps; ++s) ICON_CUDA(cudaGraphLaunch(ens->graph, stream));
+  unsigned h = 0;
+  ICON_CUDA(cudaMemcpyAsync(&h, ens->E.bar + 8, sizeof(unsigned), cudaMemcpyDeviceToHost, stream));
+  ICON_CUDA(cudaStreamSynchronize(stream));
   int worst = ICON_OK;
-  for (size_t i = 0; i < ens->members.size(); ++i) {
+  for (int i = 0; i < n; ++i) {
     int rc = sync_status(ens->members[i], stream);
     if (rc != ICON_OK) worst = rc;
+  }
+  if (h & 2u) {
+    ICON_CUDA(cudaMemsetAsync(ens->E.bar, 0, 16 * sizeof(unsigned), stream));
+    ICON_CUDA(cudaStreamSynchronize(stream));
+    set_error("icon_ensemble_step: a grid-barrier wait ran out; the members' states are not valid");
+    return ICON_ETIMEOUT;
   }
   return worst;
 }
 
-void icon_ensemble_free(icon_ensemble* ens) { delete ens; }
+void icon_ensemble_free(icon_ensemble* ens) {
+  if (!ens) return;
+  cudaDeviceSynchronize();
+  if (ens->graph) cudaGraphExecDestroy(ens->graph);
+  if (ens->capture_stream) cudaStreamDestroy(ens->capture_stream);
+  ens->E.arena.release();
+  delete ens;
+}
 
 }  // extern "C"

@@ -8,7 +8,7 @@
 // the data layout:
 //
 //  * vn and every stencil temporary are FP32, stored level-contiguous
-//    ([entity][ld]) so that a warp gathers whole neighbour rows.
+//    ([entity][ld]) so that the lanes of a warp gather whole neighbour rows.
 //  * rho, theta_v, Exner and w are FP64 prognostics stored level-major ([k][Nc]):
 //    only the thread-per-column solve reads and writes them, and in this layout
 //    its loads and stores are coalesced across the 32 columns of a warp. FP32
@@ -24,12 +24,23 @@
 //  * The predictor writes the provisional state S* only as FP32 shadows: S* is
 //    consumed by FP32 stencils, while the corrector's column uses coefficients
 //    frozen at S^n.
+//
+// Every kernel body is a per-item device function (one entity for the stencils,
+// one column for the solve) shared by the per-state kernels and by the persistent
+// ensemble kernel. The stencil kernels take the number of lanes per entity (32 or
+// 16: one or two entities per warp) and the block size from the autotuner; each
+// output is computed by one lane with a fixed summation order, so the results do
+// not depend on the tile shape.
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <string>
 #include "icon_internal.h"
 
 namespace icon {
 namespace {
 
-constexpr int kWarps = 8;
 constexpr float kRcvF = (float)(kRd / kCvd);
 
 struct MxGeo {
@@ -43,8 +54,6 @@ struct MxGeo {
   const float *inv_dz32, *wu32, *wl32, *inv_dz2_32;
 };
 
-__device__ inline int64_t warp_entity() { return (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); }
-
 __device__ inline float half32(const float* __restrict__ f, const float* __restrict__ wu,
                                const float* __restrict__ wl, int h, int N) {
   if (h == 0) return f[0];
@@ -52,12 +61,13 @@ __device__ inline float half32(const float* __restrict__ f, const float* __restr
   return wu[h] * f[h - 1] + wl[h] * f[h];
 }
 
-// zeta (full levels), w_v (half levels)
-__global__ void __launch_bounds__(256) k_mx_vertex(MxGeo G, const float* __restrict__ vn, const float* __restrict__ w,
-                                                   float* __restrict__ zeta, float* __restrict__ w_v) {
-  const int64_t v = warp_entity();
-  if (v >= G.nv) return;
-  const int lane = threadIdx.x & 31, ld = G.ld;
+// ---------------------------------------------------------------- stencil items (lanes over levels)
+
+// O3 curl (full levels) and the vertex mean of w (half levels)
+template <int LPE>
+__device__ inline void mx_vertex_item(const MxGeo& G, const float* __restrict__ vn, const float* __restrict__ w,
+                                      float* __restrict__ zeta, float* __restrict__ w_v, int64_t v, int lane) {
+  const int ld = G.ld;
   int64_t E[6], C[6];
   float rw[6];
   for (int j = 0; j < 6; ++j) {
@@ -67,12 +77,12 @@ __global__ void __launch_bounds__(256) k_mx_vertex(MxGeo G, const float* __restr
   }
   const int deg = G.vdeg[v];
   const float inv_deg = 1.0f / (float)deg;
-  for (int k = lane; k < G.N; k += 32) {
+  for (int k = lane; k < G.N; k += LPE) {
     float acc = 0.f;
     for (int j = 0; j < 6; ++j) acc += rw[j] * vn[E[j] + k];
     zeta[v * ld + k] = acc;
   }
-  for (int h = lane; h <= G.N; h += 32) {
+  for (int h = lane; h <= G.N; h += LPE) {
     float acc = 0.f;
     for (int j = 0; j < 5; ++j) acc += w[C[j] + h];
     if (deg == 6) acc += w[C[5] + h];
@@ -80,19 +90,18 @@ __global__ void __launch_bounds__(256) k_mx_vertex(MxGeo G, const float* __restr
   }
 }
 
-// vt and K_e
-__global__ void __launch_bounds__(256) k_mx_edge_diag(MxGeo G, const float* __restrict__ vn, float* __restrict__ vt,
-                                                      float* __restrict__ Ke) {
-  const int64_t e = warp_entity();
-  if (e >= G.ne) return;
-  const int lane = threadIdx.x & 31, ld = G.ld;
+// O4 vt and K_e
+template <int LPE>
+__device__ inline void mx_edge_diag_item(const MxGeo& G, const float* __restrict__ vn, float* __restrict__ vt,
+                                         float* __restrict__ Ke, int64_t e, int lane) {
+  const int ld = G.ld;
   int64_t S[5];
   float W[5];
   for (int j = 0; j < 5; ++j) {
     S[j] = (int64_t)G.e2vt[5 * e + j] * ld;
     W[j] = G.vt_w32[5 * e + j];
   }
-  for (int k = lane; k < G.N; k += 32) {
+  for (int k = lane; k < G.N; k += LPE) {
     float acc = 0.f;
     for (int j = 0; j < 5; ++j) acc += W[j] * vn[S[j] + k];
     const float v0 = vn[e * ld + k];
@@ -101,17 +110,18 @@ __global__ void __launch_bounds__(256) k_mx_edge_diag(MxGeo G, const float* __re
   }
 }
 
-__global__ void __launch_bounds__(256) k_mx_cell_ke(MxGeo G, const float* __restrict__ Ke, float* __restrict__ Kc) {
-  const int64_t c = warp_entity();
-  if (c >= G.nc) return;
-  const int lane = threadIdx.x & 31, ld = G.ld;
+// O5 K_c
+template <int LPE>
+__device__ inline void mx_cell_ke_item(const MxGeo& G, const float* __restrict__ Ke, float* __restrict__ Kc, int64_t c,
+                                       int lane) {
+  const int ld = G.ld;
   int64_t E[3];
   float kw[3];
   for (int s = 0; s < 3; ++s) {
     E[s] = (int64_t)G.c2e[3 * c + s] * ld;
     kw[s] = G.kin_w32[3 * c + s];
   }
-  for (int k = lane; k < G.N; k += 32) Kc[c * ld + k] = kw[0] * Ke[E[0] + k] + kw[1] * Ke[E[1] + k] + kw[2] * Ke[E[2] + k];
+  for (int k = lane; k < G.N; k += LPE) Kc[c * ld + k] = kw[0] * Ke[E[0] + k] + kw[1] * Ke[E[1] + k] + kw[2] * Ke[E[2] + k];
 }
 
 struct MxEdgeArgs {
@@ -127,17 +137,17 @@ struct MxEdgeArgs {
   int corrector;
 };
 
-__global__ void __launch_bounds__(256) k_mx_edge_tend(MxGeo G, MxEdgeArgs a) {
-  const int64_t e = warp_entity();
-  if (e >= G.ne) return;
-  const int lane = threadIdx.x & 31, ld = G.ld, N = G.N;
+// vn tendency and update, horizontal flux integrals, edge part of the w advection
+template <int LPE>
+__device__ inline void mx_edge_tend_item(const MxGeo& G, const MxEdgeArgs& a, int64_t e, int lane) {
+  const int ld = G.ld, N = G.N;
   const int64_t c1 = (int64_t)G.e2c[2 * e] * ld, c2 = (int64_t)G.e2c[2 * e + 1] * ld;
   const int64_t v1 = (int64_t)G.e2v[2 * e] * ld, v2 = (int64_t)G.e2v[2 * e + 1] * ld;
   const float ide = G.inv_de32[e], ile = G.inv_le32[e], fe = G.f_e32[e], le = G.l_e32[e];
   const float* vn = a.vn + e * ld;
   const float* vt = a.vt + e * ld;
   const int64_t o = e * ld;
-  for (int k = lane; k < N; k += 32) {
+  for (int k = lane; k < N; k += LPE) {
     const float vie0 = half32(vn, G.wu32, G.wl32, k, N);
     const float vie1 = half32(vn, G.wu32, G.wl32, k + 1, N);
     const float wbar = 0.25f * ((a.w[c1 + k] + a.w[c2 + k]) + (a.w[c1 + k + 1] + a.w[c2 + k + 1]));
@@ -159,10 +169,105 @@ __global__ void __launch_bounds__(256) k_mx_edge_tend(MxGeo G, MxEdgeArgs a) {
     a.gth[o + k] = phi * th_e;
     if (a.corrector) a.mflx[o + k] += (double)F * a.inv_nsub;
   }
-  for (int h = lane; h <= N; h += 32) {
+  for (int h = lane; h <= N; h += LPE) {
     const float vie = half32(vn, G.wu32, G.wl32, h, N);
     const float tie = half32(vt, G.wu32, G.wl32, h, N);
     a.a_e[o + h] = vie * (a.w[c2 + h] - a.w[c1 + h]) * ide + tie * (a.w_v[v2 + h] - a.w_v[v1 + h]) * ile;
+  }
+}
+
+// diffusion: least-squares vertex velocity and O3 curl of vn
+template <int LPE>
+__device__ inline void mx_diff_vertex_item(const MxGeo& G, const float* __restrict__ vn, float* __restrict__ ux,
+                                           float* __restrict__ uy, float* __restrict__ uz, float* __restrict__ zeta,
+                                           int64_t v, int lane) {
+  const int ld = G.ld;
+  int64_t E[6];
+  for (int j = 0; j < 6; ++j) E[j] = (int64_t)G.v2e[6 * v + j] * ld;
+  const float* lw = G.lsq_w32 + 18 * v;
+  const float* rw = G.rot_w32 + 6 * v;
+  float L[18], R[6];
+  for (int j = 0; j < 18; ++j) L[j] = lw[j];
+  for (int j = 0; j < 6; ++j) R[j] = rw[j];
+  for (int k = lane; k < G.N; k += LPE) {
+    float x = 0.f, y = 0.f, z = 0.f, r = 0.f;
+    for (int j = 0; j < 6; ++j) {
+      const float q = vn[E[j] + k];
+      x += L[3 * j] * q;
+      y += L[3 * j + 1] * q;
+      z += L[3 * j + 2] * q;
+      r += R[j] * q;
+    }
+    ux[v * ld + k] = x;
+    uy[v * ld + k] = y;
+    uz[v * ld + k] = z;
+    zeta[v * ld + k] = r;
+  }
+}
+
+// diffusion: O2 divergence of vn
+template <int LPE>
+__device__ inline void mx_diff_div_item(const MxGeo& G, const float* __restrict__ vn, float* __restrict__ divc,
+                                        int64_t c, int lane) {
+  const int ld = G.ld;
+  int64_t E[3];
+  float dw[3];
+  for (int s = 0; s < 3; ++s) {
+    E[s] = (int64_t)G.c2e[3 * c + s] * ld;
+    dw[s] = G.div_w32[3 * c + s];
+  }
+  for (int k = lane; k < G.N; k += LPE) divc[c * ld + k] = dw[0] * vn[E[0] + k] + dw[1] * vn[E[1] + k] + dw[2] * vn[E[2] + k];
+}
+
+// diffusion: Smagorinsky K_h, vn += dt K_h L(vn), theta_v flux
+template <int LPE>
+__device__ inline void mx_diff_edge_item(const MxGeo& G, float* __restrict__ vn, const float* __restrict__ ux,
+                                         const float* __restrict__ uy, const float* __restrict__ uz,
+                                         const float* __restrict__ zeta, const float* __restrict__ divc,
+                                         const float* __restrict__ thv, float* __restrict__ thflx, float dt, int64_t e,
+                                         int lane) {
+  const int ld = G.ld;
+  int64_t Q[4];
+  for (int j = 0; j < 4; ++j) Q[j] = (int64_t)G.e2q[4 * e + j] * ld;
+  const int64_t c1 = (int64_t)G.e2c[2 * e] * ld, c2 = (int64_t)G.e2c[2 * e + 1] * ld;
+  const int64_t v1 = (int64_t)G.e2v[2 * e] * ld, v2 = (int64_t)G.e2v[2 * e + 1] * ld;
+  const float nx = G.n_e32[3 * e], ny = G.n_e32[3 * e + 1], nz = G.n_e32[3 * e + 2];
+  const float tx = G.t_e32[3 * e], ty = G.t_e32[3 * e + 1], tz = G.t_e32[3 * e + 2];
+  const float ide = G.inv_de32[e], ile = G.inv_le32[e], i34 = G.L34inv32[e], le = G.l_e32[e];
+  const float cs2ld = (float)(kCsSmag * kCsSmag) * le / ide;
+  for (int k = lane; k < G.N; k += LPE) {
+    const float ax = ux[Q[3] + k] - ux[Q[2] + k], ay = uy[Q[3] + k] - uy[Q[2] + k], az = uz[Q[3] + k] - uz[Q[2] + k];
+    const float bx = ux[Q[1] + k] - ux[Q[0] + k], by = uy[Q[1] + k] - uy[Q[0] + k], bz = uz[Q[1] + k] - uz[Q[0] + k];
+    const float DT = (ax * nx + ay * ny + az * nz) * i34 - (bx * tx + by * ty + bz * tz) * ile;
+    const float DS = (ax * tx + ay * ty + az * tz) * i34 + (bx * nx + by * ny + bz * nz) * ile;
+    const float Kh = cs2ld * sqrtf(DT * DT + DS * DS);
+    const float lap = (divc[c2 + k] - divc[c1 + k]) * ide - (zeta[v2 + k] - zeta[v1 + k]) * ile;
+    vn[e * ld + k] += dt * Kh * lap;
+    thflx[e * ld + k] = le * Kh * (thv[c2 + k] - thv[c1 + k]) * ide;
+  }
+}
+
+// ---------------------------------------------------------------- column items (one thread per column)
+
+// per-level constants of the column solve for one dtau, FP64 [8][ld]:
+// wu, wl, dtau beta cpd / dzh, (1 - beta) cpd / dzh, 1/(1 + dtau r), dtau beta / dz,
+// dtau (1 - beta) / dz, Exner_ref
+enum { CC_WU = 0, CC_WL, CC_CA, CC_CX, CC_DAMP, CC_DTBDZ, CC_DT1BDZ, CC_EXREF, CC_COUNT };
+
+__global__ void k_mx_colconst(int N, int ld, const double* __restrict__ wu, const double* __restrict__ wl,
+                              const double* __restrict__ dzh, const double* __restrict__ dz,
+                              const double* __restrict__ ray, const double* __restrict__ ex_ref, double dtau,
+                              double* __restrict__ cc) {
+  for (int i = threadIdx.x; i < ld; i += blockDim.x) {
+    const bool interior = i > 0 && i < N;
+    cc[CC_WU * ld + i] = i <= N ? wu[i] : 0.0;
+    cc[CC_WL * ld + i] = i <= N ? wl[i] : 0.0;
+    cc[CC_CA * ld + i] = interior ? dtau * kBeta * kCpd / dzh[i] : 0.0;
+    cc[CC_CX * ld + i] = interior ? (1.0 - kBeta) * kCpd / dzh[i] : 0.0;
+    cc[CC_DAMP * ld + i] = i <= N ? 1.0 / (1.0 + dtau * ray[i]) : 1.0;
+    cc[CC_DTBDZ * ld + i] = i < N ? dtau * kBeta / dz[i] : 0.0;
+    cc[CC_DT1BDZ * ld + i] = i < N ? dtau * (1.0 - kBeta) / dz[i] : 0.0;
+    cc[CC_EXREF * ld + i] = i < N ? ex_ref[i] : 0.0;
   }
 }
 
@@ -176,38 +281,23 @@ struct MxColArgs {
   float* Aw0;                              // level-major [h][Nc]
   // FP32 shadows written by this stage, [Nc][ld]
   float *rho32, *thv32, *exp32, *w32;
+  const double* cc;                        // per-level constants for this dtau
   unsigned* status;
   double dtau, inv_nsub;
 };
 
-// one thread per column; CORR selects predictor (shadows of S* only) or corrector
-// (FP64 S^{n+1} in place, shadows of S^{n+1}, accumulated vertical mass flux)
+__device__ inline bool finite64(double x) {
+  return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
+}
+
+// the vertically implicit update of one column; CORR selects predictor (shadows of S*
+// only) or corrector (FP64 S^{n+1} in place, shadows of S^{n+1}, vertical mass flux)
 template <int NMAX, bool CORR>
-__global__ void __launch_bounds__(128) k_mx_column(MxGeo G, MxColArgs a) {
-  __shared__ double s_wu[NMAX + 1], s_wl[NMAX + 1], s_cA[NMAX + 1], s_cX[NMAX + 1], s_damp[NMAX + 1];
-  __shared__ double s_dtbdz[NMAX], s_dt1bdz[NMAX], s_exref[NMAX];
-  __shared__ float s_idz2[NMAX + 1];
-  const int N = G.N;
-  const double dtau = a.dtau;
-  for (int i = threadIdx.x; i <= N; i += blockDim.x) {
-    s_wu[i] = G.wu[i];
-    s_wl[i] = G.wl[i];
-    const double dzh = G.dzh[i];
-    s_cA[i] = (i > 0 && i < N) ? dtau * kBeta * kCpd / dzh : 0.0;
-    s_cX[i] = (i > 0 && i < N) ? (1.0 - kBeta) * kCpd / dzh : 0.0;
-    s_damp[i] = 1.0 / (1.0 + dtau * G.ray[i]);
-    s_idz2[i] = G.inv_dz2_32[i];
-    if (i < N) {
-      s_dtbdz[i] = dtau * kBeta / G.dz[i];
-      s_dt1bdz[i] = dtau * (1.0 - kBeta) / G.dz[i];
-      s_exref[i] = G.ex_ref[i];
-    }
-  }
-  __syncthreads();
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ inline void mx_column_item(const MxGeo& G, const MxColArgs& a, int64_t c) {
+  const int N = G.N, ld = G.ld;
   const int64_t nc = G.nc;
-  if (c >= nc) return;
-  const int ld = G.ld;
+  const double dtau = a.dtau;
+  const double* __restrict__ cc = a.cc;
   const int64_t o = c * ld;
 #define LM(p, k) (p)[(int64_t)(k) * nc + c]
   int64_t E[3];
@@ -223,23 +313,22 @@ __global__ void __launch_bounds__(128) k_mx_column(MxGeo G, MxColArgs a) {
 
   double rho_ic[NMAX + 1], M[NMAX + 1], Thx[NMAX], exx[NMAX], rhox[NMAX], cp[NMAX], dp[NMAX];
   float gam[NMAX];
-  // half-level interpolants of S^n and explicit predictors at full levels
+  // half-level interpolants of S^n
   double rho_m = LM(a.rho, 0), thv_m = LM(a.thv, 0);
   rho_ic[0] = rho_m;
   M[0] = rho_m * thv_m;
-  for (int k = 0; k < N; ++k) {
-    const double rho = (k == 0) ? rho_m : LM(a.rho, k);
-    const double thv = (k == 0) ? thv_m : LM(a.thv, k);
-    if (k > 0) {
-      const double ri = s_wu[k] * rho_m + s_wl[k] * rho;
-      rho_ic[k] = ri;
-      M[k] = ri * (s_wu[k] * thv_m + s_wl[k] * thv);
-    }
+  for (int k = 1; k < N; ++k) {
+    const double rho = LM(a.rho, k), thv = LM(a.thv, k);
+    const double wu = cc[CC_WU * ld + k], wl = cc[CC_WL * ld + k];
+    const double ri = wu * rho_m + wl * rho;
+    rho_ic[k] = ri;
+    M[k] = ri * (wu * thv_m + wl * thv);
     rho_m = rho;
     thv_m = thv;
   }
   rho_ic[N] = rho_m;
   M[N] = rho_m * thv_m;
+  // explicit predictors at full levels
   for (int k = 0; k < N; ++k) {
     // horizontal divergences: rho with an FP64 sum of the FP32 edge flux integrals
     const float p0 = sg[0] * a.phi[E[0] + k], p1 = sg[1] * a.phi[E[1] + k], p2 = sg[2] * a.phi[E[2] + k];
@@ -248,25 +337,26 @@ __global__ void __launch_bounds__(128) k_mx_column(MxGeo G, MxColArgs a) {
     const double rho = LM(a.rho, k), thv = LM(a.thv, k), ex = LM(a.ex, k);
     const double w0 = LM(a.w, k), w1 = LM(a.w, k + 1);
     const double Th = rho * thv;
-    rhox[k] = rho - dtau * Dr - s_dt1bdz[k] * (rho_ic[k] * w0 - rho_ic[k + 1] * w1);
-    const double thx = Th - (double)(dtau32 * Dt) - s_dt1bdz[k] * (M[k] * w0 - M[k + 1] * w1);
+    const double dt1 = cc[CC_DT1BDZ * ld + k];
+    rhox[k] = rho - dtau * Dr - dt1 * (rho_ic[k] * w0 - rho_ic[k + 1] * w1);
+    const double thx = Th - (double)(dtau32 * Dt) - dt1 * (M[k] * w0 - M[k + 1] * w1);
     Thx[k] = thx;
     const float g = kRcvF * ((float)ex / (float)Th);
     exx[k] = ex + (double)g * (thx - Th);
-    gam[k] = g * (float)s_dtbdz[k];
+    gam[k] = g * (float)cc[CC_DTBDZ * ld + k];
   }
   // tridiagonal system at interior half levels, Thomas forward sweep
   double thv_m1 = LM(a.thv, 0), ex_m1 = LM(a.ex, 0);
   for (int h = 1; h < N; ++h) {
     const float hadv = kw[0] * a.a_e[E[0] + h] + kw[1] * a.a_e[E[1] + h] + kw[2] * a.a_e[E[2] + h];
     const float ws = a.w_stage[o + h];
-    float Aw = -hadv - ws * (a.w_stage[o + h - 1] - a.w_stage[o + h + 1]) * s_idz2[h];
+    float Aw = -hadv - ws * (a.w_stage[o + h - 1] - a.w_stage[o + h + 1]) * G.inv_dz2_32[h];
     if (CORR) Aw = 0.5f * (LM(a.Aw0, h) + Aw);
     else LM(a.Aw0, h) = Aw;
     const double thv_h = LM(a.thv, h), ex_h = LM(a.ex, h);
-    const double th_ic = s_wu[h] * thv_m1 + s_wl[h] * thv_h;
-    const double wx = LM(a.w, h) + dtau * ((double)Aw - s_cX[h] * th_ic * (ex_m1 - ex_h) - kGrav);
-    const double aa = s_cA[h] * th_ic;
+    const double th_ic = cc[CC_WU * ld + h] * thv_m1 + cc[CC_WL * ld + h] * thv_h;
+    const double wx = LM(a.w, h) + dtau * ((double)Aw - cc[CC_CX * ld + h] * th_ic * (ex_m1 - ex_h) - kGrav);
+    const double aa = cc[CC_CA * ld + h] * th_ic;
     const double gm = (double)gam[h - 1], gk = (double)gam[h];
     const double lower = -aa * gm * M[h - 1];
     const double diag = 1.0 + aa * (gm + gk) * M[h];
@@ -288,16 +378,17 @@ __global__ void __launch_bounds__(128) k_mx_column(MxGeo G, MxColArgs a) {
   for (int i = N - 3; i >= 0; --i) dp[i] = dp[i] - cp[i] * dp[i + 1];
   // updates
   double wn_prev = 0.0;
-  bool bad = false;
+  bool ok = true;
   for (int k = 0; k < N; ++k) {
     const int h1 = k + 1;
-    const double wn1 = (h1 < N) ? dp[h1 - 1] * s_damp[h1] : 0.0;
+    const double wn1 = (h1 < N) ? dp[h1 - 1] * cc[CC_DAMP * ld + h1] : 0.0;
     const double q = M[k] * wn_prev - M[k + 1] * wn1;
     const double r = rho_ic[k] * wn_prev - rho_ic[k + 1] * wn1;
-    const double Th_n = Thx[k] - s_dtbdz[k] * q;
+    const double dtb = cc[CC_DTBDZ * ld + k];
+    const double Th_n = Thx[k] - dtb * q;
     const double ex_n = exx[k] - (double)gam[k] * q;
-    const double rho_n = rhox[k] - s_dtbdz[k] * r;
-    const float exp_n = (float)(ex_n - s_exref[k]);
+    const double rho_n = rhox[k] - dtb * r;
+    const float exp_n = (float)(ex_n - cc[CC_EXREF * ld + k]);
     if (CORR) {
       const double thv_n = Th_n / rho_n;
       const double wold = LM(a.w, k);
@@ -307,11 +398,11 @@ __global__ void __launch_bounds__(128) k_mx_column(MxGeo G, MxColArgs a) {
       LM(a.ex, k) = ex_n;
       LM(a.w, k) = wn_prev;
       a.thv32[o + k] = (float)thv_n;
-      bad |= !isfinite(thv_n) || !isfinite(ex_n) || !isfinite(wn_prev);
+      ok = ok && finite64(thv_n) && finite64(ex_n) && finite64(wn_prev);
     } else {
       const float rho32 = (float)rho_n;
       a.thv32[o + k] = (float)Th_n / rho32;
-      bad |= !isfinite(rho_n) || !isfinite(ex_n) || !isfinite(wn_prev);
+      ok = ok && finite64(rho_n) && finite64(ex_n) && finite64(wn_prev);
     }
     a.rho32[o + k] = (float)rho_n;
     a.exp32[o + k] = exp_n;
@@ -323,89 +414,16 @@ __global__ void __launch_bounds__(128) k_mx_column(MxGeo G, MxColArgs a) {
     LM(a.wflx, N) += rho_ic[N] * ((1.0 - kBeta) * LM(a.w, N)) * a.inv_nsub;
     LM(a.w, N) = 0.0;
   }
-  if (bad) atomicOr(a.status, 1u);
+  if (!ok) atomicOr(a.status, 1u);
 #undef LM
 }
 
-// ---------------------------------------------------------------- diffusion (once per step)
-__global__ void __launch_bounds__(256) k_mx_diff_vertex(MxGeo G, const float* __restrict__ vn, float* __restrict__ ux,
-                                                        float* __restrict__ uy, float* __restrict__ uz,
-                                                        float* __restrict__ zeta) {
-  const int64_t v = warp_entity();
-  if (v >= G.nv) return;
-  const int lane = threadIdx.x & 31, ld = G.ld;
-  int64_t E[6];
-  for (int j = 0; j < 6; ++j) E[j] = (int64_t)G.v2e[6 * v + j] * ld;
-  const float* lw = G.lsq_w32 + 18 * v;
-  const float* rw = G.rot_w32 + 6 * v;
-  float L[18], R[6];
-  for (int j = 0; j < 18; ++j) L[j] = lw[j];
-  for (int j = 0; j < 6; ++j) R[j] = rw[j];
-  for (int k = lane; k < G.N; k += 32) {
-    float x = 0.f, y = 0.f, z = 0.f, r = 0.f;
-    for (int j = 0; j < 6; ++j) {
-      const float q = vn[E[j] + k];
-      x += L[3 * j] * q;
-      y += L[3 * j + 1] * q;
-      z += L[3 * j + 2] * q;
-      r += R[j] * q;
-    }
-    ux[v * ld + k] = x;
-    uy[v * ld + k] = y;
-    uz[v * ld + k] = z;
-    zeta[v * ld + k] = r;
-  }
-}
-
-__global__ void __launch_bounds__(256) k_mx_diff_div(MxGeo G, const float* __restrict__ vn, float* __restrict__ divc) {
-  const int64_t c = warp_entity();
-  if (c >= G.nc) return;
-  const int lane = threadIdx.x & 31, ld = G.ld;
-  int64_t E[3];
-  float dw[3];
-  for (int s = 0; s < 3; ++s) {
-    E[s] = (int64_t)G.c2e[3 * c + s] * ld;
-    dw[s] = G.div_w32[3 * c + s];
-  }
-  for (int k = lane; k < G.N; k += 32) divc[c * ld + k] = dw[0] * vn[E[0] + k] + dw[1] * vn[E[1] + k] + dw[2] * vn[E[2] + k];
-}
-
-__global__ void __launch_bounds__(256) k_mx_diff_edge(MxGeo G, float* __restrict__ vn, const float* __restrict__ ux,
-                                                      const float* __restrict__ uy, const float* __restrict__ uz,
-                                                      const float* __restrict__ zeta, const float* __restrict__ divc,
-                                                      const float* __restrict__ thv, float* __restrict__ thflx,
-                                                      float dt) {
-  const int64_t e = warp_entity();
-  if (e >= G.ne) return;
-  const int lane = threadIdx.x & 31, ld = G.ld;
-  int64_t Q[4];
-  for (int j = 0; j < 4; ++j) Q[j] = (int64_t)G.e2q[4 * e + j] * ld;
-  const int64_t c1 = (int64_t)G.e2c[2 * e] * ld, c2 = (int64_t)G.e2c[2 * e + 1] * ld;
-  const int64_t v1 = (int64_t)G.e2v[2 * e] * ld, v2 = (int64_t)G.e2v[2 * e + 1] * ld;
-  const float nx = G.n_e32[3 * e], ny = G.n_e32[3 * e + 1], nz = G.n_e32[3 * e + 2];
-  const float tx = G.t_e32[3 * e], ty = G.t_e32[3 * e + 1], tz = G.t_e32[3 * e + 2];
-  const float ide = G.inv_de32[e], ile = G.inv_le32[e], i34 = G.L34inv32[e], le = G.l_e32[e];
-  const float cs2ld = (float)(kCsSmag * kCsSmag) * le / ide;
-  for (int k = lane; k < G.N; k += 32) {
-    const float ax = ux[Q[3] + k] - ux[Q[2] + k], ay = uy[Q[3] + k] - uy[Q[2] + k], az = uz[Q[3] + k] - uz[Q[2] + k];
-    const float bx = ux[Q[1] + k] - ux[Q[0] + k], by = uy[Q[1] + k] - uy[Q[0] + k], bz = uz[Q[1] + k] - uz[Q[0] + k];
-    const float DT = (ax * nx + ay * ny + az * nz) * i34 - (bx * tx + by * ty + bz * tz) * ile;
-    const float DS = (ax * tx + ay * ty + az * tz) * i34 + (bx * nx + by * ny + bz * nz) * ile;
-    const float Kh = cs2ld * sqrtf(DT * DT + DS * DS);
-    const float lap = (divc[c2 + k] - divc[c1 + k]) * ide - (zeta[v2 + k] - zeta[v1 + k]) * ile;
-    vn[e * ld + k] += dt * Kh * lap;
-    thflx[e * ld + k] = le * Kh * (thv[c2 + k] - thv[c1 + k]) * ide;
-  }
-}
-
-// one thread per column: theta_v += dt/A sum s l K_h dtheta/d (FP32 increment, FP64
-// accumulation), Exner at constant density, shadows refreshed
-__global__ void __launch_bounds__(128) k_mx_diff_theta(MxGeo G, const float* __restrict__ thflx, double* __restrict__ thv,
-                                                       double* __restrict__ ex, float* __restrict__ thv32,
-                                                       float* __restrict__ exp32, float dt) {
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// diffusion of theta_v for one column: FP32 increment, FP64 accumulation, Exner at
+// constant density, shadows refreshed
+__device__ inline void mx_diff_theta_item(const MxGeo& G, const float* __restrict__ thflx, double* __restrict__ thv,
+                                          double* __restrict__ ex, float* __restrict__ thv32, float* __restrict__ exp32,
+                                          float dt, int64_t c) {
   const int64_t nc = G.nc;
-  if (c >= nc) return;
   const int ld = G.ld;
   int64_t E[3];
   float sg[3];
@@ -427,6 +445,63 @@ __global__ void __launch_bounds__(128) k_mx_diff_theta(MxGeo G, const float* __r
   }
 }
 
+// ---------------------------------------------------------------- per-state kernels
+
+// warp w, lanes [sub*LPE, (sub+1)*LPE) handle entity w * (32/LPE) + sub
+#define ITEM_PROLOGUE(LPE, COUNT)                                                        \
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;             \
+  const int64_t item = gw * (32 / (LPE)) + (int64_t)((threadIdx.x & 31) / (LPE));        \
+  const int lane = (int)(threadIdx.x & ((LPE) - 1));                                     \
+  if (item >= (COUNT)) return;
+
+template <int LPE>
+__global__ void __launch_bounds__(512) k_mx_vertex(MxGeo G, const float* vn, const float* w, float* zeta, float* w_v) {
+  ITEM_PROLOGUE(LPE, G.nv)
+  mx_vertex_item<LPE>(G, vn, w, zeta, w_v, item, lane);
+}
+template <int LPE>
+__global__ void __launch_bounds__(512) k_mx_edge_diag(MxGeo G, const float* vn, float* vt, float* Ke) {
+  ITEM_PROLOGUE(LPE, G.ne)
+  mx_edge_diag_item<LPE>(G, vn, vt, Ke, item, lane);
+}
+template <int LPE>
+__global__ void __launch_bounds__(512) k_mx_cell_ke(MxGeo G, const float* Ke, float* Kc) {
+  ITEM_PROLOGUE(LPE, G.nc)
+  mx_cell_ke_item<LPE>(G, Ke, Kc, item, lane);
+}
+template <int LPE>
+__global__ void __launch_bounds__(512) k_mx_edge_tend(MxGeo G, MxEdgeArgs a) {
+  ITEM_PROLOGUE(LPE, G.ne)
+  mx_edge_tend_item<LPE>(G, a, item, lane);
+}
+template <int LPE>
+__global__ void __launch_bounds__(512) k_mx_diff_vertex(MxGeo G, const float* vn, float* ux, float* uy, float* uz,
+                                                        float* zeta, float* divc) {
+  // vertices first, then cells (divergence): both only read vn
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t item = gw * (32 / LPE) + (int64_t)((threadIdx.x & 31) / LPE);
+  const int lane = (int)(threadIdx.x & (LPE - 1));
+  if (item < G.nv) mx_diff_vertex_item<LPE>(G, vn, ux, uy, uz, zeta, item, lane);
+  else if (item < G.nv + G.nc) mx_diff_div_item<LPE>(G, vn, divc, item - G.nv, lane);
+}
+template <int LPE>
+__global__ void __launch_bounds__(512) k_mx_diff_edge(MxGeo G, float* vn, const float* ux, const float* uy,
+                                                      const float* uz, const float* zeta, const float* divc,
+                                                      const float* thv, float* thflx, float dt) {
+  ITEM_PROLOGUE(LPE, G.ne)
+  mx_diff_edge_item<LPE>(G, vn, ux, uy, uz, zeta, divc, thv, thflx, dt, item, lane);
+}
+template <int NMAX, bool CORR>
+__global__ void __launch_bounds__(128) k_mx_column(MxGeo G, MxColArgs a) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < G.nc) mx_column_item<NMAX, CORR>(G, a, c);
+}
+__global__ void __launch_bounds__(128) k_mx_diff_theta(MxGeo G, const float* thflx, double* thv, double* ex,
+                                                       float* thv32, float* exp32, float dt) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < G.nc) mx_diff_theta_item(G, thflx, thv, ex, thv32, exp32, dt, c);
+}
+
 MxGeo make_mx_geo(const icon_grid* grid, const StateDev& s) {
   const GridDev& g = grid->g;
   const Vertical& v = grid->vert;
@@ -444,6 +519,86 @@ MxGeo make_mx_geo(const icon_grid* grid, const StateDev& s) {
   return G;
 }
 
+// stage arguments of one state
+MxEdgeArgs edge_args(StateDev& s, bool corr, double dtau, int nsub) {
+  MxEdgeArgs ea;
+  ea.vn = corr ? s.vn32_s : s.vn32;
+  ea.w = corr ? s.w32_s : s.w32;
+  ea.rho = corr ? s.rho32_s : s.rho32;
+  ea.thv = corr ? s.thv32_s : s.thv32;
+  ea.exp = corr ? s.exp32_s : s.exp32;
+  ea.vt = s.vt32; ea.Kc = s.Kc32; ea.zeta = s.zeta32; ea.w_v = s.wv32;
+  ea.vn_base = s.vn32;
+  ea.vn_out = corr ? s.vn32 : s.vn32_s;
+  ea.Avn0 = s.Avn0_32;
+  ea.phi = s.F32; ea.gth = s.G32; ea.a_e = s.ae32; ea.mflx = s.mflx;
+  ea.dtau = (float)dtau; ea.inv_nsub = 1.0 / nsub; ea.corrector = corr;
+  return ea;
+}
+
+MxColArgs col_args(StateDev& s, bool corr, double dtau, int nsub) {
+  MxColArgs ca;
+  ca.rho = s.rho; ca.thv = s.thv; ca.ex = s.ex; ca.w = s.w; ca.wflx = s.wflx;
+  ca.phi = s.F32; ca.gth = s.G32; ca.a_e = s.ae32;
+  ca.w_stage = corr ? s.w32_s : s.w32;
+  ca.Aw0 = s.Aw0_32;
+  ca.rho32 = corr ? s.rho32 : s.rho32_s;
+  ca.thv32 = corr ? s.thv32 : s.thv32_s;
+  ca.exp32 = corr ? s.exp32 : s.exp32_s;
+  ca.w32 = corr ? s.w32 : s.w32_s;
+  ca.cc = s.colconst;
+  ca.status = s.status;
+  ca.dtau = dtau; ca.inv_nsub = 1.0 / nsub;
+  return ca;
+}
+
+// ---------------------------------------------------------------- launch helpers with tile choices
+unsigned item_blocks(int64_t n, int lpe, int block) {
+  const int64_t per_block = (int64_t)(block / 32) * (32 / lpe);
+  return (unsigned)((n + per_block - 1) / per_block);
+}
+
+void launch_kind(int kind, const TileChoice& t, const MxGeo& G, StateDev& s, const MxEdgeArgs& ea, float dt,
+                 cudaStream_t st) {
+  const bool l16 = t.lanes == 16;
+  const int B = t.block;
+  switch (kind) {
+    case K_MX_VERTEX:
+      if (l16) k_mx_vertex<16><<<item_blocks(G.nv, 16, B), B, 0, st>>>(G, ea.vn, ea.w, s.zeta32, s.wv32);
+      else k_mx_vertex<32><<<item_blocks(G.nv, 32, B), B, 0, st>>>(G, ea.vn, ea.w, s.zeta32, s.wv32);
+      break;
+    case K_MX_EDGE:
+      if (l16) k_mx_edge_diag<16><<<item_blocks(G.ne, 16, B), B, 0, st>>>(G, ea.vn, s.vt32, s.Ke32);
+      else k_mx_edge_diag<32><<<item_blocks(G.ne, 32, B), B, 0, st>>>(G, ea.vn, s.vt32, s.Ke32);
+      break;
+    case K_MX_CELL_KE:
+      if (l16) k_mx_cell_ke<16><<<item_blocks(G.nc, 16, B), B, 0, st>>>(G, s.Ke32, s.Kc32);
+      else k_mx_cell_ke<32><<<item_blocks(G.nc, 32, B), B, 0, st>>>(G, s.Ke32, s.Kc32);
+      break;
+    case K_MX_EDGE_TEND:
+      if (l16) k_mx_edge_tend<16><<<item_blocks(G.ne, 16, B), B, 0, st>>>(G, ea);
+      else k_mx_edge_tend<32><<<item_blocks(G.ne, 32, B), B, 0, st>>>(G, ea);
+      break;
+    case K_MX_DIFF_VERTEX:
+      if (l16)
+        k_mx_diff_vertex<16><<<item_blocks(G.nv + G.nc, 16, B), B, 0, st>>>(G, s.vn32, s.uvx32, s.uvy32, s.uvz32,
+                                                                         s.zeta32, s.Kc32);
+      else
+        k_mx_diff_vertex<32><<<item_blocks(G.nv + G.nc, 32, B), B, 0, st>>>(G, s.vn32, s.uvx32, s.uvy32, s.uvz32,
+                                                                         s.zeta32, s.Kc32);
+      break;
+    case K_MX_DIFF_EDGE:
+      if (l16)
+        k_mx_diff_edge<16><<<item_blocks(G.ne, 16, B), B, 0, st>>>(G, s.vn32, s.uvx32, s.uvy32, s.uvz32, s.zeta32,
+                                                                s.Kc32, s.thv32, s.Ke32, dt);
+      else
+        k_mx_diff_edge<32><<<item_blocks(G.ne, 32, B), B, 0, st>>>(G, s.vn32, s.uvx32, s.uvy32, s.uvz32, s.zeta32,
+                                                                s.Kc32, s.thv32, s.Ke32, dt);
+      break;
+    default: break;
+  }
+}
+
 template <bool CORR>
 void launch_mx_column(const MxGeo& G, const MxColArgs& a, cudaStream_t st) {
   const unsigned nb = blocks_for(G.nc, 128);
@@ -454,7 +609,93 @@ void launch_mx_column(const MxGeo& G, const MxColArgs& a, cudaStream_t st) {
   else k_mx_column<256, CORR><<<nb, 128, 0, st>>>(G, a);
 }
 
+// ---------------------------------------------------------------- autotuner
+// Candidate tiles over (entity, level): 32 lanes per entity (one entity per warp)
+// or 16 (two per warp), blocks of 128, 256 or 512 threads. Each stencil kind is timed
+// on the state's own data (three launches per candidate, CUDA events) and the fastest
+// kept. Choices are cached per (kind, grid size, levels, GPU) in the process and, if
+// the environment variable ICON_TUNE_CACHE names a file, in that file.
+const int kTunedKinds[] = {K_MX_VERTEX, K_MX_EDGE, K_MX_CELL_KE, K_MX_EDGE_TEND, K_MX_DIFF_VERTEX};
+std::mutex g_tune_mu;
+std::map<std::string, TileChoice> g_tune_cache;
+bool g_tune_file_loaded = false;
+
+std::string tune_key(int kind, const MxGeo& G) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp p;
+  cudaGetDeviceProperties(&p, dev);
+  char buf[160];
+  snprintf(buf, sizeof(buf), "k%d_nc%lld_N%d_sm%d%d_n%d", kind, (long long)G.nc, G.N, p.major, p.minor,
+           p.multiProcessorCount);
+  return buf;
+}
+
+void load_tune_file() {
+  if (g_tune_file_loaded) return;
+  g_tune_file_loaded = true;
+  const char* path = getenv("ICON_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = fopen(path, "r");
+  if (!f) return;
+  char key[160];
+  int lanes, block;
+  while (fscanf(f, "%159s %d %d", key, &lanes, &block) == 3) g_tune_cache[key] = TileChoice{lanes, block};
+  fclose(f);
+}
+
+void save_tune_entry(const std::string& key, const TileChoice& t) {
+  const char* path = getenv("ICON_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "%s %d %d\n", key.c_str(), t.lanes, t.block);
+  fclose(f);
+}
+
 }  // namespace
+
+void autotune_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream) {
+  StateDev& s = st->s;
+  const MxGeo G = make_mx_geo(st->grid, s);
+  const double dtau = dt / nsub;
+  // the predictor's arguments: every tuned kernel then writes only scratch or S* buffers
+  const MxEdgeArgs ea = edge_args(s, false, dtau, nsub);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  load_tune_file();
+  for (int kind : kTunedKinds) {
+    if (st->tile[kind].lanes != 0 && st->tile_forced[kind]) continue;
+    const std::string key = tune_key(kind, G);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      st->tile[kind] = it->second;
+      continue;
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    TileChoice bestc{32, 256};
+    for (int lanes : {32, 16})
+      for (int block : {128, 256, 512}) {
+        const TileChoice t{lanes, block};
+        launch_kind(kind, t, G, s, ea, (float)dt, stream);     // warm
+        cudaEventRecord(e0, stream);
+        for (int r = 0; r < 3; ++r) launch_kind(kind, t, G, s, ea, (float)dt, stream);
+        cudaEventRecord(e1, stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; bestc = t; }
+      }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    st->tile[kind] = bestc;
+    g_tune_cache[key] = bestc;
+    save_tune_entry(key, bestc);
+  }
+  st->tuned = true;
+}
 
 void enqueue_step_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream) {
   const icon_grid* grid = st->grid;
@@ -462,65 +703,337 @@ void enqueue_step_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream
   const MxGeo G = make_mx_geo(grid, s);
   const int64_t nc = G.nc;
   const double dtau = dt / nsub;
-  const unsigned nbv = blocks_for(G.nv, kWarps), nbe = blocks_for(G.ne, kWarps), nbc = blocks_for(G.nc, kWarps);
   cudaMemsetAsync(s.mflx, 0, sizeof(double) * G.ne * G.ld, stream);
   cudaMemsetAsync(s.wflx, 0, sizeof(double) * nc * (G.N + 1), stream);
+  k_mx_colconst<<<1, 128, 0, stream>>>(G.N, G.ld, G.wu, G.wl, G.dzh, G.dz, G.ray, s.ex_ref, dtau, s.colconst);
+  auto tile = [&](int kind) { return st->tile[kind].lanes ? st->tile[kind] : TileChoice{32, 256}; };
   for (int it = 0; it < nsub; ++it) {
     for (int stage = 0; stage < 2; ++stage) {
       const bool corr = stage == 1;
-      const float* vn = corr ? s.vn32_s : s.vn32;
-      const float* w = corr ? s.w32_s : s.w32;
-      prof_begin(stream, K_MX_VERTEX);
-      k_mx_vertex<<<nbv, 256, 0, stream>>>(G, vn, w, s.zeta32, s.wv32);
-      prof_end(stream);
-      prof_begin(stream, K_MX_EDGE);
-      k_mx_edge_diag<<<nbe, 256, 0, stream>>>(G, vn, s.vt32, s.Ke32);
-      prof_end(stream);
-      prof_begin(stream, K_MX_CELL_KE);
-      k_mx_cell_ke<<<nbc, 256, 0, stream>>>(G, s.Ke32, s.Kc32);
-      prof_end(stream);
-      MxEdgeArgs ea;
-      ea.vn = vn; ea.w = w;
-      ea.rho = corr ? s.rho32_s : s.rho32;
-      ea.thv = corr ? s.thv32_s : s.thv32;
-      ea.exp = corr ? s.exp32_s : s.exp32;
-      ea.vt = s.vt32; ea.Kc = s.Kc32; ea.zeta = s.zeta32; ea.w_v = s.wv32;
-      ea.vn_base = s.vn32;
-      ea.vn_out = corr ? s.vn32 : s.vn32_s;
-      ea.Avn0 = s.Avn0_32;
-      ea.phi = s.F32; ea.gth = s.G32; ea.a_e = s.ae32; ea.mflx = s.mflx;
-      ea.dtau = (float)dtau; ea.inv_nsub = 1.0 / nsub; ea.corrector = corr;
-      prof_begin(stream, K_MX_EDGE_TEND);
-      k_mx_edge_tend<<<nbe, 256, 0, stream>>>(G, ea);
-      prof_end(stream);
-      MxColArgs ca;
-      ca.rho = s.rho; ca.thv = s.thv; ca.ex = s.ex; ca.w = s.w; ca.wflx = s.wflx;
-      ca.phi = s.F32; ca.gth = s.G32; ca.a_e = s.ae32;
-      ca.w_stage = w;
-      ca.Aw0 = s.Aw0_32;
-      ca.rho32 = corr ? s.rho32 : s.rho32_s;
-      ca.thv32 = corr ? s.thv32 : s.thv32_s;
-      ca.exp32 = corr ? s.exp32 : s.exp32_s;
-      ca.w32 = corr ? s.w32 : s.w32_s;
-      ca.status = s.status;
-      ca.dtau = dtau; ca.inv_nsub = 1.0 / nsub;
+      const MxEdgeArgs ea = edge_args(s, corr, dtau, nsub);
+      for (int kind : {K_MX_VERTEX, K_MX_EDGE, K_MX_CELL_KE, K_MX_EDGE_TEND}) {
+        prof_begin(stream, kind);
+        launch_kind(kind, tile(kind), G, s, ea, (float)dt, stream);
+        prof_end(stream);
+      }
+      const MxColArgs ca = col_args(s, corr, dtau, nsub);
       prof_begin(stream, K_MX_COLUMN);
       if (corr) launch_mx_column<true>(G, ca, stream);
       else launch_mx_column<false>(G, ca, stream);
       prof_end(stream);
     }
   }
+  const MxEdgeArgs ea = edge_args(s, false, dtau, nsub);
   prof_begin(stream, K_MX_DIFF_VERTEX);
-  k_mx_diff_vertex<<<nbv, 256, 0, stream>>>(G, s.vn32, s.uvx32, s.uvy32, s.uvz32, s.zeta32);
-  k_mx_diff_div<<<nbc, 256, 0, stream>>>(G, s.vn32, s.Kc32);
+  launch_kind(K_MX_DIFF_VERTEX, tile(K_MX_DIFF_VERTEX), G, s, ea, (float)dt, stream);
   prof_end(stream);
   prof_begin(stream, K_MX_DIFF_EDGE);
-  k_mx_diff_edge<<<nbe, 256, 0, stream>>>(G, s.vn32, s.uvx32, s.uvy32, s.uvz32, s.zeta32, s.Kc32, s.thv32, s.Ke32,
-                                           (float)dt);
+  launch_kind(K_MX_DIFF_EDGE, tile(K_MX_DIFF_EDGE), G, s, ea, (float)dt, stream);
   prof_end(stream);
   prof_begin(stream, K_MX_DIFF_THETA);
   k_mx_diff_theta<<<blocks_for(nc, 128), 128, 0, stream>>>(G, s.Ke32, s.thv, s.ex, s.thv32, s.exp32, (float)dt);
   prof_end(stream);
+}
+
+// ---------------------------------------------------------------- persistent ensemble kernel
+//
+// All members of an ensemble (grids of any size, one precision, one level count)
+// advance through one step in ONE cooperative launch: every phase of the step
+// (vertex, edge diagnostics, cell kinetic energy, edge tendency, column solve for
+// predictor and corrector, then the diffusion phases) is a static work list over
+// (member, entity) or (member, column) shared by all blocks, separated by a grid
+// barrier. The barrier spins a bounded number of times; if it runs out it sets the
+// timeout bit of the status word, every block leaves at its next barrier and the
+// kernel returns normally.
+namespace {
+
+struct MemberDev {
+  MxGeo G;
+  MxEdgeArgs ea[2];
+  MxColArgs ca[2];
+  double* mflx;
+  double* wflx;
+  double* colconst;
+  const double* ex_ref;
+  float *vn32, *uvx32, *uvy32, *uvz32, *zeta32, *Kc32, *thv32, *Ke32, *exp32, *wv32, *vt32;
+  double *thv, *ex;
+  double dtau, dt;
+  int64_t off_v, off_e, off_c;  // this member's first item in each work list
+};
+
+struct EnsArgs {
+  const MemberDev* m;
+  int nm;
+  int nsub;
+  int64_t tot_v, tot_e, tot_c;
+  unsigned* bar;                // [0] arrivals, [1] generation
+  unsigned* status;             // ensemble status word (bit 1: barrier timeout)
+  long long spin_limit;
+  int skip_first_barrier;       // test hook: block 0 does not arrive at the first barrier
+};
+
+__device__ inline int find_member(const int64_t* off, int nm, int64_t item) {
+  int lo = 0, hi = nm - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= item) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// bounded grid barrier; returns false (for every thread of the block) once any block gave up
+__device__ bool grid_barrier(const EnsArgs& A, bool skip) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = A.bar + 1;
+    volatile unsigned* vstat = A.status;
+    int ok = ((*vstat) & 2u) == 0;
+    if (ok && !skip) {
+      const unsigned gen = *vgen;
+      __threadfence();
+      const unsigned arrived = atomicAdd(A.bar, 1u);
+      if (arrived == gridDim.x - 1) {
+        A.bar[0] = 0;
+        __threadfence();
+        atomicAdd(A.bar + 1, 1u);
+      } else {
+        long long spins = 0;
+        while (*vgen == gen) {
+          if ((*vstat) & 2u) { ok = 0; break; }
+          if (++spins > A.spin_limit) {
+            atomicOr(A.status, 2u);
+            ok = 0;
+            break;
+          }
+          __nanosleep(100);
+        }
+      }
+      __threadfence();
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <int NMAX>
+__global__ void __launch_bounds__(128) k_ensemble_step(EnsArgs A) {
+  __shared__ int64_t s_off_v[64], s_off_e[64], s_off_c[64];
+  for (int i = threadIdx.x; i < A.nm; i += blockDim.x) {
+    s_off_v[i] = A.m[i].off_v;
+    s_off_e[i] = A.m[i].off_e;
+    s_off_c[i] = A.m[i].off_c;
+  }
+  __syncthreads();
+  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nwarps = nthreads >> 5;
+  const int64_t gwarp = gtid >> 5;
+  const int lane = threadIdx.x & 31;
+  bool first = true;
+  auto sync = [&]() {
+    const bool skip = first && A.skip_first_barrier && blockIdx.x == 0;
+    first = false;
+    return grid_barrier(A, skip);
+  };
+
+  // phase 0: zero the accumulators
+  for (int m = 0; m < A.nm; ++m) {
+    const MemberDev& M = A.m[m];
+    const int64_t ne = M.G.ne * M.G.ld, nh = M.G.nc * (M.G.N + 1);
+    for (int64_t i = gtid; i < ne; i += nthreads) M.mflx[i] = 0.0;
+    for (int64_t i = gtid; i < nh; i += nthreads) M.wflx[i] = 0.0;
+  }
+  if (!sync()) return;
+  for (int it = 0; it < A.nsub; ++it) {
+    for (int stage = 0; stage < 2; ++stage) {
+      for (int64_t i = gwarp; i < A.tot_v; i += nwarps) {
+        const int m = find_member(s_off_v, A.nm, i);
+        const MemberDev& M = A.m[m];
+        mx_vertex_item<32>(M.G, M.ea[stage].vn, M.ea[stage].w, M.zeta32, M.wv32, i - M.off_v, lane);
+      }
+      if (!sync()) return;
+      for (int64_t i = gwarp; i < A.tot_e; i += nwarps) {
+        const int m = find_member(s_off_e, A.nm, i);
+        const MemberDev& M = A.m[m];
+        mx_edge_diag_item<32>(M.G, M.ea[stage].vn, M.vt32, M.Ke32, i - M.off_e, lane);
+      }
+      if (!sync()) return;
+      for (int64_t i = gwarp; i < A.tot_c; i += nwarps) {
+        const int m = find_member(s_off_c, A.nm, i);
+        const MemberDev& M = A.m[m];
+        mx_cell_ke_item<32>(M.G, M.Ke32, M.Kc32, i - M.off_c, lane);
+      }
+      if (!sync()) return;
+      for (int64_t i = gwarp; i < A.tot_e; i += nwarps) {
+        const int m = find_member(s_off_e, A.nm, i);
+        const MemberDev& M = A.m[m];
+        mx_edge_tend_item<32>(M.G, M.ea[stage], i - M.off_e, lane);
+      }
+      if (!sync()) return;
+      for (int64_t i = gtid; i < A.tot_c; i += nthreads) {
+        const int m = find_member(s_off_c, A.nm, i);
+        const MemberDev& M = A.m[m];
+        if (stage == 0) mx_column_item<NMAX, false>(M.G, M.ca[0], i - M.off_c);
+        else mx_column_item<NMAX, true>(M.G, M.ca[1], i - M.off_c);
+      }
+      if (!sync()) return;
+    }
+  }
+  // diffusion
+  for (int64_t i = gwarp; i < A.tot_v + A.tot_c; i += nwarps) {
+    if (i < A.tot_v) {
+      const int m = find_member(s_off_v, A.nm, i);
+      const MemberDev& M = A.m[m];
+      mx_diff_vertex_item<32>(M.G, M.vn32, M.uvx32, M.uvy32, M.uvz32, M.zeta32, i - M.off_v, lane);
+    } else {
+      const int64_t j = i - A.tot_v;
+      const int m = find_member(s_off_c, A.nm, j);
+      const MemberDev& M = A.m[m];
+      mx_diff_div_item<32>(M.G, M.vn32, M.Kc32, j - M.off_c, lane);
+    }
+  }
+  if (!sync()) return;
+  for (int64_t i = gwarp; i < A.tot_e; i += nwarps) {
+    const int m = find_member(s_off_e, A.nm, i);
+    const MemberDev& M = A.m[m];
+    mx_diff_edge_item<32>(M.G, M.vn32, M.uvx32, M.uvy32, M.uvz32, M.zeta32, M.Kc32, M.thv32, M.Ke32, (float)M.dt,
+                          i - M.off_e, lane);
+  }
+  if (!sync()) return;
+  for (int64_t i = gtid; i < A.tot_c; i += nthreads) {
+    const int m = find_member(s_off_c, A.nm, i);
+    const MemberDev& M = A.m[m];
+    mx_diff_theta_item(M.G, M.Ke32, M.thv, M.ex, M.thv32, M.exp32, (float)M.dt, i - M.off_c);
+  }
+}
+
+__global__ void k_ens_colconst(const MemberDev* m, int nm) {
+  const int i = blockIdx.x;
+  if (i >= nm) return;
+  const MemberDev& M = m[i];
+  const MxGeo& G = M.G;
+  const int ld = G.ld, N = G.N;
+  const double dtau = M.dtau;
+  double* cc = M.colconst;
+  for (int h = threadIdx.x; h < ld; h += blockDim.x) {
+    const bool interior = h > 0 && h < N;
+    cc[CC_WU * ld + h] = h <= N ? G.wu[h] : 0.0;
+    cc[CC_WL * ld + h] = h <= N ? G.wl[h] : 0.0;
+    cc[CC_CA * ld + h] = interior ? dtau * kBeta * kCpd / G.dzh[h] : 0.0;
+    cc[CC_CX * ld + h] = interior ? (1.0 - kBeta) * kCpd / G.dzh[h] : 0.0;
+    cc[CC_DAMP * ld + h] = h <= N ? 1.0 / (1.0 + dtau * G.ray[h]) : 1.0;
+    cc[CC_DTBDZ * ld + h] = h < N ? dtau * kBeta / G.dz[h] : 0.0;
+    cc[CC_DT1BDZ * ld + h] = h < N ? dtau * (1.0 - kBeta) / G.dz[h] : 0.0;
+    cc[CC_EXREF * ld + h] = h < N ? M.ex_ref[h] : 0.0;
+  }
+}
+
+}  // namespace
+
+int ensemble_prepare(EnsembleDev& E, icon_state* const* members, int n, const double* dts, int nsub) {
+  if (n > 64) {
+    set_error("icon_ensemble_step: at most 64 members in one persistent launch");
+    return ICON_EINVAL;
+  }
+  std::vector<MemberDev> host(n);
+  int64_t ov = 0, oe = 0, oc = 0;
+  int N = -1;
+  for (int i = 0; i < n; ++i) {
+    icon_state* st = members[i];
+    StateDev& s = st->s;
+    if (s.precision != ICON_MIXED) {
+      set_error("icon_ensemble_step: the persistent ensemble runs mixed-precision members");
+      return ICON_EINVAL;
+    }
+    MemberDev& M = host[i];
+    M.G = make_mx_geo(st->grid, s);
+    if (N >= 0 && M.G.N != N) {
+      set_error("icon_ensemble_step: members must share one level count");
+      return ICON_EINVAL;
+    }
+    N = M.G.N;
+    const double dtau = dts[i] / nsub;
+    M.dtau = dtau;
+    M.dt = dts[i];
+    for (int stage = 0; stage < 2; ++stage) {
+      M.ea[stage] = edge_args(s, stage == 1, dtau, nsub);
+      M.ca[stage] = col_args(s, stage == 1, dtau, nsub);
+    }
+    M.mflx = s.mflx; M.wflx = s.wflx; M.colconst = s.colconst; M.ex_ref = s.ex_ref;
+    M.vn32 = s.vn32; M.uvx32 = s.uvx32; M.uvy32 = s.uvy32; M.uvz32 = s.uvz32; M.zeta32 = s.zeta32;
+    M.Kc32 = s.Kc32; M.thv32 = s.thv32; M.Ke32 = s.Ke32; M.exp32 = s.exp32; M.thv = s.thv; M.ex = s.ex;
+    M.wv32 = s.wv32; M.vt32 = s.vt32;
+    M.off_v = ov; M.off_e = oe; M.off_c = oc;
+    ov += M.G.nv; oe += M.G.ne; oc += M.G.nc;
+  }
+  E.N = N;
+  E.tot_v = ov; E.tot_e = oe; E.tot_c = oc;
+  E.nm = n;
+  E.nsub = nsub;
+  if (!E.members) {
+    E.members = E.arena.get(sizeof(MemberDev) * 64);
+    static_assert(sizeof(MemberDev) * 64 < (1 << 20), "member table");
+    E.bar = E.arena.get_n<unsigned>(64);
+    if (!E.members || !E.bar) {
+      set_error("icon_ensemble_step: out of device memory");
+      return ICON_ENOMEM;
+    }
+  }
+  cudaStream_t st = current_stream();
+  ICON_CUDA(cudaMemcpyAsync(E.members, host.data(), sizeof(MemberDev) * n, cudaMemcpyHostToDevice, st));
+  ICON_CUDA(cudaMemsetAsync(E.bar, 0, 64 * sizeof(unsigned), st));
+  ICON_CUDA(cudaStreamSynchronize(st));
+  return ICON_OK;
+}
+
+int ensemble_launch(EnsembleDev& E, cudaStream_t st) {
+  EnsArgs A;
+  A.m = static_cast<const MemberDev*>(E.members);
+  A.nm = E.nm;
+  A.nsub = E.nsub;
+  A.tot_v = E.tot_v; A.tot_e = E.tot_e; A.tot_c = E.tot_c;
+  A.bar = E.bar;
+  A.status = E.bar + 8;
+  A.spin_limit = E.spin_limit;
+  A.skip_first_barrier = E.test_skip_barrier;
+  void (*kern)(EnsArgs);
+  if (E.N <= 32) kern = k_ensemble_step<32>;
+  else if (E.N <= 64) kern = k_ensemble_step<64>;
+  else if (E.N <= 96) kern = k_ensemble_step<96>;
+  else {
+    set_error("icon_ensemble_step: the persistent ensemble supports up to 96 levels");
+    return ICON_EINVAL;
+  }
+  if (E.grid_blocks == 0) {
+    int dev = 0, nsm = 0, per = 0;
+    ICON_CUDA(cudaGetDevice(&dev));
+    ICON_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    ICON_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 128, 0));
+    if (per < 1) {
+      set_error("icon_ensemble_step: the persistent kernel does not fit on an SM");
+      return ICON_ECUDA;
+    }
+    E.grid_blocks = nsm * per;
+  }
+  k_ens_colconst<<<E.nm, 64, 0, st>>>(A.m, E.nm);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(E.grid_blocks);
+  cfg.blockDim = dim3(128);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  prof_begin(st, K_ENSEMBLE);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, A);
+  prof_end(st);
+  if (e != cudaSuccess) return cuda_fail(e, "cooperative launch of the ensemble kernel");
+  return ICON_OK;
 }
 
 }  // namespace icon

@@ -29,8 +29,8 @@
 // Mapping: one warp per entity (edge, cell or vertex) with lanes over levels, so
 // every neighbour index is loaded once per entity and every gathered neighbour
 // row is a coalesced, aligned segment; one thread per column for the implicit
-// solve. This file is compiled without FMA contraction so that each expression
-// rounds exactly as written.
+// solve. The summation order of every stencil follows the operator definitions
+// (fixed neighbour order), so results do not depend on the launch shape.
 #include "icon_internal.h"
 
 namespace icon {

@@ -42,6 +42,12 @@ static_assert(K_KIND_COUNT <= ICON_KIND_COUNT, "kind table");
 void prof_begin(cudaStream_t st, int kind);
 void prof_end(cudaStream_t st);
 
+// tile over (entity, level) of a stencil kernel: lanes per entity (32 or 16) and block size
+struct TileChoice {
+  int lanes;
+  int block;
+};
+
 // ---------------------------------------------------------------- memory
 struct Allocator {
   void* (*alloc)(size_t, void*) = nullptr;
@@ -133,8 +139,8 @@ struct StateDev {
   // mixed mode stores rho, theta_v, Exner, w and wflx level-major ([k][Nc])
   bool level_major = false;
   double *ex_ref = nullptr;           // [ld] reference Exner profile
-  // column factorisation kept between predictor and corrector (mixed mode)
-  double *fac = nullptr;
+  // per-level constants of the column solve for the current dtau (mixed mode)
+  double* colconst = nullptr;
   // mass reduction partials and the device status word
   double *mass_part = nullptr;
   int mass_nblk = 0;
@@ -156,7 +162,27 @@ struct icon_state {
   cudaStream_t capture_stream = nullptr;
   cudaStream_t graph_stream = nullptr;
   cudaEvent_t done = nullptr;
+  // stencil tiles (mixed mode): chosen by the autotuner unless forced
+  icon::TileChoice tile[ICON_KIND_COUNT] = {};
+  bool tile_forced[ICON_KIND_COUNT] = {};
+  bool tuned = false;
 };
+
+namespace icon {
+// device side of an ensemble (dycore32.cu)
+struct EnsembleDev {
+  DeviceArena arena;
+  void* members = nullptr;     // MemberDev[64]
+  unsigned* bar = nullptr;     // [0] arrivals, [1] generation, [8] status
+  int nm = 0, nsub = 0, N = 0, grid_blocks = 0;
+  int64_t tot_v = 0, tot_e = 0, tot_c = 0;
+  long long spin_limit = 1ll << 24;
+  int test_skip_barrier = 0;
+};
+int ensemble_prepare(EnsembleDev& E, icon_state* const* members, int n, const double* dts, int nsub);
+int ensemble_launch(EnsembleDev& E, cudaStream_t st);
+void autotune_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream);
+}  // namespace icon
 
 namespace icon {
 // grid_build.cu
