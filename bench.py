@@ -35,7 +35,8 @@ from paper_2511_02021_gb300 import workloads as WL  # noqa: E402
 
 METRIC = "cell-level updates/s per dycore substep, % HBM roofline; mixed vs FP64"
 UNIT = "cell-level updates/s"
-WORKLOADS = {"r2b6-fp64": WL.R2B6_JET, "r2b8-mixed": WL.R2B8_JET_MIXED, "r2b9-mixed": WL.R2B9_JET_MIXED}
+WORKLOADS = {"r2b6-fp64": WL.R2B6_JET, "r2b8-mixed": WL.R2B8_JET_MIXED, "r2b9-mixed": WL.R2B9_JET_MIXED,
+             "ensemble": None}
 PROG = ("vn", "w", "rho", "theta_v", "exner")
 
 
@@ -298,6 +299,24 @@ def run_gpu(args, wl, rank, world, local_rank):
                  "mass_rel_drift": res_m["mass_rel_drift"], "roofline": res_m["roof"],
                  "kernels": res_m["breakdown"], "gpu_launches": res_m["kps"] * args.steps}
     m_drift = res["mass_rel_drift"]
+    err_vs_fp64 = None
+    if wl.precision == 1 and not args.no_mixed:
+        # error of one mixed step against one FP64 step from the same state (wind)
+        C.icon_state_free(st)
+        st = None
+        a = C.icon_state_init_ex(grid, 77, wl.case, noise_K=wl.noise_K, precision=0)
+        C.icon_dycore_step(a, wl.dt, wl.nsub)
+        ref = {f: C.icon_state_copy_field(a, grid, N, f) for f in ("vn", "exner")}
+        C.icon_state_free(a)
+        b = C.icon_state_init_ex(grid, 77, wl.case, noise_K=wl.noise_K, precision=1)
+        C.icon_dycore_step(b, wl.dt, wl.nsub)
+        err_vs_fp64 = {}
+        for f, x in ref.items():
+            y = C.icon_state_copy_field(b, grid, N, f)
+            err_vs_fp64[f] = float(np.linalg.norm(y - x) / np.linalg.norm(x))
+            del y
+        del ref
+        st = b
 
     # end to end through the C ABI with host buffers: h2d of the prognostic state,
     # the step, the mass integral and d2h of the updated state, every step
@@ -338,7 +357,119 @@ def run_gpu(args, wl, rank, world, local_rank):
                        else "mixed", "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (state %.2f GB)" % ((ne * N + 4 * nc * N) * 8 / 1e9)},
             "gpu_launches": kernels_per_step * args.steps, "roofline": roof, "kernels": breakdown,
-            "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "mass_rel_drift": m_drift, "mixed": other}
+            "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "mass_rel_drift": m_drift, "mixed": other,
+            "rel_l2_vs_fp64_after_1_step": err_vs_fp64}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- ensemble workload
+def run_ensemble(args, rank, world, local_rank):
+    """64 members (32 on R2B4 with dt 360 s, 32 on R2B5 with dt 180 s), 60 levels, mixed
+    precision, member perturbations from seed 3: one persistent cooperative launch per
+    step for all members, against the same members stepped one after another (each
+    from its own recorded graph)."""
+    import torch
+    torch.cuda.set_device(local_rank)
+    from paper_2511_02021_gb300 import build as B
+    B.build()
+    import paper_2511_02021_gb300 as P
+    from paper_2511_02021_gb300 import capi as C
+    P.use_torch_allocator(local_rank)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    P.bind_torch_stream(stream)
+    dist = world > 1
+    if dist:
+        import torch.distributed as td
+    E = WL.ENSEMBLE
+    N, nsub = E["nlev"], E["nsub"]
+    grids = {4: C.icon_grid_build(2, 4, N), 5: C.icon_grid_build(2, 5, N)}
+    spec = [(4, E["dt_b4"])] * E["members_b4"] + [(5, E["dt_b5"])] * E["members_b5"]
+
+    def make_states():
+        return [C.icon_state_init_ex(grids[b], E["seed"] + 1000 * rank, C.ICON_CASE_MEMBER, precision=1, member=m)
+                for m, (b, _) in enumerate(spec)]
+
+    cells = sum(20 * 4 ** (b + 1) for b, _ in spec)
+    dts = [dt for _, dt in spec]
+
+    def timed(fn, steps):
+        if dist:
+            td.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            td.barrier()
+        ms = e0.elapsed_time(e1)
+        if dist:
+            t = torch.tensor([ms], device="cuda")
+            td.all_reduce(t, op=td.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    # batched: one persistent launch per step
+    sts = make_states()
+    ens = C.icon_ensemble_create(sts)
+    C.icon_ensemble_step(ens, dts, nsub, args.warmup)
+    clocks = ClockSampler(local_rank) if rank == 0 else None
+    time.sleep(0.4)
+    ms_b = timed(lambda k: C._check(C._lib.icon_ensemble_step(ens, (C.ctypes.c_double * len(dts))(*dts), nsub, k)),
+                 args.steps)
+    clk = clocks.stop() if clocks else None
+    kms, kn = np.zeros(C.ICON_KIND_COUNT), np.zeros(C.ICON_KIND_COUNT, dtype=np.int32)
+    value_b = world * cells * N * nsub * args.steps / (ms_b * 1e-3)
+    C.icon_ensemble_free(ens)
+    for st in sts:
+        C.icon_state_free(st)
+
+    # sequential: every member from its own graph, one after another
+    sts = make_states()
+    for st, dt in zip(sts, dts):
+        for _ in range(args.warmup):
+            C.icon_dycore_step(st, dt, nsub)
+
+    def seq(k):
+        for _ in range(k):
+            for st, dt in zip(sts, dts):
+                C.icon_dycore_step_async(st, dt, nsub)
+    ms_s = timed(seq, args.steps)
+    for st in sts:
+        C.icon_state_status(st)
+    value_s = world * cells * N * nsub * args.steps / (ms_s * 1e-3)
+    launches_seq = sum(C.icon_state_step_kernels(st, dt, nsub) for st, dt in zip(sts, dts))
+    for st in sts:
+        C.icon_state_free(st)
+    for g in grids.values():
+        C.icon_grid_free(g)
+    if rank != 0:
+        return
+    hbm_peak, peak_src = peaks()
+    # algorithmic model of one persistent launch (one step of every member)
+    alg_bytes = 239.0 * cells * N * nsub
+    alg_flops = (2 * MX_COLUMN_FP64_OPS + 2.0) * cells * N * nsub
+    t_launch = ms_b / args.steps * 1e-3
+    hbm_frac = alg_bytes / t_launch / 1e9 / hbm_peak
+    alu_frac = alg_flops / t_launch / FP64_INSTR_PEAK
+    roof = {"kernel": "ensemble_persistent", "bound": "alu" if alu_frac > hbm_frac else "hbm",
+            "achieved": alg_flops / t_launch / 1e9 if alu_frac > hbm_frac else alg_bytes / t_launch / 1e9,
+            "peak": FP64_INSTR_PEAK / 1e9 if alu_frac > hbm_frac else hbm_peak,
+            "unit": "GFLOP/s (FP64)" if alu_frac > hbm_frac else "GB/s",
+            "frac": max(alu_frac, hbm_frac), "traffic": None,
+            "hbm_frac": hbm_frac, "fp64_frac": alu_frac, "launch_ms": ms_b / args.steps, "launches_per_step": 1}
+    line = {"metric": METRIC, "value": value_b, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_b / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic (64 perturbed jet members)",
+            "config": {"workload": "ensemble-32xR2B4+32xR2B5-L60-mixed", "members": len(spec), "cells": cells,
+                       "levels": N, "nsub": nsub, "dt": {"R2B4": E["dt_b4"], "R2B5": E["dt_b5"]},
+                       "l2": "inputs larger than L2 (64 member states)"},
+            "gpu_launches": 2 * args.steps, "roofline": roof, "clocks": clk,
+            "sequential": {"value": value_s, "unit": UNIT, "ms_per_step": ms_s / args.steps,
+                           "gpu_launches_per_step": launches_seq},
+            "batched_speedup_vs_sequential": value_b / value_s}
     print(json.dumps(line), flush=True)
 
 
@@ -354,6 +485,8 @@ def main():
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     world = int(os.environ.get("WORLD_SIZE", "1"))
+    if wl is None and args.impl == "reference":
+        wl = WL.Workload("ensemble member R2B5-L60", 5, 60, 3, 3, -1.0, 180.0, 5, 1, 1)
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
@@ -364,7 +497,10 @@ def main():
         import torch.distributed as td
         torch.cuda.set_device(local_rank)
         td.init_process_group("nccl")
-    run_gpu(args, wl, rank, world, local_rank)
+    if wl is None:
+        run_ensemble(args, rank, world, local_rank)
+    else:
+        run_gpu(args, wl, rank, world, local_rank)
     if world > 1:
         import torch.distributed as td
         td.destroy_process_group()
