@@ -236,9 +236,16 @@ int icon_state_step_kernels(icon_state* state, double dt, int nsubsteps, int* ou
 int icon_dycore_step_profile(icon_state* state, double dt, int nsubsteps, double* ms_per_kind,
                              int* launches_per_kind);
 
+/* Self-test of internal device helpers that replace hardware operations: the
+ * FP32 <-> FP64 conversions done on the integer pipe are compared bit for bit with
+ * the hardware conversions on n random inputs each (finite normals, zeros, exact
+ * halfway cases). *failures receives the number of mismatches (0 expected).
+ * Allocates 4 bytes with cudaMalloc (not the registered allocator). Waits. */
+int icon_selftest(long long n, unsigned* failures);
+
 /* Name of kernel kind i (0 <= i < ICON_KIND_COUNT), or NULL. Mixed-precision
  * stencil kinds: 10 vertex, 11 edge diagnostics, 12 cell kinetic energy,
- * 13 edge tendency, 16 diffusion vertex/divergence. */
+ * 13 edge tendency, 15 column-input gather, 16 diffusion vertex/divergence. */
 const char* icon_kernel_kind_name(int kind);
 #define ICON_KIND_COUNT 24
 

@@ -66,6 +66,7 @@ def _load():
         "icon_state_step_kernels": (I, [P, D, I, ctypes.POINTER(I)]),
         "icon_dycore_step_profile": (I, [P, D, I, ctypes.POINTER(D), ctypes.POINTER(I)]),
         "icon_kernel_kind_name": (ctypes.c_char_p, [I]),
+        "icon_selftest": (I, [ctypes.c_longlong, ctypes.POINTER(ctypes.c_uint)]),
         "icon_global_mass_noalloc": (I, [P, P, I, ctypes.POINTER(D)]),
         "icon_state_copy_field": (I, [P, I, P, S]), "icon_state_set_field": (I, [P, I, P, S]),
         "icon_state_precision": (I, [P, ctypes.POINTER(I)]), "icon_state_free": (None, [P]),
@@ -205,6 +206,12 @@ def icon_dycore_step_profile(state, dt, nsubsteps, ms=None, launches=None):
     return ms, launches
 
 
+def icon_selftest(n):
+    f = ctypes.c_uint()
+    _check(_lib.icon_selftest(n, ctypes.byref(f)))
+    return f.value
+
+
 def icon_kernel_kind_name(kind):
     n = _lib.icon_kernel_kind_name(kind)
     return n.decode() if n else None
@@ -257,7 +264,8 @@ def icon_ensemble_step(ens, dts, nsubsteps, nsteps):
 
 ICON_ENS_SPIN_LIMIT, ICON_ENS_TEST_SKIP_BARRIER = 1, 2
 # mixed-precision stencil kinds that take a tile
-KIND_MX_VERTEX, KIND_MX_EDGE, KIND_MX_CELL_KE, KIND_MX_EDGE_TEND, KIND_MX_DIFF_VERTEX = 10, 11, 12, 13, 16
+KIND_MX_VERTEX, KIND_MX_EDGE, KIND_MX_CELL_KE, KIND_MX_EDGE_TEND, KIND_MX_COLUMN_PREP, KIND_MX_DIFF_VERTEX = \
+    10, 11, 12, 13, 15, 16
 
 
 def icon_ensemble_set_option(ens, option, value):

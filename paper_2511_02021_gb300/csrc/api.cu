@@ -204,6 +204,20 @@ int alloc_state(icon_state* st, int precision) {
     s.zeta32 = A.get_n<float>(V); s.wv32 = A.get_n<float>(V);
     s.uvx32 = A.get_n<float>(V); s.uvy32 = A.get_n<float>(V); s.uvz32 = A.get_n<float>(V);
     s.colconst = A.get_n<double>(8 * (size_t)ld);
+    s.exref32 = A.get_n<float>(ld);
+    // stored frozen column parts: 10 FP64 fields per half level and 2 FP32 per level;
+    // kept when they take at most a quarter of the device memory
+    const size_t fac_bytes = (size_t)nc * (12 + 5) * (ld0 + 1) * 8;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) total_b = 0;
+    if (fac_bytes <= total_b / 4) {
+      s.fac64 = A.get_n<double>((size_t)nc * 12 * (ld0 + 1));
+      s.hdr = A.get_n<double>((size_t)nc * (ld0 + 1));
+      s.hdt = A.get_n<double>((size_t)nc * (ld0 + 1));
+      s.hdw = A.get_n<double>((size_t)nc * (ld0 + 1));
+      s.hdg = A.get_n<double>((size_t)nc * (ld0 + 1));
+      s.dps = A.get_n<double>((size_t)nc * (ld0 + 1));
+    }
   }
   if (A.failed) {
     set_error("out of device memory allocating the state");
@@ -548,6 +562,11 @@ int icon_dycore_step_profile(icon_state* st, double dt, int nsubsteps, double* m
   for (cudaEvent_t ev : prof.ev) cudaEventDestroy(ev);
   if (rc != ICON_OK) return rc;
   return sync_status(st, stream);
+}
+
+int icon_selftest(long long n, unsigned* failures) {
+  if (!failures || n < 1) { set_error("icon_selftest: bad argument"); return ICON_EINVAL; }
+  return selftest_conversions(n, failures);
 }
 
 const char* icon_kernel_kind_name(int kind) {

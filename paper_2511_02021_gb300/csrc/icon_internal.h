@@ -141,6 +141,12 @@ struct StateDev {
   double *ex_ref = nullptr;           // [ld] reference Exner profile
   // per-level constants of the column solve for the current dtau (mixed mode)
   double* colconst = nullptr;
+  // frozen parts of the column system shared by predictor and corrector (mixed mode;
+  // NULL when they would not fit, then both stages compute them)
+  double* fac64 = nullptr;
+  double *hdr = nullptr, *hdt = nullptr, *hdw = nullptr, *hdg = nullptr;  // gathered column inputs, level-major
+  double* dps = nullptr;      // Thomas scratch, level-major
+  float* exref32 = nullptr;   // FP32 copy of the reference Exner profile
   // mass reduction partials and the device status word
   double *mass_part = nullptr;
   int mass_nblk = 0;
@@ -182,6 +188,7 @@ struct EnsembleDev {
 int ensemble_prepare(EnsembleDev& E, icon_state* const* members, int n, const double* dts, int nsub);
 int ensemble_launch(EnsembleDev& E, cudaStream_t st);
 void autotune_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream);
+int selftest_conversions(int64_t n, unsigned* host_fails);
 }  // namespace icon
 
 namespace icon {

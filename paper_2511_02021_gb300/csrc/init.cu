@@ -311,6 +311,7 @@ int init_state_device(icon_state* st, uint64_t seed, int case_id, const icon_cas
     cd.bz = std::sin(lat);
   }
   k_exner_ref<<<1, 1, 0, stream>>>(v.N, v.d_z_f, v.d_dzh, v.d_wu, v.d_wl, s.ex_ref);
+  if (s.exref32) k_to_f32<<<1, 256, 0, stream>>>(s.ex_ref, s.exref32, v.ld);
   if (s.precision == ICON_FP64) {
     k_init_cells<<<blocks_for(g.nc, 128), 128, 0, stream>>>(cd, g.nc, g.x_c, v.d_z_f, v.d_dzh, v.d_wu, v.d_wl,
                                                             s.rho, s.thv, s.ex, s.w);

@@ -62,7 +62,8 @@ def test_results_do_not_depend_on_tiles(gpu):
     C = gpu
     N = 40
     grid = C.icon_grid_build(2, 3, N)
-    kinds = [C.KIND_MX_VERTEX, C.KIND_MX_EDGE, C.KIND_MX_CELL_KE, C.KIND_MX_EDGE_TEND, C.KIND_MX_DIFF_VERTEX]
+    kinds = [C.KIND_MX_VERTEX, C.KIND_MX_EDGE, C.KIND_MX_CELL_KE, C.KIND_MX_EDGE_TEND, C.KIND_MX_COLUMN_PREP,
+             C.KIND_MX_DIFF_VERTEX]
     out = []
     try:
         for lanes, block in ((32, 128), (16, 512), (0, 0)):

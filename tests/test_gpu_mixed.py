@@ -95,3 +95,9 @@ def test_mixed_vs_fp64_gpu_larger(gpu):
         assert rel_l2(b[f], a[f]) <= thermo_bound_mixed(180.0, 5, 2, d_min(5)), f
     assert abs(bm1 - bm0) / bm0 <= 2e-13
     assert am0 == bm0 or abs(am0 / bm0 - 1) < 1e-15
+
+
+def test_integer_pipe_conversions_match_hardware(gpu):
+    """The FP32<->FP64 conversions built from the IEEE-754 encodings agree bit for bit
+    with the hardware conversions on 2^22 random finite inputs and halfway cases."""
+    assert gpu.icon_selftest(1 << 22) == 0
