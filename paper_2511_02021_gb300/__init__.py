@@ -15,10 +15,16 @@ def use_torch_allocator(device=0):
     stream = torch.cuda.current_stream(device)
 
     def alloc(nbytes):
-        return torch.cuda.caching_allocator_alloc(nbytes, device, stream)
+        try:
+            return torch.cuda.caching_allocator_alloc(nbytes, device, stream)
+        except Exception:          # out of memory: the library sees NULL and reports ICON_ENOMEM
+            return 0
 
     def dealloc(ptr):
-        torch.cuda.caching_allocator_delete(ptr)
+        try:
+            torch.cuda.caching_allocator_delete(ptr)
+        except Exception:
+            pass
 
     capi.icon_set_allocator(alloc, dealloc)
 

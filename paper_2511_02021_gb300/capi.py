@@ -106,8 +106,22 @@ def icon_set_allocator(alloc, dealloc):
     if alloc is None:
         _check(_lib.icon_set_allocator(None, None, None))
         return
-    a = ALLOC_FN(lambda n, ctx: alloc(n))
-    d = DEALLOC_FN(lambda p, ctx: dealloc(p))
+    def _alloc(n, ctx):
+        # an exception escaping a ctypes callback leaves its return value undefined:
+        # every failure must come back as NULL
+        try:
+            return alloc(n) or None
+        except Exception:
+            return None
+
+    def _dealloc(p, ctx):
+        try:
+            dealloc(p)
+        except Exception:
+            pass
+
+    a = ALLOC_FN(_alloc)
+    d = DEALLOC_FN(_dealloc)
     _keep.append((a, d))
     _check(_lib.icon_set_allocator(ctypes.cast(a, ctypes.c_void_p), ctypes.cast(d, ctypes.c_void_p), None))
 

@@ -73,6 +73,15 @@ void* DeviceArena::get(size_t bytes) {
   void* p = nullptr;
   if (al.alloc) {
     p = al.alloc(bytes, al.ctx);
+    if (p) {
+      // never use a pointer that is not device memory (a failing allocator callback
+      // must not make kernels write through garbage)
+      cudaPointerAttributes attr;
+      if (cudaPointerGetAttributes(&attr, p) != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        p = nullptr;
+      }
+    }
   } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
     cudaGetLastError();
     p = nullptr;
@@ -195,14 +204,16 @@ int alloc_state(icon_state* st, int precision) {
     s.thv = A.get_n<double>(nc * ld0); s.ex = A.get_n<double>(nc * ld0);
     s.wflx = A.get_n<double>(nc * (ld0 + 1));
     s.vn32 = A.get_n<float>(E); s.vn32_s = A.get_n<float>(E); s.Avn0_32 = A.get_n<float>(E);
-    s.vt32 = A.get_n<float>(E); s.Ke32 = A.get_n<float>(E); s.F32 = A.get_n<float>(E);
+    s.vt32 = A.get_n<float>(E); s.F32 = A.get_n<float>(E);
     s.G32 = A.get_n<float>(E); s.ae32 = A.get_n<float>(E);
     s.rho32 = A.get_n<float>(C); s.thv32 = A.get_n<float>(C); s.exp32 = A.get_n<float>(C); s.w32 = A.get_n<float>(C);
     s.rho32_s = A.get_n<float>(C); s.thv32_s = A.get_n<float>(C); s.exp32_s = A.get_n<float>(C);
     s.w32_s = A.get_n<float>(C); s.Kc32 = A.get_n<float>(C);
     s.Aw0_32 = A.get_n<float>(nc * (ld0 + 1));
     s.zeta32 = A.get_n<float>(V); s.wv32 = A.get_n<float>(V);
-    s.uvx32 = A.get_n<float>(V); s.uvy32 = A.get_n<float>(V); s.uvz32 = A.get_n<float>(V);
+    // the diffusion's vertex vectors reuse buffers that are dead during diffusion
+    // (vertex rows Nv*ld fit in cell rows Nc*ld)
+    s.uvx32 = s.wv32; s.uvy32 = s.rho32_s; s.uvz32 = s.thv32_s;
     s.colconst = A.get_n<double>(8 * (size_t)ld);
     s.exref32 = A.get_n<float>(ld);
     // stored frozen column parts: 10 FP64 fields per half level and 2 FP32 per level;

@@ -91,10 +91,10 @@ __device__ inline void mx_vertex_item(const MxGeo& G, const float* __restrict__ 
   }
 }
 
-// O4 vt and K_e
+// O4 vt
 template <int LPE>
 __device__ inline void mx_edge_diag_item(const MxGeo& G, const float* __restrict__ vn, float* __restrict__ vt,
-                                         float* __restrict__ Ke, int64_t e, int lane) {
+                                         int64_t e, int lane) {
   const int ld = G.ld;
   int64_t S[5];
   float W[5];
@@ -105,16 +105,14 @@ __device__ inline void mx_edge_diag_item(const MxGeo& G, const float* __restrict
   for (int k = lane; k < G.N; k += LPE) {
     float acc = 0.f;
     for (int j = 0; j < 5; ++j) acc += W[j] * vn[S[j] + k];
-    const float v0 = vn[e * ld + k];
     vt[e * ld + k] = acc;
-    Ke[e * ld + k] = 0.5f * (v0 * v0 + acc * acc);
   }
 }
 
-// O5 K_c
+// O5 K_c = sum_e kappa_ce (vn_e^2 + vt_e^2)/2
 template <int LPE>
-__device__ inline void mx_cell_ke_item(const MxGeo& G, const float* __restrict__ Ke, float* __restrict__ Kc, int64_t c,
-                                       int lane) {
+__device__ inline void mx_cell_ke_item(const MxGeo& G, const float* __restrict__ vn, const float* __restrict__ vt,
+                                       float* __restrict__ Kc, int64_t c, int lane) {
   const int ld = G.ld;
   int64_t E[3];
   float kw[3];
@@ -122,7 +120,14 @@ __device__ inline void mx_cell_ke_item(const MxGeo& G, const float* __restrict__
     E[s] = (int64_t)G.c2e[3 * c + s] * ld;
     kw[s] = G.kin_w32[3 * c + s];
   }
-  for (int k = lane; k < G.N; k += LPE) Kc[c * ld + k] = kw[0] * Ke[E[0] + k] + kw[1] * Ke[E[1] + k] + kw[2] * Ke[E[2] + k];
+  for (int k = lane; k < G.N; k += LPE) {
+    float acc = 0.f;
+    for (int s = 0; s < 3; ++s) {
+      const float a = vn[E[s] + k], b = vt[E[s] + k];
+      acc += kw[s] * (0.5f * (a * a + b * b));
+    }
+    Kc[c * ld + k] = acc;
+  }
 }
 
 struct MxEdgeArgs {
@@ -692,14 +697,14 @@ __global__ void __launch_bounds__(512) k_mx_vertex(MxGeo G, const float* vn, con
   mx_vertex_item<LPE>(G, vn, w, zeta, w_v, item, lane);
 }
 template <int LPE>
-__global__ void __launch_bounds__(512) k_mx_edge_diag(MxGeo G, const float* vn, float* vt, float* Ke) {
+__global__ void __launch_bounds__(512) k_mx_edge_diag(MxGeo G, const float* vn, float* vt) {
   ITEM_PROLOGUE(LPE, G.ne)
-  mx_edge_diag_item<LPE>(G, vn, vt, Ke, item, lane);
+  mx_edge_diag_item<LPE>(G, vn, vt, item, lane);
 }
 template <int LPE>
-__global__ void __launch_bounds__(512) k_mx_cell_ke(MxGeo G, const float* Ke, float* Kc) {
+__global__ void __launch_bounds__(512) k_mx_cell_ke(MxGeo G, const float* vn, const float* vt, float* Kc) {
   ITEM_PROLOGUE(LPE, G.nc)
-  mx_cell_ke_item<LPE>(G, Ke, Kc, item, lane);
+  mx_cell_ke_item<LPE>(G, vn, vt, Kc, item, lane);
 }
 template <int LPE>
 __global__ void __launch_bounds__(512) k_mx_edge_tend(MxGeo G, MxEdgeArgs a) {
@@ -815,12 +820,12 @@ void launch_kind(int kind, const TileChoice& t, const MxGeo& G, StateDev& s, con
       else k_mx_vertex<32><<<item_blocks(G.nv, 32, B), B, 0, st>>>(G, ea.vn, ea.w, s.zeta32, s.wv32);
       break;
     case K_MX_EDGE:
-      if (l16) k_mx_edge_diag<16><<<item_blocks(G.ne, 16, B), B, 0, st>>>(G, ea.vn, s.vt32, s.Ke32);
-      else k_mx_edge_diag<32><<<item_blocks(G.ne, 32, B), B, 0, st>>>(G, ea.vn, s.vt32, s.Ke32);
+      if (l16) k_mx_edge_diag<16><<<item_blocks(G.ne, 16, B), B, 0, st>>>(G, ea.vn, s.vt32);
+      else k_mx_edge_diag<32><<<item_blocks(G.ne, 32, B), B, 0, st>>>(G, ea.vn, s.vt32);
       break;
     case K_MX_CELL_KE:
-      if (l16) k_mx_cell_ke<16><<<item_blocks(G.nc, 16, B), B, 0, st>>>(G, s.Ke32, s.Kc32);
-      else k_mx_cell_ke<32><<<item_blocks(G.nc, 32, B), B, 0, st>>>(G, s.Ke32, s.Kc32);
+      if (l16) k_mx_cell_ke<16><<<item_blocks(G.nc, 16, B), B, 0, st>>>(G, ea.vn, s.vt32, s.Kc32);
+      else k_mx_cell_ke<32><<<item_blocks(G.nc, 32, B), B, 0, st>>>(G, ea.vn, s.vt32, s.Kc32);
       break;
     case K_MX_EDGE_TEND:
       if (l16) k_mx_edge_tend<16><<<item_blocks(G.ne, 16, B), B, 0, st>>>(G, ea);
@@ -841,10 +846,10 @@ void launch_kind(int kind, const TileChoice& t, const MxGeo& G, StateDev& s, con
     case K_MX_DIFF_EDGE:
       if (l16)
         k_mx_diff_edge<16><<<item_blocks(G.ne, 16, B), B, 0, st>>>(G, s.vn32, s.uvx32, s.uvy32, s.uvz32, s.zeta32,
-                                                                s.Kc32, s.thv32, s.Ke32, dt);
+                                                                s.Kc32, s.thv32, s.vt32, dt);
       else
         k_mx_diff_edge<32><<<item_blocks(G.ne, 32, B), B, 0, st>>>(G, s.vn32, s.uvx32, s.uvy32, s.uvz32, s.zeta32,
-                                                                s.Kc32, s.thv32, s.Ke32, dt);
+                                                                s.Kc32, s.thv32, s.vt32, dt);
       break;
     default: break;
   }
@@ -997,7 +1002,7 @@ void enqueue_step_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream
   launch_kind(K_MX_DIFF_EDGE, tile(K_MX_DIFF_EDGE), G, s, ea, ca, (float)dt, stream);
   prof_end(stream);
   prof_begin(stream, K_MX_DIFF_THETA);
-  k_mx_diff_theta<<<blocks_for(nc, 128), 128, 0, stream>>>(G, s.Ke32, s.thv, s.ex, s.thv32, s.exp32, (float)dt);
+  k_mx_diff_theta<<<blocks_for(nc, 128), 128, 0, stream>>>(G, s.vt32, s.thv, s.ex, s.thv32, s.exp32, (float)dt);
   prof_end(stream);
 }
 
@@ -1068,7 +1073,7 @@ struct MemberDev {
   double* wflx;
   double* colconst;
   const double* ex_ref;
-  float *vn32, *uvx32, *uvy32, *uvz32, *zeta32, *Kc32, *thv32, *Ke32, *exp32, *wv32, *vt32;
+  float *vn32, *uvx32, *uvy32, *uvz32, *zeta32, *Kc32, *thv32, *exp32, *wv32, *vt32;
   double *thv, *ex;
   double dtau, dt;
   int64_t off_v, off_e, off_c;  // this member's first item in each work list
@@ -1171,13 +1176,13 @@ __global__ void __launch_bounds__(128) k_ensemble_step(EnsArgs A) {
       for (int64_t i = gwarp; i < A.tot_e; i += nwarps) {
         const int m = find_member(s_off_e, A.nm, i);
         const MemberDev& M = A.m[m];
-        mx_edge_diag_item<32>(M.G, M.ea[stage].vn, M.vt32, M.Ke32, i - M.off_e, lane);
+        mx_edge_diag_item<32>(M.G, M.ea[stage].vn, M.vt32, i - M.off_e, lane);
       }
       if (!sync()) return;
       for (int64_t i = gwarp; i < A.tot_c; i += nwarps) {
         const int m = find_member(s_off_c, A.nm, i);
         const MemberDev& M = A.m[m];
-        mx_cell_ke_item<32>(M.G, M.Ke32, M.Kc32, i - M.off_c, lane);
+        mx_cell_ke_item<32>(M.G, M.ea[stage].vn, M.vt32, M.Kc32, i - M.off_c, lane);
       }
       if (!sync()) return;
       for (int64_t i = gwarp; i < A.tot_e; i += nwarps) {
@@ -1220,14 +1225,14 @@ __global__ void __launch_bounds__(128) k_ensemble_step(EnsArgs A) {
   for (int64_t i = gwarp; i < A.tot_e; i += nwarps) {
     const int m = find_member(s_off_e, A.nm, i);
     const MemberDev& M = A.m[m];
-    mx_diff_edge_item<32>(M.G, M.vn32, M.uvx32, M.uvy32, M.uvz32, M.zeta32, M.Kc32, M.thv32, M.Ke32, (float)M.dt,
+    mx_diff_edge_item<32>(M.G, M.vn32, M.uvx32, M.uvy32, M.uvz32, M.zeta32, M.Kc32, M.thv32, M.vt32, (float)M.dt,
                           i - M.off_e, lane);
   }
   if (!sync()) return;
   for (int64_t i = gtid; i < A.tot_c; i += nthreads) {
     const int m = find_member(s_off_c, A.nm, i);
     const MemberDev& M = A.m[m];
-    mx_diff_theta_item(M.G, M.Ke32, M.thv, M.ex, M.thv32, M.exp32, (float)M.dt, i - M.off_c);
+    mx_diff_theta_item(M.G, M.vt32, M.thv, M.ex, M.thv32, M.exp32, (float)M.dt, i - M.off_c);
   }
 }
 
@@ -1285,7 +1290,7 @@ int ensemble_prepare(EnsembleDev& E, icon_state* const* members, int n, const do
     }
     M.mflx = s.mflx; M.wflx = s.wflx; M.colconst = s.colconst; M.ex_ref = s.ex_ref;
     M.vn32 = s.vn32; M.uvx32 = s.uvx32; M.uvy32 = s.uvy32; M.uvz32 = s.uvz32; M.zeta32 = s.zeta32;
-    M.Kc32 = s.Kc32; M.thv32 = s.thv32; M.Ke32 = s.Ke32; M.exp32 = s.exp32; M.thv = s.thv; M.ex = s.ex;
+    M.Kc32 = s.Kc32; M.thv32 = s.thv32; M.exp32 = s.exp32; M.thv = s.thv; M.ex = s.ex;
     M.wv32 = s.wv32; M.vt32 = s.vt32;
     M.off_v = ov; M.off_e = oe; M.off_c = oc;
     ov += M.G.nv; oe += M.G.ne; oc += M.G.nc;

@@ -203,8 +203,8 @@ void enqueue_step_fp64(icon_state* st, double dt, int nsub, cudaStream_t stream)
 // dycore32.cu
 void enqueue_step_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream);
 // mixed-mode state from FP64 fields in [entity][ld] layout (init.cu)
-void mixed_from_fp64(icon_state* st, const double* vn, const double* w, const double* rho, const double* thv,
-                     const double* ex, cudaStream_t stream);
+void mixed_cells_from_fp64(icon_state* st, int64_t c0, int64_t n, const double* w, const double* rho,
+                           const double* thv, const double* ex, cudaStream_t stream);
 void mixed_refresh_shadows(icon_state* st, cudaStream_t stream);
 // mass
 void enqueue_mass(const icon_state* st, double* d_out, cudaStream_t stream);

@@ -121,17 +121,19 @@ __device__ void analytic(const CaseDev& cd, double x, double y, double zu, doubl
 }
 
 // one thread per column: theta_v, discrete hydrostatic Exner, noise, rho
-__global__ void k_init_cells(CaseDev cd, int64_t nc, const double* __restrict__ x_c, const double* __restrict__ z_f,
-                             const double* __restrict__ dzh, const double* __restrict__ wu,
-                             const double* __restrict__ wl, double* __restrict__ rho, double* __restrict__ thv,
-                             double* __restrict__ ex, double* __restrict__ w) {
-  int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (c >= nc) return;
+// cells c0 .. c0+n-1; outputs at rows (c - c0) of the [n][ld] arrays
+__global__ void k_init_cells(CaseDev cd, int64_t c0, int64_t n, const double* __restrict__ x_c,
+                             const double* __restrict__ z_f, const double* __restrict__ dzh,
+                             const double* __restrict__ wu, const double* __restrict__ wl, double* __restrict__ rho,
+                             double* __restrict__ thv, double* __restrict__ ex, double* __restrict__ w) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int64_t c = c0 + t;
   const int N = cd.N, ld = cd.ld;
   double x = x_c[3 * c], y = x_c[3 * c + 1], z = x_c[3 * c + 2];
-  double* th = thv + c * ld;
-  double* pe = ex + c * ld;
-  double* rr = rho + c * ld;
+  double* th = thv + t * ld;
+  double* pe = ex + t * ld;
+  double* rr = rho + t * ld;
   const double kap = kRd / kCpd;
   double exan_bottom = 0.0;
   for (int k = 0; k < N; ++k) {
@@ -154,17 +156,18 @@ __global__ void k_init_cells(CaseDev cd, int64_t nc, const double* __restrict__ 
   }
   for (int k = 0; k < N; ++k) rr[k] = kP0 * pow(pe[k], kCvd / kRd) / (kRd * th[k]);
   for (int k = N; k < ld; ++k) { th[k] = 0.0; pe[k] = 0.0; rr[k] = 0.0; }
-  for (int h = 0; h < ld; ++h) w[c * ld + h] = 0.0;
+  for (int h = 0; h < ld; ++h) w[t * ld + h] = 0.0;
 }
 
 // one thread per (edge, level): vn = u . n with u = u_lambda e_lambda
-__global__ void k_init_edges(CaseDev cd, int64_t ne, const double* __restrict__ x_e, const double* __restrict__ n_e,
-                             const double* __restrict__ z_f, double* __restrict__ vn) {
+// edges e0 .. e0+n-1; output rows (e - e0)
+__global__ void k_init_edges(CaseDev cd, int64_t e0, int64_t n, const double* __restrict__ x_e,
+                             const double* __restrict__ n_e, const double* __restrict__ z_f, double* __restrict__ vn) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int ld = cd.ld;
-  if (t >= ne * ld) return;
-  int64_t e = t / ld;
-  int k = (int)(t % ld);
+  if (t >= n * ld) return;
+  const int64_t e = e0 + t / ld;
+  const int k = (int)(t % ld);
   if (k >= cd.N) { vn[t] = 0.0; return; }
   double x = x_e[3 * e], y = x_e[3 * e + 1], z = x_e[3 * e + 2];
   double lnp, T, u;
@@ -204,33 +207,35 @@ double jet_B() {
 
 // FP64 fields in [entity][ld] layout -> mixed-mode storage: FP64 level-major
 // prognostics, FP32 vn and FP32 shadows of S^n
-__global__ void k_mixed_cells(int64_t nc, int N, int ld, const double* __restrict__ w, const double* __restrict__ rho,
-                              const double* __restrict__ thv, const double* __restrict__ ex,
-                              const double* __restrict__ ex_ref, double* __restrict__ w_lm,
-                              double* __restrict__ rho_lm, double* __restrict__ thv_lm, double* __restrict__ ex_lm,
-                              float* __restrict__ w32, float* __restrict__ rho32, float* __restrict__ thv32,
-                              float* __restrict__ exp32) {
+// rows 0..n-1 of the [n][ld] FP64 arrays hold cells c0..c0+n-1
+__global__ void k_mixed_cells(int64_t nc, int64_t c0, int64_t n, int N, int ld, const double* __restrict__ w,
+                              const double* __restrict__ rho, const double* __restrict__ thv,
+                              const double* __restrict__ ex, const double* __restrict__ ex_ref,
+                              double* __restrict__ w_lm, double* __restrict__ rho_lm, double* __restrict__ thv_lm,
+                              double* __restrict__ ex_lm, float* __restrict__ w32, float* __restrict__ rho32,
+                              float* __restrict__ thv32, float* __restrict__ exp32) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= nc * ld) return;
-  const int64_t c = t / ld;
+  if (t >= n * ld) return;
+  const int64_t c = c0 + t / ld;
   const int k = (int)(t % ld);
+  const int64_t g = c * ld + k;
   if (k <= N) {
     w_lm[(int64_t)k * nc + c] = w[t];
-    w32[t] = (float)w[t];
+    w32[g] = (float)w[t];
   } else {
-    w32[t] = 0.0f;
+    w32[g] = 0.0f;
   }
   if (k < N) {
     rho_lm[(int64_t)k * nc + c] = rho[t];
     thv_lm[(int64_t)k * nc + c] = thv[t];
     ex_lm[(int64_t)k * nc + c] = ex[t];
-    rho32[t] = (float)rho[t];
-    thv32[t] = (float)thv[t];
-    exp32[t] = (float)(ex[t] - ex_ref[k]);
+    rho32[g] = (float)rho[t];
+    thv32[g] = (float)thv[t];
+    exp32[g] = (float)(ex[t] - ex_ref[k]);
   } else {
-    rho32[t] = 0.0f;
-    thv32[t] = 0.0f;
-    exp32[t] = 0.0f;
+    rho32[g] = 0.0f;
+    thv32[g] = 0.0f;
+    exp32[g] = 0.0f;
   }
 }
 
@@ -259,15 +264,14 @@ __global__ void k_mixed_shadows(int64_t nc, int N, int ld, const double* __restr
 
 }  // namespace
 
-void mixed_from_fp64(icon_state* st, const double* vn, const double* w, const double* rho, const double* thv,
-                     const double* ex, cudaStream_t stream) {
+void mixed_cells_from_fp64(icon_state* st, int64_t c0, int64_t n, const double* w, const double* rho,
+                           const double* thv, const double* ex, cudaStream_t stream) {
   const GridDev& g = st->grid->g;
   const Vertical& v = st->grid->vert;
   StateDev& s = st->s;
-  const int64_t ncl = g.nc * v.ld, nel = g.ne * v.ld;
-  k_to_f32<<<blocks_for(nel, 256), 256, 0, stream>>>(vn, s.vn32, nel);
-  k_mixed_cells<<<blocks_for(ncl, 256), 256, 0, stream>>>(g.nc, v.N, v.ld, w, rho, thv, ex, s.ex_ref, s.w, s.rho,
-                                                          s.thv, s.ex, s.w32, s.rho32, s.thv32, s.exp32);
+  k_mixed_cells<<<blocks_for(n * v.ld, 256), 256, 0, stream>>>(g.nc, c0, n, v.N, v.ld, w, rho, thv, ex, s.ex_ref,
+                                                               s.w, s.rho, s.thv, s.ex, s.w32, s.rho32, s.thv32,
+                                                               s.exp32);
 }
 
 void mixed_refresh_shadows(icon_state* st, cudaStream_t stream) {
@@ -313,16 +317,19 @@ int init_state_device(icon_state* st, uint64_t seed, int case_id, const icon_cas
   k_exner_ref<<<1, 1, 0, stream>>>(v.N, v.d_z_f, v.d_dzh, v.d_wu, v.d_wl, s.ex_ref);
   if (s.exref32) k_to_f32<<<1, 256, 0, stream>>>(s.ex_ref, s.exref32, v.ld);
   if (s.precision == ICON_FP64) {
-    k_init_cells<<<blocks_for(g.nc, 128), 128, 0, stream>>>(cd, g.nc, g.x_c, v.d_z_f, v.d_dzh, v.d_wu, v.d_wl,
+    k_init_cells<<<blocks_for(g.nc, 128), 128, 0, stream>>>(cd, 0, g.nc, g.x_c, v.d_z_f, v.d_dzh, v.d_wu, v.d_wl,
                                                             s.rho, s.thv, s.ex, s.w);
-    k_init_edges<<<blocks_for(g.ne * v.ld, 256), 256, 0, stream>>>(cd, g.ne, g.x_e, g.n_e, v.d_z_f, s.vn);
+    k_init_edges<<<blocks_for(g.ne * v.ld, 256), 256, 0, stream>>>(cd, 0, g.ne, g.x_e, g.n_e, v.d_z_f, s.vn);
     ICON_CUDA(cudaGetLastError());
     return ICON_OK;
   }
-  // mixed: the same FP64 initial state in temporaries, then the mixed-mode storage
+  // mixed: the same FP64 initial state, computed in chunks of at most 2^21 cells
+  // (edges) into bounded temporaries, then converted to the mixed-mode storage
   DeviceArena T;
   T.al = st->arena.al;
-  const size_t C = (size_t)(g.nc * v.ld), E = (size_t)(g.ne * v.ld);
+  const int64_t CH = (int64_t)1 << 21;
+  const int64_t cch = g.nc < CH ? g.nc : CH, ech = g.ne < CH ? g.ne : CH;
+  const size_t C = (size_t)(cch * v.ld), E = (size_t)(ech * v.ld);
   double *rho = T.get_n<double>(C), *thv = T.get_n<double>(C), *ex = T.get_n<double>(C), *w = T.get_n<double>(C);
   double* vn = T.get_n<double>(E);
   if (T.failed) {
@@ -330,10 +337,17 @@ int init_state_device(icon_state* st, uint64_t seed, int case_id, const icon_cas
     set_error("out of device memory for the initial state");
     return ICON_ENOMEM;
   }
-  k_init_cells<<<blocks_for(g.nc, 128), 128, 0, stream>>>(cd, g.nc, g.x_c, v.d_z_f, v.d_dzh, v.d_wu, v.d_wl, rho,
-                                                          thv, ex, w);
-  k_init_edges<<<blocks_for(g.ne * v.ld, 256), 256, 0, stream>>>(cd, g.ne, g.x_e, g.n_e, v.d_z_f, vn);
-  mixed_from_fp64(st, vn, w, rho, thv, ex, stream);
+  for (int64_t c0 = 0; c0 < g.nc; c0 += CH) {
+    const int64_t n = (g.nc - c0) < CH ? (g.nc - c0) : CH;
+    k_init_cells<<<blocks_for(n, 128), 128, 0, stream>>>(cd, c0, n, g.x_c, v.d_z_f, v.d_dzh, v.d_wu, v.d_wl, rho,
+                                                         thv, ex, w);
+    mixed_cells_from_fp64(st, c0, n, w, rho, thv, ex, stream);
+  }
+  for (int64_t e0 = 0; e0 < g.ne; e0 += CH) {
+    const int64_t n = (g.ne - e0) < CH ? (g.ne - e0) : CH;
+    k_init_edges<<<blocks_for(n * v.ld, 256), 256, 0, stream>>>(cd, e0, n, g.x_e, g.n_e, v.d_z_f, vn);
+    k_to_f32<<<blocks_for(n * v.ld, 256), 256, 0, stream>>>(vn, s.vn32 + e0 * v.ld, n * v.ld);
+  }
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   T.release();
