@@ -31,6 +31,11 @@
 // row is a coalesced, aligned segment; one thread per column for the implicit
 // solve. The summation order of every stencil follows the operator definitions
 // (fixed neighbour order), so results do not depend on the launch shape.
+// FP64 division issues about eight FP64-pipe instructions on this GPU, so every
+// division by a geometric or per-level constant is a multiplication by a
+// precomputed reciprocal (area factors folded into the stencil weights); the
+// column keeps the three divisions the method needs per level (pi/Theta, the
+// Thomas pivot, Theta/rho).
 #include "icon_internal.h"
 
 namespace icon {
@@ -42,9 +47,31 @@ struct Geo64 {
   int64_t nc, ne, nv;
   int N, ld;
   const int *c2e, *e2c, *e2v, *v2e, *v2c, *vdeg, *e2vt, *e2q;
-  const double *div_w, *rot_w, *A_c, *A_v, *vt_w, *kin_w, *lsq_w, *d_e, *l_e, *f_e, *L34, *n_e, *t_e, *s_ce;
-  const double *dz, *dzh, *wu, *wl, *dz2, *ray;
+  const double *div_wa, *rot_wa, *inv_Ac, *vt_w, *kin_w, *lsq_w, *inv_de, *inv_le, *l_e, *d_e, *f_e, *inv_L34;
+  const double *n_e, *t_e, *s_ce;
+  const double *wu, *wl, *inv_dz, *inv_dz2;
+  const double* cc;                        // per-level constants for the current dtau
 };
+
+// per-level constants of the column solve for one dtau, [8][ld] (same layout as the
+// mixed path): wu, wl, dtau beta cpd / dzh, (1 - beta) cpd / dzh, 1/(1 + dtau r),
+// dtau beta / dz, dtau (1 - beta) / dz, unused
+enum { C_WU = 0, C_WL, C_CA, C_CX, C_DAMP, C_DTBDZ, C_DT1BDZ, C_COUNT };
+
+__global__ void k_colconst64(int N, int ld, const double* __restrict__ wu, const double* __restrict__ wl,
+                             const double* __restrict__ dzh, const double* __restrict__ dz,
+                             const double* __restrict__ ray, double dtau, double* __restrict__ cc) {
+  for (int i = threadIdx.x; i < ld; i += blockDim.x) {
+    const bool interior = i > 0 && i < N;
+    cc[C_WU * ld + i] = i <= N ? wu[i] : 0.0;
+    cc[C_WL * ld + i] = i <= N ? wl[i] : 0.0;
+    cc[C_CA * ld + i] = interior ? dtau * kBeta * kCpd / dzh[i] : 0.0;
+    cc[C_CX * ld + i] = interior ? (1.0 - kBeta) * kCpd / dzh[i] : 0.0;
+    cc[C_DAMP * ld + i] = i <= N ? 1.0 / (1.0 + dtau * ray[i]) : 1.0;
+    cc[C_DTBDZ * ld + i] = i < N ? dtau * kBeta / dz[i] : 0.0;
+    cc[C_DT1BDZ * ld + i] = i < N ? dtau * (1.0 - kBeta) / dz[i] : 0.0;
+  }
+}
 
 __device__ inline int64_t warp_entity() {
   return (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
@@ -61,20 +88,20 @@ __global__ void __launch_bounds__(256) k_vertex(Geo64 G, const double* __restric
   for (int j = 0; j < 6; ++j) {
     E[j] = (int64_t)G.v2e[6 * v + j] * ld;
     C[j] = (int64_t)G.v2c[6 * v + j] * ld;
-    rw[j] = G.rot_w[6 * v + j];
+    rw[j] = G.rot_wa[6 * v + j];
   }
-  const double Av = G.A_v[v];
   const int deg = G.vdeg[v];
+  const double inv_deg = deg == 6 ? 1.0 / 6.0 : 1.0 / 5.0;
   for (int k = lane; k < G.N; k += 32) {
     double acc = 0.0;
     for (int j = 0; j < 6; ++j) acc += rw[j] * vn[E[j] + k];
-    zeta[v * ld + k] = acc / Av;
+    zeta[v * ld + k] = acc;
   }
   for (int h = lane; h <= G.N; h += 32) {
     double acc = 0.0;
     for (int j = 0; j < 5; ++j) acc += w[C[j] + h];
     acc += (deg == 6) ? w[C[5] + h] : 0.0;
-    w_v[v * ld + h] = acc / (double)deg;
+    w_v[v * ld + h] = acc * inv_deg;
   }
 }
 
@@ -124,7 +151,7 @@ struct EdgeArgs {
   double* vn_out;                          // vn* or vn^{n+1} (may alias vn_base)
   double* Avn0;                            // stored (predictor) or read (corrector)
   double *F, *G, *a_e, *mflx;
-  double dtau, nsub;
+  double dtau, inv_nsub;
   int corrector;
 };
 
@@ -142,7 +169,7 @@ __global__ void __launch_bounds__(256) k_edge_tend(Geo64 G, EdgeArgs a) {
   const int lane = threadIdx.x & 31, ld = G.ld, N = G.N;
   const int64_t c1 = (int64_t)G.e2c[2 * e] * ld, c2 = (int64_t)G.e2c[2 * e + 1] * ld;
   const int64_t v1 = (int64_t)G.e2v[2 * e] * ld, v2 = (int64_t)G.e2v[2 * e + 1] * ld;
-  const double de = G.d_e[e], le = G.l_e[e], fe = G.f_e[e];
+  const double ide = G.inv_de[e], ile = G.inv_le[e], fe = G.f_e[e];
   const double* vn = a.vn + e * ld;
   const double* vt = a.vt + e * ld;
   for (int k = lane; k < N; k += 32) {
@@ -153,9 +180,9 @@ __global__ void __launch_bounds__(256) k_edge_tend(Geo64 G, EdgeArgs a) {
     const double we1 = 0.5 * (a.w[c1 + k + 1] + a.w[c2 + k + 1]);
     const double wbar = 0.5 * (we0 + we1);
     const double zeta_e = 0.5 * (a.zeta[v1 + k] + a.zeta[v2 + k]);
-    const double A = (-(a.Kc[c2 + k] - a.Kc[c1 + k]) / de + (zeta_e + fe) * vt_k) - wbar * (vie0 - vie1) / G.dz[k];
+    const double A = (-(a.Kc[c2 + k] - a.Kc[c1 + k]) * ide + (zeta_e + fe) * vt_k) - wbar * (vie0 - vie1) * G.inv_dz[k];
     const double th_e = 0.5 * (a.thv[c1 + k] + a.thv[c2 + k]);
-    const double pg = (kCpd * th_e) * ((a.ex[c2 + k] - a.ex[c1 + k]) / de);
+    const double pg = (kCpd * th_e) * ((a.ex[c2 + k] - a.ex[c1 + k]) * ide);
     double vnew;
     if (a.corrector) {
       vnew = a.vn_base[e * ld + k] + a.dtau * (0.5 * (a.Avn0[e * ld + k] + A) - pg);
@@ -168,12 +195,12 @@ __global__ void __launch_bounds__(256) k_edge_tend(Geo64 G, EdgeArgs a) {
     const double F = rho_e * vnew;
     a.F[e * ld + k] = F;
     a.G[e * ld + k] = F * th_e;
-    if (a.corrector) a.mflx[e * ld + k] = a.mflx[e * ld + k] + F / a.nsub;
+    if (a.corrector) a.mflx[e * ld + k] = a.mflx[e * ld + k] + F * a.inv_nsub;
   }
   for (int h = lane; h <= N; h += 32) {
     const double vie = to_half(vn, G.wu, G.wl, h, N);
     const double tie = to_half(vt, G.wu, G.wl, h, N);
-    a.a_e[e * ld + h] = vie * (a.w[c2 + h] - a.w[c1 + h]) / de + tie * (a.w_v[v2 + h] - a.w_v[v1 + h]) / le;
+    a.a_e[e * ld + h] = vie * (a.w[c2 + h] - a.w[c1 + h]) * ide + tie * (a.w_v[v2 + h] - a.w_v[v1 + h]) * ile;
   }
 }
 
@@ -185,7 +212,7 @@ struct ColArgs {
   double *rho_o, *thv_o, *ex_o, *w_o;      // S* or S^{n+1} (may alias S^n)
   double* wflx;
   unsigned* status;
-  double dtau, nsub;
+  double dtau, inv_nsub;
   int corrector;
 };
 
@@ -195,14 +222,14 @@ __global__ void __launch_bounds__(64) k_column(Geo64 G, ColArgs a) {
   if (c >= G.nc) return;
   const int N = G.N, ld = G.ld;
   const int64_t o = c * ld;
+  const double* __restrict__ cc = G.cc;
   int64_t E[3];
   double dw[3], kw[3];
   for (int s = 0; s < 3; ++s) {
     E[s] = (int64_t)G.c2e[3 * c + s] * ld;
-    dw[s] = G.div_w[3 * c + s];
+    dw[s] = G.div_wa[3 * c + s];
     kw[s] = G.kin_w[3 * c + s];
   }
-  const double Ac = G.A_c[c];
   const double dtau = a.dtau, rcv = kRd / kCvd;
   double rho_ic[NMAX + 1], M[NMAX + 1], gam[NMAX], Th_x[NMAX], ex_x[NMAX], rho_x[NMAX], cp[NMAX], dp[NMAX];
   // half-level interpolants of S^n
@@ -211,8 +238,9 @@ __global__ void __launch_bounds__(64) k_column(Geo64 G, ColArgs a) {
     if (h == 0) { ri = a.rho[o]; ti = a.thv[o]; }
     else if (h == N) { ri = a.rho[o + N - 1]; ti = a.thv[o + N - 1]; }
     else {
-      ri = G.wu[h] * a.rho[o + h - 1] + G.wl[h] * a.rho[o + h];
-      ti = G.wu[h] * a.thv[o + h - 1] + G.wl[h] * a.thv[o + h];
+      const double wu = cc[C_WU * ld + h], wl = cc[C_WL * ld + h];
+      ri = wu * a.rho[o + h - 1] + wl * a.rho[o + h];
+      ti = wu * a.thv[o + h - 1] + wl * a.thv[o + h];
     }
     rho_ic[h] = ri;
     M[h] = ri * ti;
@@ -221,43 +249,37 @@ __global__ void __launch_bounds__(64) k_column(Geo64 G, ColArgs a) {
   for (int k = 0; k < N; ++k) {
     double Dr = 0.0, Dt = 0.0;
     for (int s = 0; s < 3; ++s) Dr += dw[s] * a.F[E[s] + k];
-    Dr = Dr / Ac;
     for (int s = 0; s < 3; ++s) Dt += dw[s] * a.G[E[s] + k];
-    Dt = Dt / Ac;
     const double rho = a.rho[o + k], thv = a.thv[o + k], ex = a.ex[o + k];
     const double w0 = a.w[o + k], w1 = a.w[o + k + 1];
     const double Th = rho * thv;
-    rho_x[k] = (rho - dtau * Dr) - dtau * (1.0 - kBeta) * (rho_ic[k] * w0 - rho_ic[k + 1] * w1) / G.dz[k];
-    Th_x[k] = (Th - dtau * Dt) - dtau * (1.0 - kBeta) * (M[k] * w0 - M[k + 1] * w1) / G.dz[k];
-    ex_x[k] = ex + rcv * (ex / Th) * (Th_x[k] - Th);
-    gam[k] = rcv * (ex / Th) * dtau * kBeta / G.dz[k];
+    const double dt1 = cc[C_DT1BDZ * ld + k];
+    rho_x[k] = (rho - dtau * Dr) - dt1 * (rho_ic[k] * w0 - rho_ic[k + 1] * w1);
+    Th_x[k] = (Th - dtau * Dt) - dt1 * (M[k] * w0 - M[k + 1] * w1);
+    const double g = rcv * (ex / Th);
+    ex_x[k] = ex + g * (Th_x[k] - Th);
+    gam[k] = g * cc[C_DTBDZ * ld + k];
   }
   // tridiagonal rows at interior half levels h = 1..N-1 (row i = h-1), Thomas forward sweep
   for (int h = 1; h < N; ++h) {
-    // advective tendency of w at half level h (stage state)
     double hadv = 0.0;
     for (int s = 0; s < 3; ++s) hadv += kw[s] * a.a_e[E[s] + h];
     const double ws = a.w_stage[o + h];
-    double Aw = -hadv - ws * (a.w_stage[o + h - 1] - a.w_stage[o + h + 1]) / G.dz2[h];
+    double Aw = -hadv - ws * (a.w_stage[o + h - 1] - a.w_stage[o + h + 1]) * G.inv_dz2[h];
     if (a.corrector) Aw = 0.5 * (a.Aw0[o + h] + Aw);
     else a.Aw0[o + h] = Aw;
-    const double th_ic = G.wu[h] * a.thv[o + h - 1] + G.wl[h] * a.thv[o + h];
+    const double th_ic = cc[C_WU * ld + h] * a.thv[o + h - 1] + cc[C_WL * ld + h] * a.thv[o + h];
     const double exm = a.ex[o + h - 1], exk = a.ex[o + h];
-    const double w_x = a.w[o + h] + dtau * ((Aw - (1.0 - kBeta) * kCpd * th_ic * (exm - exk) / G.dzh[h]) - kGrav);
-    const double aa = dtau * kBeta * kCpd * th_ic / G.dzh[h];
+    const double w_x = a.w[o + h] + dtau * ((Aw - cc[C_CX * ld + h] * th_ic * (exm - exk)) - kGrav);
+    const double aa = cc[C_CA * ld + h] * th_ic;
     const double lower = -aa * gam[h - 1] * M[h - 1];
     const double diag = 1.0 + aa * (gam[h - 1] + gam[h]) * M[h];
     const double upper = -aa * gam[h] * M[h + 1];
     const double rhs = w_x - aa * (ex_x[h - 1] - ex_x[h]);
     const int i = h - 1;
-    if (i == 0) {
-      cp[0] = upper / diag;
-      dp[0] = rhs / diag;
-    } else {
-      const double m = diag - lower * cp[i - 1];
-      cp[i] = upper / m;
-      dp[i] = (rhs - lower * dp[i - 1]) / m;
-    }
+    const double r = 1.0 / (i == 0 ? diag : diag - lower * cp[i - 1]);
+    cp[i] = upper * r;
+    dp[i] = (i == 0 ? rhs : rhs - lower * dp[i - 1]) * r;
   }
   // back substitution (dp becomes the solution), Rayleigh damping
   for (int i = N - 3; i >= 0; --i) dp[i] = dp[i] - cp[i] * dp[i + 1];
@@ -266,17 +288,18 @@ __global__ void __launch_bounds__(64) k_column(Geo64 G, ColArgs a) {
   for (int k = 0; k < N; ++k) {
     const int h1 = k + 1;
     double wn1 = 0.0;
-    if (h1 < N) wn1 = dp[h1 - 1] / (1.0 + dtau * G.ray[h1]);
+    if (h1 < N) wn1 = dp[h1 - 1] * cc[C_DAMP * ld + h1];
     const double q0 = M[k] * wn_prev, q1 = M[k + 1] * wn1;
     const double r0 = rho_ic[k] * wn_prev, r1 = rho_ic[k + 1] * wn1;
-    const double Th_n = Th_x[k] - dtau * kBeta * (q0 - q1) / G.dz[k];
+    const double dtb = cc[C_DTBDZ * ld + k];
+    const double Th_n = Th_x[k] - dtb * (q0 - q1);
     const double ex_n = ex_x[k] - gam[k] * (q0 - q1);
-    const double rho_n = rho_x[k] - dtau * kBeta * (r0 - r1) / G.dz[k];
+    const double rho_n = rho_x[k] - dtb * (r0 - r1);
     const double thv_n = Th_n / rho_n;
     if (a.corrector) {
       // step-mean vertical mass flux at the half level above this full level
       const double wold = a.w[o + k];
-      a.wflx[o + k] = a.wflx[o + k] + rho_ic[k] * (kBeta * wn_prev + (1.0 - kBeta) * wold) / a.nsub;
+      a.wflx[o + k] = a.wflx[o + k] + rho_ic[k] * (kBeta * wn_prev + (1.0 - kBeta) * wold) * a.inv_nsub;
     }
     a.rho_o[o + k] = rho_n;
     a.thv_o[o + k] = thv_n;
@@ -286,10 +309,6 @@ __global__ void __launch_bounds__(64) k_column(Geo64 G, ColArgs a) {
     wn_prev = wn1;
   }
   a.w_o[o + N] = 0.0;
-  if (a.corrector) {
-    const double wold = a.w[o + N];
-    a.wflx[o + N] = a.wflx[o + N] + rho_ic[N] * (kBeta * 0.0 + (1.0 - kBeta) * wold) / a.nsub;
-  }
   if (bad) atomicOr(a.status, 1u);
 }
 
@@ -303,8 +322,7 @@ __global__ void __launch_bounds__(256) k_diff_vertex(Geo64 G, const double* __re
   int64_t E[6];
   for (int j = 0; j < 6; ++j) E[j] = (int64_t)G.v2e[6 * v + j] * ld;
   const double* lw = G.lsq_w + 18 * v;
-  const double* rw = G.rot_w + 6 * v;
-  const double Av = G.A_v[v];
+  const double* rw = G.rot_wa + 6 * v;
   for (int k = lane; k < G.N; k += 32) {
     double x = 0.0, y = 0.0, z = 0.0, r = 0.0;
     for (int j = 0; j < 6; ++j) {
@@ -317,7 +335,7 @@ __global__ void __launch_bounds__(256) k_diff_vertex(Geo64 G, const double* __re
     ux[v * ld + k] = x;
     uy[v * ld + k] = y;
     uz[v * ld + k] = z;
-    zeta[v * ld + k] = r / Av;
+    zeta[v * ld + k] = r;
   }
 }
 
@@ -329,13 +347,12 @@ __global__ void __launch_bounds__(256) k_diff_div(Geo64 G, const double* __restr
   double dw[3];
   for (int s = 0; s < 3; ++s) {
     E[s] = (int64_t)G.c2e[3 * c + s] * ld;
-    dw[s] = G.div_w[3 * c + s];
+    dw[s] = G.div_wa[3 * c + s];
   }
-  const double Ac = G.A_c[c];
   for (int k = lane; k < G.N; k += 32) {
     double acc = 0.0;
     for (int s = 0; s < 3; ++s) acc += dw[s] * vn[E[s] + k];
-    divc[c * ld + k] = acc / Ac;
+    divc[c * ld + k] = acc;
   }
 }
 
@@ -357,20 +374,20 @@ __global__ void __launch_bounds__(256) k_diff_edge(Geo64 G, double* __restrict__
   const int64_t v1 = (int64_t)G.e2v[2 * e] * ld, v2 = (int64_t)G.e2v[2 * e + 1] * ld;
   const double* n = G.n_e + 3 * e;
   const double* t = G.t_e + 3 * e;
-  const double le = G.l_e[e], de = G.d_e[e], L34 = G.L34[e];
+  const double le = G.l_e[e], de = G.d_e[e], i34 = G.inv_L34[e], ile = G.inv_le[e], ide = G.inv_de[e];
   const double cs2ld = (kCsSmag * kCsSmag) * (le * de);
   for (int k = lane; k < G.N; k += 32) {
     const double d34x = ux[Q[3] + k] - ux[Q[2] + k], d34y = uy[Q[3] + k] - uy[Q[2] + k],
                  d34z = uz[Q[3] + k] - uz[Q[2] + k];
     const double d12x = ux[Q[1] + k] - ux[Q[0] + k], d12y = uy[Q[1] + k] - uy[Q[0] + k],
                  d12z = uz[Q[1] + k] - uz[Q[0] + k];
-    const double DT = dot3(d34x, d34y, d34z, n) / L34 - dot3(d12x, d12y, d12z, t) / le;
-    const double DS = dot3(d34x, d34y, d34z, t) / L34 + dot3(d12x, d12y, d12z, n) / le;
+    const double DT = dot3(d34x, d34y, d34z, n) * i34 - dot3(d12x, d12y, d12z, t) * ile;
+    const double DS = dot3(d34x, d34y, d34z, t) * i34 + dot3(d12x, d12y, d12z, n) * ile;
     const double Kh = cs2ld * sqrt(DT * DT + DS * DS);
-    const double lap = (divc[c2 + k] - divc[c1 + k]) / de - (zeta[v2 + k] - zeta[v1 + k]) / le;
+    const double lap = (divc[c2 + k] - divc[c1 + k]) * ide - (zeta[v2 + k] - zeta[v1 + k]) * ile;
     vn[e * ld + k] = vn[e * ld + k] + dt * Kh * lap;
     Kh_out[e * ld + k] = Kh;
-    thflx[e * ld + k] = (le * Kh) * (thv[c2 + k] - thv[c1 + k]) / de;
+    thflx[e * ld + k] = (le * Kh) * (thv[c2 + k] - thv[c1 + k]) * ide;
   }
 }
 
@@ -385,28 +402,29 @@ __global__ void __launch_bounds__(256) k_diff_theta(Geo64 G, const double* __res
     E[s] = (int64_t)G.c2e[3 * c + s] * ld;
     sg[s] = G.s_ce[3 * c + s];
   }
-  const double Ac = G.A_c[c];
+  const double dtA = dt * G.inv_Ac[c];
   for (int k = lane; k < G.N; k += 32) {
     double acc = 0.0;
     for (int s = 0; s < 3; ++s) acc += sg[s] * thflx[E[s] + k];
-    const double dth = dt * acc / Ac;
+    const double dth = dtA * acc;
     const double th = thv[c * ld + k];
     ex[c * ld + k] = ex[c * ld + k] * (1.0 + (kRd / kCvd) * dth / th);
     thv[c * ld + k] = th + dth;
   }
 }
 
-Geo64 make_geo(const icon_grid* grid) {
+Geo64 make_geo(const icon_grid* grid, const double* cc) {
   const GridDev& g = grid->g;
   const Vertical& v = grid->vert;
   Geo64 G;
   G.nc = g.nc; G.ne = g.ne; G.nv = g.nv; G.N = v.N; G.ld = v.ld;
   G.c2e = g.c2e; G.e2c = g.e2c; G.e2v = g.e2v; G.v2e = g.v2e; G.v2c = g.v2c; G.vdeg = g.vdeg;
   G.e2vt = g.e2vt; G.e2q = g.e2q;
-  G.div_w = g.div_w; G.rot_w = g.rot_w; G.A_c = g.A_c; G.A_v = g.A_v; G.vt_w = g.vt_w; G.kin_w = g.kin_w;
-  G.lsq_w = g.lsq_w; G.d_e = g.d_e; G.l_e = g.l_e; G.f_e = g.f_e; G.L34 = g.L34; G.n_e = g.n_e; G.t_e = g.t_e;
-  G.s_ce = g.s_ce;
-  G.dz = v.d_dz; G.dzh = v.d_dzh; G.wu = v.d_wu; G.wl = v.d_wl; G.dz2 = v.d_dz2; G.ray = v.d_ray;
+  G.div_wa = g.div_wa; G.rot_wa = g.rot_wa; G.inv_Ac = g.inv_Ac; G.vt_w = g.vt_w; G.kin_w = g.kin_w;
+  G.lsq_w = g.lsq_w; G.inv_de = g.inv_de; G.inv_le = g.inv_le; G.l_e = g.l_e; G.d_e = g.d_e; G.f_e = g.f_e;
+  G.inv_L34 = g.inv_L34; G.n_e = g.n_e; G.t_e = g.t_e; G.s_ce = g.s_ce;
+  G.wu = v.d_wu; G.wl = v.d_wl; G.inv_dz = v.d_inv_dz; G.inv_dz2 = v.d_inv_dz2;
+  G.cc = cc;
   return G;
 }
 
@@ -424,9 +442,11 @@ void launch_column(const Geo64& G, const ColArgs& a, cudaStream_t st) {
 void enqueue_step_fp64(icon_state* st, double dt, int nsub, cudaStream_t stream) {
   const icon_grid* grid = st->grid;
   StateDev& s = st->s;
-  const Geo64 G = make_geo(grid);
+  const Geo64 G = make_geo(grid, s.colconst);
   const int ld = G.ld;
   const double dtau = dt / nsub;
+  const Vertical& vg = grid->vert;
+  k_colconst64<<<1, 128, 0, stream>>>(vg.N, vg.ld, vg.d_wu, vg.d_wl, vg.d_dzh, vg.d_dz, vg.d_ray, dtau, s.colconst);
   const unsigned nbv = blocks_for(G.nv, kWarpsPerBlock), nbe = blocks_for(G.ne, kWarpsPerBlock),
                  nbc = blocks_for(G.nc, kWarpsPerBlock);
   cudaMemsetAsync(s.mflx, 0, sizeof(double) * G.ne * ld, stream);
@@ -455,7 +475,7 @@ void enqueue_step_fp64(icon_state* st, double dt, int nsub, cudaStream_t stream)
       ea.vn_out = corr ? s.vn : s.vn_s;
       ea.Avn0 = s.Avn0;
       ea.F = s.F; ea.G = s.G; ea.a_e = s.a_e; ea.mflx = s.mflx;
-      ea.dtau = dtau; ea.nsub = (double)nsub; ea.corrector = corr;
+      ea.dtau = dtau; ea.inv_nsub = 1.0 / nsub; ea.corrector = corr;
       prof_begin(stream, K_EDGE_TEND);
       k_edge_tend<<<nbe, 256, 0, stream>>>(G, ea);
       prof_end(stream);
@@ -470,7 +490,7 @@ void enqueue_step_fp64(icon_state* st, double dt, int nsub, cudaStream_t stream)
       ca.w_o = corr ? s.w : s.w_s;
       ca.wflx = s.wflx;
       ca.status = s.status;
-      ca.dtau = dtau; ca.nsub = (double)nsub; ca.corrector = corr;
+      ca.dtau = dtau; ca.inv_nsub = 1.0 / nsub; ca.corrector = corr;
       prof_begin(stream, K_COLUMN);
       launch_column(G, ca, stream);
       prof_end(stream);

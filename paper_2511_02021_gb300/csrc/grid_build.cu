@@ -414,18 +414,24 @@ __global__ void k_mixed_tables(int64_t nc, int64_t ne, int64_t nv, const double*
                                float* __restrict__ lsq32, float* __restrict__ ide32, float* __restrict__ ile32,
                                float* __restrict__ fe32, float* __restrict__ le32, float* __restrict__ ne32,
                                float* __restrict__ te32, float* __restrict__ i34_32, float* __restrict__ sce32,
-                               double* __restrict__ invAc) {
+                               double* __restrict__ invAc, double* __restrict__ div_wa, double* __restrict__ rot_wa,
+                               double* __restrict__ inv_de, double* __restrict__ inv_le,
+                               double* __restrict__ inv_L34) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < nc) {
     for (int s = 0; s < 3; ++s) {
       div32[3 * i + s] = (float)(div_w[3 * i + s] / A_c[i]);
       kin32[3 * i + s] = (float)kin_w[3 * i + s];
       sce32[3 * i + s] = (float)s_ce[3 * i + s];
+      div_wa[3 * i + s] = div_w[3 * i + s] / A_c[i];
     }
     invAc[i] = 1.0 / A_c[i];
   }
   if (i < nv) {
-    for (int j = 0; j < 6; ++j) rot32[6 * i + j] = (float)(rot_w[6 * i + j] / A_v[i]);
+    for (int j = 0; j < 6; ++j) {
+      rot_wa[6 * i + j] = rot_w[6 * i + j] / A_v[i];
+      rot32[6 * i + j] = (float)rot_wa[6 * i + j];
+    }
     for (int j = 0; j < 18; ++j) lsq32[18 * i + j] = (float)lsq_w[18 * i + j];
   }
   if (i < ne) {
@@ -435,6 +441,9 @@ __global__ void k_mixed_tables(int64_t nc, int64_t ne, int64_t nv, const double*
     fe32[i] = (float)f_e[i];
     le32[i] = (float)l_e[i];
     i34_32[i] = (float)(1.0 / L34[i]);
+    inv_de[i] = 1.0 / d_e[i];
+    inv_le[i] = 1.0 / l_e[i];
+    inv_L34[i] = 1.0 / L34[i];
     for (int j = 0; j < 3; ++j) {
       ne32[3 * i + j] = (float)n_e[3 * i + j];
       te32[3 * i + j] = (float)t_e[3 * i + j];
@@ -528,6 +537,8 @@ int build_grid_device(icon_grid* grid, cudaStream_t st) {
   g.inv_de32 = A.get_n<float>(ne); g.inv_le32 = A.get_n<float>(ne); g.f_e32 = A.get_n<float>(ne);
   g.l_e32 = A.get_n<float>(ne); g.n_e32 = A.get_n<float>(3 * ne); g.t_e32 = A.get_n<float>(3 * ne);
   g.L34inv32 = A.get_n<float>(ne); g.s_ce32 = A.get_n<float>(3 * nc); g.inv_Ac = A.get_n<double>(nc);
+  g.div_wa = A.get_n<double>(3 * nc); g.rot_wa = A.get_n<double>(6 * nv);
+  g.inv_de = A.get_n<double>(ne); g.inv_le = A.get_n<double>(ne); g.inv_L34 = A.get_n<double>(ne);
   double* corner_pos = T.get_n<double>(9 * nc);
   unsigned* cv = T.get_n<unsigned>(n3);
   unsigned* ce = T.get_n<unsigned>(n3);
@@ -573,7 +584,8 @@ int build_grid_device(icon_grid* grid, cudaStream_t st) {
                                                        g.kin_w, g.lsq_w, g.d_e, g.l_e, g.f_e, g.n_e, g.t_e,
                                                        g.L34, g.s_ce, g.div_w32, g.rot_w32, g.vt_w32, g.kin_w32,
                                                        g.lsq_w32, g.inv_de32, g.inv_le32, g.f_e32, g.l_e32,
-                                                       g.n_e32, g.t_e32, g.L34inv32, g.s_ce32, g.inv_Ac);
+                                                       g.n_e32, g.t_e32, g.L34inv32, g.s_ce32, g.inv_Ac,
+                                                       g.div_wa, g.rot_wa, g.inv_de, g.inv_le, g.inv_L34);
   ICON_CUDA(cudaGetLastError());
   unsigned host_u[4];
   ICON_CUDA(cudaMemcpyAsync(host_u, dev_u, sizeof(host_u), cudaMemcpyDeviceToHost, st));

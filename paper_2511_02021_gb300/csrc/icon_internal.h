@@ -78,6 +78,7 @@ struct Vertical {
   double *d_z_h = nullptr, *d_z_f = nullptr, *d_dz = nullptr, *d_dzh = nullptr,
          *d_wu = nullptr, *d_wl = nullptr, *d_ray = nullptr, *d_dz2 = nullptr;
   float *d_inv_dz32 = nullptr, *d_wu32 = nullptr, *d_wl32 = nullptr, *d_inv_dz2_32 = nullptr;
+  double *d_inv_dz = nullptr, *d_inv_dz2 = nullptr;
 };
 
 struct GridDev {
@@ -99,6 +100,8 @@ struct GridDev {
   float *inv_de32 = nullptr, *inv_le32 = nullptr, *f_e32 = nullptr;
   float *l_e32 = nullptr, *n_e32 = nullptr, *t_e32 = nullptr, *L34inv32 = nullptr, *s_ce32 = nullptr;
   double* inv_Ac = nullptr;  // 1 / A_c
+  double *div_wa = nullptr, *rot_wa = nullptr;             // s l / A_c, s d / A_v
+  double *inv_de = nullptr, *inv_le = nullptr, *inv_L34 = nullptr;
 };
 
 }  // namespace icon
