@@ -122,15 +122,18 @@ int upload_vertical(icon_grid* grid, cudaStream_t st) {
     v.h_f32[2 * v.ld + h] = (float)v.wl[h];
     v.h_f32[3 * v.ld + h] = (h > 0 && h < v.N) ? (float)(1.0 / v.dz2[h]) : 0.0f;
   }
-  // FP64 reciprocals of the layer thicknesses (full levels and the two-layer span)
-  std::vector<double> inv(2 * (size_t)v.ld, 0.0);
+  // FP64 reciprocals of the layer thicknesses (full levels, the two-layer span, and a
+  // quarter of the full-level one, exactly scaled)
+  std::vector<double> inv(3 * (size_t)v.ld, 0.0);
   for (int k = 0; k < v.N; ++k) inv[k] = 1.0 / v.dz[k];
   for (int h = 1; h < v.N; ++h) inv[v.ld + h] = 1.0 / v.dz2[h];
-  double* di = A.get_n<double>(2 * (size_t)v.ld);
+  for (int k = 0; k < v.N; ++k) inv[2 * v.ld + k] = 0.25 * inv[k];
+  double* di = A.get_n<double>(3 * (size_t)v.ld);
   if (!di) { set_error("out of device memory (vertical grid)"); return ICON_ENOMEM; }
-  ICON_CUDA(cudaMemcpy(di, inv.data(), sizeof(double) * 2 * v.ld, cudaMemcpyHostToDevice));
+  ICON_CUDA(cudaMemcpy(di, inv.data(), sizeof(double) * 3 * v.ld, cudaMemcpyHostToDevice));
   v.d_inv_dz = di;
   v.d_inv_dz2 = di + v.ld;
+  v.d_qinv_dz = di + 2 * v.ld;
   float* f = A.get_n<float>(4 * (size_t)v.ld);
   if (!f) { set_error("out of device memory (vertical grid)"); return ICON_ENOMEM; }
   ICON_CUDA(cudaMemcpyAsync(f, v.h_f32.data(), sizeof(float) * 4 * v.ld, cudaMemcpyHostToDevice, st));
@@ -199,6 +202,9 @@ int alloc_state(icon_state* st, int precision) {
     s.ex_s = A.get_n<double>(C);
     s.wflx = A.get_n<double>(C);
     s.colconst = A.get_n<double>(8 * (size_t)ld);
+    double** col[] = {&s.col_lo, &s.col_di, &s.col_up, &s.col_rh, &s.col_rx,
+                      &s.col_tx, &s.col_px, &s.col_gm, &s.col_ri, &s.col_mm};
+    for (double** p : col) *p = A.get_n<double>(C);
     s.vn = A.get_n<double>(E); s.vn_s = A.get_n<double>(E);
     s.Avn0 = A.get_n<double>(E); s.Aw0 = A.get_n<double>(C);
     s.zeta = A.get_n<double>(V); s.w_v = A.get_n<double>(V);

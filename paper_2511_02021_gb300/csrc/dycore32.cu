@@ -38,6 +38,7 @@
 #include <string>
 #include "icon_internal.h"
 #include "fastconv.h"
+#include "recip64.h"
 
 namespace icon {
 namespace {
@@ -358,11 +359,11 @@ __device__ inline void mx_column_item(const MxGeo& G, const MxColArgs& a, int64_
     const double Th = rho * thv;
     const double dt1 = cc[CC_DT1BDZ * ld + k];
     rhox[k] = rho - dtau * Dr - dt1 * (rho_ic[k] * w0 - rho_ic[k + 1] * w1);
-    const double thx = Th - (double)(dtau32 * Dt) - dt1 * (M[k] * w0 - M[k + 1] * w1);
+    const double thx = Th - f32_to_f64(dtau32 * Dt) - dt1 * (M[k] * w0 - M[k + 1] * w1);
     Thx[k] = thx;
-    const float g = kRcvF * ((float)ex / (float)Th);
-    exx[k] = ex + (double)g * (thx - Th);
-    gam[k] = g * (float)cc[CC_DTBDZ * ld + k];
+    const float g = kRcvF * (f64_to_f32(ex) / f64_to_f32(Th));
+    exx[k] = ex + f32_to_f64(g) * (thx - Th);
+    gam[k] = g * f64_to_f32(cc[CC_DTBDZ * ld + k]);
   }
   // tridiagonal system at interior half levels, Thomas forward sweep
   double thv_m1 = LM(a.thv, 0), ex_m1 = LM(a.ex, 0);
@@ -374,20 +375,20 @@ __device__ inline void mx_column_item(const MxGeo& G, const MxColArgs& a, int64_
     else LM(a.Aw0, h) = Aw;
     const double thv_h = LM(a.thv, h), ex_h = LM(a.ex, h);
     const double th_ic = cc[CC_WU * ld + h] * thv_m1 + cc[CC_WL * ld + h] * thv_h;
-    const double wx = LM(a.w, h) + dtau * ((double)Aw - cc[CC_CX * ld + h] * th_ic * (ex_m1 - ex_h) - kGrav);
+    const double wx = LM(a.w, h) + dtau * (f32_to_f64(Aw) - cc[CC_CX * ld + h] * th_ic * (ex_m1 - ex_h) - kGrav);
     const double aa = cc[CC_CA * ld + h] * th_ic;
-    const double gm = (double)gam[h - 1], gk = (double)gam[h];
+    const double gm = f32_to_f64(gam[h - 1]), gk = f32_to_f64(gam[h]);
     const double lower = -aa * gm * M[h - 1];
     const double diag = 1.0 + aa * (gm + gk) * M[h];
     const double upper = -aa * gk * M[h + 1];
     const double rhs = wx - aa * (exx[h - 1] - exx[h]);
     const int i = h - 1;
     if (i == 0) {
-      const double r = 1.0 / diag;
+      const double r = recip64(diag);
       cp[0] = upper * r;
       dp[0] = rhs * r;
     } else {
-      const double r = 1.0 / (diag - lower * cp[i - 1]);
+      const double r = recip64(diag - lower * cp[i - 1]);
       cp[i] = upper * r;
       dp[i] = (rhs - lower * dp[i - 1]) * r;
     }
@@ -405,27 +406,27 @@ __device__ inline void mx_column_item(const MxGeo& G, const MxColArgs& a, int64_
     const double r = rho_ic[k] * wn_prev - rho_ic[k + 1] * wn1;
     const double dtb = cc[CC_DTBDZ * ld + k];
     const double Th_n = Thx[k] - dtb * q;
-    const double ex_n = exx[k] - (double)gam[k] * q;
+    const double ex_n = exx[k] - f32_to_f64(gam[k]) * q;
     const double rho_n = rhox[k] - dtb * r;
-    const float exp_n = (float)(ex_n - cc[CC_EXREF * ld + k]);
+    const float exp_n = f64_to_f32(ex_n - cc[CC_EXREF * ld + k]);
+    const float rho32 = f64_to_f32(rho_n);
     if (CORR) {
-      const double thv_n = Th_n / rho_n;
+      const double thv_n = Th_n * recip64(rho_n);
       const double wold = LM(a.w, k);
       LM(a.wflx, k) += rho_ic[k] * (kBeta * wn_prev + (1.0 - kBeta) * wold) * a.inv_nsub;
       LM(a.rho, k) = rho_n;
       LM(a.thv, k) = thv_n;
       LM(a.ex, k) = ex_n;
       LM(a.w, k) = wn_prev;
-      a.thv32[o + k] = (float)thv_n;
+      a.thv32[o + k] = f64_to_f32(thv_n);
       ok = ok && finite64(thv_n) && finite64(ex_n) && finite64(wn_prev);
     } else {
-      const float rho32 = (float)rho_n;
-      a.thv32[o + k] = (float)Th_n / rho32;
+      a.thv32[o + k] = f64_to_f32(Th_n) / rho32;
       ok = ok && finite64(rho_n) && finite64(ex_n) && finite64(wn_prev);
     }
-    a.rho32[o + k] = (float)rho_n;
+    a.rho32[o + k] = rho32;
     a.exp32[o + k] = exp_n;
-    a.w32[o + k] = (float)wn_prev;
+    a.w32[o + k] = f64_to_f32(wn_prev);
     wn_prev = wn1;
   }
   a.w32[o + N] = 0.0f;
@@ -559,7 +560,7 @@ __device__ inline void mx_column_fac_item(const MxGeo& G, const MxColArgs& a, in
           const double lo = -aa * gam2 * M2;
           const double diag = 1.0 + aa * (gam2 + gam1) * M1;
           const double up = -aa * gam1 * Mh;
-          const double rp = 1.0 / (diag - lo * cp_prev);
+          const double rp = recip64(diag - lo * cp_prev);
           const double cpv = up * rp;
           F64(F_LO, h) = lo;
           F64(F_RP, h) = rp;
@@ -622,7 +623,7 @@ __device__ inline void mx_column_fac_item(const MxGeo& G, const MxColArgs& a, in
     const float exp_n = f64_to_f32(ex_n - cc[CC_EXREF * ld + h]);
     const float rho32 = f64_to_f32(rho_n);
     if (CORR) {
-      const double thv_n = Th_n / rho_n;
+      const double thv_n = Th_n * recip64(rho_n);
       const double wold = LM(a.w, h);
       LM(a.wflx, h) += rk * (kBeta * w + (1.0 - kBeta) * wold) * a.inv_nsub;
       LM(a.rho, h) = rho_n;
@@ -1007,6 +1008,7 @@ void enqueue_step_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream
 }
 
 // ---------------------------------------------------------------- self-test of the integer-pipe conversions
+// and of the Newton-Raphson reciprocal
 namespace {
 __device__ inline uint64_t st_mix(uint64_t z) {
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -1039,6 +1041,19 @@ __global__ void k_selftest_conv(int64_t n, unsigned* fails) {
     if (__double_as_longlong(f32_to_f64(-0.0f)) != __double_as_longlong(-0.0)) atomicAdd(fails, 1u);
     if (__float_as_uint(f64_to_f32(0.0)) != 0u) atomicAdd(fails, 1u);
   }
+  // Newton-Raphson reciprocal: within one ulp of the IEEE quotient 1/x, and a * recip64(b)
+  // within two ulps of a / b, for x, b of either sign with exponents in [-120, 120]
+  const uint64_t r3 = st_mix(r2 ^ 0xD1B54A32D192ED03ull);
+  const uint64_t r4 = st_mix(r3);
+  const uint64_t ex3 = 903u + (r3 >> 56) % 241u, ex4 = 903u + (r4 >> 56) % 241u;
+  const double xv = __longlong_as_double((long long)((r3 & 0x800fffffffffffffull) | (ex3 << 52)));
+  const double av = __longlong_as_double((long long)((r4 & 0x800fffffffffffffull) | (ex4 << 52)));
+  const double q1 = 1.0 / xv, y1 = recip64(xv);
+  const long long dq = __double_as_longlong(q1) - __double_as_longlong(y1);
+  if (dq > 1 || dq < -1) atomicAdd(fails, 1u);
+  const double q2 = av / xv, y2 = av * recip64(xv);
+  const long long dq2 = __double_as_longlong(q2) - __double_as_longlong(y2);
+  if (dq2 > 2 || dq2 < -2) atomicAdd(fails, 1u);
 }
 }  // namespace
 

@@ -34,9 +34,10 @@
 // FP64 division issues about eight FP64-pipe instructions on this GPU, so every
 // division by a geometric or per-level constant is a multiplication by a
 // precomputed reciprocal (area factors folded into the stencil weights); the
-// column keeps the three divisions the method needs per level (pi/Theta, the
-// Thomas pivot, Theta/rho).
+// column's three quotients per level (pi/Theta, the Thomas pivot, Theta/rho) use
+// the Newton-Raphson reciprocal of recip64.h.
 #include "icon_internal.h"
+#include "recip64.h"
 
 namespace icon {
 namespace {
@@ -49,7 +50,7 @@ struct Geo64 {
   const int *c2e, *e2c, *e2v, *v2e, *v2c, *vdeg, *e2vt, *e2q;
   const double *div_wa, *rot_wa, *inv_Ac, *vt_w, *kin_w, *lsq_w, *inv_de, *inv_le, *l_e, *d_e, *f_e, *inv_L34;
   const double *n_e, *t_e, *s_ce;
-  const double *wu, *wl, *inv_dz, *inv_dz2;
+  const double *wu, *wl, *inv_dz, *inv_dz2, *qinv_dz;
   const double* cc;                        // per-level constants for the current dtau
 };
 
@@ -155,60 +156,96 @@ struct EdgeArgs {
   int corrector;
 };
 
-__device__ inline double to_half(const double* __restrict__ f, const double* __restrict__ wu,
-                                 const double* __restrict__ wl, int h, int N) {
-  if (h == 0) return f[0];
-  if (h == N) return f[N - 1];
-  return wu[h] * f[h - 1] + wl[h] * f[h];
-}
-
-// vn tendency and update, horizontal mass/heat fluxes, edge part of w advection
+// vn tendency and update, horizontal mass/heat fluxes, edge part of w advection.
+// FP64-pipe bound, so the kernel minimises FP64 warp instructions: one pass over the
+// half levels in windows of 31 (lane l of a window holds half level h = base + l and,
+// for l < 31, full level k = h), each half-level interpolant and cell-pair sum formed
+// once and handed to the lane below with a shuffle, factors of 1/2 folded into
+// exactly-scaled constants, and the per-edge constants cpd / d_e hoisted.
 __global__ void __launch_bounds__(256) k_edge_tend(Geo64 G, EdgeArgs a) {
   const int64_t e = warp_entity();
   if (e >= G.ne) return;
   const int lane = threadIdx.x & 31, ld = G.ld, N = G.N;
   const int64_t c1 = (int64_t)G.e2c[2 * e] * ld, c2 = (int64_t)G.e2c[2 * e + 1] * ld;
   const int64_t v1 = (int64_t)G.e2v[2 * e] * ld, v2 = (int64_t)G.e2v[2 * e + 1] * ld;
+  const int64_t eo = e * ld;
   const double ide = G.inv_de[e], ile = G.inv_le[e], fe = G.f_e[e];
-  const double* vn = a.vn + e * ld;
-  const double* vt = a.vt + e * ld;
-  for (int k = lane; k < N; k += 32) {
-    const double vt_k = vt[k];
-    const double vie0 = to_half(vn, G.wu, G.wl, k, N);
-    const double vie1 = to_half(vn, G.wu, G.wl, k + 1, N);
-    const double we0 = 0.5 * (a.w[c1 + k] + a.w[c2 + k]);
-    const double we1 = 0.5 * (a.w[c1 + k + 1] + a.w[c2 + k + 1]);
-    const double wbar = 0.5 * (we0 + we1);
-    const double zeta_e = 0.5 * (a.zeta[v1 + k] + a.zeta[v2 + k]);
-    const double A = (-(a.Kc[c2 + k] - a.Kc[c1 + k]) * ide + (zeta_e + fe) * vt_k) - wbar * (vie0 - vie1) * G.inv_dz[k];
-    const double th_e = 0.5 * (a.thv[c1 + k] + a.thv[c2 + k]);
-    const double pg = (kCpd * th_e) * ((a.ex[c2 + k] - a.ex[c1 + k]) * ide);
-    double vnew;
-    if (a.corrector) {
-      vnew = a.vn_base[e * ld + k] + a.dtau * (0.5 * (a.Avn0[e * ld + k] + A) - pg);
-    } else {
-      vnew = a.vn_base[e * ld + k] + a.dtau * (A - pg);
-      a.Avn0[e * ld + k] = A;
+  const double cide = kCpd * ide;
+  const double* __restrict__ vn = a.vn + eo;
+  const double* __restrict__ vt = a.vt + eo;
+  const double dtau = a.dtau;
+  for (int base = 0; base <= N; base += 31) {
+    const int h = base + lane;
+    const bool hv = h <= N;                    // a half level of this column
+    const bool kv = lane < 31 && h < N;        // a full level owned by this lane
+    // half-level interpolation weights: f(0) = f[0], f(N) = f[N-1], linear between
+    const int hl = h > 0 ? (h - 1 < N - 1 ? h - 1 : N - 1) : 0;
+    const int hu = h < N ? h : N - 1;
+    const double wa = (h == 0) ? 0.0 : (h >= N ? 1.0 : G.wu[h]);
+    const double wb = (h == 0) ? 1.0 : (h >= N ? 0.0 : G.wl[h]);
+    double vie = 0.0, tie = 0.0, sw = 0.0, dw = 0.0, dwv = 0.0;
+    if (hv) {
+      vie = wa * vn[hl] + wb * vn[hu];
+      tie = wa * vt[hl] + wb * vt[hu];
+      const double w1 = a.w[c1 + h], w2 = a.w[c2 + h];
+      sw = w1 + w2;
+      dw = w2 - w1;
+      dwv = a.w_v[v2 + h] - a.w_v[v1 + h];
     }
-    a.vn_out[e * ld + k] = vnew;
-    const double rho_e = 0.5 * (a.rho[c1 + k] + a.rho[c2 + k]);
-    const double F = rho_e * vnew;
-    a.F[e * ld + k] = F;
-    a.G[e * ld + k] = F * th_e;
-    if (a.corrector) a.mflx[e * ld + k] = a.mflx[e * ld + k] + F * a.inv_nsub;
-  }
-  for (int h = lane; h <= N; h += 32) {
-    const double vie = to_half(vn, G.wu, G.wl, h, N);
-    const double tie = to_half(vt, G.wu, G.wl, h, N);
-    a.a_e[e * ld + h] = vie * (a.w[c2 + h] - a.w[c1 + h]) * ide + tie * (a.w_v[v2 + h] - a.w_v[v1 + h]) * ile;
+    const double vie_up = __shfl_down_sync(0xffffffffu, vie, 1);   // half level h + 1
+    const double sw_up = __shfl_down_sync(0xffffffffu, sw, 1);
+    if (hv && lane < 31) a.a_e[eo + h] = (vie * dw) * ide + (tie * dwv) * ile;
+    if (kv) {
+      const int k = h;
+      // advective tendency: -grad K + (zeta + f) vt - wbar dvn/dz, with
+      // wbar = (sum of the four w) / 4 and the 1/4 folded into the level constant
+      const double zs = a.zeta[v1 + k] + a.zeta[v2 + k];
+      const double dK = a.Kc[c2 + k] - a.Kc[c1 + k];
+      const double T = fma(-dK, ide, fma(0.5, zs, fe) * vt[k]);
+      const double A = fma(-((sw + sw_up) * (vie - vie_up)), G.qinv_dz[k], T);
+      const double ts = a.thv[c1 + k] + a.thv[c2 + k];
+      const double th_e = 0.5 * ts;
+      const double pg = th_e * ((a.ex[c2 + k] - a.ex[c1 + k]) * cide);
+      double vnew;
+      if (a.corrector) {
+        vnew = fma(dtau, fma(0.5, a.Avn0[eo + k] + A, -pg), a.vn_base[eo + k]);
+      } else {
+        vnew = fma(dtau, A - pg, a.vn_base[eo + k]);
+        a.Avn0[eo + k] = A;
+      }
+      a.vn_out[eo + k] = vnew;
+      const double F = (0.5 * (a.rho[c1 + k] + a.rho[c2 + k])) * vnew;
+      a.F[eo + k] = F;
+      a.G[eo + k] = F * th_e;
+      if (a.corrector) a.mflx[eo + k] = fma(F, a.inv_nsub, a.mflx[eo + k]);
+    }
   }
 }
 
+// ---------------------------------------------------------------- column solve
+//
+// The vertically implicit update of every column in three launches:
+//   k_col_rows   one warp per cell, lanes over levels: everything that is parallel
+//                over the levels (half-level interpolants, horizontal divergences,
+//                explicit predictors, the linearised state equation, the w predictor
+//                and the tridiagonal row of every interior half level). Rows go out
+//                level-major for the solve; the operands of the final update stay in
+//                the cell's own rows.
+//   k_col_thomas one thread per column: the Thomas recurrence on level-major rows
+//                (coalesced across the warp), Rayleigh damping; the solution w
+//                overwrites the sub-diagonal.
+//   k_col_update one warp per cell, lanes over levels: the implicit parts of rho,
+//                Theta and pi, theta_v = Theta / rho, the step-mean vertical mass flux.
+// Only the recurrence is sequential in the level; keeping it apart lets the rest run
+// with coalesced, level-contiguous loads instead of one thread walking a column.
 struct ColArgs {
-  const double *rho, *thv, *ex, *w;        // S^n
+  const double *rho, *thv, *ex, *w;        // S^n [c][ld]
   const double* w_stage;                   // w of the stage state (vertical part of A_w)
   const double *F, *G, *a_e;               // edge fluxes and w-advection edge terms
   double* Aw0;                             // stored (predictor) or read (corrector)
+  double *lo, *di, *up, *rh;               // tridiagonal rows, level-major [h][Nc], h = 1..N-1
+  double *rx, *tx, *px, *gm;               // rho*, Theta*, pi* (explicit parts), gamma: [c][ld]
+  double *ri, *mm;                         // half-level rho and rho theta_v of S^n: [c][ld]
   double *rho_o, *thv_o, *ex_o, *w_o;      // S* or S^{n+1} (may alias S^n)
   double* wflx;
   unsigned* status;
@@ -216,12 +253,13 @@ struct ColArgs {
   int corrector;
 };
 
-template <int NMAX>
-__global__ void __launch_bounds__(64) k_column(Geo64 G, ColArgs a) {
-  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+// windows of 31 levels: lane l holds full level k = base + l and the half level above
+// it (h = k); lane 31 only supplies the half level below lane 30's full level
+__global__ void __launch_bounds__(256) k_col_rows(Geo64 G, ColArgs a) {
+  const int64_t c = warp_entity();
   if (c >= G.nc) return;
-  const int N = G.N, ld = G.ld;
-  const int64_t o = c * ld;
+  const int lane = threadIdx.x & 31, ld = G.ld, N = G.N;
+  const int64_t o = c * ld, nc = G.nc;
   const double* __restrict__ cc = G.cc;
   int64_t E[3];
   double dw[3], kw[3];
@@ -231,85 +269,155 @@ __global__ void __launch_bounds__(64) k_column(Geo64 G, ColArgs a) {
     kw[s] = G.kin_w[3 * c + s];
   }
   const double dtau = a.dtau, rcv = kRd / kCvd;
-  double rho_ic[NMAX + 1], M[NMAX + 1], gam[NMAX], Th_x[NMAX], ex_x[NMAX], rho_x[NMAX], cp[NMAX], dp[NMAX];
-  // half-level interpolants of S^n
-  for (int h = 0; h <= N; ++h) {
-    double ri, ti;
-    if (h == 0) { ri = a.rho[o]; ti = a.thv[o]; }
-    else if (h == N) { ri = a.rho[o + N - 1]; ti = a.thv[o + N - 1]; }
-    else {
-      const double wu = cc[C_WU * ld + h], wl = cc[C_WL * ld + h];
-      ri = wu * a.rho[o + h - 1] + wl * a.rho[o + h];
-      ti = wu * a.thv[o + h - 1] + wl * a.thv[o + h];
+  double gam_c = 0.0, px_c = 0.0, M_c = 0.0;          // carried: full / half level base - 1
+  for (int base = 0; base <= N; base += 31) {
+    const int k = base + lane;
+    const bool hv = k <= N;                            // half level k exists
+    const bool kv = lane < 31 && k < N;                // full level k owned here
+    double rho = 0.0, thv = 0.0, ex = 0.0, rho_m = 0.0, thv_m = 0.0, ex_m = 0.0;
+    if (k < N) { rho = a.rho[o + k]; thv = a.thv[o + k]; ex = a.ex[o + k]; }
+    if (k >= 1 && k <= N) { rho_m = a.rho[o + k - 1]; thv_m = a.thv[o + k - 1]; ex_m = a.ex[o + k - 1]; }
+    // half-level interpolants of S^n: rho_ic and M = rho_ic theta_ic
+    double ri = 0.0, ti = 0.0;
+    if (k == 0) { ri = rho; ti = thv; }
+    else if (k == N) { ri = rho_m; ti = thv_m; }
+    else if (k < N) {
+      const double wu = cc[C_WU * ld + k], wl = cc[C_WL * ld + k];
+      ri = wu * rho_m + wl * rho;
+      ti = wu * thv_m + wl * thv;
     }
-    rho_ic[h] = ri;
-    M[h] = ri * ti;
+    const double M = ri * ti;
+    const double wk = hv ? a.w[o + k] : 0.0;
+    const double ri1 = __shfl_down_sync(0xffffffffu, ri, 1);      // half level k + 1
+    const double M1 = __shfl_down_sync(0xffffffffu, M, 1);
+    const double w1 = __shfl_down_sync(0xffffffffu, wk, 1);
+    double gam = 0.0, px = 0.0;
+    if (kv) {
+      // explicit predictors at full level k
+      double Dr = 0.0, Dt = 0.0;
+      for (int s = 0; s < 3; ++s) Dr += dw[s] * a.F[E[s] + k];
+      for (int s = 0; s < 3; ++s) Dt += dw[s] * a.G[E[s] + k];
+      const double Th = rho * thv;
+      const double dt1 = cc[C_DT1BDZ * ld + k];
+      const double rx = (rho - dtau * Dr) - dt1 * (ri * wk - ri1 * w1);
+      const double tx = (Th - dtau * Dt) - dt1 * (M * wk - M1 * w1);
+      const double g = (rcv * ex) * recip64(Th);
+      px = ex + g * (tx - Th);
+      gam = g * cc[C_DTBDZ * ld + k];
+      a.rx[o + k] = rx;
+      a.tx[o + k] = tx;
+      a.px[o + k] = px;
+      a.gm[o + k] = gam;
+    }
+    if (hv && lane < 31) {
+      a.ri[o + k] = ri;
+      a.mm[o + k] = M;
+    }
+    // full level and half level above: from the lane above, or carried for lane 0
+    double gam_m = __shfl_up_sync(0xffffffffu, gam, 1);
+    double px_m = __shfl_up_sync(0xffffffffu, px, 1);
+    double M_m = __shfl_up_sync(0xffffffffu, M, 1);
+    if (lane == 0) { gam_m = gam_c; px_m = px_c; M_m = M_c; }
+    if (kv && k >= 1) {
+      // row of interior half level h = k: w predictor and the implicit coupling
+      const int h = k;
+      double hadv = 0.0;
+      for (int s = 0; s < 3; ++s) hadv += kw[s] * a.a_e[E[s] + h];
+      const double ws = a.w_stage[o + h];
+      double Aw = -hadv - ws * (a.w_stage[o + h - 1] - a.w_stage[o + h + 1]) * G.inv_dz2[h];
+      if (a.corrector) Aw = 0.5 * (a.Aw0[o + h] + Aw);
+      else a.Aw0[o + h] = Aw;
+      const double th_ic = ti;
+      const double w_x = wk + dtau * ((Aw - cc[C_CX * ld + h] * th_ic * (ex_m - ex)) - kGrav);
+      const double aa = cc[C_CA * ld + h] * th_ic;
+      const int64_t i = (int64_t)h * nc + c;
+      a.lo[i] = -aa * gam_m * M_m;
+      a.di[i] = 1.0 + aa * (gam_m + gam) * M;
+      a.up[i] = -aa * gam * M1;
+      a.rh[i] = w_x - aa * (px_m - px);
+    }
+    gam_c = __shfl_sync(0xffffffffu, gam, 30);
+    px_c = __shfl_sync(0xffffffffu, px, 30);
+    M_c = __shfl_sync(0xffffffffu, M, 30);
   }
-  // explicit predictors at full levels
-  for (int k = 0; k < N; ++k) {
-    double Dr = 0.0, Dt = 0.0;
-    for (int s = 0; s < 3; ++s) Dr += dw[s] * a.F[E[s] + k];
-    for (int s = 0; s < 3; ++s) Dt += dw[s] * a.G[E[s] + k];
-    const double rho = a.rho[o + k], thv = a.thv[o + k], ex = a.ex[o + k];
-    const double w0 = a.w[o + k], w1 = a.w[o + k + 1];
-    const double Th = rho * thv;
-    const double dt1 = cc[C_DT1BDZ * ld + k];
-    rho_x[k] = (rho - dtau * Dr) - dt1 * (rho_ic[k] * w0 - rho_ic[k + 1] * w1);
-    Th_x[k] = (Th - dtau * Dt) - dt1 * (M[k] * w0 - M[k + 1] * w1);
-    const double g = rcv * (ex / Th);
-    ex_x[k] = ex + g * (Th_x[k] - Th);
-    gam[k] = g * cc[C_DTBDZ * ld + k];
-  }
-  // tridiagonal rows at interior half levels h = 1..N-1 (row i = h-1), Thomas forward sweep
+}
+
+// Thomas recurrence per column on the level-major rows; the next row is loaded before
+// the current one is stored so that its loads overlap the recurrence
+__global__ void __launch_bounds__(128) k_col_thomas(Geo64 G, ColArgs a) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= G.nc) return;
+  const int N = G.N, ld = G.ld;
+  if (N < 2) return;
+  const int64_t nc = G.nc;
+  const double* __restrict__ cc = G.cc;
+  double* __restrict__ lo = a.lo;
+  const double* __restrict__ di = a.di;
+  double* __restrict__ up = a.up;
+  double* __restrict__ rh = a.rh;
+  double cp = 0.0, dp = 0.0;
+  double l = lo[nc + c], d = di[nc + c], u = up[nc + c], r = rh[nc + c];
   for (int h = 1; h < N; ++h) {
-    double hadv = 0.0;
-    for (int s = 0; s < 3; ++s) hadv += kw[s] * a.a_e[E[s] + h];
-    const double ws = a.w_stage[o + h];
-    double Aw = -hadv - ws * (a.w_stage[o + h - 1] - a.w_stage[o + h + 1]) * G.inv_dz2[h];
-    if (a.corrector) Aw = 0.5 * (a.Aw0[o + h] + Aw);
-    else a.Aw0[o + h] = Aw;
-    const double th_ic = cc[C_WU * ld + h] * a.thv[o + h - 1] + cc[C_WL * ld + h] * a.thv[o + h];
-    const double exm = a.ex[o + h - 1], exk = a.ex[o + h];
-    const double w_x = a.w[o + h] + dtau * ((Aw - cc[C_CX * ld + h] * th_ic * (exm - exk)) - kGrav);
-    const double aa = cc[C_CA * ld + h] * th_ic;
-    const double lower = -aa * gam[h - 1] * M[h - 1];
-    const double diag = 1.0 + aa * (gam[h - 1] + gam[h]) * M[h];
-    const double upper = -aa * gam[h] * M[h + 1];
-    const double rhs = w_x - aa * (ex_x[h - 1] - ex_x[h]);
-    const int i = h - 1;
-    const double r = 1.0 / (i == 0 ? diag : diag - lower * cp[i - 1]);
-    cp[i] = upper * r;
-    dp[i] = (i == 0 ? rhs : rhs - lower * dp[i - 1]) * r;
-  }
-  // back substitution (dp becomes the solution), Rayleigh damping
-  for (int i = N - 3; i >= 0; --i) dp[i] = dp[i] - cp[i] * dp[i + 1];
-  double wn_prev = 0.0;   // w_new at the half level above the current full level
-  bool bad = false;
-  for (int k = 0; k < N; ++k) {
-    const int h1 = k + 1;
-    double wn1 = 0.0;
-    if (h1 < N) wn1 = dp[h1 - 1] * cc[C_DAMP * ld + h1];
-    const double q0 = M[k] * wn_prev, q1 = M[k + 1] * wn1;
-    const double r0 = rho_ic[k] * wn_prev, r1 = rho_ic[k + 1] * wn1;
-    const double dtb = cc[C_DTBDZ * ld + k];
-    const double Th_n = Th_x[k] - dtb * (q0 - q1);
-    const double ex_n = ex_x[k] - gam[k] * (q0 - q1);
-    const double rho_n = rho_x[k] - dtb * (r0 - r1);
-    const double thv_n = Th_n / rho_n;
-    if (a.corrector) {
-      // step-mean vertical mass flux at the half level above this full level
-      const double wold = a.w[o + k];
-      a.wflx[o + k] = a.wflx[o + k] + rho_ic[k] * (kBeta * wn_prev + (1.0 - kBeta) * wold) * a.inv_nsub;
+    double ln = 0.0, dn = 0.0, un = 0.0, rn = 0.0;
+    if (h + 1 < N) {
+      const int64_t j = (int64_t)(h + 1) * nc + c;
+      ln = lo[j]; dn = di[j]; un = up[j]; rn = rh[j];
     }
-    a.rho_o[o + k] = rho_n;
-    a.thv_o[o + k] = thv_n;
-    a.ex_o[o + k] = ex_n;
-    a.w_o[o + k] = wn_prev;
-    bad |= !isfinite(thv_n) || !isfinite(wn_prev) || !isfinite(ex_n);
-    wn_prev = wn1;
+    const double q = recip64(h == 1 ? d : d - l * cp);
+    cp = u * q;
+    dp = (h == 1 ? r : r - l * dp) * q;
+    const int64_t i = (int64_t)h * nc + c;
+    up[i] = cp;
+    rh[i] = dp;
+    l = ln; d = dn; u = un; r = rn;
   }
-  a.w_o[o + N] = 0.0;
-  if (bad) atomicOr(a.status, 1u);
+  // back substitution; the damped solution replaces the sub-diagonal
+  double x = dp;
+  lo[(int64_t)(N - 1) * nc + c] = x * cc[C_DAMP * ld + N - 1];
+  for (int h = N - 2; h >= 1; --h) {
+    const int64_t i = (int64_t)h * nc + c;
+    x = rh[i] - up[i] * x;
+    lo[i] = x * cc[C_DAMP * ld + h];
+  }
+}
+
+__global__ void __launch_bounds__(256) k_col_update(Geo64 G, ColArgs a) {
+  const int64_t c = warp_entity();
+  if (c >= G.nc) return;
+  const int lane = threadIdx.x & 31, ld = G.ld, N = G.N;
+  const int64_t o = c * ld, nc = G.nc;
+  const double* __restrict__ cc = G.cc;
+  bool bad = false;
+  for (int base = 0; base < N; base += 31) {
+    const int k = base + lane;
+    // w^{n+1} (damped) at half level k; zero at the top and the bottom
+    const double wn = (k >= 1 && k < N) ? a.lo[(int64_t)k * nc + c] : 0.0;
+    const double ri = k <= N ? a.ri[o + k] : 0.0;
+    const double M = k <= N ? a.mm[o + k] : 0.0;
+    const double wn1 = __shfl_down_sync(0xffffffffu, wn, 1);
+    const double ri1 = __shfl_down_sync(0xffffffffu, ri, 1);
+    const double M1 = __shfl_down_sync(0xffffffffu, M, 1);
+    if (lane < 31 && k < N) {
+      const double q = M * wn - M1 * wn1;
+      const double r = ri * wn - ri1 * wn1;
+      const double dtb = cc[C_DTBDZ * ld + k];
+      const double Th_n = a.tx[o + k] - dtb * q;
+      const double ex_n = a.px[o + k] - a.gm[o + k] * q;
+      const double rho_n = a.rx[o + k] - dtb * r;
+      const double thv_n = Th_n * recip64(rho_n);
+      if (a.corrector) {
+        const double wold = a.w[o + k];
+        a.wflx[o + k] = a.wflx[o + k] + ri * (kBeta * wn + (1.0 - kBeta) * wold) * a.inv_nsub;
+      }
+      a.rho_o[o + k] = rho_n;
+      a.thv_o[o + k] = thv_n;
+      a.ex_o[o + k] = ex_n;
+      a.w_o[o + k] = wn;
+      bad |= !isfinite(thv_n) || !isfinite(wn) || !isfinite(ex_n);
+    }
+  }
+  if (lane == 0) a.w_o[o + N] = 0.0;
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.status, 1u);
 }
 
 // ---------------------------------------------------------------- diffusion
@@ -423,18 +531,16 @@ Geo64 make_geo(const icon_grid* grid, const double* cc) {
   G.div_wa = g.div_wa; G.rot_wa = g.rot_wa; G.inv_Ac = g.inv_Ac; G.vt_w = g.vt_w; G.kin_w = g.kin_w;
   G.lsq_w = g.lsq_w; G.inv_de = g.inv_de; G.inv_le = g.inv_le; G.l_e = g.l_e; G.d_e = g.d_e; G.f_e = g.f_e;
   G.inv_L34 = g.inv_L34; G.n_e = g.n_e; G.t_e = g.t_e; G.s_ce = g.s_ce;
-  G.wu = v.d_wu; G.wl = v.d_wl; G.inv_dz = v.d_inv_dz; G.inv_dz2 = v.d_inv_dz2;
+  G.wu = v.d_wu; G.wl = v.d_wl; G.inv_dz = v.d_inv_dz; G.inv_dz2 = v.d_inv_dz2; G.qinv_dz = v.d_qinv_dz;
   G.cc = cc;
   return G;
 }
 
 void launch_column(const Geo64& G, const ColArgs& a, cudaStream_t st) {
-  const unsigned nb = blocks_for(G.nc, 64);
-  if (G.N <= 32) k_column<32><<<nb, 64, 0, st>>>(G, a);
-  else if (G.N <= 64) k_column<64><<<nb, 64, 0, st>>>(G, a);
-  else if (G.N <= 96) k_column<96><<<nb, 64, 0, st>>>(G, a);
-  else if (G.N <= 128) k_column<128><<<nb, 64, 0, st>>>(G, a);
-  else k_column<256><<<nb, 64, 0, st>>>(G, a);
+  const unsigned nbc = blocks_for(G.nc, kWarpsPerBlock);
+  k_col_rows<<<nbc, 256, 0, st>>>(G, a);
+  k_col_thomas<<<blocks_for(G.nc, 128), 128, 0, st>>>(G, a);
+  k_col_update<<<nbc, 256, 0, st>>>(G, a);
 }
 
 }  // namespace
@@ -484,6 +590,9 @@ void enqueue_step_fp64(icon_state* st, double dt, int nsub, cudaStream_t stream)
       ca.w_stage = w_st;
       ca.F = s.F; ca.G = s.G; ca.a_e = s.a_e;
       ca.Aw0 = s.Aw0;
+      ca.lo = s.col_lo; ca.di = s.col_di; ca.up = s.col_up; ca.rh = s.col_rh;
+      ca.rx = s.col_rx; ca.tx = s.col_tx; ca.px = s.col_px; ca.gm = s.col_gm;
+      ca.ri = s.col_ri; ca.mm = s.col_mm;
       ca.rho_o = corr ? s.rho : s.rho_s;
       ca.thv_o = corr ? s.thv : s.thv_s;
       ca.ex_o = corr ? s.ex : s.ex_s;

@@ -78,7 +78,7 @@ struct Vertical {
   double *d_z_h = nullptr, *d_z_f = nullptr, *d_dz = nullptr, *d_dzh = nullptr,
          *d_wu = nullptr, *d_wl = nullptr, *d_ray = nullptr, *d_dz2 = nullptr;
   float *d_inv_dz32 = nullptr, *d_wu32 = nullptr, *d_wl32 = nullptr, *d_inv_dz2_32 = nullptr;
-  double *d_inv_dz = nullptr, *d_inv_dz2 = nullptr;
+  double *d_inv_dz = nullptr, *d_inv_dz2 = nullptr, *d_qinv_dz = nullptr;   // 1/dz, 1/dz2, 1/(4 dz)
 };
 
 struct GridDev {
@@ -143,6 +143,10 @@ struct StateDev {
   bool level_major = false;
   double *ex_ref = nullptr;           // [ld] reference Exner profile
   // per-level constants of the column solve for the current dtau (mixed mode)
+  // FP64 column scratch: tridiagonal rows level-major [h][Nc], update operands [c][ld]
+  double *col_lo = nullptr, *col_di = nullptr, *col_up = nullptr, *col_rh = nullptr;
+  double *col_rx = nullptr, *col_tx = nullptr, *col_px = nullptr, *col_gm = nullptr;
+  double *col_ri = nullptr, *col_mm = nullptr;
   double* colconst = nullptr;
   // frozen parts of the column system shared by predictor and corrector (mixed mode;
   // NULL when they would not fit, then both stages compute them)

@@ -1,0 +1,104 @@
+"""Parity at the benchmark's full sizes, through the same calls and launch shapes the
+throughput benchmark uses (graph-captured step, default tiles).
+
+R2B6 / 90 levels FP64: sampled columns of one step against stored oracle values
+(written by tests/golden/make_step_samples.py, which runs only the oracle), plus the
+L2 norm of every full field. R2B8 / 90 levels mixed: the oracle cannot run at this
+size in a test, so the mixed step is held to the same derived bounds against the
+FP64 GPU step (itself pinned to the oracle above and in test_gpu_step), and mass is
+checked for conservation."""
+import json
+
+import numpy as np
+import pytest
+
+from tests.conftest import golden_path, rel_l2
+from tests.tolerances import thermo_bound_mixed, w_bound, w_bound_mixed
+
+pytestmark = pytest.mark.gpu
+
+TOL_STEP = 1e-12
+TOL_INIT = 1e-14
+
+
+@pytest.fixture(scope="module")
+def samples():
+    with open(golden_path("r2b6_l90_jet_step_samples.json")) as fh:
+        return json.load(fh)
+
+
+def test_r2b6_l90_fp64_step_sampled(gpu, samples):
+    C = gpu
+    cfg = samples["config"]
+    N, dt, nsub = cfg["nlev"], cfg["dt"], cfg["nsub"]
+    cells, edges = np.array(samples["cells"]), np.array(samples["edges"])
+    grid = C.icon_grid_build(cfg["root"], cfg["bisections"], N)
+    st = C.icon_state_init_ex(grid, cfg["seed"], cfg["case"], noise_K=cfg["noise_K"])
+    try:
+        for f, ref in samples["init"].items():
+            full = C.icon_state_copy_field(st, grid, N, f)
+            idx = edges if f == "vn" else cells
+            assert rel_l2(full[idx], np.array(ref)) <= TOL_INIT, f
+            assert abs(np.linalg.norm(full) / samples["norm_init"][f] - 1.0) <= TOL_INIT, f
+        m0 = C.icon_global_mass(st)
+        C.icon_dycore_step(st, dt, nsub)
+        m1 = C.icon_global_mass(st)
+        wb = w_bound(dt, nsub, 1)
+        for f, ref in samples["step"].items():
+            full = C.icon_state_copy_field(st, grid, N, f)
+            idx = edges if f in ("vn", "mflx") else cells
+            got, ref = full[idx], np.array(ref)
+            norm_ref = samples["norm_step"][f]
+            if f in ("w", "wflx"):
+                # absolute bound (w is a small residual of a large balance), scaled by the
+                # density for the mass flux
+                scale = 1.0 if f == "w" else float(np.max(np.abs(np.array(samples["step"]["rho"]))))
+                assert np.sqrt(np.mean((got - ref) ** 2)) <= wb * scale, f
+                assert abs(np.linalg.norm(full) - norm_ref) / np.sqrt(full.size) <= wb * scale, f
+            else:
+                assert rel_l2(got, ref) <= TOL_STEP, (f, rel_l2(got, ref))
+                assert abs(np.linalg.norm(full) / norm_ref - 1.0) <= TOL_STEP, f
+            del full
+        om0, om1 = samples["mass"]
+        assert abs(m0 / om0 - 1.0) <= 1e-14 and abs(m1 / om1 - 1.0) <= 1e-14
+        assert abs(m1 / m0 - 1.0) <= 1e-13
+    finally:
+        C.icon_state_free(st)
+        C.icon_grid_free(grid)
+
+
+def test_r2b8_l90_mixed_vs_fp64(gpu):
+    """The mixed-precision R2B8 / 90-level workload (jet, 0.1 K noise, seed 2, dt 22.5 s,
+    5 substeps): one step against the FP64 GPU step from the same initial state."""
+    C = gpu
+    N, dt, nsub = 90, 22.5, 5
+    grid = C.icon_grid_build(2, 8, N)
+    a = b = None
+    try:
+        a = C.icon_state_init_ex(grid, 2, C.ICON_CASE_JET, noise_K=0.1, precision=C.ICON_FP64)
+        b = C.icon_state_init_ex(grid, 2, C.ICON_CASE_JET, noise_K=0.1, precision=C.ICON_MIXED)
+        am0, bm0 = C.icon_global_mass(a), C.icon_global_mass(b)
+        C.icon_dycore_step(a, dt, nsub)
+        C.icon_dycore_step(b, dt, nsub)
+        am1, bm1 = C.icon_global_mass(a), C.icon_global_mass(b)
+        with open(golden_path("grid_dual_edge_min.json")) as fh:
+            d_min = json.load(fh)["d_e_min_m"]["8"]
+        for f in ("vn", "rho", "theta_v", "exner"):
+            x = C.icon_state_copy_field(a, grid, N, f)
+            y = C.icon_state_copy_field(b, grid, N, f)
+            err = rel_l2(y, x)
+            bound = 1e-5 if f == "vn" else thermo_bound_mixed(dt, nsub, 1, d_min)
+            assert err <= bound, (f, err, bound)
+            del x, y
+        x = C.icon_state_copy_field(a, grid, N, "w")
+        y = C.icon_state_copy_field(b, grid, N, "w")
+        assert np.sqrt(np.mean((y - x) ** 2)) <= w_bound_mixed(dt, nsub, 1)
+        del x, y
+        assert abs(am1 / am0 - 1.0) <= 1e-13
+        assert abs(bm1 / bm0 - 1.0) <= 1e-13
+        assert abs(am0 / bm0 - 1.0) <= 1e-15
+    finally:
+        for s in (a, b):
+            if s is not None:
+                C.icon_state_free(s)
+        C.icon_grid_free(grid)
