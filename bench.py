@@ -52,11 +52,22 @@ def peaks():
 # probe on this pool (505 G instr/s; NVIDIA's nominal 1.25 TFLOP/s FMA is 625 G instr/s
 # at 2.07 GHz). Used as the peak of kernels bound by FP64 arithmetic.
 FP64_INSTR_PEAK = 505e9
-# FP64 arithmetic operations per cell-level of one mixed column-solve launch (predictor and
-# corrector averaged), counted from the kernel source: interpolation 6, explicit predictors
-# and flux sums 17, w predictor and tridiagonal row 16, Thomas sweeps with one reciprocal
-# (counted as 1) 6, updates 14, conversions to and from FP32 10.
-MX_COLUMN_FP64_OPS = 69
+# FP64 arithmetic per cell-level of one launch of the column solves, counted from the
+# kernel source as FP64 instructions (a fused multiply-add is one, the Newton-Raphson
+# reciprocal three), averaged over predictor and corrector; ncu's executed FP64
+# instruction counts agree within 10 %.
+# FP64 step, per full level: rows kernel 28 (explicit predictors, linearised state
+# equation) + 5 (half-level interpolants) + 24 (w predictor and tridiagonal row),
+# Thomas 9, update 11 (corrector 16), finiteness checks on the integer pipe; executed
+# count (ncu, R2B6/90): 72 predictor, 78 corrector.
+COLUMN_FP64_OPS = 76
+# mixed step with stored factors: predictor 52 (one downward sweep forming and factoring
+# the rows, one upward sweep), corrector 28 (right-hand side, substitution, updates,
+# vertical mass flux).
+MX_COLUMN_FP64_OPS = 40
+# mixed step recomputing the factors in both stages (when the stored factors would
+# exceed a quarter of the device memory): about 66 in each stage.
+MX_COLUMN_RECOMPUTE_FP64_OPS = 66
 
 
 def counts(wl):
@@ -65,7 +76,7 @@ def counts(wl):
     return nc, ne, nv
 
 
-def kernel_model(kind, wl):
+def kernel_model(kind, wl, stored_factors=True):
     """(algorithmic bytes, FP64 arithmetic ops) of ONE launch of a kernel kind, averaged
     over predictor and corrector launches: every input and output array element read
     or written once (8 B in FP64), and the FP64 operations of the expressions as
@@ -75,12 +86,12 @@ def kernel_model(kind, wl):
     H = N + 1
     b = 8.0
     table = {
-        "vertex_curl_wmean": (b * (ne * N + nc * H + nv * N + nv * H), nv * N * 13 + nv * H * 6),
-        "edge_vt_ke": (b * 3 * ne * N, ne * N * 14),
-        "cell_ke": (b * (ne + nc) * N, nc * N * 6),
+        "vertex_curl_wmean": (b * (ne * N + nc * H + nv * N + nv * H), nv * N * 6 + nv * H * 7),
+        "edge_vt_ke": (b * 3 * ne * N, ne * N * 8),
+        "cell_ke": (b * (ne + nc) * N, nc * N * 3),
         "edge_tendency_flux": (b * (ne * N * 6.5 + nc * N * 4 + nv * N + nc * H + nv * H + ne * H),
-                               ne * N * 30 + ne * H * 10),
-        "column_solve": (b * (nc * N * 8 + ne * N * 2 + ne * H + nc * H * 2.5), nc * N * 120),
+                               ne * N * 23 + ne * H * 11),
+        "column_solve": (b * (nc * N * 8 + ne * N * 2 + ne * H + nc * H * 2.5), nc * N * COLUMN_FP64_OPS),
         "diff_vertex": (b * (ne * N + 4 * nv * N), nv * N * 25),
         "diff_div": (b * (ne + nc) * N, nc * N * 7),
         "diff_edge": (b * (ne * N * 4 + nv * N * 5 + nc * N * 2), ne * N * 45),
@@ -92,7 +103,9 @@ def kernel_model(kind, wl):
         "mx_cell_ke": (4.0 * (ne + nc) * N, 0),
         "mx_edge_tendency_flux": (4.0 * (ne * N * 6.5 + ne * H + nc * N * 4 + nv * N + nc * H + nv * H)
                                   + 8.0 * ne * N, ne * N * 1.0),
-        "mx_column_solve": (nc * N * 98.0, nc * N * MX_COLUMN_FP64_OPS),
+        "mx_column_solve": (nc * N * 98.0, nc * N * (MX_COLUMN_FP64_OPS if stored_factors
+                                                     else MX_COLUMN_RECOMPUTE_FP64_OPS)),
+        "mx_column_prep": (4.0 * (3 * ne * N + ne * H + nc * H * 3) + 8.0 * (nc * N * 3 + nc * H), nc * N * 3),
         "mx_diff_vertex": (4.0 * (2 * ne * N + 4 * nv * N + nc * N), 0),
         "mx_diff_edge": (4.0 * (ne * N * 4 + nv * N * 3 + nc * N * 2), 0),
         "mx_diff_theta": (4.0 * ne * N + 40.0 * nc * N, nc * N * 6),
@@ -243,12 +256,15 @@ def run_gpu(args, wl, rank, world, local_rank):
         for _ in range(2):
             kms, kn = C.icon_dycore_step_profile(st, wl.dt, wl.nsub, kms, kn)
         rows = []
+        # the mixed column with stored factors is the one that launches the gather kernel
+        names = [C.icon_kernel_kind_name(k) for k in range(C.ICON_KIND_COUNT)]
+        stored = kn[names.index("mx_column_prep")] > 0
         for k in range(C.ICON_KIND_COUNT):
             if kn[k] == 0:
                 continue
-            name = C.icon_kernel_kind_name(k)
+            name = names[k]
             avg = kms[k] / kn[k]
-            model = kernel_model(name, wl)
+            model = kernel_model(name, wl, stored)
             gbs = model[0] / (avg * 1e-3) / 1e9 if model else None
             fops = model[1] / (avg * 1e-3) if model else None
             rows.append((kms[k] / 2, name, avg, int(kn[k] // 2), gbs, fops))

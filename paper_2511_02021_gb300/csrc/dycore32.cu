@@ -56,13 +56,6 @@ struct MxGeo {
   const float *inv_dz32, *wu32, *wl32, *inv_dz2_32;
 };
 
-__device__ inline float half32(const float* __restrict__ f, const float* __restrict__ wu,
-                               const float* __restrict__ wl, int h, int N) {
-  if (h == 0) return f[0];
-  if (h == N) return f[N - 1];
-  return wu[h] * f[h - 1] + wl[h] * f[h];
-}
-
 // ---------------------------------------------------------------- stencil items (lanes over levels)
 
 // O3 curl (full levels) and the vertex mean of w (half levels)
@@ -144,24 +137,58 @@ struct MxEdgeArgs {
   int corrector;
 };
 
-// vn tendency and update, horizontal flux integrals, edge part of the w advection
+// vn tendency and update, horizontal flux integrals, edge part of the w advection.
+// One pass over the half levels in windows of LPE - 1: lane l of an entity's lane
+// group holds half level h = base + l and, except the last lane, full level k = h;
+// each half-level interpolant and cell-pair sum of w is formed once and passed to the
+// lane below with a shuffle (only the group's own lanes take part, so the two halves
+// of a warp may serve different entities).
 template <int LPE>
 __device__ inline void mx_edge_tend_item(const MxGeo& G, const MxEdgeArgs& a, int64_t e, int lane) {
   const int ld = G.ld, N = G.N;
   const int64_t c1 = (int64_t)G.e2c[2 * e] * ld, c2 = (int64_t)G.e2c[2 * e + 1] * ld;
   const int64_t v1 = (int64_t)G.e2v[2 * e] * ld, v2 = (int64_t)G.e2v[2 * e + 1] * ld;
   const float ide = G.inv_de32[e], ile = G.inv_le32[e], fe = G.f_e32[e], le = G.l_e32[e];
-  const float* vn = a.vn + e * ld;
-  const float* vt = a.vt + e * ld;
+  const float cide = (float)kCpd * ide;
   const int64_t o = e * ld;
-  for (int k = lane; k < N; k += LPE) {
-    const float vie0 = half32(vn, G.wu32, G.wl32, k, N);
-    const float vie1 = half32(vn, G.wu32, G.wl32, k + 1, N);
-    const float wbar = 0.25f * ((a.w[c1 + k] + a.w[c2 + k]) + (a.w[c1 + k + 1] + a.w[c2 + k + 1]));
-    const float zeta_e = 0.5f * (a.zeta[v1 + k] + a.zeta[v2 + k]);
-    const float A = -(a.Kc[c2 + k] - a.Kc[c1 + k]) * ide + (zeta_e + fe) * vt[k] - wbar * (vie0 - vie1) * G.inv_dz32[k];
-    const float th_e = 0.5f * (a.thv[c1 + k] + a.thv[c2 + k]);
-    const float pg = (float)kCpd * th_e * ((a.exp[c2 + k] - a.exp[c1 + k]) * ide);
+  const float* __restrict__ vn = a.vn + o;
+  const float* __restrict__ vt = a.vt + o;
+  const float* __restrict__ w = a.w;
+  const float* __restrict__ wv = a.w_v;
+  const float* __restrict__ zeta = a.zeta;
+  const float* __restrict__ Kc = a.Kc;
+  const float* __restrict__ thv = a.thv;
+  const float* __restrict__ exq = a.exp;
+  const float* __restrict__ rho = a.rho;
+  const unsigned seg = LPE == 32 ? 0xffffffffu : (0xffffu << (threadIdx.x & 16));
+  for (int base = 0; base <= N; base += LPE - 1) {
+    const int h = base + lane;
+    const bool hv = h <= N;
+    const int hl = h > 0 ? (h - 1 < N - 1 ? h - 1 : N - 1) : 0;
+    const int hu = h < N ? h : N - 1;
+    const bool inner = h > 0 && h < N;
+    const float wa = inner ? G.wu32[h] : (h == 0 ? 0.0f : 1.0f);
+    const float wb = inner ? G.wl32[h] : (h == 0 ? 1.0f : 0.0f);
+    float vie = 0.f, tie = 0.f, sw = 0.f, dw = 0.f, dwv = 0.f;
+    if (hv) {
+      vie = wa * vn[hl] + wb * vn[hu];
+      tie = wa * vt[hl] + wb * vt[hu];
+      const float w1 = w[c1 + h], w2 = w[c2 + h];
+      sw = w1 + w2;
+      dw = w2 - w1;
+      dwv = wv[v2 + h] - wv[v1 + h];
+    }
+    const float vie_up = __shfl_down_sync(seg, vie, 1, LPE);
+    const float sw_up = __shfl_down_sync(seg, sw, 1, LPE);
+    if (!hv || lane == LPE - 1) continue;
+    a.a_e[o + h] = vie * dw * ide + tie * dwv * ile;
+    if (h == N) continue;
+    const int k = h;
+    const float wbar = 0.25f * (sw + sw_up);
+    const float zeta_e = 0.5f * (zeta[v1 + k] + zeta[v2 + k]);
+    const float A = -(Kc[c2 + k] - Kc[c1 + k]) * ide + (zeta_e + fe) * vt[k] - wbar * (vie - vie_up) * G.inv_dz32[k];
+    const float th_e = 0.5f * (thv[c1 + k] + thv[c2 + k]);
+    const float pg = th_e * ((exq[c2 + k] - exq[c1 + k]) * cide);
     float vnew;
     if (a.corrector) {
       vnew = a.vn_base[o + k] + a.dtau * (0.5f * (a.Avn0[o + k] + A) - pg);
@@ -170,16 +197,11 @@ __device__ inline void mx_edge_tend_item(const MxGeo& G, const MxEdgeArgs& a, in
       a.Avn0[o + k] = A;
     }
     a.vn_out[o + k] = vnew;
-    const float F = 0.5f * (a.rho[c1 + k] + a.rho[c2 + k]) * vnew;
+    const float F = 0.5f * (rho[c1 + k] + rho[c2 + k]) * vnew;
     const float phi = le * F;
     a.phi[o + k] = phi;
     a.gth[o + k] = phi * th_e;
     if (a.corrector) a.mflx[o + k] += f32_to_f64(F) * a.inv_nsub;
-  }
-  for (int h = lane; h <= N; h += LPE) {
-    const float vie = half32(vn, G.wu32, G.wl32, h, N);
-    const float tie = half32(vt, G.wu32, G.wl32, h, N);
-    a.a_e[o + h] = vie * (a.w[c2 + h] - a.w[c1 + h]) * ide + tie * (a.w_v[v2 + h] - a.w_v[v1 + h]) * ile;
   }
 }
 
@@ -708,7 +730,7 @@ __global__ void __launch_bounds__(512) k_mx_cell_ke(MxGeo G, const float* vn, co
   mx_cell_ke_item<LPE>(G, vn, vt, Kc, item, lane);
 }
 template <int LPE>
-__global__ void __launch_bounds__(512) k_mx_edge_tend(MxGeo G, MxEdgeArgs a) {
+__global__ void __launch_bounds__(512, LPE == 32 ? 2 : 1) k_mx_edge_tend(MxGeo G, MxEdgeArgs a) {
   ITEM_PROLOGUE(LPE, G.ne)
   mx_edge_tend_item<LPE>(G, a, item, lane);
 }

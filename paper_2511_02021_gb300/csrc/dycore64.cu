@@ -74,6 +74,12 @@ __global__ void k_colconst64(int N, int ld, const double* __restrict__ wu, const
   }
 }
 
+// finiteness from the exponent bits (integer pipe; a floating-point compare would
+// take an FP64-pipe slot)
+__device__ inline bool finite_bits(double x) {
+  return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
+}
+
 __device__ inline int64_t warp_entity() {
   return (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
 }
@@ -413,7 +419,7 @@ __global__ void __launch_bounds__(256) k_col_update(Geo64 G, ColArgs a) {
       a.thv_o[o + k] = thv_n;
       a.ex_o[o + k] = ex_n;
       a.w_o[o + k] = wn;
-      bad |= !isfinite(thv_n) || !isfinite(wn) || !isfinite(ex_n);
+      bad |= !finite_bits(thv_n) || !finite_bits(wn) || !finite_bits(ex_n);
     }
   }
   if (lane == 0) a.w_o[o + N] = 0.0;
