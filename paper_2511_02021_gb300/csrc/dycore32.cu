@@ -314,7 +314,7 @@ struct MxColArgs {
   // parts of the column system frozen at S^n, written by the predictor and read by the
   // corrector (NULL: both stages compute them); level-major [field][level][Nc]
   double* fac64;
-  // per-stage horizontal inputs of the column gathered by k_mx_cell_gather, level-major:
+  // per-stage horizontal inputs of the column gathered by k_mx_gather_tile, level-major:
   // FP64 mass-flux divergence, FP32 heat-flux divergence, FP32 w-advection tendency
   // (already averaged with the predictor's in the corrector), and the Thomas scratch
   double* hdr;
@@ -471,8 +471,9 @@ __device__ inline void mx_column_item(const MxGeo& G, const MxColArgs& a, int64_
 // about 70 in each stage when both compute everything.
 enum { F_LO = 0, F_RP, F_CP, F_WX, F_AA, F_M, F_RI, F_RX, F_TX, F_PX, F_GD, F_GAM, F_COUNT64 };  // FP64 [f][h][Nc]
 
-// Gather step of the stored-factor column path: one warp per cell, lanes over levels
-// (coalesced gathers of the three edge rows), writes the cell's horizontal
+// Gather step of the stored-factor column path for one cell (the persistent ensemble's
+// form; single states use the shared-memory transposing k_mx_gather_tile): lanes over
+// levels (coalesced gathers of the three edge rows), writes the cell's horizontal
 // divergences and w-advection tendency level-major so that the thread-per-column
 // solve reads them coalesced.
 template <int LPE, bool CORR>
@@ -625,6 +626,15 @@ __device__ inline void mx_column_fac_item(const MxGeo& G, const MxColArgs& a, in
     }
   }
   // ---- upward sweep: back substitution, Rayleigh damping, updates of full level h
+  double* __restrict__ rho_io = a.rho;
+  double* __restrict__ thv_io = a.thv;
+  double* __restrict__ ex_io = a.ex;
+  double* __restrict__ w_io = a.w;
+  double* __restrict__ wflx_io = a.wflx;
+  float* __restrict__ rho32 = a.rho32;
+  float* __restrict__ thv32 = a.thv32;
+  float* __restrict__ exp32 = a.exp32;
+  float* __restrict__ w32 = a.w32;
   double x_next = 0.0, w_next = 0.0;                 // half level h+1 (undamped, damped)
   double M_next = F64(F_M, N), ri_next = F64(F_RI, N);
   bool ok = true;
@@ -643,30 +653,30 @@ __device__ inline void mx_column_fac_item(const MxGeo& G, const MxColArgs& a, in
     const double ex_n = (F64(F_PX, h) - F64(F_GD, h) * Dt) - F64(F_GAM, h) * q;
     const double rho_n = (F64(F_RX, h) - dtau * LM(hdr, h)) - dtb * r;
     const float exp_n = f64_to_f32(ex_n - cc[CC_EXREF * ld + h]);
-    const float rho32 = f64_to_f32(rho_n);
+    const float rho_n32 = f64_to_f32(rho_n);
     if (CORR) {
       const double thv_n = Th_n * recip64(rho_n);
-      const double wold = LM(a.w, h);
-      LM(a.wflx, h) += rk * (kBeta * w + (1.0 - kBeta) * wold) * a.inv_nsub;
-      LM(a.rho, h) = rho_n;
-      LM(a.thv, h) = thv_n;
-      LM(a.ex, h) = ex_n;
-      LM(a.w, h) = w;
-      a.thv32[o + h] = f64_to_f32(thv_n);
+      const double wold = LM(w_io, h);
+      LM(wflx_io, h) += rk * (kBeta * w + (1.0 - kBeta) * wold) * a.inv_nsub;
+      LM(rho_io, h) = rho_n;
+      LM(thv_io, h) = thv_n;
+      LM(ex_io, h) = ex_n;
+      LM(w_io, h) = w;
+      thv32[o + h] = f64_to_f32(thv_n);
       ok = ok && finite64(thv_n) && finite64(ex_n) && finite64(w);
     } else {
-      a.thv32[o + h] = f64_to_f32(Th_n) / rho32;
+      thv32[o + h] = f64_to_f32(Th_n) / rho_n32;
       ok = ok && finite64(rho_n) && finite64(ex_n) && finite64(w);
     }
-    a.rho32[o + h] = rho32;
-    a.exp32[o + h] = exp_n;
-    a.w32[o + h] = f64_to_f32(w);
+    rho32[o + h] = rho_n32;
+    exp32[o + h] = exp_n;
+    w32[o + h] = f64_to_f32(w);
     x_next = x;
     w_next = w;
     M_next = Mk;
     ri_next = rk;
   }
-  a.w32[o + N] = 0.0f;
+  w32[o + N] = 0.0f;
   if (!ok) atomicOr(a.status, 1u);
 #undef LM
 #undef F64
@@ -751,10 +761,81 @@ __global__ void __launch_bounds__(512) k_mx_diff_edge(MxGeo G, float* vn, const 
   ITEM_PROLOGUE(LPE, G.ne)
   mx_diff_edge_item<LPE>(G, vn, ux, uy, uz, zeta, divc, thv, thflx, dt, item, lane);
 }
+// Gather step of the stored-factor column path for one state: a block takes 32
+// consecutive cells and walks the levels in chunks of LPE; lane groups of LPE
+// threads compute one cell's chunk (coalesced reads of its edge and cell rows), the
+// results are transposed through shared memory and written level-major as 32
+// consecutive cells per level (whole 128/256-byte lines instead of scattered words).
+// Same arithmetic as mx_cell_gather_item.
 template <int LPE, bool CORR>
-__global__ void __launch_bounds__(512) k_mx_cell_gather(MxGeo G, MxColArgs a) {
-  ITEM_PROLOGUE(LPE, G.nc)
-  mx_cell_gather_item<LPE, CORR>(G, a, item, lane);
+__global__ void __launch_bounds__(512) k_mx_gather_tile(MxGeo G, MxColArgs a) {
+  constexpr int CB = 32;
+  __shared__ double sh[4][LPE][CB + 1];                // hdr, hdt, hdg, hdw
+  __shared__ float sa[LPE][CB + 1];                    // Aw0
+  const int N = G.N, ld = G.ld;
+  const int64_t nc = G.nc, c0 = (int64_t)blockIdx.x * CB;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int grp = tid / LPE, ngrp = nthr / LPE, lane = tid % LPE;
+  for (int k0 = 0; k0 < N; k0 += LPE) {
+    if (CORR) {
+      for (int i = tid; i < LPE * CB; i += nthr) {
+        const int r = i / CB, cl = i % CB, h = k0 + r;
+        const int64_t c = c0 + cl;
+        sa[r][cl] = (h >= 1 && h < N && c < nc) ? a.Aw0[(int64_t)h * nc + c] : 0.0f;
+      }
+      __syncthreads();
+    }
+    for (int cl = grp; cl < CB; cl += ngrp) {
+      const int64_t c = c0 + cl;
+      if (c >= nc) break;
+      const int64_t o = c * ld;
+      int64_t E[3];
+      float sg[3], kw[3];
+      for (int s = 0; s < 3; ++s) {
+        E[s] = (int64_t)G.c2e[3 * c + s] * ld;
+        sg[s] = G.s_ce32[3 * c + s];
+        kw[s] = G.kin_w32[3 * c + s];
+      }
+      const double invA = G.inv_Ac[c];
+      const float invA32 = (float)invA;
+      const int k = k0 + lane;
+      if (k < N) {
+        const float p0 = sg[0] * a.phi[E[0] + k], p1 = sg[1] * a.phi[E[1] + k], p2 = sg[2] * a.phi[E[2] + k];
+        sh[0][lane][cl] = ((f32_to_f64(p0) + f32_to_f64(p1)) + f32_to_f64(p2)) * invA;
+        sh[1][lane][cl] =
+            f32_to_f64((sg[0] * a.gth[E[0] + k] + sg[1] * a.gth[E[1] + k] + sg[2] * a.gth[E[2] + k]) * invA32);
+        if (!CORR) {
+          const float pi = a.exp32n[o + k] + a.exref32[k];
+          sh[2][lane][cl] = f32_to_f64(kRcvF * (pi / (a.rho32n[o + k] * a.thv32n[o + k])));
+        }
+      }
+      if (k >= 1 && k < N) {
+        const float hadv = kw[0] * a.a_e[E[0] + k] + kw[1] * a.a_e[E[1] + k] + kw[2] * a.a_e[E[2] + k];
+        const float ws = a.w_stage[o + k];
+        float Aw = -hadv - ws * (a.w_stage[o + k - 1] - a.w_stage[o + k + 1]) * G.inv_dz2_32[k];
+        if (CORR) Aw = 0.5f * (sa[lane][cl] + Aw);
+        else sa[lane][cl] = Aw;
+        sh[3][lane][cl] = f32_to_f64(Aw);
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < LPE * CB; i += nthr) {
+      const int r = i / CB, cl = i % CB, k = k0 + r;
+      const int64_t c = c0 + cl;
+      if (c >= nc) continue;
+      const int64_t j = (int64_t)k * nc + c;
+      if (k < N) {
+        a.hdr[j] = sh[0][r][cl];
+        a.hdt[j] = sh[1][r][cl];
+        if (!CORR) a.hdg[j] = sh[2][r][cl];
+      }
+      if (k >= 1 && k < N) {
+        a.hdw[j] = sh[3][r][cl];
+        if (!CORR) a.Aw0[j] = sa[r][cl];
+      }
+    }
+    __syncthreads();
+  }
 }
 template <int NMAX, bool CORR>
 __global__ void __launch_bounds__(128) k_mx_column(MxGeo G, MxColArgs a) {
@@ -862,10 +943,12 @@ void launch_kind(int kind, const TileChoice& t, const MxGeo& G, StateDev& s, con
         k_mx_diff_vertex<32><<<item_blocks(G.nv + G.nc, 32, B), B, 0, st>>>(G, s.vn32, s.uvx32, s.uvy32, s.uvz32,
                                                                          s.zeta32, s.Kc32);
       break;
-    case K_MX_COLUMN_PREP:   // the predictor's gather (the corrector's only differs in the Aw0 average)
-      if (l16) k_mx_cell_gather<16, false><<<item_blocks(G.nc, 16, B), B, 0, st>>>(G, ca);
-      else k_mx_cell_gather<32, false><<<item_blocks(G.nc, 32, B), B, 0, st>>>(G, ca);
+    case K_MX_COLUMN_PREP: {   // the predictor's gather (the corrector's only differs in the Aw0 average)
+      const unsigned nb = (unsigned)((G.nc + 31) / 32);
+      if (l16) k_mx_gather_tile<16, false><<<nb, B, 0, st>>>(G, ca);
+      else k_mx_gather_tile<32, false><<<nb, B, 0, st>>>(G, ca);
       break;
+    }
     case K_MX_DIFF_EDGE:
       if (l16)
         k_mx_diff_edge<16><<<item_blocks(G.ne, 16, B), B, 0, st>>>(G, s.vn32, s.uvx32, s.uvy32, s.uvz32, s.zeta32,
@@ -1000,13 +1083,14 @@ void enqueue_step_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream
       }
       if (s.fac64) {
         const TileChoice t = tile(K_MX_COLUMN_PREP);
+        const unsigned nb = (unsigned)((nc + 31) / 32);
         prof_begin(stream, K_MX_COLUMN_PREP);
         if (corr) {
-          if (t.lanes == 16) k_mx_cell_gather<16, true><<<item_blocks(nc, 16, t.block), t.block, 0, stream>>>(G, ca);
-          else k_mx_cell_gather<32, true><<<item_blocks(nc, 32, t.block), t.block, 0, stream>>>(G, ca);
+          if (t.lanes == 16) k_mx_gather_tile<16, true><<<nb, t.block, 0, stream>>>(G, ca);
+          else k_mx_gather_tile<32, true><<<nb, t.block, 0, stream>>>(G, ca);
         } else {
-          if (t.lanes == 16) k_mx_cell_gather<16, false><<<item_blocks(nc, 16, t.block), t.block, 0, stream>>>(G, ca);
-          else k_mx_cell_gather<32, false><<<item_blocks(nc, 32, t.block), t.block, 0, stream>>>(G, ca);
+          if (t.lanes == 16) k_mx_gather_tile<16, false><<<nb, t.block, 0, stream>>>(G, ca);
+          else k_mx_gather_tile<32, false><<<nb, t.block, 0, stream>>>(G, ca);
         }
         prof_end(stream);
       }
