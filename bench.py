@@ -58,13 +58,15 @@ FP64_INSTR_PEAK = 505e9
 # instruction counts agree within 10 %.
 # FP64 step, per full level: rows kernel 28 (explicit predictors, linearised state
 # equation) + 5 (half-level interpolants) + 24 (w predictor and tridiagonal row),
-# Thomas 9, update 11 (corrector 16), finiteness checks on the integer pipe; executed
-# count (ncu, R2B6/90): 72 predictor, 78 corrector.
+# Thomas 9, update 11 (corrector 16), finiteness checks on the integer pipe: 77 to 82;
+# the executed count (ncu, R2B6/90) is 72 in the predictor and 78 in the corrector,
+# and the smaller average is the one used.
 COLUMN_FP64_OPS = 76
-# mixed step with stored factors: predictor 52 (one downward sweep forming and factoring
-# the rows, one upward sweep), corrector 28 (right-hand side, substitution, updates,
-# vertical mass flux).
-MX_COLUMN_FP64_OPS = 40
+# mixed step with stored factors: predictor 42 (one downward sweep forming and factoring
+# the rows, 39; the upward back substitution and damping, 3, with the provisional
+# state's FP32 shadows formed in FP32), corrector 28 (right-hand side, substitution,
+# FP64 updates, vertical mass flux).
+MX_COLUMN_FP64_OPS = 35
 # mixed step recomputing the factors in both stages (when the stored factors would
 # exceed a quarter of the device memory): about 66 in each stage.
 MX_COLUMN_RECOMPUTE_FP64_OPS = 66

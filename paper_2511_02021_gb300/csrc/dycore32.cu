@@ -635,26 +635,24 @@ __device__ inline void mx_column_fac_item(const MxGeo& G, const MxColArgs& a, in
   float* __restrict__ thv32 = a.thv32;
   float* __restrict__ exp32 = a.exp32;
   float* __restrict__ w32 = a.w32;
-  double x_next = 0.0, w_next = 0.0;                 // half level h+1 (undamped, damped)
-  double M_next = F64(F_M, N), ri_next = F64(F_RI, N);
   bool ok = true;
-  for (int h = N - 1; h >= 0; --h) {
-    double x = 0.0, w = 0.0;
-    if (h >= 1) {
-      x = LM(dps, h) - F64(F_CP, h) * x_next;
-      w = x * cc[CC_DAMP * ld + h];
-    }
-    const double Mk = F64(F_M, h), rk = F64(F_RI, h);
-    const double q = Mk * w - M_next * w_next;
-    const double r = rk * w - ri_next * w_next;
-    const double dtb = cc[CC_DTBDZ * ld + h];
-    const double Dt = LM(hdt, h);
-    const double Th_n = (F64(F_TX, h) - dtau * Dt) - dtb * q;
-    const double ex_n = (F64(F_PX, h) - F64(F_GD, h) * Dt) - F64(F_GAM, h) * q;
-    const double rho_n = (F64(F_RX, h) - dtau * LM(hdr, h)) - dtb * r;
-    const float exp_n = f64_to_f32(ex_n - cc[CC_EXREF * ld + h]);
-    const float rho_n32 = f64_to_f32(rho_n);
-    if (CORR) {
+  if (CORR) {
+    double x_next = 0.0, w_next = 0.0;               // half level h+1 (undamped, damped)
+    double M_next = F64(F_M, N), ri_next = F64(F_RI, N);
+    for (int h = N - 1; h >= 0; --h) {
+      double x = 0.0, w = 0.0;
+      if (h >= 1) {
+        x = LM(dps, h) - F64(F_CP, h) * x_next;
+        w = x * cc[CC_DAMP * ld + h];
+      }
+      const double Mk = F64(F_M, h), rk = F64(F_RI, h);
+      const double q = Mk * w - M_next * w_next;
+      const double r = rk * w - ri_next * w_next;
+      const double dtb = cc[CC_DTBDZ * ld + h];
+      const double Dt = LM(hdt, h);
+      const double Th_n = (F64(F_TX, h) - dtau * Dt) - dtb * q;
+      const double ex_n = (F64(F_PX, h) - F64(F_GD, h) * Dt) - F64(F_GAM, h) * q;
+      const double rho_n = (F64(F_RX, h) - dtau * LM(hdr, h)) - dtb * r;
       const double thv_n = Th_n * recip64(rho_n);
       const double wold = LM(w_io, h);
       LM(wflx_io, h) += rk * (kBeta * w + (1.0 - kBeta) * wold) * a.inv_nsub;
@@ -663,18 +661,49 @@ __device__ inline void mx_column_fac_item(const MxGeo& G, const MxColArgs& a, in
       LM(ex_io, h) = ex_n;
       LM(w_io, h) = w;
       thv32[o + h] = f64_to_f32(thv_n);
+      rho32[o + h] = f64_to_f32(rho_n);
+      exp32[o + h] = f64_to_f32(ex_n - cc[CC_EXREF * ld + h]);
+      w32[o + h] = f64_to_f32(w);
       ok = ok && finite64(thv_n) && finite64(ex_n) && finite64(w);
-    } else {
-      thv32[o + h] = f64_to_f32(Th_n) / rho_n32;
-      ok = ok && finite64(rho_n) && finite64(ex_n) && finite64(w);
+      x_next = x;
+      w_next = w;
+      M_next = Mk;
+      ri_next = rk;
     }
-    rho32[o + h] = rho_n32;
-    exp32[o + h] = exp_n;
-    w32[o + h] = f64_to_f32(w);
-    x_next = x;
-    w_next = w;
-    M_next = Mk;
-    ri_next = rk;
+  } else {
+    // The predictor's S* exists only as the FP32 shadows the corrector's stencils read:
+    // the back substitution and damping stay FP64, the implicit increments of rho,
+    // Theta and pi are formed in FP32 from the FP64 explicit parts (pi relative to
+    // its reference profile in FP64 first, since pi - pi_ref is what is stored).
+    const float dtau32 = f64_to_f32(dtau);
+    double x_next = 0.0;
+    float w_next = 0.0f, M_next = f64_to_f32(F64(F_M, N)), ri_next = f64_to_f32(F64(F_RI, N));
+    for (int h = N - 1; h >= 0; --h) {
+      double x = 0.0, w = 0.0;
+      if (h >= 1) {
+        x = LM(dps, h) - F64(F_CP, h) * x_next;
+        w = x * cc[CC_DAMP * ld + h];
+      }
+      const float w_f = f64_to_f32(w);
+      const float Mk = f64_to_f32(F64(F_M, h)), rk = f64_to_f32(F64(F_RI, h));
+      const float q = Mk * w_f - M_next * w_next;
+      const float r = rk * w_f - ri_next * w_next;
+      const float dtb = f64_to_f32(cc[CC_DTBDZ * ld + h]);
+      const float Dt = f64_to_f32(LM(hdt, h));
+      const float Th_n = (f64_to_f32(F64(F_TX, h)) - dtau32 * Dt) - dtb * q;
+      const float exp_n = (f64_to_f32(F64(F_PX, h) - cc[CC_EXREF * ld + h]) - f64_to_f32(F64(F_GD, h)) * Dt) -
+                          f64_to_f32(F64(F_GAM, h)) * q;
+      const float rho_n = (f64_to_f32(F64(F_RX, h)) - dtau32 * f64_to_f32(LM(hdr, h))) - dtb * r;
+      thv32[o + h] = Th_n / rho_n;
+      rho32[o + h] = rho_n;
+      exp32[o + h] = exp_n;
+      w32[o + h] = w_f;
+      ok = ok && isfinite(Th_n / rho_n) && isfinite(exp_n) && finite64(w);
+      x_next = x;
+      w_next = w_f;
+      M_next = Mk;
+      ri_next = rk;
+    }
   }
   w32[o + N] = 0.0f;
   if (!ok) atomicOr(a.status, 1u);
