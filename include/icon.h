@@ -159,7 +159,12 @@ void icon_grid_free(icon_grid* grid);
  * state borrows the grid, which must outlive it. */
 int icon_state_init(const icon_grid* grid, uint64_t seed, int case_id, icon_state** out);
 
-/* As icon_state_init with explicit parameters (params may be NULL). */
+/* As icon_state_init with explicit parameters (params may be NULL).
+ * A mixed-precision state stores the parts of the column system that the predictor
+ * and corrector share (17 level-major FP64 fields per cell) when they take at most a
+ * quarter of the device memory, and otherwise recomputes them in both stages. If the
+ * environment variable ICON_MIXED_RECOMPUTE is "1" when the state is created, it
+ * recomputes regardless (for testing the second form on small grids). */
 int icon_state_init_ex(const icon_grid* grid, uint64_t seed, int case_id,
                        const icon_case_params* params, icon_state** out);
 

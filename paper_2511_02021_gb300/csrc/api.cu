@@ -1,6 +1,7 @@
 // C ABI of the dycore library: argument checks, handle lifetimes, device memory
 // through the registered allocator, the recorded step graph and host copies.
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -237,7 +238,9 @@ int alloc_state(icon_state* st, int precision) {
     const size_t fac_bytes = (size_t)nc * (12 + 5) * (ld0 + 1) * 8;
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) total_b = 0;
-    if (fac_bytes <= total_b / 4) {
+    const char* force_recompute = getenv("ICON_MIXED_RECOMPUTE");
+    const bool recompute = force_recompute && force_recompute[0] == '1' && force_recompute[1] == '\0';
+    if (fac_bytes <= total_b / 4 && !recompute) {
       s.fac64 = A.get_n<double>((size_t)nc * 12 * (ld0 + 1));
       s.hdr = A.get_n<double>((size_t)nc * (ld0 + 1));
       s.hdt = A.get_n<double>((size_t)nc * (ld0 + 1));

@@ -424,15 +424,13 @@ __device__ inline void mx_column_item(const MxGeo& G, const MxColArgs& a, int64_
   for (int k = 0; k < N; ++k) {
     const int h1 = k + 1;
     const double wn1 = (h1 < N) ? dp[h1 - 1] * cc[CC_DAMP * ld + h1] : 0.0;
-    const double q = M[k] * wn_prev - M[k + 1] * wn1;
-    const double r = rho_ic[k] * wn_prev - rho_ic[k + 1] * wn1;
     const double dtb = cc[CC_DTBDZ * ld + k];
-    const double Th_n = Thx[k] - dtb * q;
-    const double ex_n = exx[k] - f32_to_f64(gam[k]) * q;
-    const double rho_n = rhox[k] - dtb * r;
-    const float exp_n = f64_to_f32(ex_n - cc[CC_EXREF * ld + k]);
-    const float rho32 = f64_to_f32(rho_n);
     if (CORR) {
+      const double q = M[k] * wn_prev - M[k + 1] * wn1;
+      const double r = rho_ic[k] * wn_prev - rho_ic[k + 1] * wn1;
+      const double Th_n = Thx[k] - dtb * q;
+      const double ex_n = exx[k] - f32_to_f64(gam[k]) * q;
+      const double rho_n = rhox[k] - dtb * r;
       const double thv_n = Th_n * recip64(rho_n);
       const double wold = LM(a.w, k);
       LM(a.wflx, k) += rho_ic[k] * (kBeta * wn_prev + (1.0 - kBeta) * wold) * a.inv_nsub;
@@ -441,13 +439,24 @@ __device__ inline void mx_column_item(const MxGeo& G, const MxColArgs& a, int64_
       LM(a.ex, k) = ex_n;
       LM(a.w, k) = wn_prev;
       a.thv32[o + k] = f64_to_f32(thv_n);
+      a.rho32[o + k] = f64_to_f32(rho_n);
+      a.exp32[o + k] = f64_to_f32(ex_n - cc[CC_EXREF * ld + k]);
       ok = ok && finite64(thv_n) && finite64(ex_n) && finite64(wn_prev);
     } else {
-      a.thv32[o + k] = f64_to_f32(Th_n) / rho32;
-      ok = ok && finite64(rho_n) && finite64(ex_n) && finite64(wn_prev);
+      // provisional state: FP32 shadows formed in FP32 from the FP64 solve (as in the
+      // stored-factor path)
+      const float wf = f64_to_f32(wn_prev), wf1 = f64_to_f32(wn1), dtb32 = f64_to_f32(dtb);
+      const float q = f64_to_f32(M[k]) * wf - f64_to_f32(M[k + 1]) * wf1;
+      const float r = f64_to_f32(rho_ic[k]) * wf - f64_to_f32(rho_ic[k + 1]) * wf1;
+      const float Th_n = f64_to_f32(Thx[k]) - dtb32 * q;
+      const float exp_n = f64_to_f32(exx[k] - cc[CC_EXREF * ld + k]) - gam[k] * q;
+      const float rho_n = f64_to_f32(rhox[k]) - dtb32 * r;
+      const float thv_n = Th_n / rho_n;
+      a.thv32[o + k] = thv_n;
+      a.rho32[o + k] = rho_n;
+      a.exp32[o + k] = exp_n;
+      ok = ok && isfinite(thv_n) && isfinite(exp_n) && finite64(wn_prev);
     }
-    a.rho32[o + k] = rho32;
-    a.exp32[o + k] = exp_n;
     a.w32[o + k] = f64_to_f32(wn_prev);
     wn_prev = wn1;
   }
@@ -470,46 +479,6 @@ __device__ inline void mx_column_item(const MxGeo& G, const MxColArgs& a, int64_
 // cell-level: about 60 operations in the predictor and 40 in the corrector, against
 // about 70 in each stage when both compute everything.
 enum { F_LO = 0, F_RP, F_CP, F_WX, F_AA, F_M, F_RI, F_RX, F_TX, F_PX, F_GD, F_GAM, F_COUNT64 };  // FP64 [f][h][Nc]
-
-// Gather step of the stored-factor column path for one cell (the persistent ensemble's
-// form; single states use the shared-memory transposing k_mx_gather_tile): lanes over
-// levels (coalesced gathers of the three edge rows), writes the cell's horizontal
-// divergences and w-advection tendency level-major so that the thread-per-column
-// solve reads them coalesced.
-template <int LPE, bool CORR>
-__device__ inline void mx_cell_gather_item(const MxGeo& G, const MxColArgs& a, int64_t c, int lane) {
-  const int N = G.N, ld = G.ld;
-  const int64_t nc = G.nc, o = c * ld;
-  int64_t E[3];
-  float sg[3], kw[3];
-  for (int s = 0; s < 3; ++s) {
-    E[s] = (int64_t)G.c2e[3 * c + s] * ld;
-    sg[s] = G.s_ce32[3 * c + s];
-    kw[s] = G.kin_w32[3 * c + s];
-  }
-  const double invA = G.inv_Ac[c];
-  const float invA32 = (float)invA;
-  for (int k = lane; k < N; k += LPE) {
-    const float p0 = sg[0] * a.phi[E[0] + k], p1 = sg[1] * a.phi[E[1] + k], p2 = sg[2] * a.phi[E[2] + k];
-    a.hdr[(int64_t)k * nc + c] = ((f32_to_f64(p0) + f32_to_f64(p1)) + f32_to_f64(p2)) * invA;
-    a.hdt[(int64_t)k * nc + c] =
-        f32_to_f64((sg[0] * a.gth[E[0] + k] + sg[1] * a.gth[E[1] + k] + sg[2] * a.gth[E[2] + k]) * invA32);
-    if (!CORR) {
-      // coefficient of the linearised state equation at S^n, from the FP32 shadows
-      const float pi = a.exp32n[o + k] + a.exref32[k];
-      a.hdg[(int64_t)k * nc + c] = f32_to_f64(kRcvF * (pi / (a.rho32n[o + k] * a.thv32n[o + k])));
-    }
-  }
-  for (int h = lane + 1; h < N; h += LPE) {
-    const float hadv = kw[0] * a.a_e[E[0] + h] + kw[1] * a.a_e[E[1] + h] + kw[2] * a.a_e[E[2] + h];
-    const float ws = a.w_stage[o + h];
-    float Aw = -hadv - ws * (a.w_stage[o + h - 1] - a.w_stage[o + h + 1]) * G.inv_dz2_32[h];
-    const int64_t i = (int64_t)h * nc + c;
-    if (CORR) Aw = 0.5f * (a.Aw0[i] + Aw);
-    else a.Aw0[i] = Aw;
-    a.hdw[i] = f32_to_f64(Aw);
-  }
-}
 
 template <int NMAX, bool CORR>
 __device__ inline void mx_column_fac_item(const MxGeo& G, const MxColArgs& a, int64_t c) {
@@ -795,14 +764,21 @@ __global__ void __launch_bounds__(512) k_mx_diff_edge(MxGeo G, float* vn, const 
 // threads compute one cell's chunk (coalesced reads of its edge and cell rows), the
 // results are transposed through shared memory and written level-major as 32
 // consecutive cells per level (whole 128/256-byte lines instead of scattered words).
-// Same arithmetic as mx_cell_gather_item.
+constexpr int kGatherCells = 32;
+template <int LPE>
+struct GatherTile {
+  double sh[4][LPE][kGatherCells + 1];                 // hdr, hdt, hdg, hdw
+  float sa[LPE][kGatherCells + 1];                     // Aw0
+};
+
+// one tile of 32 cells starting at c0; every thread of the block takes part
 template <int LPE, bool CORR>
-__global__ void __launch_bounds__(512) k_mx_gather_tile(MxGeo G, MxColArgs a) {
-  constexpr int CB = 32;
-  __shared__ double sh[4][LPE][CB + 1];                // hdr, hdt, hdg, hdw
-  __shared__ float sa[LPE][CB + 1];                    // Aw0
+__device__ inline void mx_gather_tile_body(const MxGeo& G, const MxColArgs& a, int64_t c0, GatherTile<LPE>& T) {
+  constexpr int CB = kGatherCells;
+  auto& sh = T.sh;
+  auto& sa = T.sa;
   const int N = G.N, ld = G.ld;
-  const int64_t nc = G.nc, c0 = (int64_t)blockIdx.x * CB;
+  const int64_t nc = G.nc;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int grp = tid / LPE, ngrp = nthr / LPE, lane = tid % LPE;
   for (int k0 = 0; k0 < N; k0 += LPE) {
@@ -866,6 +842,13 @@ __global__ void __launch_bounds__(512) k_mx_gather_tile(MxGeo G, MxColArgs a) {
     __syncthreads();
   }
 }
+
+template <int LPE, bool CORR>
+__global__ void __launch_bounds__(512) k_mx_gather_tile(MxGeo G, MxColArgs a) {
+  __shared__ GatherTile<LPE> T;
+  mx_gather_tile_body<LPE, CORR>(G, a, (int64_t)blockIdx.x * kGatherCells, T);
+}
+
 template <int NMAX, bool CORR>
 __global__ void __launch_bounds__(128) k_mx_column(MxGeo G, MxColArgs a) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1210,9 +1193,13 @@ int selftest_conversions(int64_t n, unsigned* host_fails) {
 // (vertex, edge diagnostics, cell kinetic energy, edge tendency, column solve for
 // predictor and corrector, then the diffusion phases) is a static work list over
 // (member, entity) or (member, column) shared by all blocks, separated by a grid
-// barrier. The barrier spins a bounded number of times; if it runs out it sets the
-// timeout bit of the status word, every block leaves at its next barrier and the
-// kernel returns normally.
+// barrier. The column-input gather is a work list over (member, 32-cell tile) taken
+// by whole blocks. Blocks of 128 threads held to 64 registers and a 21 KB gather tile
+// keep 8 blocks (32 warps) on every SM: the stencil phases are latency bound and gain
+// more from occupancy than they lose to the few spilled kernel-level registers. The
+// barrier spins a bounded number of times; if it runs out it sets the timeout bit of
+// the status word, every block leaves at its next barrier and the kernel returns
+// normally.
 namespace {
 
 struct MemberDev {
@@ -1227,13 +1214,14 @@ struct MemberDev {
   double *thv, *ex;
   double dtau, dt;
   int64_t off_v, off_e, off_c;  // this member's first item in each work list
+  int64_t off_t;                // first 32-cell tile of the column-input gather
 };
 
 struct EnsArgs {
   const MemberDev* m;
   int nm;
   int nsub;
-  int64_t tot_v, tot_e, tot_c;
+  int64_t tot_v, tot_e, tot_c, tot_t;
   unsigned* bar;                // [0] arrivals, [1] generation
   unsigned* status;             // ensemble status word (bit 1: barrier timeout)
   long long spin_limit;
@@ -1248,6 +1236,25 @@ __device__ inline int find_member(const int64_t* off, int nm, int64_t item) {
     else hi = mid - 1;
   }
   return lo;
+}
+
+// warp-level work list: warp w takes items [K w, K w + K), then the next chunk K * nwarps
+// further on; the member is looked up once per chunk and advanced at member boundaries
+template <int K, typename F>
+__device__ inline void warp_items(const int64_t* off, int nm, int64_t tot, int64_t gwarp, int64_t nwarps, F f) {
+  for (int64_t i0 = gwarp * K; i0 < tot; i0 += nwarps * K) {
+    int m = find_member(off, nm, i0);
+    int64_t next = m + 1 < nm ? off[m + 1] : tot;
+    for (int j = 0; j < K; ++j) {
+      const int64_t i = i0 + j;
+      if (i >= tot) break;
+      while (i >= next) {
+        ++m;
+        next = m + 1 < nm ? off[m + 1] : tot;
+      }
+      f(m, i - off[m]);
+    }
+  }
 }
 
 // bounded grid barrier; returns false (for every thread of the block) once any block gave up
@@ -1286,13 +1293,17 @@ __device__ bool grid_barrier(const EnsArgs& A, bool skip) {
   return s_ok != 0;
 }
 
-template <int NMAX>
-__global__ void __launch_bounds__(128) k_ensemble_step(EnsArgs A) {
-  __shared__ int64_t s_off_v[64], s_off_e[64], s_off_c[64];
+constexpr int kChunk = 4;   // consecutive work items per warp
+
+template <int NMAX, bool ALLFAC>
+__global__ void __launch_bounds__(128, 8) k_ensemble_step(EnsArgs A) {
+  __shared__ int64_t s_off_v[64], s_off_e[64], s_off_c[64], s_off_t[64];
+  __shared__ GatherTile<16> tileT;
   for (int i = threadIdx.x; i < A.nm; i += blockDim.x) {
     s_off_v[i] = A.m[i].off_v;
     s_off_e[i] = A.m[i].off_e;
     s_off_c[i] = A.m[i].off_c;
+    s_off_t[i] = A.m[i].off_t;
   }
   __syncthreads();
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
@@ -1317,43 +1328,46 @@ __global__ void __launch_bounds__(128) k_ensemble_step(EnsArgs A) {
   if (!sync()) return;
   for (int it = 0; it < A.nsub; ++it) {
     for (int stage = 0; stage < 2; ++stage) {
-      for (int64_t i = gwarp; i < A.tot_v; i += nwarps) {
-        const int m = find_member(s_off_v, A.nm, i);
+      warp_items<kChunk>(s_off_v, A.nm, A.tot_v, gwarp, nwarps, [&](int m, int64_t j) {
         const MemberDev& M = A.m[m];
-        mx_vertex_item<32>(M.G, M.ea[stage].vn, M.ea[stage].w, M.zeta32, M.wv32, i - M.off_v, lane);
-      }
+        mx_vertex_item<32>(M.G, M.ea[stage].vn, M.ea[stage].w, M.zeta32, M.wv32, j, lane);
+      });
       if (!sync()) return;
-      for (int64_t i = gwarp; i < A.tot_e; i += nwarps) {
-        const int m = find_member(s_off_e, A.nm, i);
+      warp_items<kChunk>(s_off_e, A.nm, A.tot_e, gwarp, nwarps, [&](int m, int64_t j) {
         const MemberDev& M = A.m[m];
-        mx_edge_diag_item<32>(M.G, M.ea[stage].vn, M.vt32, i - M.off_e, lane);
-      }
+        mx_edge_diag_item<32>(M.G, M.ea[stage].vn, M.vt32, j, lane);
+      });
       if (!sync()) return;
-      for (int64_t i = gwarp; i < A.tot_c; i += nwarps) {
-        const int m = find_member(s_off_c, A.nm, i);
+      warp_items<kChunk>(s_off_c, A.nm, A.tot_c, gwarp, nwarps, [&](int m, int64_t j) {
         const MemberDev& M = A.m[m];
-        mx_cell_ke_item<32>(M.G, M.ea[stage].vn, M.vt32, M.Kc32, i - M.off_c, lane);
-      }
+        mx_cell_ke_item<32>(M.G, M.ea[stage].vn, M.vt32, M.Kc32, j, lane);
+      });
       if (!sync()) return;
-      for (int64_t i = gwarp; i < A.tot_e; i += nwarps) {
-        const int m = find_member(s_off_e, A.nm, i);
+      warp_items<kChunk>(s_off_e, A.nm, A.tot_e, gwarp, nwarps, [&](int m, int64_t j) {
         const MemberDev& M = A.m[m];
-        mx_edge_tend_item<32>(M.G, M.ea[stage], i - M.off_e, lane);
-      }
+        mx_edge_tend_item<32>(M.G, M.ea[stage], j, lane);
+      });
       if (!sync()) return;
-      for (int64_t i = gwarp; i < A.tot_c; i += nwarps) {
-        const int m = find_member(s_off_c, A.nm, i);
+      // column-input gather: one 32-cell tile per block at a time (members without
+      // stored factors have no tiles)
+      for (int64_t t = blockIdx.x; t < A.tot_t; t += gridDim.x) {
+        const int m = find_member(s_off_t, A.nm, t);
         const MemberDev& M = A.m[m];
-        if (!M.ca[stage].fac64) continue;
-        if (stage == 0) mx_cell_gather_item<32, false>(M.G, M.ca[0], i - M.off_c, lane);
-        else mx_cell_gather_item<32, true>(M.G, M.ca[1], i - M.off_c, lane);
+        const int64_t c0 = (t - M.off_t) * kGatherCells;
+        if (stage == 0) mx_gather_tile_body<16, false>(M.G, M.ca[0], c0, tileT);
+        else mx_gather_tile_body<16, true>(M.G, M.ca[1], c0, tileT);
       }
       if (!sync()) return;
       for (int64_t i = gtid; i < A.tot_c; i += nthreads) {
         const int m = find_member(s_off_c, A.nm, i);
         const MemberDev& M = A.m[m];
-        if (stage == 0) mx_column_any<NMAX, false>(M.G, M.ca[0], i - M.off_c);
-        else mx_column_any<NMAX, true>(M.G, M.ca[1], i - M.off_c);
+        if (ALLFAC) {
+          if (stage == 0) mx_column_fac_item<NMAX, false>(M.G, M.ca[0], i - M.off_c);
+          else mx_column_fac_item<NMAX, true>(M.G, M.ca[1], i - M.off_c);
+        } else {
+          if (stage == 0) mx_column_any<NMAX, false>(M.G, M.ca[0], i - M.off_c);
+          else mx_column_any<NMAX, true>(M.G, M.ca[1], i - M.off_c);
+        }
       }
       if (!sync()) return;
     }
@@ -1372,12 +1386,11 @@ __global__ void __launch_bounds__(128) k_ensemble_step(EnsArgs A) {
     }
   }
   if (!sync()) return;
-  for (int64_t i = gwarp; i < A.tot_e; i += nwarps) {
-    const int m = find_member(s_off_e, A.nm, i);
+  warp_items<kChunk>(s_off_e, A.nm, A.tot_e, gwarp, nwarps, [&](int m, int64_t j) {
     const MemberDev& M = A.m[m];
     mx_diff_edge_item<32>(M.G, M.vn32, M.uvx32, M.uvy32, M.uvz32, M.zeta32, M.Kc32, M.thv32, M.vt32, (float)M.dt,
-                          i - M.off_e, lane);
-  }
+                          j, lane);
+  });
   if (!sync()) return;
   for (int64_t i = gtid; i < A.tot_c; i += nthreads) {
     const int m = find_member(s_off_c, A.nm, i);
@@ -1415,8 +1428,9 @@ int ensemble_prepare(EnsembleDev& E, icon_state* const* members, int n, const do
     return ICON_EINVAL;
   }
   std::vector<MemberDev> host(n);
-  int64_t ov = 0, oe = 0, oc = 0;
+  int64_t ov = 0, oe = 0, oc = 0, ot = 0;
   int N = -1;
+  bool all_fac = true;
   for (int i = 0; i < n; ++i) {
     icon_state* st = members[i];
     StateDev& s = st->s;
@@ -1442,11 +1456,14 @@ int ensemble_prepare(EnsembleDev& E, icon_state* const* members, int n, const do
     M.vn32 = s.vn32; M.uvx32 = s.uvx32; M.uvy32 = s.uvy32; M.uvz32 = s.uvz32; M.zeta32 = s.zeta32;
     M.Kc32 = s.Kc32; M.thv32 = s.thv32; M.exp32 = s.exp32; M.thv = s.thv; M.ex = s.ex;
     M.wv32 = s.wv32; M.vt32 = s.vt32;
-    M.off_v = ov; M.off_e = oe; M.off_c = oc;
+    M.off_v = ov; M.off_e = oe; M.off_c = oc; M.off_t = ot;
     ov += M.G.nv; oe += M.G.ne; oc += M.G.nc;
+    if (s.fac64) ot += (M.G.nc + kGatherCells - 1) / kGatherCells;
+    else all_fac = false;
   }
   E.N = N;
-  E.tot_v = ov; E.tot_e = oe; E.tot_c = oc;
+  E.tot_v = ov; E.tot_e = oe; E.tot_c = oc; E.tot_t = ot;
+  E.all_fac = all_fac;
   E.nm = n;
   E.nsub = nsub;
   if (!E.members) {
@@ -1470,15 +1487,15 @@ int ensemble_launch(EnsembleDev& E, cudaStream_t st) {
   A.m = static_cast<const MemberDev*>(E.members);
   A.nm = E.nm;
   A.nsub = E.nsub;
-  A.tot_v = E.tot_v; A.tot_e = E.tot_e; A.tot_c = E.tot_c;
+  A.tot_v = E.tot_v; A.tot_e = E.tot_e; A.tot_c = E.tot_c; A.tot_t = E.tot_t;
   A.bar = E.bar;
   A.status = E.bar + 8;
   A.spin_limit = E.spin_limit;
   A.skip_first_barrier = E.test_skip_barrier;
   void (*kern)(EnsArgs);
-  if (E.N <= 32) kern = k_ensemble_step<32>;
-  else if (E.N <= 64) kern = k_ensemble_step<64>;
-  else if (E.N <= 96) kern = k_ensemble_step<96>;
+  if (E.N <= 32) kern = E.all_fac ? k_ensemble_step<32, true> : k_ensemble_step<32, false>;
+  else if (E.N <= 64) kern = E.all_fac ? k_ensemble_step<64, true> : k_ensemble_step<64, false>;
+  else if (E.N <= 96) kern = E.all_fac ? k_ensemble_step<96, true> : k_ensemble_step<96, false>;
   else {
     set_error("icon_ensemble_step: the persistent ensemble supports up to 96 levels");
     return ICON_EINVAL;

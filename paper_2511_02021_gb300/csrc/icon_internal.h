@@ -188,7 +188,8 @@ struct EnsembleDev {
   void* members = nullptr;     // MemberDev[64]
   unsigned* bar = nullptr;     // [0] arrivals, [1] generation, [8] status
   int nm = 0, nsub = 0, N = 0, grid_blocks = 0;
-  int64_t tot_v = 0, tot_e = 0, tot_c = 0;
+  int64_t tot_v = 0, tot_e = 0, tot_c = 0, tot_t = 0;
+  bool all_fac = true;         // every member stores its column factors
   long long spin_limit = 1ll << 24;
   int test_skip_barrier = 0;
 };

@@ -65,9 +65,14 @@ def test_mixed_initial_state(gpu):
         C.icon_grid_free(grid)
 
 
+@pytest.mark.parametrize("recompute", [False, True], ids=["stored-factors", "recompute"])
 @pytest.mark.parametrize("bis,nlev,case,dt,noise", [(2, 20, 1, 300.0, 0.01), (3, 30, 2, 150.0, 0.1),
                                                     (1, 60, 3, 400.0, 0.0)])
-def test_mixed_one_step_vs_oracle(gpu, bis, nlev, case, dt, noise):
+def test_mixed_one_step_vs_oracle(gpu, monkeypatch, bis, nlev, case, dt, noise, recompute):
+    """Both forms of the mixed column (stored shared factors, or recomputed in each
+    stage, as on grids whose factors would not fit) against the FP64 oracle."""
+    if recompute:
+        monkeypatch.setenv("ICON_MIXED_RECOMPUTE", "1")
     out, m0, m1 = gpu_run(gpu, bis, nlev, 6, case, dt, 5, 1, gpu.ICON_MIXED, noise)
     ref = oracle_run(bis, nlev, 6, case, dt, 5, 1, noise)
     assert rel_l2(out["vn"], ref["vn"]) <= TOL_WIND
@@ -101,3 +106,16 @@ def test_integer_pipe_conversions_match_hardware(gpu):
     """The FP32<->FP64 conversions built from the IEEE-754 encodings agree bit for bit
     with the hardware conversions on 2^22 random finite inputs and halfway cases."""
     assert gpu.icon_selftest(1 << 22) == 0
+
+
+def test_mixed_column_forms_agree(gpu, monkeypatch):
+    """R2B4 / 60 levels, 2 steps: the recomputing column against the stored-factor one
+    (different operation order, same arithmetic precision per term)."""
+    a, am0, am1 = gpu_run(gpu, 4, 60, 3, 2, 240.0, 5, 2, gpu.ICON_MIXED, 0.1)
+    monkeypatch.setenv("ICON_MIXED_RECOMPUTE", "1")
+    b, bm0, bm1 = gpu_run(gpu, 4, 60, 3, 2, 240.0, 5, 2, gpu.ICON_MIXED, 0.1)
+    assert rel_l2(b["vn"], a["vn"]) <= TOL_WIND
+    for f in ("rho", "theta_v", "exner"):
+        assert rel_l2(b[f], a[f]) <= thermo_bound_mixed(240.0, 5, 2, d_min(4)), f
+    assert np.sqrt(np.mean((b["w"] - a["w"]) ** 2)) <= w_bound_mixed(240.0, 5, 2)
+    assert abs(am1 / am0 - 1) <= 1e-13 and abs(bm1 / bm0 - 1) <= 1e-13
