@@ -582,6 +582,7 @@ __device__ inline void mx_column_fac_item(const MxGeo& G, const MxColArgs& a, in
   } else {
     // ---- corrector: stage right-hand side with the stored rows and factors
     double dp_prev = 0.0, exx_prev = 0.0;
+    #pragma unroll 4   // lets the loads of four levels overlap (latency bound)
     for (int k = 0; k < N; ++k) {
       const double exx = F64(F_PX, k) - F64(F_GD, k) * LM(hdt, k);
       if (k >= 1) {
@@ -608,6 +609,7 @@ __device__ inline void mx_column_fac_item(const MxGeo& G, const MxColArgs& a, in
   if (CORR) {
     double x_next = 0.0, w_next = 0.0;               // half level h+1 (undamped, damped)
     double M_next = F64(F_M, N), ri_next = F64(F_RI, N);
+    #pragma unroll 4   // lets the loads of four levels overlap (latency bound)
     for (int h = N - 1; h >= 0; --h) {
       double x = 0.0, w = 0.0;
       if (h >= 1) {
@@ -738,7 +740,7 @@ __global__ void __launch_bounds__(512) k_mx_cell_ke(MxGeo G, const float* vn, co
   mx_cell_ke_item<LPE>(G, vn, vt, Kc, item, lane);
 }
 template <int LPE>
-__global__ void __launch_bounds__(512, LPE == 32 ? 2 : 1) k_mx_edge_tend(MxGeo G, MxEdgeArgs a) {
+__global__ void __launch_bounds__(512, 2) k_mx_edge_tend(MxGeo G, MxEdgeArgs a) {
   ITEM_PROLOGUE(LPE, G.ne)
   mx_edge_tend_item<LPE>(G, a, item, lane);
 }
