@@ -48,28 +48,37 @@ def peaks():
     return 6800.0, "fallback"
 
 
-# FP64 arithmetic-instruction rate of the GB300 measured with an FMA/ADD throughput
-# probe on this pool (505 G instr/s; NVIDIA's nominal 1.25 TFLOP/s FMA is 625 G instr/s
-# at 2.07 GHz). Used as the peak of kernels bound by FP64 arithmetic.
-FP64_INSTR_PEAK = 505e9
-# FP64 arithmetic per cell-level of one launch of the column solves, counted from the
-# kernel source as FP64 instructions (a fused multiply-add is one, the Newton-Raphson
-# reciprocal three), averaged over predictor and corrector; ncu's executed FP64
-# instruction counts agree within 10 %.
-# FP64 step, per full level: rows kernel 28 (explicit predictors, linearised state
-# equation) + 5 (half-level interpolants) + 24 (w predictor and tridiagonal row),
-# Thomas 9, update 11 (corrector 16), finiteness checks on the integer pipe: 77 to 82;
-# the executed count (ncu, R2B6/90) is 72 in the predictor and 78 in the corrector,
-# and the smaller average is the one used.
-COLUMN_FP64_OPS = 76
+# Peak FP64 instruction rate of the GB300, from its unit counts and clock: 152 SMs x 2 FP64
+# operations per SM per cycle (a fused multiply-add is one) x 2.07 GHz = 629 G/s; NVIDIA's
+# nominal 1.25 TFLOP/s counts an FMA as two. ncu's "FP64 pipe active" percentages are
+# relative to the same rate. An FMA/ADD throughput probe of this machine sustained 505 G/s.
+FP64_INSTR_PEAK = 152 * 2 * 2.07e9
+# FP64 instructions per cell-level of one launch of the column solves (a fused multiply-add
+# is one, the Newton-Raphson reciprocal three), averaged over predictor and corrector,
+# counted from the kernel source and checked against ncu's executed counts
+# (profiles/ncu_fp64_column_edge_r2b6_l90.md, profiles/ncu_mixed_column_stencils_r2b6_l90.md).
+# FP64 step: rows kernel 28 (explicit predictors, linearised state equation) + 5 (half-level
+# interpolants) + 24 (w predictor and tridiagonal row), Thomas 9, update 11 (corrector 16);
+# executed 71.8 (predictor) and 77.7 (corrector).
+COLUMN_FP64_OPS = 75
 # mixed step with stored factors: predictor 42 (one downward sweep forming and factoring
-# the rows, 39; the upward back substitution and damping, 3, with the provisional
-# state's FP32 shadows formed in FP32), corrector 28 (right-hand side, substitution,
-# FP64 updates, vertical mass flux).
-MX_COLUMN_FP64_OPS = 35
-# mixed step recomputing the factors in both stages (when the stored factors would
-# exceed a quarter of the device memory): about 66 in each stage.
-MX_COLUMN_RECOMPUTE_FP64_OPS = 66
+# the rows, 39; the upward back substitution and damping, 3, with the provisional state's
+# FP32 shadows formed in FP32), corrector 28 (right-hand side, substitution, FP64 updates,
+# vertical mass flux); executed 42.7 and 29.4.
+MX_COLUMN_FP64_OPS = 36
+# mixed step recomputing the factors in both stages (when the stored factors would exceed a
+# quarter of the device memory): executed 47.5 (predictor) and 64.5 (corrector).
+MX_COLUMN_RECOMPUTE_FP64_OPS = 56
+# DRAM bytes (read + write) per launch of the dominant kernel kind, from ncu captures of the
+# current kernels (mean of predictor and corrector; same files): FP64 column at R2B6/90
+# measured; mixed column at R2B6/90 measured and scaled by cells to R2B8/90; recomputing
+# mixed column measured at R2B5/60 and scaled by cells to R2B9/60.
+NCU_TRAFFIC = {
+    ("R2B6-L90-jet-fp64", "column_solve"): 10.07e9,
+    ("R2B6-L90-jet-fp64", "mx_column_solve"): 8.37e9,
+    ("R2B8-L90-jet-mixed", "mx_column_solve"): 8.37e9 * 16,
+    ("R2B9-L60-jet-mixed", "mx_column_solve"): 1.627e9 * 256,
+}
 
 
 def counts(wl):
@@ -276,18 +285,24 @@ def run_gpu(args, wl, rank, world, local_rank):
         alu_frac = top[5] / FP64_INSTR_PEAK if top[5] else None
         if alu_frac is not None and hbm_frac is not None and alu_frac > hbm_frac:
             roof = {"kernel": top[1], "bound": "alu", "achieved": top[5] / 1e9, "peak": FP64_INSTR_PEAK / 1e9,
-                    "unit": "GFLOP/s (FP64)", "frac": alu_frac, "traffic": None,
+                    "unit": "G FP64 instr/s", "frac": alu_frac, "traffic": NCU_TRAFFIC.get((wl.name, top[1])),
+                    "peak_source": "derived: 152 SMs x 2 FP64/cycle x 2.07 GHz",
                     "hbm": {"achieved": top[4], "peak": hbm_peak, "unit": "GB/s", "frac": hbm_frac,
                             "peak_source": peak_src},
                     "launch_ms": top[2], "launches_per_step": top[3]}
         else:
             roof = {"kernel": top[1], "bound": "hbm", "achieved": top[4], "peak": hbm_peak, "unit": "GB/s",
-                    "frac": hbm_frac, "traffic": None, "peak_source": peak_src, "launch_ms": top[2],
+                    "frac": hbm_frac, "traffic": NCU_TRAFFIC.get((wl.name, top[1])), "peak_source": peak_src,
+                    "launch_ms": top[2],
                     "launches_per_step": top[3],
                     "fp64": {"achieved": (top[5] or 0) / 1e9, "peak": FP64_INSTR_PEAK / 1e9,
-                             "unit": "GFLOP/s", "frac": alu_frac}}
+                             "unit": "G FP64 instr/s", "frac": alu_frac}}
         tot = sum(x[0] for x in rows)
         breakdown = {r[1]: {"ms_per_step": round(r[0], 4), "share": round(r[0] / tot, 4)} for r in rows}
+        # the per-kind durations come from two eager steps right after the timed region, on the
+        # same stream: their sum against the timed step says how much time lies between kernels
+        roof["kernel_ms_per_step_sum"] = tot
+        roof["timed_ms_per_step"] = ms / args.steps
         return st, {"value": value, "ms": ms, "kps": kps, "roof": roof, "breakdown": breakdown, "clocks": clk,
                     "mass_rel_drift": abs(m1 - m0) / m0}
 
@@ -485,7 +500,7 @@ def run_ensemble(args, rank, world, local_rank):
     roof = {"kernel": "ensemble_persistent", "bound": "alu" if alu_frac > hbm_frac else "hbm",
             "achieved": alg_flops / t_launch / 1e9 if alu_frac > hbm_frac else alg_bytes / t_launch / 1e9,
             "peak": FP64_INSTR_PEAK / 1e9 if alu_frac > hbm_frac else hbm_peak,
-            "unit": "GFLOP/s (FP64)" if alu_frac > hbm_frac else "GB/s",
+            "unit": "G FP64 instr/s" if alu_frac > hbm_frac else "GB/s",
             "frac": max(alu_frac, hbm_frac), "traffic": None,
             "hbm_frac": hbm_frac, "fp64_frac": alu_frac, "launch_ms": ms_b / args.steps, "launches_per_step": 1}
     line = {"metric": METRIC, "value": value_b, "unit": UNIT, "n_gpus": world, "steps": args.steps,
