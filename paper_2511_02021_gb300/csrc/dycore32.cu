@@ -161,6 +161,7 @@ __device__ inline void mx_edge_tend_item(const MxGeo& G, const MxEdgeArgs& a, in
   const float* __restrict__ exq = a.exp;
   const float* __restrict__ rho = a.rho;
   const unsigned seg = LPE == 32 ? 0xffffffffu : (0xffffu << (threadIdx.x & 16));
+#pragma unroll 2   // two windows' loads in flight (the kernel is bound by load latency)
   for (int base = 0; base <= N; base += LPE - 1) {
     const int h = base + lane;
     const bool hv = h <= N;
@@ -851,6 +852,123 @@ __global__ void __launch_bounds__(512) k_mx_gather_tile(MxGeo G, MxColArgs a) {
   mx_gather_tile_body<LPE, CORR>(G, a, (int64_t)blockIdx.x * kGatherCells, T);
 }
 
+// ---- corrector of the stored-factor column for one state, in two launches. Its only
+// sequential parts are the forward elimination of the right-hand side and the back
+// substitution; everything else is parallel over the levels.
+//   k_mx_corr_solve   one thread per column: right-hand side from the stored rows, forward
+//                     elimination with the stored factors, back substitution, damping; the
+//                     damped w overwrites the Thomas scratch (level-major, coalesced).
+//   k_mx_corr_update  one element per (cell, level), 32 cells by a chunk of levels per
+//                     block: the FP64 updates of S^{n+1} and the vertical mass flux from
+//                     level-major operands, the FP32 shadows transposed through shared
+//                     memory into the cells' [c][ld] rows.
+// Same arithmetic as the corrector branch of mx_column_fac_item (which the persistent
+// ensemble keeps in one pass).
+__global__ void __launch_bounds__(128) k_mx_corr_solve(MxGeo G, MxColArgs a) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= G.nc) return;
+  const int N = G.N, ld = G.ld;
+  const int64_t nc = G.nc, H = N + 1;
+  const double dtau = a.dtau;
+  const double* __restrict__ cc = a.cc;
+  const double* __restrict__ fac = a.fac64;
+  double* __restrict__ dps = a.dps;
+  const double* __restrict__ hdt = a.hdt;
+  const double* __restrict__ hdw = a.hdw;
+#define LM(p, k) (p)[(int64_t)(k) * nc + c]
+#define F64(f, k) fac[((int64_t)(f) * H + (k)) * nc + c]
+  double dp_prev = 0.0, exx_prev = 0.0;
+#pragma unroll 4
+  for (int k = 0; k < N; ++k) {
+    const double exx = F64(F_PX, k) - F64(F_GD, k) * LM(hdt, k);
+    if (k >= 1) {
+      const double rhs = F64(F_WX, k) + dtau * LM(hdw, k) - F64(F_AA, k) * (exx_prev - exx);
+      const double dpv = (rhs - F64(F_LO, k) * dp_prev) * F64(F_RP, k);
+      LM(dps, k) = dpv;
+      dp_prev = dpv;
+    }
+    exx_prev = exx;
+  }
+  double x_next = 0.0;
+#pragma unroll 4
+  for (int h = N - 1; h >= 1; --h) {
+    const double x = LM(dps, h) - F64(F_CP, h) * x_next;
+    LM(dps, h) = x * cc[CC_DAMP * ld + h];
+    x_next = x;
+  }
+#undef LM
+#undef F64
+}
+
+constexpr int kUpdCells = 32, kUpdLevels = 32;
+__global__ void __launch_bounds__(256) k_mx_corr_update(MxGeo G, MxColArgs a) {
+  __shared__ float sf[4][kUpdLevels][kUpdCells + 1];   // theta_v, rho, pi - pi_ref, w
+  const int N = G.N, ld = G.ld;
+  const int64_t nc = G.nc, H = N + 1, c0 = (int64_t)blockIdx.x * kUpdCells;
+  const double dtau = a.dtau;
+  const double* __restrict__ cc = a.cc;
+  const double* __restrict__ fac = a.fac64;
+  const double* __restrict__ wd = a.dps;               // damped w^{n+1}, half levels 1..N-1
+  const double* __restrict__ hdt = a.hdt;
+  const double* __restrict__ hdr = a.hdr;
+  double* __restrict__ rho_io = a.rho;
+  double* __restrict__ thv_io = a.thv;
+  double* __restrict__ ex_io = a.ex;
+  double* __restrict__ w_io = a.w;
+  double* __restrict__ wflx_io = a.wflx;
+  const int tid = threadIdx.x, cl = tid % kUpdCells, r0 = tid / kUpdCells, nr = blockDim.x / kUpdCells;
+  const int64_t c = c0 + cl;
+  bool ok = true;
+  for (int k0 = 0; k0 < N; k0 += kUpdLevels) {
+    for (int r = r0; r < kUpdLevels; r += nr) {
+      const int h = k0 + r;
+      if (h >= N || c >= nc) continue;
+#define LM(p, k) (p)[(int64_t)(k) * nc + c]
+#define F64(f, k) fac[((int64_t)(f) * H + (k)) * nc + c]
+      const double w = h >= 1 ? LM(wd, h) : 0.0;
+      const double w1 = h + 1 < N ? LM(wd, h + 1) : 0.0;
+      const double Mk = F64(F_M, h), rk = F64(F_RI, h);
+      const double q = Mk * w - F64(F_M, h + 1) * w1;
+      const double rr = rk * w - F64(F_RI, h + 1) * w1;
+      const double dtb = cc[CC_DTBDZ * ld + h];
+      const double Dt = LM(hdt, h);
+      const double Th_n = (F64(F_TX, h) - dtau * Dt) - dtb * q;
+      const double ex_n = (F64(F_PX, h) - F64(F_GD, h) * Dt) - F64(F_GAM, h) * q;
+      const double rho_n = (F64(F_RX, h) - dtau * LM(hdr, h)) - dtb * rr;
+      const double thv_n = Th_n * recip64(rho_n);
+      const double wold = LM(w_io, h);
+      LM(wflx_io, h) += rk * (kBeta * w + (1.0 - kBeta) * wold) * a.inv_nsub;
+      LM(rho_io, h) = rho_n;
+      LM(thv_io, h) = thv_n;
+      LM(ex_io, h) = ex_n;
+      LM(w_io, h) = w;
+      sf[0][r][cl] = f64_to_f32(thv_n);
+      sf[1][r][cl] = f64_to_f32(rho_n);
+      sf[2][r][cl] = f64_to_f32(ex_n - cc[CC_EXREF * ld + h]);
+      sf[3][r][cl] = f64_to_f32(w);
+      ok = ok && finite64(thv_n) && finite64(ex_n) && finite64(w);
+#undef LM
+#undef F64
+    }
+    __syncthreads();
+    // shadows: each warp writes whole level runs of its cells' [c][ld] rows
+    const int lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+    for (int j = warp; j < kUpdCells; j += nwarp) {
+      const int64_t cj = c0 + j;
+      const int h = k0 + lane;
+      if (cj >= nc || h >= N) continue;
+      const int64_t o = cj * ld + h;
+      a.thv32[o] = sf[0][lane][j];
+      a.rho32[o] = sf[1][lane][j];
+      a.exp32[o] = sf[2][lane][j];
+      a.w32[o] = sf[3][lane][j];
+    }
+    __syncthreads();
+  }
+  if (tid < kUpdCells && c < nc) a.w32[c * ld + N] = 0.0f;
+  if (__syncthreads_or(!ok) && tid == 0) atomicOr(a.status, 1u);
+}
+
 template <int NMAX, bool CORR>
 __global__ void __launch_bounds__(128) k_mx_column(MxGeo G, MxColArgs a) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -978,6 +1096,11 @@ void launch_kind(int kind, const TileChoice& t, const MxGeo& G, StateDev& s, con
 template <bool CORR>
 void launch_mx_column(const MxGeo& G, const MxColArgs& a, cudaStream_t st) {
   const unsigned nb = blocks_for(G.nc, 128);
+  if (CORR && a.fac64) {
+    k_mx_corr_solve<<<nb, 128, 0, st>>>(G, a);
+    k_mx_corr_update<<<(unsigned)((G.nc + kUpdCells - 1) / kUpdCells), 256, 0, st>>>(G, a);
+    return;
+  }
   if (G.N <= 32) k_mx_column<32, CORR><<<nb, 128, 0, st>>>(G, a);
   else if (G.N <= 64) k_mx_column<64, CORR><<<nb, 128, 0, st>>>(G, a);
   else if (G.N <= 96) k_mx_column<96, CORR><<<nb, 128, 0, st>>>(G, a);
