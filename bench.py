@@ -81,6 +81,35 @@ NCU_TRAFFIC = {
 }
 
 
+def max_over_ranks(ms, device):
+    """The slowest rank's time: every rank passes its own and receives the maximum."""
+    import torch
+    import torch.distributed as td
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, world, ms):
+    """Whole-job throughput: the units all ranks processed (the same on every rank)
+    over the slowest rank's time in milliseconds."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
+# algorithmic bytes per cell-level-substep of the whole step: the state read and written by
+# the two stages (5 volumes of vn, w, rho, theta_v, pi), the FP64 accumulators and the
+# diffusion spread over the substeps
+STEP_BYTES = {0: 271.0, 1: 239.0}
+
+
+def step_hbm_roofline(value, precision, hbm_peak):
+    """The whole step against the HBM roofline by its algorithmic bytes (the metric's
+    '% HBM roofline'; the dominant kernel's own bound is in "roofline")."""
+    b = STEP_BYTES[precision]
+    return {"algorithmic_bytes_per_unit": b, "achieved_gbs": value * b / 1e9, "peak_gbs": hbm_peak,
+            "frac": value * b / 1e9 / hbm_peak}
+
+
 def counts(wl):
     L = wl.bisections + 1
     nc, ne, nv = 20 * 4 ** L, 30 * 4 ** L, 10 * 4 ** L + 2
@@ -258,10 +287,8 @@ def run_gpu(args, wl, rank, world, local_rank):
         C.icon_state_status(st)                               # raises on non-finite values
         m1 = float(mass_host[0])
         if dist:
-            t = torch.tensor([ms], device="cuda")
-            td.all_reduce(t, op=td.ReduceOp.MAX)
-            ms = float(t.item())
-        value = world * nc * N * wl.nsub * args.steps / (ms * 1e-3)
+            ms = max_over_ranks(ms, "cuda")
+        value = job_value(nc * N * wl.nsub * args.steps, world, ms)
         # per-kernel durations, measured live with CUDA events around every launch
         kms, kn = None, None
         for _ in range(2):
@@ -330,7 +357,8 @@ def run_gpu(args, wl, rank, world, local_rank):
                  "value": res_m["value"], "unit": UNIT, "ms_per_step": res_m["ms"] / args.steps,
                  "speedup_vs_fp64": res_m["value"] / value, "rel_l2_vs_fp64_after_1_step": err,
                  "mass_rel_drift": res_m["mass_rel_drift"], "roofline": res_m["roof"],
-                 "kernels": res_m["breakdown"], "gpu_launches": res_m["kps"] * args.steps}
+                 "kernels": res_m["breakdown"], "gpu_launches": res_m["kps"] * args.steps,
+                 "hbm_roofline": step_hbm_roofline(res_m["value"], 1, hbm_peak)}
     m_drift = res["mass_rel_drift"]
     err_vs_fp64 = None
     if wl.precision == 1 and not args.no_mixed:
@@ -396,7 +424,8 @@ def run_gpu(args, wl, rank, world, local_rank):
                        "levels": N, "dt": wl.dt, "nsub": wl.nsub, "precision": "fp64" if wl.precision == 0
                        else "mixed", "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (state %.2f GB)" % ((ne * N + 4 * nc * N) * 8 / 1e9)},
-            "gpu_launches": kernels_per_step * args.steps, "roofline": roof, "kernels": breakdown,
+            "gpu_launches": kernels_per_step * args.steps, "roofline": roof,
+            "hbm_roofline": step_hbm_roofline(value, wl.precision, hbm_peak), "kernels": breakdown,
             "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "mass_rel_drift": m_drift, "mixed": other,
             "rel_l2_vs_fp64_after_1_step": err_vs_fp64,
             "simulated_days_per_day": wl.dt / (ms / args.steps * 1e-3),
@@ -449,9 +478,7 @@ def run_ensemble(args, rank, world, local_rank):
             td.barrier()
         ms = e0.elapsed_time(e1)
         if dist:
-            t = torch.tensor([ms], device="cuda")
-            td.all_reduce(t, op=td.ReduceOp.MAX)
-            ms = float(t.item())
+            ms = max_over_ranks(ms, "cuda")
         return ms
 
     # batched: one persistent launch per step
@@ -464,7 +491,7 @@ def run_ensemble(args, rank, world, local_rank):
                  args.steps)
     clk = clocks.stop() if clocks else None
     kms, kn = np.zeros(C.ICON_KIND_COUNT), np.zeros(C.ICON_KIND_COUNT, dtype=np.int32)
-    value_b = world * cells * N * nsub * args.steps / (ms_b * 1e-3)
+    value_b = job_value(cells * N * nsub * args.steps, world, ms_b)
     C.icon_ensemble_free(ens)
     for st in sts:
         C.icon_state_free(st)
@@ -482,7 +509,7 @@ def run_ensemble(args, rank, world, local_rank):
     ms_s = timed(seq, args.steps)
     for st in sts:
         C.icon_state_status(st)
-    value_s = world * cells * N * nsub * args.steps / (ms_s * 1e-3)
+    value_s = job_value(cells * N * nsub * args.steps, world, ms_s)
     launches_seq = sum(C.icon_state_step_kernels(st, dt, nsub) for st, dt in zip(sts, dts))
     for st in sts:
         C.icon_state_free(st)
@@ -510,6 +537,7 @@ def run_ensemble(args, rank, world, local_rank):
                        "levels": N, "nsub": nsub, "dt": {"R2B4": E["dt_b4"], "R2B5": E["dt_b5"]},
                        "l2": "inputs larger than L2 (64 member states)"},
             "gpu_launches": 2 * args.steps, "roofline": roof, "clocks": clk,
+            "hbm_roofline": step_hbm_roofline(value_b, 1, hbm_peak),
             "sequential": {"value": value_s, "unit": UNIT, "ms_per_step": ms_s / args.steps,
                            "gpu_launches_per_step": launches_seq},
             "batched_speedup_vs_sequential": value_b / value_s}
