@@ -9,3 +9,4 @@ from .grid import build_grid, R_EARTH, OMEGA          # noqa: F401
 from .state import (vertical_grid, init_state, exner_ref, splitmix64, uniform01,   # noqa: F401
                     member_params, CASE_REST, CASE_SBR, CASE_JET, CASE_MEMBER)
 from .dycore import dycore_step, global_mass, tendencies, diffusion    # noqa: F401
+from .tracer import tracer_step, tracer_mass, cell_gradient, cell_neighbours, cell_lsq_weights   # noqa: F401
