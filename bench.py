@@ -69,6 +69,10 @@ MX_COLUMN_FP64_OPS = 36
 # mixed step recomputing the factors in both stages (when the stored factors would exceed a
 # quarter of the device memory): executed 47.5 (predictor) and 64.5 (corrector).
 MX_COLUMN_RECOMPUTE_FP64_OPS = 56
+# FP64 instructions per cell-level of the tracer transport of one tracer: cell kernel
+# (least-squares gradient 12, vertical slope, departure point and flux 14), edge kernel
+# (25 per edge-level, 1.5 edges per cell), update (12).
+TRACER_FP64_OPS = 75
 # DRAM bytes (read + write) per launch of the dominant kernel kind, from ncu captures of the
 # current kernels (mean of predictor and corrector; same files): FP64 column at R2B6/90
 # measured; mixed column at R2B6/90 measured and scaled by cells to R2B8/90; recomputing
@@ -359,6 +363,43 @@ def run_gpu(args, wl, rank, world, local_rank):
                  "mass_rel_drift": res_m["mass_rel_drift"], "roofline": res_m["roof"],
                  "kernels": res_m["breakdown"], "gpu_launches": res_m["kps"] * args.steps,
                  "hbm_roofline": step_hbm_roofline(res_m["value"], 1, hbm_peak)}
+    # tracer transport (one tracer, same workload and precision): its kernel time per step
+    # from the profiled eager steps, and the step time with it from timed graph replays
+    tracer = None
+    if not args.no_tracer:
+        tst = None
+        try:
+            tst = C.icon_state_init_ex(grid, wl.seed + rank, wl.case, noise_K=wl.noise_K, precision=wl.precision)
+            C.icon_state_add_tracers(tst, 1)
+            xc = C.icon_grid_copy_table(grid, "x_c")
+            C.icon_state_set_tracer(tst, grid, N, 0, np.repeat(1.0 + 0.5 * xc[:, 2:3], N, axis=1))
+            for _ in range(args.warmup):
+                C.icon_dycore_step(tst, wl.dt, wl.nsub)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                C.icon_dycore_step_async(tst, wl.dt, wl.nsub)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            C.icon_state_status(tst)
+            ms_t = e0.elapsed_time(e1) / args.steps
+            kms, kn = None, None
+            for _ in range(2):
+                kms, kn = C.icon_dycore_step_profile(tst, wl.dt, wl.nsub, kms, kn)
+            names = [C.icon_kernel_kind_name(k) for k in range(C.ICON_KIND_COUNT)]
+            t_ms = kms[names.index("tracer_transport")] / 2
+            ops = nc * N * TRACER_FP64_OPS
+            tracer = {"tracers": 1, "ms_per_step_with_tracer": ms_t, "ms_per_step_without": ms / args.steps,
+                      "tracer_kernels_ms_per_step": t_ms,
+                      "roofline": {"bound": "alu", "achieved": ops / (t_ms * 1e-3) / 1e9,
+                                   "peak": FP64_INSTR_PEAK / 1e9, "unit": "G FP64 instr/s",
+                                   "frac": ops / (t_ms * 1e-3) / FP64_INSTR_PEAK, "traffic": None}}
+        except C.IconError as exc:
+            tracer = {"skipped": str(exc)}
+        finally:
+            if tst is not None:
+                C.icon_state_free(tst)
     m_drift = res["mass_rel_drift"]
     err_vs_fp64 = None
     if wl.precision == 1 and not args.no_mixed:
@@ -427,7 +468,7 @@ def run_gpu(args, wl, rank, world, local_rank):
             "gpu_launches": kernels_per_step * args.steps, "roofline": roof,
             "hbm_roofline": step_hbm_roofline(value, wl.precision, hbm_peak), "kernels": breakdown,
             "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "mass_rel_drift": m_drift, "mixed": other,
-            "rel_l2_vs_fp64_after_1_step": err_vs_fp64,
+            "rel_l2_vs_fp64_after_1_step": err_vs_fp64, "tracer": tracer,
             "simulated_days_per_day": wl.dt / (ms / args.steps * 1e-3),
             "device_memory_gb": {"peak_allocated": round(torch.cuda.max_memory_allocated() / 1e9, 2),
                                  "total": round(torch.cuda.get_device_properties(0).total_memory / 1e9, 2)}}
@@ -553,6 +594,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="r2b6-fp64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision variant of an FP64 workload")
+    ap.add_argument("--no-tracer", action="store_true", help="skip the tracer-transport measurement")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     world = int(os.environ.get("WORLD_SIZE", "1"))

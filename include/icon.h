@@ -71,7 +71,8 @@ typedef enum {
   ICON_T_V2C = 5,   /* [Nv][6] cell between v2e[j] and v2e[j+1]; pentagons repeat [0]   */
   ICON_T_VDEG = 6,  /* [Nv]    5 or 6                                                   */
   ICON_T_E2VT = 7,  /* [Ne][5] own edge, two other edges of c1, two other edges of c2   */
-  ICON_T_E2Q = 8    /* [Ne][4] v1, v2, vertex of c1 opposite e, vertex of c2 opposite e */
+  ICON_T_E2Q = 8,   /* [Ne][4] v1, v2, vertex of c1 opposite e, vertex of c2 opposite e */
+  ICON_T_C2C = 9    /* [Nc][3] cell across edge slot s (tracer transport; built on demand) */
 } icon_table_int;
 
 /* FP64 geometry tables (unit vectors are on the unit sphere; lengths in m, areas in m^2). */
@@ -91,7 +92,9 @@ typedef enum {
   ICON_G_LSQW = 28, /* [Nv][6][3] least-squares vertex-velocity weights                */
   ICON_G_L34 = 29,  /* [Ne] distance of the two opposite quad vertices                 */
   ICON_G_SCE = 30,  /* [Nc][3] outward sign of each cell edge (+1 if c is c1)          */
-  ICON_G_SVE = 31   /* [Nv][6] circulation sign (-1 if v is v1, +1 if v2, 0 padding)   */
+  ICON_G_SVE = 31,  /* [Nv][6] circulation sign (-1 if v is v1, +1 if v2, 0 padding)   */
+  ICON_G_LSQC = 32, /* [Nc][3][3] least-squares gradient weights (3-vectors, tracers)  */
+  ICON_G_ROFF = 33  /* [Ne][2][3] R (x_e - x_c1), R (x_e - x_c2) (tracers)             */
 } icon_table_geom;
 
 /* Fields (copied out as FP64, row-major [entity][level], unpadded). */
@@ -252,7 +255,8 @@ int icon_selftest(long long n, unsigned* failures);
 
 /* Name of kernel kind i (0 <= i < ICON_KIND_COUNT), or NULL. Mixed-precision
  * stencil kinds: 10 vertex, 11 edge diagnostics, 12 cell kinetic energy,
- * 13 edge tendency, 15 column-input gather, 16 diffusion vertex/divergence. */
+ * 13 edge tendency, 15 column-input gather, 16 diffusion vertex/divergence;
+ * 20 tracer transport. */
 const char* icon_kernel_kind_name(int kind);
 #define ICON_KIND_COUNT 24
 
@@ -260,6 +264,27 @@ const char* icon_kernel_kind_name(int kind);
 int icon_state_precision(const icon_state* state, int* out);
 
 void icon_state_free(icon_state* state);
+
+/* ---------------------------------------------------------------- tracers */
+
+/* Give the state ntracers (1..8) mixing-ratio tracers, FP64 in both precisions,
+ * initially 0; once per state. From then on every icon_dycore_step also transports
+ * them after the dycore substeps and the diffusion with that step's substep-averaged
+ * FP64 mass fluxes (ICON_F_MFLX, ICON_F_WFLX): flux form, second order (least-squares
+ * cell gradients, upwind edge and half-level values at the half-step departure point),
+ * consistent with the continuity equation of the step (a uniform tracer stays uniform,
+ * tracer mass is conserved), no limiter. The atmosphere of the paper's model carries
+ * tracers (Sec. "Overview of the Problem"); the scheme is this library's reading. Builds
+ * the grid's tracer tables on first use and allocates 6 (FP64) or 8 (mixed) cell fields
+ * and one edge field of scratch plus the tracers; ICON_ENOMEM if they do not fit.
+ * States with tracers cannot join an ensemble. */
+int icon_state_add_tracers(icon_state* state, int ntracers);
+int icon_state_tracers(const icon_state* state, int* ntracers);
+
+/* Copy tracer t (0 <= t < ntracers) from / to host memory: count must be Nc*N doubles
+ * laid out [cell][level] (level 0 at the top), else ICON_EINVAL. Synchronous. */
+int icon_state_set_tracer(icon_state* state, int t, const double* host_src, size_t count);
+int icon_state_copy_tracer(const icon_state* state, int t, double* host_dst, size_t count);
 
 /* ---------------------------------------------------------------- ensemble */
 

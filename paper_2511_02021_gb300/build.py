@@ -27,6 +27,7 @@ SOURCES = {
     "dycore64.cu": [],
     "mass.cu": ["-fmad=false"],
     "dycore32.cu": [],
+    "tracer.cu": [],
 }
 
 

@@ -29,6 +29,8 @@ TABLES = {
     "f_e": (25, np.float64, "e", 1), "vt_w": (26, np.float64, "e", 5), "kin_w": (27, np.float64, "c", 3),
     "lsq_w": (28, np.float64, "v", 18), "L34": (29, np.float64, "e", 1), "s_ce": (30, np.float64, "c", 3),
     "s_ve": (31, np.float64, "v", 6),
+    # tracer transport tables (built on demand)
+    "c2c": (9, np.int32, "c", 3), "lsq_c": (32, np.float64, "c", 9), "roff": (33, np.float64, "e", 6),
 }
 # field ids: name -> (id, entity, half-level field)
 FIELDS = {"vn": (0, "e", False), "w": (1, "c", True), "rho": (2, "c", False), "theta_v": (3, "c", False),
@@ -75,6 +77,8 @@ def _load():
         "icon_ensemble_set_option": (I, [P, I, ctypes.c_longlong]),
         "icon_state_tiling": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "icon_state_set_tiling": (I, [P, I, I, I]),
+        "icon_state_add_tracers": (I, [P, I]), "icon_state_tracers": (I, [P, ctypes.POINTER(I)]),
+        "icon_state_set_tracer": (I, [P, I, P, S]), "icon_state_copy_tracer": (I, [P, I, P, S]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -298,3 +302,31 @@ def icon_state_set_tiling(state, kind, lanes, block):
 
 def icon_ensemble_free(ens):
     _lib.icon_ensemble_free(ens)
+
+
+# ---------------------------------------------------------------- tracers
+def icon_state_add_tracers(state, n):
+    _check(_lib.icon_state_add_tracers(state, n))
+
+
+def icon_state_tracers(state):
+    n = ctypes.c_int()
+    _check(_lib.icon_state_tracers(state, ctypes.byref(n)))
+    return n.value
+
+
+def _tracer_shape(grid, nlev):
+    nc, _, _ = icon_grid_counts(grid)
+    return (nc, nlev)
+
+
+def icon_state_set_tracer(state, grid, nlev, t, values):
+    values = np.ascontiguousarray(values, dtype=np.float64)
+    assert values.shape == _tracer_shape(grid, nlev)
+    _check(_lib.icon_state_set_tracer(state, t, values.ctypes.data, values.size))
+
+
+def icon_state_copy_tracer(state, grid, nlev, t):
+    out = np.empty(_tracer_shape(grid, nlev), dtype=np.float64)
+    _check(_lib.icon_state_copy_tracer(state, t, out.ctypes.data, out.size))
+    return out

@@ -60,7 +60,7 @@ static const char* kKindNames[K_KIND_COUNT] = {
     "vertex_curl_wmean", "edge_vt_ke", "cell_ke", "edge_tendency_flux", "column_solve",
     "diff_vertex", "diff_div", "diff_edge", "diff_theta", "global_mass",
     "mx_vertex", "mx_edge_diag", "mx_cell_ke", "mx_edge_tendency_flux", "mx_column_solve", "mx_column_prep",
-    "mx_diff_vertex", "mx_diff_edge", "mx_diff_theta", "ensemble_persistent"};
+    "mx_diff_vertex", "mx_diff_edge", "mx_diff_theta", "ensemble_persistent", "tracer_transport"};
 
 Allocator current_allocator() {
   std::lock_guard<std::mutex> lk(g_alloc_mu);
@@ -180,6 +180,9 @@ bool table_ref(const icon_grid* grid, int id, TableRef& t) {
     case ICON_G_L34: t = {g.L34, 8, ne}; return true;
     case ICON_G_SCE: t = {g.s_ce, 8, 3 * nc}; return true;
     case ICON_G_SVE: t = {g.s_ve, 8, 6 * nv}; return true;
+    case ICON_T_C2C: t = {g.c2c, 4, 3 * nc}; return g.c2c != nullptr;
+    case ICON_G_LSQC: t = {g.lsq_c, 8, 9 * nc}; return g.lsq_c != nullptr;
+    case ICON_G_ROFF: t = {g.roff, 8, 6 * ne}; return g.roff != nullptr;
     default: return false;
   }
 }
@@ -274,8 +277,10 @@ int sync_status(icon_state* st, cudaStream_t stream) {
 }
 
 void enqueue_step(icon_state* st, double dt, int nsub, cudaStream_t stream) {
+  if (st->s.ntr > 0) tracer_begin(st, stream);
   if (st->s.precision == ICON_FP64) enqueue_step_fp64(st, dt, nsub, stream);
   else enqueue_step_mixed(st, dt, nsub, stream);
+  if (st->s.ntr > 0) tracer_end(st, dt, stream);
 }
 
 // record the graph of one step for (dt, nsub) unless it is already recorded
@@ -437,6 +442,10 @@ int icon_grid_counts(const icon_grid* grid, int64_t* nc, int64_t* ne, int64_t* n
 
 int icon_grid_copy_table(const icon_grid* grid, int table_id, void* host_dst, size_t bytes) {
   if (!grid || !host_dst) { set_error("icon_grid_copy_table: NULL argument"); return ICON_EINVAL; }
+  if ((table_id == ICON_T_C2C || table_id == ICON_G_LSQC || table_id == ICON_G_ROFF) && !grid->g.c2c) {
+    const int rc = build_tracer_tables(const_cast<icon_grid*>(grid), current_stream());
+    if (rc != ICON_OK) return rc;
+  }
   TableRef t;
   if (!table_ref(grid, table_id, t)) { set_error("icon_grid_copy_table: unknown table %d", table_id); return ICON_EINVAL; }
   if (bytes != t.elem * t.count) {
@@ -734,12 +743,64 @@ struct icon_ensemble {
 
 extern "C" {
 
+int icon_state_add_tracers(icon_state* st, int ntracers) {
+  if (!st) { set_error("icon_state_add_tracers: state is NULL"); return ICON_EINVAL; }
+  if (ntracers < 1 || ntracers > 8) { set_error("icon_state_add_tracers: need 1..8 tracers"); return ICON_EINVAL; }
+  if (st->s.ntr != 0) { set_error("icon_state_add_tracers: the state already has tracers"); return ICON_EINVAL; }
+  const int rc = tracer_alloc(st, ntracers);
+  if (rc != ICON_OK) return rc;
+  if (st->graph) {                      // the step's graph now has to transport them too
+    cudaGraphExecDestroy(st->graph);
+    st->graph = nullptr;
+  }
+  return ICON_OK;
+}
+
+int icon_state_tracers(const icon_state* st, int* out) {
+  if (!st || !out) { set_error("icon_state_tracers: NULL argument"); return ICON_EINVAL; }
+  *out = st->s.ntr;
+  return ICON_OK;
+}
+
+static int tracer_copy(icon_state* st, int t, double* host, size_t count, bool to_host) {
+  const char* fn = to_host ? "icon_state_copy_tracer" : "icon_state_set_tracer";
+  if (!st || !host) { set_error("%s: NULL argument", fn); return ICON_EINVAL; }
+  if (t < 0 || t >= st->s.ntr) { set_error("%s: tracer %d of %d", fn, t, st->s.ntr); return ICON_EINVAL; }
+  const int64_t nc = st->grid->g.nc;
+  const int N = st->grid->vert.N, ld = st->grid->vert.ld;
+  if (count != (size_t)(nc * N)) {
+    set_error("%s: a tracer has %lld elements, got %zu", fn, (long long)(nc * N), count);
+    return ICON_EINVAL;
+  }
+  double* dev = st->s.q + (size_t)t * nc * ld;
+  cudaStream_t stream = current_stream();
+  cudaError_t e = to_host ? cudaMemcpy2DAsync(host, sizeof(double) * N, dev, sizeof(double) * ld, sizeof(double) * N,
+                                              nc, cudaMemcpyDeviceToHost, stream)
+                          : cudaMemcpy2DAsync(dev, sizeof(double) * ld, host, sizeof(double) * N, sizeof(double) * N,
+                                              nc, cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return cuda_fail(e, fn);
+  return ICON_OK;
+}
+
+int icon_state_set_tracer(icon_state* st, int t, const double* host_src, size_t count) {
+  return tracer_copy(st, t, const_cast<double*>(host_src), count, false);
+}
+
+int icon_state_copy_tracer(const icon_state* st, int t, double* host_dst, size_t count) {
+  return tracer_copy(const_cast<icon_state*>(st), t, host_dst, count, true);
+}
+
 int icon_ensemble_create(icon_state* const* members, int n, icon_ensemble** out) {
   if (!members || !out || n < 1 || n > 64) { set_error("icon_ensemble_create: need 1..64 members"); return ICON_EINVAL; }
   for (int i = 0; i < n; ++i) {
     if (!members[i]) { set_error("icon_ensemble_create: member %d is NULL", i); return ICON_EINVAL; }
     if (members[i]->s.precision != ICON_MIXED) {
       set_error("icon_ensemble_create: members must be mixed-precision states");
+      return ICON_EINVAL;
+    }
+    if (members[i]->s.ntr != 0) {
+      set_error("icon_ensemble_create: the persistent ensemble does not transport tracers (member %d has some)", i);
       return ICON_EINVAL;
     }
     if (members[i]->grid->vert.N != members[0]->grid->vert.N || members[i]->grid->vert.N > 96) {

@@ -52,6 +52,7 @@ struct MxGeo {
   const float *div_w32, *rot_w32, *vt_w32, *kin_w32, *lsq_w32, *inv_de32, *inv_le32, *f_e32, *l_e32;
   const float *n_e32, *t_e32, *L34inv32, *s_ce32;
   const double* inv_Ac;                    // 1 / A_c (FP64)
+  const double* div_wa;                    // [Nc][3] s_ce l_e / A_c (FP64)
   const double *dz, *dzh, *wu, *wl, *dz2, *ray, *ex_ref;
   const float *inv_dz32, *wu32, *wl32, *inv_dz2_32;
 };
@@ -130,7 +131,7 @@ struct MxEdgeArgs {
   const float* vn_base;
   float* vn_out;
   float* Avn0;
-  float *phi, *gth, *a_e;                  // l_e rho_e vn, l_e rho_e vn theta_e, w-advection edge term
+  float *phi, *gth, *a_e;                  // rho_e vn, l_e rho_e vn theta_e, w-advection edge term
   double* mflx;
   float dtau;
   double inv_nsub;
@@ -199,9 +200,8 @@ __device__ inline void mx_edge_tend_item(const MxGeo& G, const MxEdgeArgs& a, in
     }
     a.vn_out[o + k] = vnew;
     const float F = 0.5f * (rho[c1 + k] + rho[c2 + k]) * vnew;
-    const float phi = le * F;
-    a.phi[o + k] = phi;
-    a.gth[o + k] = phi * th_e;
+    a.phi[o + k] = F;
+    a.gth[o + k] = (le * F) * th_e;
     if (a.corrector) a.mflx[o + k] += f32_to_f64(F) * a.inv_nsub;
   }
 }
@@ -306,7 +306,7 @@ struct MxColArgs {
   double *rho, *thv, *ex, *w;
   double* wflx;                            // level-major [h][Nc]
   // FP32 inputs
-  const float *phi, *gth, *a_e;            // [Ne][ld]
+  const float *phi, *gth, *a_e;            // [Ne][ld]: rho_e vn, l_e rho_e vn theta_e, w-advection term
   const float* w_stage;                    // [Nc][ld] w shadow of the stage state
   float* Aw0;                              // level-major [h][Nc]
   // FP32 shadows written by this stage, [Nc][ld]
@@ -353,6 +353,7 @@ __device__ inline void mx_column_item(const MxGeo& G, const MxColArgs& a, int64_
   const double invA = G.inv_Ac[c];
   const float invA32 = (float)invA;
   const float dtau32 = (float)dtau;
+  const double dwa[3] = {G.div_wa[3 * c], G.div_wa[3 * c + 1], G.div_wa[3 * c + 2]};
 
   double rho_ic[NMAX + 1], M[NMAX + 1], Thx[NMAX], exx[NMAX], rhox[NMAX], cp[NMAX], dp[NMAX];
   float gam[NMAX];
@@ -373,9 +374,10 @@ __device__ inline void mx_column_item(const MxGeo& G, const MxColArgs& a, int64_
   M[N] = rho_m * thv_m;
   // explicit predictors at full levels
   for (int k = 0; k < N; ++k) {
-    // horizontal divergences: rho with an FP64 sum of the FP32 edge flux integrals
-    const float p0 = sg[0] * a.phi[E[0] + k], p1 = sg[1] * a.phi[E[1] + k], p2 = sg[2] * a.phi[E[2] + k];
-    const double Dr = ((f32_to_f64(p0) + f32_to_f64(p1)) + f32_to_f64(p2)) * invA;
+    // horizontal divergences: rho in FP64 from the FP32 mass fluxes (the values the
+    // step-mean mass flux accumulates, so tracer transport sees the same divergence)
+    const double Dr = (dwa[0] * f32_to_f64(a.phi[E[0] + k]) + dwa[1] * f32_to_f64(a.phi[E[1] + k])) +
+                      dwa[2] * f32_to_f64(a.phi[E[2] + k]);
     const float Dt = (sg[0] * a.gth[E[0] + k] + sg[1] * a.gth[E[1] + k] + sg[2] * a.gth[E[2] + k]) * invA32;
     const double rho = LM(a.rho, k), thv = LM(a.thv, k), ex = LM(a.ex, k);
     const double w0 = LM(a.w, k), w1 = LM(a.w, k + 1);
@@ -806,10 +808,11 @@ __device__ inline void mx_gather_tile_body(const MxGeo& G, const MxColArgs& a, i
       }
       const double invA = G.inv_Ac[c];
       const float invA32 = (float)invA;
+      const double dwa[3] = {G.div_wa[3 * c], G.div_wa[3 * c + 1], G.div_wa[3 * c + 2]};
       const int k = k0 + lane;
       if (k < N) {
-        const float p0 = sg[0] * a.phi[E[0] + k], p1 = sg[1] * a.phi[E[1] + k], p2 = sg[2] * a.phi[E[2] + k];
-        sh[0][lane][cl] = ((f32_to_f64(p0) + f32_to_f64(p1)) + f32_to_f64(p2)) * invA;
+        sh[0][lane][cl] = (dwa[0] * f32_to_f64(a.phi[E[0] + k]) + dwa[1] * f32_to_f64(a.phi[E[1] + k])) +
+                          dwa[2] * f32_to_f64(a.phi[E[2] + k]);
         sh[1][lane][cl] =
             f32_to_f64((sg[0] * a.gth[E[0] + k] + sg[1] * a.gth[E[1] + k] + sg[2] * a.gth[E[2] + k]) * invA32);
         if (!CORR) {
@@ -991,6 +994,7 @@ MxGeo make_mx_geo(const icon_grid* grid, const StateDev& s) {
   G.lsq_w32 = g.lsq_w32; G.inv_de32 = g.inv_de32; G.inv_le32 = g.inv_le32; G.f_e32 = g.f_e32;
   G.l_e32 = g.l_e32; G.n_e32 = g.n_e32; G.t_e32 = g.t_e32; G.L34inv32 = g.L34inv32; G.s_ce32 = g.s_ce32;
   G.inv_Ac = g.inv_Ac;
+  G.div_wa = g.div_wa;
   G.dz = v.d_dz; G.dzh = v.d_dzh; G.wu = v.d_wu; G.wl = v.d_wl; G.dz2 = v.d_dz2; G.ray = v.d_ray;
   G.ex_ref = s.ex_ref;
   G.inv_dz32 = v.d_inv_dz32; G.wu32 = v.d_wu32; G.wl32 = v.d_wl32; G.inv_dz2_32 = v.d_inv_dz2_32;

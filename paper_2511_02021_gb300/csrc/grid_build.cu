@@ -26,6 +26,7 @@
 //    weights, kinetic-energy weights and least-squares vertex-velocity weights.
 #include <cmath>
 #include <cstdio>
+#include <vector>
 #include "icon_internal.h"
 
 namespace icon {
@@ -483,6 +484,60 @@ void root_tables(double pos[36], int faces[60], signed char redge[144]) {
     }
 }
 
+
+// Tables of the tracer transport (built on demand): the neighbour across each cell
+// edge, least-squares gradient weights per (cell, neighbour) as 3-vectors in the tangent
+// plane at the cell centre, and the offsets R (x_e - x_c1), R (x_e - x_c2) of every edge.
+// Least squares: g = argmin sum_s (q_s - q_c - g . d_s)^2 with d_s the neighbour offset
+// R (x_s - x_c) projected on the tangent plane, solved in the basis e1 = normalize(ref x
+// x_c) (ref the z axis unless |z_c| >= 0.9, else the x axis), e2 = x_c x e1.
+__global__ void k_tracer_cells(int64_t nc, const int* __restrict__ c2e, const int* __restrict__ e2c,
+                               const double* __restrict__ x_c, double R, int* __restrict__ c2c,
+                               double* __restrict__ lsq_c) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  const V3 xc = ld3(x_c, c);
+  V3 d[3];
+  for (int s = 0; s < 3; ++s) {
+    const int e = c2e[3 * c + s];
+    const int a = e2c[2 * e], b = e2c[2 * e + 1];
+    const int nb = (a == (int)c) ? b : a;
+    c2c[3 * c + s] = nb;
+    const V3 xs = ld3(x_c, nb);
+    V3 v = v3((xs.x - xc.x) * R, (xs.y - xc.y) * R, (xs.z - xc.z) * R);
+    const double vn = dot(v, xc);
+    d[s] = v3(v.x - vn * xc.x, v.y - vn * xc.y, v.z - vn * xc.z);
+  }
+  const V3 ref = fabs(xc.z) < 0.9 ? v3(0.0, 0.0, 1.0) : v3(1.0, 0.0, 0.0);
+  const V3 e1 = normalize(cross(ref, xc));
+  const V3 e2 = cross(xc, e1);
+  double p1[3], p2[3];
+  for (int s = 0; s < 3; ++s) {
+    p1[s] = dot(d[s], e1);
+    p2[s] = dot(d[s], e2);
+  }
+  const double m11 = (p1[0] * p1[0] + p1[1] * p1[1]) + p1[2] * p1[2];
+  const double m12 = (p1[0] * p2[0] + p1[1] * p2[1]) + p1[2] * p2[2];
+  const double m22 = (p2[0] * p2[0] + p2[1] * p2[1]) + p2[2] * p2[2];
+  const double det = m11 * m22 - m12 * m12;
+  const double i11 = m22 / det, i12 = -m12 / det, i22 = m11 / det;
+  for (int s = 0; s < 3; ++s) {
+    const double q1 = i11 * p1[s] + i12 * p2[s];
+    const double q2 = i12 * p1[s] + i22 * p2[s];
+    st3(lsq_c, 3 * c + s, v3(q1 * e1.x + q2 * e2.x, q1 * e1.y + q2 * e2.y, q1 * e1.z + q2 * e2.z));
+  }
+}
+
+__global__ void k_tracer_edges(int64_t ne, const int* __restrict__ e2c, const double* __restrict__ x_c,
+                               const double* __restrict__ x_e, double R, double* __restrict__ roff) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  const V3 xe = ld3(x_e, e);
+  for (int j = 0; j < 2; ++j) {
+    const V3 xc = ld3(x_c, e2c[2 * e + j]);
+    st3(roff, 2 * e + j, v3((xe.x - xc.x) * R, (xe.y - xc.y) * R, (xe.z - xc.z) * R));
+  }
+}
 }  // namespace
 
 int exclusive_scan_u32(const unsigned* in, unsigned* out, int64_t n, unsigned* total_dev, DeviceArena& tmp,
@@ -595,6 +650,38 @@ int build_grid_device(icon_grid* grid, cudaStream_t st) {
               (long long)nv, host_u[1], (long long)ne, host_u[2]);
     return ICON_EINDEX;
   }
+  return ICON_OK;
+}
+
+int build_tracer_tables(icon_grid* grid, cudaStream_t st) {
+  GridDev& g = grid->g;
+  if (g.c2c) return ICON_OK;
+  DeviceArena& A = grid->arena;
+  int* c2c = A.get_n<int>(3 * g.nc);
+  double* lsq_c = A.get_n<double>(9 * g.nc);
+  double* roff = A.get_n<double>(6 * g.ne);
+  const Vertical& v = grid->vert;
+  std::vector<double> lev(3 * (size_t)v.ld, 0.0);
+  for (int k = 1; k + 1 < v.N; ++k) lev[k] = 1.0 / (v.z_f[k - 1] - v.z_f[k + 1]);
+  for (int h = 1; h < v.N; ++h) {
+    lev[v.ld + h] = v.z_h[h] - v.z_f[h];
+    lev[2 * v.ld + h] = v.z_h[h] - v.z_f[h - 1];
+  }
+  double* tr_lev = A.get_n<double>(3 * (size_t)v.ld);
+  if (!c2c || !lsq_c || !roff || !tr_lev) {
+    set_error("out of device memory (tracer tables)");
+    return ICON_ENOMEM;
+  }
+  const int TB = 256;
+  k_tracer_cells<<<blocks_for(g.nc, TB), TB, 0, st>>>(g.nc, g.c2e, g.e2c, g.x_c, kR, c2c, lsq_c);
+  k_tracer_edges<<<blocks_for(g.ne, TB), TB, 0, st>>>(g.ne, g.e2c, g.x_c, g.x_e, kR, roff);
+  ICON_CUDA(cudaMemcpyAsync(tr_lev, lev.data(), sizeof(double) * lev.size(), cudaMemcpyHostToDevice, st));
+  ICON_CUDA(cudaGetLastError());
+  ICON_CUDA(cudaStreamSynchronize(st));
+  g.tr_lev = tr_lev;
+  g.c2c = c2c;
+  g.lsq_c = lsq_c;
+  g.roff = roff;
   return ICON_OK;
 }
 

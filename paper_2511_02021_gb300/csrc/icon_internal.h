@@ -35,7 +35,7 @@ enum KernelKind {
   K_VERTEX = 0, K_EDGE_VT, K_CELL_KE, K_EDGE_TEND, K_COLUMN,
   K_DIFF_VERTEX, K_DIFF_DIV, K_DIFF_EDGE, K_DIFF_THETA, K_MASS,
   K_MX_VERTEX, K_MX_EDGE, K_MX_CELL_KE, K_MX_EDGE_TEND, K_MX_COLUMN, K_MX_COLUMN_PREP,
-  K_MX_DIFF_VERTEX, K_MX_DIFF_EDGE, K_MX_DIFF_THETA, K_ENSEMBLE, K_KIND_COUNT
+  K_MX_DIFF_VERTEX, K_MX_DIFF_EDGE, K_MX_DIFF_THETA, K_ENSEMBLE, K_TRACER, K_KIND_COUNT
 };
 static_assert(K_KIND_COUNT <= ICON_KIND_COUNT, "kind table");
 // When a profile is active on this thread, every launch is bracketed by events.
@@ -102,6 +102,13 @@ struct GridDev {
   double* inv_Ac = nullptr;  // 1 / A_c
   double *div_wa = nullptr, *rot_wa = nullptr;             // s l / A_c, s d / A_v
   double *inv_de = nullptr, *inv_le = nullptr, *inv_L34 = nullptr;
+  // tracer transport tables, built on demand (build_tracer_tables)
+  int* c2c = nullptr;           // [Nc][3] neighbour across each edge slot
+  double* lsq_c = nullptr;      // [Nc][3][3] least-squares gradient weights (3-vectors)
+  double* roff = nullptr;       // [Ne][2][3] R (x_e - x_c1), R (x_e - x_c2)
+  // per level [3][ld]: 1/(z_f[k-1] - z_f[k+1]) (0 at the top and bottom level),
+  // z_h[h] - z_f[h] (donor below), z_h[h] - z_f[h-1] (donor above)
+  double* tr_lev = nullptr;
 };
 
 }  // namespace icon
@@ -148,6 +155,11 @@ struct StateDev {
   double *col_rx = nullptr, *col_tx = nullptr, *col_px = nullptr, *col_gm = nullptr;
   double *col_ri = nullptr, *col_mm = nullptr;
   double* colconst = nullptr;
+  // tracers (mixing ratios, FP64 [t][Nc][ld]) and their transport scratch
+  int ntr = 0;
+  double* q = nullptr;
+  double *tr_rho0 = nullptr, *tr_rho1 = nullptr, *tr_W = nullptr;   // [Nc][ld] (rho1, W: mixed only)
+  double *tr_gx = nullptr, *tr_gy = nullptr, *tr_gz = nullptr, *tr_V = nullptr, *tr_F = nullptr;
   // frozen parts of the column system shared by predictor and corrector (mixed mode;
   // NULL when they would not fit, then both stages compute them)
   double* fac64 = nullptr;
@@ -202,6 +214,11 @@ int selftest_conversions(int64_t n, unsigned* host_fails);
 namespace icon {
 // grid_build.cu
 int build_grid_device(icon_grid* grid, cudaStream_t st);
+int build_tracer_tables(icon_grid* grid, cudaStream_t st);
+// tracer.cu
+int tracer_alloc(icon_state* st, int ntracers);
+void tracer_begin(icon_state* st, cudaStream_t stream);
+void tracer_end(icon_state* st, double dt, cudaStream_t stream);
 // init.cu
 void make_vertical(Vertical& v, int nlev, double top_m, double stretch_s, double damp_m);
 int init_state_device(icon_state* st, uint64_t seed, int case_id, const icon_case_params& p,

@@ -38,6 +38,11 @@ def test_host_argument_checks(built_lib):
     assert lib.icon_dycore_step(None, 1.0, 1) == C.ICON_EINVAL
     assert lib.icon_global_mass(None, None) == C.ICON_EINVAL
     assert lib.icon_ensemble_create(None, 0, ctypes.byref(h)) == C.ICON_EINVAL
+    n = ctypes.c_int()
+    assert lib.icon_state_add_tracers(None, 1) == C.ICON_EINVAL
+    assert lib.icon_state_tracers(None, ctypes.byref(n)) == C.ICON_EINVAL
+    assert lib.icon_state_set_tracer(None, 0, None, 0) == C.ICON_EINVAL
+    assert lib.icon_state_copy_tracer(None, 0, None, 0) == C.ICON_EINVAL
     lib.icon_grid_free(None)
     lib.icon_state_free(None)
     lib.icon_ensemble_free(None)
