@@ -70,9 +70,10 @@ MX_COLUMN_FP64_OPS = 36
 # quarter of the device memory): executed 47.5 (predictor) and 64.5 (corrector).
 MX_COLUMN_RECOMPUTE_FP64_OPS = 56
 # FP64 instructions per cell-level of the tracer transport of one tracer: cell kernel
-# (least-squares gradient 12, vertical slope, departure point and flux 14), edge kernel
-# (25 per edge-level, 1.5 edges per cell), update (12).
-TRACER_FP64_OPS = 75
+# (least-squares gradient 12, vertical slope, departure point and flux 12), edge kernel
+# (27 per edge-level, 1.5 edges per cell), update (12); executed (ncu, R2B6/90): 24.2,
+# 41.0 and 12.0 (profiles/ncu_tracer_r2b6_l90.md).
+TRACER_FP64_OPS = 77
 # DRAM bytes (read + write) per launch of the dominant kernel kind, from ncu captures of the
 # current kernels (mean of predictor and corrector; same files): FP64 column at R2B6/90
 # measured; mixed column at R2B6/90 measured and scaled by cells to R2B8/90; recomputing
