@@ -375,6 +375,34 @@ __global__ void k_rm_to_lm(const double* __restrict__ b, double* __restrict__ a,
   int64_t k = t / n, i = t % n;
   a[t] = b[i * ld + k];
 }
+// host-order [n][nlev] staging <-> the device layout of a field: mode 0 FP64 rows of
+// ld, mode 1 FP32 rows of ld, mode 2 FP64 level-major [k][n]
+__global__ void k_unpack(const double* __restrict__ stage, void* __restrict__ dst, int64_t n, int nlev, int ld,
+                         int mode) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * nlev) return;
+  if (mode == 2) {
+    const int64_t k = t / n, i = t % n;
+    static_cast<double*>(dst)[t] = stage[i * nlev + k];
+  } else {
+    const int64_t i = t / nlev, k = t % nlev;
+    if (mode == 0) static_cast<double*>(dst)[i * ld + k] = stage[t];
+    else static_cast<float*>(dst)[i * ld + k] = (float)stage[t];
+  }
+}
+__global__ void k_pack(const void* __restrict__ src, double* __restrict__ stage, int64_t n, int nlev, int ld,
+                       int mode) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * nlev) return;
+  if (mode == 2) {
+    const int64_t k = t / n, i = t % n;
+    stage[i * nlev + k] = static_cast<const double*>(src)[t];
+  } else {
+    const int64_t i = t / nlev, k = t % nlev;
+    stage[t] = mode == 0 ? static_cast<const double*>(src)[i * ld + k]
+                         : (double)static_cast<const float*>(src)[i * ld + k];
+  }
+}
 
 }  // namespace
 }  // namespace icon
@@ -626,20 +654,16 @@ int icon_state_copy_field(const icon_state* st, int field_id, double* host_dst, 
     set_error("icon_state_copy_field: field %d has %lld elements, got %zu", field_id, (long long)(n * nlev), count);
     return ICON_EINVAL;
   }
+  // pack into host order on the device, then one contiguous transfer
   const int ld = st->grid->vert.ld;
   cudaStream_t stream = current_stream();
-  const double* src = static_cast<const double*>(ptr);
   DeviceArena tmp;
   tmp.al = st->arena.al;
-  if (f32 || lm) {
-    double* d = tmp.get_n<double>((size_t)n * ld);
-    if (!d) { set_error("icon_state_copy_field: out of device memory"); return ICON_ENOMEM; }
-    if (f32) k_f32_to_f64<<<blocks_for(n * ld, 256), 256, 0, stream>>>(static_cast<const float*>(ptr), d, n * ld);
-    else k_lm_to_rm<<<blocks_for(n * nlev, 256), 256, 0, stream>>>(static_cast<const double*>(ptr), d, n, nlev, ld);
-    src = d;
-  }
-  cudaError_t e = cudaMemcpy2DAsync(host_dst, sizeof(double) * nlev, src, sizeof(double) * ld,
-                                    sizeof(double) * nlev, n, cudaMemcpyDeviceToHost, stream);
+  double* stage = tmp.get_n<double>((size_t)n * nlev);
+  if (!stage) { set_error("icon_state_copy_field: out of device memory"); return ICON_ENOMEM; }
+  k_pack<<<blocks_for(n * nlev, 256), 256, 0, stream>>>(ptr, stage, n, nlev, ld, lm ? 2 : (f32 ? 1 : 0));
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host_dst, stage, sizeof(double) * n * nlev, cudaMemcpyDeviceToHost, stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   tmp.release();
   if (e != cudaSuccess) return cuda_fail(e, "icon_state_copy_field");
@@ -660,23 +684,19 @@ int icon_state_set_field(icon_state* st, int field_id, const double* host_src, s
     set_error("icon_state_set_field: field %d has %lld elements, got %zu", field_id, (long long)(n * nlev), count);
     return ICON_EINVAL;
   }
+  // one contiguous transfer into a staging buffer, then unpack into the device layout
   const int ld = st->grid->vert.ld;
   cudaStream_t stream = current_stream();
   DeviceArena tmp;
   tmp.al = st->arena.al;
-  double* dst = static_cast<double*>(ptr);
-  if (f32 || lm) {
-    dst = tmp.get_n<double>((size_t)n * ld);
-    if (!dst) { set_error("icon_state_set_field: out of device memory"); return ICON_ENOMEM; }
-  }
-  cudaError_t e = cudaMemcpy2DAsync(dst, sizeof(double) * ld, host_src, sizeof(double) * nlev,
-                                    sizeof(double) * nlev, n, cudaMemcpyHostToDevice, stream);
-  if (e == cudaSuccess && f32) {
-    k_f64_to_f32<<<blocks_for(n * ld, 256), 256, 0, stream>>>(dst, static_cast<float*>(ptr), n * ld);
+  double* stage = tmp.get_n<double>((size_t)n * nlev);
+  if (!stage) { set_error("icon_state_set_field: out of device memory"); return ICON_ENOMEM; }
+  cudaError_t e = cudaMemcpyAsync(stage, host_src, sizeof(double) * n * nlev, cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) {
+    k_unpack<<<blocks_for(n * nlev, 256), 256, 0, stream>>>(stage, ptr, n, nlev, ld, lm ? 2 : (f32 ? 1 : 0));
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && lm) {
-    k_rm_to_lm<<<blocks_for(n * nlev, 256), 256, 0, stream>>>(dst, static_cast<double*>(ptr), n, nlev, ld);
     mixed_refresh_shadows(st, stream);
     e = cudaGetLastError();
   }

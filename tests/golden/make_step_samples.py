@@ -5,8 +5,9 @@
 Runs the oracle (and nothing else) on the R2B6 grid with 90 levels, the balanced jet
 with its 1 m/s wind bump and no theta_v noise (seed 1), one step of dt = 90 s in 5
 substeps: the workload the throughput benchmark times. It stores, for a fixed random
-sample of cells and edges, every level of every prognostic field and of the two
-step-mean mass fluxes, plus the L2 norm of each full field, in
+sample of cells and edges, every level of every prognostic field, of the two
+step-mean mass fluxes and of one tracer (q0 = 1 + z/2 with z the unit-sphere height
+of the cell centre) transported with them, plus the L2 norm of each full field, in
 r2b6_l90_jet_step_samples.json. The oracle needs about four minutes and 14 GB here.
 """
 import json
@@ -33,6 +34,10 @@ def main():
     s1, acc = O.dycore_step(g, v, s0, DT, NSUB)
     out = dict(s1, **acc)
     m1 = O.global_mass(g, v, s1)
+    # one tracer, q0 = 1 + z/2 (unit-sphere z of the cell centre) at every level,
+    # transported with the step's mean fluxes
+    q0 = np.repeat(1.0 + 0.5 * g.x_c[:, 2:3], NLEV, axis=1)
+    out["tracer"] = O.tracer_step(g, v, q0, s0["rho"], s1["rho"], acc["mflx"], acc["wflx"], DT)
     nc, ne = s0["rho"].shape[0], s0["vn"].shape[0]
     rng = np.random.default_rng(SAMPLE_SEED)
     cells = sorted(set([0, nc - 1] + rng.choice(nc, N_SAMPLE, replace=False).tolist()))
@@ -49,7 +54,7 @@ def main():
         idx = edges if f == "vn" else cells
         doc["init"][f] = [[float(x) for x in s0[f][i]] for i in idx]
         doc["norm_init"][f] = float(np.linalg.norm(s0[f]))
-    for f in ("vn", "w", "rho", "theta_v", "exner", "mflx", "wflx"):
+    for f in ("vn", "w", "rho", "theta_v", "exner", "mflx", "wflx", "tracer"):
         idx = edges if f in ("vn", "mflx") else cells
         doc["step"][f] = [[float(x) for x in out[f][i]] for i in idx]
         doc["norm_step"][f] = float(np.linalg.norm(out[f]))
