@@ -867,9 +867,7 @@ __global__ void __launch_bounds__(512) k_mx_gather_tile(MxGeo G, MxColArgs a) {
 //                     memory into the cells' [c][ld] rows.
 // Same arithmetic as the corrector branch of mx_column_fac_item (which the persistent
 // ensemble keeps in one pass).
-__global__ void __launch_bounds__(128) k_mx_corr_solve(MxGeo G, MxColArgs a) {
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= G.nc) return;
+__device__ inline void mx_corr_solve_item(const MxGeo& G, const MxColArgs& a, int64_t c) {
   const int N = G.N, ld = G.ld;
   const int64_t nc = G.nc, H = N + 1;
   const double dtau = a.dtau;
@@ -903,11 +901,22 @@ __global__ void __launch_bounds__(128) k_mx_corr_solve(MxGeo G, MxColArgs a) {
 #undef F64
 }
 
+__global__ void __launch_bounds__(128) k_mx_corr_solve(MxGeo G, MxColArgs a) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < G.nc) mx_corr_solve_item(G, a, c);
+}
+
 constexpr int kUpdCells = 32, kUpdLevels = 32;
-__global__ void __launch_bounds__(256) k_mx_corr_update(MxGeo G, MxColArgs a) {
-  __shared__ float sf[4][kUpdLevels][kUpdCells + 1];   // theta_v, rho, pi - pi_ref, w
+struct UpdTile {
+  float sf[4][kUpdLevels][kUpdCells + 1];              // theta_v, rho, pi - pi_ref, w
+};
+
+// one tile of 32 cells starting at c0; every thread of the block takes part (a multiple
+// of 32 threads); returns false if a non-finite value appeared
+__device__ inline bool mx_corr_update_tile(const MxGeo& G, const MxColArgs& a, int64_t c0, UpdTile& T) {
+  auto& sf = T.sf;
   const int N = G.N, ld = G.ld;
-  const int64_t nc = G.nc, H = N + 1, c0 = (int64_t)blockIdx.x * kUpdCells;
+  const int64_t nc = G.nc, H = N + 1;
   const double dtau = a.dtau;
   const double* __restrict__ cc = a.cc;
   const double* __restrict__ fac = a.fac64;
@@ -969,7 +978,13 @@ __global__ void __launch_bounds__(256) k_mx_corr_update(MxGeo G, MxColArgs a) {
     __syncthreads();
   }
   if (tid < kUpdCells && c < nc) a.w32[c * ld + N] = 0.0f;
-  if (__syncthreads_or(!ok) && tid == 0) atomicOr(a.status, 1u);
+  return ok;
+}
+
+__global__ void __launch_bounds__(256) k_mx_corr_update(MxGeo G, MxColArgs a) {
+  __shared__ UpdTile T;
+  const bool ok = mx_corr_update_tile(G, a, (int64_t)blockIdx.x * kUpdCells, T);
+  if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(a.status, 1u);
 }
 
 template <int NMAX, bool CORR>
@@ -1427,7 +1442,11 @@ constexpr int kChunk = 4;   // consecutive work items per warp
 template <int NMAX, bool ALLFAC>
 __global__ void __launch_bounds__(128, 8) k_ensemble_step(EnsArgs A) {
   __shared__ int64_t s_off_v[64], s_off_e[64], s_off_c[64], s_off_t[64];
-  __shared__ GatherTile<16> tileT;
+  __shared__ union {
+    GatherTile<16> g;
+    UpdTile u;
+  } tiles;
+  GatherTile<16>& tileT = tiles.g;
   for (int i = threadIdx.x; i < A.nm; i += blockDim.x) {
     s_off_v[i] = A.m[i].off_v;
     s_off_e[i] = A.m[i].off_e;
@@ -1492,10 +1511,21 @@ __global__ void __launch_bounds__(128, 8) k_ensemble_step(EnsArgs A) {
         const MemberDev& M = A.m[m];
         if (ALLFAC) {
           if (stage == 0) mx_column_fac_item<NMAX, false>(M.G, M.ca[0], i - M.off_c);
-          else mx_column_fac_item<NMAX, true>(M.G, M.ca[1], i - M.off_c);
+          else mx_corr_solve_item(M.G, M.ca[1], i - M.off_c);
         } else {
           if (stage == 0) mx_column_any<NMAX, false>(M.G, M.ca[0], i - M.off_c);
           else mx_column_any<NMAX, true>(M.G, M.ca[1], i - M.off_c);
+        }
+      }
+      if (ALLFAC && stage == 1) {
+        // corrector updates: element-parallel 32-cell tiles (the member's tile list)
+        if (!sync()) return;
+        static_assert(kUpdCells == kGatherCells, "the corrector update reuses the gather tile list");
+        for (int64_t t = blockIdx.x; t < A.tot_t; t += gridDim.x) {
+          const int m = find_member(s_off_t, A.nm, t);
+          const MemberDev& M = A.m[m];
+          if (!mx_corr_update_tile(M.G, M.ca[1], (t - M.off_t) * kUpdCells, tiles.u)) atomicOr(M.ca[1].status, 1u);
+          __syncthreads();
         }
       }
       if (!sync()) return;
