@@ -80,12 +80,15 @@ __device__ inline bool finite_bits(double x) {
   return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
 }
 
+// The warp-per-entity FP64 kernels are held to 64 registers (4 blocks of 8 warps per SM):
+// they are bound by the FP64 pipe, and the extra warps hide more load latency than the few
+// spilled registers of the rows kernel cost (R2B6/90 step 97.5 -> 94.4 ms).
 __device__ inline int64_t warp_entity() {
   return (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
 }
 
 // zeta_v (full levels) and w_v (half levels)
-__global__ void __launch_bounds__(256) k_vertex(Geo64 G, const double* __restrict__ vn, const double* __restrict__ w,
+__global__ void __launch_bounds__(256, 4) k_vertex(Geo64 G, const double* __restrict__ vn, const double* __restrict__ w,
                                                 double* __restrict__ zeta, double* __restrict__ w_v) {
   const int64_t v = warp_entity();
   if (v >= G.nv) return;
@@ -168,7 +171,7 @@ struct EdgeArgs {
 // for l < 31, full level k = h), each half-level interpolant and cell-pair sum formed
 // once and handed to the lane below with a shuffle, factors of 1/2 folded into
 // exactly-scaled constants, and the per-edge constants cpd / d_e hoisted.
-__global__ void __launch_bounds__(256) k_edge_tend(Geo64 G, EdgeArgs a) {
+__global__ void __launch_bounds__(256, 4) k_edge_tend(Geo64 G, EdgeArgs a) {
   const int64_t e = warp_entity();
   if (e >= G.ne) return;
   const int lane = threadIdx.x & 31, ld = G.ld, N = G.N;
@@ -261,7 +264,7 @@ struct ColArgs {
 
 // windows of 31 levels: lane l holds full level k = base + l and the half level above
 // it (h = k); lane 31 only supplies the half level below lane 30's full level
-__global__ void __launch_bounds__(256) k_col_rows(Geo64 G, ColArgs a) {
+__global__ void __launch_bounds__(256, 4) k_col_rows(Geo64 G, ColArgs a) {
   const int64_t c = warp_entity();
   if (c >= G.nc) return;
   const int lane = threadIdx.x & 31, ld = G.ld, N = G.N;
@@ -427,7 +430,7 @@ __global__ void __launch_bounds__(256) k_col_update(Geo64 G, ColArgs a) {
 }
 
 // ---------------------------------------------------------------- diffusion
-__global__ void __launch_bounds__(256) k_diff_vertex(Geo64 G, const double* __restrict__ vn, double* __restrict__ ux,
+__global__ void __launch_bounds__(256, 4) k_diff_vertex(Geo64 G, const double* __restrict__ vn, double* __restrict__ ux,
                                                      double* __restrict__ uy, double* __restrict__ uz,
                                                      double* __restrict__ zeta) {
   const int64_t v = warp_entity();
@@ -474,7 +477,7 @@ __device__ inline double dot3(double ax, double ay, double az, const double* b) 
   return (ax * b[0] + ay * b[1]) + az * b[2];
 }
 
-__global__ void __launch_bounds__(256) k_diff_edge(Geo64 G, double* __restrict__ vn, const double* __restrict__ ux,
+__global__ void __launch_bounds__(256, 4) k_diff_edge(Geo64 G, double* __restrict__ vn, const double* __restrict__ ux,
                                                    const double* __restrict__ uy, const double* __restrict__ uz,
                                                    const double* __restrict__ zeta, const double* __restrict__ divc,
                                                    const double* __restrict__ thv, double* __restrict__ Kh_out,
