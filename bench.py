@@ -364,43 +364,6 @@ def run_gpu(args, wl, rank, world, local_rank):
                  "mass_rel_drift": res_m["mass_rel_drift"], "roofline": res_m["roof"],
                  "kernels": res_m["breakdown"], "gpu_launches": res_m["kps"] * args.steps,
                  "hbm_roofline": step_hbm_roofline(res_m["value"], 1, hbm_peak)}
-    # tracer transport (one tracer, same workload and precision): its kernel time per step
-    # from the profiled eager steps, and the step time with it from timed graph replays
-    tracer = None
-    if not args.no_tracer:
-        tst = None
-        try:
-            tst = C.icon_state_init_ex(grid, wl.seed + rank, wl.case, noise_K=wl.noise_K, precision=wl.precision)
-            C.icon_state_add_tracers(tst, 1)
-            xc = C.icon_grid_copy_table(grid, "x_c")
-            C.icon_state_set_tracer(tst, grid, N, 0, np.repeat(1.0 + 0.5 * xc[:, 2:3], N, axis=1))
-            for _ in range(args.warmup):
-                C.icon_dycore_step(tst, wl.dt, wl.nsub)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(args.steps):
-                C.icon_dycore_step_async(tst, wl.dt, wl.nsub)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            C.icon_state_status(tst)
-            ms_t = e0.elapsed_time(e1) / args.steps
-            kms, kn = None, None
-            for _ in range(2):
-                kms, kn = C.icon_dycore_step_profile(tst, wl.dt, wl.nsub, kms, kn)
-            names = [C.icon_kernel_kind_name(k) for k in range(C.ICON_KIND_COUNT)]
-            t_ms = kms[names.index("tracer_transport")] / 2
-            ops = nc * N * TRACER_FP64_OPS
-            tracer = {"tracers": 1, "ms_per_step_with_tracer": ms_t, "ms_per_step_without": ms / args.steps,
-                      "tracer_kernels_ms_per_step": t_ms,
-                      "roofline": {"bound": "alu", "achieved": ops / (t_ms * 1e-3) / 1e9,
-                                   "peak": FP64_INSTR_PEAK / 1e9, "unit": "G FP64 instr/s",
-                                   "frac": ops / (t_ms * 1e-3) / FP64_INSTR_PEAK, "traffic": None}}
-        except C.IconError as exc:
-            tracer = {"skipped": str(exc)}
-        finally:
-            if tst is not None:
-                C.icon_state_free(tst)
     m_drift = res["mass_rel_drift"]
     err_vs_fp64 = None
     if wl.precision == 1 and not args.no_mixed:
@@ -449,6 +412,40 @@ def run_gpu(args, wl, rank, world, local_rank):
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e = {"value": nc * N * wl.nsub / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": h2d + 8}
+
+    # tracer transport (one tracer, same workload and precision), on the state the
+    # end-to-end loop used: its kernel time per step from the profiled eager steps, and
+    # the step time with it from timed graph replays
+    tracer = None
+    if not args.no_tracer:
+        try:
+            C.icon_state_add_tracers(st, 1)
+            xc = C.icon_grid_copy_table(grid, "x_c")
+            C.icon_state_set_tracer(st, grid, N, 0, np.repeat(1.0 + 0.5 * xc[:, 2:3], N, axis=1))
+            for _ in range(args.warmup):
+                C.icon_dycore_step(st, wl.dt, wl.nsub)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                C.icon_dycore_step_async(st, wl.dt, wl.nsub)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            C.icon_state_status(st)
+            ms_t = e0.elapsed_time(e1) / args.steps
+            kms, kn = None, None
+            for _ in range(2):
+                kms, kn = C.icon_dycore_step_profile(st, wl.dt, wl.nsub, kms, kn)
+            names = [C.icon_kernel_kind_name(k) for k in range(C.ICON_KIND_COUNT)]
+            t_ms = kms[names.index("tracer_transport")] / 2
+            ops = nc * N * TRACER_FP64_OPS
+            tracer = {"tracers": 1, "ms_per_step_with_tracer": ms_t, "ms_per_step_without": ms / args.steps,
+                      "tracer_kernels_ms_per_step": t_ms,
+                      "roofline": {"bound": "alu", "achieved": ops / (t_ms * 1e-3) / 1e9,
+                                   "peak": FP64_INSTR_PEAK / 1e9, "unit": "G FP64 instr/s",
+                                   "frac": ops / (t_ms * 1e-3) / FP64_INSTR_PEAK, "traffic": None}}
+        except C.IconError as exc:
+            tracer = {"skipped": str(exc)}
 
     C.icon_state_free(st)
     C.icon_grid_free(grid)
