@@ -748,7 +748,7 @@ __global__ void __launch_bounds__(512, 2) k_mx_edge_tend(MxGeo G, MxEdgeArgs a) 
   mx_edge_tend_item<LPE>(G, a, item, lane);
 }
 template <int LPE>
-__global__ void __launch_bounds__(512) k_mx_diff_vertex(MxGeo G, const float* vn, float* ux, float* uy, float* uz,
+__global__ void __launch_bounds__(512, 2) k_mx_diff_vertex(MxGeo G, const float* vn, float* ux, float* uy, float* uz,
                                                         float* zeta, float* divc) {
   // vertices first, then cells (divergence): both only read vn
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -850,7 +850,7 @@ __device__ inline void mx_gather_tile_body(const MxGeo& G, const MxColArgs& a, i
 }
 
 template <int LPE, bool CORR>
-__global__ void __launch_bounds__(512) k_mx_gather_tile(MxGeo G, MxColArgs a) {
+__global__ void __launch_bounds__(512, 3) k_mx_gather_tile(MxGeo G, MxColArgs a) {
   __shared__ GatherTile<LPE> T;
   mx_gather_tile_body<LPE, CORR>(G, a, (int64_t)blockIdx.x * kGatherCells, T);
 }
