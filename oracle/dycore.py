@@ -32,6 +32,7 @@ Step (dt, nsub substeps of dtau = dt/nsub, off-centring beta = 0.65):
 """
 import numpy as np
 
+from .grid import R_EARTH
 from .state import GRAV, RD, CPD, CVD, to_half
 
 BETA = 0.65             # vertical off-centring (implicit weight)
@@ -234,15 +235,31 @@ def diffusion(g, v, s, dt):
     return out, Kh
 
 
+# ------------------------------------------------------------------ divergence damping (option)
+def divergence_damping(g, vn, c4):
+    """DD (fourth-order divergence damping, an option; ICON applies one in its corrector,
+    the paper prints none): vn - c4 Abar^2 grad(div(grad(div vn))), Abar = 4 pi R^2 / Nc
+    the mean cell area, with the O1/O2 operators. Rotational fields (div = 0) pass
+    unchanged; a divergent mode of wavenumber k is scaled by about 1 - c4 Abar^2 k^4."""
+    abar = 4.0 * np.pi * R_EARTH * R_EARTH / g.nc
+    D = divergence(g, vn)
+    L = divergence(g, gradient(g, D))
+    return vn - (c4 * abar * abar) * gradient(g, L)
+
+
 # ------------------------------------------------------------------ step and mass
-def substep(g, v, s, dtau, nsub, acc):
-    """One predictor-corrector substep; updates the accumulators in `acc`."""
+def substep(g, v, s, dtau, nsub, acc, divdamp4=0.0):
+    """One predictor-corrector substep; updates the accumulators in `acc`. With
+    divdamp4 > 0 the corrector's vn^{n+1} is divergence-damped (DD) before its mass and
+    heat fluxes are formed."""
     A_vn0, A_w0 = tendencies(g, v, s)
     vn_star = s["vn"] + dtau * (A_vn0 - pressure_gradient(g, s))
     cs, _ = column(g, v, s, vn_star, A_w0, edge_mean(g, s["rho"]), edge_mean(g, s["theta_v"]), dtau)
     s_star = dict(cs, vn=vn_star)
     A_vn1, A_w1 = tendencies(g, v, s_star)
     vn_new = s["vn"] + dtau * (0.5 * (A_vn0 + A_vn1) - pressure_gradient(g, s_star))
+    if divdamp4 > 0.0:
+        vn_new = divergence_damping(g, vn_new, divdamp4)
     rho_e1 = edge_mean(g, s_star["rho"])
     cn, rho_ic0 = column(g, v, s, vn_new, 0.5 * (A_w0 + A_w1), rho_e1,
                          edge_mean(g, s_star["theta_v"]), dtau)
@@ -251,13 +268,13 @@ def substep(g, v, s, dtau, nsub, acc):
     return dict(cn, vn=vn_new)
 
 
-def dycore_step(g, v, s, dt, nsub):
+def dycore_step(g, v, s, dt, nsub, divdamp4=0.0):
     """One step: nsub substeps of dt/nsub, then diffusion with dt. Returns
     (new state, accumulators {mflx (Ne,N), wflx (Nc,N+1)})."""
     dtau = dt / nsub
     acc = {"mflx": np.zeros((g.ne, v.N)), "wflx": np.zeros((g.nc, v.N + 1))}
     for _ in range(nsub):
-        s = substep(g, v, s, dtau, nsub, acc)
+        s = substep(g, v, s, dtau, nsub, acc, divdamp4)
     s, _ = diffusion(g, v, s, dt)
     return s, acc
 
