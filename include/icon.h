@@ -256,7 +256,7 @@ int icon_selftest(long long n, unsigned* failures);
 /* Name of kernel kind i (0 <= i < ICON_KIND_COUNT), or NULL. Mixed-precision
  * stencil kinds: 10 vertex, 11 edge diagnostics, 12 cell kinetic energy,
  * 13 edge tendency, 15 column-input gather, 16 diffusion vertex/divergence;
- * 20 tracer transport. */
+ * 20 tracer transport, 21 divergence damping (option). */
 const char* icon_kernel_kind_name(int kind);
 #define ICON_KIND_COUNT 24
 
@@ -264,6 +264,22 @@ const char* icon_kernel_kind_name(int kind);
 int icon_state_precision(const icon_state* state, int* out);
 
 void icon_state_free(icon_state* state);
+
+/* ---------------------------------------------------------------- options */
+
+/* Option ids of icon_state_set_option. */
+enum {
+  /* Fourth-order divergence damping of the corrector's vn^{n+1} before its fluxes are
+   * formed: vn -= c4 Abar^2 grad(div(grad(div vn))), Abar = 4 pi R^2 / Nc, with the
+   * step's own divergence and gradient operators (an ICON option; the paper prints none).
+   * value = c4 in [0, 0.05]; 0 (the default) turns it off. Both precisions; not in the
+   * persistent ensemble (icon_ensemble_create rejects members that set it). */
+  ICON_OPT_DIVDAMP4 = 1
+};
+
+/* Set an option of a state; the next step records a new graph. ICON_EINVAL for an
+ * unknown option or a value outside its range. */
+int icon_state_set_option(icon_state* state, int option, double value);
 
 /* ---------------------------------------------------------------- tracers */
 

@@ -77,6 +77,7 @@ def _load():
         "icon_ensemble_set_option": (I, [P, I, ctypes.c_longlong]),
         "icon_state_tiling": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "icon_state_set_tiling": (I, [P, I, I, I]),
+        "icon_state_set_option": (I, [P, I, D]),
         "icon_state_add_tracers": (I, [P, I]), "icon_state_tracers": (I, [P, ctypes.POINTER(I)]),
         "icon_state_set_tracer": (I, [P, I, P, S]), "icon_state_copy_tracer": (I, [P, I, P, S]),
     }
@@ -330,3 +331,11 @@ def icon_state_copy_tracer(state, grid, nlev, t):
     out = np.empty(_tracer_shape(grid, nlev), dtype=np.float64)
     _check(_lib.icon_state_copy_tracer(state, t, out.ctypes.data, out.size))
     return out
+
+
+# ---------------------------------------------------------------- options
+ICON_OPT_DIVDAMP4 = 1
+
+
+def icon_state_set_option(state, option, value):
+    _check(_lib.icon_state_set_option(state, option, float(value)))

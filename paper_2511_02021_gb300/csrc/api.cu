@@ -60,7 +60,7 @@ static const char* kKindNames[K_KIND_COUNT] = {
     "vertex_curl_wmean", "edge_vt_ke", "cell_ke", "edge_tendency_flux", "column_solve",
     "diff_vertex", "diff_div", "diff_edge", "diff_theta", "global_mass",
     "mx_vertex", "mx_edge_diag", "mx_cell_ke", "mx_edge_tendency_flux", "mx_column_solve", "mx_column_prep",
-    "mx_diff_vertex", "mx_diff_edge", "mx_diff_theta", "ensemble_persistent", "tracer_transport"};
+    "mx_diff_vertex", "mx_diff_edge", "mx_diff_theta", "ensemble_persistent", "tracer_transport", "divergence_damping"};
 
 Allocator current_allocator() {
   std::lock_guard<std::mutex> lk(g_alloc_mu);
@@ -776,6 +776,21 @@ int icon_state_add_tracers(icon_state* st, int ntracers) {
   return ICON_OK;
 }
 
+int icon_state_set_option(icon_state* st, int option, double value) {
+  if (!st) { set_error("icon_state_set_option: state is NULL"); return ICON_EINVAL; }
+  if (option != ICON_OPT_DIVDAMP4) { set_error("icon_state_set_option: unknown option %d", option); return ICON_EINVAL; }
+  if (!(value >= 0.0 && value <= 0.05)) {
+    set_error("icon_state_set_option: divergence damping coefficient %g outside [0, 0.05]", value);
+    return ICON_EINVAL;
+  }
+  st->divdamp4 = value;
+  if (st->graph) {                      // the step's graph changes with the option
+    cudaGraphExecDestroy(st->graph);
+    st->graph = nullptr;
+  }
+  return ICON_OK;
+}
+
 int icon_state_tracers(const icon_state* st, int* out) {
   if (!st || !out) { set_error("icon_state_tracers: NULL argument"); return ICON_EINVAL; }
   *out = st->s.ntr;
@@ -817,6 +832,10 @@ int icon_ensemble_create(icon_state* const* members, int n, icon_ensemble** out)
     if (!members[i]) { set_error("icon_ensemble_create: member %d is NULL", i); return ICON_EINVAL; }
     if (members[i]->s.precision != ICON_MIXED) {
       set_error("icon_ensemble_create: members must be mixed-precision states");
+      return ICON_EINVAL;
+    }
+    if (members[i]->divdamp4 != 0.0) {
+      set_error("icon_ensemble_create: the persistent ensemble has no divergence damping (member %d sets it)", i);
       return ICON_EINVAL;
     }
     if (members[i]->s.ntr != 0) {

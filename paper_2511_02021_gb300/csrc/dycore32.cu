@@ -31,6 +31,7 @@
 // 16: one or two entities per warp) and the block size from the autotuner; each
 // output is computed by one lane with a fixed summation order, so the results do
 // not depend on the tile shape.
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <map>
@@ -136,6 +137,7 @@ struct MxEdgeArgs {
   float dtau;
   double inv_nsub;
   int corrector;
+  int skip_flux;                           // fluxes formed after divergence damping instead
 };
 
 // vn tendency and update, horizontal flux integrals, edge part of the w advection.
@@ -199,10 +201,68 @@ __device__ inline void mx_edge_tend_item(const MxGeo& G, const MxEdgeArgs& a, in
       a.Avn0[o + k] = A;
     }
     a.vn_out[o + k] = vnew;
+    if (a.skip_flux) continue;
     const float F = 0.5f * (rho[c1 + k] + rho[c2 + k]) * vnew;
     a.phi[o + k] = F;
     a.gth[o + k] = (le * F) * th_e;
     if (a.corrector) a.mflx[o + k] += f32_to_f64(F) * a.inv_nsub;
+  }
+}
+
+// fourth-order divergence damping of the corrector's vn^{n+1} (option), FP32 like the other
+// stencils: cell divergence, its cell Laplacian, then the edge update with the corrector's
+// fluxes (the same expressions as the edge tendency) and the FP64 step-mean mass flux
+__global__ void __launch_bounds__(256) k_mx_dd_div(MxGeo G, const float* __restrict__ vn, float* __restrict__ D) {
+  const int64_t c = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (c >= G.nc) return;
+  const int lane = threadIdx.x & 31, ld = G.ld;
+  int64_t E[3];
+  float dw[3];
+  for (int s = 0; s < 3; ++s) {
+    E[s] = (int64_t)G.c2e[3 * c + s] * ld;
+    dw[s] = G.div_w32[3 * c + s];
+  }
+  for (int k = lane; k < G.N; k += 32) D[c * ld + k] = dw[0] * vn[E[0] + k] + dw[1] * vn[E[1] + k] + dw[2] * vn[E[2] + k];
+}
+
+__global__ void __launch_bounds__(256) k_mx_dd_lap(MxGeo G, const float* __restrict__ D, float* __restrict__ L) {
+  const int64_t c = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (c >= G.nc) return;
+  const int lane = threadIdx.x & 31, ld = G.ld;
+  int64_t A[3], B[3];
+  float wt[3];
+  for (int s = 0; s < 3; ++s) {
+    const int e = G.c2e[3 * c + s];
+    A[s] = (int64_t)G.e2c[2 * e] * ld;
+    B[s] = (int64_t)G.e2c[2 * e + 1] * ld;
+    wt[s] = G.div_w32[3 * c + s] * G.inv_de32[e];
+  }
+  for (int k = lane; k < G.N; k += 32)
+    L[c * ld + k] = wt[0] * (D[B[0] + k] - D[A[0] + k]) + wt[1] * (D[B[1] + k] - D[A[1] + k]) +
+                    wt[2] * (D[B[2] + k] - D[A[2] + k]);
+}
+
+struct MxDDArgs {
+  const float *L, *rho, *thv;
+  float *vn, *phi, *gth;
+  double* mflx;
+  float scale;                             // c4 Abar^2
+  double inv_nsub;
+};
+
+__global__ void __launch_bounds__(256) k_mx_dd_edge(MxGeo G, MxDDArgs a) {
+  const int64_t e = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (e >= G.ne) return;
+  const int lane = threadIdx.x & 31, ld = G.ld;
+  const int64_t c1 = (int64_t)G.e2c[2 * e] * ld, c2 = (int64_t)G.e2c[2 * e + 1] * ld, o = e * ld;
+  const float sc = a.scale * G.inv_de32[e], le = G.l_e32[e];
+  for (int k = lane; k < G.N; k += 32) {
+    const float vn = a.vn[o + k] - sc * (a.L[c2 + k] - a.L[c1 + k]);
+    a.vn[o + k] = vn;
+    const float F = 0.5f * (a.rho[c1 + k] + a.rho[c2 + k]) * vn;
+    a.phi[o + k] = F;
+    a.gth[o + k] = (le * F) * (0.5f * (a.thv[c1 + k] + a.thv[c2 + k]));
+    a.mflx[o + k] += f32_to_f64(F) * a.inv_nsub;
   }
 }
 
@@ -1030,6 +1090,7 @@ MxEdgeArgs edge_args(StateDev& s, bool corr, double dtau, int nsub) {
   ea.Avn0 = s.Avn0_32;
   ea.phi = s.F32; ea.gth = s.G32; ea.a_e = s.ae32; ea.mflx = s.mflx;
   ea.dtau = (float)dtau; ea.inv_nsub = 1.0 / nsub; ea.corrector = corr;
+  ea.skip_flux = 0;
   return ea;
 }
 
@@ -1232,9 +1293,27 @@ void enqueue_step_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream
       const bool corr = stage == 1;
       const MxEdgeArgs ea = edge_args(s, corr, dtau, nsub);
       const MxColArgs ca = col_args(s, corr, dtau, nsub);
+      const bool damp = corr && st->divdamp4 > 0.0;
+      MxEdgeArgs ead = ea;
+      ead.skip_flux = damp ? 1 : 0;
       for (int kind : {K_MX_VERTEX, K_MX_EDGE, K_MX_CELL_KE, K_MX_EDGE_TEND}) {
         prof_begin(stream, kind);
-        launch_kind(kind, tile(kind), G, s, ea, ca, (float)dt, stream);
+        launch_kind(kind, tile(kind), G, s, ead, ca, (float)dt, stream);
+        prof_end(stream);
+      }
+      if (damp) {
+        // scratch until the next stage's diagnostics: Kc32 holds the divergence, vt32 (an
+        // edge array, larger than a cell array) its Laplacian
+        const double abar = 4.0 * M_PI * kR * kR / (double)nc;
+        MxDDArgs da;
+        da.L = s.vt32; da.rho = ea.rho; da.thv = ea.thv;
+        da.vn = s.vn32; da.phi = s.F32; da.gth = s.G32; da.mflx = s.mflx;
+        da.scale = (float)(st->divdamp4 * abar * abar); da.inv_nsub = 1.0 / nsub;
+        const unsigned nbc8 = (unsigned)((nc + 7) / 8), nbe8 = (unsigned)((G.ne + 7) / 8);
+        prof_begin(stream, K_DIVDAMP);
+        k_mx_dd_div<<<nbc8, 256, 0, stream>>>(G, s.vn32, s.Kc32);
+        k_mx_dd_lap<<<nbc8, 256, 0, stream>>>(G, s.Kc32, s.vt32);
+        k_mx_dd_edge<<<nbe8, 256, 0, stream>>>(G, da);
         prof_end(stream);
       }
       if (s.fac64) {

@@ -36,6 +36,7 @@
 // precomputed reciprocal (area factors folded into the stencil weights); the
 // column's three quotients per level (pi/Theta, the Thomas pivot, Theta/rho) use
 // the Newton-Raphson reciprocal of recip64.h.
+#include <cmath>
 #include "icon_internal.h"
 #include "recip64.h"
 
@@ -163,6 +164,7 @@ struct EdgeArgs {
   double *F, *G, *a_e, *mflx;
   double dtau, inv_nsub;
   int corrector;
+  int skip_flux;                           // fluxes formed after divergence damping instead
 };
 
 // vn tendency and update, horizontal mass/heat fluxes, edge part of w advection.
@@ -223,11 +225,69 @@ __global__ void __launch_bounds__(256, 4) k_edge_tend(Geo64 G, EdgeArgs a) {
         a.Avn0[eo + k] = A;
       }
       a.vn_out[eo + k] = vnew;
+      if (a.skip_flux) continue;
       const double F = (0.5 * (a.rho[c1 + k] + a.rho[c2 + k])) * vnew;
       a.F[eo + k] = F;
       a.G[eo + k] = F * th_e;
       if (a.corrector) a.mflx[eo + k] = fma(F, a.inv_nsub, a.mflx[eo + k]);
     }
+  }
+}
+
+// ---------------------------------------------------------------- divergence damping (option)
+// Fourth-order divergence damping of the corrector's vn^{n+1} before its fluxes are formed:
+// vn -= c4 Abar^2 grad(div(grad(div vn))), Abar the mean cell area (an ICON option; the
+// paper prints none). Cell divergence, cell Laplacian of it, then the edge update together
+// with the corrector's mass and heat fluxes and the step-mean mass flux.
+__global__ void __launch_bounds__(256, 4) k_dd_div(Geo64 G, const double* __restrict__ vn, double* __restrict__ D) {
+  const int64_t c = warp_entity();
+  if (c >= G.nc) return;
+  const int lane = threadIdx.x & 31, ld = G.ld;
+  int64_t E[3];
+  double dw[3];
+  for (int s = 0; s < 3; ++s) {
+    E[s] = (int64_t)G.c2e[3 * c + s] * ld;
+    dw[s] = G.div_wa[3 * c + s];
+  }
+  for (int k = lane; k < G.N; k += 32) D[c * ld + k] = (dw[0] * vn[E[0] + k] + dw[1] * vn[E[1] + k]) + dw[2] * vn[E[2] + k];
+}
+
+__global__ void __launch_bounds__(256, 4) k_dd_lap(Geo64 G, const double* __restrict__ D, double* __restrict__ L) {
+  const int64_t c = warp_entity();
+  if (c >= G.nc) return;
+  const int lane = threadIdx.x & 31, ld = G.ld;
+  int64_t A[3], B[3];
+  double wt[3];
+  for (int s = 0; s < 3; ++s) {
+    const int e = G.c2e[3 * c + s];
+    A[s] = (int64_t)G.e2c[2 * e] * ld;
+    B[s] = (int64_t)G.e2c[2 * e + 1] * ld;
+    wt[s] = G.div_wa[3 * c + s] * G.inv_de[e];
+  }
+  for (int k = lane; k < G.N; k += 32)
+    L[c * ld + k] = (wt[0] * (D[B[0] + k] - D[A[0] + k]) + wt[1] * (D[B[1] + k] - D[A[1] + k])) +
+                    wt[2] * (D[B[2] + k] - D[A[2] + k]);
+}
+
+struct DDArgs {
+  const double *L, *rho, *thv;             // Laplacian of the divergence, stage state S*
+  double *vn, *F, *G, *mflx;
+  double scale, inv_nsub;                  // c4 Abar^2
+};
+
+__global__ void __launch_bounds__(256, 4) k_dd_edge(Geo64 G, DDArgs a) {
+  const int64_t e = warp_entity();
+  if (e >= G.ne) return;
+  const int lane = threadIdx.x & 31, ld = G.ld;
+  const int64_t c1 = (int64_t)G.e2c[2 * e] * ld, c2 = (int64_t)G.e2c[2 * e + 1] * ld, eo = e * ld;
+  const double s = a.scale * G.inv_de[e];
+  for (int k = lane; k < G.N; k += 32) {
+    const double vn = a.vn[eo + k] - s * (a.L[c2 + k] - a.L[c1 + k]);
+    a.vn[eo + k] = vn;
+    const double F = (0.5 * (a.rho[c1 + k] + a.rho[c2 + k])) * vn;
+    a.F[eo + k] = F;
+    a.G[eo + k] = F * (0.5 * (a.thv[c1 + k] + a.thv[c2 + k]));
+    a.mflx[eo + k] = fma(F, a.inv_nsub, a.mflx[eo + k]);
   }
 }
 
@@ -591,9 +651,24 @@ void enqueue_step_fp64(icon_state* st, double dt, int nsub, cudaStream_t stream)
       ea.Avn0 = s.Avn0;
       ea.F = s.F; ea.G = s.G; ea.a_e = s.a_e; ea.mflx = s.mflx;
       ea.dtau = dtau; ea.inv_nsub = 1.0 / nsub; ea.corrector = corr;
+      const bool damp = corr && st->divdamp4 > 0.0;
+      ea.skip_flux = damp ? 1 : 0;
       prof_begin(stream, K_EDGE_TEND);
       k_edge_tend<<<nbe, 256, 0, stream>>>(G, ea);
       prof_end(stream);
+      if (damp) {
+        // Kc and the column's update-operand scratch are free until the column runs
+        const double abar = 4.0 * M_PI * kR * kR / (double)G.nc;
+        DDArgs da;
+        da.L = s.col_rx; da.rho = rho_st; da.thv = thv_st;
+        da.vn = s.vn; da.F = s.F; da.G = s.G; da.mflx = s.mflx;
+        da.scale = st->divdamp4 * abar * abar; da.inv_nsub = 1.0 / nsub;
+        prof_begin(stream, K_DIVDAMP);
+        k_dd_div<<<nbc, 256, 0, stream>>>(G, s.vn, s.Kc);
+        k_dd_lap<<<nbc, 256, 0, stream>>>(G, s.Kc, s.col_rx);
+        k_dd_edge<<<nbe, 256, 0, stream>>>(G, da);
+        prof_end(stream);
+      }
       ColArgs ca;
       ca.rho = s.rho; ca.thv = s.thv; ca.ex = s.ex; ca.w = s.w;
       ca.w_stage = w_st;
