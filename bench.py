@@ -446,6 +446,32 @@ def run_gpu(args, wl, rank, world, local_rank):
                                    "frac": ops / (t_ms * 1e-3) / FP64_INSTR_PEAK, "traffic": None}}
         except C.IconError as exc:
             tracer = {"skipped": str(exc)}
+    # the divergence-damping option (c4 = 0.004) on the same state: step time with it, and
+    # its kernels' time per step from the profiled eager steps
+    divdamp = None
+    if not args.no_tracer:
+        try:
+            C.icon_state_set_option(st, C.ICON_OPT_DIVDAMP4, 0.004)
+            for _ in range(args.warmup):
+                C.icon_dycore_step(st, wl.dt, wl.nsub)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                C.icon_dycore_step_async(st, wl.dt, wl.nsub)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            C.icon_state_status(st)
+            ms_d = e0.elapsed_time(e1) / args.steps
+            kms, kn = None, None
+            for _ in range(2):
+                kms, kn = C.icon_dycore_step_profile(st, wl.dt, wl.nsub, kms, kn)
+            names = [C.icon_kernel_kind_name(k) for k in range(C.ICON_KIND_COUNT)]
+            divdamp = {"c4": 0.004, "ms_per_step_with_it": ms_d,
+                       "kernels_ms_per_step": kms[names.index("divergence_damping")] / 2,
+                       "note": "on the state of the tracer measurement (one tracer transported)"}
+        except C.IconError as exc:
+            divdamp = {"skipped": str(exc)}
 
     C.icon_state_free(st)
     C.icon_grid_free(grid)
@@ -466,7 +492,7 @@ def run_gpu(args, wl, rank, world, local_rank):
             "gpu_launches": kernels_per_step * args.steps, "roofline": roof,
             "hbm_roofline": step_hbm_roofline(value, wl.precision, hbm_peak), "kernels": breakdown,
             "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "mass_rel_drift": m_drift, "mixed": other,
-            "rel_l2_vs_fp64_after_1_step": err_vs_fp64, "tracer": tracer,
+            "rel_l2_vs_fp64_after_1_step": err_vs_fp64, "tracer": tracer, "divergence_damping": divdamp,
             "simulated_days_per_day": wl.dt / (ms / args.steps * 1e-3),
             "device_memory_gb": {"peak_allocated": round(torch.cuda.max_memory_allocated() / 1e9, 2),
                                  "total": round(torch.cuda.get_device_properties(0).total_memory / 1e9, 2)}}
@@ -592,7 +618,8 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="r2b6-fp64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision variant of an FP64 workload")
-    ap.add_argument("--no-tracer", action="store_true", help="skip the tracer-transport measurement")
+    ap.add_argument("--no-tracer", action="store_true",
+                    help="skip the tracer-transport and divergence-damping measurements")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     world = int(os.environ.get("WORLD_SIZE", "1"))
