@@ -28,9 +28,11 @@
 //
 // Mapping: one warp per entity (edge, cell or vertex) with lanes over levels, so
 // every neighbour index is loaded once per entity and every gathered neighbour
-// row is a coalesced, aligned segment; one thread per column for the implicit
-// solve. The summation order of every stencil follows the operator definitions
-// (fixed neighbour order), so results do not depend on the launch shape.
+// row is a coalesced, aligned segment; the implicit column solve runs its
+// level-parallel parts the same way and only its Thomas recurrence one thread per
+// column (see "column solve" below). The summation order of every stencil follows
+// the operator definitions (fixed neighbour order), so results do not depend on the
+// launch shape.
 // FP64 division issues about eight FP64-pipe instructions on this GPU, so every
 // division by a geometric or per-level constant is a multiplication by a
 // precomputed reciprocal (area factors folded into the stencil weights); the
