@@ -14,6 +14,7 @@ import pytest
 
 from tests.conftest import golden_path, rel_l2
 from tests.tolerances import thermo_bound_mixed, w_bound, w_bound_mixed
+from paper_2511_02021_gb300 import workloads as WL
 
 pytestmark = pytest.mark.gpu
 
@@ -132,3 +133,44 @@ def test_r2b8_l90_mixed_vs_fp64(gpu):
             if s is not None:
                 C.icon_state_free(s)
         C.icon_grid_free(grid)
+
+
+def test_ensemble_64_members_spot_check(gpu):
+    """The benchmark's ensemble (32 members on R2B4 with dt 360 s, 32 on R2B5 with dt 180 s,
+    60 levels, member perturbations from seed 3), one step in one persistent launch:
+    member 0 (R2B4) against the oracle within the mixed bounds, member 40 (R2B5) against
+    its own solo step."""
+    import oracle as O
+    C = gpu
+    E = WL.ENSEMBLE
+    N, nsub = E["nlev"], E["nsub"]
+    grids = {4: C.icon_grid_build(2, 4, N), 5: C.icon_grid_build(2, 5, N)}
+    spec = [(4, E["dt_b4"])] * E["members_b4"] + [(5, E["dt_b5"])] * E["members_b5"]
+    sts = [C.icon_state_init_ex(grids[b], E["seed"], C.ICON_CASE_MEMBER, precision=1, member=m)
+           for m, (b, _) in enumerate(spec)]
+    solo = C.icon_state_init_ex(grids[5], E["seed"], C.ICON_CASE_MEMBER, precision=1, member=40)
+    ens = C.icon_ensemble_create(sts)
+    try:
+        C.icon_ensemble_step(ens, [dt for _, dt in spec], nsub, 1)
+        got0 = {f: C.icon_state_copy_field(sts[0], grids[4], N, f) for f in ("vn", "rho", "theta_v", "exner", "w")}
+        C.icon_dycore_step(solo, E["dt_b5"], nsub)
+        for f in ("vn", "rho", "theta_v", "exner"):
+            a = C.icon_state_copy_field(sts[40], grids[5], N, f)
+            b = C.icon_state_copy_field(solo, grids[5], N, f)
+            assert rel_l2(a, b) <= 1e-6, f
+    finally:
+        C.icon_ensemble_free(ens)
+        for st in sts + [solo]:
+            C.icon_state_free(st)
+        for gr in grids.values():
+            C.icon_grid_free(gr)
+    g = O.build_grid(2, 4)
+    v = O.vertical_grid(N)
+    s0 = O.init_state(g, v, E["seed"], O.CASE_MEMBER, member=0)
+    s1, _ = O.dycore_step(g, v, s0, E["dt_b4"], nsub)
+    assert rel_l2(got0["vn"], s1["vn"]) <= 1e-5
+    with open(golden_path("grid_dual_edge_min.json")) as fh:
+        d_min = json.load(fh)["d_e_min_m"]["4"]
+    for f in ("rho", "theta_v", "exner"):
+        assert rel_l2(got0[f], s1[f]) <= thermo_bound_mixed(E["dt_b4"], nsub, 1, d_min), f
+    assert np.sqrt(np.mean((got0["w"] - s1["w"]) ** 2)) <= w_bound_mixed(E["dt_b4"], nsub, 1)
