@@ -217,12 +217,19 @@ def smagorinsky_coefficient(g, vn):
     return (CS_SMAG * CS_SMAG) * (g.l_e * g.d_e)[:, None] * np.sqrt(DT * DT + DS * DS)
 
 
-def diffusion(g, v, s, dt):
+def diffusion(g, v, s, dt, diff4=0.0):
     """Smagorinsky diffusion of vn and flux-form diffusion of theta_v (rho untouched,
-    Exner adjusted at constant density)."""
+    Exner adjusted at constant density). With diff4 > 0, fourth-order background
+    diffusion of vn as well (BD, an option; ICON's background diffusion of order 4, the
+    paper prints none): - diff4 Abar^2 L(L(vn)) with the O6 vector Laplacian L and the
+    mean cell area Abar, applied once per step."""
     vn = s["vn"]
     Kh = smagorinsky_coefficient(g, vn)
-    vn_new = vn + dt * Kh * vector_laplacian(g, vn)
+    L1 = vector_laplacian(g, vn)
+    vn_new = vn + dt * Kh * L1
+    if diff4 > 0.0:
+        abar = 4.0 * np.pi * R_EARTH * R_EARTH / g.nc
+        vn_new = vn_new - (diff4 * abar * abar) * vector_laplacian(g, L1)
     thv = s["theta_v"]
     flux = (g.l_e[:, None] * Kh) * (thv[g.e2c[:, 1]] - thv[g.e2c[:, 0]]) / g.d_e[:, None]
     acc = np.zeros_like(thv)
@@ -268,14 +275,14 @@ def substep(g, v, s, dtau, nsub, acc, divdamp4=0.0):
     return dict(cn, vn=vn_new)
 
 
-def dycore_step(g, v, s, dt, nsub, divdamp4=0.0):
+def dycore_step(g, v, s, dt, nsub, divdamp4=0.0, diff4=0.0):
     """One step: nsub substeps of dt/nsub, then diffusion with dt. Returns
     (new state, accumulators {mflx (Ne,N), wflx (Nc,N+1)})."""
     dtau = dt / nsub
     acc = {"mflx": np.zeros((g.ne, v.N)), "wflx": np.zeros((g.nc, v.N + 1))}
     for _ in range(nsub):
         s = substep(g, v, s, dtau, nsub, acc, divdamp4)
-    s, _ = diffusion(g, v, s, dt)
+    s, _ = diffusion(g, v, s, dt, diff4)
     return s, acc
 
 
