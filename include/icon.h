@@ -256,7 +256,7 @@ int icon_selftest(long long n, unsigned* failures);
 /* Name of kernel kind i (0 <= i < ICON_KIND_COUNT), or NULL. Mixed-precision
  * stencil kinds: 10 vertex, 11 edge diagnostics, 12 cell kinetic energy,
  * 13 edge tendency, 15 column-input gather, 16 diffusion vertex/divergence;
- * 20 tracer transport, 21 divergence damping (option). */
+ * 20 tracer transport, 21 divergence damping, 22 background diffusion (options). */
 const char* icon_kernel_kind_name(int kind);
 #define ICON_KIND_COUNT 24
 
@@ -274,7 +274,12 @@ enum {
    * step's own divergence and gradient operators (an ICON option; the paper prints none).
    * value = c4 in [0, 0.05]; 0 (the default) turns it off. Both precisions; not in the
    * persistent ensemble (icon_ensemble_create rejects members that set it). */
-  ICON_OPT_DIVDAMP4 = 1
+  ICON_OPT_DIVDAMP4 = 1,
+  /* Fourth-order background diffusion of vn in the diffusion step, once per step:
+   * vn -= c Abar^2 L(L(vn)) with the step's vector Laplacian L (an ICON option; the paper
+   * prints none). value = c in [0, 0.01]; 0 (the default) turns it off. Both precisions;
+   * not in the persistent ensemble. */
+  ICON_OPT_DIFF4 = 2
 };
 
 /* Set an option of a state; the next step records a new graph. ICON_EINVAL for an

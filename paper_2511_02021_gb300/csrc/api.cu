@@ -60,7 +60,7 @@ static const char* kKindNames[K_KIND_COUNT] = {
     "vertex_curl_wmean", "edge_vt_ke", "cell_ke", "edge_tendency_flux", "column_solve",
     "diff_vertex", "diff_div", "diff_edge", "diff_theta", "global_mass",
     "mx_vertex", "mx_edge_diag", "mx_cell_ke", "mx_edge_tendency_flux", "mx_column_solve", "mx_column_prep",
-    "mx_diff_vertex", "mx_diff_edge", "mx_diff_theta", "ensemble_persistent", "tracer_transport", "divergence_damping"};
+    "mx_diff_vertex", "mx_diff_edge", "mx_diff_theta", "ensemble_persistent", "tracer_transport", "divergence_damping", "background_diffusion"};
 
 Allocator current_allocator() {
   std::lock_guard<std::mutex> lk(g_alloc_mu);
@@ -778,12 +778,22 @@ int icon_state_add_tracers(icon_state* st, int ntracers) {
 
 int icon_state_set_option(icon_state* st, int option, double value) {
   if (!st) { set_error("icon_state_set_option: state is NULL"); return ICON_EINVAL; }
-  if (option != ICON_OPT_DIVDAMP4) { set_error("icon_state_set_option: unknown option %d", option); return ICON_EINVAL; }
-  if (!(value >= 0.0 && value <= 0.05)) {
-    set_error("icon_state_set_option: divergence damping coefficient %g outside [0, 0.05]", value);
+  if (option == ICON_OPT_DIVDAMP4) {
+    if (!(value >= 0.0 && value <= 0.05)) {
+      set_error("icon_state_set_option: divergence damping coefficient %g outside [0, 0.05]", value);
+      return ICON_EINVAL;
+    }
+    st->divdamp4 = value;
+  } else if (option == ICON_OPT_DIFF4) {
+    if (!(value >= 0.0 && value <= 0.01)) {
+      set_error("icon_state_set_option: background diffusion coefficient %g outside [0, 0.01]", value);
+      return ICON_EINVAL;
+    }
+    st->diff4 = value;
+  } else {
+    set_error("icon_state_set_option: unknown option %d", option);
     return ICON_EINVAL;
   }
-  st->divdamp4 = value;
   if (st->graph) {                      // the step's graph changes with the option
     cudaGraphExecDestroy(st->graph);
     st->graph = nullptr;
@@ -834,8 +844,9 @@ int icon_ensemble_create(icon_state* const* members, int n, icon_ensemble** out)
       set_error("icon_ensemble_create: members must be mixed-precision states");
       return ICON_EINVAL;
     }
-    if (members[i]->divdamp4 != 0.0) {
-      set_error("icon_ensemble_create: the persistent ensemble has no divergence damping (member %d sets it)", i);
+    if (members[i]->divdamp4 != 0.0 || members[i]->diff4 != 0.0) {
+      set_error("icon_ensemble_create: the persistent ensemble has no divergence damping or fourth-order "
+                "background diffusion (member %d sets one)", i);
       return ICON_EINVAL;
     }
     if (members[i]->s.ntr != 0) {

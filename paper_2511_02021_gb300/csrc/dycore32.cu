@@ -317,7 +317,8 @@ __device__ inline void mx_diff_edge_item(const MxGeo& G, float* __restrict__ vn,
                                          const float* __restrict__ uy, const float* __restrict__ uz,
                                          const float* __restrict__ zeta, const float* __restrict__ divc,
                                          const float* __restrict__ thv, float* __restrict__ thflx, float dt, int64_t e,
-                                         int lane) {
+                                         int lane, const float* __restrict__ D1 = nullptr,
+                                         const float* __restrict__ zeta1 = nullptr, float bd_scale = 0.0f) {
   const int ld = G.ld;
   int64_t Q[4];
   for (int j = 0; j < 4; ++j) Q[j] = (int64_t)G.e2q[4 * e + j] * ld;
@@ -334,8 +335,49 @@ __device__ inline void mx_diff_edge_item(const MxGeo& G, float* __restrict__ vn,
     const float DS = (ax * tx + ay * ty + az * tz) * i34 + (bx * nx + by * ny + bz * nz) * ile;
     const float Kh = cs2ld * sqrtf(DT * DT + DS * DS);
     const float lap = (divc[c2 + k] - divc[c1 + k]) * ide - (zeta[v2 + k] - zeta[v1 + k]) * ile;
-    vn[e * ld + k] += dt * Kh * lap;
+    float vnew = vn[e * ld + k] + dt * Kh * lap;
+    if (D1) {                              // fourth-order background diffusion (option)
+      const float lap2 = (D1[c2 + k] - D1[c1 + k]) * ide - (zeta1[v2 + k] - zeta1[v1 + k]) * ile;
+      vnew -= bd_scale * lap2;
+    }
+    vn[e * ld + k] = vnew;
     thflx[e * ld + k] = le * Kh * (thv[c2 + k] - thv[c1 + k]) * ide;
+  }
+}
+
+// fourth-order background diffusion (option), FP32: L1 = L(vn) at edges, then the curl
+// (vertices) and divergence (cells) of L1 for the second Laplacian in the edge item
+__global__ void __launch_bounds__(256) k_mx_bd_lap(MxGeo G, const float* __restrict__ zeta,
+                                                   const float* __restrict__ divc, float* __restrict__ L1) {
+  const int64_t e = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (e >= G.ne) return;
+  const int lane = threadIdx.x & 31, ld = G.ld;
+  const int64_t c1 = (int64_t)G.e2c[2 * e] * ld, c2 = (int64_t)G.e2c[2 * e + 1] * ld;
+  const int64_t v1 = (int64_t)G.e2v[2 * e] * ld, v2 = (int64_t)G.e2v[2 * e + 1] * ld;
+  const float ide = G.inv_de32[e], ile = G.inv_le32[e];
+  for (int k = lane; k < G.N; k += 32)
+    L1[e * ld + k] = (divc[c2 + k] - divc[c1 + k]) * ide - (zeta[v2 + k] - zeta[v1 + k]) * ile;
+}
+
+__global__ void __launch_bounds__(256) k_mx_bd_curldiv(MxGeo G, const float* __restrict__ L1, float* __restrict__ zeta1,
+                                                       float* __restrict__ D1) {
+  const int64_t item = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31, ld = G.ld;
+  if (item < G.nv) {
+    const int64_t v = item;
+    int64_t E[6];
+    float rw[6];
+    for (int j = 0; j < 6; ++j) {
+      E[j] = (int64_t)G.v2e[6 * v + j] * ld;
+      rw[j] = G.rot_w32[6 * v + j];
+    }
+    for (int k = lane; k < G.N; k += 32) {
+      float r = 0.0f;
+      for (int j = 0; j < 6; ++j) r += rw[j] * L1[E[j] + k];
+      zeta1[v * ld + k] = r;
+    }
+  } else if (item < G.nv + G.nc) {
+    mx_diff_div_item<32>(G, L1, D1, item - G.nv, lane);
   }
 }
 
@@ -911,6 +953,16 @@ __device__ inline void mx_gather_tile_body(const MxGeo& G, const MxColArgs& a, i
   }
 }
 
+// the diffusion edge step with fourth-order background diffusion (option): 32 lanes per edge
+__global__ void __launch_bounds__(256) k_mx_diff_edge_bd(MxGeo G, float* vn, const float* ux, const float* uy,
+                                                         const float* uz, const float* zeta, const float* divc,
+                                                         const float* thv, float* thflx, float dt, const float* D1,
+                                                         const float* zeta1, float bd_scale) {
+  const int64_t e = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (e >= G.ne) return;
+  mx_diff_edge_item<32>(G, vn, ux, uy, uz, zeta, divc, thv, thflx, dt, e, threadIdx.x & 31, D1, zeta1, bd_scale);
+}
+
 template <int LPE, bool CORR>
 __global__ void __launch_bounds__(512, 3) k_mx_gather_tile(MxGeo G, MxColArgs a) {
   __shared__ GatherTile<LPE> T;
@@ -1342,9 +1394,23 @@ void enqueue_step_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream
   prof_begin(stream, K_MX_DIFF_VERTEX);
   launch_kind(K_MX_DIFF_VERTEX, tile(K_MX_DIFF_VERTEX), G, s, ea, ca, (float)dt, stream);
   prof_end(stream);
-  prof_begin(stream, K_MX_DIFF_EDGE);
-  launch_kind(K_MX_DIFF_EDGE, tile(K_MX_DIFF_EDGE), G, s, ea, ca, (float)dt, stream);
-  prof_end(stream);
+  if (st->diff4 > 0.0) {
+    // dead after the substeps: ae32 (edges) holds L(vn), w32_s its curl, exp32_s its divergence
+    const double abar = 4.0 * M_PI * kR * kR / (double)nc;
+    prof_begin(stream, K_DIFF4);
+    k_mx_bd_lap<<<(unsigned)((G.ne + 7) / 8), 256, 0, stream>>>(G, s.zeta32, s.Kc32, s.ae32);
+    k_mx_bd_curldiv<<<(unsigned)((G.nv + nc + 7) / 8), 256, 0, stream>>>(G, s.ae32, s.w32_s, s.exp32_s);
+    prof_end(stream);
+    prof_begin(stream, K_MX_DIFF_EDGE);
+    const unsigned nbe8 = (unsigned)((G.ne + 7) / 8);
+    k_mx_diff_edge_bd<<<nbe8, 256, 0, stream>>>(G, s.vn32, s.uvx32, s.uvy32, s.uvz32, s.zeta32, s.Kc32, s.thv32,
+                                                s.vt32, (float)dt, s.exp32_s, s.w32_s, (float)(st->diff4 * abar * abar));
+    prof_end(stream);
+  } else {
+    prof_begin(stream, K_MX_DIFF_EDGE);
+    launch_kind(K_MX_DIFF_EDGE, tile(K_MX_DIFF_EDGE), G, s, ea, ca, (float)dt, stream);
+    prof_end(stream);
+  }
   prof_begin(stream, K_MX_DIFF_THETA);
   k_mx_diff_theta<<<blocks_for(nc, 128), 128, 0, stream>>>(G, s.vt32, s.thv, s.ex, s.thv32, s.exp32, (float)dt);
   prof_end(stream);

@@ -539,11 +539,47 @@ __device__ inline double dot3(double ax, double ay, double az, const double* b) 
   return (ax * b[0] + ay * b[1]) + az * b[2];
 }
 
+// fourth-order background diffusion (option): L1 = L(vn) at edges, then the divergence
+// and curl of L1 for the second Laplacian in k_diff_edge
+__global__ void __launch_bounds__(256, 4) k_bd_lap(Geo64 G, const double* __restrict__ zeta,
+                                                const double* __restrict__ divc, double* __restrict__ L1) {
+  const int64_t e = warp_entity();
+  if (e >= G.ne) return;
+  const int lane = threadIdx.x & 31, ld = G.ld;
+  const int64_t c1 = (int64_t)G.e2c[2 * e] * ld, c2 = (int64_t)G.e2c[2 * e + 1] * ld;
+  const int64_t v1 = (int64_t)G.e2v[2 * e] * ld, v2 = (int64_t)G.e2v[2 * e + 1] * ld;
+  const double ile = G.inv_le[e], ide = G.inv_de[e];
+  for (int k = lane; k < G.N; k += 32)
+    L1[e * ld + k] = (divc[c2 + k] - divc[c1 + k]) * ide - (zeta[v2 + k] - zeta[v1 + k]) * ile;
+}
+
+__global__ void __launch_bounds__(256, 4) k_bd_curl(Geo64 G, const double* __restrict__ L1, double* __restrict__ zeta1) {
+  const int64_t v = warp_entity();
+  if (v >= G.nv) return;
+  const int lane = threadIdx.x & 31, ld = G.ld;
+  int64_t E[6];
+  double rw[6];
+  for (int j = 0; j < 6; ++j) {
+    E[j] = (int64_t)G.v2e[6 * v + j] * ld;
+    rw[j] = G.rot_wa[6 * v + j];
+  }
+  for (int k = lane; k < G.N; k += 32) {
+    double r = 0.0;
+    for (int j = 0; j < 6; ++j) r += rw[j] * L1[E[j] + k];
+    zeta1[v * ld + k] = r;
+  }
+}
+
+struct BDArgs {
+  const double *D1, *zeta1;                // divergence and curl of L(vn); NULL: no background diffusion
+  double scale;                            // c Abar^2
+};
+
 __global__ void __launch_bounds__(256, 4) k_diff_edge(Geo64 G, double* __restrict__ vn, const double* __restrict__ ux,
                                                    const double* __restrict__ uy, const double* __restrict__ uz,
                                                    const double* __restrict__ zeta, const double* __restrict__ divc,
                                                    const double* __restrict__ thv, double* __restrict__ Kh_out,
-                                                   double* __restrict__ thflx, double dt) {
+                                                   double* __restrict__ thflx, double dt, BDArgs bd) {
   const int64_t e = warp_entity();
   if (e >= G.ne) return;
   const int lane = threadIdx.x & 31, ld = G.ld;
@@ -564,7 +600,12 @@ __global__ void __launch_bounds__(256, 4) k_diff_edge(Geo64 G, double* __restric
     const double DS = dot3(d34x, d34y, d34z, t) * i34 + dot3(d12x, d12y, d12z, n) * ile;
     const double Kh = cs2ld * sqrt(DT * DT + DS * DS);
     const double lap = (divc[c2 + k] - divc[c1 + k]) * ide - (zeta[v2 + k] - zeta[v1 + k]) * ile;
-    vn[e * ld + k] = vn[e * ld + k] + dt * Kh * lap;
+    double vnew = vn[e * ld + k] + dt * Kh * lap;
+    if (bd.D1) {
+      const double lap2 = (bd.D1[c2 + k] - bd.D1[c1 + k]) * ide - (bd.zeta1[v2 + k] - bd.zeta1[v1 + k]) * ile;
+      vnew -= bd.scale * lap2;
+    }
+    vn[e * ld + k] = vnew;
     Kh_out[e * ld + k] = Kh;
     thflx[e * ld + k] = (le * Kh) * (thv[c2 + k] - thv[c1 + k]) * ide;
   }
@@ -697,8 +738,20 @@ void enqueue_step_fp64(icon_state* st, double dt, int nsub, cudaStream_t stream)
   prof_begin(stream, K_DIFF_DIV);
   k_diff_div<<<nbc, 256, 0, stream>>>(G, s.vn, s.divc);
   prof_end(stream);
+  BDArgs bd;
+  bd.D1 = nullptr; bd.zeta1 = nullptr; bd.scale = 0.0;
+  if (st->diff4 > 0.0) {
+    // scratch that is dead during diffusion: a_e (edges), two column-scratch cell arrays
+    const double abar = 4.0 * M_PI * kR * kR / (double)G.nc;
+    prof_begin(stream, K_DIFF4);
+    k_bd_lap<<<nbe, 256, 0, stream>>>(G, s.zeta, s.divc, s.a_e);
+    k_bd_curl<<<nbv, 256, 0, stream>>>(G, s.a_e, s.col_di);
+    k_diff_div<<<nbc, 256, 0, stream>>>(G, s.a_e, s.col_lo);
+    prof_end(stream);
+    bd.D1 = s.col_lo; bd.zeta1 = s.col_di; bd.scale = st->diff4 * abar * abar;
+  }
   prof_begin(stream, K_DIFF_EDGE);
-  k_diff_edge<<<nbe, 256, 0, stream>>>(G, s.vn, s.uvx, s.uvy, s.uvz, s.zeta, s.divc, s.thv, s.Kh, s.thflx, dt);
+  k_diff_edge<<<nbe, 256, 0, stream>>>(G, s.vn, s.uvx, s.uvy, s.uvz, s.zeta, s.divc, s.thv, s.Kh, s.thflx, dt, bd);
   prof_end(stream);
   prof_begin(stream, K_DIFF_THETA);
   k_diff_theta<<<nbc, 256, 0, stream>>>(G, s.thflx, s.thv, s.ex, dt);

@@ -35,7 +35,7 @@ enum KernelKind {
   K_VERTEX = 0, K_EDGE_VT, K_CELL_KE, K_EDGE_TEND, K_COLUMN,
   K_DIFF_VERTEX, K_DIFF_DIV, K_DIFF_EDGE, K_DIFF_THETA, K_MASS,
   K_MX_VERTEX, K_MX_EDGE, K_MX_CELL_KE, K_MX_EDGE_TEND, K_MX_COLUMN, K_MX_COLUMN_PREP,
-  K_MX_DIFF_VERTEX, K_MX_DIFF_EDGE, K_MX_DIFF_THETA, K_ENSEMBLE, K_TRACER, K_DIVDAMP, K_KIND_COUNT
+  K_MX_DIFF_VERTEX, K_MX_DIFF_EDGE, K_MX_DIFF_THETA, K_ENSEMBLE, K_TRACER, K_DIVDAMP, K_DIFF4, K_KIND_COUNT
 };
 static_assert(K_KIND_COUNT <= ICON_KIND_COUNT, "kind table");
 // When a profile is active on this thread, every launch is bracketed by events.
@@ -193,6 +193,7 @@ struct icon_state {
   bool tuned = false;
   // options (icon_state_set_option)
   double divdamp4 = 0.0;        // fourth-order divergence damping coefficient (0: off)
+  double diff4 = 0.0;           // fourth-order background diffusion coefficient (0: off)
 };
 
 namespace icon {
