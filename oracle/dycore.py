@@ -99,6 +99,12 @@ def edge_mean(g, f):
     return 0.5 * (f[g.e2c[:, 0]] + f[g.e2c[:, 1]])
 
 
+def edge_upwind(g, f, vn):
+    """UT (an option): the value of the cell the edge-normal flow comes from, f_c1 where
+    vn >= 0 (flow from c1 to c2) else f_c2; used for theta_v in the heat flux."""
+    return np.where(vn >= 0.0, f[g.e2c[:, 0]], f[g.e2c[:, 1]])
+
+
 # ------------------------------------------------------------------ tendencies
 def tendencies(g, v, s):
     """Explicit tendencies at state s: A_vn (Ne, N) at full levels and A_w (Nc, N+1),
@@ -255,33 +261,35 @@ def divergence_damping(g, vn, c4):
 
 
 # ------------------------------------------------------------------ step and mass
-def substep(g, v, s, dtau, nsub, acc, divdamp4=0.0):
+def substep(g, v, s, dtau, nsub, acc, divdamp4=0.0, upwind_theta=False):
     """One predictor-corrector substep; updates the accumulators in `acc`. With
     divdamp4 > 0 the corrector's vn^{n+1} is divergence-damped (DD) before its mass and
-    heat fluxes are formed."""
+    heat fluxes are formed; with upwind_theta the heat fluxes carry the upwind theta_v (UT)
+    instead of the centred one (the pressure gradient keeps the centred value)."""
+    theta_e = (lambda st, vn: edge_upwind(g, st["theta_v"], vn)) if upwind_theta else \
+        (lambda st, vn: edge_mean(g, st["theta_v"]))
     A_vn0, A_w0 = tendencies(g, v, s)
     vn_star = s["vn"] + dtau * (A_vn0 - pressure_gradient(g, s))
-    cs, _ = column(g, v, s, vn_star, A_w0, edge_mean(g, s["rho"]), edge_mean(g, s["theta_v"]), dtau)
+    cs, _ = column(g, v, s, vn_star, A_w0, edge_mean(g, s["rho"]), theta_e(s, vn_star), dtau)
     s_star = dict(cs, vn=vn_star)
     A_vn1, A_w1 = tendencies(g, v, s_star)
     vn_new = s["vn"] + dtau * (0.5 * (A_vn0 + A_vn1) - pressure_gradient(g, s_star))
     if divdamp4 > 0.0:
         vn_new = divergence_damping(g, vn_new, divdamp4)
     rho_e1 = edge_mean(g, s_star["rho"])
-    cn, rho_ic0 = column(g, v, s, vn_new, 0.5 * (A_w0 + A_w1), rho_e1,
-                         edge_mean(g, s_star["theta_v"]), dtau)
+    cn, rho_ic0 = column(g, v, s, vn_new, 0.5 * (A_w0 + A_w1), rho_e1, theta_e(s_star, vn_new), dtau)
     acc["mflx"] += rho_e1 * vn_new / nsub
     acc["wflx"] += rho_ic0 * (BETA * cn["w"] + (1.0 - BETA) * s["w"]) / nsub
     return dict(cn, vn=vn_new)
 
 
-def dycore_step(g, v, s, dt, nsub, divdamp4=0.0, diff4=0.0):
+def dycore_step(g, v, s, dt, nsub, divdamp4=0.0, diff4=0.0, upwind_theta=False):
     """One step: nsub substeps of dt/nsub, then diffusion with dt. Returns
     (new state, accumulators {mflx (Ne,N), wflx (Nc,N+1)})."""
     dtau = dt / nsub
     acc = {"mflx": np.zeros((g.ne, v.N)), "wflx": np.zeros((g.nc, v.N + 1))}
     for _ in range(nsub):
-        s = substep(g, v, s, dtau, nsub, acc, divdamp4)
+        s = substep(g, v, s, dtau, nsub, acc, divdamp4, upwind_theta)
     s, _ = diffusion(g, v, s, dt, diff4)
     return s, acc
 
