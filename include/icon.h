@@ -279,7 +279,12 @@ enum {
    * vn -= c Abar^2 L(L(vn)) with the step's vector Laplacian L (an ICON option; the paper
    * prints none). value = c in [0, 0.01]; 0 (the default) turns it off. Both precisions;
    * not in the persistent ensemble. */
-  ICON_OPT_DIFF4 = 2
+  ICON_OPT_DIFF4 = 2,
+  /* Upwind theta_v in the heat fluxes (value 1; 0, the default, is the centred mean):
+   * the flux through an edge carries theta_v of the cell the flow comes from, in both
+   * stages; the pressure gradient keeps the centred value (an ICON option, first order
+   * here; the paper prints none). Both precisions; not in the persistent ensemble. */
+  ICON_OPT_UPWIND_THETA = 3
 };
 
 /* Set an option of a state; the next step records a new graph. ICON_EINVAL for an

@@ -334,7 +334,7 @@ def icon_state_copy_tracer(state, grid, nlev, t):
 
 
 # ---------------------------------------------------------------- options
-ICON_OPT_DIVDAMP4, ICON_OPT_DIFF4 = 1, 2
+ICON_OPT_DIVDAMP4, ICON_OPT_DIFF4, ICON_OPT_UPWIND_THETA = 1, 2, 3
 
 
 def icon_state_set_option(state, option, value):

@@ -790,6 +790,12 @@ int icon_state_set_option(icon_state* st, int option, double value) {
       return ICON_EINVAL;
     }
     st->diff4 = value;
+  } else if (option == ICON_OPT_UPWIND_THETA) {
+    if (value != 0.0 && value != 1.0) {
+      set_error("icon_state_set_option: upwind theta takes 0 or 1, got %g", value);
+      return ICON_EINVAL;
+    }
+    st->upwind_theta = value == 1.0;
   } else {
     set_error("icon_state_set_option: unknown option %d", option);
     return ICON_EINVAL;
@@ -844,9 +850,9 @@ int icon_ensemble_create(icon_state* const* members, int n, icon_ensemble** out)
       set_error("icon_ensemble_create: members must be mixed-precision states");
       return ICON_EINVAL;
     }
-    if (members[i]->divdamp4 != 0.0 || members[i]->diff4 != 0.0) {
-      set_error("icon_ensemble_create: the persistent ensemble has no divergence damping or fourth-order "
-                "background diffusion (member %d sets one)", i);
+    if (members[i]->divdamp4 != 0.0 || members[i]->diff4 != 0.0 || members[i]->upwind_theta) {
+      set_error("icon_ensemble_create: the persistent ensemble has none of the step options (member %d sets one)",
+                i);
       return ICON_EINVAL;
     }
     if (members[i]->s.ntr != 0) {

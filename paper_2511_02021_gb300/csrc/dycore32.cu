@@ -140,6 +140,7 @@ struct MxEdgeArgs {
   double inv_nsub;
   int corrector;
   int skip_flux;                           // fluxes formed after divergence damping instead
+  int upwind_theta;                        // heat flux with the upwind theta_v (option)
 };
 
 // vn tendency and update, horizontal flux integrals, edge part of the w advection.
@@ -193,7 +194,8 @@ __device__ inline void mx_edge_tend_item(const MxGeo& G, const MxEdgeArgs& a, in
     const float wbar = 0.25f * (sw + sw_up);
     const float zeta_e = 0.5f * (zeta[v1 + k] + zeta[v2 + k]);
     const float A = -(Kc[c2 + k] - Kc[c1 + k]) * ide + (zeta_e + fe) * vt[k] - wbar * (vie - vie_up) * G.inv_dz32[k];
-    const float th_e = 0.5f * (thv[c1 + k] + thv[c2 + k]);
+    const float t1 = thv[c1 + k], t2 = thv[c2 + k];
+    const float th_e = 0.5f * (t1 + t2);
     const float pg = th_e * ((exq[c2 + k] - exq[c1 + k]) * cide);
     float vnew;
     if (a.corrector) {
@@ -206,7 +208,7 @@ __device__ inline void mx_edge_tend_item(const MxGeo& G, const MxEdgeArgs& a, in
     if (a.skip_flux) continue;
     const float F = 0.5f * (rho[c1 + k] + rho[c2 + k]) * vnew;
     a.phi[o + k] = F;
-    a.gth[o + k] = (le * F) * th_e;
+    a.gth[o + k] = (le * F) * (a.upwind_theta ? (vnew >= 0.0f ? t1 : t2) : th_e);
     if (a.corrector) a.mflx[o + k] += f32_to_f64(F) * a.inv_nsub;
   }
 }
@@ -250,6 +252,7 @@ struct MxDDArgs {
   double* mflx;
   float scale;                             // c4 Abar^2
   double inv_nsub;
+  int upwind_theta;
 };
 
 __global__ void __launch_bounds__(256) k_mx_dd_edge(MxGeo G, MxDDArgs a) {
@@ -263,7 +266,8 @@ __global__ void __launch_bounds__(256) k_mx_dd_edge(MxGeo G, MxDDArgs a) {
     a.vn[o + k] = vn;
     const float F = 0.5f * (a.rho[c1 + k] + a.rho[c2 + k]) * vn;
     a.phi[o + k] = F;
-    a.gth[o + k] = (le * F) * (0.5f * (a.thv[c1 + k] + a.thv[c2 + k]));
+    const float t1 = a.thv[c1 + k], t2 = a.thv[c2 + k];
+    a.gth[o + k] = (le * F) * (a.upwind_theta ? (vn >= 0.0f ? t1 : t2) : 0.5f * (t1 + t2));
     a.mflx[o + k] += f32_to_f64(F) * a.inv_nsub;
   }
 }
@@ -1145,6 +1149,7 @@ MxEdgeArgs edge_args(StateDev& s, bool corr, double dtau, int nsub) {
   ea.phi = s.F32; ea.gth = s.G32; ea.a_e = s.ae32; ea.mflx = s.mflx;
   ea.dtau = (float)dtau; ea.inv_nsub = 1.0 / nsub; ea.corrector = corr;
   ea.skip_flux = 0;
+  ea.upwind_theta = 0;
   return ea;
 }
 
@@ -1350,6 +1355,7 @@ void enqueue_step_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream
       const bool damp = corr && st->divdamp4 > 0.0;
       MxEdgeArgs ead = ea;
       ead.skip_flux = damp ? 1 : 0;
+      ead.upwind_theta = st->upwind_theta ? 1 : 0;
       for (int kind : {K_MX_VERTEX, K_MX_EDGE, K_MX_CELL_KE, K_MX_EDGE_TEND}) {
         prof_begin(stream, kind);
         launch_kind(kind, tile(kind), G, s, ead, ca, (float)dt, stream);
@@ -1363,6 +1369,7 @@ void enqueue_step_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream
         da.L = s.vt32; da.rho = ea.rho; da.thv = ea.thv;
         da.vn = s.vn32; da.phi = s.F32; da.gth = s.G32; da.mflx = s.mflx;
         da.scale = (float)(st->divdamp4 * abar * abar); da.inv_nsub = 1.0 / nsub;
+        da.upwind_theta = st->upwind_theta ? 1 : 0;
         const unsigned nbc8 = (unsigned)((nc + 7) / 8), nbe8 = (unsigned)((G.ne + 7) / 8);
         prof_begin(stream, K_DIVDAMP);
         k_mx_dd_div<<<nbc8, 256, 0, stream>>>(G, s.vn32, s.Kc32);

@@ -167,6 +167,7 @@ struct EdgeArgs {
   double dtau, inv_nsub;
   int corrector;
   int skip_flux;                           // fluxes formed after divergence damping instead
+  int upwind_theta;                        // heat flux with the upwind theta_v (option)
 };
 
 // vn tendency and update, horizontal mass/heat fluxes, edge part of w advection.
@@ -216,8 +217,8 @@ __global__ void __launch_bounds__(256, 4) k_edge_tend(Geo64 G, EdgeArgs a) {
       const double dK = a.Kc[c2 + k] - a.Kc[c1 + k];
       const double T = fma(-dK, ide, fma(0.5, zs, fe) * vt[k]);
       const double A = fma(-((sw + sw_up) * (vie - vie_up)), G.qinv_dz[k], T);
-      const double ts = a.thv[c1 + k] + a.thv[c2 + k];
-      const double th_e = 0.5 * ts;
+      const double t1 = a.thv[c1 + k], t2 = a.thv[c2 + k];
+      const double th_e = 0.5 * (t1 + t2);
       const double pg = th_e * ((a.ex[c2 + k] - a.ex[c1 + k]) * cide);
       double vnew;
       if (a.corrector) {
@@ -230,7 +231,7 @@ __global__ void __launch_bounds__(256, 4) k_edge_tend(Geo64 G, EdgeArgs a) {
       if (a.skip_flux) continue;
       const double F = (0.5 * (a.rho[c1 + k] + a.rho[c2 + k])) * vnew;
       a.F[eo + k] = F;
-      a.G[eo + k] = F * th_e;
+      a.G[eo + k] = F * (a.upwind_theta ? (vnew >= 0.0 ? t1 : t2) : th_e);
       if (a.corrector) a.mflx[eo + k] = fma(F, a.inv_nsub, a.mflx[eo + k]);
     }
   }
@@ -275,6 +276,7 @@ struct DDArgs {
   const double *L, *rho, *thv;             // Laplacian of the divergence, stage state S*
   double *vn, *F, *G, *mflx;
   double scale, inv_nsub;                  // c4 Abar^2
+  int upwind_theta;
 };
 
 __global__ void __launch_bounds__(256, 4) k_dd_edge(Geo64 G, DDArgs a) {
@@ -288,7 +290,8 @@ __global__ void __launch_bounds__(256, 4) k_dd_edge(Geo64 G, DDArgs a) {
     a.vn[eo + k] = vn;
     const double F = (0.5 * (a.rho[c1 + k] + a.rho[c2 + k])) * vn;
     a.F[eo + k] = F;
-    a.G[eo + k] = F * (0.5 * (a.thv[c1 + k] + a.thv[c2 + k]));
+    const double t1 = a.thv[c1 + k], t2 = a.thv[c2 + k];
+    a.G[eo + k] = F * (a.upwind_theta ? (vn >= 0.0 ? t1 : t2) : 0.5 * (t1 + t2));
     a.mflx[eo + k] = fma(F, a.inv_nsub, a.mflx[eo + k]);
   }
 }
@@ -696,6 +699,7 @@ void enqueue_step_fp64(icon_state* st, double dt, int nsub, cudaStream_t stream)
       ea.dtau = dtau; ea.inv_nsub = 1.0 / nsub; ea.corrector = corr;
       const bool damp = corr && st->divdamp4 > 0.0;
       ea.skip_flux = damp ? 1 : 0;
+      ea.upwind_theta = st->upwind_theta ? 1 : 0;
       prof_begin(stream, K_EDGE_TEND);
       k_edge_tend<<<nbe, 256, 0, stream>>>(G, ea);
       prof_end(stream);
@@ -706,6 +710,7 @@ void enqueue_step_fp64(icon_state* st, double dt, int nsub, cudaStream_t stream)
         da.L = s.col_rx; da.rho = rho_st; da.thv = thv_st;
         da.vn = s.vn; da.F = s.F; da.G = s.G; da.mflx = s.mflx;
         da.scale = st->divdamp4 * abar * abar; da.inv_nsub = 1.0 / nsub;
+        da.upwind_theta = st->upwind_theta ? 1 : 0;
         prof_begin(stream, K_DIVDAMP);
         k_dd_div<<<nbc, 256, 0, stream>>>(G, s.vn, s.Kc);
         k_dd_lap<<<nbc, 256, 0, stream>>>(G, s.Kc, s.col_rx);

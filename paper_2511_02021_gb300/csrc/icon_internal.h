@@ -194,6 +194,7 @@ struct icon_state {
   // options (icon_state_set_option)
   double divdamp4 = 0.0;        // fourth-order divergence damping coefficient (0: off)
   double diff4 = 0.0;           // fourth-order background diffusion coefficient (0: off)
+  bool upwind_theta = false;    // heat fluxes with the upwind theta_v
 };
 
 namespace icon {

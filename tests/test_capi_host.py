@@ -42,6 +42,7 @@ def test_host_argument_checks(built_lib):
     assert lib.icon_state_add_tracers(None, 1) == C.ICON_EINVAL
     assert lib.icon_state_set_option(None, 1, 0.0) == C.ICON_EINVAL
     assert lib.icon_state_set_option(None, 2, 0.0) == C.ICON_EINVAL
+    assert lib.icon_state_set_option(None, 3, 1.0) == C.ICON_EINVAL
     assert lib.icon_state_tracers(None, ctypes.byref(n)) == C.ICON_EINVAL
     assert lib.icon_state_set_tracer(None, 0, None, 0) == C.ICON_EINVAL
     assert lib.icon_state_copy_tracer(None, 0, None, 0) == C.ICON_EINVAL
