@@ -174,8 +174,10 @@ int icon_state_init_ex(const icon_grid* grid, uint64_t seed, int case_id,
 /* Advance the state by one dycore step of length dt seconds: nsubsteps
  * predictor-corrector substeps of dt/nsubsteps (each with the vertically
  * implicit w/Exner column solve) followed by one Smagorinsky diffusion step
- * with dt. The step-mean mass fluxes (ICON_F_MFLX, ICON_F_WFLX) are recomputed.
- * The first call for a given (dt, nsubsteps) records a CUDA graph of the step;
+ * with dt. The step-mean mass fluxes (ICON_F_MFLX, ICON_F_WFLX) are recomputed;
+ * the state's tracers, if any, are then transported with them, and the options set
+ * with icon_state_set_option apply. The first call for a given (dt, nsubsteps)
+ * records a CUDA graph of the step (again after an option or tracers are added);
  * later calls replay it. Waits for completion and returns ICON_ENONFINITE if a
  * non-finite value was produced. dt > 0, 1 <= nsubsteps <= 64. */
 int icon_dycore_step(icon_state* state, double dt, int nsubsteps);

@@ -354,27 +354,6 @@ bool field_ref(const icon_state* st, int id, void** ptr, int* is_f32, int64_t* n
   }
 }
 
-__global__ void k_f32_to_f64(const float* __restrict__ a, double* __restrict__ b, int64_t n) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) b[i] = (double)a[i];
-}
-__global__ void k_f64_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) b[i] = (float)a[i];
-}
-// level-major [k][n] <-> row-major [n][ld] for the first nlev levels
-__global__ void k_lm_to_rm(const double* __restrict__ a, double* __restrict__ b, int64_t n, int nlev, int ld) {
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= n * nlev) return;
-  int64_t k = t / n, i = t % n;
-  b[i * ld + k] = a[t];
-}
-__global__ void k_rm_to_lm(const double* __restrict__ b, double* __restrict__ a, int64_t n, int nlev, int ld) {
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= n * nlev) return;
-  int64_t k = t / n, i = t % n;
-  a[t] = b[i * ld + k];
-}
 // host-order [n][nlev] staging <-> the device layout of a field: mode 0 FP64 rows of
 // ld, mode 1 FP32 rows of ld, mode 2 FP64 level-major [k][n]
 __global__ void k_unpack(const double* __restrict__ stage, void* __restrict__ dst, int64_t n, int nlev, int ld,
