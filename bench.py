@@ -64,7 +64,7 @@ COLUMN_FP64_OPS = 75
 # mixed step with stored factors: predictor 42 (one downward sweep forming and factoring
 # the rows, 39; the upward back substitution and damping, 3, with the provisional state's
 # FP32 shadows formed in FP32), corrector 28 (right-hand side, substitution, FP64 updates,
-# vertical mass flux); executed 42.7 and 29.4.
+# vertical mass flux); executed 42.7 and 29.9.
 MX_COLUMN_FP64_OPS = 36
 # mixed step recomputing the factors in both stages (when the stored factors would exceed a
 # quarter of the device memory): executed 47.5 (predictor) and 64.5 (corrector).
@@ -79,9 +79,9 @@ TRACER_FP64_OPS = 77
 # measured; mixed column at R2B6/90 measured and scaled by cells to R2B8/90; recomputing
 # mixed column measured at R2B5/60 and scaled by cells to R2B9/60.
 NCU_TRAFFIC = {
-    ("R2B6-L90-jet-fp64", "column_solve"): 10.07e9,
-    ("R2B6-L90-jet-fp64", "mx_column_solve"): 8.37e9,
-    ("R2B8-L90-jet-mixed", "mx_column_solve"): 8.37e9 * 16,
+    ("R2B6-L90-jet-fp64", "column_solve"): 10.61e9,
+    ("R2B6-L90-jet-fp64", "mx_column_solve"): 7.82e9,
+    ("R2B8-L90-jet-mixed", "mx_column_solve"): 7.82e9 * 16,
     ("R2B9-L60-jet-mixed", "mx_column_solve"): 1.627e9 * 256,
 }
 
