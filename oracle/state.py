@@ -107,11 +107,17 @@ def vertical_grid(nlev, top_m=None, stretch_s=None, damp_m=None):
 def to_half(v, f):
     """Linear-in-z interpolation of a full-level field (n, N) to half levels (n, N+1);
     the top and bottom half levels take the adjacent full value."""
-    N = v.N
+    return to_half_w(v.wu, f)
+
+
+def to_half_w(wu, f):
+    """to_half with the weights of the upper full level given per half level (N+1,)
+    or per point and half level (n, N+1) (a terrain-following grid)."""
+    N = f.shape[1]
     out = np.empty((f.shape[0], N + 1))
     out[:, 0] = f[:, 0]
     out[:, N] = f[:, N - 1]
-    out[:, 1:N] = v.wu[1:N] * f[:, :N - 1] + (1.0 - v.wu[1:N]) * f[:, 1:N]
+    out[:, 1:N] = wu[..., 1:N] * f[:, :N - 1] + (1.0 - wu[..., 1:N]) * f[:, 1:N]
     return out
 
 
@@ -126,13 +132,22 @@ def _latlon_basis(x):
     return cphi, sphi, e_lam, e_phi
 
 
+def heights(z):
+    """Heights as a (1, m) row shared by every point, or the (n, m) heights of each point
+    (a terrain-following grid)."""
+    z = np.asarray(z, dtype=np.float64)
+    return z if z.ndim == 2 else z[None, :]
+
+
 def sbr_state(x, z, u0=20.0, T0=250.0):
-    """Solid-body rotation: (ln p, T, u_lambda) at unit positions x (n,3), heights z (m,)."""
+    """Solid-body rotation: (ln p, T, u_lambda) at unit positions x (n,3), heights z (m,)
+    or (n, m)."""
     cphi, sphi, _, _ = _latlon_basis(x)
-    lnp = (np.log(P0) - GRAV * z[None, :] / (RD * T0)
+    Z = heights(z)
+    lnp = (np.log(P0) - GRAV * Z / (RD * T0)
            - ((R_EARTH * OMEGA * u0 + 0.5 * u0 * u0) * sphi[:, None] ** 2) / (RD * T0))
     T = np.full(lnp.shape, T0)
-    u = np.repeat((u0 * cphi)[:, None], len(z), axis=1)
+    u = (u0 * cphi)[:, None] + np.zeros(lnp.shape)
     return lnp, T, u
 
 
@@ -163,14 +178,15 @@ def jet_state(x, z):
     cphi, sphi, _, _ = _latlon_basis(x)
     B = jet_B()
     H0 = RD * JET_T / GRAV
-    S = np.exp(-((z - JET_ZJ) / JET_HJ) ** 2)
-    dS = -2.0 * (z - JET_ZJ) / (JET_HJ * JET_HJ) * S
+    Z = heights(z)
+    S = np.exp(-((Z - JET_ZJ) / JET_HJ) ** 2)
+    dS = -2.0 * (Z - JET_ZJ) / (JET_HJ * JET_HJ) * S
     Phi = -4.0 * (cphi ** 3 / 3.0 - cphi ** 5 / 5.0)
-    lnp = np.log(P0) - z[None, :] / H0 - B * S[None, :] * Phi[:, None]
-    T = GRAV / (RD * (1.0 / H0 + B * dS[None, :] * Phi[:, None]))
+    lnp = np.log(P0) - Z / H0 - B * S * Phi[:, None]
+    T = GRAV / (RD * (1.0 / H0 + B * dS * Phi[:, None]))
     # divided by sin(phi): a u^2 + b u = c with a = 1/(R cos), b = 2 Omega,
     # c = (Rd T / R) B S * 4 cos^2 sin^2 (= -(Rd T/R) dlnp/dphi / sin)
-    c = (RD * T / R_EARTH) * B * S[None, :] * (4.0 * cphi ** 2 * sphi ** 2)[:, None]
+    c = (RD * T / R_EARTH) * B * S * (4.0 * cphi ** 2 * sphi ** 2)[:, None]
     a = np.where(cphi > 1e-12, 1.0 / (R_EARTH * np.where(cphi > 1e-12, cphi, 1.0)), 0.0)[:, None]
     b = 2.0 * OMEGA
     u = 2.0 * c / (b + np.sqrt(b * b + 4.0 * a * c))
@@ -190,8 +206,11 @@ def case_defaults(case):
     return {CASE_REST: 0.0, CASE_SBR: 0.01, CASE_JET: 0.0, CASE_MEMBER: 0.0}[case]
 
 
-def init_state(g, v, seed, case, noise_K=None, member=0):
-    """Initial prognostic state {vn (Ne,N), w (Nc,N+1), rho, theta_v, exner (Nc,N)}."""
+def init_state(g, v, seed, case, noise_K=None, member=0, terrain=None):
+    """Initial prognostic state {vn (Ne,N), w (Nc,N+1), rho, theta_v, exner (Nc,N)}.
+    With a terrain-following grid (`terrain`, from oracle.terrain.terrain_geometry) the
+    analytic state is taken at each cell's and edge's own full-level heights and the
+    hydrostatic integration runs with each cell's own spacings."""
     N = v.N
     if noise_K is None:
         noise_K = case_defaults(case)
@@ -206,7 +225,7 @@ def init_state(g, v, seed, case, noise_K=None, member=0):
 
     def analytic(x, z):
         if case == CASE_REST:
-            lnp = np.log(P0) - GRAV * z[None, :] / (RD * 250.0) + 0.0 * x[:, :1]
+            lnp = np.log(P0) - GRAV * heights(z) / (RD * 250.0) + 0.0 * x[:, :1]
             return lnp, np.full(lnp.shape, 250.0), np.zeros(lnp.shape)
         if case == CASE_SBR:
             return sbr_state(x, z)
@@ -216,21 +235,24 @@ def init_state(g, v, seed, case, noise_K=None, member=0):
 
     kappa = RD / CPD
     # scalars at cell centres, full levels
-    lnp, T, _ = analytic(g.x_c, v.z_f)
+    zc = v.z_f if terrain is None else terrain.zf_c
+    ze = v.z_f if terrain is None else terrain.zf_e
+    lnp, T, _ = analytic(g.x_c, zc)
     ex_an = np.exp(kappa * (lnp - np.log(P0)))
     thv = T / ex_an
     ex = np.empty_like(thv)
     ex[:, N - 1] = ex_an[:, N - 1]
-    th_ic = to_half(v, thv)
+    th_ic = to_half(v, thv) if terrain is None else to_half_w(terrain.wu_c, thv)
+    dzh = v.dzh[None, :] if terrain is None else terrain.dzh_c
     for k in range(N - 1, 0, -1):
-        ex[:, k - 1] = ex[:, k] - GRAV * v.dzh[k] / (CPD * th_ic[:, k])
+        ex[:, k - 1] = ex[:, k] - GRAV * dzh[:, k] / (CPD * th_ic[:, k])
     if noise_K > 0.0:
         idx = np.arange(g.nc, dtype=np.uint64)[:, None] * np.uint64(N) + np.arange(N, dtype=np.uint64)[None, :]
         thv = thv + noise_K * (2.0 * uniform01(seed_used, idx) - 1.0)
     rho = P0 * ex ** (CVD / RD) / (RD * thv)
 
     # wind at edge midpoints
-    _, _, u = analytic(g.x_e, v.z_f)
+    _, _, u = analytic(g.x_e, ze)
     if bump is not None:
         u = u + _bump(g.x_e, *bump)[:, None]
     _, _, e_lam, _ = _latlon_basis(g.x_e)
