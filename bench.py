@@ -491,6 +491,41 @@ def run_gpu(args, wl, rank, world, local_rank):
             divdamp = {"skipped": str(exc)}
 
     C.icon_state_free(st)
+    # the same workload on terrain-following levels over a Gaussian mountain (1500 m,
+    # e-folding radius 800 km at 90E 30N; FP64 form only): timed graph replays, the kernel
+    # time per kind from two profiled eager steps, and the mass drift
+    topo = None
+    if not args.no_tracer and wl.precision == 0:
+        try:
+            st = C.icon_state_init_ex(grid, wl.seed, wl.case, noise_K=wl.noise_K, topo_height_m=1500.0,
+                                      topo_radius_m=800e3)
+            try:
+                tm0 = C.icon_global_mass(st)
+                for _ in range(args.warmup):
+                    C.icon_dycore_step(st, wl.dt, wl.nsub)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(args.steps):
+                    C.icon_dycore_step_async(st, wl.dt, wl.nsub)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                C.icon_state_status(st)
+                ms_topo = e0.elapsed_time(e1) / args.steps
+                kms, kn = None, None
+                for _ in range(2):
+                    kms, kn = C.icon_dycore_step_profile(st, wl.dt, wl.nsub, kms, kn)
+                names = [C.icon_kernel_kind_name(k) for k in range(C.ICON_KIND_COUNT)]
+                tm1 = C.icon_global_mass(st)
+                topo = {"height_m": 1500.0, "radius_m": 800e3, "value": nc * N * wl.nsub / (ms_topo * 1e-3),
+                        "unit": UNIT, "ms_per_step": ms_topo, "ms_per_step_flat": ms / args.steps,
+                        "kernels_ms_per_step": {n: round(kms[i] / 2, 4) for i, n in enumerate(names)
+                                                if n and kn[i] > 0},
+                        "mass_rel_drift": abs(tm1 - tm0) / tm0}
+            finally:
+                C.icon_state_free(st)
+        except C.IconError as exc:
+            topo = {"skipped": str(exc)}
     C.icon_grid_free(grid)
     if rank != 0:
         return
@@ -510,6 +545,7 @@ def run_gpu(args, wl, rank, world, local_rank):
             "hbm_roofline": step_hbm_roofline(value, wl.precision, hbm_peak), "kernels": breakdown,
             "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "mass_rel_drift": m_drift, "mixed": other,
             "rel_l2_vs_fp64_after_1_step": err_vs_fp64, "tracer": tracer, "divergence_damping": divdamp,
+            "topography": topo,
             "simulated_days_per_day": wl.dt / (ms / args.steps * 1e-3),
             "device_memory_gb": {"peak_allocated": round(torch.cuda.max_memory_allocated() / 1e9, 2),
                                  "total": round(torch.cuda.get_device_properties(0).total_memory / 1e9, 2)}}

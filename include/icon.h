@@ -116,6 +116,21 @@ typedef struct {
   double damp_m;     /* base of the Rayleigh damping layer, m (<=0: 45 km / 20 km)               */
   int precision;     /* icon_precision                                                           */
   int member;        /* ensemble member index for ICON_CASE_MEMBER                               */
+  /* Topography (terrain-following levels; ICON_FP64 only). A Gaussian mountain
+   * hs = topo_height_m exp(-(r / topo_radius_m)^2), r the great-circle distance to 90E 30N,
+   * under SLEVE-type levels z = zeta + hs b(zeta), b = sinh((z_top - zeta)/4 km) /
+   * sinh(z_top/4 km): the lowest level follows the ground, the lid stays flat. The step then
+   * takes the horizontal pressure gradient at constant height (metric correction on the
+   * Exner perturbation from exp(-g z/(cpd 250 K))), the contravariant vertical velocity
+   * w - (vn dz/dn + vt dz/dt) in vertical advection and vertical fluxes (zero at the ground:
+   * w there is the terrain-following value), and thickness-weighted horizontal fluxes;
+   * ICON_F_MFLX is then rho_e vn dz_e (kg/m/s per layer) and ICON_F_WFLX contravariant. The
+   * paper's vertical coordinate is ICON's terrain-following hybrid height coordinate
+   * (Sec. "Current State of the Art"). 0 = flat ground (default); 0 < topo_height_m <= 2000
+   * and topo_radius_m >= 1e4, else ICON_EINVAL. States with topography take no tracers and
+   * join no ensemble. */
+  double topo_height_m;
+  double topo_radius_m;
 } icon_case_params;
 
 /* ---------------------------------------------------------------- allocator, stream */

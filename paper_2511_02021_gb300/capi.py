@@ -45,7 +45,8 @@ class IconError(RuntimeError):
 
 class CaseParams(ctypes.Structure):
     _fields_ = [("noise_K", ctypes.c_double), ("top_m", ctypes.c_double), ("stretch_s", ctypes.c_double),
-                ("damp_m", ctypes.c_double), ("precision", ctypes.c_int), ("member", ctypes.c_int)]
+                ("damp_m", ctypes.c_double), ("precision", ctypes.c_int), ("member", ctypes.c_int),
+                ("topo_height_m", ctypes.c_double), ("topo_radius_m", ctypes.c_double)]
 
 
 def _load():
@@ -168,8 +169,9 @@ def icon_state_init(grid, seed, case_id):
     return h
 
 
-def icon_state_init_ex(grid, seed, case_id, noise_K=-1.0, precision=ICON_FP64, member=0):
-    p = CaseParams(noise_K, -1.0, -1.0, -1.0, precision, member)
+def icon_state_init_ex(grid, seed, case_id, noise_K=-1.0, precision=ICON_FP64, member=0,
+                       topo_height_m=0.0, topo_radius_m=0.0):
+    p = CaseParams(noise_K, -1.0, -1.0, -1.0, precision, member, topo_height_m, topo_radius_m)
     h = ctypes.c_void_p()
     _check(_lib.icon_state_init_ex(grid, seed, case_id, ctypes.byref(p), ctypes.byref(h)))
     return h

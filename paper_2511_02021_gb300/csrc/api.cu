@@ -60,7 +60,8 @@ static const char* kKindNames[K_KIND_COUNT] = {
     "vertex_curl_wmean", "edge_vt_ke", "cell_ke", "edge_tendency_flux", "column_solve",
     "diff_vertex", "diff_div", "diff_edge", "diff_theta", "global_mass",
     "mx_vertex", "mx_edge_diag", "mx_cell_ke", "mx_edge_tendency_flux", "mx_column_solve", "mx_column_prep",
-    "mx_diff_vertex", "mx_diff_edge", "mx_diff_theta", "ensemble_persistent", "tracer_transport", "divergence_damping", "background_diffusion"};
+    "mx_diff_vertex", "mx_diff_edge", "mx_diff_theta", "ensemble_persistent", "tracer_transport", "divergence_damping", "background_diffusion",
+    "terrain_metrics"};
 
 Allocator current_allocator() {
   std::lock_guard<std::mutex> lk(g_alloc_mu);
@@ -482,7 +483,18 @@ int icon_state_init_ex(const icon_grid* grid, uint64_t seed, int case_id, const 
   if (grid->vert.N < 2) { set_error("icon_state_init: the dycore needs nlev >= 2"); return ICON_EINVAL; }
   icon_case_params p;
   p.noise_K = -1.0; p.top_m = -1.0; p.stretch_s = -1.0; p.damp_m = -1.0; p.precision = ICON_FP64; p.member = 0;
+  p.topo_height_m = 0.0; p.topo_radius_m = 0.0;
   if (params) p = *params;
+  const bool topo = p.topo_height_m != 0.0;
+  if (topo && !(p.topo_height_m > 0.0 && p.topo_height_m <= 0.5 * kTopoDecay && p.topo_radius_m >= 1e4)) {
+    set_error("icon_state_init: topography needs 0 < height <= %g m and radius >= 1e4 m (got %g, %g)",
+              0.5 * kTopoDecay, p.topo_height_m, p.topo_radius_m);
+    return ICON_EINVAL;
+  }
+  if (topo && p.precision != ICON_FP64) {
+    set_error("icon_state_init: topography is built for the FP64 form only");
+    return ICON_EINVAL;
+  }
   if (p.precision != ICON_FP64 && p.precision != ICON_MIXED) {
     set_error("icon_state_init: unknown precision %d", p.precision);
     return ICON_EINVAL;
@@ -505,6 +517,7 @@ int icon_state_init_ex(const icon_grid* grid, uint64_t seed, int case_id, const 
     cudaError_t e = cudaMemsetAsync(st->s.status, 0, 64 * sizeof(unsigned), stream);
     if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemsetAsync");
   }
+  if (rc == ICON_OK && topo) rc = topo_build(st, p.topo_height_m, p.topo_radius_m, stream);
   if (rc == ICON_OK) rc = init_state_device(st, seed, case_id, p, stream);
   if (rc == ICON_OK) {
     cudaError_t e = cudaEventCreateWithFlags(&st->done, cudaEventDisableTiming);
@@ -746,6 +759,10 @@ int icon_state_add_tracers(icon_state* st, int ntracers) {
   if (!st) { set_error("icon_state_add_tracers: state is NULL"); return ICON_EINVAL; }
   if (ntracers < 1 || ntracers > 8) { set_error("icon_state_add_tracers: need 1..8 tracers"); return ICON_EINVAL; }
   if (st->s.ntr != 0) { set_error("icon_state_add_tracers: the state already has tracers"); return ICON_EINVAL; }
+  if (st->s.topo.on) {
+    set_error("icon_state_add_tracers: tracer transport on terrain-following levels is not built");
+    return ICON_EINVAL;
+  }
   const int rc = tracer_alloc(st, ntracers);
   if (rc != ICON_OK) return rc;
   if (st->graph) {                      // the step's graph now has to transport them too

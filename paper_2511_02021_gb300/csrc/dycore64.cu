@@ -55,6 +55,11 @@ struct Geo64 {
   const double *n_e, *t_e, *s_ce;
   const double *wu, *wl, *inv_dz, *inv_dz2, *qinv_dz;
   const double* cc;                        // per-level constants for the current dtau
+  // terrain-following levels (the TOPO kernel variants; see terrain.cu): per-edge normal
+  // slope factor, full-level decay, per-entity tables [entity][ld], the stage's
+  // contravariant correction and Exner-perturbation derivative
+  const double *t_sn, *t_bf, *t_wu_e, *t_inv_dz_e, *t_dz_e;
+  const double *t_wu_c, *t_inv_dz_c, *t_inv_dzh_c, *t_exref_c, *t_wcc, *t_dpdz;
 };
 
 // per-level constants of the column solve for one dtau, [8][ld] (same layout as the
@@ -176,6 +181,13 @@ struct EdgeArgs {
 // for l < 31, full level k = h), each half-level interpolant and cell-pair sum formed
 // once and handed to the lane below with a shuffle, factors of 1/2 folded into
 // exactly-scaled constants, and the per-edge constants cpd / d_e hoisted.
+//
+// TOPO (terrain-following levels): per-edge interpolation weights, the contravariant
+// vertical velocity w - wcc (zero at lid and ground) in the vertical advection of vn,
+// the metric correction of the pressure gradient on pi' = pi - pi_ref,
+//   (pi'_c2 - pi'_c1)/d_e - sn_e bf_k (d pi'/dz at c1 and c2)/2,
+// and mass fluxes through layers of thickness dz_e.
+template <bool TOPO>
 __global__ void __launch_bounds__(256, 4) k_edge_tend(Geo64 G, EdgeArgs a) {
   const int64_t e = warp_entity();
   if (e >= G.ne) return;
@@ -185,6 +197,7 @@ __global__ void __launch_bounds__(256, 4) k_edge_tend(Geo64 G, EdgeArgs a) {
   const int64_t eo = e * ld;
   const double ide = G.inv_de[e], ile = G.inv_le[e], fe = G.f_e[e];
   const double cide = kCpd * ide;
+  const double sne = TOPO ? G.t_sn[e] : 0.0;
   const double* __restrict__ vn = a.vn + eo;
   const double* __restrict__ vt = a.vt + eo;
   const double dtau = a.dtau;
@@ -195,14 +208,23 @@ __global__ void __launch_bounds__(256, 4) k_edge_tend(Geo64 G, EdgeArgs a) {
     // half-level interpolation weights: f(0) = f[0], f(N) = f[N-1], linear between
     const int hl = h > 0 ? (h - 1 < N - 1 ? h - 1 : N - 1) : 0;
     const int hu = h < N ? h : N - 1;
-    const double wa = (h == 0) ? 0.0 : (h >= N ? 1.0 : G.wu[h]);
-    const double wb = (h == 0) ? 1.0 : (h >= N ? 0.0 : G.wl[h]);
+    double wa, wb;
+    if (TOPO) {
+      wa = (h == 0) ? 0.0 : (h >= N ? 1.0 : G.t_wu_e[eo + h]);
+      wb = (h == 0) ? 1.0 : (h >= N ? 0.0 : 1.0 - wa);
+    } else {
+      wa = (h == 0) ? 0.0 : (h >= N ? 1.0 : G.wu[h]);
+      wb = (h == 0) ? 1.0 : (h >= N ? 0.0 : G.wl[h]);
+    }
     double vie = 0.0, tie = 0.0, sw = 0.0, dw = 0.0, dwv = 0.0;
     if (hv) {
       vie = wa * vn[hl] + wb * vn[hu];
       tie = wa * vt[hl] + wb * vt[hu];
       const double w1 = a.w[c1 + h], w2 = a.w[c2 + h];
-      sw = w1 + w2;
+      if (TOPO)
+        sw = (h > 0 && h < N) ? (w1 - G.t_wcc[c1 + h]) + (w2 - G.t_wcc[c2 + h]) : 0.0;
+      else
+        sw = w1 + w2;
       dw = w2 - w1;
       dwv = a.w_v[v2 + h] - a.w_v[v1 + h];
     }
@@ -216,10 +238,17 @@ __global__ void __launch_bounds__(256, 4) k_edge_tend(Geo64 G, EdgeArgs a) {
       const double zs = a.zeta[v1 + k] + a.zeta[v2 + k];
       const double dK = a.Kc[c2 + k] - a.Kc[c1 + k];
       const double T = fma(-dK, ide, fma(0.5, zs, fe) * vt[k]);
-      const double A = fma(-((sw + sw_up) * (vie - vie_up)), G.qinv_dz[k], T);
+      const double A = fma(-((sw + sw_up) * (vie - vie_up)), TOPO ? 0.25 * G.t_inv_dz_e[eo + k] : G.qinv_dz[k], T);
       const double t1 = a.thv[c1 + k], t2 = a.thv[c2 + k];
       const double th_e = 0.5 * (t1 + t2);
-      const double pg = th_e * ((a.ex[c2 + k] - a.ex[c1 + k]) * cide);
+      double pg;
+      if (TOPO) {
+        const double ep1 = a.ex[c1 + k] - G.t_exref_c[c1 + k], ep2 = a.ex[c2 + k] - G.t_exref_c[c2 + k];
+        const double corr = (sne * G.t_bf[k]) * (0.5 * (G.t_dpdz[c1 + k] + G.t_dpdz[c2 + k]));
+        pg = th_e * (kCpd * ((ep2 - ep1) * ide - corr));
+      } else {
+        pg = th_e * ((a.ex[c2 + k] - a.ex[c1 + k]) * cide);
+      }
       double vnew;
       if (a.corrector) {
         vnew = fma(dtau, fma(0.5, a.Avn0[eo + k] + A, -pg), a.vn_base[eo + k]);
@@ -229,7 +258,8 @@ __global__ void __launch_bounds__(256, 4) k_edge_tend(Geo64 G, EdgeArgs a) {
       }
       a.vn_out[eo + k] = vnew;
       if (a.skip_flux) continue;
-      const double F = (0.5 * (a.rho[c1 + k] + a.rho[c2 + k])) * vnew;
+      double F = (0.5 * (a.rho[c1 + k] + a.rho[c2 + k])) * vnew;
+      if (TOPO) F *= G.t_dz_e[eo + k];
       a.F[eo + k] = F;
       a.G[eo + k] = F * (a.upwind_theta ? (vnew >= 0.0 ? t1 : t2) : th_e);
       if (a.corrector) a.mflx[eo + k] = fma(F, a.inv_nsub, a.mflx[eo + k]);
@@ -275,6 +305,7 @@ __global__ void __launch_bounds__(256, 4) k_dd_lap(Geo64 G, const double* __rest
 struct DDArgs {
   const double *L, *rho, *thv;             // Laplacian of the divergence, stage state S*
   double *vn, *F, *G, *mflx;
+  const double* dz_e;                      // layer thickness at edges (terrain-following), or NULL
   double scale, inv_nsub;                  // c4 Abar^2
   int upwind_theta;
 };
@@ -288,7 +319,8 @@ __global__ void __launch_bounds__(256, 4) k_dd_edge(Geo64 G, DDArgs a) {
   for (int k = lane; k < G.N; k += 32) {
     const double vn = a.vn[eo + k] - s * (a.L[c2 + k] - a.L[c1 + k]);
     a.vn[eo + k] = vn;
-    const double F = (0.5 * (a.rho[c1 + k] + a.rho[c2 + k])) * vn;
+    double F = (0.5 * (a.rho[c1 + k] + a.rho[c2 + k])) * vn;
+    if (a.dz_e) F *= a.dz_e[eo + k];
     a.F[eo + k] = F;
     const double t1 = a.thv[c1 + k], t2 = a.thv[c2 + k];
     a.G[eo + k] = F * (a.upwind_theta ? (vn >= 0.0 ? t1 : t2) : 0.5 * (t1 + t2));
@@ -328,7 +360,12 @@ struct ColArgs {
 };
 
 // windows of 31 levels: lane l holds full level k = base + l and the half level above
-// it (h = k); lane 31 only supplies the half level below lane 30's full level
+// it (h = k); lane 31 only supplies the half level below lane 30's full level.
+// TOPO (terrain-following levels): each cell's own spacings and interpolation weights,
+// thickness-weighted horizontal fluxes (already carrying dz_e) divided by the cell's dz,
+// the explicit vertical fluxes with the contravariant (1 - beta) w - wcc, and the
+// vertical advection of w with w - wcc.
+template <bool TOPO>
 __global__ void __launch_bounds__(256, 4) k_col_rows(Geo64 G, ColArgs a) {
   const int64_t c = warp_entity();
   if (c >= G.nc) return;
@@ -356,15 +393,25 @@ __global__ void __launch_bounds__(256, 4) k_col_rows(Geo64 G, ColArgs a) {
     if (k == 0) { ri = rho; ti = thv; }
     else if (k == N) { ri = rho_m; ti = thv_m; }
     else if (k < N) {
-      const double wu = cc[C_WU * ld + k], wl = cc[C_WL * ld + k];
-      ri = wu * rho_m + wl * rho;
-      ti = wu * thv_m + wl * thv;
+      if constexpr (TOPO) {
+        const double wu = G.t_wu_c[o + k], wl = 1.0 - wu;
+        ri = wu * rho_m + wl * rho;
+        ti = wu * thv_m + wl * thv;
+      } else {
+        const double wu = cc[C_WU * ld + k], wl = cc[C_WL * ld + k];
+        ri = wu * rho_m + wl * rho;
+        ti = wu * thv_m + wl * thv;
+      }
     }
     const double M = ri * ti;
     const double wk = hv ? a.w[o + k] : 0.0;
+    // TOPO: explicit part of the contravariant velocity at interior half levels
+    const double ve = (TOPO && k >= 1 && k < N) ? (1.0 - kBeta) * wk - G.t_wcc[o + k] : 0.0;
     const double ri1 = __shfl_down_sync(0xffffffffu, ri, 1);      // half level k + 1
     const double M1 = __shfl_down_sync(0xffffffffu, M, 1);
     const double w1 = __shfl_down_sync(0xffffffffu, wk, 1);
+    double ve1 = 0.0;
+    if constexpr (TOPO) ve1 = __shfl_down_sync(0xffffffffu, ve, 1);
     double gam = 0.0, px = 0.0;
     if (kv) {
       // explicit predictors at full level k
@@ -372,12 +419,20 @@ __global__ void __launch_bounds__(256, 4) k_col_rows(Geo64 G, ColArgs a) {
       for (int s = 0; s < 3; ++s) Dr += dw[s] * a.F[E[s] + k];
       for (int s = 0; s < 3; ++s) Dt += dw[s] * a.G[E[s] + k];
       const double Th = rho * thv;
-      const double dt1 = cc[C_DT1BDZ * ld + k];
-      const double rx = (rho - dtau * Dr) - dt1 * (ri * wk - ri1 * w1);
-      const double tx = (Th - dtau * Dt) - dt1 * (M * wk - M1 * w1);
+      double rx, tx;
+      if constexpr (TOPO) {
+        const double idz = G.t_inv_dz_c[o + k];
+        rx = rho - (dtau * ((Dr + ri * ve) - ri1 * ve1)) * idz;
+        tx = Th - (dtau * ((Dt + M * ve) - M1 * ve1)) * idz;
+      } else {
+        const double dt1 = cc[C_DT1BDZ * ld + k];
+        rx = (rho - dtau * Dr) - dt1 * (ri * wk - ri1 * w1);
+        tx = (Th - dtau * Dt) - dt1 * (M * wk - M1 * w1);
+      }
       const double g = (rcv * ex) * recip64(Th);
       px = ex + g * (tx - Th);
-      gam = g * cc[C_DTBDZ * ld + k];
+      if constexpr (TOPO) gam = g * (dtau * kBeta * G.t_inv_dz_c[o + k]);
+      else gam = g * cc[C_DTBDZ * ld + k];
       a.rx[o + k] = rx;
       a.tx[o + k] = tx;
       a.px[o + k] = px;
@@ -398,12 +453,24 @@ __global__ void __launch_bounds__(256, 4) k_col_rows(Geo64 G, ColArgs a) {
       double hadv = 0.0;
       for (int s = 0; s < 3; ++s) hadv += kw[s] * a.a_e[E[s] + h];
       const double ws = a.w_stage[o + h];
-      double Aw = -hadv - ws * (a.w_stage[o + h - 1] - a.w_stage[o + h + 1]) * G.inv_dz2[h];
+      double Aw;
+      if constexpr (TOPO)
+        Aw = -hadv - (ws - G.t_wcc[o + h]) * (a.w_stage[o + h - 1] - a.w_stage[o + h + 1]) *
+                         (0.5 * G.t_inv_dzh_c[o + h]);
+      else
+        Aw = -hadv - ws * (a.w_stage[o + h - 1] - a.w_stage[o + h + 1]) * G.inv_dz2[h];
       if (a.corrector) Aw = 0.5 * (a.Aw0[o + h] + Aw);
       else a.Aw0[o + h] = Aw;
       const double th_ic = ti;
-      const double w_x = wk + dtau * ((Aw - cc[C_CX * ld + h] * th_ic * (ex_m - ex)) - kGrav);
-      const double aa = cc[C_CA * ld + h] * th_ic;
+      double w_x, aa;
+      if constexpr (TOPO) {
+        const double idzh = G.t_inv_dzh_c[o + h];
+        w_x = wk + dtau * ((Aw - ((1.0 - kBeta) * kCpd * idzh) * th_ic * (ex_m - ex)) - kGrav);
+        aa = (dtau * kBeta * kCpd * idzh) * th_ic;
+      } else {
+        w_x = wk + dtau * ((Aw - cc[C_CX * ld + h] * th_ic * (ex_m - ex)) - kGrav);
+        aa = cc[C_CA * ld + h] * th_ic;
+      }
       const int64_t i = (int64_t)h * nc + c;
       a.lo[i] = -aa * gam_m * M_m;
       a.di[i] = 1.0 + aa * (gam_m + gam) * M;
@@ -455,6 +522,9 @@ __global__ void __launch_bounds__(128) k_col_thomas(Geo64 G, ColArgs a) {
   }
 }
 
+// TOPO: each cell's dz, the contravariant step-mean vertical flux, and the ground w of
+// the stage (its wcc, so that w - wcc = 0 there)
+template <bool TOPO>
 __global__ void __launch_bounds__(256) k_col_update(Geo64 G, ColArgs a) {
   const int64_t c = warp_entity();
   if (c >= G.nc) return;
@@ -474,14 +544,16 @@ __global__ void __launch_bounds__(256) k_col_update(Geo64 G, ColArgs a) {
     if (lane < 31 && k < N) {
       const double q = M * wn - M1 * wn1;
       const double r = ri * wn - ri1 * wn1;
-      const double dtb = cc[C_DTBDZ * ld + k];
+      const double dtb = TOPO ? a.dtau * kBeta * G.t_inv_dz_c[o + k] : cc[C_DTBDZ * ld + k];
       const double Th_n = a.tx[o + k] - dtb * q;
       const double ex_n = a.px[o + k] - a.gm[o + k] * q;
       const double rho_n = a.rx[o + k] - dtb * r;
       const double thv_n = Th_n * recip64(rho_n);
       if (a.corrector) {
         const double wold = a.w[o + k];
-        a.wflx[o + k] = a.wflx[o + k] + ri * (kBeta * wn + (1.0 - kBeta) * wold) * a.inv_nsub;
+        double wc = kBeta * wn + (1.0 - kBeta) * wold;
+        if (TOPO) wc -= G.t_wcc[o + k];
+        a.wflx[o + k] = a.wflx[o + k] + ri * wc * a.inv_nsub;
       }
       a.rho_o[o + k] = rho_n;
       a.thv_o[o + k] = thv_n;
@@ -490,7 +562,7 @@ __global__ void __launch_bounds__(256) k_col_update(Geo64 G, ColArgs a) {
       bad |= !finite_bits(thv_n) || !finite_bits(wn) || !finite_bits(ex_n);
     }
   }
-  if (lane == 0) a.w_o[o + N] = 0.0;
+  if (lane == 0) a.w_o[o + N] = TOPO ? G.t_wcc[o + N] : 0.0;
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.status, 1u);
 }
 
@@ -648,14 +720,18 @@ Geo64 make_geo(const icon_grid* grid, const double* cc) {
   G.inv_L34 = g.inv_L34; G.n_e = g.n_e; G.t_e = g.t_e; G.s_ce = g.s_ce;
   G.wu = v.d_wu; G.wl = v.d_wl; G.inv_dz = v.d_inv_dz; G.inv_dz2 = v.d_inv_dz2; G.qinv_dz = v.d_qinv_dz;
   G.cc = cc;
+  G.t_sn = G.t_bf = G.t_wu_e = G.t_inv_dz_e = G.t_dz_e = nullptr;
+  G.t_wu_c = G.t_inv_dz_c = G.t_inv_dzh_c = G.t_exref_c = G.t_wcc = G.t_dpdz = nullptr;
   return G;
 }
 
-void launch_column(const Geo64& G, const ColArgs& a, cudaStream_t st) {
+void launch_column(const Geo64& G, const ColArgs& a, bool topo, cudaStream_t st) {
   const unsigned nbc = blocks_for(G.nc, kWarpsPerBlock);
-  k_col_rows<<<nbc, 256, 0, st>>>(G, a);
+  if (topo) k_col_rows<true><<<nbc, 256, 0, st>>>(G, a);
+  else k_col_rows<false><<<nbc, 256, 0, st>>>(G, a);
   k_col_thomas<<<blocks_for(G.nc, 128), 128, 0, st>>>(G, a);
-  k_col_update<<<nbc, 256, 0, st>>>(G, a);
+  if (topo) k_col_update<true><<<nbc, 256, 0, st>>>(G, a);
+  else k_col_update<false><<<nbc, 256, 0, st>>>(G, a);
 }
 
 }  // namespace
@@ -663,7 +739,14 @@ void launch_column(const Geo64& G, const ColArgs& a, cudaStream_t st) {
 void enqueue_step_fp64(icon_state* st, double dt, int nsub, cudaStream_t stream) {
   const icon_grid* grid = st->grid;
   StateDev& s = st->s;
-  const Geo64 G = make_geo(grid, s.colconst);
+  Geo64 G = make_geo(grid, s.colconst);
+  const TopoDev& T = s.topo;
+  const bool topo = T.on;
+  if (topo) {
+    G.t_sn = T.sn; G.t_bf = T.bf; G.t_wu_e = T.wu_e; G.t_inv_dz_e = T.inv_dz_e; G.t_dz_e = T.dz_e;
+    G.t_wu_c = T.wu_c; G.t_inv_dz_c = T.inv_dz_c; G.t_inv_dzh_c = T.inv_dzh_c; G.t_exref_c = T.exref_c;
+    G.t_wcc = T.wcc; G.t_dpdz = T.dpdz;
+  }
   const int ld = G.ld;
   const double dtau = dt / nsub;
   const Vertical& vg = grid->vert;
@@ -689,6 +772,7 @@ void enqueue_step_fp64(icon_state* st, double dt, int nsub, cudaStream_t stream)
       prof_begin(stream, K_CELL_KE);
       k_cell_ke<<<nbc, 256, 0, stream>>>(G, s.Ke, s.Kc);
       prof_end(stream);
+      if (topo) topo_stage(st, vn_st, s.vt, ex_st, stream);
       EdgeArgs ea;
       ea.vn = vn_st; ea.w = w_st; ea.rho = rho_st; ea.thv = thv_st; ea.ex = ex_st;
       ea.vt = s.vt; ea.Kc = s.Kc; ea.zeta = s.zeta; ea.w_v = s.w_v;
@@ -701,7 +785,8 @@ void enqueue_step_fp64(icon_state* st, double dt, int nsub, cudaStream_t stream)
       ea.skip_flux = damp ? 1 : 0;
       ea.upwind_theta = st->upwind_theta ? 1 : 0;
       prof_begin(stream, K_EDGE_TEND);
-      k_edge_tend<<<nbe, 256, 0, stream>>>(G, ea);
+      if (topo) k_edge_tend<true><<<nbe, 256, 0, stream>>>(G, ea);
+      else k_edge_tend<false><<<nbe, 256, 0, stream>>>(G, ea);
       prof_end(stream);
       if (damp) {
         // Kc and the column's update-operand scratch are free until the column runs
@@ -709,6 +794,7 @@ void enqueue_step_fp64(icon_state* st, double dt, int nsub, cudaStream_t stream)
         DDArgs da;
         da.L = s.col_rx; da.rho = rho_st; da.thv = thv_st;
         da.vn = s.vn; da.F = s.F; da.G = s.G; da.mflx = s.mflx;
+        da.dz_e = topo ? T.dz_e : nullptr;
         da.scale = st->divdamp4 * abar * abar; da.inv_nsub = 1.0 / nsub;
         da.upwind_theta = st->upwind_theta ? 1 : 0;
         prof_begin(stream, K_DIVDAMP);
@@ -733,7 +819,7 @@ void enqueue_step_fp64(icon_state* st, double dt, int nsub, cudaStream_t stream)
       ca.status = s.status;
       ca.dtau = dtau; ca.inv_nsub = 1.0 / nsub; ca.corrector = corr;
       prof_begin(stream, K_COLUMN);
-      launch_column(G, ca, stream);
+      launch_column(G, ca, topo, stream);
       prof_end(stream);
     }
   }

@@ -35,7 +35,8 @@ enum KernelKind {
   K_VERTEX = 0, K_EDGE_VT, K_CELL_KE, K_EDGE_TEND, K_COLUMN,
   K_DIFF_VERTEX, K_DIFF_DIV, K_DIFF_EDGE, K_DIFF_THETA, K_MASS,
   K_MX_VERTEX, K_MX_EDGE, K_MX_CELL_KE, K_MX_EDGE_TEND, K_MX_COLUMN, K_MX_COLUMN_PREP,
-  K_MX_DIFF_VERTEX, K_MX_DIFF_EDGE, K_MX_DIFF_THETA, K_ENSEMBLE, K_TRACER, K_DIVDAMP, K_DIFF4, K_KIND_COUNT
+  K_MX_DIFF_VERTEX, K_MX_DIFF_EDGE, K_MX_DIFF_THETA, K_ENSEMBLE, K_TRACER, K_DIVDAMP, K_DIFF4, K_TERRAIN,
+  K_KIND_COUNT
 };
 static_assert(K_KIND_COUNT <= ICON_KIND_COUNT, "kind table");
 // When a profile is active on this thread, every launch is bracketed by events.
@@ -123,8 +124,25 @@ struct icon_grid {
 namespace icon {
 // Device buffers of one state. Full-level fields are [n][ld], half-level fields
 // [n][ld] with N+1 used entries. "star" holds the predictor state.
+// terrain-following levels over topography (FP64 form): z = zeta_h + hs b_h per column
+struct TopoDev {
+  bool on = false;
+  double h0 = 0.0, radius = 0.0;      // Gaussian mountain height and e-folding radius, m
+  double* hs = nullptr;               // [Nc] surface height
+  double *b = nullptr, *bf = nullptr; // [ld] decay at half and full levels
+  double *sn = nullptr, *st = nullptr;   // [Ne] (hs_c2 - hs_c1)/d_e, (hs_v2 - hs_v1)/l_e
+  // per cell and level [Nc][ld]: 1/dz, 1/dzh (interior half levels), upper interpolation
+  // weight (interior half levels), reference Exner at the full level, dz
+  double *inv_dz_c = nullptr, *inv_dzh_c = nullptr, *wu_c = nullptr, *exref_c = nullptr, *dz_c = nullptr;
+  // per edge and level [Ne][ld]: upper interpolation weight, 1/dz, dz
+  double *wu_e = nullptr, *inv_dz_e = nullptr, *dz_e = nullptr;
+  // per stage [Nc][ld]: contravariant correction at half levels, d pi'/dz at full levels
+  double *wcc = nullptr, *dpdz = nullptr;
+};
+
 struct StateDev {
   int precision = ICON_FP64;
+  TopoDev topo;
   // prognostics S^n (FP64 in both modes except vn in mixed mode)
   double *vn = nullptr, *w = nullptr, *rho = nullptr, *thv = nullptr, *ex = nullptr;
   float *vn32 = nullptr;
@@ -219,6 +237,11 @@ namespace icon {
 // grid_build.cu
 int build_grid_device(icon_grid* grid, cudaStream_t st);
 int build_tracer_tables(icon_grid* grid, cudaStream_t st);
+// terrain.cu
+constexpr double kTopoDecay = 4000.0;   // SLEVE decay scale, m
+constexpr double kTopoTref = 250.0;     // temperature of the reference Exner profile, K
+int topo_build(icon_state* st, double h0, double radius, cudaStream_t stream);
+void topo_stage(icon_state* st, const double* vn, const double* vt, const double* ex, cudaStream_t stream);
 // tracer.cu
 int tracer_alloc(icon_state* st, int ntracers);
 void tracer_begin(icon_state* st, cudaStream_t stream);

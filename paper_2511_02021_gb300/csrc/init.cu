@@ -122,9 +122,13 @@ __device__ void analytic(const CaseDev& cd, double x, double y, double zu, doubl
 
 // one thread per column: theta_v, discrete hydrostatic Exner, noise, rho
 // cells c0 .. c0+n-1; outputs at rows (c - c0) of the [n][ld] arrays
+// On terrain-following levels (hs != NULL) a cell's full levels lie at z_f + hs bf and its
+// centre spacings and interpolation weights are its own (wu_c, [Nc][ld]).
 __global__ void k_init_cells(CaseDev cd, int64_t c0, int64_t n, const double* __restrict__ x_c,
                              const double* __restrict__ z_f, const double* __restrict__ dzh,
-                             const double* __restrict__ wu, const double* __restrict__ wl, double* __restrict__ rho,
+                             const double* __restrict__ wu, const double* __restrict__ wl,
+                             const double* __restrict__ hs, const double* __restrict__ bf,
+                             const double* __restrict__ wu_c, double* __restrict__ rho,
                              double* __restrict__ thv, double* __restrict__ ex, double* __restrict__ w) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= n) return;
@@ -136,17 +140,26 @@ __global__ void k_init_cells(CaseDev cd, int64_t c0, int64_t n, const double* __
   double* rr = rho + t * ld;
   const double kap = kRd / kCpd;
   double exan_bottom = 0.0;
+  const double hsc = hs ? hs[c] : 0.0;
   for (int k = 0; k < N; ++k) {
     double lnp, T, u;
-    analytic(cd, x, y, z, z_f[k], lnp, T, u);
+    analytic(cd, x, y, z, hs ? z_f[k] + hsc * bf[k] : z_f[k], lnp, T, u);
     double exan = exp(kap * (lnp - log(kP0)));
     th[k] = T / exan;
     if (k == N - 1) exan_bottom = exan;
   }
   pe[N - 1] = exan_bottom;
   for (int k = N - 1; k > 0; --k) {
-    double thic = wu[k] * th[k - 1] + wl[k] * th[k];
-    pe[k - 1] = pe[k] - kGrav * dzh[k] / (kCpd * thic);
+    double thic, dzk;
+    if (hs) {
+      const double wuc = wu_c[c * ld + k];
+      thic = wuc * th[k - 1] + (1.0 - wuc) * th[k];
+      dzk = dzh[k] + hsc * (bf[k - 1] - bf[k]);
+    } else {
+      thic = wu[k] * th[k - 1] + wl[k] * th[k];
+      dzk = dzh[k];
+    }
+    pe[k - 1] = pe[k] - kGrav * dzk / (kCpd * thic);
   }
   if (cd.noise > 0.0) {
     for (int k = 0; k < N; ++k) {
@@ -161,8 +174,12 @@ __global__ void k_init_cells(CaseDev cd, int64_t c0, int64_t n, const double* __
 
 // one thread per (edge, level): vn = u . n with u = u_lambda e_lambda
 // edges e0 .. e0+n-1; output rows (e - e0)
+// on terrain-following levels an edge's full levels lie at z_f + hs_e bf, hs_e the mean of
+// its two cells' surface heights
 __global__ void k_init_edges(CaseDev cd, int64_t e0, int64_t n, const double* __restrict__ x_e,
-                             const double* __restrict__ n_e, const double* __restrict__ z_f, double* __restrict__ vn) {
+                             const double* __restrict__ n_e, const double* __restrict__ z_f,
+                             const int* __restrict__ e2c, const double* __restrict__ hs,
+                             const double* __restrict__ bf, double* __restrict__ vn) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int ld = cd.ld;
   if (t >= n * ld) return;
@@ -171,7 +188,8 @@ __global__ void k_init_edges(CaseDev cd, int64_t e0, int64_t n, const double* __
   if (k >= cd.N) { vn[t] = 0.0; return; }
   double x = x_e[3 * e], y = x_e[3 * e + 1], z = x_e[3 * e + 2];
   double lnp, T, u;
-  analytic(cd, x, y, z, z_f[k], lnp, T, u);
+  const double zz = hs ? z_f[k] + (0.5 * (hs[e2c[2 * e]] + hs[e2c[2 * e + 1]])) * bf[k] : z_f[k];
+  analytic(cd, x, y, z, zz, lnp, T, u);
   if (cd.has_bump) {
     double cx = y * cd.bz - z * cd.by, cy = z * cd.bx - x * cd.bz, cz = x * cd.by - y * cd.bx;
     double r = kR * atan2(sqrt((cx * cx + cy * cy) + cz * cz), (x * cd.bx + y * cd.by) + z * cd.bz);
@@ -317,9 +335,12 @@ int init_state_device(icon_state* st, uint64_t seed, int case_id, const icon_cas
   k_exner_ref<<<1, 1, 0, stream>>>(v.N, v.d_z_f, v.d_dzh, v.d_wu, v.d_wl, s.ex_ref);
   if (s.exref32) k_to_f32<<<1, 256, 0, stream>>>(s.ex_ref, s.exref32, v.ld);
   if (s.precision == ICON_FP64) {
+    const TopoDev& T = s.topo;
     k_init_cells<<<blocks_for(g.nc, 128), 128, 0, stream>>>(cd, 0, g.nc, g.x_c, v.d_z_f, v.d_dzh, v.d_wu, v.d_wl,
-                                                            s.rho, s.thv, s.ex, s.w);
-    k_init_edges<<<blocks_for(g.ne * v.ld, 256), 256, 0, stream>>>(cd, 0, g.ne, g.x_e, g.n_e, v.d_z_f, s.vn);
+                                                            T.on ? T.hs : nullptr, T.bf, T.wu_c, s.rho, s.thv,
+                                                            s.ex, s.w);
+    k_init_edges<<<blocks_for(g.ne * v.ld, 256), 256, 0, stream>>>(cd, 0, g.ne, g.x_e, g.n_e, v.d_z_f, g.e2c,
+                                                                   T.on ? T.hs : nullptr, T.bf, s.vn);
     ICON_CUDA(cudaGetLastError());
     return ICON_OK;
   }
@@ -339,13 +360,14 @@ int init_state_device(icon_state* st, uint64_t seed, int case_id, const icon_cas
   }
   for (int64_t c0 = 0; c0 < g.nc; c0 += CH) {
     const int64_t n = (g.nc - c0) < CH ? (g.nc - c0) : CH;
-    k_init_cells<<<blocks_for(n, 128), 128, 0, stream>>>(cd, c0, n, g.x_c, v.d_z_f, v.d_dzh, v.d_wu, v.d_wl, rho,
-                                                         thv, ex, w);
+    k_init_cells<<<blocks_for(n, 128), 128, 0, stream>>>(cd, c0, n, g.x_c, v.d_z_f, v.d_dzh, v.d_wu, v.d_wl,
+                                                         nullptr, nullptr, nullptr, rho, thv, ex, w);
     mixed_cells_from_fp64(st, c0, n, w, rho, thv, ex, stream);
   }
   for (int64_t e0 = 0; e0 < g.ne; e0 += CH) {
     const int64_t n = (g.ne - e0) < CH ? (g.ne - e0) : CH;
-    k_init_edges<<<blocks_for(n * v.ld, 256), 256, 0, stream>>>(cd, e0, n, g.x_e, g.n_e, v.d_z_f, vn);
+    k_init_edges<<<blocks_for(n * v.ld, 256), 256, 0, stream>>>(cd, e0, n, g.x_e, g.n_e, v.d_z_f, g.e2c, nullptr,
+                                                                nullptr, vn);
     k_to_f32<<<blocks_for(n * v.ld, 256), 256, 0, stream>>>(vn, s.vn32 + e0 * v.ld, n * v.ld);
   }
   cudaError_t e = cudaGetLastError();

@@ -1,4 +1,5 @@
-// Global air mass  M = sum_c A_c sum_k dz_k rho_ck  in FP64 (both precision modes).
+// Global air mass  M = sum_c A_c sum_k dz_ck rho_ck  in FP64 (both precision modes; dz_ck
+// = dz_k on flat levels).
 //
 // Deterministic: a fixed launch shape assigns cells to warps in a fixed pattern,
 // each warp reduces a column over levels with a fixed shuffle tree, each block
@@ -17,6 +18,7 @@ constexpr int kMassThreads = 256;
 __global__ void __launch_bounds__(kMassThreads) k_mass_partial(int64_t nc, int N, int ld,
                                                                const double* __restrict__ rho,
                                                                const double* __restrict__ dz,
+                                                               const double* __restrict__ dzc,
                                                                const double* __restrict__ A_c,
                                                                double* __restrict__ part) {
   __shared__ double ws[kMassThreads / 32];
@@ -25,7 +27,11 @@ __global__ void __launch_bounds__(kMassThreads) k_mass_partial(int64_t nc, int N
   double acc = 0.0;
   for (int64_t c = (int64_t)blockIdx.x * (kMassThreads / 32) + wid; c < nc; c += nwarps) {
     double col = 0.0;
-    for (int k = lane; k < N; k += 32) col += rho[c * ld + k] * dz[k];
+    // dzc: each cell's own layer thickness on terrain-following levels
+    if (dzc)
+      for (int k = lane; k < N; k += 32) col += rho[c * ld + k] * dzc[c * ld + k];
+    else
+      for (int k = lane; k < N; k += 32) col += rho[c * ld + k] * dz[k];
     for (int o = 16; o > 0; o >>= 1) col += __shfl_xor_sync(0xffffffffu, col, o);
     acc += A_c[c] * col;
   }
@@ -85,7 +91,8 @@ void enqueue_mass(const icon_state* st, double* d_out, cudaStream_t stream) {
                                                                 grid->g.A_c, st->s.mass_part);
   else
     k_mass_partial<<<kMassBlocks, kMassThreads, 0, stream>>>(grid->g.nc, grid->vert.N, grid->vert.ld, st->s.rho,
-                                                             grid->vert.d_dz, grid->g.A_c, st->s.mass_part);
+                                                             grid->vert.d_dz, st->s.topo.on ? st->s.topo.dz_c : nullptr,
+                                                             grid->g.A_c, st->s.mass_part);
   k_mass_final<<<1, 1024, 0, stream>>>(st->s.mass_part, kMassBlocks, d_out);
   prof_end(stream);
 }

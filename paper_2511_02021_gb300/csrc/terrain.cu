@@ -1,0 +1,251 @@
+// Terrain-following height coordinate over topography (FP64 form).
+//
+// The paper's atmosphere computes on a terrain-following hybrid height coordinate
+// (Sec. "Current State of the Art") and prints none of its formulas. The levels
+// here are of SLEVE type with one decay scale s_d = 4000 m: half level h of a
+// column standing on surface height hs lies at
+//   z_h = zeta_h + hs b_h,   b_h = sinh((z_top - zeta_h)/s_d) / sinh(z_top/s_d),
+// zeta_h the flat levels, so the lowest level is the ground and the lid is flat;
+// full levels lie midway (zf = zeta_f + hs bf, bf the mean of the two b). An edge
+// is a column at the mean of its two cells' hs, a vertex one at the mean of its
+// cells'. The topography is a Gaussian mountain hs = h0 exp(-(r/a)^2), r the
+// great-circle distance to 90E 30N.
+//
+// Everything metric is separable (an entity scalar times a level profile): the
+// slope of a coordinate surface at an edge is b_h (hs_c2 - hs_c1)/d_e normal to it
+// and b_h (hs_v2 - hs_v1)/l_e along it. What the FP64-bound step kernels would
+// otherwise divide for at every cell- or edge-level (1/dz, 1/dzh, the half-level
+// interpolation weights, the reference Exner exp(-g zf/(cpd 250 K))) is tabulated
+// once here in [entity][ld] rows: the kernels have spare memory bandwidth but no
+// spare FP64 issue slots.
+//
+// Per stage, k_topo_cell forms at every cell (one warp, lanes over levels)
+//   wcc_c,h = sum_e kappa_ce b_h (vn_ie sn_e + vt_ie st_e)   (contravariant correction)
+//   d pi'/dz at full levels, pi' = pi - pi_ref: the half-level interpolants
+//            differenced over dz, one-sided at the top and bottom full levels,
+// which the edge tendency (vertical advection of vn, metric pressure gradient) and
+// the column solve (contravariant vertical fluxes, advection of w) consume.
+#include <cmath>
+#include "icon_internal.h"
+
+namespace icon {
+namespace {
+
+constexpr int kWarps = 8;
+
+// surface height of every cell: the Gaussian mountain
+__global__ void k_topo_hs(int64_t nc, const double* __restrict__ x_c, double h0, double radius, double cx, double cy,
+                          double cz, double* __restrict__ hs) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  const double x = x_c[3 * c], y = x_c[3 * c + 1], z = x_c[3 * c + 2];
+  const double px = y * cz - z * cy, py = z * cx - x * cz, pz = x * cy - y * cx;
+  const double r = kR * atan2(sqrt((px * px + py * py) + pz * pz), (x * cx + y * cy) + z * cz);
+  const double q = r / radius;
+  hs[c] = h0 * exp(-(q * q));
+}
+
+struct LevelArgs {
+  int N, ld;
+  const double *dz, *dzh, *z_f, *b, *bf;      // flat profiles and the decay, [ld]
+};
+
+// one thread per (cell, level slot): the cell tables
+__global__ void k_topo_cells(LevelArgs L, int64_t nc, const double* __restrict__ hs, double* __restrict__ inv_dz,
+                             double* __restrict__ inv_dzh, double* __restrict__ wu, double* __restrict__ exref,
+                             double* __restrict__ dzc) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nc * L.ld) return;
+  const int64_t c = t / L.ld;
+  const int k = (int)(t % L.ld);
+  const double h = hs[c];
+  double idz = 0.0, idzh = 0.0, w = 0.0, er = 0.0, d = 0.0;
+  if (k < L.N) {
+    d = L.dz[k] + h * (L.b[k] - L.b[k + 1]);
+    idz = 1.0 / d;
+    const double zf = L.z_f[k] + h * L.bf[k];
+    er = exp(-kGrav * zf / (kCpd * kTopoTref));
+  }
+  if (k >= 1 && k < L.N) {
+    idzh = 1.0 / (L.dzh[k] + h * (L.bf[k - 1] - L.bf[k]));
+    const double dm = L.dz[k - 1] + h * (L.b[k - 1] - L.b[k]);
+    w = d / (dm + d);
+  }
+  inv_dz[t] = idz;
+  inv_dzh[t] = idzh;
+  wu[t] = w;
+  exref[t] = er;
+  dzc[t] = d;
+}
+
+// mean surface height of the cells around vertex v (the O5 vertex mean)
+__device__ inline double vertex_hs(int64_t v, const int* __restrict__ v2c, const int* __restrict__ vdeg,
+                                   const double* __restrict__ hs) {
+  double acc = 0.0;
+  for (int j = 0; j < 5; ++j) acc += hs[v2c[6 * v + j]];
+  const int deg = vdeg[v];
+  acc += deg == 6 ? hs[v2c[6 * v + 5]] : 0.0;
+  return acc / (double)deg;
+}
+
+// one thread per (edge, level slot): the edge tables and, at slot 0, the two slopes
+__global__ void k_topo_edges(LevelArgs L, int64_t ne, const int* __restrict__ e2c, const int* __restrict__ e2v,
+                             const int* __restrict__ v2c, const int* __restrict__ vdeg,
+                             const double* __restrict__ d_e, const double* __restrict__ l_e,
+                             const double* __restrict__ hs, double* __restrict__ wu, double* __restrict__ inv_dz,
+                             double* __restrict__ dze, double* __restrict__ sn, double* __restrict__ st) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= ne * L.ld) return;
+  const int64_t e = t / L.ld;
+  const int k = (int)(t % L.ld);
+  const double h1 = hs[e2c[2 * e]], h2 = hs[e2c[2 * e + 1]];
+  const double h = 0.5 * (h1 + h2);
+  double idz = 0.0, w = 0.0, d = 0.0;
+  if (k < L.N) {
+    d = L.dz[k] + h * (L.b[k] - L.b[k + 1]);
+    idz = 1.0 / d;
+  }
+  if (k >= 1 && k < L.N) {
+    const double dm = L.dz[k - 1] + h * (L.b[k - 1] - L.b[k]);
+    w = d / (dm + d);
+  }
+  wu[t] = w;
+  inv_dz[t] = idz;
+  dze[t] = d;
+  if (k == 0) {
+    sn[e] = (h2 - h1) / d_e[e];
+    const double hv1 = vertex_hs(e2v[2 * e], v2c, vdeg, hs), hv2 = vertex_hs(e2v[2 * e + 1], v2c, vdeg, hs);
+    st[e] = (hv2 - hv1) / l_e[e];
+  }
+}
+
+struct StageArgs {
+  int64_t nc;
+  int N, ld;
+  const int* c2e;
+  const double* kin_w;
+  const double *vn, *vt, *ex;                 // stage state and its tangential velocity
+  const double *b, *sn, *st, *wu_e;
+  const double *wu_c, *inv_dz_c, *inv_dzh_c, *exref_c;
+  double *wcc, *dpdz;
+};
+
+// one warp per cell, lanes over levels: the stage's contravariant correction at half
+// levels and the vertical derivative of the Exner perturbation at full levels
+__global__ void __launch_bounds__(256, 4) k_topo_cell(StageArgs a) {
+  const int64_t c = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  if (c >= a.nc) return;
+  const int lane = threadIdx.x & 31, ld = a.ld, N = a.N;
+  const int64_t o = c * ld;
+  int64_t E[3];
+  double kw[3], sn[3], st[3];
+  for (int s = 0; s < 3; ++s) {
+    const int e = a.c2e[3 * c + s];
+    E[s] = (int64_t)e * ld;
+    kw[s] = a.kin_w[3 * c + s];
+    sn[s] = a.sn[e];
+    st[s] = a.st[e];
+  }
+  for (int h = lane; h <= N; h += 32) {
+    double acc = 0.0;
+    if (h > 0) {
+      const double bh = a.b[h];
+      for (int s = 0; s < 3; ++s) {
+        double vie, tie;
+        if (h >= N) {
+          vie = a.vn[E[s] + N - 1];
+          tie = a.vt[E[s] + N - 1];
+        } else {
+          const double wu = a.wu_e[E[s] + h];
+          vie = wu * a.vn[E[s] + h - 1] + (1.0 - wu) * a.vn[E[s] + h];
+          tie = wu * a.vt[E[s] + h - 1] + (1.0 - wu) * a.vt[E[s] + h];
+        }
+        acc += kw[s] * (vie * (sn[s] * bh) + tie * (st[s] * bh));
+      }
+    }
+    a.wcc[o + h] = acc;
+  }
+  for (int k = lane; k < N; k += 32) {
+    const double* ex = a.ex + o;
+    const double* er = a.exref_c + o;
+    double d;
+    if (k == 0) {
+      d = ((ex[0] - er[0]) - (ex[1] - er[1])) * a.inv_dzh_c[o + 1];
+    } else if (k == N - 1) {
+      d = ((ex[N - 2] - er[N - 2]) - (ex[N - 1] - er[N - 1])) * a.inv_dzh_c[o + N - 1];
+    } else {
+      const double pm = ex[k - 1] - er[k - 1], p0 = ex[k] - er[k], pp = ex[k + 1] - er[k + 1];
+      const double wa = a.wu_c[o + k], wb = a.wu_c[o + k + 1];
+      const double fa = wa * pm + (1.0 - wa) * p0;
+      const double fb = wb * p0 + (1.0 - wb) * pp;
+      d = (fa - fb) * a.inv_dz_c[o + k];
+    }
+    a.dpdz[o + k] = d;
+  }
+}
+
+}  // namespace
+
+int topo_build(icon_state* st, double h0, double radius, cudaStream_t stream) {
+  const icon_grid* grid = st->grid;
+  const GridDev& g = grid->g;
+  const Vertical& v = grid->vert;
+  TopoDev& T = st->s.topo;
+  DeviceArena& A = st->arena;
+  const size_t C = (size_t)(g.nc * v.ld), E = (size_t)(g.ne * v.ld);
+  T.h0 = h0;
+  T.radius = radius;
+  T.hs = A.get_n<double>(g.nc);
+  T.b = A.get_n<double>(v.ld);
+  T.bf = A.get_n<double>(v.ld);
+  T.sn = A.get_n<double>(g.ne);
+  T.st = A.get_n<double>(g.ne);
+  double** cells[] = {&T.inv_dz_c, &T.inv_dzh_c, &T.wu_c, &T.exref_c, &T.dz_c, &T.wcc, &T.dpdz};
+  for (double** p : cells) *p = A.get_n<double>(C);
+  double** edges[] = {&T.wu_e, &T.inv_dz_e, &T.dz_e};
+  for (double** p : edges) *p = A.get_n<double>(E);
+  if (A.failed) {
+    set_error("out of device memory for the terrain-following metric tables");
+    return ICON_ENOMEM;
+  }
+  // decay profile on the host (per level, once)
+  std::vector<double> b(v.ld, 0.0), bf(v.ld, 0.0);
+  const double den = std::sinh(v.z_top / kTopoDecay);
+  for (int h = 0; h <= v.N; ++h) b[h] = std::sinh((v.z_top - v.z_h[h]) / kTopoDecay) / den;
+  for (int k = 0; k < v.N; ++k) bf[k] = 0.5 * (b[k] + b[k + 1]);
+  ICON_CUDA(cudaMemcpyAsync(T.b, b.data(), sizeof(double) * v.ld, cudaMemcpyHostToDevice, stream));
+  ICON_CUDA(cudaMemcpyAsync(T.bf, bf.data(), sizeof(double) * v.ld, cudaMemcpyHostToDevice, stream));
+  const double pi = 3.141592653589793, lon = 90.0 * pi / 180.0, lat = 30.0 * pi / 180.0;
+  k_topo_hs<<<blocks_for(g.nc, 256), 256, 0, stream>>>(g.nc, g.x_c, h0, radius, std::cos(lat) * std::cos(lon),
+                                                       std::cos(lat) * std::sin(lon), std::sin(lat), T.hs);
+  LevelArgs L;
+  L.N = v.N; L.ld = v.ld; L.dz = v.d_dz; L.dzh = v.d_dzh; L.z_f = v.d_z_f; L.b = T.b; L.bf = T.bf;
+  k_topo_cells<<<blocks_for(g.nc * v.ld, 256), 256, 0, stream>>>(L, g.nc, T.hs, T.inv_dz_c, T.inv_dzh_c, T.wu_c,
+                                                                 T.exref_c, T.dz_c);
+  k_topo_edges<<<blocks_for(g.ne * v.ld, 256), 256, 0, stream>>>(L, g.ne, g.e2c, g.e2v, g.v2c, g.vdeg, g.d_e, g.l_e,
+                                                                 T.hs, T.wu_e, T.inv_dz_e, T.dz_e, T.sn, T.st);
+  ICON_CUDA(cudaGetLastError());
+  ICON_CUDA(cudaMemsetAsync(T.wcc, 0, sizeof(double) * C, stream));
+  ICON_CUDA(cudaMemsetAsync(T.dpdz, 0, sizeof(double) * C, stream));
+  T.on = true;
+  return ICON_OK;
+}
+
+void topo_stage(icon_state* st, const double* vn, const double* vt, const double* ex, cudaStream_t stream) {
+  const icon_grid* grid = st->grid;
+  const GridDev& g = grid->g;
+  const Vertical& v = grid->vert;
+  const TopoDev& T = st->s.topo;
+  StageArgs a;
+  a.nc = g.nc; a.N = v.N; a.ld = v.ld;
+  a.c2e = g.c2e; a.kin_w = g.kin_w;
+  a.vn = vn; a.vt = vt; a.ex = ex;
+  a.b = T.b; a.sn = T.sn; a.st = T.st; a.wu_e = T.wu_e;
+  a.wu_c = T.wu_c; a.inv_dz_c = T.inv_dz_c; a.inv_dzh_c = T.inv_dzh_c; a.exref_c = T.exref_c;
+  a.wcc = T.wcc; a.dpdz = T.dpdz;
+  prof_begin(stream, K_TERRAIN);
+  k_topo_cell<<<blocks_for(g.nc, kWarps), 256, 0, stream>>>(a);
+  prof_end(stream);
+}
+
+}  // namespace icon
