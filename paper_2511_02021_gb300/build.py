@@ -28,7 +28,7 @@ SOURCES = {
     "mass.cu": ["-fmad=false"],
     "dycore32.cu": [],
     "tracer.cu": [],
-    "terrain.cu": ["-fmad=false"],
+    "terrain.cu": [],
 }
 
 

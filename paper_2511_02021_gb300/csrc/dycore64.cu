@@ -56,10 +56,11 @@ struct Geo64 {
   const double *wu, *wl, *inv_dz, *inv_dz2, *qinv_dz;
   const double* cc;                        // per-level constants for the current dtau
   // terrain-following levels (the TOPO kernel variants; see terrain.cu): per-edge normal
-  // slope factor, full-level decay, per-entity tables [entity][ld], the stage's
-  // contravariant correction and Exner-perturbation derivative
-  const double *t_sn, *t_bf, *t_wu_e, *t_inv_dz_e, *t_dz_e;
-  const double *t_wu_c, *t_inv_dz_c, *t_inv_dzh_c, *t_exref_c, *t_wcc, *t_dpdz;
+  // slope factor, full-level decay, per-entity tables [entity][ld], and the stage's
+  // contravariant correction, contravariant velocity, Exner perturbation and half its
+  // vertical derivative
+  const double *t_sn, *t_bf, *t_wu_e, *t_qinv_dz_e, *t_dz_e;
+  const double *t_wu_c, *t_inv_dz_c, *t_inv_dzh_c, *t_wcc, *t_wcon, *t_ep, *t_hdpdz;
 };
 
 // per-level constants of the column solve for one dtau, [8][ld] (same layout as the
@@ -186,7 +187,8 @@ struct EdgeArgs {
 // vertical velocity w - wcc (zero at lid and ground) in the vertical advection of vn,
 // the metric correction of the pressure gradient on pi' = pi - pi_ref,
 //   (pi'_c2 - pi'_c1)/d_e - sn_e bf_k (d pi'/dz at c1 and c2)/2,
-// and mass fluxes through layers of thickness dz_e.
+// and mass fluxes through layers of thickness dz_e; w - wcc, pi' and d pi'/dz come from
+// the stage's k_topo_cell.
 template <bool TOPO>
 __global__ void __launch_bounds__(256, 4) k_edge_tend(Geo64 G, EdgeArgs a) {
   const int64_t e = warp_entity();
@@ -197,7 +199,7 @@ __global__ void __launch_bounds__(256, 4) k_edge_tend(Geo64 G, EdgeArgs a) {
   const int64_t eo = e * ld;
   const double ide = G.inv_de[e], ile = G.inv_le[e], fe = G.f_e[e];
   const double cide = kCpd * ide;
-  const double sne = TOPO ? G.t_sn[e] : 0.0;
+  const double csne = TOPO ? kCpd * G.t_sn[e] : 0.0;
   const double* __restrict__ vn = a.vn + eo;
   const double* __restrict__ vt = a.vt + eo;
   const double dtau = a.dtau;
@@ -222,7 +224,7 @@ __global__ void __launch_bounds__(256, 4) k_edge_tend(Geo64 G, EdgeArgs a) {
       tie = wa * vt[hl] + wb * vt[hu];
       const double w1 = a.w[c1 + h], w2 = a.w[c2 + h];
       if (TOPO)
-        sw = (h > 0 && h < N) ? (w1 - G.t_wcc[c1 + h]) + (w2 - G.t_wcc[c2 + h]) : 0.0;
+        sw = G.t_wcon[c1 + h] + G.t_wcon[c2 + h];        // 0 at the lid and the ground
       else
         sw = w1 + w2;
       dw = w2 - w1;
@@ -238,14 +240,13 @@ __global__ void __launch_bounds__(256, 4) k_edge_tend(Geo64 G, EdgeArgs a) {
       const double zs = a.zeta[v1 + k] + a.zeta[v2 + k];
       const double dK = a.Kc[c2 + k] - a.Kc[c1 + k];
       const double T = fma(-dK, ide, fma(0.5, zs, fe) * vt[k]);
-      const double A = fma(-((sw + sw_up) * (vie - vie_up)), TOPO ? 0.25 * G.t_inv_dz_e[eo + k] : G.qinv_dz[k], T);
+      const double A = fma(-((sw + sw_up) * (vie - vie_up)), TOPO ? G.t_qinv_dz_e[eo + k] : G.qinv_dz[k], T);
       const double t1 = a.thv[c1 + k], t2 = a.thv[c2 + k];
       const double th_e = 0.5 * (t1 + t2);
       double pg;
       if (TOPO) {
-        const double ep1 = a.ex[c1 + k] - G.t_exref_c[c1 + k], ep2 = a.ex[c2 + k] - G.t_exref_c[c2 + k];
-        const double corr = (sne * G.t_bf[k]) * (0.5 * (G.t_dpdz[c1 + k] + G.t_dpdz[c2 + k]));
-        pg = th_e * (kCpd * ((ep2 - ep1) * ide - corr));
+        const double corr = (csne * G.t_bf[k]) * (G.t_hdpdz[c1 + k] + G.t_hdpdz[c2 + k]);
+        pg = th_e * fma(G.t_ep[c2 + k] - G.t_ep[c1 + k], cide, -corr);
       } else {
         pg = th_e * ((a.ex[c2 + k] - a.ex[c1 + k]) * cide);
       }
@@ -455,8 +456,7 @@ __global__ void __launch_bounds__(256, 4) k_col_rows(Geo64 G, ColArgs a) {
       const double ws = a.w_stage[o + h];
       double Aw;
       if constexpr (TOPO)
-        Aw = -hadv - (ws - G.t_wcc[o + h]) * (a.w_stage[o + h - 1] - a.w_stage[o + h + 1]) *
-                         (0.5 * G.t_inv_dzh_c[o + h]);
+        Aw = -hadv - G.t_wcon[o + h] * (a.w_stage[o + h - 1] - a.w_stage[o + h + 1]) * (0.5 * G.t_inv_dzh_c[o + h]);
       else
         Aw = -hadv - ws * (a.w_stage[o + h - 1] - a.w_stage[o + h + 1]) * G.inv_dz2[h];
       if (a.corrector) Aw = 0.5 * (a.Aw0[o + h] + Aw);
@@ -720,8 +720,8 @@ Geo64 make_geo(const icon_grid* grid, const double* cc) {
   G.inv_L34 = g.inv_L34; G.n_e = g.n_e; G.t_e = g.t_e; G.s_ce = g.s_ce;
   G.wu = v.d_wu; G.wl = v.d_wl; G.inv_dz = v.d_inv_dz; G.inv_dz2 = v.d_inv_dz2; G.qinv_dz = v.d_qinv_dz;
   G.cc = cc;
-  G.t_sn = G.t_bf = G.t_wu_e = G.t_inv_dz_e = G.t_dz_e = nullptr;
-  G.t_wu_c = G.t_inv_dz_c = G.t_inv_dzh_c = G.t_exref_c = G.t_wcc = G.t_dpdz = nullptr;
+  G.t_sn = G.t_bf = G.t_wu_e = G.t_qinv_dz_e = G.t_dz_e = nullptr;
+  G.t_wu_c = G.t_inv_dz_c = G.t_inv_dzh_c = G.t_wcc = G.t_wcon = G.t_ep = G.t_hdpdz = nullptr;
   return G;
 }
 
@@ -743,9 +743,9 @@ void enqueue_step_fp64(icon_state* st, double dt, int nsub, cudaStream_t stream)
   const TopoDev& T = s.topo;
   const bool topo = T.on;
   if (topo) {
-    G.t_sn = T.sn; G.t_bf = T.bf; G.t_wu_e = T.wu_e; G.t_inv_dz_e = T.inv_dz_e; G.t_dz_e = T.dz_e;
-    G.t_wu_c = T.wu_c; G.t_inv_dz_c = T.inv_dz_c; G.t_inv_dzh_c = T.inv_dzh_c; G.t_exref_c = T.exref_c;
-    G.t_wcc = T.wcc; G.t_dpdz = T.dpdz;
+    G.t_sn = T.sn; G.t_bf = T.bf; G.t_wu_e = T.wu_e; G.t_qinv_dz_e = T.qinv_dz_e; G.t_dz_e = T.dz_e;
+    G.t_wu_c = T.wu_c; G.t_inv_dz_c = T.inv_dz_c; G.t_inv_dzh_c = T.inv_dzh_c;
+    G.t_wcc = T.wcc; G.t_wcon = T.wcon; G.t_ep = T.ep; G.t_hdpdz = T.hdpdz;
   }
   const int ld = G.ld;
   const double dtau = dt / nsub;
@@ -772,7 +772,7 @@ void enqueue_step_fp64(icon_state* st, double dt, int nsub, cudaStream_t stream)
       prof_begin(stream, K_CELL_KE);
       k_cell_ke<<<nbc, 256, 0, stream>>>(G, s.Ke, s.Kc);
       prof_end(stream);
-      if (topo) topo_stage(st, vn_st, s.vt, ex_st, stream);
+      if (topo) topo_stage(st, vn_st, s.vt, w_st, ex_st, stream);
       EdgeArgs ea;
       ea.vn = vn_st; ea.w = w_st; ea.rho = rho_st; ea.thv = thv_st; ea.ex = ex_st;
       ea.vt = s.vt; ea.Kc = s.Kc; ea.zeta = s.zeta; ea.w_v = s.w_v;

@@ -134,10 +134,12 @@ struct TopoDev {
   // per cell and level [Nc][ld]: 1/dz, 1/dzh (interior half levels), upper interpolation
   // weight (interior half levels), reference Exner at the full level, dz
   double *inv_dz_c = nullptr, *inv_dzh_c = nullptr, *wu_c = nullptr, *exref_c = nullptr, *dz_c = nullptr;
-  // per edge and level [Ne][ld]: upper interpolation weight, 1/dz, dz
-  double *wu_e = nullptr, *inv_dz_e = nullptr, *dz_e = nullptr;
-  // per stage [Nc][ld]: contravariant correction at half levels, d pi'/dz at full levels
-  double *wcc = nullptr, *dpdz = nullptr;
+  // per edge and level [Ne][ld]: upper interpolation weight, 1/(4 dz), dz
+  double *wu_e = nullptr, *qinv_dz_e = nullptr, *dz_e = nullptr;
+  // per stage [Nc][ld]: contravariant correction wcc and velocity w - wcc (0 at lid and
+  // ground) at half levels; Exner perturbation pi - pi_ref and half its vertical
+  // derivative at full levels
+  double *wcc = nullptr, *wcon = nullptr, *ep = nullptr, *hdpdz = nullptr;
 };
 
 struct StateDev {
@@ -241,7 +243,8 @@ int build_tracer_tables(icon_grid* grid, cudaStream_t st);
 constexpr double kTopoDecay = 4000.0;   // SLEVE decay scale, m
 constexpr double kTopoTref = 250.0;     // temperature of the reference Exner profile, K
 int topo_build(icon_state* st, double h0, double radius, cudaStream_t stream);
-void topo_stage(icon_state* st, const double* vn, const double* vt, const double* ex, cudaStream_t stream);
+void topo_stage(icon_state* st, const double* vn, const double* vt, const double* w, const double* ex,
+                cudaStream_t stream);
 // tracer.cu
 int tracer_alloc(icon_state* st, int ntracers);
 void tracer_begin(icon_state* st, cudaStream_t stream);

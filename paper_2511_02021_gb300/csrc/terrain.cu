@@ -20,11 +20,13 @@
 // spare FP64 issue slots.
 //
 // Per stage, k_topo_cell forms at every cell (one warp, lanes over levels)
-//   wcc_c,h = sum_e kappa_ce b_h (vn_ie sn_e + vt_ie st_e)   (contravariant correction)
-//   d pi'/dz at full levels, pi' = pi - pi_ref: the half-level interpolants
-//            differenced over dz, one-sided at the top and bottom full levels,
+//   wcc_c,h = b_h sum_e (kappa_ce sn_e vn_ie + kappa_ce st_e vt_ie)   (contravariant correction)
+//   w - wcc at interior half levels (0 at the lid and the ground),
+//   pi' = pi - pi_ref and half of d pi'/dz at full levels (the half-level interpolants
+//            differenced over dz, one-sided at the top and bottom full levels),
 // which the edge tendency (vertical advection of vn, metric pressure gradient) and
-// the column solve (contravariant vertical fluxes, advection of w) consume.
+// the column solve (contravariant vertical fluxes, advection of w) consume, so that
+// those FP64-bound kernels load these terms instead of forming them per edge.
 #include <cmath>
 #include "icon_internal.h"
 
@@ -33,14 +35,18 @@ namespace {
 
 constexpr int kWarps = 8;
 
+// The tables are formed with explicitly rounded products (__dmul_rn is never fused into
+// a multiply-add), the same arithmetic as a plain evaluation of the formulas.
+#define MUL __dmul_rn
+
 // surface height of every cell: the Gaussian mountain
 __global__ void k_topo_hs(int64_t nc, const double* __restrict__ x_c, double h0, double radius, double cx, double cy,
                           double cz, double* __restrict__ hs) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= nc) return;
   const double x = x_c[3 * c], y = x_c[3 * c + 1], z = x_c[3 * c + 2];
-  const double px = y * cz - z * cy, py = z * cx - x * cz, pz = x * cy - y * cx;
-  const double r = kR * atan2(sqrt((px * px + py * py) + pz * pz), (x * cx + y * cy) + z * cz);
+  const double px = MUL(y, cz) - MUL(z, cy), py = MUL(z, cx) - MUL(x, cz), pz = MUL(x, cy) - MUL(y, cx);
+  const double r = kR * atan2(sqrt((MUL(px, px) + MUL(py, py)) + MUL(pz, pz)), (MUL(x, cx) + MUL(y, cy)) + MUL(z, cz));
   const double q = r / radius;
   hs[c] = h0 * exp(-(q * q));
 }
@@ -61,14 +67,14 @@ __global__ void k_topo_cells(LevelArgs L, int64_t nc, const double* __restrict__
   const double h = hs[c];
   double idz = 0.0, idzh = 0.0, w = 0.0, er = 0.0, d = 0.0;
   if (k < L.N) {
-    d = L.dz[k] + h * (L.b[k] - L.b[k + 1]);
+    d = L.dz[k] + MUL(h, L.b[k] - L.b[k + 1]);
     idz = 1.0 / d;
-    const double zf = L.z_f[k] + h * L.bf[k];
+    const double zf = L.z_f[k] + MUL(h, L.bf[k]);
     er = exp(-kGrav * zf / (kCpd * kTopoTref));
   }
   if (k >= 1 && k < L.N) {
-    idzh = 1.0 / (L.dzh[k] + h * (L.bf[k - 1] - L.bf[k]));
-    const double dm = L.dz[k - 1] + h * (L.b[k - 1] - L.b[k]);
+    idzh = 1.0 / (L.dzh[k] + MUL(h, L.bf[k - 1] - L.bf[k]));
+    const double dm = L.dz[k - 1] + MUL(h, L.b[k - 1] - L.b[k]);
     w = d / (dm + d);
   }
   inv_dz[t] = idz;
@@ -92,7 +98,7 @@ __device__ inline double vertex_hs(int64_t v, const int* __restrict__ v2c, const
 __global__ void k_topo_edges(LevelArgs L, int64_t ne, const int* __restrict__ e2c, const int* __restrict__ e2v,
                              const int* __restrict__ v2c, const int* __restrict__ vdeg,
                              const double* __restrict__ d_e, const double* __restrict__ l_e,
-                             const double* __restrict__ hs, double* __restrict__ wu, double* __restrict__ inv_dz,
+                             const double* __restrict__ hs, double* __restrict__ wu, double* __restrict__ qinv_dz,
                              double* __restrict__ dze, double* __restrict__ sn, double* __restrict__ st) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= ne * L.ld) return;
@@ -100,17 +106,17 @@ __global__ void k_topo_edges(LevelArgs L, int64_t ne, const int* __restrict__ e2
   const int k = (int)(t % L.ld);
   const double h1 = hs[e2c[2 * e]], h2 = hs[e2c[2 * e + 1]];
   const double h = 0.5 * (h1 + h2);
-  double idz = 0.0, w = 0.0, d = 0.0;
+  double qidz = 0.0, w = 0.0, d = 0.0;
   if (k < L.N) {
-    d = L.dz[k] + h * (L.b[k] - L.b[k + 1]);
-    idz = 1.0 / d;
+    d = L.dz[k] + MUL(h, L.b[k] - L.b[k + 1]);
+    qidz = 0.25 / d;
   }
   if (k >= 1 && k < L.N) {
-    const double dm = L.dz[k - 1] + h * (L.b[k - 1] - L.b[k]);
+    const double dm = L.dz[k - 1] + MUL(h, L.b[k - 1] - L.b[k]);
     w = d / (dm + d);
   }
   wu[t] = w;
-  inv_dz[t] = idz;
+  qinv_dz[t] = qidz;
   dze[t] = d;
   if (k == 0) {
     sn[e] = (h2 - h1) / d_e[e];
@@ -124,32 +130,34 @@ struct StageArgs {
   int N, ld;
   const int* c2e;
   const double* kin_w;
-  const double *vn, *vt, *ex;                 // stage state and its tangential velocity
+  const double *vn, *vt, *w, *ex;             // stage state and its tangential velocity
   const double *b, *sn, *st, *wu_e;
   const double *wu_c, *inv_dz_c, *inv_dzh_c, *exref_c;
-  double *wcc, *dpdz;
+  double *wcc, *wcon, *ep, *hdpdz;
 };
 
-// one warp per cell, lanes over levels: the stage's contravariant correction at half
-// levels and the vertical derivative of the Exner perturbation at full levels
+// one warp per cell, lanes over levels: the stage's contravariant correction and
+// contravariant velocity at half levels, the Exner perturbation and half its vertical
+// derivative at full levels. FP64-pipe bound like the step's stencils: the kappa and
+// slope factors of the three edges are combined once per cell, and each half-level
+// interpolant is one subtraction and one fused multiply-add.
 __global__ void __launch_bounds__(256, 4) k_topo_cell(StageArgs a) {
   const int64_t c = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
   if (c >= a.nc) return;
   const int lane = threadIdx.x & 31, ld = a.ld, N = a.N;
   const int64_t o = c * ld;
   int64_t E[3];
-  double kw[3], sn[3], st[3];
+  double An[3], At[3];
   for (int s = 0; s < 3; ++s) {
     const int e = a.c2e[3 * c + s];
     E[s] = (int64_t)e * ld;
-    kw[s] = a.kin_w[3 * c + s];
-    sn[s] = a.sn[e];
-    st[s] = a.st[e];
+    const double kw = a.kin_w[3 * c + s];
+    An[s] = kw * a.sn[e];
+    At[s] = kw * a.st[e];
   }
   for (int h = lane; h <= N; h += 32) {
     double acc = 0.0;
     if (h > 0) {
-      const double bh = a.b[h];
       for (int s = 0; s < 3; ++s) {
         double vie, tie;
         if (h >= N) {
@@ -157,30 +165,35 @@ __global__ void __launch_bounds__(256, 4) k_topo_cell(StageArgs a) {
           tie = a.vt[E[s] + N - 1];
         } else {
           const double wu = a.wu_e[E[s] + h];
-          vie = wu * a.vn[E[s] + h - 1] + (1.0 - wu) * a.vn[E[s] + h];
-          tie = wu * a.vt[E[s] + h - 1] + (1.0 - wu) * a.vt[E[s] + h];
+          const double v0 = a.vn[E[s] + h], t0 = a.vt[E[s] + h];
+          vie = fma(wu, a.vn[E[s] + h - 1] - v0, v0);
+          tie = fma(wu, a.vt[E[s] + h - 1] - t0, t0);
         }
-        acc += kw[s] * (vie * (sn[s] * bh) + tie * (st[s] * bh));
+        acc = fma(An[s], vie, acc);
+        acc = fma(At[s], tie, acc);
       }
+      acc *= a.b[h];
     }
     a.wcc[o + h] = acc;
+    a.wcon[o + h] = (h > 0 && h < N) ? a.w[o + h] - acc : 0.0;
   }
   for (int k = lane; k < N; k += 32) {
     const double* ex = a.ex + o;
     const double* er = a.exref_c + o;
+    const double p0 = ex[k] - er[k];
     double d;
     if (k == 0) {
-      d = ((ex[0] - er[0]) - (ex[1] - er[1])) * a.inv_dzh_c[o + 1];
+      d = (p0 - (ex[1] - er[1])) * a.inv_dzh_c[o + 1];
     } else if (k == N - 1) {
-      d = ((ex[N - 2] - er[N - 2]) - (ex[N - 1] - er[N - 1])) * a.inv_dzh_c[o + N - 1];
+      d = ((ex[N - 2] - er[N - 2]) - p0) * a.inv_dzh_c[o + N - 1];
     } else {
-      const double pm = ex[k - 1] - er[k - 1], p0 = ex[k] - er[k], pp = ex[k + 1] - er[k + 1];
-      const double wa = a.wu_c[o + k], wb = a.wu_c[o + k + 1];
-      const double fa = wa * pm + (1.0 - wa) * p0;
-      const double fb = wb * p0 + (1.0 - wb) * pp;
+      const double pm = ex[k - 1] - er[k - 1], pp = ex[k + 1] - er[k + 1];
+      const double fa = fma(a.wu_c[o + k], pm - p0, p0);
+      const double fb = fma(a.wu_c[o + k + 1], p0 - pp, pp);
       d = (fa - fb) * a.inv_dz_c[o + k];
     }
-    a.dpdz[o + k] = d;
+    a.ep[o + k] = p0;
+    a.hdpdz[o + k] = 0.5 * d;
   }
 }
 
@@ -200,9 +213,9 @@ int topo_build(icon_state* st, double h0, double radius, cudaStream_t stream) {
   T.bf = A.get_n<double>(v.ld);
   T.sn = A.get_n<double>(g.ne);
   T.st = A.get_n<double>(g.ne);
-  double** cells[] = {&T.inv_dz_c, &T.inv_dzh_c, &T.wu_c, &T.exref_c, &T.dz_c, &T.wcc, &T.dpdz};
+  double** cells[] = {&T.inv_dz_c, &T.inv_dzh_c, &T.wu_c, &T.exref_c, &T.dz_c, &T.wcc, &T.wcon, &T.ep, &T.hdpdz};
   for (double** p : cells) *p = A.get_n<double>(C);
-  double** edges[] = {&T.wu_e, &T.inv_dz_e, &T.dz_e};
+  double** edges[] = {&T.wu_e, &T.qinv_dz_e, &T.dz_e};
   for (double** p : edges) *p = A.get_n<double>(E);
   if (A.failed) {
     set_error("out of device memory for the terrain-following metric tables");
@@ -223,15 +236,15 @@ int topo_build(icon_state* st, double h0, double radius, cudaStream_t stream) {
   k_topo_cells<<<blocks_for(g.nc * v.ld, 256), 256, 0, stream>>>(L, g.nc, T.hs, T.inv_dz_c, T.inv_dzh_c, T.wu_c,
                                                                  T.exref_c, T.dz_c);
   k_topo_edges<<<blocks_for(g.ne * v.ld, 256), 256, 0, stream>>>(L, g.ne, g.e2c, g.e2v, g.v2c, g.vdeg, g.d_e, g.l_e,
-                                                                 T.hs, T.wu_e, T.inv_dz_e, T.dz_e, T.sn, T.st);
+                                                                 T.hs, T.wu_e, T.qinv_dz_e, T.dz_e, T.sn, T.st);
   ICON_CUDA(cudaGetLastError());
-  ICON_CUDA(cudaMemsetAsync(T.wcc, 0, sizeof(double) * C, stream));
-  ICON_CUDA(cudaMemsetAsync(T.dpdz, 0, sizeof(double) * C, stream));
+  for (double* p : {T.wcc, T.wcon, T.ep, T.hdpdz}) ICON_CUDA(cudaMemsetAsync(p, 0, sizeof(double) * C, stream));
   T.on = true;
   return ICON_OK;
 }
 
-void topo_stage(icon_state* st, const double* vn, const double* vt, const double* ex, cudaStream_t stream) {
+void topo_stage(icon_state* st, const double* vn, const double* vt, const double* w, const double* ex,
+                cudaStream_t stream) {
   const icon_grid* grid = st->grid;
   const GridDev& g = grid->g;
   const Vertical& v = grid->vert;
@@ -239,10 +252,10 @@ void topo_stage(icon_state* st, const double* vn, const double* vt, const double
   StageArgs a;
   a.nc = g.nc; a.N = v.N; a.ld = v.ld;
   a.c2e = g.c2e; a.kin_w = g.kin_w;
-  a.vn = vn; a.vt = vt; a.ex = ex;
+  a.vn = vn; a.vt = vt; a.w = w; a.ex = ex;
   a.b = T.b; a.sn = T.sn; a.st = T.st; a.wu_e = T.wu_e;
   a.wu_c = T.wu_c; a.inv_dz_c = T.inv_dz_c; a.inv_dzh_c = T.inv_dzh_c; a.exref_c = T.exref_c;
-  a.wcc = T.wcc; a.dpdz = T.dpdz;
+  a.wcc = T.wcc; a.wcon = T.wcon; a.ep = T.ep; a.hdpdz = T.hdpdz;
   prof_begin(stream, K_TERRAIN);
   k_topo_cell<<<blocks_for(g.nc, kWarps), 256, 0, stream>>>(a);
   prof_end(stream);
