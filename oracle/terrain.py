@@ -26,13 +26,15 @@ R-Z3 Horizontal derivatives run along the coordinate surfaces; only the pressure
      (pi'_0 - pi'_1)/dzh_1, (pi'_{N-2} - pi'_{N-1})/dzh_{N-1} at the top and
      bottom full levels. Kinetic-energy gradient, vorticity and the horizontal
      advection of w take none (as ICON does).
-R-Z4 Contravariant vertical velocity w_con = w - wcc, with the correction at
-     edges wcc_e,h = vn_ie sn_e,h + vt_ie st_e,h (half-level slopes: sn from the
-     two cells, st = (z_v2,h - z_v1,h)/l_e from the two vertices) and at cells
-     wcc_c = sum_e kappa_ce wcc_e (the O5 weights). w_con replaces w in the
-     vertical advection of vn and w and in the vertical mass and heat fluxes;
-     w_con = 0 at the lid and at the ground (free slip: the w a column leaves at
-     the ground is its stage's wcc).
+R-Z4 Contravariant vertical velocity w_con = w - wcc, with the correction formed
+     in ICON's order: at edges and full levels X_e,k = vn sn_e,k + vt st_e,k
+     (full-level slopes: sn from the two cells, st = (zf_v2,k - zf_v1,k)/l_e from
+     the two vertices), at cells X_c = sum_e kappa_ce X_e (the O5 weights), then
+     interpolated to the interior half levels with the cell's own weights; at the
+     ground wcc = sum_e kappa_ce (vn sn + vt st) with the lowest full level's wind
+     and the surface slopes. w_con replaces w in the vertical advection of vn and
+     w and in the vertical mass and heat fluxes; w_con = 0 at the lid and at the
+     ground (free slip: the w a column leaves at the ground is its stage's wcc).
 R-Z5 Flux form with layer thickness: the horizontal mass and heat fluxes carry
      dz_e (rho_e vn dz_e), each cell's budget is divided by its dz_c, and the
      vertical implicit solve is R-S's with each cell's own spacings. The
@@ -103,9 +105,9 @@ def terrain_geometry(g, v, hs, decay_m=DECAY_M):
     # slopes of the coordinate surfaces at edges: the zeta_h of the two columns cancel
     dn = (t.hs[c2] - t.hs[c1]) / g.d_e
     dt = (t.hs_v[g.e2v[:, 1]] - t.hs_v[g.e2v[:, 0]]) / g.l_e
+    t.sn_s, t.st_s = dn, dt                            # at the ground (b = 1)
     t.sn_f = dn[:, None] * t.bf[None, :]               # full levels
-    t.sn_h = dn[:, None] * t.b[None, :]                # half levels
-    t.st_h = dt[:, None] * t.b[None, :]
+    t.st_f = dt[:, None] * t.bf[None, :]
     t.ex_ref = np.exp(-GRAV * t.zf_c / (CPD * T_REF))
     t.N = N
     return t
@@ -141,8 +143,13 @@ def pressure_gradient(g, t, s):
 
 def contravariant_correction(g, t, vn, vt):
     """R-Z4: wcc at cells and half levels (Nc, N+1) for the edge velocities vn, vt."""
-    wcc_e = to_half_w(t.wu_e, vn) * t.sn_h + to_half_w(t.wu_e, vt) * t.st_h
-    return cell_kinetic(g, wcc_e)
+    N = t.N
+    X = cell_kinetic(g, vn * t.sn_f + vt * t.st_f)
+    wcc = to_half_w(t.wu_c, X)
+    wcc[:, 0] = 0.0
+    ground = vn[:, N - 1:N] * t.sn_s[:, None] + vt[:, N - 1:N] * t.st_s[:, None]
+    wcc[:, N] = cell_kinetic(g, ground)[:, 0]
+    return wcc
 
 
 def tendencies(g, v, t, s):

@@ -20,7 +20,10 @@
 // spare FP64 issue slots.
 //
 // Per stage, k_topo_cell forms at every cell (one warp, lanes over levels)
-//   wcc_c,h = b_h sum_e (kappa_ce sn_e vn_ie + kappa_ce st_e vt_ie)   (contravariant correction)
+//   X_c,k = bf_k sum_e (kappa_ce sn_e vn_e,k + kappa_ce st_e vt_e,k)   (full levels)
+//   wcc_c,h = the half-level interpolant of X with the cell's weights (contravariant
+//            correction, in ICON's order); at the ground sum_e kappa_ce (sn_e vn + st_e vt)
+//            with the lowest full level's wind,
 //   w - wcc at interior half levels (0 at the lid and the ground),
 //   pi' = pi - pi_ref and half of d pi'/dz at full levels (the half-level interpolants
 //            differenced over dz, one-sided at the top and bottom full levels),
@@ -131,7 +134,7 @@ struct StageArgs {
   const int* c2e;
   const double* kin_w;
   const double *vn, *vt, *w, *ex;             // stage state and its tangential velocity
-  const double *b, *sn, *st, *wu_e;
+  const double *bf, *sn, *st;
   const double *wu_c, *inv_dz_c, *inv_dzh_c, *exref_c;
   double *wcc, *wcon, *ep, *hdpdz;
 };
@@ -139,8 +142,10 @@ struct StageArgs {
 // one warp per cell, lanes over levels: the stage's contravariant correction and
 // contravariant velocity at half levels, the Exner perturbation and half its vertical
 // derivative at full levels. FP64-pipe bound like the step's stencils: the kappa and
-// slope factors of the three edges are combined once per cell, and each half-level
-// interpolant is one subtraction and one fused multiply-add.
+// slope factors of the three edges are combined once per cell (6 fused multiply-adds
+// per full level), and the half-level interpolant takes the level above from the
+// neighbouring lane. Windows of 31 levels: lane l holds full level k = base + l and the
+// half level above it; lane 30's full level is carried to the next window.
 __global__ void __launch_bounds__(256, 4) k_topo_cell(StageArgs a) {
   const int64_t c = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
   if (c >= a.nc) return;
@@ -155,27 +160,32 @@ __global__ void __launch_bounds__(256, 4) k_topo_cell(StageArgs a) {
     An[s] = kw * a.sn[e];
     At[s] = kw * a.st[e];
   }
-  for (int h = lane; h <= N; h += 32) {
-    double acc = 0.0;
-    if (h > 0) {
+  double carry = 0.0;                       // X of the full level above the window
+  for (int base = 0; base <= N; base += 31) {
+    const int k = base + lane;
+    const bool own = lane < 31 && k <= N;   // half level k (and full level k if k < N)
+    double Y = 0.0;
+    if (lane < 31 && k < N) {
       for (int s = 0; s < 3; ++s) {
-        double vie, tie;
-        if (h >= N) {
-          vie = a.vn[E[s] + N - 1];
-          tie = a.vt[E[s] + N - 1];
-        } else {
-          const double wu = a.wu_e[E[s] + h];
-          const double v0 = a.vn[E[s] + h], t0 = a.vt[E[s] + h];
-          vie = fma(wu, a.vn[E[s] + h - 1] - v0, v0);
-          tie = fma(wu, a.vt[E[s] + h - 1] - t0, t0);
-        }
-        acc = fma(An[s], vie, acc);
-        acc = fma(At[s], tie, acc);
+        Y = fma(An[s], a.vn[E[s] + k], Y);
+        Y = fma(At[s], a.vt[E[s] + k], Y);
       }
-      acc *= a.b[h];
     }
-    a.wcc[o + h] = acc;
-    a.wcon[o + h] = (h > 0 && h < N) ? a.w[o + h] - acc : 0.0;
+    const double X = (lane < 31 && k < N) ? Y * a.bf[k] : 0.0;
+    double Xm = __shfl_up_sync(0xffffffffu, X, 1);
+    if (lane == 0) Xm = carry;
+    carry = __shfl_sync(0xffffffffu, X, 30);
+    if (own) {
+      if (k > 0 && k < N) {
+        const double wcc = fma(a.wu_c[o + k], Xm - X, X);
+        a.wcc[o + k] = wcc;
+        a.wcon[o + k] = a.w[o + k] - wcc;
+      } else {
+        if (k == 0) a.wcc[o] = 0.0;
+        a.wcon[o + k] = 0.0;
+      }
+      if (k == N - 1) a.wcc[o + N] = Y;     // ground: surface slopes, lowest full level's wind
+    }
   }
   for (int k = lane; k < N; k += 32) {
     const double* ex = a.ex + o;
@@ -253,7 +263,7 @@ void topo_stage(icon_state* st, const double* vn, const double* vt, const double
   a.nc = g.nc; a.N = v.N; a.ld = v.ld;
   a.c2e = g.c2e; a.kin_w = g.kin_w;
   a.vn = vn; a.vt = vt; a.w = w; a.ex = ex;
-  a.b = T.b; a.sn = T.sn; a.st = T.st; a.wu_e = T.wu_e;
+  a.bf = T.bf; a.sn = T.sn; a.st = T.st;
   a.wu_c = T.wu_c; a.inv_dz_c = T.inv_dz_c; a.inv_dzh_c = T.inv_dzh_c; a.exref_c = T.exref_c;
   a.wcc = T.wcc; a.wcon = T.wcon; a.ep = T.ep; a.hdpdz = T.hdpdz;
   prof_begin(stream, K_TERRAIN);
