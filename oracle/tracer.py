@@ -27,11 +27,17 @@ T5  update: (rho q)^{n+1} = rho^n q^n - dt [ (1/A_c) sum_s s_ce l_e M_e q_e
 With the dycore's own fluxes, rho^{n+1} = rho^n - dt div(M, W) up to rounding, so a
 uniform tracer stays uniform and the tracer mass sum_c A_c sum_k dz_k rho q is
 conserved (flux form). The scheme has no limiter.
+T6  on terrain-following levels (oracle.terrain; M then carries the layer thickness,
+    M = rho_e vn dz_e, and W is contravariant): v_n = M / (rho_e dz_e) and
+    v_t = M_t / (rho_e dz_e) in T3; each cell's own full and half heights, spacings and
+    interpolation weights in T4; in T5 the horizontal and vertical flux divergences
+    together are divided by the cell's dz_k: (rho q)^{n+1} = rho^n q^n - dt [(1/A_c)
+    sum_s s_ce l_e M_e q_e + W_k q_k - W_{k+1} q_{k+1}] / dz_ck.
 """
 import numpy as np
 
 from .grid import R_EARTH
-from .state import to_half
+from .state import to_half, to_half_w
 
 
 def cell_neighbours(g):
@@ -75,11 +81,13 @@ def cell_gradient(g, q, G=None):
     return out
 
 
-def edge_values(g, q, grad, M, rho, dt):
+def edge_values(g, q, grad, M, rho, dt, terrain=None):
     """T3: (Ne, N) upwind edge values with the half-step back-trajectory."""
     c1, c2 = g.e2c[:, 0], g.e2c[:, 1]
     cd = np.where(M >= 0.0, c1[:, None], c2[:, None])          # (Ne, N) donor cells
     rho_e = 0.5 * (rho[c1] + rho[c2])
+    if terrain is not None:
+        rho_e = rho_e * terrain.dz_e                           # T6: M carries dz_e
     vn = M / rho_e
     Mt = np.zeros_like(M)
     for j in range(5):
@@ -92,39 +100,51 @@ def edge_values(g, q, grad, M, rho, dt):
     return q[cd, k] + np.sum(gd * off, axis=2)
 
 
-def half_values(v, q, W, rho, dt):
+def half_values(v, q, W, rho, dt, terrain=None):
     """T4: (Nc, N+1) half-level values; 0 at the lid and the ground (no flux there)."""
     N = v.N
     nc = q.shape[0]
+    if terrain is None:
+        zf = np.broadcast_to(v.z_f[None, :], q.shape)
+        zh = np.broadcast_to(v.z_h[None, :], (nc, N + 1))
+        rho_ic = to_half(v, rho)
+    else:                                                      # T6: each cell's own levels
+        zf, zh = terrain.zf_c, terrain.zh_c
+        rho_ic = to_half_w(terrain.wu_c, rho)
     s = np.zeros_like(q)
     if N >= 3:
-        s[:, 1:N - 1] = (q[:, :N - 2] - q[:, 2:]) / (v.z_f[:N - 2] - v.z_f[2:])[None, :]
-    rho_ic = to_half(v, rho)
+        s[:, 1:N - 1] = (q[:, :N - 2] - q[:, 2:]) / (zf[:, :N - 2] - zf[:, 2:])
+    rows = np.arange(nc)
     out = np.zeros((nc, N + 1))
     for h in range(1, N):
         up = W[:, h] >= 0.0
         kd = np.where(up, h, h - 1)
-        qd = q[np.arange(nc), kd]
-        sd = s[np.arange(nc), kd]
+        qd = q[rows, kd]
+        sd = s[rows, kd]
         wh = W[:, h] / rho_ic[:, h]
-        out[:, h] = qd + sd * (v.z_h[h] - v.z_f[kd] - 0.5 * dt * wh)
+        out[:, h] = qd + sd * (zh[:, h] - zf[rows, kd] - 0.5 * dt * wh)
     return out
 
 
-def tracer_step(g, v, q, rho_old, rho_new, mflx, wflx, dt):
-    """T5: one transport step of the tracer q (Nc, N) with the step-mean fluxes."""
+def tracer_step(g, v, q, rho_old, rho_new, mflx, wflx, dt, terrain=None):
+    """T5: one transport step of the tracer q (Nc, N) with the step-mean fluxes (T6 on
+    terrain-following levels)."""
     grad = cell_gradient(g, q)
-    qe = edge_values(g, q, grad, mflx, rho_old, dt)
+    qe = edge_values(g, q, grad, mflx, rho_old, dt, terrain)
     F = mflx * qe
     div = np.zeros_like(q)
     for s in range(3):
         div += (g.s_ce[:, s] * g.l_e[g.c2e[:, s]])[:, None] * F[g.c2e[:, s]]
     div /= g.A_c[:, None]
-    V = wflx * half_values(v, q, wflx, rho_old, dt)
+    V = wflx * half_values(v, q, wflx, rho_old, dt, terrain)
+    if terrain is not None:
+        return (rho_old * q - dt * (div + (V[:, :v.N] - V[:, 1:])) / terrain.dz_c) / rho_new
     vert = (V[:, :v.N] - V[:, 1:]) / v.dz[None, :]
     return (rho_old * q - dt * (div + vert)) / rho_new
 
 
-def tracer_mass(g, v, rho, q):
-    """sum_c A_c sum_k dz_k rho q (kg of tracer per kg-of-air unit)."""
-    return float(np.sum(g.A_c * np.sum(rho * q * v.dz[None, :], axis=1)))
+def tracer_mass(g, v, rho, q, terrain=None):
+    """sum_c A_c sum_k dz_k rho q (kg of tracer per kg-of-air unit); each cell's own dz
+    on terrain-following levels."""
+    dz = v.dz[None, :] if terrain is None else terrain.dz_c
+    return float(np.sum(g.A_c * np.sum(rho * q * dz, axis=1)))

@@ -143,3 +143,63 @@ def test_mass_is_conserved_over_terrain(mountain_grid):
     assert abs(T.terrain_mass(g, t, s1) / m0 - 1.0) < 1e-13
     assert np.max(np.abs(s1["vn"] - s["vn"])) > 1e-3                # it moved
     assert np.all(acc["wflx"][:, 0] == 0.0) and np.all(acc["wflx"][:, -1] == 0.0)
+
+
+# ------------------------------------------------------------------ tracers on terrain (T6)
+@pytest.fixture(scope="module")
+def terrain_jet_step(mountain_grid):
+    g, v, t = mountain_grid
+    s0 = O.init_state(g, v, 1, O.CASE_JET, noise_K=0.1, terrain=t)
+    s1, acc = T.terrain_step(g, v, t, s0, 300.0, 5)
+    return g, v, t, s0, s1, acc
+
+
+def test_uniform_tracer_stays_uniform_over_terrain(terrain_jet_step):
+    """The terrain step's own thickness-weighted and contravariant fluxes satisfy
+    rho^{n+1} dz = rho^n dz - dt div(M, W): a uniform mixing ratio stays uniform."""
+    g, v, t, s0, s1, acc = terrain_jet_step
+    q = np.full_like(s0["rho"], 3.7)
+    q1 = O.tracer_step(g, v, q, s0["rho"], s1["rho"], acc["mflx"], acc["wflx"], 300.0, terrain=t)
+    assert np.max(np.abs(q1 / 3.7 - 1.0)) < 1e-13
+
+
+def test_tracer_mass_is_conserved_over_terrain(terrain_jet_step):
+    g, v, t, s0, s1, acc = terrain_jet_step
+    q = 1.0 + 0.5 * g.x_c[:, 2:3] + 0.01 * np.arange(v.N)[None, :]
+    m0 = O.tracer_mass(g, v, s0["rho"], q, terrain=t)
+    q1 = O.tracer_step(g, v, q, s0["rho"], s1["rho"], acc["mflx"], acc["wflx"], 300.0, terrain=t)
+    assert abs(O.tracer_mass(g, v, s1["rho"], q1, terrain=t) / m0 - 1.0) < 1e-14
+    assert np.max(np.abs(q1 - q)) > 1e-6
+    # the flat formula misses the cells' own thicknesses
+    assert abs(O.tracer_mass(g, v, s1["rho"], q1) / O.tracer_mass(g, v, s0["rho"], q) - 1.0) > 1e-9
+
+
+def test_tracer_over_flat_ground_reduces_to_the_flat_step():
+    g = O.build_grid(2, 2)
+    v = O.vertical_grid(20)
+    t = T.terrain_geometry(g, v, np.zeros(g.nc))
+    s0 = O.init_state(g, v, 1, O.CASE_JET, noise_K=0.1)
+    s1, acc = O.dycore_step(g, v, s0, 300.0, 5)
+    st1, acct = T.terrain_step(g, v, t, s0, 300.0, 5)
+    q = 1.0 + 0.5 * g.x_c[:, 2:3] + 0.01 * np.arange(v.N)[None, :]
+    a = O.tracer_step(g, v, q, s0["rho"], s1["rho"], acc["mflx"], acc["wflx"], 300.0)
+    b = O.tracer_step(g, v, q, s0["rho"], st1["rho"], acct["mflx"], acct["wflx"], 300.0, terrain=t)
+    assert np.max(np.abs(a - b)) < 1e-13
+
+
+def test_vertical_transport_of_a_linear_profile_is_exact_over_terrain(mountain_grid):
+    """Uniform density and upward mass flux, q linear in true height on the sloping
+    levels: at every level away from the boundary slopes the update is q(z - w dt)."""
+    g, v, t = mountain_grid
+    N, w, dt = v.N, 0.7, 40.0
+    rho = np.ones((g.nc, N))
+    W = np.zeros((g.nc, N + 1))
+    W[:, 1:N] = w
+    q = 2.0 + 1e-4 * t.zf_c
+    rho_new = rho - dt * (W[:, :N] - W[:, 1:]) / t.dz_c
+    q1 = O.tracer_step(g, v, q, rho, rho_new, np.zeros((g.ne, N)), W, dt, terrain=t)
+    exact = 2.0 + 1e-4 * (t.zf_c - w * dt)
+    assert np.max(np.abs(q1[:, 2:N - 2] - exact[:, 2:N - 2])) < 1e-12
+    # with the flat grid's heights the same update is off by the slope of the levels
+    q2 = O.tracer_step(g, v, q, rho, rho_new, np.zeros((g.ne, N)), W, dt)
+    assert np.max(np.abs(q2[:, 2:N - 2] - exact[:, 2:N - 2])) > 1e-6
