@@ -127,8 +127,8 @@ typedef struct {
    * ICON_F_MFLX is then rho_e vn dz_e (kg/m/s per layer) and ICON_F_WFLX contravariant. The
    * paper's vertical coordinate is ICON's terrain-following hybrid height coordinate
    * (Sec. "Current State of the Art"). 0 = flat ground (default); 0 < topo_height_m <= 2000
-   * and topo_radius_m >= 1e4, else ICON_EINVAL. States with topography take no tracers and
-   * join no ensemble. */
+   * and topo_radius_m >= 1e4, else ICON_EINVAL. Tracers of a state with topography are
+   * transported with these fluxes on its own levels; such states join no ensemble. */
   double topo_height_m;
   double topo_radius_m;
 } icon_case_params;
@@ -273,7 +273,8 @@ int icon_selftest(long long n, unsigned* failures);
 /* Name of kernel kind i (0 <= i < ICON_KIND_COUNT), or NULL. Mixed-precision
  * stencil kinds: 10 vertex, 11 edge diagnostics, 12 cell kinetic energy,
  * 13 edge tendency, 15 column-input gather, 16 diffusion vertex/divergence;
- * 20 tracer transport, 21 divergence damping, 22 background diffusion (options). */
+ * 20 tracer transport, 21 divergence damping, 22 background diffusion (options),
+ * 23 terrain metrics (states with topography). */
 const char* icon_kernel_kind_name(int kind);
 #define ICON_KIND_COUNT 24
 

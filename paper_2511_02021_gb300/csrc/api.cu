@@ -759,10 +759,6 @@ int icon_state_add_tracers(icon_state* st, int ntracers) {
   if (!st) { set_error("icon_state_add_tracers: state is NULL"); return ICON_EINVAL; }
   if (ntracers < 1 || ntracers > 8) { set_error("icon_state_add_tracers: need 1..8 tracers"); return ICON_EINVAL; }
   if (st->s.ntr != 0) { set_error("icon_state_add_tracers: the state already has tracers"); return ICON_EINVAL; }
-  if (st->s.topo.on) {
-    set_error("icon_state_add_tracers: tracer transport on terrain-following levels is not built");
-    return ICON_EINVAL;
-  }
   const int rc = tracer_alloc(st, ntracers);
   if (rc != ICON_OK) return rc;
   if (st->graph) {                      // the step's graph now has to transport them too

@@ -20,6 +20,10 @@
 // lanes over levels per tracer: cell (gradient and vertical fluxes), edge (horizontal
 // fluxes), cell (update, in place). Densities and W are read in the [cell][level]
 // layout; a mixed-precision state's level-major FP64 fields are transposed first.
+// On terrain-following levels (the TOPO instances) M carries the layer thickness dz_e
+// and W is contravariant: v_n = M / (rho_e dz_e), each cell's own spacings and weights
+// in the vertical reconstruction, and the update divides both flux divergences by the
+// cell's dz.
 #include "icon_internal.h"
 #include "recip64.h"
 
@@ -35,6 +39,7 @@ struct TrArgs {
   const double *lsq_c, *roff, *n_e, *t_e, *vt_w, *div_wa;
   const double *inv_dz, *wu, *wl, *lev;     // lev: [3][ld] slope 1/(dz), offsets below / above
   const double *rho0, *rho1, *W, *M;        // [c][ld], [c][ld], [c][ld] (half levels), [e][ld]
+  const double *t_dz_c, *t_inv_dz_c, *t_wu_c, *t_dz_e;   // terrain-following levels, [entity][ld]
   double* q;                                // [c][ld], updated in place
   double *gx, *gy, *gz, *V, *F;
   unsigned* status;
@@ -50,6 +55,7 @@ __device__ inline bool tr_finite(double x) {
 }
 
 // least-squares gradient at full levels; vertical flux W q_h at half levels
+template <bool TOPO>
 __global__ void __launch_bounds__(256) k_tr_cell(TrArgs a) {
   const int64_t c = tr_warp();
   if (c >= a.nc) return;
@@ -76,10 +82,21 @@ __global__ void __launch_bounds__(256) k_tr_cell(TrArgs a) {
       const double W = a.W[o + h];
       const bool up = W >= 0.0;
       const int kd = up ? h : h - 1;
-      const double sd = (kd >= 1 && kd + 1 < N) ? (q[o + kd - 1] - q[o + kd + 1]) * a.lev[kd] : 0.0;
-      const double rho_ic = a.wu[h] * a.rho0[o + h - 1] + a.wl[h] * a.rho0[o + h];
+      double sd = 0.0, rho_ic, off;
+      if constexpr (TOPO) {
+        // zf_{k-1} - zf_{k+1} = dz_{k-1}/2 + dz_k + dz_{k+1}/2; z_h - zf of the donor = +-dz/2
+        const double* dz = a.t_dz_c + o;
+        if (kd >= 1 && kd + 1 < N)
+          sd = (q[o + kd - 1] - q[o + kd + 1]) * recip64((0.5 * dz[kd - 1] + dz[kd]) + 0.5 * dz[kd + 1]);
+        const double wu = a.t_wu_c[o + h];
+        rho_ic = wu * a.rho0[o + h - 1] + (1.0 - wu) * a.rho0[o + h];
+        off = up ? 0.5 * dz[h] : -0.5 * dz[h - 1];
+      } else {
+        sd = (kd >= 1 && kd + 1 < N) ? (q[o + kd - 1] - q[o + kd + 1]) * a.lev[kd] : 0.0;
+        rho_ic = a.wu[h] * a.rho0[o + h - 1] + a.wl[h] * a.rho0[o + h];
+        off = up ? a.lev[ld + h] : a.lev[2 * ld + h];
+      }
       const double wh = W * recip64(rho_ic);
-      const double off = up ? a.lev[ld + h] : a.lev[2 * ld + h];
       flux = W * (q[o + kd] + sd * (off - hdt * wh));
     }
     a.V[o + h] = flux;
@@ -87,6 +104,7 @@ __global__ void __launch_bounds__(256) k_tr_cell(TrArgs a) {
 }
 
 // horizontal flux M q_e at edge-levels
+template <bool TOPO>
 __global__ void __launch_bounds__(256) k_tr_edge(TrArgs a) {
   const int64_t e = tr_warp();
   if (e >= a.ne) return;
@@ -110,7 +128,9 @@ __global__ void __launch_bounds__(256) k_tr_edge(TrArgs a) {
     const double M = a.M[o + k];
     const bool up = M >= 0.0;
     const int64_t cd = (up ? c1 : c2) + k;
-    const double r = recip64(0.5 * (a.rho0[c1 + k] + a.rho0[c2 + k]));
+    double rho_e = 0.5 * (a.rho0[c1 + k] + a.rho0[c2 + k]);
+    if constexpr (TOPO) rho_e *= a.t_dz_e[o + k];
+    const double r = recip64(rho_e);
     double Mt = 0.0;
     for (int j = 0; j < 5; ++j) Mt += wt[j] * a.M[S[j] + k];
     const double vn = M * r, vt = Mt * r;
@@ -123,6 +143,7 @@ __global__ void __launch_bounds__(256) k_tr_edge(TrArgs a) {
 }
 
 // flux-form update of the mixing ratio, in place
+template <bool TOPO>
 __global__ void __launch_bounds__(256) k_tr_update(TrArgs a) {
   const int64_t c = tr_warp();
   if (c >= a.nc) return;
@@ -137,8 +158,10 @@ __global__ void __launch_bounds__(256) k_tr_update(TrArgs a) {
   bool bad = false;
   for (int k = lane; k < N; k += 32) {
     const double div = (dw[0] * a.F[E[0] + k] + dw[1] * a.F[E[1] + k]) + dw[2] * a.F[E[2] + k];
-    const double vert = (a.V[o + k] - a.V[o + k + 1]) * a.inv_dz[k];
-    const double qn = (a.rho0[o + k] * a.q[o + k] - a.dt * (div + vert)) * recip64(a.rho1[o + k]);
+    double tend;
+    if constexpr (TOPO) tend = (div + (a.V[o + k] - a.V[o + k + 1])) * a.t_inv_dz_c[o + k];
+    else tend = div + (a.V[o + k] - a.V[o + k + 1]) * a.inv_dz[k];
+    const double qn = (a.rho0[o + k] * a.q[o + k] - a.dt * tend) * recip64(a.rho1[o + k]);
     a.q[o + k] = qn;
     bad |= !tr_finite(qn);
   }
@@ -216,6 +239,8 @@ void tracer_end(icon_state* st, double dt, cudaStream_t stream) {
   a.inv_dz = v.d_inv_dz; a.wu = v.d_wu; a.wl = v.d_wl; a.lev = g.tr_lev;
   a.rho0 = s.tr_rho0;
   a.M = s.mflx;
+  const TopoDev& T = s.topo;
+  a.t_dz_c = T.dz_c; a.t_inv_dz_c = T.inv_dz_c; a.t_wu_c = T.wu_c; a.t_dz_e = T.dz_e;
   a.gx = s.tr_gx; a.gy = s.tr_gy; a.gz = s.tr_gz; a.V = s.tr_V; a.F = s.tr_F;
   a.status = s.status;
   a.dt = dt;
@@ -232,9 +257,15 @@ void tracer_end(icon_state* st, double dt, cudaStream_t stream) {
   const unsigned nbc = blocks_for(nc, kTrWarps), nbe = blocks_for(g.ne, kTrWarps);
   for (int t = 0; t < s.ntr; ++t) {
     a.q = s.q + (size_t)t * nc * v.ld;
-    k_tr_cell<<<nbc, 256, 0, stream>>>(a);
-    k_tr_edge<<<nbe, 256, 0, stream>>>(a);
-    k_tr_update<<<nbc, 256, 0, stream>>>(a);
+    if (T.on) {
+      k_tr_cell<true><<<nbc, 256, 0, stream>>>(a);
+      k_tr_edge<true><<<nbe, 256, 0, stream>>>(a);
+      k_tr_update<true><<<nbc, 256, 0, stream>>>(a);
+    } else {
+      k_tr_cell<false><<<nbc, 256, 0, stream>>>(a);
+      k_tr_edge<false><<<nbe, 256, 0, stream>>>(a);
+      k_tr_update<false><<<nbc, 256, 0, stream>>>(a);
+    }
   }
   prof_end(stream);
 }

@@ -95,12 +95,41 @@ def test_topography_arguments(gpu):
             with pytest.raises(C.IconError) as ei:
                 C.icon_state_init_ex(grid, 1, 2, topo_height_m=h0, topo_radius_m=a, precision=prec)
             assert ei.value.status == C.ICON_EINVAL
-        st = C.icon_state_init_ex(grid, 1, 2, topo_height_m=1000.0, topo_radius_m=RADIUS)
-        try:
-            with pytest.raises(C.IconError) as ei:
-                C.icon_state_add_tracers(st, 1)
-            assert ei.value.status == C.ICON_EINVAL
-        finally:
-            C.icon_state_free(st)
     finally:
         C.icon_grid_free(grid)
+
+
+def test_tracer_over_terrain_vs_oracle(gpu):
+    """Two tracers (uniform and a smooth field) on the terrain-following levels through
+    two steps: the uniform one stays uniform, the other matches the oracle's transport
+    with the oracle's terrain fluxes, and tracer mass is conserved."""
+    C = gpu
+    bis, nlev, dt = 2, 20, 300.0
+    g = O.build_grid(2, bis)
+    v = O.vertical_grid(nlev)
+    t = T.terrain_geometry(g, v, T.mountain(g.x_c, H0, RADIUS))
+    q0 = 1.0 + 0.5 * g.x_c[:, 2:3] + 0.01 * np.arange(nlev)[None, :]
+    grid = C.icon_grid_build(2, bis, nlev)
+    st = C.icon_state_init_ex(grid, 8, 2, noise_K=0.1, topo_height_m=H0, topo_radius_m=RADIUS)
+    try:
+        C.icon_state_add_tracers(st, 2)
+        C.icon_state_set_tracer(st, grid, nlev, 0, np.full((g.nc, nlev), 3.7))
+        C.icon_state_set_tracer(st, grid, nlev, 1, q0)
+        for _ in range(2):
+            C.icon_dycore_step(st, dt, 5)
+        gq = [C.icon_state_copy_tracer(st, grid, nlev, i) for i in range(2)]
+        grho = C.icon_state_copy_field(st, grid, nlev, "rho")
+    finally:
+        C.icon_state_free(st)
+        C.icon_grid_free(grid)
+    s = O.init_state(g, v, 8, 2, noise_K=0.1, terrain=t)
+    m0 = O.tracer_mass(g, v, s["rho"], q0, terrain=t)
+    q = q0
+    for _ in range(2):
+        s1, acc = T.terrain_step(g, v, t, s, dt, 5)
+        q = O.tracer_step(g, v, q, s["rho"], s1["rho"], acc["mflx"], acc["wflx"], dt, terrain=t)
+        s = s1
+    assert np.max(np.abs(gq[0] / 3.7 - 1.0)) < 1e-13
+    assert np.max(np.abs(gq[1] - q)) < 1e-12
+    assert np.max(np.abs(gq[1] - q0)) > 1e-5                         # it moved (7e-5)
+    assert abs(O.tracer_mass(g, v, grho, gq[1], terrain=t) / m0 - 1.0) < 1e-13
