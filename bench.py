@@ -262,7 +262,15 @@ def run_gpu(args, wl, rank, world, local_rank):
 
     nc, ne, nv = counts(wl)
     N = wl.nlev
+    # one-time setup, wall clock (untimed by the step metric): grid build (connectivity,
+    # geometry, weights on the device) and the initial state of the measured precision
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     grid = C.icon_grid_build(2, wl.bisections, N)
+    setup = {"grid_build_ms": (time.perf_counter() - t0) * 1e3}
+    t0 = time.perf_counter()
+    C.icon_state_free(C.icon_state_init_ex(grid, wl.seed, wl.case, noise_K=wl.noise_K, precision=wl.precision))
+    setup["state_init_ms"] = (time.perf_counter() - t0) * 1e3
     hbm_peak, peak_src = peaks()
 
     def measure(precision, sample_clocks):
@@ -545,7 +553,7 @@ def run_gpu(args, wl, rank, world, local_rank):
             "hbm_roofline": step_hbm_roofline(value, wl.precision, hbm_peak), "kernels": breakdown,
             "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "mass_rel_drift": m_drift, "mixed": other,
             "rel_l2_vs_fp64_after_1_step": err_vs_fp64, "tracer": tracer, "divergence_damping": divdamp,
-            "topography": topo,
+            "topography": topo, "setup": setup,
             "simulated_days_per_day": wl.dt / (ms / args.steps * 1e-3),
             "device_memory_gb": {"peak_allocated": round(torch.cuda.max_memory_allocated() / 1e9, 2),
                                  "total": round(torch.cuda.get_device_properties(0).total_memory / 1e9, 2)}}
