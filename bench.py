@@ -532,6 +532,28 @@ def run_gpu(args, wl, rank, world, local_rank):
                         "mass_rel_drift": abs(tm1 - tm0) / tm0}
             finally:
                 C.icon_state_free(st)
+            # the mixed form on the same levels (its column recomputes its factors there)
+            st = C.icon_state_init_ex(grid, wl.seed, wl.case, noise_K=wl.noise_K, precision=1,
+                                      topo_height_m=1500.0, topo_radius_m=800e3)
+            try:
+                for _ in range(args.warmup):
+                    C.icon_dycore_step(st, wl.dt, wl.nsub)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                for _ in range(args.steps):
+                    C.icon_dycore_step_async(st, wl.dt, wl.nsub)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                C.icon_state_status(st)
+                ms_tm = e0.elapsed_time(e1) / args.steps
+                kms, kn = None, None
+                for _ in range(2):
+                    kms, kn = C.icon_dycore_step_profile(st, wl.dt, wl.nsub, kms, kn)
+                topo["mixed"] = {"value": nc * N * wl.nsub / (ms_tm * 1e-3), "unit": UNIT, "ms_per_step": ms_tm,
+                                 "kernels_ms_per_step": {n: round(kms[i] / 2, 4) for i, n in enumerate(names)
+                                                         if n and kn[i] > 0}}
+            finally:
+                C.icon_state_free(st)
         except C.IconError as exc:
             topo = {"skipped": str(exc)}
     C.icon_grid_free(grid)

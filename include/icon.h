@@ -116,7 +116,7 @@ typedef struct {
   double damp_m;     /* base of the Rayleigh damping layer, m (<=0: 45 km / 20 km)               */
   int precision;     /* icon_precision                                                           */
   int member;        /* ensemble member index for ICON_CASE_MEMBER                               */
-  /* Topography (terrain-following levels; ICON_FP64 only). A Gaussian mountain
+  /* Topography (terrain-following levels, both precisions). A Gaussian mountain
    * hs = topo_height_m exp(-(r / topo_radius_m)^2), r the great-circle distance to 90E 30N,
    * under SLEVE-type levels z = zeta + hs b(zeta), b = sinh((z_top - zeta)/4 km) /
    * sinh(z_top/4 km): the lowest level follows the ground, the lid stays flat. The step then
@@ -128,7 +128,9 @@ typedef struct {
    * paper's vertical coordinate is ICON's terrain-following hybrid height coordinate
    * (Sec. "Current State of the Art"). 0 = flat ground (default); 0 < topo_height_m <= 2000
    * and topo_radius_m >= 1e4, else ICON_EINVAL. Tracers of a state with topography are
-   * transported with these fluxes on its own levels; such states join no ensemble. */
+   * transported with these fluxes on its own levels; such states join no ensemble. A
+   * mixed-precision state with topography forms the metric terms in FP32 with its other
+   * stencils and its column always recomputes its factors (no stored-factor form). */
   double topo_height_m;
   double topo_radius_m;
 } icon_case_params;

@@ -189,7 +189,7 @@ bool table_ref(const icon_grid* grid, int id, TableRef& t) {
 }
 
 // allocate every buffer of a state; returns ICON_ENOMEM (arena then released by the caller)
-int alloc_state(icon_state* st, int precision) {
+int alloc_state(icon_state* st, int precision, bool topo) {
   const icon_grid* grid = st->grid;
   const int64_t ld = grid->vert.ld, nc = grid->g.nc, ne = grid->g.ne, nv = grid->g.nv;
   DeviceArena& A = st->arena;
@@ -244,7 +244,10 @@ int alloc_state(icon_state* st, int precision) {
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) total_b = 0;
     const char* force_recompute = getenv("ICON_MIXED_RECOMPUTE");
     const bool recompute = force_recompute && force_recompute[0] == '1' && force_recompute[1] == '\0';
-    if (fac_bytes <= total_b / 4 && !recompute) {
+    // on terrain-following levels the column recomputes its factors (the stored-factor
+    // form freezes the explicit vertical fluxes, which there carry each stage's own
+    // contravariant correction)
+    if (fac_bytes <= total_b / 4 && !recompute && !topo) {
       s.fac64 = A.get_n<double>((size_t)nc * 12 * (ld0 + 1));
       s.hdr = A.get_n<double>((size_t)nc * (ld0 + 1));
       s.hdt = A.get_n<double>((size_t)nc * (ld0 + 1));
@@ -491,10 +494,7 @@ int icon_state_init_ex(const icon_grid* grid, uint64_t seed, int case_id, const 
               0.5 * kTopoDecay, p.topo_height_m, p.topo_radius_m);
     return ICON_EINVAL;
   }
-  if (topo && p.precision != ICON_FP64) {
-    set_error("icon_state_init: topography is built for the FP64 form only");
-    return ICON_EINVAL;
-  }
+
   if (p.precision != ICON_FP64 && p.precision != ICON_MIXED) {
     set_error("icon_state_init: unknown precision %d", p.precision);
     return ICON_EINVAL;
@@ -512,7 +512,7 @@ int icon_state_init_ex(const icon_grid* grid, uint64_t seed, int case_id, const 
   st->case_id = case_id;
   st->arena.al = current_allocator();
   cudaStream_t stream = current_stream();
-  int rc = alloc_state(st, p.precision);
+  int rc = alloc_state(st, p.precision, topo);
   if (rc == ICON_OK) {
     cudaError_t e = cudaMemsetAsync(st->s.status, 0, 64 * sizeof(unsigned), stream);
     if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemsetAsync");
@@ -849,6 +849,10 @@ int icon_ensemble_create(icon_state* const* members, int n, icon_ensemble** out)
     }
     if (members[i]->s.ntr != 0) {
       set_error("icon_ensemble_create: the persistent ensemble does not transport tracers (member %d has some)", i);
+      return ICON_EINVAL;
+    }
+    if (members[i]->s.topo.on) {
+      set_error("icon_ensemble_create: the persistent ensemble runs on flat levels only (member %d has topography)", i);
       return ICON_EINVAL;
     }
     if (members[i]->grid->vert.N != members[0]->grid->vert.N || members[i]->grid->vert.N > 96) {

@@ -141,6 +141,10 @@ struct MxEdgeArgs {
   int corrector;
   int skip_flux;                           // fluxes formed after divergence damping instead
   int upwind_theta;                        // heat flux with the upwind theta_v (option)
+  // terrain-following levels (TOPO instances only; see terrain.cu): per-edge weights,
+  // 1/dz and dz ([Ne][ld]), cpd times the normal slope factor per edge, the full-level
+  // decay, and the stage's w - wcc and half of d(pi')/dz at cells ([Nc][ld])
+  const float *t_wu_e, *t_inv_dz_e, *t_dz_e, *t_csn, *t_bf, *t_wcon, *t_hdpdz;
 };
 
 // vn tendency and update, horizontal flux integrals, edge part of the w advection.
@@ -148,14 +152,17 @@ struct MxEdgeArgs {
 // group holds half level h = base + l and, except the last lane, full level k = h;
 // each half-level interpolant and cell-pair sum of w is formed once and passed to the
 // lane below with a shuffle (only the group's own lanes take part, so the two halves
-// of a warp may serve different entities).
-template <int LPE>
+// of a warp may serve different entities). TOPO (terrain-following levels): per-edge
+// interpolation weights, w - wcc in the vertical advection, the metric correction of the
+// pressure gradient (exp is then against the per-cell reference), fluxes through dz_e.
+template <int LPE, bool TOPO = false>
 __device__ inline void mx_edge_tend_item(const MxGeo& G, const MxEdgeArgs& a, int64_t e, int lane) {
   const int ld = G.ld, N = G.N;
   const int64_t c1 = (int64_t)G.e2c[2 * e] * ld, c2 = (int64_t)G.e2c[2 * e + 1] * ld;
   const int64_t v1 = (int64_t)G.e2v[2 * e] * ld, v2 = (int64_t)G.e2v[2 * e + 1] * ld;
   const float ide = G.inv_de32[e], ile = G.inv_le32[e], fe = G.f_e32[e], le = G.l_e32[e];
   const float cide = (float)kCpd * ide;
+  const float csn = TOPO ? a.t_csn[e] : 0.0f;
   const int64_t o = e * ld;
   const float* __restrict__ vn = a.vn + o;
   const float* __restrict__ vt = a.vt + o;
@@ -174,14 +181,21 @@ __device__ inline void mx_edge_tend_item(const MxGeo& G, const MxEdgeArgs& a, in
     const int hl = h > 0 ? (h - 1 < N - 1 ? h - 1 : N - 1) : 0;
     const int hu = h < N ? h : N - 1;
     const bool inner = h > 0 && h < N;
-    const float wa = inner ? G.wu32[h] : (h == 0 ? 0.0f : 1.0f);
-    const float wb = inner ? G.wl32[h] : (h == 0 ? 1.0f : 0.0f);
+    float wa, wb;
+    if constexpr (TOPO) {
+      wa = inner ? a.t_wu_e[o + h] : (h == 0 ? 0.0f : 1.0f);
+      wb = inner ? 1.0f - wa : (h == 0 ? 1.0f : 0.0f);
+    } else {
+      wa = inner ? G.wu32[h] : (h == 0 ? 0.0f : 1.0f);
+      wb = inner ? G.wl32[h] : (h == 0 ? 1.0f : 0.0f);
+    }
     float vie = 0.f, tie = 0.f, sw = 0.f, dw = 0.f, dwv = 0.f;
     if (hv) {
       vie = wa * vn[hl] + wb * vn[hu];
       tie = wa * vt[hl] + wb * vt[hu];
       const float w1 = w[c1 + h], w2 = w[c2 + h];
-      sw = w1 + w2;
+      if constexpr (TOPO) sw = a.t_wcon[c1 + h] + a.t_wcon[c2 + h];     // 0 at the lid and the ground
+      else sw = w1 + w2;
       dw = w2 - w1;
       dwv = wv[v2 + h] - wv[v1 + h];
     }
@@ -193,10 +207,15 @@ __device__ inline void mx_edge_tend_item(const MxGeo& G, const MxEdgeArgs& a, in
     const int k = h;
     const float wbar = 0.25f * (sw + sw_up);
     const float zeta_e = 0.5f * (zeta[v1 + k] + zeta[v2 + k]);
-    const float A = -(Kc[c2 + k] - Kc[c1 + k]) * ide + (zeta_e + fe) * vt[k] - wbar * (vie - vie_up) * G.inv_dz32[k];
+    const float A = -(Kc[c2 + k] - Kc[c1 + k]) * ide + (zeta_e + fe) * vt[k] -
+                    wbar * (vie - vie_up) * (TOPO ? a.t_inv_dz_e[o + k] : G.inv_dz32[k]);
     const float t1 = thv[c1 + k], t2 = thv[c2 + k];
     const float th_e = 0.5f * (t1 + t2);
-    const float pg = th_e * ((exq[c2 + k] - exq[c1 + k]) * cide);
+    float pg;
+    if constexpr (TOPO)
+      pg = th_e * ((exq[c2 + k] - exq[c1 + k]) * cide - (csn * a.t_bf[k]) * (a.t_hdpdz[c1 + k] + a.t_hdpdz[c2 + k]));
+    else
+      pg = th_e * ((exq[c2 + k] - exq[c1 + k]) * cide);
     float vnew;
     if (a.corrector) {
       vnew = a.vn_base[o + k] + a.dtau * (0.5f * (a.Avn0[o + k] + A) - pg);
@@ -206,7 +225,8 @@ __device__ inline void mx_edge_tend_item(const MxGeo& G, const MxEdgeArgs& a, in
     }
     a.vn_out[o + k] = vnew;
     if (a.skip_flux) continue;
-    const float F = 0.5f * (rho[c1 + k] + rho[c2 + k]) * vnew;
+    float F = 0.5f * (rho[c1 + k] + rho[c2 + k]) * vnew;
+    if constexpr (TOPO) F *= a.t_dz_e[o + k];
     a.phi[o + k] = F;
     a.gth[o + k] = (le * F) * (a.upwind_theta ? (vnew >= 0.0f ? t1 : t2) : th_e);
     if (a.corrector) a.mflx[o + k] += f32_to_f64(F) * a.inv_nsub;
@@ -248,6 +268,7 @@ __global__ void __launch_bounds__(256) k_mx_dd_lap(MxGeo G, const float* __restr
 
 struct MxDDArgs {
   const float *L, *rho, *thv;
+  const float* dz_e;                       // layer thickness at edges (terrain-following), or NULL
   float *vn, *phi, *gth;
   double* mflx;
   float scale;                             // c4 Abar^2
@@ -264,7 +285,8 @@ __global__ void __launch_bounds__(256) k_mx_dd_edge(MxGeo G, MxDDArgs a) {
   for (int k = lane; k < G.N; k += 32) {
     const float vn = a.vn[o + k] - sc * (a.L[c2 + k] - a.L[c1 + k]);
     a.vn[o + k] = vn;
-    const float F = 0.5f * (a.rho[c1 + k] + a.rho[c2 + k]) * vn;
+    float F = 0.5f * (a.rho[c1 + k] + a.rho[c2 + k]) * vn;
+    if (a.dz_e) F *= a.dz_e[o + k];
     a.phi[o + k] = F;
     const float t1 = a.thv[c1 + k], t2 = a.thv[c2 + k];
     a.gth[o + k] = (le * F) * (a.upwind_theta ? (vn >= 0.0f ? t1 : t2) : 0.5f * (t1 + t2));
@@ -435,6 +457,10 @@ struct MxColArgs {
   double* dps;
   unsigned* status;
   double dtau, inv_nsub;
+  // terrain-following levels (TOPO instances only): each cell's weights, 1/dz, 1/dzh and
+  // reference Exner (FP64, [Nc][ld]), FP32 1/dzh, and the stage's FP32 wcc and w - wcc
+  const double *t_wu_c, *t_inv_dz_c, *t_inv_dzh_c, *t_exref_c;
+  const float *t_inv_dzh32, *t_wcc, *t_wcon;
 };
 
 __device__ inline bool finite64(double x) {
@@ -442,8 +468,12 @@ __device__ inline bool finite64(double x) {
 }
 
 // the vertically implicit update of one column; CORR selects predictor (shadows of S*
-// only) or corrector (FP64 S^{n+1} in place, shadows of S^{n+1}, vertical mass flux)
-template <int NMAX, bool CORR>
+// only) or corrector (FP64 S^{n+1} in place, shadows of S^{n+1}, vertical mass flux).
+// TOPO (terrain-following levels): each cell's spacings and weights, the thickness-
+// weighted horizontal divergences over the cell's dz, the explicit vertical fluxes with
+// the contravariant (1 - beta) w - wcc, the vertical advection of w with w - wcc, the
+// contravariant step-mean vertical flux, and the ground w of the stage (its wcc).
+template <int NMAX, bool CORR, bool TOPO = false>
 __device__ inline void mx_column_item(const MxGeo& G, const MxColArgs& a, int64_t c) {
   const int N = G.N, ld = G.ld;
   const int64_t nc = G.nc;
@@ -471,7 +501,14 @@ __device__ inline void mx_column_item(const MxGeo& G, const MxColArgs& a, int64_
   M[0] = rho_m * thv_m;
   for (int k = 1; k < N; ++k) {
     const double rho = LM(a.rho, k), thv = LM(a.thv, k);
-    const double wu = cc[CC_WU * ld + k], wl = cc[CC_WL * ld + k];
+    double wu, wl;
+    if constexpr (TOPO) {
+      wu = a.t_wu_c[o + k];
+      wl = 1.0 - wu;
+    } else {
+      wu = cc[CC_WU * ld + k];
+      wl = cc[CC_WL * ld + k];
+    }
     const double ri = wu * rho_m + wl * rho;
     rho_ic[k] = ri;
     M[k] = ri * (wu * thv_m + wl * thv);
@@ -490,26 +527,52 @@ __device__ inline void mx_column_item(const MxGeo& G, const MxColArgs& a, int64_
     const double rho = LM(a.rho, k), thv = LM(a.thv, k), ex = LM(a.ex, k);
     const double w0 = LM(a.w, k), w1 = LM(a.w, k + 1);
     const double Th = rho * thv;
-    const double dt1 = cc[CC_DT1BDZ * ld + k];
-    rhox[k] = rho - dtau * Dr - dt1 * (rho_ic[k] * w0 - rho_ic[k + 1] * w1);
-    const double thx = Th - f32_to_f64(dtau32 * Dt) - dt1 * (M[k] * w0 - M[k + 1] * w1);
+    double thx;
+    float gfac;
+    if constexpr (TOPO) {
+      const double idz = a.t_inv_dz_c[o + k];
+      const double ve0 = k >= 1 ? (1.0 - kBeta) * w0 - f32_to_f64(a.t_wcc[o + k]) : 0.0;
+      const double ve1 = k + 1 < N ? (1.0 - kBeta) * w1 - f32_to_f64(a.t_wcc[o + k + 1]) : 0.0;
+      rhox[k] = rho - (dtau * ((Dr + rho_ic[k] * ve0) - rho_ic[k + 1] * ve1)) * idz;
+      thx = Th - (f32_to_f64(dtau32 * Dt) + dtau * (M[k] * ve0 - M[k + 1] * ve1)) * idz;
+      gfac = f64_to_f32(dtau * kBeta * idz);
+    } else {
+      const double dt1 = cc[CC_DT1BDZ * ld + k];
+      rhox[k] = rho - dtau * Dr - dt1 * (rho_ic[k] * w0 - rho_ic[k + 1] * w1);
+      thx = Th - f32_to_f64(dtau32 * Dt) - dt1 * (M[k] * w0 - M[k + 1] * w1);
+      gfac = f64_to_f32(cc[CC_DTBDZ * ld + k]);
+    }
     Thx[k] = thx;
     const float g = kRcvF * (f64_to_f32(ex) / f64_to_f32(Th));
     exx[k] = ex + f32_to_f64(g) * (thx - Th);
-    gam[k] = g * f64_to_f32(cc[CC_DTBDZ * ld + k]);
+    gam[k] = g * gfac;
   }
   // tridiagonal system at interior half levels, Thomas forward sweep
   double thv_m1 = LM(a.thv, 0), ex_m1 = LM(a.ex, 0);
   for (int h = 1; h < N; ++h) {
     const float hadv = kw[0] * a.a_e[E[0] + h] + kw[1] * a.a_e[E[1] + h] + kw[2] * a.a_e[E[2] + h];
     const float ws = a.w_stage[o + h];
-    float Aw = -hadv - ws * (a.w_stage[o + h - 1] - a.w_stage[o + h + 1]) * G.inv_dz2_32[h];
+    float Aw;
+    if constexpr (TOPO)
+      Aw = -hadv - a.t_wcon[o + h] * (a.w_stage[o + h - 1] - a.w_stage[o + h + 1]) * (0.5f * a.t_inv_dzh32[o + h]);
+    else
+      Aw = -hadv - ws * (a.w_stage[o + h - 1] - a.w_stage[o + h + 1]) * G.inv_dz2_32[h];
     if (CORR) Aw = 0.5f * (LM(a.Aw0, h) + Aw);
     else LM(a.Aw0, h) = Aw;
     const double thv_h = LM(a.thv, h), ex_h = LM(a.ex, h);
-    const double th_ic = cc[CC_WU * ld + h] * thv_m1 + cc[CC_WL * ld + h] * thv_h;
-    const double wx = LM(a.w, h) + dtau * (f32_to_f64(Aw) - cc[CC_CX * ld + h] * th_ic * (ex_m1 - ex_h) - kGrav);
-    const double aa = cc[CC_CA * ld + h] * th_ic;
+    double th_ic, cx, ca;
+    if constexpr (TOPO) {
+      const double wu = a.t_wu_c[o + h], idzh = a.t_inv_dzh_c[o + h];
+      th_ic = wu * thv_m1 + (1.0 - wu) * thv_h;
+      cx = (1.0 - kBeta) * kCpd * idzh;
+      ca = dtau * kBeta * kCpd * idzh;
+    } else {
+      th_ic = cc[CC_WU * ld + h] * thv_m1 + cc[CC_WL * ld + h] * thv_h;
+      cx = cc[CC_CX * ld + h];
+      ca = cc[CC_CA * ld + h];
+    }
+    const double wx = LM(a.w, h) + dtau * (f32_to_f64(Aw) - cx * th_ic * (ex_m1 - ex_h) - kGrav);
+    const double aa = ca * th_ic;
     const double gm = f32_to_f64(gam[h - 1]), gk = f32_to_f64(gam[h]);
     const double lower = -aa * gm * M[h - 1];
     const double diag = 1.0 + aa * (gm + gk) * M[h];
@@ -535,7 +598,8 @@ __device__ inline void mx_column_item(const MxGeo& G, const MxColArgs& a, int64_
   for (int k = 0; k < N; ++k) {
     const int h1 = k + 1;
     const double wn1 = (h1 < N) ? dp[h1 - 1] * cc[CC_DAMP * ld + h1] : 0.0;
-    const double dtb = cc[CC_DTBDZ * ld + k];
+    const double dtb = TOPO ? dtau * kBeta * a.t_inv_dz_c[o + k] : cc[CC_DTBDZ * ld + k];
+    const double exref = TOPO ? a.t_exref_c[o + k] : cc[CC_EXREF * ld + k];
     if (CORR) {
       const double q = M[k] * wn_prev - M[k + 1] * wn1;
       const double r = rho_ic[k] * wn_prev - rho_ic[k + 1] * wn1;
@@ -544,14 +608,16 @@ __device__ inline void mx_column_item(const MxGeo& G, const MxColArgs& a, int64_
       const double rho_n = rhox[k] - dtb * r;
       const double thv_n = Th_n * recip64(rho_n);
       const double wold = LM(a.w, k);
-      LM(a.wflx, k) += rho_ic[k] * (kBeta * wn_prev + (1.0 - kBeta) * wold) * a.inv_nsub;
+      double wc = kBeta * wn_prev + (1.0 - kBeta) * wold;
+      if constexpr (TOPO) wc -= k >= 1 ? f32_to_f64(a.t_wcc[o + k]) : 0.0;
+      LM(a.wflx, k) += rho_ic[k] * wc * a.inv_nsub;
       LM(a.rho, k) = rho_n;
       LM(a.thv, k) = thv_n;
       LM(a.ex, k) = ex_n;
       LM(a.w, k) = wn_prev;
       a.thv32[o + k] = f64_to_f32(thv_n);
       a.rho32[o + k] = f64_to_f32(rho_n);
-      a.exp32[o + k] = f64_to_f32(ex_n - cc[CC_EXREF * ld + k]);
+      a.exp32[o + k] = f64_to_f32(ex_n - exref);
       ok = ok && finite64(thv_n) && finite64(ex_n) && finite64(wn_prev);
     } else {
       // provisional state: FP32 shadows formed in FP32 from the FP64 solve (as in the
@@ -560,7 +626,7 @@ __device__ inline void mx_column_item(const MxGeo& G, const MxColArgs& a, int64_
       const float q = f64_to_f32(M[k]) * wf - f64_to_f32(M[k + 1]) * wf1;
       const float r = f64_to_f32(rho_ic[k]) * wf - f64_to_f32(rho_ic[k + 1]) * wf1;
       const float Th_n = f64_to_f32(Thx[k]) - dtb32 * q;
-      const float exp_n = f64_to_f32(exx[k] - cc[CC_EXREF * ld + k]) - gam[k] * q;
+      const float exp_n = f64_to_f32(exx[k] - exref) - gam[k] * q;
       const float rho_n = f64_to_f32(rhox[k]) - dtb32 * r;
       const float thv_n = Th_n / rho_n;
       a.thv32[o + k] = thv_n;
@@ -571,10 +637,16 @@ __device__ inline void mx_column_item(const MxGeo& G, const MxColArgs& a, int64_
     a.w32[o + k] = f64_to_f32(wn_prev);
     wn_prev = wn1;
   }
-  a.w32[o + N] = 0.0f;
-  if (CORR) {
-    LM(a.wflx, N) += rho_ic[N] * ((1.0 - kBeta) * LM(a.w, N)) * a.inv_nsub;
-    LM(a.w, N) = 0.0;
+  if constexpr (TOPO) {
+    // ground: no flux through it; w there is the stage's terrain-following value
+    a.w32[o + N] = a.t_wcc[o + N];
+    if (CORR) LM(a.w, N) = f32_to_f64(a.t_wcc[o + N]);
+  } else {
+    a.w32[o + N] = 0.0f;
+    if (CORR) {
+      LM(a.wflx, N) += rho_ic[N] * ((1.0 - kBeta) * LM(a.w, N)) * a.inv_nsub;
+      LM(a.w, N) = 0.0;
+    }
   }
   if (!ok) atomicOr(a.status, 1u);
 #undef LM
@@ -801,9 +873,10 @@ __device__ inline void mx_column_any(const MxGeo& G, const MxColArgs& a, int64_t
 
 // diffusion of theta_v for one column: FP32 increment, FP64 accumulation, Exner at
 // constant density, shadows refreshed
+// (exref_c: the per-cell reference of terrain-following levels, [Nc][ld], or NULL)
 __device__ inline void mx_diff_theta_item(const MxGeo& G, const float* __restrict__ thflx, double* __restrict__ thv,
                                           double* __restrict__ ex, float* __restrict__ thv32, float* __restrict__ exp32,
-                                          float dt, int64_t c) {
+                                          float dt, int64_t c, const double* __restrict__ exref_c = nullptr) {
   const int64_t nc = G.nc;
   const int ld = G.ld;
   int64_t E[3];
@@ -822,7 +895,7 @@ __device__ inline void mx_diff_theta_item(const MxGeo& G, const float* __restric
     thv[i] = th_n;
     ex[i] = ex_n;
     thv32[c * ld + k] = f64_to_f32(th_n);
-    exp32[c * ld + k] = f64_to_f32(ex_n - G.ex_ref[k]);
+    exp32[c * ld + k] = f64_to_f32(ex_n - (exref_c ? exref_c[c * ld + k] : G.ex_ref[k]));
   }
 }
 
@@ -850,10 +923,10 @@ __global__ void __launch_bounds__(512) k_mx_cell_ke(MxGeo G, const float* vn, co
   ITEM_PROLOGUE(LPE, G.nc)
   mx_cell_ke_item<LPE>(G, vn, vt, Kc, item, lane);
 }
-template <int LPE>
+template <int LPE, bool TOPO = false>
 __global__ void __launch_bounds__(512, 2) k_mx_edge_tend(MxGeo G, MxEdgeArgs a) {
   ITEM_PROLOGUE(LPE, G.ne)
-  mx_edge_tend_item<LPE>(G, a, item, lane);
+  mx_edge_tend_item<LPE, TOPO>(G, a, item, lane);
 }
 template <int LPE>
 __global__ void __launch_bounds__(512, 2) k_mx_diff_vertex(MxGeo G, const float* vn, float* ux, float* uy, float* uz,
@@ -1105,15 +1178,17 @@ __global__ void __launch_bounds__(256) k_mx_corr_update(MxGeo G, MxColArgs a) {
   if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(a.status, 1u);
 }
 
-template <int NMAX, bool CORR>
+template <int NMAX, bool CORR, bool TOPO = false>
 __global__ void __launch_bounds__(128) k_mx_column(MxGeo G, MxColArgs a) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < G.nc) mx_column_any<NMAX, CORR>(G, a, c);
+  if (c >= G.nc) return;
+  if constexpr (TOPO) mx_column_item<NMAX, CORR, true>(G, a, c);     // always recomputes its factors
+  else mx_column_any<NMAX, CORR>(G, a, c);
 }
 __global__ void __launch_bounds__(128) k_mx_diff_theta(MxGeo G, const float* thflx, double* thv, double* ex,
-                                                       float* thv32, float* exp32, float dt) {
+                                                       float* thv32, float* exp32, float dt, const double* exref_c) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < G.nc) mx_diff_theta_item(G, thflx, thv, ex, thv32, exp32, dt, c);
+  if (c < G.nc) mx_diff_theta_item(G, thflx, thv, ex, thv32, exp32, dt, c, exref_c);
 }
 
 MxGeo make_mx_geo(const icon_grid* grid, const StateDev& s) {
@@ -1150,6 +1225,9 @@ MxEdgeArgs edge_args(StateDev& s, bool corr, double dtau, int nsub) {
   ea.dtau = (float)dtau; ea.inv_nsub = 1.0 / nsub; ea.corrector = corr;
   ea.skip_flux = 0;
   ea.upwind_theta = 0;
+  const TopoDev& T = s.topo;
+  ea.t_wu_e = T.wu_e32; ea.t_inv_dz_e = T.inv_dz_e32; ea.t_dz_e = T.dz_e32; ea.t_csn = T.csn32; ea.t_bf = T.bf32;
+  ea.t_wcon = T.wcon32; ea.t_hdpdz = T.hdpdz32;
   return ea;
 }
 
@@ -1176,6 +1254,9 @@ MxColArgs col_args(StateDev& s, bool corr, double dtau, int nsub) {
   ca.dps = s.dps;
   ca.status = s.status;
   ca.dtau = dtau; ca.inv_nsub = 1.0 / nsub;
+  const TopoDev& T = s.topo;
+  ca.t_wu_c = T.wu_c; ca.t_inv_dz_c = T.inv_dz_c; ca.t_inv_dzh_c = T.inv_dzh_c; ca.t_exref_c = T.exref_c;
+  ca.t_inv_dzh32 = T.inv_dzh_c32; ca.t_wcc = T.wcc32; ca.t_wcon = T.wcon32;
   return ca;
 }
 
@@ -1203,8 +1284,13 @@ void launch_kind(int kind, const TileChoice& t, const MxGeo& G, StateDev& s, con
       else k_mx_cell_ke<32><<<item_blocks(G.nc, 32, B), B, 0, st>>>(G, ea.vn, s.vt32, s.Kc32);
       break;
     case K_MX_EDGE_TEND:
-      if (l16) k_mx_edge_tend<16><<<item_blocks(G.ne, 16, B), B, 0, st>>>(G, ea);
-      else k_mx_edge_tend<32><<<item_blocks(G.ne, 32, B), B, 0, st>>>(G, ea);
+      if (s.topo.on) {
+        if (l16) k_mx_edge_tend<16, true><<<item_blocks(G.ne, 16, B), B, 0, st>>>(G, ea);
+        else k_mx_edge_tend<32, true><<<item_blocks(G.ne, 32, B), B, 0, st>>>(G, ea);
+      } else {
+        if (l16) k_mx_edge_tend<16><<<item_blocks(G.ne, 16, B), B, 0, st>>>(G, ea);
+        else k_mx_edge_tend<32><<<item_blocks(G.ne, 32, B), B, 0, st>>>(G, ea);
+      }
       break;
     case K_MX_DIFF_VERTEX:
       if (l16)
@@ -1233,8 +1319,16 @@ void launch_kind(int kind, const TileChoice& t, const MxGeo& G, StateDev& s, con
 }
 
 template <bool CORR>
-void launch_mx_column(const MxGeo& G, const MxColArgs& a, cudaStream_t st) {
+void launch_mx_column(const MxGeo& G, const MxColArgs& a, bool topo, cudaStream_t st) {
   const unsigned nb = blocks_for(G.nc, 128);
+  if (topo) {
+    if (G.N <= 32) k_mx_column<32, CORR, true><<<nb, 128, 0, st>>>(G, a);
+    else if (G.N <= 64) k_mx_column<64, CORR, true><<<nb, 128, 0, st>>>(G, a);
+    else if (G.N <= 96) k_mx_column<96, CORR, true><<<nb, 128, 0, st>>>(G, a);
+    else if (G.N <= 128) k_mx_column<128, CORR, true><<<nb, 128, 0, st>>>(G, a);
+    else k_mx_column<256, CORR, true><<<nb, 128, 0, st>>>(G, a);
+    return;
+  }
   if (CORR && a.fac64) {
     k_mx_corr_solve<<<nb, 128, 0, st>>>(G, a);
     k_mx_corr_update<<<(unsigned)((G.nc + kUpdCells - 1) / kUpdCells), 256, 0, st>>>(G, a);
@@ -1357,6 +1451,7 @@ void enqueue_step_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream
       ead.skip_flux = damp ? 1 : 0;
       ead.upwind_theta = st->upwind_theta ? 1 : 0;
       for (int kind : {K_MX_VERTEX, K_MX_EDGE, K_MX_CELL_KE, K_MX_EDGE_TEND}) {
+        if (kind == K_MX_EDGE_TEND && s.topo.on) topo_stage32(st, ea.vn, s.vt32, ea.w, ea.exp, stream);
         prof_begin(stream, kind);
         launch_kind(kind, tile(kind), G, s, ead, ca, (float)dt, stream);
         prof_end(stream);
@@ -1367,6 +1462,7 @@ void enqueue_step_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream
         const double abar = 4.0 * M_PI * kR * kR / (double)nc;
         MxDDArgs da;
         da.L = s.vt32; da.rho = ea.rho; da.thv = ea.thv;
+        da.dz_e = s.topo.on ? s.topo.dz_e32 : nullptr;
         da.vn = s.vn32; da.phi = s.F32; da.gth = s.G32; da.mflx = s.mflx;
         da.scale = (float)(st->divdamp4 * abar * abar); da.inv_nsub = 1.0 / nsub;
         da.upwind_theta = st->upwind_theta ? 1 : 0;
@@ -1391,8 +1487,8 @@ void enqueue_step_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream
         prof_end(stream);
       }
       prof_begin(stream, K_MX_COLUMN);
-      if (corr) launch_mx_column<true>(G, ca, stream);
-      else launch_mx_column<false>(G, ca, stream);
+      if (corr) launch_mx_column<true>(G, ca, s.topo.on, stream);
+      else launch_mx_column<false>(G, ca, s.topo.on, stream);
       prof_end(stream);
     }
   }
@@ -1419,7 +1515,8 @@ void enqueue_step_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream
     prof_end(stream);
   }
   prof_begin(stream, K_MX_DIFF_THETA);
-  k_mx_diff_theta<<<blocks_for(nc, 128), 128, 0, stream>>>(G, s.vt32, s.thv, s.ex, s.thv32, s.exp32, (float)dt);
+  k_mx_diff_theta<<<blocks_for(nc, 128), 128, 0, stream>>>(G, s.vt32, s.thv, s.ex, s.thv32, s.exp32, (float)dt,
+                                                           s.topo.on ? s.topo.exref_c : nullptr);
   prof_end(stream);
 }
 

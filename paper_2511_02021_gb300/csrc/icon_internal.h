@@ -140,6 +140,12 @@ struct TopoDev {
   // ground) at half levels; Exner perturbation pi - pi_ref and half its vertical
   // derivative at full levels
   double *wcc = nullptr, *wcon = nullptr, *ep = nullptr, *hdpdz = nullptr;
+  // mixed-precision states: FP32 copies for the FP32 stencils ([entity][ld]; per edge;
+  // per level) and the stage's FP32 contravariant terms (the Exner perturbation is the
+  // state's own FP32 shadow, taken against this per-cell reference)
+  float *wu_e32 = nullptr, *inv_dz_e32 = nullptr, *dz_e32 = nullptr, *csn32 = nullptr, *bf32 = nullptr;
+  float *wu_c32 = nullptr, *inv_dz_c32 = nullptr, *inv_dzh_c32 = nullptr;
+  float *wcc32 = nullptr, *wcon32 = nullptr, *hdpdz32 = nullptr;
 };
 
 struct StateDev {
@@ -245,6 +251,10 @@ constexpr double kTopoTref = 250.0;     // temperature of the reference Exner pr
 int topo_build(icon_state* st, double h0, double radius, cudaStream_t stream);
 void topo_stage(icon_state* st, const double* vn, const double* vt, const double* w, const double* ex,
                 cudaStream_t stream);
+// mixed-precision states: the same stage terms in FP32 from the FP32 stage shadows
+// (exp = Exner - the per-cell reference)
+void topo_stage32(icon_state* st, const float* vn, const float* vt, const float* w, const float* exp,
+                  cudaStream_t stream);
 // tracer.cu
 int tracer_alloc(icon_state* st, int ntracers);
 void tracer_begin(icon_state* st, cudaStream_t stream);

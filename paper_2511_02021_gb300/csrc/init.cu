@@ -229,7 +229,7 @@ double jet_B() {
 __global__ void k_mixed_cells(int64_t nc, int64_t c0, int64_t n, int N, int ld, const double* __restrict__ w,
                               const double* __restrict__ rho, const double* __restrict__ thv,
                               const double* __restrict__ ex, const double* __restrict__ ex_ref,
-                              double* __restrict__ w_lm, double* __restrict__ rho_lm, double* __restrict__ thv_lm,
+                              const double* __restrict__ exref_c, double* __restrict__ w_lm, double* __restrict__ rho_lm, double* __restrict__ thv_lm,
                               double* __restrict__ ex_lm, float* __restrict__ w32, float* __restrict__ rho32,
                               float* __restrict__ thv32, float* __restrict__ exp32) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -249,7 +249,7 @@ __global__ void k_mixed_cells(int64_t nc, int64_t c0, int64_t n, int N, int ld, 
     ex_lm[(int64_t)k * nc + c] = ex[t];
     rho32[g] = (float)rho[t];
     thv32[g] = (float)thv[t];
-    exp32[g] = (float)(ex[t] - ex_ref[k]);
+    exp32[g] = (float)(ex[t] - (exref_c ? exref_c[g] : ex_ref[k]));
   } else {
     rho32[g] = 0.0f;
     thv32[g] = 0.0f;
@@ -266,7 +266,7 @@ __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, in
 __global__ void k_mixed_shadows(int64_t nc, int N, int ld, const double* __restrict__ w_lm,
                                 const double* __restrict__ rho_lm, const double* __restrict__ thv_lm,
                                 const double* __restrict__ ex_lm, const double* __restrict__ ex_ref,
-                                float* __restrict__ w32, float* __restrict__ rho32, float* __restrict__ thv32,
+                                const double* __restrict__ exref_c, float* __restrict__ w32, float* __restrict__ rho32, float* __restrict__ thv32,
                                 float* __restrict__ exp32) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nc * ld) return;
@@ -276,7 +276,7 @@ __global__ void k_mixed_shadows(int64_t nc, int N, int ld, const double* __restr
   if (k < N) {
     rho32[t] = (float)rho_lm[(int64_t)k * nc + c];
     thv32[t] = (float)thv_lm[(int64_t)k * nc + c];
-    exp32[t] = (float)(ex_lm[(int64_t)k * nc + c] - ex_ref[k]);
+    exp32[t] = (float)(ex_lm[(int64_t)k * nc + c] - (exref_c ? exref_c[t] : ex_ref[k]));
   }
 }
 
@@ -288,6 +288,7 @@ void mixed_cells_from_fp64(icon_state* st, int64_t c0, int64_t n, const double* 
   const Vertical& v = st->grid->vert;
   StateDev& s = st->s;
   k_mixed_cells<<<blocks_for(n * v.ld, 256), 256, 0, stream>>>(g.nc, c0, n, v.N, v.ld, w, rho, thv, ex, s.ex_ref,
+                                                               s.topo.on ? s.topo.exref_c : nullptr,
                                                                s.w, s.rho, s.thv, s.ex, s.w32, s.rho32, s.thv32,
                                                                s.exp32);
 }
@@ -298,6 +299,7 @@ void mixed_refresh_shadows(icon_state* st, cudaStream_t stream) {
   StateDev& s = st->s;
   const int64_t ncl = g.nc * v.ld;
   k_mixed_shadows<<<blocks_for(ncl, 256), 256, 0, stream>>>(g.nc, v.N, v.ld, s.w, s.rho, s.thv, s.ex, s.ex_ref,
+                                                            s.topo.on ? s.topo.exref_c : nullptr,
                                                             s.w32, s.rho32, s.thv32, s.exp32);
 }
 
@@ -361,13 +363,14 @@ int init_state_device(icon_state* st, uint64_t seed, int case_id, const icon_cas
   for (int64_t c0 = 0; c0 < g.nc; c0 += CH) {
     const int64_t n = (g.nc - c0) < CH ? (g.nc - c0) : CH;
     k_init_cells<<<blocks_for(n, 128), 128, 0, stream>>>(cd, c0, n, g.x_c, v.d_z_f, v.d_dzh, v.d_wu, v.d_wl,
-                                                         nullptr, nullptr, nullptr, rho, thv, ex, w);
+                                                         s.topo.on ? s.topo.hs : nullptr, s.topo.bf, s.topo.wu_c,
+                                                         rho, thv, ex, w);
     mixed_cells_from_fp64(st, c0, n, w, rho, thv, ex, stream);
   }
   for (int64_t e0 = 0; e0 < g.ne; e0 += CH) {
     const int64_t n = (g.ne - e0) < CH ? (g.ne - e0) : CH;
-    k_init_edges<<<blocks_for(n * v.ld, 256), 256, 0, stream>>>(cd, e0, n, g.x_e, g.n_e, v.d_z_f, g.e2c, nullptr,
-                                                                nullptr, vn);
+    k_init_edges<<<blocks_for(n * v.ld, 256), 256, 0, stream>>>(cd, e0, n, g.x_e, g.n_e, v.d_z_f, g.e2c,
+                                                                s.topo.on ? s.topo.hs : nullptr, s.topo.bf, vn);
     k_to_f32<<<blocks_for(n * v.ld, 256), 256, 0, stream>>>(vn, s.vn32 + e0 * v.ld, n * v.ld);
   }
   cudaError_t e = cudaGetLastError();

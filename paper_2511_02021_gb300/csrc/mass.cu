@@ -45,8 +45,10 @@ __global__ void __launch_bounds__(kMassThreads) k_mass_partial(int64_t nc, int N
 }
 
 // level-major density [k][Nc]: one thread per column, same fixed assignment and tree
-__global__ void __launch_bounds__(kMassThreads) k_mass_partial_lm(int64_t nc, int N, const double* __restrict__ rho,
+__global__ void __launch_bounds__(kMassThreads) k_mass_partial_lm(int64_t nc, int N, int ld,
+                                                                  const double* __restrict__ rho,
                                                                   const double* __restrict__ dz,
+                                                                  const double* __restrict__ dzc,
                                                                   const double* __restrict__ A_c,
                                                                   double* __restrict__ part) {
   __shared__ double ws[kMassThreads];
@@ -54,7 +56,10 @@ __global__ void __launch_bounds__(kMassThreads) k_mass_partial_lm(int64_t nc, in
   double acc = 0.0;
   for (int64_t c = (int64_t)blockIdx.x * kMassThreads + threadIdx.x; c < nc; c += nthr) {
     double col = 0.0;
-    for (int k = 0; k < N; ++k) col += rho[(int64_t)k * nc + c] * dz[k];
+    if (dzc)
+      for (int k = 0; k < N; ++k) col += rho[(int64_t)k * nc + c] * dzc[c * ld + k];
+    else
+      for (int k = 0; k < N; ++k) col += rho[(int64_t)k * nc + c] * dz[k];
     acc += A_c[c] * col;
   }
   ws[threadIdx.x] = acc;
@@ -87,7 +92,9 @@ void enqueue_mass(const icon_state* st, double* d_out, cudaStream_t stream) {
   const icon_grid* grid = st->grid;
   prof_begin(stream, K_MASS);
   if (st->s.level_major)
-    k_mass_partial_lm<<<kMassBlocks, kMassThreads, 0, stream>>>(grid->g.nc, grid->vert.N, st->s.rho, grid->vert.d_dz,
+    k_mass_partial_lm<<<kMassBlocks, kMassThreads, 0, stream>>>(grid->g.nc, grid->vert.N, grid->vert.ld, st->s.rho,
+                                                                grid->vert.d_dz,
+                                                                st->s.topo.on ? st->s.topo.dz_c : nullptr,
                                                                 grid->g.A_c, st->s.mass_part);
   else
     k_mass_partial<<<kMassBlocks, kMassThreads, 0, stream>>>(grid->g.nc, grid->vert.N, grid->vert.ld, st->s.rho,

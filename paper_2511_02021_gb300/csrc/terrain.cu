@@ -207,6 +207,89 @@ __global__ void __launch_bounds__(256, 4) k_topo_cell(StageArgs a) {
   }
 }
 
+// FP32 copy of an FP64 table
+__global__ void k_topo_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n, double scale) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)(scale * a[i]);
+}
+
+// FP32 1/dz at edges from the FP64 thickness
+__global__ void k_topo_inv32(const double* __restrict__ dz, float* __restrict__ out, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = dz[i] != 0.0 ? (float)(1.0 / dz[i]) : 0.0f;
+}
+
+struct StageArgs32 {
+  int64_t nc;
+  int N, ld;
+  const int* c2e;
+  const float* kin_w;
+  const double *sn, *st;
+  const float *vn, *vt, *w, *exp;             // FP32 stage shadows (exp against the per-cell reference)
+  const float *bf, *wu_c, *inv_dz_c, *inv_dzh_c;
+  float *wcc, *wcon, *hdpdz;
+};
+
+// the mixed-precision form of k_topo_cell: the same terms in FP32 (the precision of the
+// stencils that consume them), the Exner perturbation being the state's FP32 shadow
+__global__ void __launch_bounds__(256) k_topo_cell32(StageArgs32 a) {
+  const int64_t c = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  if (c >= a.nc) return;
+  const int lane = threadIdx.x & 31, ld = a.ld, N = a.N;
+  const int64_t o = c * ld;
+  int64_t E[3];
+  float An[3], At[3];
+  for (int s = 0; s < 3; ++s) {
+    const int e = a.c2e[3 * c + s];
+    E[s] = (int64_t)e * ld;
+    const float kw = a.kin_w[3 * c + s];
+    An[s] = kw * (float)a.sn[e];
+    At[s] = kw * (float)a.st[e];
+  }
+  float carry = 0.0f;
+  for (int base = 0; base <= N; base += 31) {
+    const int k = base + lane;
+    const bool own = lane < 31 && k <= N;
+    float Y = 0.0f;
+    if (lane < 31 && k < N) {
+      for (int s = 0; s < 3; ++s) {
+        Y = fmaf(An[s], a.vn[E[s] + k], Y);
+        Y = fmaf(At[s], a.vt[E[s] + k], Y);
+      }
+    }
+    const float X = (lane < 31 && k < N) ? Y * a.bf[k] : 0.0f;
+    float Xm = __shfl_up_sync(0xffffffffu, X, 1);
+    if (lane == 0) Xm = carry;
+    carry = __shfl_sync(0xffffffffu, X, 30);
+    if (own) {
+      if (k > 0 && k < N) {
+        const float wcc = fmaf(a.wu_c[o + k], Xm - X, X);
+        a.wcc[o + k] = wcc;
+        a.wcon[o + k] = a.w[o + k] - wcc;
+      } else {
+        if (k == 0) a.wcc[o] = 0.0f;
+        a.wcon[o + k] = 0.0f;
+      }
+      if (k == N - 1) a.wcc[o + N] = Y;
+    }
+  }
+  for (int k = lane; k < N; k += 32) {
+    const float* ep = a.exp + o;
+    const float p0 = ep[k];
+    float d;
+    if (k == 0) {
+      d = (p0 - ep[1]) * a.inv_dzh_c[o + 1];
+    } else if (k == N - 1) {
+      d = (ep[N - 2] - p0) * a.inv_dzh_c[o + N - 1];
+    } else {
+      const float fa = fmaf(a.wu_c[o + k], ep[k - 1] - p0, p0);
+      const float fb = fmaf(a.wu_c[o + k + 1], p0 - ep[k + 1], ep[k + 1]);
+      d = (fa - fb) * a.inv_dz_c[o + k];
+    }
+    a.hdpdz[o + k] = 0.5f * d;
+  }
+}
+
 }  // namespace
 
 int topo_build(icon_state* st, double h0, double radius, cudaStream_t stream) {
@@ -249,6 +332,29 @@ int topo_build(icon_state* st, double h0, double radius, cudaStream_t stream) {
                                                                  T.hs, T.wu_e, T.qinv_dz_e, T.dz_e, T.sn, T.st);
   ICON_CUDA(cudaGetLastError());
   for (double* p : {T.wcc, T.wcon, T.ep, T.hdpdz}) ICON_CUDA(cudaMemsetAsync(p, 0, sizeof(double) * C, stream));
+  if (st->s.precision == ICON_MIXED) {
+    float** e32[] = {&T.wu_e32, &T.inv_dz_e32, &T.dz_e32};
+    for (float** p : e32) *p = A.get_n<float>(E);
+    float** c32[] = {&T.wu_c32, &T.inv_dz_c32, &T.inv_dzh_c32, &T.wcc32, &T.wcon32, &T.hdpdz32};
+    for (float** p : c32) *p = A.get_n<float>(C);
+    T.csn32 = A.get_n<float>(g.ne);
+    T.bf32 = A.get_n<float>(v.ld);
+    if (A.failed) {
+      set_error("out of device memory for the terrain-following metric tables");
+      return ICON_ENOMEM;
+    }
+    const unsigned bE = blocks_for((int64_t)E, 256), bC = blocks_for((int64_t)C, 256);
+    k_topo_f32<<<bE, 256, 0, stream>>>(T.wu_e, T.wu_e32, (int64_t)E, 1.0);
+    k_topo_inv32<<<bE, 256, 0, stream>>>(T.dz_e, T.inv_dz_e32, (int64_t)E);
+    k_topo_f32<<<bE, 256, 0, stream>>>(T.dz_e, T.dz_e32, (int64_t)E, 1.0);
+    k_topo_f32<<<bC, 256, 0, stream>>>(T.wu_c, T.wu_c32, (int64_t)C, 1.0);
+    k_topo_f32<<<bC, 256, 0, stream>>>(T.inv_dz_c, T.inv_dz_c32, (int64_t)C, 1.0);
+    k_topo_f32<<<bC, 256, 0, stream>>>(T.inv_dzh_c, T.inv_dzh_c32, (int64_t)C, 1.0);
+    k_topo_f32<<<blocks_for(g.ne, 256), 256, 0, stream>>>(T.sn, T.csn32, g.ne, kCpd);
+    k_topo_f32<<<1, 256, 0, stream>>>(T.bf, T.bf32, v.ld, 1.0);
+    ICON_CUDA(cudaGetLastError());
+    for (float* p : {T.wcc32, T.wcon32, T.hdpdz32}) ICON_CUDA(cudaMemsetAsync(p, 0, sizeof(float) * C, stream));
+  }
   T.on = true;
   return ICON_OK;
 }
@@ -268,6 +374,24 @@ void topo_stage(icon_state* st, const double* vn, const double* vt, const double
   a.wcc = T.wcc; a.wcon = T.wcon; a.ep = T.ep; a.hdpdz = T.hdpdz;
   prof_begin(stream, K_TERRAIN);
   k_topo_cell<<<blocks_for(g.nc, kWarps), 256, 0, stream>>>(a);
+  prof_end(stream);
+}
+
+void topo_stage32(icon_state* st, const float* vn, const float* vt, const float* w, const float* exp,
+                  cudaStream_t stream) {
+  const icon_grid* grid = st->grid;
+  const GridDev& g = grid->g;
+  const Vertical& v = grid->vert;
+  const TopoDev& T = st->s.topo;
+  StageArgs32 a;
+  a.nc = g.nc; a.N = v.N; a.ld = v.ld;
+  a.c2e = g.c2e; a.kin_w = g.kin_w32;
+  a.sn = T.sn; a.st = T.st;
+  a.vn = vn; a.vt = vt; a.w = w; a.exp = exp;
+  a.bf = T.bf32; a.wu_c = T.wu_c32; a.inv_dz_c = T.inv_dz_c32; a.inv_dzh_c = T.inv_dzh_c32;
+  a.wcc = T.wcc32; a.wcon = T.wcon32; a.hdpdz = T.hdpdz32;
+  prof_begin(stream, K_TERRAIN);
+  k_topo_cell32<<<blocks_for(g.nc, kWarps), 256, 0, stream>>>(a);
   prof_end(stream);
 }
 

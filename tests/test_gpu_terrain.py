@@ -1,13 +1,15 @@
-"""The FP64 step on terrain-following levels over a Gaussian mountain against the
-oracle's (oracle.terrain), through the C ABI: initial state, one and two steps, with
-and without the step options, mass, and the argument checks of the topography."""
+"""The step on terrain-following levels over a Gaussian mountain against the oracle's
+(oracle.terrain), through the C ABI: initial state, one and two steps, with and without
+the step options, mass, tracers, the mixed-precision form, and the argument checks of
+the topography."""
 import numpy as np
 import pytest
 
 import oracle as O
 import oracle.terrain as T
 from tests.conftest import rel_l2
-from tests.tolerances import w_bound
+from tests.tolerances import w_bound, thermo_bound_mixed, w_bound_mixed
+from tests.test_gpu_mixed import d_min, TOL_WIND
 
 pytestmark = pytest.mark.gpu
 
@@ -15,9 +17,11 @@ PROG = ("vn", "w", "rho", "theta_v", "exner")
 H0, RADIUS = 1500.0, 800e3
 
 
-def run_gpu(C, bis, nlev, seed, case, dt, nsub, nsteps, c4=0.0, d4=0.0, ut=False, h0=H0, radius=RADIUS):
+def run_gpu(C, bis, nlev, seed, case, dt, nsub, nsteps, c4=0.0, d4=0.0, ut=False, h0=H0, radius=RADIUS,
+            precision=0):
     grid = C.icon_grid_build(2, bis, nlev)
-    st = C.icon_state_init_ex(grid, seed, case, noise_K=0.1, topo_height_m=h0, topo_radius_m=radius)
+    st = C.icon_state_init_ex(grid, seed, case, noise_K=0.1, topo_height_m=h0, topo_radius_m=radius,
+                              precision=precision)
     try:
         init = {f: C.icon_state_copy_field(st, grid, nlev, f) for f in PROG}
         C.icon_state_set_option(st, C.ICON_OPT_DIVDAMP4, c4)
@@ -91,10 +95,18 @@ def test_topography_arguments(gpu):
     C = gpu
     grid = C.icon_grid_build(2, 1, 10)
     try:
-        for h0, a, prec in [(-100.0, RADIUS, 0), (3000.0, RADIUS, 0), (1000.0, 10.0, 0), (1000.0, RADIUS, 1)]:
+        for h0, a, prec in [(-100.0, RADIUS, 0), (3000.0, RADIUS, 0), (1000.0, 10.0, 0), (1000.0, 10.0, 1)]:
             with pytest.raises(C.IconError) as ei:
                 C.icon_state_init_ex(grid, 1, 2, topo_height_m=h0, topo_radius_m=a, precision=prec)
             assert ei.value.status == C.ICON_EINVAL
+        # the persistent ensemble runs on flat levels only
+        m = C.icon_state_init_ex(grid, 1, 3, precision=1, topo_height_m=1000.0, topo_radius_m=RADIUS)
+        try:
+            with pytest.raises(C.IconError) as ei:
+                C.icon_ensemble_create([m])
+            assert ei.value.status == C.ICON_EINVAL
+        finally:
+            C.icon_state_free(m)
     finally:
         C.icon_grid_free(grid)
 
@@ -133,3 +145,48 @@ def test_tracer_over_terrain_vs_oracle(gpu):
     assert np.max(np.abs(gq[1] - q)) < 1e-12
     assert np.max(np.abs(gq[1] - q0)) > 1e-5                         # it moved (7e-5)
     assert abs(O.tracer_mass(g, v, grho, gq[1], terrain=t) / m0 - 1.0) < 1e-13
+
+
+# ------------------------------------------------------------------ mixed precision
+@pytest.mark.parametrize("bis,nlev,case,dt", [(2, 20, 2, 300.0), (3, 30, 3, 200.0)])
+def test_mixed_terrain_one_step_vs_oracle(gpu, bis, nlev, case, dt):
+    """The mixed form on terrain-following levels (FP32 stencils and metric terms, FP64
+    column with each cell's spacings) against the FP64 oracle, with the mixed form's
+    tolerances."""
+    gi, go, m0, m1 = run_gpu(gpu, bis, nlev, 8, case, dt, 5, 1, precision=1)
+    oi, oo, _, _ = run_oracle(bis, nlev, 8, case, dt, 5, 1)
+    for f in ("rho", "theta_v", "exner"):
+        assert np.array_equal(gi[f], oi[f]) or rel_l2(gi[f], oi[f]) <= 1e-14, f
+    assert rel_l2(go["vn"], oo["vn"]) <= TOL_WIND
+    assert rel_l2(go["mflx"], oo["mflx"]) <= TOL_WIND
+    for f in ("rho", "theta_v", "exner"):
+        assert rel_l2(go[f], oo[f]) <= thermo_bound_mixed(dt, 5, 1, d_min(bis)), f
+    assert np.sqrt(np.mean((go["w"] - oo["w"]) ** 2)) <= w_bound_mixed(dt, 5, 1)
+    assert abs(m1 - m0) / m0 <= 1e-13
+
+
+def test_mixed_terrain_vs_fp64_gpu_larger(gpu):
+    """R2B4 with 60 levels over the mountain, 2 steps: mixed against the FP64 GPU step."""
+    _, a, am0, _ = run_gpu(gpu, 4, 60, 2, 2, 240.0, 5, 2)
+    _, b, bm0, bm1 = run_gpu(gpu, 4, 60, 2, 2, 240.0, 5, 2, precision=1)
+    assert rel_l2(b["vn"], a["vn"]) <= 2 * TOL_WIND
+    for f in ("rho", "theta_v", "exner"):
+        assert rel_l2(b[f], a[f]) <= thermo_bound_mixed(240.0, 5, 2, d_min(4)), f
+    assert abs(bm1 - bm0) / bm0 <= 2e-13
+    assert abs(am0 / bm0 - 1) < 1e-15
+
+
+def test_mixed_terrain_tracer_stays_uniform(gpu):
+    C = gpu
+    grid = C.icon_grid_build(2, 2, 20)
+    st = C.icon_state_init_ex(grid, 8, 2, noise_K=0.1, precision=1, topo_height_m=H0, topo_radius_m=RADIUS)
+    try:
+        C.icon_state_add_tracers(st, 1)
+        C.icon_state_set_tracer(st, grid, 20, 0, np.full((1280, 20), 3.7))
+        for _ in range(2):
+            C.icon_dycore_step(st, 300.0, 5)
+        q = C.icon_state_copy_tracer(st, grid, 20, 0)
+    finally:
+        C.icon_state_free(st)
+        C.icon_grid_free(grid)
+    assert np.max(np.abs(q / 3.7 - 1.0)) < 1e-13
