@@ -458,9 +458,9 @@ struct MxColArgs {
   unsigned* status;
   double dtau, inv_nsub;
   // terrain-following levels (TOPO instances only): each cell's weights, 1/dz, 1/dzh and
-  // reference Exner (FP64, [Nc][ld]), FP32 1/dzh, and the stage's FP32 wcc and w - wcc
-  const double *t_wu_c, *t_inv_dz_c, *t_inv_dzh_c, *t_exref_c;
-  const float *t_inv_dzh32, *t_wcc, *t_wcon;
+  // reference Exner (FP64, level-major [k][Nc]), and the stage's FP32 wcc and w - wcc ([Nc][ld])
+  const double *t_wu_lm, *t_idz_lm, *t_idzh_lm, *t_exref_lm;
+  const float *t_wcc, *t_wcon;
 };
 
 __device__ inline bool finite64(double x) {
@@ -503,7 +503,7 @@ __device__ inline void mx_column_item(const MxGeo& G, const MxColArgs& a, int64_
     const double rho = LM(a.rho, k), thv = LM(a.thv, k);
     double wu, wl;
     if constexpr (TOPO) {
-      wu = a.t_wu_c[o + k];
+      wu = LM(a.t_wu_lm, k);
       wl = 1.0 - wu;
     } else {
       wu = cc[CC_WU * ld + k];
@@ -530,7 +530,7 @@ __device__ inline void mx_column_item(const MxGeo& G, const MxColArgs& a, int64_
     double thx;
     float gfac;
     if constexpr (TOPO) {
-      const double idz = a.t_inv_dz_c[o + k];
+      const double idz = LM(a.t_idz_lm, k);
       const double ve0 = k >= 1 ? (1.0 - kBeta) * w0 - f32_to_f64(a.t_wcc[o + k]) : 0.0;
       const double ve1 = k + 1 < N ? (1.0 - kBeta) * w1 - f32_to_f64(a.t_wcc[o + k + 1]) : 0.0;
       rhox[k] = rho - (dtau * ((Dr + rho_ic[k] * ve0) - rho_ic[k + 1] * ve1)) * idz;
@@ -552,9 +552,10 @@ __device__ inline void mx_column_item(const MxGeo& G, const MxColArgs& a, int64_
   for (int h = 1; h < N; ++h) {
     const float hadv = kw[0] * a.a_e[E[0] + h] + kw[1] * a.a_e[E[1] + h] + kw[2] * a.a_e[E[2] + h];
     const float ws = a.w_stage[o + h];
+    const double idzh = TOPO ? LM(a.t_idzh_lm, h) : 0.0;
     float Aw;
     if constexpr (TOPO)
-      Aw = -hadv - a.t_wcon[o + h] * (a.w_stage[o + h - 1] - a.w_stage[o + h + 1]) * (0.5f * a.t_inv_dzh32[o + h]);
+      Aw = -hadv - a.t_wcon[o + h] * (a.w_stage[o + h - 1] - a.w_stage[o + h + 1]) * f64_to_f32(0.5 * idzh);
     else
       Aw = -hadv - ws * (a.w_stage[o + h - 1] - a.w_stage[o + h + 1]) * G.inv_dz2_32[h];
     if (CORR) Aw = 0.5f * (LM(a.Aw0, h) + Aw);
@@ -562,7 +563,7 @@ __device__ inline void mx_column_item(const MxGeo& G, const MxColArgs& a, int64_
     const double thv_h = LM(a.thv, h), ex_h = LM(a.ex, h);
     double th_ic, cx, ca;
     if constexpr (TOPO) {
-      const double wu = a.t_wu_c[o + h], idzh = a.t_inv_dzh_c[o + h];
+      const double wu = LM(a.t_wu_lm, h);
       th_ic = wu * thv_m1 + (1.0 - wu) * thv_h;
       cx = (1.0 - kBeta) * kCpd * idzh;
       ca = dtau * kBeta * kCpd * idzh;
@@ -598,8 +599,8 @@ __device__ inline void mx_column_item(const MxGeo& G, const MxColArgs& a, int64_
   for (int k = 0; k < N; ++k) {
     const int h1 = k + 1;
     const double wn1 = (h1 < N) ? dp[h1 - 1] * cc[CC_DAMP * ld + h1] : 0.0;
-    const double dtb = TOPO ? dtau * kBeta * a.t_inv_dz_c[o + k] : cc[CC_DTBDZ * ld + k];
-    const double exref = TOPO ? a.t_exref_c[o + k] : cc[CC_EXREF * ld + k];
+    const double dtb = TOPO ? dtau * kBeta * LM(a.t_idz_lm, k) : cc[CC_DTBDZ * ld + k];
+    const double exref = TOPO ? LM(a.t_exref_lm, k) : cc[CC_EXREF * ld + k];
     if (CORR) {
       const double q = M[k] * wn_prev - M[k + 1] * wn1;
       const double r = rho_ic[k] * wn_prev - rho_ic[k + 1] * wn1;
@@ -1255,8 +1256,8 @@ MxColArgs col_args(StateDev& s, bool corr, double dtau, int nsub) {
   ca.status = s.status;
   ca.dtau = dtau; ca.inv_nsub = 1.0 / nsub;
   const TopoDev& T = s.topo;
-  ca.t_wu_c = T.wu_c; ca.t_inv_dz_c = T.inv_dz_c; ca.t_inv_dzh_c = T.inv_dzh_c; ca.t_exref_c = T.exref_c;
-  ca.t_inv_dzh32 = T.inv_dzh_c32; ca.t_wcc = T.wcc32; ca.t_wcon = T.wcon32;
+  ca.t_wu_lm = T.wu_lm; ca.t_idz_lm = T.idz_lm; ca.t_idzh_lm = T.idzh_lm; ca.t_exref_lm = T.exref_lm;
+  ca.t_wcc = T.wcc32; ca.t_wcon = T.wcon32;
   return ca;
 }
 

@@ -146,6 +146,9 @@ struct TopoDev {
   float *wu_e32 = nullptr, *inv_dz_e32 = nullptr, *dz_e32 = nullptr, *csn32 = nullptr, *bf32 = nullptr;
   float *wu_c32 = nullptr, *inv_dz_c32 = nullptr, *inv_dzh_c32 = nullptr;
   float *wcc32 = nullptr, *wcon32 = nullptr, *hdpdz32 = nullptr;
+  // and level-major copies ([k][Nc], N+1 rows) of the column's per-cell tables, which the
+  // mixed column reads one column per thread
+  double *wu_lm = nullptr, *idz_lm = nullptr, *idzh_lm = nullptr, *exref_lm = nullptr;
 };
 
 struct StateDev {

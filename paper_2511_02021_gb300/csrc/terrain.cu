@@ -219,6 +219,14 @@ __global__ void k_topo_inv32(const double* __restrict__ dz, float* __restrict__ 
   if (i < n) out[i] = dz[i] != 0.0 ? (float)(1.0 / dz[i]) : 0.0f;
 }
 
+// [c][ld] -> level-major [k][nc], rows 0..rows-1
+__global__ void k_topo_lm(const double* __restrict__ src, double* __restrict__ dst, int64_t nc, int rows, int ld) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nc * rows) return;
+  const int64_t k = t / nc, c = t % nc;
+  dst[t] = src[c * ld + k];
+}
+
 struct StageArgs32 {
   int64_t nc;
   int N, ld;
@@ -339,6 +347,9 @@ int topo_build(icon_state* st, double h0, double radius, cudaStream_t stream) {
     for (float** p : c32) *p = A.get_n<float>(C);
     T.csn32 = A.get_n<float>(g.ne);
     T.bf32 = A.get_n<float>(v.ld);
+    const size_t LMN = (size_t)g.nc * (v.N + 1);
+    double** lm[] = {&T.wu_lm, &T.idz_lm, &T.idzh_lm, &T.exref_lm};
+    for (double** p : lm) *p = A.get_n<double>(LMN);
     if (A.failed) {
       set_error("out of device memory for the terrain-following metric tables");
       return ICON_ENOMEM;
@@ -352,6 +363,11 @@ int topo_build(icon_state* st, double h0, double radius, cudaStream_t stream) {
     k_topo_f32<<<bC, 256, 0, stream>>>(T.inv_dzh_c, T.inv_dzh_c32, (int64_t)C, 1.0);
     k_topo_f32<<<blocks_for(g.ne, 256), 256, 0, stream>>>(T.sn, T.csn32, g.ne, kCpd);
     k_topo_f32<<<1, 256, 0, stream>>>(T.bf, T.bf32, v.ld, 1.0);
+    const unsigned bL = blocks_for((int64_t)LMN, 256);
+    k_topo_lm<<<bL, 256, 0, stream>>>(T.wu_c, T.wu_lm, g.nc, v.N + 1, v.ld);
+    k_topo_lm<<<bL, 256, 0, stream>>>(T.inv_dz_c, T.idz_lm, g.nc, v.N + 1, v.ld);
+    k_topo_lm<<<bL, 256, 0, stream>>>(T.inv_dzh_c, T.idzh_lm, g.nc, v.N + 1, v.ld);
+    k_topo_lm<<<bL, 256, 0, stream>>>(T.exref_c, T.exref_lm, g.nc, v.N + 1, v.ld);
     ICON_CUDA(cudaGetLastError());
     for (float* p : {T.wcc32, T.wcon32, T.hdpdz32}) ICON_CUDA(cudaMemsetAsync(p, 0, sizeof(float) * C, stream));
   }
