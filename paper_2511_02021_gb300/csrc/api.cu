@@ -215,6 +215,7 @@ int alloc_state(icon_state* st, int precision, bool topo) {
     s.zeta = A.get_n<double>(V); s.w_v = A.get_n<double>(V);
     s.vt = A.get_n<double>(E); s.Ke = A.get_n<double>(E); s.Kc = A.get_n<double>(C);
     s.a_e = A.get_n<double>(E); s.F = A.get_n<double>(E); s.G = A.get_n<double>(E);
+    s.kin_w_h = A.get_n<double>(3 * (size_t)nc); s.div_wa_h = A.get_n<double>(3 * (size_t)nc);
     // diffusion scratch reuses substep scratch (they never overlap in time)
     s.Kh = s.vt; s.thflx = s.Ke; s.divc = s.Kc; s.uvx = s.w_v;
     s.uvy = A.get_n<double>(V); s.uvz = A.get_n<double>(V);

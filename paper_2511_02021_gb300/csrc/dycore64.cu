@@ -55,6 +55,7 @@ struct Geo64 {
   const double *n_e, *t_e, *s_ce;
   const double *wu, *wl, *inv_dz, *inv_dz2, *qinv_dz;
   const double* cc;                        // per-level constants for the current dtau
+  const double *kin_w_h, *div_wa_h;        // half the cell weights (state tables, [Nc][3])
   // terrain-following levels (the TOPO kernel variants; see terrain.cu): per-edge normal
   // slope factor, full-level decay, per-entity tables [entity][ld], and the stage's
   // contravariant correction, contravariant velocity, Exner perturbation and half its
@@ -124,7 +125,7 @@ __global__ void __launch_bounds__(256, 4) k_vertex(Geo64 G, const double* __rest
   }
 }
 
-// vt (Perot) and K_e at edges
+// vt (Perot) and 2 K_e = vn^2 + vt^2 at edges (the 1/2 is folded into k_cell_ke's weights)
 __global__ void __launch_bounds__(256) k_edge_vt(Geo64 G, const double* __restrict__ vn, double* __restrict__ vt,
                                                  double* __restrict__ Ke) {
   const int64_t e = warp_entity();
@@ -141,11 +142,11 @@ __global__ void __launch_bounds__(256) k_edge_vt(Geo64 G, const double* __restri
     for (int j = 0; j < 5; ++j) acc += W[j] * vn[S[j] + k];
     const double v0 = vn[e * ld + k];
     vt[e * ld + k] = acc;
-    Ke[e * ld + k] = 0.5 * (v0 * v0 + acc * acc);
+    Ke[e * ld + k] = fma(v0, v0, acc * acc);
   }
 }
 
-// K_c at cells
+// K_c at cells (from 2 K_e)
 __global__ void __launch_bounds__(256) k_cell_ke(Geo64 G, const double* __restrict__ Ke, double* __restrict__ Kc) {
   const int64_t c = warp_entity();
   if (c >= G.nc) return;
@@ -154,7 +155,7 @@ __global__ void __launch_bounds__(256) k_cell_ke(Geo64 G, const double* __restri
   double kw[3];
   for (int s = 0; s < 3; ++s) {
     E[s] = (int64_t)G.c2e[3 * c + s] * ld;
-    kw[s] = G.kin_w[3 * c + s];
+    kw[s] = G.kin_w_h[3 * c + s];
   }
   for (int k = lane; k < G.N; k += 32) {
     double acc = 0.0;
@@ -171,6 +172,7 @@ struct EdgeArgs {
   double* Avn0;                            // stored (predictor) or read (corrector)
   double *F, *G, *a_e, *mflx;
   double dtau, inv_nsub;
+  double hinv_nsub;                        // inv_nsub / 2 (set on the host)
   int corrector;
   int skip_flux;                           // fluxes formed after divergence damping instead
   int upwind_theta;                        // heat flux with the upwind theta_v (option)
@@ -189,7 +191,7 @@ struct EdgeArgs {
 //   (pi'_c2 - pi'_c1)/d_e - sn_e bf_k (d pi'/dz at c1 and c2)/2,
 // and mass fluxes through layers of thickness dz_e; w - wcc, pi' and d pi'/dz come from
 // the stage's k_topo_cell.
-template <bool TOPO>
+template <bool TOPO, bool UT>
 __global__ void __launch_bounds__(256, 4) k_edge_tend(Geo64 G, EdgeArgs a) {
   const int64_t e = warp_entity();
   if (e >= G.ne) return;
@@ -198,8 +200,11 @@ __global__ void __launch_bounds__(256, 4) k_edge_tend(Geo64 G, EdgeArgs a) {
   const int64_t v1 = (int64_t)G.e2v[2 * e] * ld, v2 = (int64_t)G.e2v[2 * e + 1] * ld;
   const int64_t eo = e * ld;
   const double ide = G.inv_de[e], ile = G.inv_le[e], fe = G.f_e[e];
-  const double cide = kCpd * ide;
-  const double csne = TOPO ? kCpd * G.t_sn[e] : 0.0;
+  // the factors 1/2 of theta_e = (t1 + t2)/2 and rho_e = (rho1 + rho2)/2 are folded into
+  // these constants (and the column's divergence weights), exact scalings by powers of two
+  const double hcide = 0.5 * (kCpd * ide);
+  const double hcsne = TOPO ? 0.5 * (kCpd * G.t_sn[e]) : 0.0;
+  const double hinv_nsub = a.hinv_nsub;
   const double* __restrict__ vn = a.vn + eo;
   const double* __restrict__ vt = a.vt + eo;
   const double dtau = a.dtau;
@@ -242,13 +247,13 @@ __global__ void __launch_bounds__(256, 4) k_edge_tend(Geo64 G, EdgeArgs a) {
       const double T = fma(-dK, ide, fma(0.5, zs, fe) * vt[k]);
       const double A = fma(-((sw + sw_up) * (vie - vie_up)), TOPO ? G.t_qinv_dz_e[eo + k] : G.qinv_dz[k], T);
       const double t1 = a.thv[c1 + k], t2 = a.thv[c2 + k];
-      const double th_e = 0.5 * (t1 + t2);
+      const double th_s = t1 + t2;                     // 2 theta_e
       double pg;
       if (TOPO) {
-        const double corr = (csne * G.t_bf[k]) * (G.t_hdpdz[c1 + k] + G.t_hdpdz[c2 + k]);
-        pg = th_e * fma(G.t_ep[c2 + k] - G.t_ep[c1 + k], cide, -corr);
+        const double corr = (hcsne * G.t_bf[k]) * (G.t_hdpdz[c1 + k] + G.t_hdpdz[c2 + k]);
+        pg = th_s * fma(G.t_ep[c2 + k] - G.t_ep[c1 + k], hcide, -corr);
       } else {
-        pg = th_e * ((a.ex[c2 + k] - a.ex[c1 + k]) * cide);
+        pg = th_s * ((a.ex[c2 + k] - a.ex[c1 + k]) * hcide);
       }
       double vnew;
       if (a.corrector) {
@@ -259,11 +264,13 @@ __global__ void __launch_bounds__(256, 4) k_edge_tend(Geo64 G, EdgeArgs a) {
       }
       a.vn_out[eo + k] = vnew;
       if (a.skip_flux) continue;
-      double F = (0.5 * (a.rho[c1 + k] + a.rho[c2 + k])) * vnew;
+      // F = 2 rho_e vn and G = 4 rho_e vn theta_e (exactly; the column weights carry 1/2)
+      double F = (a.rho[c1 + k] + a.rho[c2 + k]) * vnew;
       if (TOPO) F *= G.t_dz_e[eo + k];
       a.F[eo + k] = F;
-      a.G[eo + k] = F * (a.upwind_theta ? (vnew >= 0.0 ? t1 : t2) : th_e);
-      if (a.corrector) a.mflx[eo + k] = fma(F, a.inv_nsub, a.mflx[eo + k]);
+      if constexpr (UT) a.G[eo + k] = F * (2.0 * (vnew >= 0.0 ? t1 : t2));     // upwind theta_v (option)
+      else a.G[eo + k] = F * th_s;
+      if (a.corrector) a.mflx[eo + k] = fma(F, hinv_nsub, a.mflx[eo + k]);
     }
   }
 }
@@ -320,12 +327,12 @@ __global__ void __launch_bounds__(256, 4) k_dd_edge(Geo64 G, DDArgs a) {
   for (int k = lane; k < G.N; k += 32) {
     const double vn = a.vn[eo + k] - s * (a.L[c2 + k] - a.L[c1 + k]);
     a.vn[eo + k] = vn;
-    double F = (0.5 * (a.rho[c1 + k] + a.rho[c2 + k])) * vn;
+    double F = (a.rho[c1 + k] + a.rho[c2 + k]) * vn;      // 2 rho_e vn, as k_edge_tend
     if (a.dz_e) F *= a.dz_e[eo + k];
     a.F[eo + k] = F;
     const double t1 = a.thv[c1 + k], t2 = a.thv[c2 + k];
-    a.G[eo + k] = F * (a.upwind_theta ? (vn >= 0.0 ? t1 : t2) : 0.5 * (t1 + t2));
-    a.mflx[eo + k] = fma(F, a.inv_nsub, a.mflx[eo + k]);
+    a.G[eo + k] = F * (a.upwind_theta ? (vn >= 0.0 ? t1 + t1 : t2 + t2) : t1 + t2);
+    a.mflx[eo + k] = fma(F, 0.5 * a.inv_nsub, a.mflx[eo + k]);
   }
 }
 
@@ -357,6 +364,7 @@ struct ColArgs {
   double* wflx;
   unsigned* status;
   double dtau, inv_nsub;
+  double hdtau;                            // dtau / 2 (set on the host: a kernel would recompute it per use)
   int corrector;
 };
 
@@ -377,10 +385,10 @@ __global__ void __launch_bounds__(256, 4) k_col_rows(Geo64 G, ColArgs a) {
   double dw[3], kw[3];
   for (int s = 0; s < 3; ++s) {
     E[s] = (int64_t)G.c2e[3 * c + s] * ld;
-    dw[s] = G.div_wa[3 * c + s];
+    dw[s] = G.div_wa_h[3 * c + s];         // the edge fluxes are 2 rho_e vn and 4 rho_e vn theta_e
     kw[s] = G.kin_w[3 * c + s];
   }
-  const double dtau = a.dtau, rcv = kRd / kCvd;
+  const double dtau = a.dtau, hdtau = a.hdtau, rcv = kRd / kCvd;
   double gam_c = 0.0, px_c = 0.0, M_c = 0.0;          // carried: full / half level base - 1
   for (int base = 0; base <= N; base += 31) {
     const int k = base + lane;
@@ -416,19 +424,20 @@ __global__ void __launch_bounds__(256, 4) k_col_rows(Geo64 G, ColArgs a) {
     double gam = 0.0, px = 0.0;
     if (kv) {
       // explicit predictors at full level k
-      double Dr = 0.0, Dt = 0.0;
+      // Dr: the mass-flux divergence; Dt2: twice the heat-flux divergence
+      double Dr = 0.0, Dt2 = 0.0;
       for (int s = 0; s < 3; ++s) Dr += dw[s] * a.F[E[s] + k];
-      for (int s = 0; s < 3; ++s) Dt += dw[s] * a.G[E[s] + k];
+      for (int s = 0; s < 3; ++s) Dt2 += dw[s] * a.G[E[s] + k];
       const double Th = rho * thv;
       double rx, tx;
       if constexpr (TOPO) {
         const double idz = G.t_inv_dz_c[o + k];
         rx = rho - (dtau * ((Dr + ri * ve) - ri1 * ve1)) * idz;
-        tx = Th - (dtau * ((Dt + M * ve) - M1 * ve1)) * idz;
+        tx = Th - (dtau * ((0.5 * Dt2 + M * ve) - M1 * ve1)) * idz;
       } else {
         const double dt1 = cc[C_DT1BDZ * ld + k];
         rx = (rho - dtau * Dr) - dt1 * (ri * wk - ri1 * w1);
-        tx = (Th - dtau * Dt) - dt1 * (M * wk - M1 * w1);
+        tx = (Th - hdtau * Dt2) - dt1 * (M * wk - M1 * w1);
       }
       const double g = (rcv * ex) * recip64(Th);
       px = ex + g * (tx - Th);
@@ -720,6 +729,7 @@ Geo64 make_geo(const icon_grid* grid, const double* cc) {
   G.inv_L34 = g.inv_L34; G.n_e = g.n_e; G.t_e = g.t_e; G.s_ce = g.s_ce;
   G.wu = v.d_wu; G.wl = v.d_wl; G.inv_dz = v.d_inv_dz; G.inv_dz2 = v.d_inv_dz2; G.qinv_dz = v.d_qinv_dz;
   G.cc = cc;
+  G.kin_w_h = G.div_wa_h = nullptr;
   G.t_sn = G.t_bf = G.t_wu_e = G.t_qinv_dz_e = G.t_dz_e = nullptr;
   G.t_wu_c = G.t_inv_dz_c = G.t_inv_dzh_c = G.t_wcc = G.t_wcon = G.t_ep = G.t_hdpdz = nullptr;
   return G;
@@ -740,6 +750,8 @@ void enqueue_step_fp64(icon_state* st, double dt, int nsub, cudaStream_t stream)
   const icon_grid* grid = st->grid;
   StateDev& s = st->s;
   Geo64 G = make_geo(grid, s.colconst);
+  G.kin_w_h = s.kin_w_h;
+  G.div_wa_h = s.div_wa_h;
   const TopoDev& T = s.topo;
   const bool topo = T.on;
   if (topo) {
@@ -781,12 +793,18 @@ void enqueue_step_fp64(icon_state* st, double dt, int nsub, cudaStream_t stream)
       ea.Avn0 = s.Avn0;
       ea.F = s.F; ea.G = s.G; ea.a_e = s.a_e; ea.mflx = s.mflx;
       ea.dtau = dtau; ea.inv_nsub = 1.0 / nsub; ea.corrector = corr;
+      ea.hinv_nsub = 0.5 / nsub;
       const bool damp = corr && st->divdamp4 > 0.0;
       ea.skip_flux = damp ? 1 : 0;
       ea.upwind_theta = st->upwind_theta ? 1 : 0;
       prof_begin(stream, K_EDGE_TEND);
-      if (topo) k_edge_tend<true><<<nbe, 256, 0, stream>>>(G, ea);
-      else k_edge_tend<false><<<nbe, 256, 0, stream>>>(G, ea);
+      if (topo) {
+        if (ea.upwind_theta) k_edge_tend<true, true><<<nbe, 256, 0, stream>>>(G, ea);
+        else k_edge_tend<true, false><<<nbe, 256, 0, stream>>>(G, ea);
+      } else {
+        if (ea.upwind_theta) k_edge_tend<false, true><<<nbe, 256, 0, stream>>>(G, ea);
+        else k_edge_tend<false, false><<<nbe, 256, 0, stream>>>(G, ea);
+      }
       prof_end(stream);
       if (damp) {
         // Kc and the column's update-operand scratch are free until the column runs
@@ -818,6 +836,7 @@ void enqueue_step_fp64(icon_state* st, double dt, int nsub, cudaStream_t stream)
       ca.wflx = s.wflx;
       ca.status = s.status;
       ca.dtau = dtau; ca.inv_nsub = 1.0 / nsub; ca.corrector = corr;
+      ca.hdtau = 0.5 * dtau;
       prof_begin(stream, K_COLUMN);
       launch_column(G, ca, topo, stream);
       prof_end(stream);

@@ -168,6 +168,9 @@ struct StateDev {
   // scratch (FP64 mode)
   double *zeta = nullptr, *w_v = nullptr, *vt = nullptr, *Ke = nullptr, *Kc = nullptr;
   double *a_e = nullptr, *F = nullptr, *G = nullptr;
+  // half the cell weights kappa_ce and s_ce l_e / A_c ([Nc][3]): the FP64 step stores
+  // 2 K_e, 2 rho_e vn and 4 rho_e vn theta_e at edges and folds the factors in here
+  double *kin_w_h = nullptr, *div_wa_h = nullptr;
   double *uvx = nullptr, *uvy = nullptr, *uvz = nullptr, *divc = nullptr, *Kh = nullptr, *thflx = nullptr;
   // mixed-mode scratch and shadows
   float *zeta32 = nullptr, *wv32 = nullptr, *vt32 = nullptr, *Ke32 = nullptr, *Kc32 = nullptr,

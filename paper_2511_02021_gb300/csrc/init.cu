@@ -257,6 +257,11 @@ __global__ void k_mixed_cells(int64_t nc, int64_t c0, int64_t n, int N, int ld, 
   }
 }
 
+__global__ void k_half(const double* __restrict__ a, double* __restrict__ b, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = 0.5 * a[i];
+}
+
 __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) b[i] = (float)a[i];
@@ -337,6 +342,8 @@ int init_state_device(icon_state* st, uint64_t seed, int case_id, const icon_cas
   k_exner_ref<<<1, 1, 0, stream>>>(v.N, v.d_z_f, v.d_dzh, v.d_wu, v.d_wl, s.ex_ref);
   if (s.exref32) k_to_f32<<<1, 256, 0, stream>>>(s.ex_ref, s.exref32, v.ld);
   if (s.precision == ICON_FP64) {
+    k_half<<<blocks_for(3 * g.nc, 256), 256, 0, stream>>>(g.kin_w, s.kin_w_h, 3 * g.nc);
+    k_half<<<blocks_for(3 * g.nc, 256), 256, 0, stream>>>(g.div_wa, s.div_wa_h, 3 * g.nc);
     const TopoDev& T = s.topo;
     k_init_cells<<<blocks_for(g.nc, 128), 128, 0, stream>>>(cd, 0, g.nc, g.x_c, v.d_z_f, v.d_dzh, v.d_wu, v.d_wl,
                                                             T.on ? T.hs : nullptr, T.bf, T.wu_c, s.rho, s.thv,
