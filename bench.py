@@ -79,7 +79,7 @@ TRACER_FP64_OPS = 77
 # measured; mixed column at R2B6/90 measured and scaled by cells to R2B8/90; recomputing
 # mixed column measured at R2B5/60 and scaled by cells to R2B9/60.
 NCU_TRAFFIC = {
-    ("R2B6-L90-jet-fp64", "column_solve"): 10.61e9,
+    ("R2B6-L90-jet-fp64", "column_solve"): 10.60e9,
     ("R2B6-L90-jet-fp64", "mx_column_solve"): 7.82e9,
     ("R2B8-L90-jet-mixed", "mx_column_solve"): 7.82e9 * 16,
     ("R2B9-L60-jet-mixed", "mx_column_solve"): 1.627e9 * 256,
