@@ -49,3 +49,26 @@ def test_host_argument_checks(built_lib):
     lib.icon_grid_free(None)
     lib.icon_state_free(None)
     lib.icon_ensemble_free(None)
+
+
+def test_case_params_layout_matches_the_header(tmp_path):
+    """The Python binding's icon_case_params has the C struct's size and field offsets
+    (compiled from include/icon.h with the host C compiler)."""
+    import shutil
+    import subprocess
+    import pytest
+    from paper_2511_02021_gb300 import capi as C
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    fields = [f for f, _ in C.CaseParams._fields_]
+    src = tmp_path / "layout.c"
+    body = "".join('printf("%%zu\\n", offsetof(icon_case_params, %s));\n' % f for f in fields)
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include <stdint.h>\n#include "icon.h"\n'
+                   'int main(void) {\nprintf("%zu\\n", sizeof(icon_case_params));\n' + body + 'return 0;\n}\n')
+    exe = tmp_path / "layout"
+    inc = os.path.join(ROOT, "include")
+    subprocess.run([cc, "-std=c11", "-I", inc, str(src), "-o", str(exe)], check=True, capture_output=True)
+    out = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(C.CaseParams)
+    assert out[1:] == [getattr(C.CaseParams, f).offset for f in fields]
