@@ -3,7 +3,8 @@ throughput benchmark uses (graph-captured step, default tiles).
 
 R2B6 / 90 levels FP64: sampled columns of one step against stored oracle values
 (written by tests/golden/make_step_samples.py, which runs only the oracle), plus the
-L2 norm of every full field. R2B8 / 90 levels mixed: the oracle cannot run at this
+L2 norm of every full field; the same on terrain-following levels over the benchmark's
+mountain (make_terrain_samples.py), FP64 and mixed. R2B8 / 90 levels mixed: the oracle cannot run at this
 size in a test, so the mixed step is held to the same derived bounds against the
 FP64 GPU step (itself pinned to the oracle above and in test_gpu_step), and mass is
 checked for conservation."""
@@ -96,6 +97,61 @@ def test_r2b6_l90_fp64_tracer_sampled(gpu, samples):
     # hold the difference to a few hundred ulps of q rather than relative to the change
     assert np.max(np.abs(q[cells] - ref)) <= 1e-13
     assert abs(np.linalg.norm(q) / samples["norm_step"]["tracer"] - 1.0) <= TOL_STEP
+
+
+@pytest.fixture(scope="module")
+def terrain_samples():
+    with open(golden_path("r2b6_l90_jet_terrain_step_samples.json")) as fh:
+        return json.load(fh)
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_r2b6_l90_terrain_step_sampled(gpu, terrain_samples, precision):
+    """The benchmark's terrain variant (R2B6 / 90 levels over the 1500 m mountain, the jet
+    with its bump): one step at sampled columns, half of them on the mountain's slopes,
+    against stored oracle values (written by tests/golden/make_terrain_samples.py) -- FP64
+    at the FP64 tolerances, the mixed form within its bounds."""
+    C = gpu
+    smp = terrain_samples
+    cfg = smp["config"]
+    N, dt, nsub = cfg["nlev"], cfg["dt"], cfg["nsub"]
+    cells, edges = np.array(smp["cells"]), np.array(smp["edges"])
+    with open(golden_path("grid_dual_edge_min.json")) as fh:
+        d_min = json.load(fh)["d_e_min_m"][str(cfg["bisections"])]
+    grid = C.icon_grid_build(cfg["root"], cfg["bisections"], N)
+    st = C.icon_state_init_ex(grid, cfg["seed"], cfg["case"], noise_K=cfg["noise_K"], precision=precision,
+                              topo_height_m=cfg["topo_height_m"], topo_radius_m=cfg["topo_radius_m"])
+    try:
+        for f, ref in smp["init"].items():
+            if f == "vn" and precision == 1:
+                continue                               # stored in FP32
+            full = C.icon_state_copy_field(st, grid, N, f)
+            idx = edges if f == "vn" else cells
+            assert rel_l2(full[idx], np.array(ref)) <= TOL_INIT, f
+        m0 = C.icon_global_mass(st)
+        C.icon_dycore_step(st, dt, nsub)
+        m1 = C.icon_global_mass(st)
+        for f, ref in smp["step"].items():
+            full = C.icon_state_copy_field(st, grid, N, f)
+            idx = edges if f in ("vn", "mflx") else cells
+            got, ref = full[idx], np.array(ref)
+            if f in ("w", "wflx"):
+                wb = w_bound(dt, nsub, 1) if precision == 0 else w_bound_mixed(dt, nsub, 1)
+                scale = 1.0 if f == "w" else float(np.max(np.abs(np.array(smp["step"]["rho"]))))
+                assert np.sqrt(np.mean((got - ref) ** 2)) <= wb * scale, f
+            elif precision == 0:
+                assert rel_l2(got, ref) <= TOL_STEP, (f, rel_l2(got, ref))
+                assert abs(np.linalg.norm(full) / smp["norm_step"][f] - 1.0) <= TOL_STEP, f
+            else:
+                bound = 1e-5 if f in ("vn", "mflx") else thermo_bound_mixed(dt, nsub, 1, d_min)
+                assert rel_l2(got, ref) <= bound, (f, rel_l2(got, ref), bound)
+            del full
+        om0, om1 = smp["mass"]
+        assert abs(m0 / om0 - 1.0) <= 1e-14
+        assert abs(m1 / m0 - 1.0) <= 1e-13 and abs(om1 / om0 - 1.0) <= 1e-13
+    finally:
+        C.icon_state_free(st)
+        C.icon_grid_free(grid)
 
 
 def test_r2b8_l90_mixed_vs_fp64(gpu):
