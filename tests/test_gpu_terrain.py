@@ -49,7 +49,7 @@ def run_oracle(bis, nlev, seed, case, dt, nsub, nsteps, c4=0.0, d4=0.0, ut=False
     return s0, dict(s, **acc), T.terrain_mass(g, t, s0), T.terrain_mass(g, t, s)
 
 
-CASES = [(2, 20, 2, 300.0, 1), (3, 30, 3, 200.0, 2)]
+CASES = [(2, 20, 2, 300.0, 1), (3, 30, 3, 200.0, 2), (1, 2, 2, 300.0, 1), (1, 3, 3, 300.0, 1)]
 
 
 @pytest.mark.parametrize("bis,nlev,case,dt,nsteps", CASES)

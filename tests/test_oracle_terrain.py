@@ -203,3 +203,17 @@ def test_vertical_transport_of_a_linear_profile_is_exact_over_terrain(mountain_g
     # with the flat grid's heights the same update is off by the slope of the levels
     q2 = O.tracer_step(g, v, q, rho, rho_new, np.zeros((g.ne, N)), W, dt)
     assert np.max(np.abs(q2[:, 2:N - 2] - exact[:, 2:N - 2])) > 1e-6
+
+
+@pytest.mark.parametrize("nlev", [2, 3])
+def test_fewest_levels_conserve_mass(nlev):
+    """The smallest columns (two and three levels: both full levels use the one-sided
+    vertical derivative, no interior interpolant) still conserve mass and move."""
+    g = O.build_grid(2, 1)
+    v = O.vertical_grid(nlev)
+    t = T.terrain_geometry(g, v, T.mountain(g.x_c, 1500.0, 1.5e6))
+    s = O.init_state(g, v, 8, O.CASE_JET, noise_K=0.1, terrain=t)
+    s1, _ = T.terrain_step(g, v, t, s, 300.0, 5)
+    assert abs(T.terrain_mass(g, t, s1) / T.terrain_mass(g, t, s) - 1.0) < 1e-13
+    assert all(np.all(np.isfinite(s1[k])) for k in s1)
+    assert np.max(np.abs(s1["vn"] - s["vn"])) > 1e-2
