@@ -365,6 +365,7 @@ struct ColArgs {
   unsigned* status;
   double dtau, inv_nsub;
   double hdtau;                            // dtau / 2 (set on the host: a kernel would recompute it per use)
+  double b_new, b_old;                     // beta / nsub, (1 - beta) / nsub
   int corrector;
 };
 
@@ -481,9 +482,10 @@ __global__ void __launch_bounds__(256, 4) k_col_rows(Geo64 G, ColArgs a) {
         aa = cc[C_CA * ld + h] * th_ic;
       }
       const int64_t i = (int64_t)h * nc + c;
-      a.lo[i] = -aa * gam_m * M_m;
-      a.di[i] = 1.0 + aa * (gam_m + gam) * M;
-      a.up[i] = -aa * gam * M1;
+      const double P = aa * gam_m, Q = aa * gam;
+      a.lo[i] = -P * M_m;
+      a.di[i] = fma(P + Q, M, 1.0);
+      a.up[i] = -Q * M1;
       a.rh[i] = w_x - aa * (px_m - px);
     }
     gam_c = __shfl_sync(0xffffffffu, gam, 30);
@@ -559,10 +561,11 @@ __global__ void __launch_bounds__(256) k_col_update(Geo64 G, ColArgs a) {
       const double rho_n = a.rx[o + k] - dtb * r;
       const double thv_n = Th_n * recip64(rho_n);
       if (a.corrector) {
+        // (beta wn + (1 - beta) wold - wcc) / nsub with the weights divided on the host
         const double wold = a.w[o + k];
-        double wc = kBeta * wn + (1.0 - kBeta) * wold;
-        if (TOPO) wc -= G.t_wcc[o + k];
-        a.wflx[o + k] = a.wflx[o + k] + ri * wc * a.inv_nsub;
+        double wc = fma(a.b_new, wn, a.b_old * wold);
+        if (TOPO) wc = fma(-a.inv_nsub, G.t_wcc[o + k], wc);
+        a.wflx[o + k] = fma(ri, wc, a.wflx[o + k]);
       }
       a.rho_o[o + k] = rho_n;
       a.thv_o[o + k] = thv_n;
@@ -837,6 +840,8 @@ void enqueue_step_fp64(icon_state* st, double dt, int nsub, cudaStream_t stream)
       ca.status = s.status;
       ca.dtau = dtau; ca.inv_nsub = 1.0 / nsub; ca.corrector = corr;
       ca.hdtau = 0.5 * dtau;
+      ca.b_new = kBeta / nsub;
+      ca.b_old = (1.0 - kBeta) / nsub;
       prof_begin(stream, K_COLUMN);
       launch_column(G, ca, topo, stream);
       prof_end(stream);
