@@ -58,9 +58,9 @@ FP64_INSTR_PEAK = 152 * 2 * 2.07e9
 # counted from the kernel source and checked against ncu's executed counts
 # (profiles/ncu_fp64_column_edge_r2b6_l90.md, profiles/ncu_mixed_column_stencils_r2b6_l90.md).
 # FP64 step: rows kernel 28 (explicit predictors, linearised state equation) + 5 (half-level
-# interpolants) + 24 (w predictor and tridiagonal row), Thomas 9, update 11 (corrector 16);
-# executed 71.8 (predictor) and 77.7 (corrector).
-COLUMN_FP64_OPS = 75
+# interpolants) + 23 (w predictor and tridiagonal row), Thomas 9, update 11 (corrector 15);
+# executed 70.8 (predictor) and 75.8 (corrector).
+COLUMN_FP64_OPS = 73
 # mixed step with stored factors: predictor 42 (one downward sweep forming and factoring
 # the rows, 39; the upward back substitution and damping, 3, with the provisional state's
 # FP32 shadows formed in FP32), corrector 28 (right-hand side, substitution, FP64 updates,
