@@ -9,6 +9,7 @@ import pytest
 import oracle as O
 import oracle.terrain as T
 from oracle.state import GRAV, CPD, RD, CVD, P0, to_half_w, _latlon_basis
+from oracle.dycore import divergence, tangential
 
 R = O.R_EARTH
 
@@ -217,3 +218,37 @@ def test_fewest_levels_conserve_mass(nlev):
     assert abs(T.terrain_mass(g, t, s1) / T.terrain_mass(g, t, s) - 1.0) < 1e-13
     assert all(np.all(np.isfinite(s1[k])) for k in s1)
     assert np.max(np.abs(s1["vn"] - s["vn"])) > 1e-2
+
+
+def _layer_budget_residual(bis, flat_dz=False, sign=1.0):
+    """Mass budget of the interior layers for a divergence-free wind (zonal solid-body
+    rotation, uniform density) over the mountain with w = 0: the thickness-weighted
+    horizontal divergence against the contravariant fluxes -wcc through the sloping layer
+    surfaces. Returns (relative L2 over the mountain's cells, max abs)."""
+    g = O.build_grid(2, bis)
+    v = O.vertical_grid(20)
+    t = T.terrain_geometry(g, v, T.mountain(g.x_c, 1500.0, 800e3))
+    cphi, _, el, _ = _latlon_basis(g.x_e)
+    ue = (20.0 * cphi)[:, None] * el
+    vn = np.repeat(np.sum(ue * g.n_e, 1)[:, None], v.N, 1)
+    wcc = sign * T.contravariant_correction(g, t, vn, tangential(g, vn))
+    dz_e = np.broadcast_to(v.dz[None, :], vn.shape) if flat_dz else t.dz_e
+    D = divergence(g, vn * dz_e)[:, :v.N - 1]                     # layers above the lowest
+    R = D - wcc[:, :v.N - 1] + wcc[:, 1:v.N]
+    on = t.hs > 1.0
+    return np.sqrt(np.sum(R[on] ** 2) / np.sum(D[on] ** 2)), np.abs(R).max()
+
+
+def test_layer_mass_budget_closes_for_a_divergence_free_wind():
+    """Geometric conservation of the metric terms: in the continuum the layer's horizontal
+    divergence of u dz equals u . grad(dz), which the contravariant fluxes -u . grad(z)
+    through its top and bottom cancel. Discretely the residual relative to the divergence
+    falls at first order (measured 0.28, 0.17, 0.087 on R2B2..R2B4); without the thickness
+    weighting the residual does not fall, and with the correction's sign flipped the ratio
+    stays near 2."""
+    r = [_layer_budget_residual(b)[0] for b in (2, 3, 4)]
+    assert all(np.log2(r[i] / r[i + 1]) > 0.6 for i in range(2)), r
+    assert r[-1] < 0.1
+    flat = [_layer_budget_residual(b, flat_dz=True)[1] for b in (2, 4)]
+    assert flat[1] > 0.8 * flat[0]
+    assert _layer_budget_residual(4, sign=-1.0)[0] > 1.5
