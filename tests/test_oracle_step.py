@@ -171,3 +171,150 @@ def test_w_conditioning():
     assert np.sqrt(np.mean((b["w"] - a["w"]) ** 2)) < w_bound(300.0, 5, 1)
     for f in ("vn", "rho", "theta_v", "exner"):
         assert rel(b[f], a[f]) < 1e-14
+
+
+# ------------------------------------------------------------------ vertical advection and the linearised
+# state equation, pinned against the mathematics (a mistake planted in the oracle fails these)
+import inspect
+
+
+def _planted(module, func, old, new, count=1):
+    """A copy of module.func with the source text `old` replaced by `new` (a planted mistake)."""
+    src = inspect.getsource(getattr(module, func))
+    assert src.count(old) == count, (func, old)
+    ns = dict(vars(module))
+    exec(compile(src.replace(old, new), "<planted %s>" % func, "exec"), ns)
+    return ns[func]
+
+
+def _linear_column_state(g, v, b_vn, c_w, d_w):
+    """Horizontally uniform column state: vn = 3 + b_vn z at every edge (full levels), w = c_w + d_w z
+    at every cell (half levels); the scalars are irrelevant to the tendencies."""
+    vn = np.repeat((3.0 + b_vn * v.z_f)[None, :], g.ne, axis=0)
+    w = np.repeat((c_w + d_w * v.z_h)[None, :], g.nc, axis=0)
+    return {"vn": vn, "w": w}
+
+
+def _vertical_advection_errors(tend, g, v, flat_terrain=None):
+    """Max deviation of the vertical advection terms of `tend` from -w dvn/dz and -w dw/dz
+    (momentum equation in advective form, z upward) for linear profiles, where the centred
+    differences and the linear interpolation to half levels are exact. The vn term is the
+    difference of A_vn with and without w (the horizontal terms do not depend on w). The
+    terrain-following form advects with the contravariant velocity, which is 0 at the lid and
+    the ground by definition (R-Z4); the layers next to them then see half their w."""
+    N = v.N
+    b, c, d = 2.0e-3, 0.3, -1.5e-5              # dvn/dz (1/s), w = c + d z
+    s = _linear_column_state(g, v, b, c, d)
+    s0 = dict(s, w=np.zeros_like(s["w"]))
+    call = (lambda st: tend(g, v, st)) if flat_terrain is None else (lambda st: tend(g, v, flat_terrain, st))
+    A_vn, A_w = call(s)[:2]
+    A_vn0 = call(s0)[0]
+    wh = c + d * v.z_h
+    if flat_terrain is not None:
+        wh[0] = wh[N] = 0.0
+    wbar = 0.5 * (wh[:-1] + wh[1:])              # mean of the two half-level w of a layer
+    exp_vn = -wbar * b
+    # top and bottom full levels: the half level outside takes the adjacent full value (R-B1),
+    # so the one-layer difference sees half the gradient there
+    exp_vn_edge = -wbar * b / 2.0
+    dvn = A_vn - A_vn0
+    err_vn = max(np.abs(dvn[:, 1:N - 1] - exp_vn[None, 1:N - 1]).max(),
+                 np.abs(dvn[:, [0, N - 1]] - exp_vn_edge[None, [0, N - 1]]).max())
+    exp_w = -(c + d * v.z_h[1:N]) * d             # -w dw/dz at the interior half levels
+    err_w = np.abs(A_w[:, 1:N] - exp_w[None, :]).max()
+    scale_vn = np.abs(exp_vn).max()
+    scale_w = np.abs(exp_w).max()
+    return err_vn / scale_vn, err_w / scale_w
+
+
+def test_vertical_advection_matches_the_advective_form():
+    g = O.build_grid(2, 0)
+    v = O.vertical_grid(20)
+    e_vn, e_w = _vertical_advection_errors(D.tendencies, g, v)
+    assert e_vn < 1e-10 and e_w < 1e-12, (e_vn, e_w)
+
+
+def test_vertical_advection_of_the_terrain_oracle_over_flat_ground():
+    from oracle import terrain as T
+    g = O.build_grid(2, 0)
+    v = O.vertical_grid(20)
+    t = T.terrain_geometry(g, v, np.zeros(g.nc))
+    e_vn, e_w = _vertical_advection_errors(T.tendencies, g, v, flat_terrain=t)
+    assert e_vn < 1e-10 and e_w < 1e-12, (e_vn, e_w)
+
+
+@pytest.mark.parametrize("old,new,which", [
+    ("- wbar * (vn_ie[:, :N] - vn_ie[:, 1:])", "+ wbar * (vn_ie[:, :N] - vn_ie[:, 1:])", 0),
+    ("- w[:, 1:N] * (w[:, 0:N - 1]", "+ w[:, 1:N] * (w[:, 0:N - 1]", 1),
+    # the single-interval denominator printed in the survey's O7 (the centred difference spans two)
+    ("(v.z_h[0:N - 1] - v.z_h[2:N + 1])", "(v.z_f[0:N - 1] - v.z_f[1:N])", 1),
+])
+def test_planted_vertical_advection_mistakes_fail(old, new, which):
+    g = O.build_grid(2, 0)
+    v = O.vertical_grid(20)
+    bad = _planted(D, "tendencies", old, new)
+    errs = _vertical_advection_errors(bad, g, v)
+    assert errs[which] > 0.3, errs
+
+
+def _state_equation_residual(substep, g, v, s, dtau, terrain=None):
+    """max |pi - (Rd rho theta_v / p0)^(Rd/cvd)| / pi after one predictor-corrector substep."""
+    acc = {"mflx": np.zeros((g.ne, v.N)), "wflx": np.zeros((g.nc, v.N + 1))}
+    if terrain is None:
+        s1 = substep(g, v, s, dtau, 1, acc)
+    else:
+        s1 = substep(g, v, terrain, s, dtau, 1, acc)
+    eos = (S.RD * s1["rho"] * s1["theta_v"] / S.P0) ** (S.RD / S.CVD)
+    return np.abs(s1["exner"] / eos - 1.0).max()
+
+
+def _moving_state(g, v, terrain=None):
+    """Solid-body rotation with theta_v noise and a smooth vertical velocity, so that both the
+    explicit and the implicit vertical fluxes change Theta at first order in dtau."""
+    s = O.init_state(g, v, 3, O.CASE_SBR, noise_K=0.05, terrain=terrain)
+    zz = v.z_h / v.z_top
+    w = 0.4 * np.sin(np.pi * zz)[None, :] * (1.0 + 0.5 * g.x_c[:, 0:1])
+    return dict(s, w=w)
+
+
+def _orders(substep, g, v, s, terrain=None, dtaus=(20.0, 10.0, 5.0)):
+    r = [_state_equation_residual(substep, g, v, s, dt, terrain) for dt in dtaus]
+    return [r[i] / r[i + 1] for i in range(len(r) - 1)], r
+
+
+def test_linearised_state_equation_is_second_order():
+    """The column updates Exner by the state equation linearised about S^n,
+    pi^{n+1} - pi^n = (Rd/cvd)(pi/Theta)(Theta^{n+1} - Theta^n); the state equation itself,
+    pi = (Rd rho theta_v/p0)^(Rd/cvd), then holds up to a residual quadratic in the increment:
+    halving dtau divides it by about 4."""
+    g = O.build_grid(2, 0)
+    v = O.vertical_grid(20)
+    s = _moving_state(g, v)
+    eos0 = (S.RD * s["rho"] * s["theta_v"] / S.P0) ** (S.RD / S.CVD)
+    assert np.abs(s["exner"] / eos0 - 1.0).max() < 1e-14
+    ratios, r = _orders(D.substep, g, v, s)
+    assert all(3.5 < q < 4.5 for q in ratios), (ratios, r)
+
+
+def test_linearised_state_equation_is_second_order_over_terrain():
+    from oracle import terrain as T
+    g = O.build_grid(2, 0)
+    v = O.vertical_grid(20)
+    t = T.terrain_geometry(g, v, T.mountain(g.x_c, 1500.0, 1.5e6))
+    s = _moving_state(g, v, terrain=t)
+    ratios, r = _orders(T.substep, g, v, s, terrain=t)
+    assert all(3.5 < q < 4.5 for q in ratios), (ratios, r)
+
+
+@pytest.mark.parametrize("old,new", [
+    ("ex_x = ex + (RD / CVD)", "ex_x = ex + (RD / CPD)"),
+    ("gam = (RD / CVD)", "gam = (RD / CPD)"),
+])
+def test_planted_state_equation_mistakes_fail(old, new, monkeypatch):
+    """With Rd/cpd in place of Rd/cvd in either place the residual is first order in dtau."""
+    g = O.build_grid(2, 0)
+    v = O.vertical_grid(20)
+    s = _moving_state(g, v)
+    monkeypatch.setattr(D, "column", _planted(D, "column", old, new))
+    ratios, r = _orders(D.substep, g, v, s)
+    assert all(q < 2.6 for q in ratios), (ratios, r)
