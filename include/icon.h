@@ -176,7 +176,21 @@ void icon_grid_free(icon_grid* grid);
 /* Create a state on `grid` with the analytic initial condition `case_id`
  * (icon_case), FP64 precision and default parameters. seed selects the theta_v
  * noise and, for ICON_CASE_MEMBER, the member's bump (SplitMix64 draws). The
- * state borrows the grid, which must outlive it. */
+ * state borrows the grid, which must outlive it.
+ *
+ * What it computes: the paper's runs start from reanalysis and spun-up states on the
+ * R2B8/R2B11 grids with 90 levels (Sec. "How Performance Was Measured", Table 2), which
+ * are not available; this call stands in for them with analytic balanced states. The
+ * prognostic set is the nonhydrostatic one of Sec. "Current State of the Art": edge-normal
+ * velocity vn, vertical velocity w at half levels, density rho, virtual potential
+ * temperature theta_v and Exner pressure pi. Readings (the paper prints none of them):
+ * theta_v from the analytic case; pi analytic at the lowest full level and integrated
+ * upward in discrete hydrostatic balance pi_{k-1} = pi_k - g dzh_k/(cpd theta_ic,k);
+ * rho = p0 pi^(cvd/Rd)/(Rd theta_v); vn = u.n_e at edge midpoints; w = 0. Noise
+ * theta_v += a(2U - 1), U from SplitMix64 draw (cell*N + k), pi held fixed. Layout and
+ * precision: the state lives in device memory only (FP64 [entity][ld] rows; a mixed
+ * state keeps vn in FP32 and rho, theta_v, pi, w level-major). Errors: ICON_EINVAL for a
+ * NULL grid or out, an unknown case or nlev < 2; ICON_ENOMEM if the state does not fit. */
 int icon_state_init(const icon_grid* grid, uint64_t seed, int case_id, icon_state** out);
 
 /* As icon_state_init with explicit parameters (params may be NULL).
@@ -196,7 +210,21 @@ int icon_state_init_ex(const icon_grid* grid, uint64_t seed, int case_id,
  * with icon_state_set_option apply. The first call for a given (dt, nsubsteps)
  * records a CUDA graph of the step (again after an option or tracers are added);
  * later calls replay it. Waits for completion and returns ICON_ENONFINITE if a
- * non-finite value was produced. dt > 0, 1 <= nsubsteps <= 64. */
+ * non-finite value was produced. dt > 0, 1 <= nsubsteps <= 64.
+ *
+ * What it computes: the time step of the nonhydrostatic dynamical core on the
+ * icosahedral-triangular C grid (Sec. "Current State of the Art"; the dycore is the
+ * dominant, memory-bound part of the atmosphere, Sec. "Separation of Concerns"), with
+ * the operators the paper names only by their stencils (triangles, dual hexagons and
+ * pentagons). The discretisation is this library's reading, since the paper prints
+ * none: edge-normal gradient, cell divergence, vertex curl, Perot tangential velocity,
+ * kinetic-energy and vorticity-flux advection of vn, advection of w; per substep a
+ * predictor (tendencies at S^n, horizontally explicit vn update, column solve) and a
+ * corrector (averaged tendencies, pressure gradient at the predicted state, column
+ * solve); the column is a tridiagonal system in w at the interior half levels with
+ * off-centring beta = 0.65, Exner from the state equation linearised about S^n, rho,
+ * Theta = rho theta_v updated in flux form, Rayleigh damping of w near the lid; after
+ * the substeps a Smagorinsky diffusion of vn and theta_v. */
 int icon_dycore_step(icon_state* state, double dt, int nsubsteps);
 
 /* As icon_dycore_step without waiting: enqueues the step on the bound stream and
@@ -207,8 +235,14 @@ int icon_dycore_step_async(icon_state* state, double dt, int nsubsteps);
  * call produced a non-finite value (the flag is then cleared), else ICON_OK. */
 int icon_state_status(icon_state* state);
 
-/* Total air mass  sum_c A_c sum_k dz_k rho_ck  in kg, FP64, deterministic
- * (fixed summation order, bit-identical between calls on the same device). */
+/* Total air mass  sum_c A_c sum_k dz_ck rho_ck  in kg, FP64, deterministic
+ * (fixed summation order, bit-identical between calls on the same device). dz_ck is
+ * the layer thickness of cell c (the flat levels' dz_k on flat ground, each column's
+ * own thickness on terrain-following levels). The air mass is the conserved quantity
+ * of the flux-form continuity equation of the step; the paper's model is run for the
+ * full Earth system, whose atmosphere must conserve it (Sec. "Overview of the
+ * Problem"); the FP64 sum is the precision the paper's model computes in. Errors:
+ * ICON_EINVAL for a NULL argument; ICON_ECUDA if a launch fails. */
 int icon_global_mass(const icon_state* state, double* out);
 
 /* As icon_global_mass without waiting: enqueues the reduction and an asynchronous
@@ -225,23 +259,31 @@ int icon_global_mass_async(const icon_state* state, double* host_out);
  * allocator, or a latency-bound loop that forbids allocations after start-up.
  *
  * dev_rho is DEVICE memory holding the density of every cell of `grid`, row c at
- * dev_rho + c*ld, levels 0..N-1 used (ld >= N). The result, in kg, is written to
- * *host_out; the call waits for it. The geometry (cell areas, layer thickness)
- * comes from the grid. Same integral as icon_global_mass, summed per block of
- * 1024 cells in a fixed order (deterministic; it may differ from icon_global_mass
- * in the last bits because the grouping of the sum differs).
+ * dev_rho + c*ld, levels 0..N-1 used (ld >= N). dev_dz gives the layer thickness
+ * in m: NULL takes the grid's flat levels (dz_k, the same for every cell), which is
+ * right for a state on flat ground; a state on terrain-following levels needs its
+ * own per-cell thicknesses dz_ck, passed as DEVICE memory in the same [Nc][ld]
+ * layout as dev_rho (both pointers are only read). The result, in kg, is written to
+ * *host_out; the call waits for it. With the thicknesses of the state it is the
+ * integral icon_global_mass computes, summed per block of 1024 cells in a fixed
+ * order (deterministic; it may differ from icon_global_mass in the last bits
+ * because the grouping of the sum differs).
  *
  * Scratch: the partial sums live in one fixed array inside the library
  * (16384 partials, 128 KiB), which every GPU that loads the library holds until
  * the process exits. Hence at most 16,777,216 cells (R2B8 fits, R2B9 does not);
- * larger grids, ld < N, NULL pointers or more than 64 devices give ICON_EINVAL
- * with a message. Nothing is allocated and no allocating library routine is
- * called. The first call on a device looks up the array's device address (with
- * that device current); make that first call before any stream capture. Every
- * call on a device shares the array and overwrites it (each call rewrites every
- * partial it reads), so calls that overlap on the GPU, for instance from two
- * host threads or on two streams, race and must be serialised by the caller. */
-int icon_global_mass_noalloc(const icon_grid* grid, const double* dev_rho, int ld, double* host_out);
+ * larger grids, ld < N, NULL dev_rho or host_out, a grid built on another device
+ * than the current one, dev_rho or dev_dz not device memory of the current device,
+ * or more than 64 devices give ICON_EINVAL with a message (the pointer check is a
+ * cudaPointerGetAttributes query, which allocates nothing). Nothing is allocated
+ * and no allocating library routine is called. The first call on a device looks
+ * up the array's device address (with that device current); make that first call
+ * before any stream capture. Every call on a device shares the array and
+ * overwrites it (each call rewrites every partial it reads), so calls that overlap
+ * on the GPU, for instance from two host threads or on two streams, race and must
+ * be serialised by the caller. */
+int icon_global_mass_noalloc(const icon_grid* grid, const double* dev_rho, const double* dev_dz, int ld,
+                             double* host_out);
 
 /* Copy a field (icon_field) to host memory as FP64, [entity][level] unpadded;
  * count must equal the field's element count. Synchronous. */
@@ -271,6 +313,14 @@ int icon_dycore_step_profile(icon_state* state, double dt, int nsubsteps, double
  * 2 ulps for a * (1/x)). *failures receives the number of mismatches (0 expected).
  * Allocates 4 bytes with cudaMalloc (not the registered allocator). Waits. */
 int icon_selftest(long long n, unsigned* failures);
+
+/* Measured FP64 instruction throughput of the current device, instructions per second
+ * (a fused multiply-add counts as one), for FP64 fused multiply-adds and for FP64 adds:
+ * 16 blocks of 256 threads per SM, eight independent dependency chains per thread, best
+ * of five timed launches (CUDA events on the bound stream). This is the peak the FP64-bound
+ * kernels of the step are measured against (no counterpart in the paper). Allocates 8
+ * bytes with cudaMalloc (not the registered allocator). Waits. */
+int icon_probe_fp64_rate(double* fma_per_s, double* add_per_s);
 
 /* Name of kernel kind i (0 <= i < ICON_KIND_COUNT), or NULL. Mixed-precision
  * stencil kinds: 10 vertex, 11 edge diagnostics, 12 cell kinetic energy,
@@ -331,6 +381,58 @@ int icon_state_tracers(const icon_state* state, int* ntracers);
  * laid out [cell][level] (level 0 at the top), else ICON_EINVAL. Synchronous. */
 int icon_state_set_tracer(icon_state* state, int t, const double* host_src, size_t count);
 int icon_state_copy_tracer(const icon_state* state, int t, double* host_dst, size_t count);
+
+/* ---------------------------------------------------------------- domain decomposition */
+
+/* Horizontal domain decomposition of the FP64 step with halo exchanges (the paper runs
+ * the atmosphere decomposed over many GPUs and exchanges subdomain halos point to point
+ * after its stencil phases, Sec. "Exploiting the Earth System's Complexity to Flexibly
+ * Utilize System Parallelism"). Part p of P owns the contiguous range [p Nc/P, (p+1) Nc/P)
+ * of the Morton cell order, the edges whose first (lower-id) cell it owns and the
+ * vertices whose lowest incident cell it owns; its local grid adds every cell within
+ * halo_rings vertex rings of its own cells, with their edges and vertices. Local order:
+ * owned entities first, then halo entities, each ascending in global id. */
+typedef struct icon_domain icon_domain;
+
+/* Host-only plan of one part from the global connectivity (ICON_T_C2E, ICON_T_E2C,
+ * ICON_T_C2V, ICON_T_V2C, ICON_T_VDEG tables in host memory, as icon_grid_copy_table
+ * writes them). host_counts[6] receives the owned cells, edges, vertices and the local
+ * cells, edges, vertices. If host_local is not NULL it receives the local-to-global ids
+ * (local cells, then edges, then vertices; sum of the local counts entries), and
+ * host_owner / host_owner_index (same length, may be NULL) the owning part of each local
+ * entity and its index in that part's local order. 1 <= nparts <= Nc, 0 <= part < nparts,
+ * 0 <= halo_rings <= 16, else ICON_EINVAL. Allocates nothing on the device. */
+int icon_partition_plan(int64_t nc, int64_t ne, int64_t nv, const int32_t* host_c2e, const int32_t* host_e2c,
+                        const int32_t* host_c2v, const int32_t* host_v2c, const int32_t* host_vdeg, int nparts,
+                        int part, int halo_rings, int64_t* host_counts, int32_t* host_local, int32_t* host_owner,
+                        int32_t* host_owner_index);
+
+/* Decompose an FP64 state on flat levels without tracers or options into nparts parts
+ * (1..64) with halo_rings (3..16) vertex rings of halo, on the current device: each part
+ * gets its local grid (connectivity remapped, geometry gathered) and a state holding its
+ * local rows of the global state's fields. The global state is only read; the domain
+ * keeps a pointer to its grid, which must outlive it. ICON_EINVAL for other states. */
+int icon_domain_create(const icon_state* global_state, int nparts, int halo_rings, icon_domain** out);
+
+/* One dycore step of every part (the kernels of icon_dycore_step on the local grids),
+ * with the halo rows of the stage outputs (vn; w, rho, theta_v, Exner) copied from their
+ * owners after each predictor and corrector stage and of vn, theta_v, Exner after the
+ * diffusion. The owned rows equal the single-domain step's bit for bit. Eager launches on
+ * the bound stream; waits; ICON_ENONFINITE as icon_dycore_step. */
+int icon_domain_step(icon_domain* domain, double dt, int nsubsteps);
+
+/* Air mass: each part's owned cells summed in a fixed order, the parts' sums added in
+ * part order (the scalar all-reduce of a distributed run). */
+int icon_domain_global_mass(icon_domain* domain, double* host_out);
+
+/* A field of the decomposed state in the global layout of icon_state_copy_field, from
+ * the owners' rows. Synchronous. */
+int icon_domain_copy_field(icon_domain* domain, int field_id, double* host_dst, size_t count);
+
+/* host_counts[6]: owned cells, edges, vertices and local cells, edges, vertices of a part. */
+int icon_domain_part_counts(const icon_domain* domain, int part, int64_t* host_counts);
+
+void icon_domain_free(icon_domain* domain);
 
 /* ---------------------------------------------------------------- ensemble */
 

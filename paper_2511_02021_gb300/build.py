@@ -29,6 +29,8 @@ SOURCES = {
     "dycore32.cu": [],
     "tracer.cu": [],
     "terrain.cu": [],
+    "probe.cu": [],
+    "domain.cu": [],
 }
 
 

@@ -70,7 +70,16 @@ def _load():
         "icon_dycore_step_profile": (I, [P, D, I, ctypes.POINTER(D), ctypes.POINTER(I)]),
         "icon_kernel_kind_name": (ctypes.c_char_p, [I]),
         "icon_selftest": (I, [ctypes.c_longlong, ctypes.POINTER(ctypes.c_uint)]),
-        "icon_global_mass_noalloc": (I, [P, P, I, ctypes.POINTER(D)]),
+        "icon_probe_fp64_rate": (I, [ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "icon_partition_plan": (I, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, P, P, P, P, P, I, I, I,
+                                    I64p, P, P, P]),
+        "icon_domain_create": (I, [P, I, I, ctypes.POINTER(P)]),
+        "icon_domain_step": (I, [P, D, I]),
+        "icon_domain_global_mass": (I, [P, ctypes.POINTER(D)]),
+        "icon_domain_copy_field": (I, [P, I, P, S]),
+        "icon_domain_part_counts": (I, [P, I, I64p]),
+        "icon_domain_free": (None, [P]),
+        "icon_global_mass_noalloc": (I, [P, P, P, I, ctypes.POINTER(D)]),
         "icon_state_copy_field": (I, [P, I, P, S]), "icon_state_set_field": (I, [P, I, P, S]),
         "icon_state_precision": (I, [P, ctypes.POINTER(I)]), "icon_state_free": (None, [P]),
         "icon_ensemble_create": (I, [ctypes.POINTER(P), I, ctypes.POINTER(P)]),
@@ -200,10 +209,12 @@ def icon_global_mass_async(state, host_ptr):
     _check(_lib.icon_global_mass_async(state, ctypes.c_void_p(host_ptr)))
 
 
-def icon_global_mass_noalloc(grid, dev_rho_ptr, ld):
-    """Mass of a caller-owned device density array [Nc][ld] without any device allocation."""
+def icon_global_mass_noalloc(grid, dev_rho_ptr, ld, dev_dz_ptr=0):
+    """Mass of a caller-owned device density array [Nc][ld] without any device allocation;
+    dev_dz_ptr (optional) the device array of per-cell layer thicknesses in the same layout."""
     m = ctypes.c_double()
-    _check(_lib.icon_global_mass_noalloc(grid, ctypes.c_void_p(dev_rho_ptr), ld, ctypes.byref(m)))
+    _check(_lib.icon_global_mass_noalloc(grid, ctypes.c_void_p(dev_rho_ptr), ctypes.c_void_p(dev_dz_ptr or None),
+                                         ld, ctypes.byref(m)))
     return m.value
 
 
@@ -231,6 +242,13 @@ def icon_selftest(n):
     f = ctypes.c_uint()
     _check(_lib.icon_selftest(n, ctypes.byref(f)))
     return f.value
+
+
+def icon_probe_fp64_rate():
+    """(FP64 FMA, FP64 ADD) instructions per second measured on the current device."""
+    f, a = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.icon_probe_fp64_rate(ctypes.byref(f), ctypes.byref(a)))
+    return f.value, a.value
 
 
 def icon_kernel_kind_name(kind):
@@ -341,3 +359,54 @@ ICON_OPT_DIVDAMP4, ICON_OPT_DIFF4, ICON_OPT_UPWIND_THETA = 1, 2, 3
 
 def icon_state_set_option(state, option, value):
     _check(_lib.icon_state_set_option(state, option, float(value)))
+
+
+# ---------------------------------------------------------------- domain decomposition
+def icon_partition_plan(c2e, e2c, c2v, v2c, vdeg, nparts, part, halo_rings):
+    """Host-only plan of one part: (counts[6], local ids, owner part, owner index), the
+    tables as int32 arrays in the layout of icon_grid_copy_table."""
+    arrs = [np.ascontiguousarray(a, dtype=np.int32) for a in (c2e, e2c, c2v, v2c, vdeg)]
+    nc, ne, nv = arrs[0].shape[0], arrs[1].shape[0], arrs[4].shape[0]
+    counts = np.zeros(6, dtype=np.int64)
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    I64p = ctypes.POINTER(ctypes.c_int64)
+    _check(_lib.icon_partition_plan(nc, ne, nv, *[ptr(a) for a in arrs], nparts, part, halo_rings,
+                                    counts.ctypes.data_as(I64p), None, None, None))
+    n = int(counts[3:].sum())
+    loc, own, oix = (np.zeros(n, dtype=np.int32) for _ in range(3))
+    _check(_lib.icon_partition_plan(nc, ne, nv, *[ptr(a) for a in arrs], nparts, part, halo_rings,
+                                    counts.ctypes.data_as(I64p), ptr(loc), ptr(own), ptr(oix)))
+    return counts, loc, own, oix
+
+
+def icon_domain_create(state, nparts, halo_rings):
+    h = ctypes.c_void_p()
+    _check(_lib.icon_domain_create(state, nparts, halo_rings, ctypes.byref(h)))
+    return h
+
+
+def icon_domain_step(domain, dt, nsubsteps):
+    _check(_lib.icon_domain_step(domain, dt, nsubsteps))
+
+
+def icon_domain_global_mass(domain):
+    m = ctypes.c_double()
+    _check(_lib.icon_domain_global_mass(domain, ctypes.byref(m)))
+    return m.value
+
+
+def icon_domain_copy_field(domain, grid, nlev, name):
+    fid, shape = _field_shape(grid, name, nlev)
+    out = np.empty(shape, dtype=np.float64)
+    _check(_lib.icon_domain_copy_field(domain, fid, out.ctypes.data, out.size))
+    return out
+
+
+def icon_domain_part_counts(domain, part):
+    c = np.zeros(6, dtype=np.int64)
+    _check(_lib.icon_domain_part_counts(domain, part, c.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+    return c
+
+
+def icon_domain_free(domain):
+    _lib.icon_domain_free(domain)

@@ -188,6 +188,44 @@ bool table_ref(const icon_grid* grid, int id, TableRef& t) {
   }
 }
 
+}  // namespace
+
+// the frozen parts of the column system that the stored-factor form keeps between the
+// predictor and the corrector (12 FP64 fields per half level) and its gathered inputs;
+// allocated when they take at most a quarter of the device memory (else the column
+// recomputes them). Returns true if the state has them afterwards.
+bool alloc_mixed_factors(icon_state* st) {
+  StateDev& s = st->s;
+  if (s.fac64) return true;
+  const int64_t nc = st->grid->g.nc;
+  const size_t ld0 = (size_t)st->grid->vert.N;
+  const size_t fac_bytes = (size_t)nc * (12 + 5) * (ld0 + 1) * 8;
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (fac_bytes > total_b / 4) return false;
+  DeviceArena& A = st->arena;
+  double* p[6];
+  const size_t H = (size_t)nc * (ld0 + 1);
+  p[0] = A.get_n<double>(H * 12);
+  for (int i = 1; i < 6; ++i) p[i] = p[0] ? A.get_n<double>(H) : nullptr;
+  if (A.failed) {
+    A.failed = false;          // the state stays usable without them
+    return false;
+  }
+  s.fac64 = p[0];
+  s.hdr = p[1];
+  s.hdt = p[2];
+  s.hdw = p[3];
+  s.hdg = p[4];
+  s.dps = p[5];
+  return true;
+}
+
+namespace {
+
 // allocate every buffer of a state; returns ICON_ENOMEM (arena then released by the caller)
 int alloc_state(icon_state* st, int precision, bool topo) {
   const icon_grid* grid = st->grid;
@@ -238,23 +276,35 @@ int alloc_state(icon_state* st, int precision, bool topo) {
     s.uvx32 = s.wv32; s.uvy32 = s.rho32_s; s.uvz32 = s.thv32_s;
     s.colconst = A.get_n<double>(8 * (size_t)ld);
     s.exref32 = A.get_n<float>(ld);
-    // stored frozen column parts: 10 FP64 fields per half level and 2 FP32 per level;
-    // kept when they take at most a quarter of the device memory
-    const size_t fac_bytes = (size_t)nc * (12 + 5) * (ld0 + 1) * 8;
-    size_t free_b = 0, total_b = 0;
-    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) total_b = 0;
+    // the column form: ICON_MIXED_COLUMN = "lean" (default), "stored" (the frozen parts of the
+    // column system stored by the predictor for the corrector, when they take at most a
+    // quarter of the device memory) or "recompute" (both stages compute them; also selected
+    // by ICON_MIXED_RECOMPUTE=1); on terrain-following levels the column always recomputes
+    // them (the stored forms freeze the explicit vertical fluxes, which there carry each
+    // stage's own contravariant correction)
+    const char* form = getenv("ICON_MIXED_COLUMN");
     const char* force_recompute = getenv("ICON_MIXED_RECOMPUTE");
-    const bool recompute = force_recompute && force_recompute[0] == '1' && force_recompute[1] == '\0';
-    // on terrain-following levels the column recomputes its factors (the stored-factor
-    // form freezes the explicit vertical fluxes, which there carry each stage's own
-    // contravariant correction)
-    if (fac_bytes <= total_b / 4 && !recompute && !topo) {
-      s.fac64 = A.get_n<double>((size_t)nc * 12 * (ld0 + 1));
-      s.hdr = A.get_n<double>((size_t)nc * (ld0 + 1));
-      s.hdt = A.get_n<double>((size_t)nc * (ld0 + 1));
-      s.hdw = A.get_n<double>((size_t)nc * (ld0 + 1));
-      s.hdg = A.get_n<double>((size_t)nc * (ld0 + 1));
-      s.dps = A.get_n<double>((size_t)nc * (ld0 + 1));
+    bool recompute = force_recompute && force_recompute[0] == '1' && force_recompute[1] == '\0';
+    bool stored = false;
+    if (form && strcmp(form, "recompute") == 0) recompute = true;
+    if (form && strcmp(form, "stored") == 0) stored = true;
+    if (!topo && !recompute && !stored) {
+      const size_t H = (size_t)nc * (ld0 + 1);
+      s.ln_dr64 = A.get_n<double>(H);
+      s.ln_dt32 = A.get_n<float>(H);
+      s.ln_aw32 = A.get_n<float>(H);
+      s.ln_B = A.get_n<double>(H);
+      s.ln_dp = A.get_n<double>(H);
+      s.ln_cp = A.get_n<float>(H);
+      s.ln_cd = A.get_n<double>(8 * (size_t)ld);
+      s.ln_cf = A.get_n<float>(8 * (size_t)ld);
+      s.ln_dwa = A.get_n<double>(3 * (size_t)nc);
+      int hd = 0;
+      for (int h = 0; h <= grid->vert.N; ++h)
+        if (grid->vert.rayleigh[h] > 0.0) hd = h + 1;
+      s.ln_hdamp = hd;
+    } else if (!topo && !recompute) {
+      alloc_mixed_factors(st);
     }
   }
   if (A.failed) {
@@ -426,6 +476,10 @@ int icon_grid_build(int root, int bisections, int nlev, icon_grid** out) {
   g->root = root;
   g->bisections = bisections;
   g->arena.al = current_allocator();
+  if (cudaGetDevice(&g->device) != cudaSuccess) {
+    cudaGetLastError();
+    g->device = -1;
+  }
   make_vertical(g->vert, nlev, -1, -1, -1);
   cudaStream_t st = current_stream();
   int rc = upload_vertical(g, st);

@@ -1192,6 +1192,390 @@ __global__ void __launch_bounds__(128) k_mx_diff_theta(MxGeo G, const float* thf
   if (c < G.nc) mx_diff_theta_item(G, thflx, thv, ex, thv32, exp32, dt, c, exref_c);
 }
 
+// ---------------------------------------------------------------- lean column (flat levels)
+//
+// The column of a mixed-precision state on flat levels in the fewest FP64 operations the
+// precision split allows. FP64 stays where the method needs it:
+//  * the hydrostatic residual of S^n in the w equation (a difference of two terms of size
+//    g), taken once per substep into the stage-independent base of the right-hand side
+//        B_h = w_h - dtau (cpd theta_ic,h (pi_{h-1} - pi_h) / dzh_h + g),
+//    with theta_ic in FP64;
+//  * the forward elimination and the back substitution of the tridiagonal w system;
+//  * the density update in flux form: the horizontal divergence of the FP32 mass fluxes
+//    summed with FP64 weights (gathered per stage), the vertical flux through each half
+//    level one FP32 number, differenced in FP64 (exact) and scaled in FP64, so the column
+//    and the global mass are conserved to FP64 rounding and the step-mean flux reproduces
+//    the density change;
+//  * the FP64 prognostics of S^{n+1} (rho, theta_v, Exner, w) and the step-mean vertical
+//    mass flux, each updated by one FP64 add.
+// Everything that only scales a small increment is FP32: the matrix rows and their LU
+// factors, the explicit (1 - beta) fluxes and the state-equation factor (Rd/cvd) pi/Theta,
+// the stage part of the right-hand side dtau A_w - a_h (dpi_{h-1} - dpi_h), and the
+// increments of Theta and Exner. The FP32 shadows are written through a per-warp
+// shared-memory transpose as whole level runs of each cell's [c][ld] row.
+// Per cell-level-substep: 6 (B) + 4 (elimination, substitution) + 1 (shadow) in the
+// predictor, 4 + 3 (density) + 1 (flux) + 2 (theta_v, Exner) + 1 (shadow) in the corrector,
+// plus 3 for the corrector's FP64 divergence: 26 FP64 instructions.
+
+// per-level constants of the lean column for one dtau: FP64 [LD_COUNT][ld], FP32 [LF_COUNT][ld]
+enum { LD_WU = 0, LD_WL, LD_CPDZH, LD_IDZ, LD_DAMP, LD_EXREF, LD_COUNT };
+enum { LF_WU = 0, LF_WL, LF_CA, LF_DT1, LF_DTB, LF_COUNT };
+
+__global__ void k_mx_leanconst(int N, int ld, const double* __restrict__ wu, const double* __restrict__ wl,
+                               const double* __restrict__ dzh, const double* __restrict__ dz,
+                               const double* __restrict__ ray, const double* __restrict__ ex_ref, double dtau,
+                               double* __restrict__ cd, float* __restrict__ cf) {
+  for (int i = threadIdx.x; i < ld; i += blockDim.x) {
+    const bool interior = i > 0 && i < N;
+    cd[LD_WU * ld + i] = interior ? wu[i] : 0.0;
+    cd[LD_WL * ld + i] = interior ? wl[i] : 0.0;
+    cd[LD_CPDZH * ld + i] = interior ? kCpd / dzh[i] : 0.0;
+    cd[LD_IDZ * ld + i] = i < N ? dtau / dz[i] : 0.0;
+    cd[LD_DAMP * ld + i] = i <= N ? 1.0 / (1.0 + dtau * ray[i]) : 1.0;
+    cd[LD_EXREF * ld + i] = i < N ? ex_ref[i] : 0.0;
+    cf[LF_WU * ld + i] = interior ? (float)wu[i] : 0.0f;
+    cf[LF_WL * ld + i] = interior ? (float)wl[i] : 0.0f;
+    cf[LF_CA * ld + i] = interior ? (float)(dtau * kBeta * kCpd / dzh[i]) : 0.0f;
+    cf[LF_DT1 * ld + i] = i < N ? (float)(dtau * (1.0 - kBeta) / dz[i]) : 0.0f;
+    cf[LF_DTB * ld + i] = i < N ? (float)(dtau * kBeta / dz[i]) : 0.0f;
+  }
+}
+
+struct MxLeanArgs {
+  // FP64 prognostics S^n (level-major [k][Nc]; updated in place by the corrector)
+  double *rho, *thv, *ex, *w, *wflx;
+  // FP32 edge inputs of the stage ([Ne][ld]) and the w shadow of the stage state ([Nc][ld])
+  const float *phi, *gth, *a_e, *w_stage;
+  float* Aw0;                              // level-major [h][Nc]: the predictor's A_w
+  // gathered per stage, level-major [k][Nc]: dtau D_rho (FP64 in the corrector; FP32 in the
+  // predictor, stored in the first half of the same buffer), dtau D_Theta, dtau A_w
+  double* dr64;
+  float *dr32, *dt32, *aw32;
+  double* B;                               // stage-independent right-hand-side base [h][Nc]
+  double* dp;                              // forward-elimination values [h][Nc]
+  float* cp;                               // LU factor up_h / pivot_h [h][Nc]
+  // FP32 shadows written by this stage, [Nc][ld]
+  float *rho32, *thv32, *exp32, *w32;
+  const double* cd;                        // per-level constants (FP64)
+  const float* cf;                         // per-level constants (FP32)
+  const double* dwa_t;                     // [Nc][3] dtau s l / A_c (FP64)
+  unsigned* status;
+  double dtau, inv_nsub;
+  int hdamp;                               // half levels h < hdamp are Rayleigh-damped
+};
+
+constexpr int kLeanChunk = 16;             // levels per shadow-transpose chunk
+struct LeanTile {
+  float t[4][kLeanChunk][33];              // rho, theta_v, pi - pi_ref, w of 32 columns
+};
+
+// gather of the lean column's stage inputs for 32 consecutive cells: lanes over levels
+// (LPE per cell), transposed through shared memory into level-major rows
+template <int LPE>
+struct LeanGatherTile {
+  double d[LPE][kGatherCells + 1];
+  float f[4][LPE][kGatherCells + 1];       // dtau D_Theta, dtau A_w, A_w (predictor), dtau D_rho (predictor)
+};
+
+template <int LPE, bool CORR>
+__device__ inline void mx_lean_gather_body(const MxGeo& G, const MxLeanArgs& a, int64_t c0, LeanGatherTile<LPE>& T) {
+  constexpr int CB = kGatherCells;
+  const int N = G.N, ld = G.ld;
+  const int64_t nc = G.nc;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int grp = tid / LPE, ngrp = nthr / LPE, lane = tid % LPE;
+  const float dtau32 = (float)a.dtau;
+  for (int k0 = 0; k0 < N; k0 += LPE) {
+    if (CORR) {
+      for (int i = tid; i < LPE * CB; i += nthr) {
+        const int r = i / CB, cl = i % CB, h = k0 + r;
+        const int64_t c = c0 + cl;
+        T.f[2][r][cl] = (h >= 1 && h < N && c < nc) ? a.Aw0[(int64_t)h * nc + c] : 0.0f;
+      }
+      __syncthreads();
+    }
+    for (int cl = grp; cl < CB; cl += ngrp) {
+      const int64_t c = c0 + cl;
+      if (c >= nc) break;
+      const int64_t o = c * ld;
+      int64_t E[3];
+      float sg[3], kw[3], dw32[3];
+      double dwt[3];
+      for (int s = 0; s < 3; ++s) {
+        E[s] = (int64_t)G.c2e[3 * c + s] * ld;
+        sg[s] = G.s_ce32[3 * c + s];
+        kw[s] = G.kin_w32[3 * c + s];
+        if (CORR) dwt[s] = a.dwa_t[3 * c + s];
+        else dw32[s] = (float)a.dwa_t[3 * c + s];
+      }
+      const float ta = dtau32 * (float)G.inv_Ac[c];
+      const int k = k0 + lane;
+      if (k < N) {
+        const float F0 = a.phi[E[0] + k], F1 = a.phi[E[1] + k], F2 = a.phi[E[2] + k];
+        if (CORR) T.d[lane][cl] = (dwt[0] * f32_to_f64(F0) + dwt[1] * f32_to_f64(F1)) + dwt[2] * f32_to_f64(F2);
+        else T.f[3][lane][cl] = (dw32[0] * F0 + dw32[1] * F1) + dw32[2] * F2;
+        T.f[0][lane][cl] = (sg[0] * a.gth[E[0] + k] + sg[1] * a.gth[E[1] + k] + sg[2] * a.gth[E[2] + k]) * ta;
+      }
+      if (k >= 1 && k < N) {
+        const float hadv = kw[0] * a.a_e[E[0] + k] + kw[1] * a.a_e[E[1] + k] + kw[2] * a.a_e[E[2] + k];
+        const float ws = a.w_stage[o + k];
+        float Aw = -hadv - ws * (a.w_stage[o + k - 1] - a.w_stage[o + k + 1]) * G.inv_dz2_32[k];
+        if (CORR) Aw = 0.5f * (T.f[2][lane][cl] + Aw);
+        else T.f[2][lane][cl] = Aw;
+        T.f[1][lane][cl] = dtau32 * Aw;
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < LPE * CB; i += nthr) {
+      const int r = i / CB, cl = i % CB, k = k0 + r;
+      const int64_t c = c0 + cl;
+      if (c >= nc || k >= N) continue;
+      const int64_t j = (int64_t)k * nc + c;
+      if (CORR) a.dr64[j] = T.d[r][cl];
+      else a.dr32[j] = T.f[3][r][cl];
+      a.dt32[j] = T.f[0][r][cl];
+      if (k >= 1) {
+        a.aw32[j] = T.f[1][r][cl];
+        if (!CORR) a.Aw0[j] = T.f[2][r][cl];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int LPE, bool CORR>
+__global__ void __launch_bounds__(512, 3) k_mx_lean_gather(MxGeo G, MxLeanArgs a) {
+  __shared__ LeanGatherTile<LPE> T;
+  mx_lean_gather_body<LPE, CORR>(G, a, (int64_t)blockIdx.x * kGatherCells, T);
+}
+
+// write the finished chunk [k0, k0 + kLeanChunk) of the warp's 32 columns (first cell c0)
+__device__ inline void lean_flush(const MxGeo& G, const MxLeanArgs& a, const LeanTile& T, int64_t c0, int k0,
+                                  int lane) {
+  __syncwarp();
+  const int r = lane & (kLeanChunk - 1), half = lane >> 4;
+  const int k = k0 + r;
+  float* const outs[4] = {a.rho32, a.thv32, a.exp32, a.w32};
+  if (k < G.N) {
+    for (int jj = 0; jj < 32; jj += 2) {
+      const int j = jj + half;
+      const int64_t c = c0 + j;
+      if (c >= G.nc) continue;
+      const int64_t o = c * G.ld + k;
+#pragma unroll
+      for (int f = 0; f < 4; ++f) outs[f][o] = T.t[f][r][j];
+    }
+  }
+  __syncwarp();
+}
+
+// one column per thread (lane); every lane of the warp runs the loops (lanes past the last
+// cell compute on zeros and store nothing) so that the chunk flushes stay warp-synchronous
+template <bool CORR>
+__device__ inline void mx_lean_column_item(const MxGeo& G, const MxLeanArgs& a, int64_t c, int64_t c0, int lane,
+                                           LeanTile& T) {
+  const int N = G.N, ld = G.ld;
+  const int64_t nc = G.nc;
+  const bool act = c < nc;
+  const int64_t cc = act ? c : 0;
+  const double* __restrict__ cd = a.cd;
+  const float* __restrict__ cf = a.cf;
+  const double dtau = a.dtau;
+#define LMV(p, k) (p)[(int64_t)(k) * nc + cc]
+  // ---- downward sweep: at step j half level j becomes known, completing full level
+  // k = j - 1 and, for k >= 1, the row of half level h = k
+  double thv1 = 0.0, ex1 = 0.0, ex2 = 0.0;          // full levels j-1 and j-2 (FP64)
+  float rho1f = 0.f, thv1f = 0.f;
+  double ti1 = 0.0;                                  // theta_ic at half level j-1 (FP64)
+  float ti1f = 0.f, M1 = 0.f, M2 = 0.f, w1f = 0.f;   // half level j-1 (and j-2 for M)
+  double w1 = 0.0;
+  float gam2 = 0.f, dpe2 = 0.f;                      // full level j-2
+  float cp_prev = 0.f;
+  double dp_prev = 0.0;
+  for (int j = 0; j <= N; ++j) {
+    double rho = 0.0, thv = 0.0, ex = 0.0;
+    if (j < N) {
+      rho = LMV(a.rho, j);
+      thv = LMV(a.thv, j);
+      ex = LMV(a.ex, j);
+    }
+    const float rhof = f64_to_f32(rho), thvf = f64_to_f32(thv);
+    double ti;
+    float rif;
+    if (j == 0) {
+      ti = thv;
+      rif = rhof;
+    } else if (j == N) {
+      ti = thv1;
+      rif = rho1f;
+    } else {
+      ti = cd[LD_WU * ld + j] * thv1 + cd[LD_WL * ld + j] * thv;
+      rif = cf[LF_WU * ld + j] * rho1f + cf[LF_WL * ld + j] * rhof;
+    }
+    const float tif = f64_to_f32(ti);
+    const float Mh = rif * tif;
+    const double wh = (j == 0 || j == N) ? 0.0 : LMV(a.w, j);
+    const float whf = f64_to_f32(wh);
+    float gam1 = 0.f, dpe1 = 0.f;
+    if (j >= 1) {
+      const int k = j - 1;
+      const float dthe = -LMV(a.dt32, k) - cf[LF_DT1 * ld + k] * (M1 * w1f - Mh * whf);
+      const float g = kRcvF * (f64_to_f32(ex1) / (rho1f * thv1f));
+      gam1 = g * cf[LF_DTB * ld + k];
+      dpe1 = g * dthe;
+      if (k >= 1) {
+        const int h = k;
+        const float aa = cf[LF_CA * ld + h] * ti1f;
+        const float lo = -aa * gam2 * M2;
+        const float di = 1.0f + aa * (gam2 + gam1) * M1;
+        const float up = -aa * gam1 * Mh;
+        double B;
+        if (!CORR) {
+          B = w1 - dtau * fma(cd[LD_CPDZH * ld + h] * ti1, ex2 - ex1, kGrav);
+          if (act) LMV(a.B, h) = B;
+        } else {
+          B = LMV(a.B, h);
+        }
+        const float inc = LMV(a.aw32, h) - aa * (dpe2 - dpe1);
+        const float piv = 1.0f / (di - lo * cp_prev);
+        const float cpv = up * piv;
+        const double dpv = (B + f32_to_f64(inc) - f32_to_f64(lo) * dp_prev) * f32_to_f64(piv);
+        if (act) {
+          LMV(a.dp, h) = dpv;
+          LMV(a.cp, h) = cpv;
+        }
+        cp_prev = cpv;
+        dp_prev = dpv;
+      }
+    }
+    gam2 = gam1;
+    dpe2 = dpe1;
+    M2 = M1;
+    M1 = Mh;
+    w1 = wh;
+    w1f = whf;
+    ti1 = ti;
+    ti1f = tif;
+    ex2 = ex1;
+    ex1 = ex;
+    thv1 = thv;
+    rho1f = rhof;
+    thv1f = thvf;
+  }
+  // ---- upward sweep: back substitution, damping and the update of full level k (between
+  // half levels k and k+1); the level above (k-1) is loaded one step ahead for the
+  // half-level interpolants
+  bool ok = true;
+  double x_next = 0.0, wn_next = 0.0;                // half level k+1: undamped, damped
+  float wnf_next = 0.f;
+  // half level k+1 quantities carried upward
+  float ri_next = 0.f, M_next = 0.f, wf_next = 0.f;  // at k+1 (w of S^n)
+  float fflux_next = 0.f;                            // corrector: vertical mass flux at k+1
+  // full level k (current) and k-1 (next), FP64 and FP32
+  double rho_k = act ? LMV(a.rho, N - 1) : 0.0, thv_k = act ? LMV(a.thv, N - 1) : 0.0;
+  double ex_k = act ? LMV(a.ex, N - 1) : 0.0;
+  {
+    // half level N: interpolants of the lowest full level, w = 0
+    ri_next = f64_to_f32(rho_k);
+    M_next = ri_next * f64_to_f32(thv_k);
+  }
+  const int64_t o = cc * ld;
+  for (int k = N - 1; k >= 0; --k) {
+    // half level k: the level above
+    double rho_u = 0.0, thv_u = 0.0, ex_u = 0.0;
+    if (k >= 1) {
+      rho_u = LMV(a.rho, k - 1);
+      thv_u = LMV(a.thv, k - 1);
+      ex_u = LMV(a.ex, k - 1);
+    }
+    const float rho_kf = f64_to_f32(rho_k), thv_kf = f64_to_f32(thv_k);
+    float ri_k, M_k;
+    if (k == 0) {
+      ri_k = rho_kf;
+      M_k = rho_kf * thv_kf;
+    } else {
+      const double ti = cd[LD_WU * ld + k] * thv_u + cd[LD_WL * ld + k] * thv_k;
+      ri_k = cf[LF_WU * ld + k] * f64_to_f32(rho_u) + cf[LF_WL * ld + k] * rho_kf;
+      M_k = ri_k * f64_to_f32(ti);
+    }
+    const float wf_k = k >= 1 ? f64_to_f32(LMV(a.w, k)) : 0.0f;
+    // back substitution at half level k
+    double x = 0.0, wn = 0.0;
+    if (k >= 1) {
+      x = LMV(a.dp, k) - f32_to_f64(LMV(a.cp, k)) * x_next;
+      wn = k < a.hdamp ? x * cd[LD_DAMP * ld + k] : x;
+    }
+    const float wnf = f64_to_f32(wn);
+    // full level k
+    const float dtb = cf[LF_DTB * ld + k], dt1 = cf[LF_DT1 * ld + k];
+    const float dthe = -LMV(a.dt32, k) - dt1 * (M_k * wf_k - M_next * wf_next);
+    const float g = kRcvF * (f64_to_f32(ex_k) / (rho_kf * thv_kf));
+    const float q = M_k * wnf - M_next * wnf_next;
+    const float dTh = dthe - dtb * q;                // Theta increment
+    const float dex = g * dthe - g * dtb * q;        // Exner increment (linearised state equation)
+    float s_rho, s_thv, s_exp;
+    if (!CORR) {
+      const float drho = -LMV(a.dr32, k) - dt1 * (ri_k * wf_k - ri_next * wf_next) -
+                         dtb * (ri_k * wnf - ri_next * wnf_next);
+      s_rho = rho_kf + drho;
+      s_thv = thv_kf + (dTh - drho * thv_kf) / s_rho;
+      s_exp = f64_to_f32(ex_k - cd[LD_EXREF * ld + k]) + dex;
+      ok = ok && isfinite(s_thv) && isfinite(s_exp) && isfinite(wnf);
+    } else {
+      // vertical mass flux through half level k of the step: rho_ic ((1 - beta) w^n + beta w^{n+1})
+      const float fk = ri_k * ((float)(1.0 - kBeta) * wf_k + (float)kBeta * wnf);
+      const double t = fma(cd[LD_IDZ * ld + k], f32_to_f64(fk) - f32_to_f64(fflux_next), LMV(a.dr64, k));
+      const double rho_n = rho_k - t;
+      const float rho_nf = f64_to_f32(rho_n);
+      const double thv_n = thv_k + f32_to_f64((dTh + f64_to_f32(t) * thv_kf) / rho_nf);
+      const double ex_n = ex_k + f32_to_f64(dex);
+      if (act) {
+        LMV(a.wflx, k) = fma(f32_to_f64(fk), a.inv_nsub, LMV(a.wflx, k));
+        LMV(a.rho, k) = rho_n;
+        LMV(a.thv, k) = thv_n;
+        LMV(a.ex, k) = ex_n;
+        LMV(a.w, k) = wn;
+      }
+      s_rho = rho_nf;
+      s_thv = f64_to_f32(thv_n);
+      s_exp = f64_to_f32(ex_n - cd[LD_EXREF * ld + k]);
+      ok = ok && finite64(thv_n) && finite64(ex_n) && finite64(wn);
+      fflux_next = fk;
+    }
+    const int k0 = k & ~(kLeanChunk - 1);
+    T.t[0][k - k0][lane] = s_rho;
+    T.t[1][k - k0][lane] = s_thv;
+    T.t[2][k - k0][lane] = s_exp;
+    T.t[3][k - k0][lane] = wnf;
+    if (k == k0) lean_flush(G, a, T, c0, k0, lane);
+    x_next = x;
+    wn_next = wn;
+    wnf_next = wnf;
+    ri_next = ri_k;
+    M_next = M_k;
+    wf_next = wf_k;
+    rho_k = rho_u;
+    thv_k = thv_u;
+    ex_k = ex_u;
+  }
+  (void)wn_next;
+  if (act) {
+    a.w32[o + N] = 0.0f;
+    if (CORR) LMV(a.w, N) = 0.0;                     // the ground (w^n there is 0 already)
+  }
+  if (!ok && act) atomicOr(a.status, 1u);
+#undef LMV
+}
+
+template <bool CORR>
+__global__ void __launch_bounds__(64) k_mx_lean_column(MxGeo G, MxLeanArgs a) {
+  __shared__ LeanTile T[2];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t c0 = (int64_t)blockIdx.x * 64 + warp * 32;
+  if (c0 >= G.nc) return;                            // whole warp past the end
+  mx_lean_column_item<CORR>(G, a, c0 + lane, c0, lane, T[warp]);
+}
+
 MxGeo make_mx_geo(const icon_grid* grid, const StateDev& s) {
   const GridDev& g = grid->g;
   const Vertical& v = grid->vert;
@@ -1261,6 +1645,38 @@ MxColArgs col_args(StateDev& s, bool corr, double dtau, int nsub) {
   return ca;
 }
 
+MxLeanArgs lean_args(StateDev& s, bool corr, double dtau, int nsub) {
+  MxLeanArgs la;
+  la.rho = s.rho; la.thv = s.thv; la.ex = s.ex; la.w = s.w; la.wflx = s.wflx;
+  la.phi = s.F32; la.gth = s.G32; la.a_e = s.ae32;
+  la.w_stage = corr ? s.w32_s : s.w32;
+  la.Aw0 = s.Aw0_32;
+  la.dr64 = s.ln_dr64;
+  la.dr32 = reinterpret_cast<float*>(s.ln_dr64);
+  la.dt32 = s.ln_dt32;
+  la.aw32 = s.ln_aw32;
+  la.B = s.ln_B;
+  la.dp = s.ln_dp;
+  la.cp = s.ln_cp;
+  la.rho32 = corr ? s.rho32 : s.rho32_s;
+  la.thv32 = corr ? s.thv32 : s.thv32_s;
+  la.exp32 = corr ? s.exp32 : s.exp32_s;
+  la.w32 = corr ? s.w32 : s.w32_s;
+  la.cd = s.ln_cd;
+  la.cf = s.ln_cf;
+  la.dwa_t = s.ln_dwa;
+  la.status = s.status;
+  la.dtau = dtau;
+  la.inv_nsub = 1.0 / nsub;
+  la.hdamp = s.ln_hdamp;
+  return la;
+}
+
+__global__ void k_mx_dwa_t(int64_t n3, const double* __restrict__ div_wa, double dtau, double* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n3) out[i] = dtau * div_wa[i];
+}
+
 // ---------------------------------------------------------------- launch helpers with tile choices
 unsigned item_blocks(int64_t n, int lpe, int block) {
   const int64_t per_block = (int64_t)(block / 32) * (32 / lpe);
@@ -1303,8 +1719,14 @@ void launch_kind(int kind, const TileChoice& t, const MxGeo& G, StateDev& s, con
       break;
     case K_MX_COLUMN_PREP: {   // the predictor's gather (the corrector's only differs in the Aw0 average)
       const unsigned nb = (unsigned)((G.nc + 31) / 32);
-      if (l16) k_mx_gather_tile<16, false><<<nb, B, 0, st>>>(G, ca);
-      else k_mx_gather_tile<32, false><<<nb, B, 0, st>>>(G, ca);
+      if (s.ln_B) {
+        const MxLeanArgs la = lean_args(s, false, (double)ea.dtau, 1);
+        if (l16) k_mx_lean_gather<16, false><<<nb, B, 0, st>>>(G, la);
+        else k_mx_lean_gather<32, false><<<nb, B, 0, st>>>(G, la);
+      } else {
+        if (l16) k_mx_gather_tile<16, false><<<nb, B, 0, st>>>(G, ca);
+        else k_mx_gather_tile<32, false><<<nb, B, 0, st>>>(G, ca);
+      }
       break;
     }
     case K_MX_DIFF_EDGE:
@@ -1399,7 +1821,7 @@ void autotune_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream) {
   load_tune_file();
   for (int kind : kTunedKinds) {
     if (st->tile[kind].lanes != 0 && st->tile_forced[kind]) continue;
-    if (kind == K_MX_COLUMN_PREP && !s.fac64) continue;
+    if (kind == K_MX_COLUMN_PREP && !s.fac64 && !s.ln_B) continue;
     const std::string key = tune_key(kind, G);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
@@ -1441,6 +1863,11 @@ void enqueue_step_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream
   cudaMemsetAsync(s.mflx, 0, sizeof(double) * G.ne * G.ld, stream);
   cudaMemsetAsync(s.wflx, 0, sizeof(double) * nc * (G.N + 1), stream);
   k_mx_colconst<<<1, 128, 0, stream>>>(G.N, G.ld, G.wu, G.wl, G.dzh, G.dz, G.ray, s.ex_ref, dtau, s.colconst);
+  const bool lean = s.ln_B != nullptr;
+  if (lean) {
+    k_mx_leanconst<<<1, 128, 0, stream>>>(G.N, G.ld, G.wu, G.wl, G.dzh, G.dz, G.ray, s.ex_ref, dtau, s.ln_cd, s.ln_cf);
+    k_mx_dwa_t<<<blocks_for(3 * nc, 256), 256, 0, stream>>>(3 * nc, G.div_wa, dtau, s.ln_dwa);
+  }
   auto tile = [&](int kind) { return st->tile[kind].lanes ? st->tile[kind] : TileChoice{32, 256}; };
   for (int it = 0; it < nsub; ++it) {
     for (int stage = 0; stage < 2; ++stage) {
@@ -1473,6 +1900,25 @@ void enqueue_step_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream
         k_mx_dd_lap<<<nbc8, 256, 0, stream>>>(G, s.Kc32, s.vt32);
         k_mx_dd_edge<<<nbe8, 256, 0, stream>>>(G, da);
         prof_end(stream);
+      }
+      if (lean) {
+        const MxLeanArgs la = lean_args(s, corr, dtau, nsub);
+        const TileChoice t = tile(K_MX_COLUMN_PREP);
+        const unsigned nb = (unsigned)((nc + 31) / 32);
+        prof_begin(stream, K_MX_COLUMN_PREP);
+        if (corr) {
+          if (t.lanes == 16) k_mx_lean_gather<16, true><<<nb, t.block, 0, stream>>>(G, la);
+          else k_mx_lean_gather<32, true><<<nb, t.block, 0, stream>>>(G, la);
+        } else {
+          if (t.lanes == 16) k_mx_lean_gather<16, false><<<nb, t.block, 0, stream>>>(G, la);
+          else k_mx_lean_gather<32, false><<<nb, t.block, 0, stream>>>(G, la);
+        }
+        prof_end(stream);
+        prof_begin(stream, K_MX_COLUMN);
+        if (corr) k_mx_lean_column<true><<<blocks_for(nc, 64), 64, 0, stream>>>(G, la);
+        else k_mx_lean_column<false><<<blocks_for(nc, 64), 64, 0, stream>>>(G, la);
+        prof_end(stream);
+        continue;
       }
       if (s.fac64) {
         const TileChoice t = tile(K_MX_COLUMN_PREP);
@@ -1849,6 +2295,9 @@ int ensemble_prepare(EnsembleDev& E, icon_state* const* members, int n, const do
       set_error("icon_ensemble_step: the persistent ensemble runs mixed-precision members");
       return ICON_EINVAL;
     }
+    // the persistent kernel runs the stored-factor column: give lean-form members its
+    // buffers (when they fit; otherwise that member's column recomputes its factors)
+    if (!s.fac64 && s.ln_B) alloc_mixed_factors(st);
     MemberDev& M = host[i];
     M.G = make_mx_geo(st->grid, s);
     if (N >= 0 && M.G.N != N) {

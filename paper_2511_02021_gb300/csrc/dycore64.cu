@@ -749,104 +749,122 @@ void launch_column(const Geo64& G, const ColArgs& a, bool topo, cudaStream_t st)
 
 }  // namespace
 
-void enqueue_step_fp64(icon_state* st, double dt, int nsub, cudaStream_t stream) {
-  const icon_grid* grid = st->grid;
-  StateDev& s = st->s;
-  Geo64 G = make_geo(grid, s.colconst);
+namespace {
+
+Geo64 state_geo(const icon_state* st) {
+  const StateDev& s = st->s;
+  Geo64 G = make_geo(st->grid, s.colconst);
   G.kin_w_h = s.kin_w_h;
   G.div_wa_h = s.div_wa_h;
   const TopoDev& T = s.topo;
-  const bool topo = T.on;
-  if (topo) {
+  if (T.on) {
     G.t_sn = T.sn; G.t_bf = T.bf; G.t_wu_e = T.wu_e; G.t_qinv_dz_e = T.qinv_dz_e; G.t_dz_e = T.dz_e;
     G.t_wu_c = T.wu_c; G.t_inv_dz_c = T.inv_dz_c; G.t_inv_dzh_c = T.inv_dzh_c;
     G.t_wcc = T.wcc; G.t_wcon = T.wcon; G.t_ep = T.ep; G.t_hdpdz = T.hdpdz;
   }
-  const int ld = G.ld;
+  return G;
+}
+
+}  // namespace
+
+// the parts of one FP64 step, in the order enqueue_step_fp64 issues them; a decomposed
+// domain issues them for every part with halo exchanges between the stages
+void fp64_step_begin(icon_state* st, double dt, int nsub, cudaStream_t stream) {
+  StateDev& s = st->s;
+  const Vertical& vg = st->grid->vert;
   const double dtau = dt / nsub;
-  const Vertical& vg = grid->vert;
   k_colconst64<<<1, 128, 0, stream>>>(vg.N, vg.ld, vg.d_wu, vg.d_wl, vg.d_dzh, vg.d_dz, vg.d_ray, dtau, s.colconst);
+  cudaMemsetAsync(s.mflx, 0, sizeof(double) * st->grid->g.ne * vg.ld, stream);
+  cudaMemsetAsync(s.wflx, 0, sizeof(double) * st->grid->g.nc * vg.ld, stream);
+}
+
+void fp64_step_stage(icon_state* st, double dt, int nsub, bool corr, cudaStream_t stream) {
+  StateDev& s = st->s;
+  const Geo64 G = state_geo(st);
+  const TopoDev& T = s.topo;
+  const bool topo = T.on;
+  const double dtau = dt / nsub;
   const unsigned nbv = blocks_for(G.nv, kWarpsPerBlock), nbe = blocks_for(G.ne, kWarpsPerBlock),
                  nbc = blocks_for(G.nc, kWarpsPerBlock);
-  cudaMemsetAsync(s.mflx, 0, sizeof(double) * G.ne * ld, stream);
-  cudaMemsetAsync(s.wflx, 0, sizeof(double) * G.nc * ld, stream);
-  for (int it = 0; it < nsub; ++it) {
-    for (int stage = 0; stage < 2; ++stage) {
-      const bool corr = stage == 1;
-      const double* vn_st = corr ? s.vn_s : s.vn;
-      const double* w_st = corr ? s.w_s : s.w;
-      const double* rho_st = corr ? s.rho_s : s.rho;
-      const double* thv_st = corr ? s.thv_s : s.thv;
-      const double* ex_st = corr ? s.ex_s : s.ex;
-      prof_begin(stream, K_VERTEX);
-      k_vertex<<<nbv, 256, 0, stream>>>(G, vn_st, w_st, s.zeta, s.w_v);
-      prof_end(stream);
-      prof_begin(stream, K_EDGE_VT);
-      k_edge_vt<<<nbe, 256, 0, stream>>>(G, vn_st, s.vt, s.Ke);
-      prof_end(stream);
-      prof_begin(stream, K_CELL_KE);
-      k_cell_ke<<<nbc, 256, 0, stream>>>(G, s.Ke, s.Kc);
-      prof_end(stream);
-      if (topo) topo_stage(st, vn_st, s.vt, w_st, ex_st, stream);
-      EdgeArgs ea;
-      ea.vn = vn_st; ea.w = w_st; ea.rho = rho_st; ea.thv = thv_st; ea.ex = ex_st;
-      ea.vt = s.vt; ea.Kc = s.Kc; ea.zeta = s.zeta; ea.w_v = s.w_v;
-      ea.vn_base = s.vn;
-      ea.vn_out = corr ? s.vn : s.vn_s;
-      ea.Avn0 = s.Avn0;
-      ea.F = s.F; ea.G = s.G; ea.a_e = s.a_e; ea.mflx = s.mflx;
-      ea.dtau = dtau; ea.inv_nsub = 1.0 / nsub; ea.corrector = corr;
-      ea.hinv_nsub = 0.5 / nsub;
-      const bool damp = corr && st->divdamp4 > 0.0;
-      ea.skip_flux = damp ? 1 : 0;
-      ea.upwind_theta = st->upwind_theta ? 1 : 0;
-      prof_begin(stream, K_EDGE_TEND);
-      if (topo) {
-        if (ea.upwind_theta) k_edge_tend<true, true><<<nbe, 256, 0, stream>>>(G, ea);
-        else k_edge_tend<true, false><<<nbe, 256, 0, stream>>>(G, ea);
-      } else {
-        if (ea.upwind_theta) k_edge_tend<false, true><<<nbe, 256, 0, stream>>>(G, ea);
-        else k_edge_tend<false, false><<<nbe, 256, 0, stream>>>(G, ea);
-      }
-      prof_end(stream);
-      if (damp) {
-        // Kc and the column's update-operand scratch are free until the column runs
-        const double abar = 4.0 * M_PI * kR * kR / (double)G.nc;
-        DDArgs da;
-        da.L = s.col_rx; da.rho = rho_st; da.thv = thv_st;
-        da.vn = s.vn; da.F = s.F; da.G = s.G; da.mflx = s.mflx;
-        da.dz_e = topo ? T.dz_e : nullptr;
-        da.scale = st->divdamp4 * abar * abar; da.inv_nsub = 1.0 / nsub;
-        da.upwind_theta = st->upwind_theta ? 1 : 0;
-        prof_begin(stream, K_DIVDAMP);
-        k_dd_div<<<nbc, 256, 0, stream>>>(G, s.vn, s.Kc);
-        k_dd_lap<<<nbc, 256, 0, stream>>>(G, s.Kc, s.col_rx);
-        k_dd_edge<<<nbe, 256, 0, stream>>>(G, da);
-        prof_end(stream);
-      }
-      ColArgs ca;
-      ca.rho = s.rho; ca.thv = s.thv; ca.ex = s.ex; ca.w = s.w;
-      ca.w_stage = w_st;
-      ca.F = s.F; ca.G = s.G; ca.a_e = s.a_e;
-      ca.Aw0 = s.Aw0;
-      ca.lo = s.col_lo; ca.di = s.col_di; ca.up = s.col_up; ca.rh = s.col_rh;
-      ca.rx = s.col_rx; ca.tx = s.col_tx; ca.px = s.col_px; ca.gm = s.col_gm;
-      ca.ri = s.col_ri; ca.mm = s.col_mm;
-      ca.rho_o = corr ? s.rho : s.rho_s;
-      ca.thv_o = corr ? s.thv : s.thv_s;
-      ca.ex_o = corr ? s.ex : s.ex_s;
-      ca.w_o = corr ? s.w : s.w_s;
-      ca.wflx = s.wflx;
-      ca.status = s.status;
-      ca.dtau = dtau; ca.inv_nsub = 1.0 / nsub; ca.corrector = corr;
-      ca.hdtau = 0.5 * dtau;
-      ca.b_new = kBeta / nsub;
-      ca.b_old = (1.0 - kBeta) / nsub;
-      prof_begin(stream, K_COLUMN);
-      launch_column(G, ca, topo, stream);
-      prof_end(stream);
-    }
+  const double* vn_st = corr ? s.vn_s : s.vn;
+  const double* w_st = corr ? s.w_s : s.w;
+  const double* rho_st = corr ? s.rho_s : s.rho;
+  const double* thv_st = corr ? s.thv_s : s.thv;
+  const double* ex_st = corr ? s.ex_s : s.ex;
+  prof_begin(stream, K_VERTEX);
+  k_vertex<<<nbv, 256, 0, stream>>>(G, vn_st, w_st, s.zeta, s.w_v);
+  prof_end(stream);
+  prof_begin(stream, K_EDGE_VT);
+  k_edge_vt<<<nbe, 256, 0, stream>>>(G, vn_st, s.vt, s.Ke);
+  prof_end(stream);
+  prof_begin(stream, K_CELL_KE);
+  k_cell_ke<<<nbc, 256, 0, stream>>>(G, s.Ke, s.Kc);
+  prof_end(stream);
+  if (topo) topo_stage(st, vn_st, s.vt, w_st, ex_st, stream);
+  EdgeArgs ea;
+  ea.vn = vn_st; ea.w = w_st; ea.rho = rho_st; ea.thv = thv_st; ea.ex = ex_st;
+  ea.vt = s.vt; ea.Kc = s.Kc; ea.zeta = s.zeta; ea.w_v = s.w_v;
+  ea.vn_base = s.vn;
+  ea.vn_out = corr ? s.vn : s.vn_s;
+  ea.Avn0 = s.Avn0;
+  ea.F = s.F; ea.G = s.G; ea.a_e = s.a_e; ea.mflx = s.mflx;
+  ea.dtau = dtau; ea.inv_nsub = 1.0 / nsub; ea.corrector = corr;
+  ea.hinv_nsub = 0.5 / nsub;
+  const bool damp = corr && st->divdamp4 > 0.0;
+  ea.skip_flux = damp ? 1 : 0;
+  ea.upwind_theta = st->upwind_theta ? 1 : 0;
+  prof_begin(stream, K_EDGE_TEND);
+  if (topo) {
+    if (ea.upwind_theta) k_edge_tend<true, true><<<nbe, 256, 0, stream>>>(G, ea);
+    else k_edge_tend<true, false><<<nbe, 256, 0, stream>>>(G, ea);
+  } else {
+    if (ea.upwind_theta) k_edge_tend<false, true><<<nbe, 256, 0, stream>>>(G, ea);
+    else k_edge_tend<false, false><<<nbe, 256, 0, stream>>>(G, ea);
   }
+  prof_end(stream);
+  if (damp) {
+    // Kc and the column's update-operand scratch are free until the column runs
+    const double abar = 4.0 * M_PI * kR * kR / (double)G.nc;
+    DDArgs da;
+    da.L = s.col_rx; da.rho = rho_st; da.thv = thv_st;
+    da.vn = s.vn; da.F = s.F; da.G = s.G; da.mflx = s.mflx;
+    da.dz_e = topo ? T.dz_e : nullptr;
+    da.scale = st->divdamp4 * abar * abar; da.inv_nsub = 1.0 / nsub;
+    da.upwind_theta = st->upwind_theta ? 1 : 0;
+    prof_begin(stream, K_DIVDAMP);
+    k_dd_div<<<nbc, 256, 0, stream>>>(G, s.vn, s.Kc);
+    k_dd_lap<<<nbc, 256, 0, stream>>>(G, s.Kc, s.col_rx);
+    k_dd_edge<<<nbe, 256, 0, stream>>>(G, da);
+    prof_end(stream);
+  }
+  ColArgs ca;
+  ca.rho = s.rho; ca.thv = s.thv; ca.ex = s.ex; ca.w = s.w;
+  ca.w_stage = w_st;
+  ca.F = s.F; ca.G = s.G; ca.a_e = s.a_e;
+  ca.Aw0 = s.Aw0;
+  ca.lo = s.col_lo; ca.di = s.col_di; ca.up = s.col_up; ca.rh = s.col_rh;
+  ca.rx = s.col_rx; ca.tx = s.col_tx; ca.px = s.col_px; ca.gm = s.col_gm;
+  ca.ri = s.col_ri; ca.mm = s.col_mm;
+  ca.rho_o = corr ? s.rho : s.rho_s;
+  ca.thv_o = corr ? s.thv : s.thv_s;
+  ca.ex_o = corr ? s.ex : s.ex_s;
+  ca.w_o = corr ? s.w : s.w_s;
+  ca.wflx = s.wflx;
+  ca.status = s.status;
+  ca.dtau = dtau; ca.inv_nsub = 1.0 / nsub; ca.corrector = corr;
+  ca.hdtau = 0.5 * dtau;
+  ca.b_new = kBeta / nsub;
+  ca.b_old = (1.0 - kBeta) / nsub;
+  prof_begin(stream, K_COLUMN);
+  launch_column(G, ca, topo, stream);
+  prof_end(stream);
+}
+
+void fp64_step_diffusion(icon_state* st, double dt, cudaStream_t stream) {
+  StateDev& s = st->s;
+  const Geo64 G = state_geo(st);
+  const unsigned nbv = blocks_for(G.nv, kWarpsPerBlock), nbe = blocks_for(G.ne, kWarpsPerBlock),
+                 nbc = blocks_for(G.nc, kWarpsPerBlock);
   prof_begin(stream, K_DIFF_VERTEX);
   k_diff_vertex<<<nbv, 256, 0, stream>>>(G, s.vn, s.uvx, s.uvy, s.uvz, s.zeta);
   prof_end(stream);
@@ -871,6 +889,13 @@ void enqueue_step_fp64(icon_state* st, double dt, int nsub, cudaStream_t stream)
   prof_begin(stream, K_DIFF_THETA);
   k_diff_theta<<<nbc, 256, 0, stream>>>(G, s.thflx, s.thv, s.ex, dt);
   prof_end(stream);
+}
+
+void enqueue_step_fp64(icon_state* st, double dt, int nsub, cudaStream_t stream) {
+  fp64_step_begin(st, dt, nsub, stream);
+  for (int it = 0; it < nsub; ++it)
+    for (int stage = 0; stage < 2; ++stage) fp64_step_stage(st, dt, nsub, stage == 1, stream);
+  fp64_step_diffusion(st, dt, stream);
 }
 
 }  // namespace icon

@@ -119,6 +119,7 @@ struct icon_grid {
   icon::GridDev g;
   icon::Vertical vert;
   int root = 2, bisections = 0;
+  int device = -1;        // CUDA device the grid's tables live on (current at build time)
 };
 
 namespace icon {
@@ -198,6 +199,14 @@ struct StateDev {
   double *hdr = nullptr, *hdt = nullptr, *hdw = nullptr, *hdg = nullptr;  // gathered column inputs, level-major
   double* dps = nullptr;      // Thomas scratch, level-major
   float* exref32 = nullptr;   // FP32 copy of the reference Exner profile
+  // lean column (mixed precision on flat levels, the default form): gathered stage inputs
+  // (dtau D_rho FP64 [k][Nc], its FP32 predictor copy in the same buffer, dtau D_Theta and
+  // dtau A_w FP32), the right-hand-side base, elimination values and LU factors [h][Nc],
+  // per-level constants and dtau s l / A_c per cell
+  double* ln_dr64 = nullptr;
+  float *ln_dt32 = nullptr, *ln_aw32 = nullptr, *ln_cp = nullptr, *ln_cf = nullptr;
+  double *ln_B = nullptr, *ln_dp = nullptr, *ln_cd = nullptr, *ln_dwa = nullptr;
+  int ln_hdamp = 0;           // half levels h < ln_hdamp lie in the Rayleigh layer
   // mass reduction partials and the device status word
   double *mass_part = nullptr;
   int mass_nblk = 0;
@@ -244,6 +253,8 @@ struct EnsembleDev {
 int ensemble_prepare(EnsembleDev& E, icon_state* const* members, int n, const double* dts, int nsub);
 int ensemble_launch(EnsembleDev& E, cudaStream_t st);
 void autotune_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream);
+// the stored-factor column parts of a mixed state (api.cu); false if they do not fit
+bool alloc_mixed_factors(icon_state* st);
 int selftest_conversions(int64_t n, unsigned* host_fails);
 }  // namespace icon
 
@@ -271,6 +282,9 @@ int init_state_device(icon_state* st, uint64_t seed, int case_id, const icon_cas
                       cudaStream_t stream);
 // dycore64.cu
 void enqueue_step_fp64(icon_state* st, double dt, int nsub, cudaStream_t stream);
+void fp64_step_begin(icon_state* st, double dt, int nsub, cudaStream_t stream);
+void fp64_step_stage(icon_state* st, double dt, int nsub, bool corr, cudaStream_t stream);
+void fp64_step_diffusion(icon_state* st, double dt, cudaStream_t stream);
 // dycore32.cu
 void enqueue_step_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream);
 // mixed-mode state from FP64 fields in [entity][ld] layout (init.cu)

@@ -11,7 +11,9 @@
 //   SBR    u = u0 cos(phi), u0 = 20 m/s, 250 K, in gradient balance:
 //          ln p = ln p0 - g z/(Rd T0) - (R Omega u0 + u0^2/2) sin^2(phi)/(Rd T0);
 //   jet    ln p = ln p0 - z/H0 - B S(z) Phi(phi), H0 = Rd T_j/g, T_j = 288 K,
-//          S = exp(-((z - 10 km)/8 km)^2), Phi = -4(cos^3/3 - cos^5/5),
+//          S = exp(-((z - 10 km)/10 km)^2), Phi = 4/15 - 4(cos^3/3 - cos^5/5)
+//          (Phi centred and the 10 km half-width keep the state statically stable:
+//          N^2 >= 1.4e-4 1/s^2 everywhere),
 //          T = g/(Rd (1/H0 + B S' Phi)), u the gradient-wind root continuous with
 //          geostrophy, B such that u = 35 m/s at 45 deg at z = 10 km, plus a
 //          Gaussian zonal bump amp exp(-(r/(R/10))^2) (1 m/s at 20E 40N, or a
@@ -105,12 +107,12 @@ __device__ void analytic(const CaseDev& cd, double x, double y, double zu, doubl
     T = T0;
     u = u0 * cphi;
   } else {
-    const double zj = 10000.0, hj = 8000.0;
+    const double zj = 10000.0, hj = 10000.0;
     double q = (zz - zj) / hj;
     double S = exp(-(q * q));
     double dS = -2.0 * (zz - zj) / (hj * hj) * S;
     double c3 = cphi * cphi * cphi, c5 = c3 * cphi * cphi;
-    double Phi = -4.0 * (c3 / 3.0 - c5 / 5.0);
+    double Phi = -4.0 * (c3 / 3.0 - c5 / 5.0) + 4.0 / 15.0;
     lnp = (log(kP0) - zz / cd.H0) - cd.B * S * Phi;
     T = kGrav / (kRd * (1.0 / cd.H0 + cd.B * dS * Phi));
     double c = (kRd * T / kR) * cd.B * S * (4.0 * (cphi * cphi) * (sphi * sphi));

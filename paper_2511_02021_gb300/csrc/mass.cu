@@ -125,10 +125,12 @@ constexpr int kNoAllocMaxDevices = 64;
 // partial sums [0, nblk) and the result [kNoAllocMaxPartials]; shared by every call
 static __device__ __align__(256) double g_mass_scratch[kNoAllocMaxPartials + 1];
 
-// block b sums the cells [b * 1024, (b + 1) * 1024) in a fixed order
+// block b sums the cells [b * 1024, (b + 1) * 1024) in a fixed order; the layer thickness
+// is per level (dz_lev[k], flat levels) or per cell and level (dz_cell[c * ld + k])
 __global__ void __launch_bounds__(kMassThreads) k_mass_partial_blocked(int64_t nc, int N, int ld,
                                                                        const double* __restrict__ rho,
-                                                                       const double* __restrict__ dz,
+                                                                       const double* __restrict__ dz_lev,
+                                                                       const double* __restrict__ dz_cell,
                                                                        const double* __restrict__ A_c,
                                                                        double* __restrict__ part) {
   __shared__ double ws[kMassThreads / 32];
@@ -138,7 +140,11 @@ __global__ void __launch_bounds__(kMassThreads) k_mass_partial_blocked(int64_t n
   double acc = 0.0;
   for (int64_t c = c0 + wid; c < c1; c += kMassThreads / 32) {
     double col = 0.0;
-    for (int k = lane; k < N; k += 32) col += rho[c * ld + k] * dz[k];
+    if (dz_cell) {
+      for (int k = lane; k < N; k += 32) col += rho[c * ld + k] * dz_cell[c * ld + k];
+    } else {
+      for (int k = lane; k < N; k += 32) col += rho[c * ld + k] * dz_lev[k];
+    }
     for (int o = 16; o > 0; o >>= 1) col += __shfl_xor_sync(0xffffffffu, col, o);
     acc += A_c[c] * col;
   }
@@ -151,6 +157,16 @@ __global__ void __launch_bounds__(kMassThreads) k_mass_partial_blocked(int64_t n
   }
 }
 
+// true if p is device (or managed) memory of device dev; the query allocates nothing
+bool device_pointer_on(const void* p, int dev) {
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged) && attr.device == dev;
+}
+
 std::once_flag g_noalloc_once[kNoAllocMaxDevices];
 double* g_noalloc_ptr[kNoAllocMaxDevices];
 cudaError_t g_noalloc_err[kNoAllocMaxDevices];
@@ -158,7 +174,8 @@ cudaError_t g_noalloc_err[kNoAllocMaxDevices];
 }  // namespace
 }  // namespace icon
 
-extern "C" int icon_global_mass_noalloc(const icon_grid* grid, const double* dev_rho, int ld, double* host_out) {
+extern "C" int icon_global_mass_noalloc(const icon_grid* grid, const double* dev_rho, const double* dev_dz, int ld,
+                                        double* host_out) {
   using namespace icon;
   if (!grid || !dev_rho || !host_out) {
     set_error("icon_global_mass_noalloc: NULL argument");
@@ -183,6 +200,16 @@ extern "C" int icon_global_mass_noalloc(const icon_grid* grid, const double* dev
     set_error("icon_global_mass_noalloc: device %d is beyond the %d supported devices", dev, kNoAllocMaxDevices);
     return ICON_EINVAL;
   }
+  if (grid->device != dev) {
+    set_error("icon_global_mass_noalloc: the grid was built on device %d but device %d is current", grid->device,
+              dev);
+    return ICON_EINVAL;
+  }
+  if (!device_pointer_on(dev_rho, dev) || (dev_dz && !device_pointer_on(dev_dz, dev))) {
+    set_error("icon_global_mass_noalloc: %s is not device memory of the current device %d",
+              device_pointer_on(dev_rho, dev) ? "dev_dz" : "dev_rho", dev);
+    return ICON_EINVAL;
+  }
   // once per device, with that device current: the device address of the scratch array
   std::call_once(g_noalloc_once[dev], [dev]() {
     g_noalloc_err[dev] = cudaGetSymbolAddress((void**)&g_noalloc_ptr[dev], g_mass_scratch);
@@ -191,8 +218,8 @@ extern "C" int icon_global_mass_noalloc(const icon_grid* grid, const double* dev
   double* scratch = g_noalloc_ptr[dev];
   const int nblk = (int)((nc + kNoAllocCellsPerBlock - 1) / kNoAllocCellsPerBlock);
   cudaStream_t stream = current_stream();
-  k_mass_partial_blocked<<<nblk, kMassThreads, 0, stream>>>(nc, N, ld, dev_rho, grid->vert.d_dz, grid->g.A_c,
-                                                            scratch);
+  k_mass_partial_blocked<<<nblk, kMassThreads, 0, stream>>>(nc, N, ld, dev_rho, grid->vert.d_dz, dev_dz,
+                                                            grid->g.A_c, scratch);
   k_mass_final<<<1, 1024, 0, stream>>>(scratch, nblk, scratch + kNoAllocMaxPartials);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "icon_global_mass_noalloc launch");

@@ -21,6 +21,10 @@ pytestmark = pytest.mark.gpu
 
 TOL_STEP = 1e-12
 TOL_INIT = 1e-14
+# full-field L2 norms of ~4e7 entries: the stored norms were summed by the BLAS of the machine
+# that wrote them, this one by the test machine's, in another order; the rounding of such a sum
+# is up to about sqrt(n) eps = 1.4e-12 relative (the sampled entries carry the tight bounds)
+TOL_NORM = 2e-12
 
 
 @pytest.fixture(scope="module")
@@ -41,7 +45,7 @@ def test_r2b6_l90_fp64_step_sampled(gpu, samples):
             full = C.icon_state_copy_field(st, grid, N, f)
             idx = edges if f == "vn" else cells
             assert rel_l2(full[idx], np.array(ref)) <= TOL_INIT, f
-            assert abs(np.linalg.norm(full) / samples["norm_init"][f] - 1.0) <= TOL_INIT, f
+            assert abs(np.linalg.norm(full) / samples["norm_init"][f] - 1.0) <= TOL_NORM, f
         m0 = C.icon_global_mass(st)
         C.icon_dycore_step(st, dt, nsub)
         m1 = C.icon_global_mass(st)
@@ -61,7 +65,7 @@ def test_r2b6_l90_fp64_step_sampled(gpu, samples):
                 assert abs(np.linalg.norm(full) - norm_ref) / np.sqrt(full.size) <= wb * scale, f
             else:
                 assert rel_l2(got, ref) <= TOL_STEP, (f, rel_l2(got, ref))
-                assert abs(np.linalg.norm(full) / norm_ref - 1.0) <= TOL_STEP, f
+                assert abs(np.linalg.norm(full) / norm_ref - 1.0) <= max(TOL_STEP, TOL_NORM), f
             del full
         om0, om1 = samples["mass"]
         assert abs(m0 / om0 - 1.0) <= 1e-14 and abs(m1 / om1 - 1.0) <= 1e-14
@@ -96,7 +100,7 @@ def test_r2b6_l90_fp64_tracer_sampled(gpu, samples):
     # this tracer barely changes in one step (it varies with latitude, the jet is zonal):
     # hold the difference to a few hundred ulps of q rather than relative to the change
     assert np.max(np.abs(q[cells] - ref)) <= 1e-13
-    assert abs(np.linalg.norm(q) / samples["norm_step"]["tracer"] - 1.0) <= TOL_STEP
+    assert abs(np.linalg.norm(q) / samples["norm_step"]["tracer"] - 1.0) <= max(TOL_STEP, TOL_NORM)
 
 
 @pytest.fixture(scope="module")
@@ -141,7 +145,7 @@ def test_r2b6_l90_terrain_step_sampled(gpu, terrain_samples, precision):
                 assert np.sqrt(np.mean((got - ref) ** 2)) <= wb * scale, f
             elif precision == 0:
                 assert rel_l2(got, ref) <= TOL_STEP, (f, rel_l2(got, ref))
-                assert abs(np.linalg.norm(full) / smp["norm_step"][f] - 1.0) <= TOL_STEP, f
+                assert abs(np.linalg.norm(full) / smp["norm_step"][f] - 1.0) <= max(TOL_STEP, TOL_NORM), f
             else:
                 bound = 1e-5 if f in ("vn", "mflx") else thermo_bound_mixed(dt, nsub, 1, d_min)
                 assert rel_l2(got, ref) <= bound, (f, rel_l2(got, ref), bound)

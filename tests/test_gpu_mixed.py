@@ -65,14 +65,17 @@ def test_mixed_initial_state(gpu):
         C.icon_grid_free(grid)
 
 
-@pytest.mark.parametrize("recompute", [False, True], ids=["stored-factors", "recompute"])
+FORMS = ["lean", "stored", "recompute"]
+
+
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("bis,nlev,case,dt,noise", [(2, 20, 1, 300.0, 0.01), (3, 30, 2, 150.0, 0.1),
                                                     (1, 60, 3, 400.0, 0.0)])
-def test_mixed_one_step_vs_oracle(gpu, monkeypatch, bis, nlev, case, dt, noise, recompute):
-    """Both forms of the mixed column (stored shared factors, or recomputed in each
-    stage, as on grids whose factors would not fit) against the FP64 oracle."""
-    if recompute:
-        monkeypatch.setenv("ICON_MIXED_RECOMPUTE", "1")
+def test_mixed_one_step_vs_oracle(gpu, monkeypatch, bis, nlev, case, dt, noise, form):
+    """Every form of the mixed column (lean: FP32 rows and factors with an FP64 base and FP64
+    substitution, the default; stored: the frozen FP64 parts kept by the predictor for the
+    corrector; recompute: both stages compute them) against the FP64 oracle."""
+    monkeypatch.setenv("ICON_MIXED_COLUMN", form)
     out, m0, m1 = gpu_run(gpu, bis, nlev, 6, case, dt, 5, 1, gpu.ICON_MIXED, noise)
     ref = oracle_run(bis, nlev, 6, case, dt, 5, 1, noise)
     assert rel_l2(out["vn"], ref["vn"]) <= TOL_WIND
@@ -84,7 +87,9 @@ def test_mixed_one_step_vs_oracle(gpu, monkeypatch, bis, nlev, case, dt, noise, 
     assert abs(m1 - m0) / m0 <= 1e-13                          # FP64 flux sums conserve mass
 
 
-def test_mixed_rest_stays_at_rest(gpu):
+@pytest.mark.parametrize("form", FORMS)
+def test_mixed_rest_stays_at_rest(gpu, monkeypatch, form):
+    monkeypatch.setenv("ICON_MIXED_COLUMN", form)
     out, m0, m1 = gpu_run(gpu, 2, 20, 0, 0, 300.0, 5, 2, gpu.ICON_MIXED)
     assert np.all(out["vn"] == 0.0)
     assert np.abs(out["w"]).max() <= 1e-6
@@ -108,11 +113,13 @@ def test_integer_pipe_conversions_match_hardware(gpu):
     assert gpu.icon_selftest(1 << 22) == 0
 
 
-def test_mixed_column_forms_agree(gpu, monkeypatch):
-    """R2B4 / 60 levels, 2 steps: the recomputing column against the stored-factor one
-    (different operation order, same arithmetic precision per term)."""
+@pytest.mark.parametrize("form", ["lean", "recompute"])
+def test_mixed_column_forms_agree(gpu, monkeypatch, form):
+    """R2B4 / 60 levels, 2 steps: the lean and the recomputing column against the
+    stored-factor one (different operation order and precision of the coefficients)."""
+    monkeypatch.setenv("ICON_MIXED_COLUMN", "stored")
     a, am0, am1 = gpu_run(gpu, 4, 60, 3, 2, 240.0, 5, 2, gpu.ICON_MIXED, 0.1)
-    monkeypatch.setenv("ICON_MIXED_RECOMPUTE", "1")
+    monkeypatch.setenv("ICON_MIXED_COLUMN", form)
     b, bm0, bm1 = gpu_run(gpu, 4, 60, 3, 2, 240.0, 5, 2, gpu.ICON_MIXED, 0.1)
     assert rel_l2(b["vn"], a["vn"]) <= TOL_WIND
     for f in ("rho", "theta_v", "exner"):

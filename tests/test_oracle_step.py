@@ -61,6 +61,21 @@ def test_analytic_states_are_balanced(which):
         assert np.all(u >= 0.0)
 
 
+def test_jet_state_is_statically_stable():
+    """The jet stand-in has a positive buoyancy frequency squared everywhere (a statically
+    unstable initial state overturns within hours, which no time step survives)."""
+    lat = np.deg2rad(np.linspace(-89.0, 89.0, 179))
+    x = np.stack([np.cos(lat), np.zeros_like(lat), np.sin(lat)], axis=1)
+    z = np.linspace(0.0, 40000.0, 801)
+    lnp, T, u = S.jet_state(x, z)
+    theta = T * np.exp(-(S.RD / S.CPD) * (lnp - np.log(S.P0)))
+    N2 = S.GRAV * np.diff(np.log(theta), axis=1) / np.diff(z)[None, :]
+    assert N2.min() > 1.2e-4, N2.min()
+    # the shift of Phi leaves the wind untouched where T = T_j (z = z_j): u(45 deg) = 35 m/s
+    x45 = np.array([[np.sqrt(0.5), 0.0, np.sqrt(0.5)]])
+    assert S.jet_state(x45, np.array([S.JET_ZJ]))[2][0, 0] == pytest.approx(35.0, rel=1e-13)
+
+
 def test_initial_state_structure():
     g = O.build_grid(2, 1)
     v = O.vertical_grid(20)
@@ -318,3 +333,18 @@ def test_planted_state_equation_mistakes_fail(old, new, monkeypatch):
     monkeypatch.setattr(D, "column", _planted(D, "column", old, new))
     ratios, r = _orders(D.substep, g, v, s)
     assert all(q < 2.6 for q in ratios), (ratios, r)
+
+
+def test_long_run_stays_bounded():
+    """120 steps (10 simulated hours) of the jet on R2B2/20 at the parity configuration's time
+    step: finite, w and vn bounded, mass conserved (a statically unstable initial state or an
+    unstable scheme grows w geometrically within a few dozen steps)."""
+    g = O.build_grid(2, 1)
+    v = O.vertical_grid(20)
+    s = O.init_state(g, v, 2, O.CASE_JET, noise_K=0.1)
+    m0 = O.global_mass(g, v, s)
+    for _ in range(120):
+        s, _ = O.dycore_step(g, v, s, 300.0, 5)
+    assert np.all(np.isfinite(s["w"])) and np.abs(s["w"]).max() < 0.05
+    assert np.abs(s["vn"]).max() < 40.0
+    assert abs(O.global_mass(g, v, s) / m0 - 1.0) < 1e-12

@@ -247,7 +247,10 @@ def test_layer_mass_budget_closes_for_a_divergence_free_wind():
     weighting the residual does not fall, and with the correction's sign flipped the ratio
     stays near 2."""
     r = [_layer_budget_residual(b)[0] for b in (2, 3, 4)]
-    assert all(np.log2(r[i] / r[i + 1]) > 0.6 for i in range(2)), r
+    # first order over the three refinements (least-squares slope of log2 r), and the finest
+    # pair on its own: the coarsest grid resolves the 800 km mountain with a few cells only
+    slope = -np.polyfit(np.arange(3), np.log2(r), 1)[0]
+    assert slope > 0.8 and np.log2(r[1] / r[2]) > 0.8, r
     assert r[-1] < 0.1
     flat = [_layer_budget_residual(b, flat_dz=True)[1] for b in (2, 4)]
     assert flat[1] > 0.8 * flat[0]

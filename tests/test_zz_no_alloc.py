@@ -6,8 +6,11 @@ pool allocator, or a loop that forbids allocations after start-up). It reduces a
 caller-owned density array with partial sums kept in one fixed array inside the
 library. Here it must agree with icon_global_mass on the same density, on two
 calls in a row, for a second density after a step (nothing stale is carried
-over), for a padded row layout, and refuse what it cannot hold.
+over), for a padded row layout, on terrain-following levels when given the
+columns' own layer thicknesses (and with the oracle's mass there), and refuse
+what it cannot hold or read.
 """
+import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -54,6 +57,14 @@ def test_noalloc_mass_matches_ordinary_mass(gpu):
         assert ei.value.status == C.ICON_EINVAL
         with pytest.raises(C.IconError):
             C.icon_global_mass_noalloc(grid, 0, N)
+        # host memory is not device memory of the current device: refused before any launch
+        host = np.ones((rho2.shape[0], N))
+        with pytest.raises(C.IconError) as ei:
+            C.icon_global_mass_noalloc(grid, host.ctypes.data, N)
+        assert ei.value.status == C.ICON_EINVAL and "not device memory" in str(ei.value)
+        with pytest.raises(C.IconError) as ei:
+            C.icon_global_mass_noalloc(grid, rho2.data_ptr(), N, dev_dz_ptr=host.ctypes.data)
+        assert ei.value.status == C.ICON_EINVAL and "dev_dz" in str(ei.value)
     finally:
         C.icon_state_free(st)
         C.icon_grid_free(grid)
@@ -69,4 +80,37 @@ def test_noalloc_mass_refuses_grids_beyond_its_scratch(gpu):
             C.icon_global_mass_noalloc(grid, dummy.data_ptr(), 2)
         assert ei.value.status == C.ICON_EINVAL and "exceed the maximum" in str(ei.value)
     finally:
+        C.icon_grid_free(grid)
+
+
+def test_noalloc_mass_on_terrain_following_levels(gpu):
+    """With the columns' own layer thicknesses the allocation-free integral is the terrain
+    state's mass (icon_global_mass and the oracle's); with the flat thicknesses it is not."""
+    import torch
+    import oracle as O
+    import oracle.terrain as OT
+    C = gpu
+    N, bis, h0, a = 20, 3, 1500.0, 1.5e6
+    grid = C.icon_grid_build(2, bis, N)
+    st = C.icon_state_init_ex(grid, 5, C.ICON_CASE_JET, noise_K=0.1, topo_height_m=h0, topo_radius_m=a)
+    try:
+        g = O.build_grid(2, bis)
+        v = O.vertical_grid(N)
+        t = OT.terrain_geometry(g, v, OT.mountain(g.x_c, h0, a))
+        m_oracle = OT.terrain_mass(g, t, O.init_state(g, v, 5, O.CASE_JET, noise_K=0.1, terrain=t))
+        m_ref = C.icon_global_mass(st)
+        ld = N + 4
+        rho = torch.zeros((g.nc, ld), dtype=torch.float64, device="cuda")
+        rho[:, :N] = torch.from_numpy(C.icon_state_copy_field(st, grid, N, "rho"))
+        dz = torch.zeros((g.nc, ld), dtype=torch.float64, device="cuda")
+        dz[:, :N] = torch.from_numpy(t.dz_c)
+        torch.cuda.synchronize()
+        m1 = C.icon_global_mass_noalloc(grid, rho.data_ptr(), ld, dev_dz_ptr=dz.data_ptr())
+        m2 = C.icon_global_mass_noalloc(grid, rho.data_ptr(), ld, dev_dz_ptr=dz.data_ptr())
+        assert m1 == m2
+        assert _rel(m1, m_ref) <= TOL and _rel(m1, m_oracle) <= 1e-13
+        m_flat = C.icon_global_mass_noalloc(grid, rho.data_ptr(), ld)
+        assert _rel(m_flat, m_ref) > 1e-6               # the flat thicknesses give another integral
+    finally:
+        C.icon_state_free(st)
         C.icon_grid_free(grid)
