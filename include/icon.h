@@ -286,12 +286,15 @@ int icon_global_mass_noalloc(const icon_grid* grid, const double* dev_rho, const
                              double* host_out);
 
 /* Copy a field (icon_field) to host memory as FP64, [entity][level] unpadded;
- * count must equal the field's element count. Synchronous. */
+ * count must equal the field's element count. Synchronous. Pinned (page-locked) host
+ * memory of a field stored in entity rows is written directly by the packing kernel over
+ * the CPU-GPU link; other host memory goes through a device staging buffer and one copy. */
 int icon_state_copy_field(const icon_state* state, int field_id, double* host_dst, size_t count);
 
 /* Overwrite a prognostic field (ICON_F_VN .. ICON_F_EXNER) from FP64 host memory
  * in the same layout (rounded to FP32 where the state stores FP32). w at the lid
- * and the ground must be 0. Synchronous with respect to host_src. */
+ * and the ground must be 0. Synchronous with respect to host_src. Pinned host memory
+ * of a field stored in entity rows is read directly by the unpacking kernel. */
 int icon_state_set_field(icon_state* state, int field_id, const double* host_src, size_t count);
 
 /* Number of kernel launches in the recorded graph of one step with the given
@@ -326,9 +329,10 @@ int icon_probe_fp64_rate(double* fma_per_s, double* add_per_s);
  * stencil kinds: 10 vertex, 11 edge diagnostics, 12 cell kinetic energy,
  * 13 edge tendency, 15 column-input gather, 16 diffusion vertex/divergence;
  * 20 tracer transport, 21 divergence damping, 22 background diffusion (options),
- * 23 terrain metrics (states with topography). */
+ * 23 terrain metrics (states with topography), 24 and 25 the lean mixed column and
+ * its input gather (the default column of mixed states on flat levels). */
 const char* icon_kernel_kind_name(int kind);
-#define ICON_KIND_COUNT 24
+#define ICON_KIND_COUNT 26
 
 /* Storage precision of the state (icon_precision). */
 int icon_state_precision(const icon_state* state, int* out);
@@ -341,9 +345,12 @@ void icon_state_free(icon_state* state);
 enum {
   /* Fourth-order divergence damping of the corrector's vn^{n+1} before its fluxes are
    * formed: vn -= c4 Abar^2 grad(div(grad(div vn))), Abar = 4 pi R^2 / Nc, with the
-   * step's own divergence and gradient operators (an ICON option; the paper prints none).
-   * value = c4 in [0, 0.05]; 0 (the default) turns it off. Both precisions; not in the
-   * persistent ensemble (icon_ensemble_create rejects members that set it). */
+   * step's own divergence and gradient operators (ICON damps its corrector's divergence
+   * this way; the paper prints none). value = c4 in [0, 0.05]; 0 turns it off. Default
+   * 0.0025 (ICON's default fourth-order coefficient): without it the triangular grid's
+   * divergence noise grows at the pentagons under the jet and the R2B6/90 benchmark state
+   * goes non-finite after about 23 simulated hours. Both precisions, the persistent
+   * ensemble and the decomposed domain. */
   ICON_OPT_DIVDAMP4 = 1,
   /* Fourth-order background diffusion of vn in the diffusion step, once per step:
    * vn -= c Abar^2 L(L(vn)) with the step's vector Laplacian L (an ICON option; the paper
@@ -407,8 +414,9 @@ int icon_partition_plan(int64_t nc, int64_t ne, int64_t nv, const int32_t* host_
                         int part, int halo_rings, int64_t* host_counts, int32_t* host_local, int32_t* host_owner,
                         int32_t* host_owner_index);
 
-/* Decompose an FP64 state on flat levels without tracers or options into nparts parts
- * (1..64) with halo_rings (3..16) vertex rings of halo, on the current device: each part
+/* Decompose an FP64 state on flat levels without tracers, background diffusion or upwind
+ * theta (its divergence damping is kept, with the global grid's mean cell area) into
+ * nparts parts (1..64) with halo_rings (3..16) vertex rings of halo, on the current device: each part
  * gets its local grid (connectivity remapped, geometry gathered) and a state holding its
  * local rows of the global state's fields. The global state is only read; the domain
  * keeps a pointer to its grid, which must outlive it. ICON_EINVAL for other states. */

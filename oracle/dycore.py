@@ -24,7 +24,8 @@ O7 w advection   w_v = mean of w over the cells of v; at edges
 Step (dt, nsub substeps of dtau = dt/nsub, off-centring beta = 0.65):
   predictor  T0 = tend(S^n); vn* = vn^n + dtau (A_vn0 - cpd thv_e dpi/dn);
              column(S^n, vn*, A_w0) -> w*, rho*, thv*, pi*
-  corrector  T* = tend(S*); vn^{n+1} = vn^n + dtau ((A_vn0 + A_vn*)/2 - cpd thv_e* dpi*/dn);
+  corrector  T* = tend(S*); vn^{n+1} = vn^n + dtau ((A_vn0 + A_vn*)/2 - cpd thv_e* dpi*/dn),
+             divergence-damped with c4 = DIVDAMP4 (DD);
              column(S^n, vn^{n+1}, (A_w0 + A_w*)/2) with fluxes from rho_e*, thv_e*;
              mass-flux accumulators += rho_e* vn^{n+1} / nsub and
              rho_ic (beta w^{n+1} + (1-beta) w^n) / nsub.
@@ -37,6 +38,10 @@ from .state import GRAV, RD, CPD, CVD, to_half
 
 BETA = 0.65             # vertical off-centring (implicit weight)
 CS_SMAG = 0.15          # Smagorinsky constant
+# DD-base: fourth-order divergence damping of the corrector's vn in every substep with ICON's
+# default coefficient; without it the C grid's grid-scale divergence noise grows at the
+# pentagons under the jet and the R2B6/90 jet state goes non-finite after about 23 hours
+DIVDAMP4 = 0.0025
 
 
 # ------------------------------------------------------------------ operators
@@ -261,7 +266,7 @@ def divergence_damping(g, vn, c4):
 
 
 # ------------------------------------------------------------------ step and mass
-def substep(g, v, s, dtau, nsub, acc, divdamp4=0.0, upwind_theta=False):
+def substep(g, v, s, dtau, nsub, acc, divdamp4=DIVDAMP4, upwind_theta=False):
     """One predictor-corrector substep; updates the accumulators in `acc`. With
     divdamp4 > 0 the corrector's vn^{n+1} is divergence-damped (DD) before its mass and
     heat fluxes are formed; with upwind_theta the heat fluxes carry the upwind theta_v (UT)
@@ -283,7 +288,7 @@ def substep(g, v, s, dtau, nsub, acc, divdamp4=0.0, upwind_theta=False):
     return dict(cn, vn=vn_new)
 
 
-def dycore_step(g, v, s, dt, nsub, divdamp4=0.0, diff4=0.0, upwind_theta=False):
+def dycore_step(g, v, s, dt, nsub, divdamp4=DIVDAMP4, diff4=0.0, upwind_theta=False):
     """One step: nsub substeps of dt/nsub, then diffusion with dt. Returns
     (new state, accumulators {mflx (Ne,N), wflx (Nc,N+1)})."""
     dtau = dt / nsub

@@ -49,7 +49,7 @@ import numpy as np
 
 from .grid import R_EARTH
 from .state import GRAV, RD, CPD, CVD, to_half_w
-from .dycore import (BETA, curl, tangential, cell_kinetic, vertex_mean, edge_mean, edge_upwind,
+from .dycore import (BETA, DIVDAMP4, curl, tangential, cell_kinetic, vertex_mean, edge_mean, edge_upwind,
                      divergence, thomas, diffusion, divergence_damping)
 
 DECAY_M = 4000.0                    # SLEVE decay scale
@@ -233,7 +233,7 @@ def column(g, v, t, s0, vn_new, A_w, rho_e, thv_e, wcc, dtau):
 
 
 # ------------------------------------------------------------------ step and mass
-def substep(g, v, t, s, dtau, nsub, acc, divdamp4=0.0, upwind_theta=False):
+def substep(g, v, t, s, dtau, nsub, acc, divdamp4=DIVDAMP4, upwind_theta=False):
     """One predictor-corrector substep on the terrain-following grid (R-Z6)."""
     theta_e = (lambda st, vn: edge_upwind(g, st["theta_v"], vn)) if upwind_theta else \
         (lambda st, vn: edge_mean(g, st["theta_v"]))
@@ -257,7 +257,7 @@ def substep(g, v, t, s, dtau, nsub, acc, divdamp4=0.0, upwind_theta=False):
     return dict(cn, vn=vn_new)
 
 
-def terrain_step(g, v, t, s, dt, nsub, divdamp4=0.0, diff4=0.0, upwind_theta=False):
+def terrain_step(g, v, t, s, dt, nsub, divdamp4=DIVDAMP4, diff4=0.0, upwind_theta=False):
     """One step on the terrain-following grid: nsub substeps of dt/nsub, then diffusion
     with dt. Returns (new state, accumulators {mflx (Ne,N), wflx (Nc,N+1)})."""
     dtau = dt / nsub

@@ -224,7 +224,7 @@ def icon_state_step_kernels(state, dt, nsubsteps):
     return n.value
 
 
-ICON_KIND_COUNT = 24
+ICON_KIND_COUNT = 26
 
 
 def icon_dycore_step_profile(state, dt, nsubsteps, ms=None, launches=None):

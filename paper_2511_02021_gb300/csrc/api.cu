@@ -61,7 +61,7 @@ static const char* kKindNames[K_KIND_COUNT] = {
     "diff_vertex", "diff_div", "diff_edge", "diff_theta", "global_mass",
     "mx_vertex", "mx_edge_diag", "mx_cell_ke", "mx_edge_tendency_flux", "mx_column_solve", "mx_column_prep",
     "mx_diff_vertex", "mx_diff_edge", "mx_diff_theta", "ensemble_persistent", "tracer_transport", "divergence_damping", "background_diffusion",
-    "terrain_metrics"};
+    "terrain_metrics", "mx_lean_column", "mx_lean_gather"};
 
 Allocator current_allocator() {
   std::lock_guard<std::mutex> lk(g_alloc_mu);
@@ -409,6 +409,17 @@ bool field_ref(const icon_state* st, int id, void** ptr, int* is_f32, int64_t* n
   }
 }
 
+// the device address of pinned (page-locked, mapped) host memory, or NULL for any other
+// pointer; the query allocates nothing
+const void* mapped_host_ptr(const void* p) {
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return attr.type == cudaMemoryTypeHost ? attr.devicePointer : nullptr;
+}
+
 // host-order [n][nlev] staging <-> the device layout of a field: mode 0 FP64 rows of
 // ld, mode 1 FP32 rows of ld, mode 2 FP64 level-major [k][n]
 __global__ void k_unpack(const double* __restrict__ stage, void* __restrict__ dst, int64_t n, int nlev, int ld,
@@ -565,6 +576,8 @@ int icon_state_init_ex(const icon_grid* grid, uint64_t seed, int case_id, const 
   st->grid = grid;
   st->seed = seed;
   st->case_id = case_id;
+  st->divdamp4 = kDivDamp4;
+  st->abar = 4.0 * M_PI * kR * kR / (double)grid->g.nc;
   st->arena.al = current_allocator();
   cudaStream_t stream = current_stream();
   int rc = alloc_state(st, p.precision, topo);
@@ -701,9 +714,22 @@ int icon_state_copy_field(const icon_state* st, int field_id, double* host_dst, 
     set_error("icon_state_copy_field: field %d has %lld elements, got %zu", field_id, (long long)(n * nlev), count);
     return ICON_EINVAL;
   }
-  // pack into host order on the device, then one contiguous transfer
+  // pack into host order on the device, then one contiguous transfer; into pinned host
+  // memory of a row-layout field the pack kernel writes the host buffer directly (the GPU
+  // reaches page-locked host memory over the CPU-GPU link: one pass, no staging copy)
   const int ld = st->grid->vert.ld;
   cudaStream_t stream = current_stream();
+  if (!lm) {
+    void* hd = const_cast<void*>(mapped_host_ptr(host_dst));
+    if (hd) {
+      k_pack<<<blocks_for(n * nlev, 256), 256, 0, stream>>>(ptr, static_cast<double*>(hd), n, nlev, ld,
+                                                           f32 ? 1 : 0);
+      cudaError_t e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+      if (e != cudaSuccess) return cuda_fail(e, "icon_state_copy_field");
+      return ICON_OK;
+    }
+  }
   DeviceArena tmp;
   tmp.al = st->arena.al;
   double* stage = tmp.get_n<double>((size_t)n * nlev);
@@ -731,9 +757,21 @@ int icon_state_set_field(icon_state* st, int field_id, const double* host_src, s
     set_error("icon_state_set_field: field %d has %lld elements, got %zu", field_id, (long long)(n * nlev), count);
     return ICON_EINVAL;
   }
-  // one contiguous transfer into a staging buffer, then unpack into the device layout
+  // one contiguous transfer into a staging buffer, then unpack into the device layout; from
+  // pinned host memory into a row-layout field the unpack kernel reads the host buffer directly
   const int ld = st->grid->vert.ld;
   cudaStream_t stream = current_stream();
+  if (!lm) {
+    const void* hs = mapped_host_ptr(host_src);
+    if (hs) {
+      k_unpack<<<blocks_for(n * nlev, 256), 256, 0, stream>>>(static_cast<const double*>(hs), ptr, n, nlev, ld,
+                                                             f32 ? 1 : 0);
+      cudaError_t e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+      if (e != cudaSuccess) return cuda_fail(e, "icon_state_set_field");
+      return ICON_OK;
+    }
+  }
   DeviceArena tmp;
   tmp.al = st->arena.al;
   double* stage = tmp.get_n<double>((size_t)n * nlev);
@@ -897,9 +935,9 @@ int icon_ensemble_create(icon_state* const* members, int n, icon_ensemble** out)
       set_error("icon_ensemble_create: members must be mixed-precision states");
       return ICON_EINVAL;
     }
-    if (members[i]->divdamp4 != 0.0 || members[i]->diff4 != 0.0 || members[i]->upwind_theta) {
-      set_error("icon_ensemble_create: the persistent ensemble has none of the step options (member %d sets one)",
-                i);
+    if (members[i]->diff4 != 0.0 || members[i]->upwind_theta) {
+      set_error("icon_ensemble_create: the persistent ensemble has the divergence damping but not the other step "
+                "options (member %d sets one)", i);
       return ICON_EINVAL;
     }
     if (members[i]->s.ntr != 0) {

@@ -16,13 +16,14 @@
 //    to local ids); a neighbour outside the local set points at local entity 0, which
 //    keeps every access in bounds (the values computed there are discarded: they lie in
 //    the outer halo and are overwritten by the next exchange).
-//  * Step: every part runs the same kernels as the single-domain step on its local grid;
-//    after each predictor and corrector stage the halo rows of the stage's outputs (vn on
-//    edges; w, rho, theta_v, Exner on cells) are copied from their owners, and after the
-//    diffusion the halo rows of vn, theta_v and Exner. With R >= 3 the owned entities of
-//    every stage read only values that are correct, so each part's owned results are
-//    bit-identical to the single-domain step's (the kernels compute every entity in the
-//    same order from the same inputs).
+//  * Step: every part runs the same kernels as the single-domain step on its local grid
+//    (the divergence damping with the global grid's mean cell area); after each predictor
+//    and corrector stage the halo rows of the stage's outputs (vn on edges; w, rho,
+//    theta_v, Exner on cells) are copied from their owners, and after the diffusion the
+//    halo rows of vn, theta_v and Exner. With R >= 3 the owned entities of every stage
+//    read only values that are correct, so each part's owned results are bit-identical to
+//    the single-domain step's (the kernels compute every entity in the same order from
+//    the same inputs).
 //  * Mass: each part sums its owned cells (fixed order), the P partial sums are added in
 //    part order on the host (the scalar all-reduce of a multi-GPU run).
 //
@@ -396,9 +397,10 @@ int icon_domain_create(const icon_state* global_state, int nparts, int halo_ring
   }
   const icon_grid* grid = global_state->grid;
   const StateDev& gs = global_state->s;
-  if (gs.precision != ICON_FP64 || gs.topo.on || gs.ntr > 0 || global_state->divdamp4 > 0.0 ||
-      global_state->diff4 > 0.0 || global_state->upwind_theta) {
-    set_error("icon_domain_create: decomposes FP64 states on flat levels without tracers or options");
+  if (gs.precision != ICON_FP64 || gs.topo.on || gs.ntr > 0 || global_state->diff4 > 0.0 ||
+      global_state->upwind_theta) {
+    set_error("icon_domain_create: decomposes FP64 states on flat levels without tracers, background diffusion "
+              "or upwind theta");
     return ICON_EINVAL;
   }
   if (nparts < 1 || nparts > 64 || nparts > grid->g.nc || halo_rings < 3 || halo_rings > 16) {
@@ -444,6 +446,9 @@ int icon_domain_create(const icon_state* global_state, int nparts, int halo_ring
     rc = icon_state_init_ex(L, 0, ICON_CASE_REST, &cp, &ps);
     if (rc != ICON_OK) break;
     D->states.push_back(ps);
+    // the damping's length scale is the global grid's mean cell area
+    ps->abar = global_state->abar;
+    ps->divdamp4 = global_state->divdamp4;
     const PartPlan& pl = D->plans[p];
     const DeviceArena& LA = L->arena;
     (void)LA;

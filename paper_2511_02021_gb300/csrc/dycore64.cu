@@ -824,7 +824,7 @@ void fp64_step_stage(icon_state* st, double dt, int nsub, bool corr, cudaStream_
   prof_end(stream);
   if (damp) {
     // Kc and the column's update-operand scratch are free until the column runs
-    const double abar = 4.0 * M_PI * kR * kR / (double)G.nc;
+    const double abar = st->abar;
     DDArgs da;
     da.L = s.col_rx; da.rho = rho_st; da.thv = thv_st;
     da.vn = s.vn; da.F = s.F; da.G = s.G; da.mflx = s.mflx;
@@ -875,7 +875,7 @@ void fp64_step_diffusion(icon_state* st, double dt, cudaStream_t stream) {
   bd.D1 = nullptr; bd.zeta1 = nullptr; bd.scale = 0.0;
   if (st->diff4 > 0.0) {
     // scratch that is dead during diffusion: a_e (edges), two column-scratch cell arrays
-    const double abar = 4.0 * M_PI * kR * kR / (double)G.nc;
+    const double abar = st->abar;
     prof_begin(stream, K_DIFF4);
     k_bd_lap<<<nbe, 256, 0, stream>>>(G, s.zeta, s.divc, s.a_e);
     k_bd_curl<<<nbv, 256, 0, stream>>>(G, s.a_e, s.col_di);

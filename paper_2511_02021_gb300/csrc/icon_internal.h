@@ -20,6 +20,7 @@ constexpr double kCvd = kCpd - kRd;
 constexpr double kP0 = 1.0e5;            // Pa
 constexpr double kBeta = 0.65;           // vertical off-centring (implicit weight)
 constexpr double kCsSmag = 0.15;         // Smagorinsky constant
+constexpr double kDivDamp4 = 0.0025;     // default fourth-order divergence damping coefficient
 
 // ---------------------------------------------------------------- errors
 void set_error(const char* fmt, ...);
@@ -36,7 +37,7 @@ enum KernelKind {
   K_DIFF_VERTEX, K_DIFF_DIV, K_DIFF_EDGE, K_DIFF_THETA, K_MASS,
   K_MX_VERTEX, K_MX_EDGE, K_MX_CELL_KE, K_MX_EDGE_TEND, K_MX_COLUMN, K_MX_COLUMN_PREP,
   K_MX_DIFF_VERTEX, K_MX_DIFF_EDGE, K_MX_DIFF_THETA, K_ENSEMBLE, K_TRACER, K_DIVDAMP, K_DIFF4, K_TERRAIN,
-  K_KIND_COUNT
+  K_MX_LEAN, K_MX_LEAN_GATHER, K_KIND_COUNT
 };
 static_assert(K_KIND_COUNT <= ICON_KIND_COUNT, "kind table");
 // When a profile is active on this thread, every launch is bracketed by events.
@@ -233,7 +234,8 @@ struct icon_state {
   bool tile_forced[ICON_KIND_COUNT] = {};
   bool tuned = false;
   // options (icon_state_set_option)
-  double divdamp4 = 0.0;        // fourth-order divergence damping coefficient (0: off)
+  double divdamp4 = 0.0;        // fourth-order divergence damping coefficient (0: off; set at init)
+  double abar = 0.0;            // mean cell area of the (global) grid, m^2: the damping's length scale
   double diff4 = 0.0;           // fourth-order background diffusion coefficient (0: off)
   bool upwind_theta = false;    // heat fluxes with the upwind theta_v
 };
@@ -247,6 +249,7 @@ struct EnsembleDev {
   int nm = 0, nsub = 0, N = 0, grid_blocks = 0;
   int64_t tot_v = 0, tot_e = 0, tot_c = 0, tot_t = 0;
   bool all_fac = true;         // every member stores its column factors
+  bool any_damp = false;       // some member damps the corrector's divergence
   long long spin_limit = 1ll << 24;
   int test_skip_barrier = 0;
 };

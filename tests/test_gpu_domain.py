@@ -83,7 +83,7 @@ def test_domain_rejects_what_it_does_not_decompose(gpu):
         with pytest.raises(C.IconError) as ei:
             C.icon_domain_create(fp, 2, 2)                       # halo too shallow for a stage
         assert ei.value.status == C.ICON_EINVAL
-        C.icon_state_set_option(fp, C.ICON_OPT_DIVDAMP4, 0.004)
+        C.icon_state_set_option(fp, C.ICON_OPT_DIFF4, 0.005)          # background diffusion: not decomposed
         with pytest.raises(C.IconError) as ei:
             C.icon_domain_create(fp, 2, 3)
         assert ei.value.status == C.ICON_EINVAL
