@@ -326,12 +326,13 @@ def run_reference(args, wl, rank):
     t = sum(vals) / len(vals)
     nc, _, _ = counts(wl)
     value = procs * nc * wl.nlev / t
-    cfg = dict(gpu_config(wl), sample="each step = one substep of the workload on each of %d replicas" % procs)
+    cfg = gpu_config(wl)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle",
-                             "sample": SAMPLE_DESC % wl.name, "cpu": cpu_model(), "host_cores": host_cores()},
+                             "sample": SAMPLE_DESC % wl.name + "; each step = one concurrent substep on every "
+                                       "replica", "cpu": cpu_model(), "host_cores": host_cores()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -548,8 +549,19 @@ def e2e_rate(gpu, grid, wl, steps):
         e2e_s = (time.perf_counter() - t0) / steps
     finally:
         C.icon_state_free(st)
+    # the host link on its own: one pinned buffer of the state's size copied to the device and
+    # back with plain copies (CUDA events), the floor of the end-to-end transfers
+    torch = gpu.torch
+    hb = torch.empty(h2d // 8, dtype=torch.float64, pin_memory=True)
+    db = torch.empty(h2d // 8, dtype=torch.float64, device="cuda")
+    db.copy_(hb, non_blocking=True)
+    t_h2d = gpu.timed(lambda: db.copy_(hb, non_blocking=True))
+    t_d2h = gpu.timed(lambda: hb.copy_(db, non_blocking=True))
+    del hb, db
     return {"value": nc * N * wl.nsub / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": h2d + 8, "steps": steps}
+            "d2h_bytes_per_step": h2d + 8, "steps": steps, "ms_per_step": e2e_s * 1e3,
+            "host_link": {"h2d_gbs": h2d / (t_h2d * 1e-3) / 1e9, "d2h_gbs": h2d / (t_d2h * 1e-3) / 1e9,
+                          "how": "one pinned buffer of the state's size, torch copy_, CUDA events"}}
 
 
 def leg(fn, *a, **k):

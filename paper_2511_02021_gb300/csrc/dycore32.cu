@@ -1273,11 +1273,22 @@ struct MxLeanArgs {
   unsigned* status;
   double dtau, inv_nsub;
   int hdamp;                               // half levels h < hdamp are Rayleigh-damped
+  // corrector with divergence damping (fused into its gather): the undamped vn^{n+1}, the
+  // cell Laplacian of its divergence, the stage shadows for the fluxes, c4 Abar^2, the
+  // damped vn^{n+1} (stored by each edge's lower-id cell, which also accumulates the
+  // step-mean mass flux)
+  const float *dd_vn, *dd_L, *dd_rho, *dd_thv;
+  float* dd_out;
+  double* mflx;
+  float dd_scale;
+  int dd_upwind;
 };
 
-constexpr int kLeanChunk = 16;             // levels per shadow-transpose chunk
+// per-warp shadow transpose: CH levels of 32 columns (16 in the per-state kernel, 8 in the
+// persistent ensemble, whose blocks hold four warps' tiles)
+template <int CH>
 struct LeanTile {
-  float t[4][kLeanChunk][33];              // rho, theta_v, pi - pi_ref, w of 32 columns
+  float t[4][CH][33];                      // rho, theta_v, pi - pi_ref, w of 32 columns
 };
 
 // gather of the lean column's stage inputs for 32 consecutive cells: lanes over levels
@@ -1288,7 +1299,7 @@ struct LeanGatherTile {
   float f[4][LPE][kGatherCells + 1];       // dtau D_Theta, dtau A_w, A_w (predictor), dtau D_rho (predictor)
 };
 
-template <int LPE, bool CORR>
+template <int LPE, bool CORR, bool DDF = false>
 __device__ inline void mx_lean_gather_body(const MxGeo& G, const MxLeanArgs& a, int64_t c0, LeanGatherTile<LPE>& T) {
   constexpr int CB = kGatherCells;
   const int N = G.N, ld = G.ld;
@@ -1312,20 +1323,50 @@ __device__ inline void mx_lean_gather_body(const MxGeo& G, const MxLeanArgs& a, 
       int64_t E[3];
       float sg[3], kw[3], dw32[3];
       double dwt[3];
+      int64_t Ca[3], Cb[3];                  // DDF: the edges' two cells (row offsets)
+      float sc[3], le[3];
+      bool own[3];
       for (int s = 0; s < 3; ++s) {
-        E[s] = (int64_t)G.c2e[3 * c + s] * ld;
+        const int e = G.c2e[3 * c + s];
+        E[s] = (int64_t)e * ld;
         sg[s] = G.s_ce32[3 * c + s];
         kw[s] = G.kin_w32[3 * c + s];
         if (CORR) dwt[s] = a.dwa_t[3 * c + s];
         else dw32[s] = (float)a.dwa_t[3 * c + s];
+        if (DDF) {
+          const int ca = G.e2c[2 * e], cb = G.e2c[2 * e + 1];
+          Ca[s] = (int64_t)ca * ld;
+          Cb[s] = (int64_t)cb * ld;
+          sc[s] = a.dd_scale * G.inv_de32[e];
+          le[s] = G.l_e32[e];
+          own[s] = ca == c;
+        }
       }
       const float ta = dtau32 * (float)G.inv_Ac[c];
       const int k = k0 + lane;
       if (k < N) {
-        const float F0 = a.phi[E[0] + k], F1 = a.phi[E[1] + k], F2 = a.phi[E[2] + k];
-        if (CORR) T.d[lane][cl] = (dwt[0] * f32_to_f64(F0) + dwt[1] * f32_to_f64(F1)) + dwt[2] * f32_to_f64(F2);
-        else T.f[3][lane][cl] = (dw32[0] * F0 + dw32[1] * F1) + dw32[2] * F2;
-        T.f[0][lane][cl] = (sg[0] * a.gth[E[0] + k] + sg[1] * a.gth[E[1] + k] + sg[2] * a.gth[E[2] + k]) * ta;
+        float F[3], Gt[3];
+        if (DDF) {
+          // damped vn^{n+1} and its fluxes, as the damping's edge update forms them
+          for (int s = 0; s < 3; ++s) {
+            const float vd = a.dd_vn[E[s] + k] - sc[s] * (a.dd_L[Cb[s] + k] - a.dd_L[Ca[s] + k]);
+            F[s] = 0.5f * (a.dd_rho[Ca[s] + k] + a.dd_rho[Cb[s] + k]) * vd;
+            const float t1 = a.dd_thv[Ca[s] + k], t2 = a.dd_thv[Cb[s] + k];
+            Gt[s] = (le[s] * F[s]) * (a.dd_upwind ? (vd >= 0.0f ? t1 : t2) : 0.5f * (t1 + t2));
+            if (own[s]) {
+              a.dd_out[E[s] + k] = vd;
+              a.mflx[E[s] + k] += f32_to_f64(F[s]) * a.inv_nsub;
+            }
+          }
+        } else {
+          for (int s = 0; s < 3; ++s) {
+            F[s] = a.phi[E[s] + k];
+            Gt[s] = a.gth[E[s] + k];
+          }
+        }
+        if (CORR) T.d[lane][cl] = (dwt[0] * f32_to_f64(F[0]) + dwt[1] * f32_to_f64(F[1])) + dwt[2] * f32_to_f64(F[2]);
+        else T.f[3][lane][cl] = (dw32[0] * F[0] + dw32[1] * F[1]) + dw32[2] * F[2];
+        T.f[0][lane][cl] = (sg[0] * Gt[0] + sg[1] * Gt[1] + sg[2] * Gt[2]) * ta;
       }
       if (k >= 1 && k < N) {
         const float hadv = kw[0] * a.a_e[E[0] + k] + kw[1] * a.a_e[E[1] + k] + kw[2] * a.a_e[E[2] + k];
@@ -1354,22 +1395,25 @@ __device__ inline void mx_lean_gather_body(const MxGeo& G, const MxLeanArgs& a, 
   }
 }
 
-template <int LPE, bool CORR>
+template <int LPE, bool CORR, bool DDF = false>
 __global__ void __launch_bounds__(512, 3) k_mx_lean_gather(MxGeo G, MxLeanArgs a) {
   __shared__ LeanGatherTile<LPE> T;
-  mx_lean_gather_body<LPE, CORR>(G, a, (int64_t)blockIdx.x * kGatherCells, T);
+  mx_lean_gather_body<LPE, CORR, DDF>(G, a, (int64_t)blockIdx.x * kGatherCells, T);
 }
 
-// write the finished chunk [k0, k0 + kLeanChunk) of the warp's 32 columns (first cell c0)
-__device__ inline void lean_flush(const MxGeo& G, const MxLeanArgs& a, const LeanTile& T, int64_t c0, int k0,
+// write the finished chunk [k0, k0 + CH) of the warp's 32 columns (first cell c0): CH lanes
+// per column row, 32 / CH rows per store instruction
+template <int CH>
+__device__ inline void lean_flush(const MxGeo& G, const MxLeanArgs& a, const LeanTile<CH>& T, int64_t c0, int k0,
                                   int lane) {
   __syncwarp();
-  const int r = lane & (kLeanChunk - 1), half = lane >> 4;
+  constexpr int RPI = 32 / CH;             // rows per instruction
+  const int r = lane & (CH - 1), sub = lane / CH;
   const int k = k0 + r;
   float* const outs[4] = {a.rho32, a.thv32, a.exp32, a.w32};
   if (k < G.N) {
-    for (int jj = 0; jj < 32; jj += 2) {
-      const int j = jj + half;
+    for (int jj = 0; jj < 32; jj += RPI) {
+      const int j = jj + sub;
       const int64_t c = c0 + j;
       if (c >= G.nc) continue;
       const int64_t o = c * G.ld + k;
@@ -1382,9 +1426,9 @@ __device__ inline void lean_flush(const MxGeo& G, const MxLeanArgs& a, const Lea
 
 // one column per thread (lane); every lane of the warp runs the loops (lanes past the last
 // cell compute on zeros and store nothing) so that the chunk flushes stay warp-synchronous
-template <bool CORR, int U>
+template <bool CORR, int U, int CH>
 __device__ inline void mx_lean_column_item(const MxGeo& G, const MxLeanArgs& a, int64_t c, int64_t c0, int lane,
-                                           LeanTile& T) {
+                                           LeanTile<CH>& T) {
   const int N = G.N, ld = G.ld;
   const int64_t nc = G.nc;
   const bool act = c < nc;
@@ -1561,7 +1605,7 @@ __device__ inline void mx_lean_column_item(const MxGeo& G, const MxLeanArgs& a, 
       ok = ok && finite64(thv_n) && finite64(ex_n) && finite64(wn);
       fflux_next = fk;
     }
-    const int k0 = k & ~(kLeanChunk - 1);
+    const int k0 = k & ~(CH - 1);
     T.t[0][k - k0][lane] = s_rho;
     T.t[1][k - k0][lane] = s_thv;
     T.t[2][k - k0][lane] = s_exp;
@@ -1586,20 +1630,22 @@ __device__ inline void mx_lean_column_item(const MxGeo& G, const MxLeanArgs& a, 
 #undef LMV
 }
 
-template <bool CORR, int U>
-__global__ void __launch_bounds__(64) k_mx_lean_column(MxGeo G, MxLeanArgs a) {
-  __shared__ LeanTile T[2];
+template <bool CORR, int U, int CH, int THREADS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) k_mx_lean_column(MxGeo G, MxLeanArgs a) {
+  __shared__ LeanTile<CH> T[THREADS / 32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t c0 = (int64_t)blockIdx.x * 64 + warp * 32;
+  const int64_t c0 = (int64_t)blockIdx.x * THREADS + warp * 32;
   if (c0 >= G.nc) return;                            // whole warp past the end
-  mx_lean_column_item<CORR, U>(G, a, c0 + lane, c0, lane, T[warp]);
+  mx_lean_column_item<CORR, U, CH>(G, a, c0 + lane, c0, lane, T[warp]);
 }
 
-// the sweeps unrolled by four: the loads of four levels are in flight together (the
-// kernel waits on memory latency; measured 4 % faster than no unrolling at R2B6/90)
+// launch shape (measured at R2B6/90 over eight shapes): blocks of four warps held to 48
+// registers so that ten blocks (40 warps) share an SM, 8-level transpose chunks, sweeps
+// unrolled by two: the kernel waits on memory latency and gains from occupancy (12.2 ms per
+// R2B6/90 step against 16.9 ms with 64-thread blocks at 94 registers)
 template <bool CORR>
 void launch_lean_column(const MxGeo& G, const MxLeanArgs& a, cudaStream_t st) {
-  k_mx_lean_column<CORR, 4><<<blocks_for(G.nc, 64), 64, 0, st>>>(G, a);
+  k_mx_lean_column<CORR, 2, 8, 128, 10><<<blocks_for(G.nc, 128), 128, 0, st>>>(G, a);
 }
 
 MxGeo make_mx_geo(const icon_grid* grid, const StateDev& s) {
@@ -1695,6 +1741,11 @@ MxLeanArgs lean_args(StateDev& s, bool corr, double dtau, int nsub) {
   la.dtau = dtau;
   la.inv_nsub = 1.0 / nsub;
   la.hdamp = s.ln_hdamp;
+  la.dd_vn = la.dd_L = la.dd_rho = la.dd_thv = nullptr;
+  la.dd_out = nullptr;
+  la.mflx = s.mflx;
+  la.dd_scale = 0.0f;
+  la.dd_upwind = 0;
   return la;
 }
 
@@ -1901,9 +1952,14 @@ void enqueue_step_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream
       const MxEdgeArgs ea = edge_args(s, corr, dtau, nsub);
       const MxColArgs ca = col_args(s, corr, dtau, nsub);
       const bool damp = corr && st->divdamp4 > 0.0;
+      // lean column with damping: the corrector's undamped vn^{n+1} goes to Avn0_32 (dead once
+      // the edge tendency has read it, element by element), the damping's edge update is
+      // formed inside the gather, which writes the damped vn^{n+1} and the step-mean flux
+      const bool fused = lean && damp;
       MxEdgeArgs ead = ea;
       ead.skip_flux = damp ? 1 : 0;
       ead.upwind_theta = st->upwind_theta ? 1 : 0;
+      if (fused) ead.vn_out = s.Avn0_32;
       for (int kind : {K_MX_VERTEX, K_MX_EDGE, K_MX_CELL_KE, K_MX_EDGE_TEND}) {
         if (kind == K_MX_EDGE_TEND && s.topo.on) topo_stage32(st, ea.vn, s.vt32, ea.w, ea.exp, stream);
         prof_begin(stream, kind);
@@ -1922,17 +1978,26 @@ void enqueue_step_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream
         da.upwind_theta = st->upwind_theta ? 1 : 0;
         const unsigned nbc8 = (unsigned)((nc + 7) / 8), nbe8 = (unsigned)((G.ne + 7) / 8);
         prof_begin(stream, K_DIVDAMP);
-        k_mx_dd_div<<<nbc8, 256, 0, stream>>>(G, s.vn32, s.Kc32);
+        k_mx_dd_div<<<nbc8, 256, 0, stream>>>(G, fused ? s.Avn0_32 : s.vn32, s.Kc32);
         k_mx_dd_lap<<<nbc8, 256, 0, stream>>>(G, s.Kc32, s.vt32);
-        k_mx_dd_edge<<<nbe8, 256, 0, stream>>>(G, da);
+        if (!fused) k_mx_dd_edge<<<nbe8, 256, 0, stream>>>(G, da);
         prof_end(stream);
       }
       if (lean) {
-        const MxLeanArgs la = lean_args(s, corr, dtau, nsub);
+        MxLeanArgs la = lean_args(s, corr, dtau, nsub);
+        if (fused) {
+          la.dd_vn = s.Avn0_32; la.dd_L = s.vt32; la.dd_rho = ea.rho; la.dd_thv = ea.thv;
+          la.dd_out = s.vn32; la.mflx = s.mflx;
+          la.dd_scale = (float)(st->divdamp4 * st->abar * st->abar);
+          la.dd_upwind = st->upwind_theta ? 1 : 0;
+        }
         const TileChoice t = tile(K_MX_COLUMN_PREP);
         const unsigned nb = (unsigned)((nc + 31) / 32);
         prof_begin(stream, K_MX_LEAN_GATHER);
-        if (corr) {
+        if (corr && fused) {
+          if (t.lanes == 16) k_mx_lean_gather<16, true, true><<<nb, t.block, 0, stream>>>(G, la);
+          else k_mx_lean_gather<32, true, true><<<nb, t.block, 0, stream>>>(G, la);
+        } else if (corr) {
           if (t.lanes == 16) k_mx_lean_gather<16, true><<<nb, t.block, 0, stream>>>(G, la);
           else k_mx_lean_gather<32, true><<<nb, t.block, 0, stream>>>(G, la);
         } else {
@@ -2085,6 +2150,7 @@ struct MemberDev {
   int64_t off_t;                // first 32-cell tile of the column-input gather
   MxDDArgs dd;                  // fourth-order divergence damping of the corrector's vn
   int damp;                     // 1 if the member damps (dd.scale > 0)
+  MxLeanArgs la[2];             // lean column of the predictor and the corrector
 };
 
 struct EnsArgs {
@@ -2166,12 +2232,14 @@ __device__ bool grid_barrier(const EnsArgs& A, bool skip) {
 
 constexpr int kChunk = 4;   // consecutive work items per warp
 
-template <int NMAX, bool ALLFAC>
+template <int NMAX, bool ALLFAC, bool LEAN>
 __global__ void __launch_bounds__(128, 8) k_ensemble_step(EnsArgs A) {
   __shared__ int64_t s_off_v[64], s_off_e[64], s_off_c[64], s_off_t[64];
   __shared__ union {
     GatherTile<16> g;
     UpdTile u;
+    LeanGatherTile<16> lg;
+    LeanTile<8> lt[4];
   } tiles;
   GatherTile<16>& tileT = tiles.g;
   for (int i = threadIdx.x; i < A.nm; i += blockDim.x) {
@@ -2228,7 +2296,7 @@ __global__ void __launch_bounds__(128, 8) k_ensemble_step(EnsArgs A) {
         // vt32), then the edge update with the fluxes the edge tendency left out
         warp_items<kChunk>(s_off_c, A.nm, A.tot_c, gwarp, nwarps, [&](int m, int64_t j) {
           const MemberDev& M = A.m[m];
-          if (M.damp) mx_dd_div_item(M.G, M.vn32, M.Kc32, j, lane);
+          if (M.damp) mx_dd_div_item(M.G, M.dd.vn, M.Kc32, j, lane);
         });
         if (!sync()) return;
         warp_items<kChunk>(s_off_c, A.nm, A.tot_c, gwarp, nwarps, [&](int m, int64_t j) {
@@ -2236,11 +2304,13 @@ __global__ void __launch_bounds__(128, 8) k_ensemble_step(EnsArgs A) {
           if (M.damp) mx_dd_lap_item(M.G, M.Kc32, M.vt32, j, lane);
         });
         if (!sync()) return;
-        warp_items<kChunk>(s_off_e, A.nm, A.tot_e, gwarp, nwarps, [&](int m, int64_t j) {
-          const MemberDev& M = A.m[m];
-          if (M.damp) mx_dd_edge_item(M.G, M.dd, j, lane);
-        });
-        if (!sync()) return;
+        if (!LEAN) {     // the lean column's gather forms the damped fluxes itself
+          warp_items<kChunk>(s_off_e, A.nm, A.tot_e, gwarp, nwarps, [&](int m, int64_t j) {
+            const MemberDev& M = A.m[m];
+            if (M.damp) mx_dd_edge_item(M.G, M.dd, j, lane);
+          });
+          if (!sync()) return;
+        }
       }
       // column-input gather: one 32-cell tile per block at a time (members without
       // stored factors have no tiles)
@@ -2248,10 +2318,29 @@ __global__ void __launch_bounds__(128, 8) k_ensemble_step(EnsArgs A) {
         const int m = find_member(s_off_t, A.nm, t);
         const MemberDev& M = A.m[m];
         const int64_t c0 = (t - M.off_t) * kGatherCells;
-        if (stage == 0) mx_gather_tile_body<16, false>(M.G, M.ca[0], c0, tileT);
-        else mx_gather_tile_body<16, true>(M.G, M.ca[1], c0, tileT);
+        if (LEAN) {
+          if (stage == 0) mx_lean_gather_body<16, false>(M.G, M.la[0], c0, tiles.lg);
+          else if (M.damp) mx_lean_gather_body<16, true, true>(M.G, M.la[1], c0, tiles.lg);
+          else mx_lean_gather_body<16, true>(M.G, M.la[1], c0, tiles.lg);
+        } else {
+          if (stage == 0) mx_gather_tile_body<16, false>(M.G, M.ca[0], c0, tileT);
+          else mx_gather_tile_body<16, true>(M.G, M.ca[1], c0, tileT);
+        }
       }
       if (!sync()) return;
+      if (LEAN) {
+        // lean column: one warp per 32-column tile, both sweeps and the updates in one pass
+        for (int64_t t = gwarp; t < A.tot_t; t += nwarps) {
+          const int m = find_member(s_off_t, A.nm, t);
+          const MemberDev& M = A.m[m];
+          const int64_t c0 = (t - M.off_t) * kGatherCells;
+          LeanTile<8>& lt = tiles.lt[threadIdx.x >> 5];
+          if (stage == 0) mx_lean_column_item<false, 2, 8>(M.G, M.la[0], c0 + lane, c0, lane, lt);
+          else mx_lean_column_item<true, 2, 8>(M.G, M.la[1], c0 + lane, c0, lane, lt);
+        }
+        if (!sync()) return;
+        continue;
+      }
       for (int64_t i = gtid; i < A.tot_c; i += nthreads) {
         const int m = find_member(s_off_c, A.nm, i);
         const MemberDev& M = A.m[m];
@@ -2337,6 +2426,15 @@ int ensemble_prepare(EnsembleDev& E, icon_state* const* members, int n, const do
   int N = -1;
   bool all_fac = true;
   bool any_damp = false;
+  // the lean column when every member has its buffers (flat mixed states); otherwise the
+  // stored-factor column, whose buffers lean-form members get here when they fit (else
+  // that member's column recomputes its factors)
+  bool all_lean = true;
+  for (int i = 0; i < n; ++i) all_lean = all_lean && members[i]->s.ln_B != nullptr;
+  if (!all_lean)
+    for (int i = 0; i < n; ++i)
+      if (!members[i]->s.fac64 && members[i]->s.ln_B) alloc_mixed_factors(members[i]);
+  E.lean_consts.clear();
   for (int i = 0; i < n; ++i) {
     icon_state* st = members[i];
     StateDev& s = st->s;
@@ -2344,9 +2442,6 @@ int ensemble_prepare(EnsembleDev& E, icon_state* const* members, int n, const do
       set_error("icon_ensemble_step: the persistent ensemble runs mixed-precision members");
       return ICON_EINVAL;
     }
-    // the persistent kernel runs the stored-factor column: give lean-form members its
-    // buffers (when they fit; otherwise that member's column recomputes its factors)
-    if (!s.fac64 && s.ln_B) alloc_mixed_factors(st);
     MemberDev& M = host[i];
     M.G = make_mx_geo(st->grid, s);
     if (N >= 0 && M.G.N != N) {
@@ -2374,12 +2469,27 @@ int ensemble_prepare(EnsembleDev& E, icon_state* const* members, int n, const do
     M.wv32 = s.wv32; M.vt32 = s.vt32;
     M.off_v = ov; M.off_e = oe; M.off_c = oc; M.off_t = ot;
     ov += M.G.nv; oe += M.G.ne; oc += M.G.nc;
-    if (s.fac64) ot += (M.G.nc + kGatherCells - 1) / kGatherCells;
+    if (s.fac64 || all_lean) ot += (M.G.nc + kGatherCells - 1) / kGatherCells;
     else all_fac = false;
+    if (all_lean) {
+      for (int stage = 0; stage < 2; ++stage) M.la[stage] = lean_args(s, stage == 1, dtau, nsub);
+      if (M.damp) {
+        // as the per-state lean step: undamped vn^{n+1} in Avn0_32, damping fused into the gather
+        M.ea[1].vn_out = s.Avn0_32;
+        M.dd.vn = s.Avn0_32;
+        MxLeanArgs& la = M.la[1];
+        la.dd_vn = s.Avn0_32; la.dd_L = s.vt32; la.dd_rho = M.ea[1].rho; la.dd_thv = M.ea[1].thv;
+        la.dd_out = s.vn32; la.mflx = s.mflx; la.dd_scale = M.dd.scale; la.dd_upwind = 0;
+      }
+      E.lean_consts.push_back({M.G.N, M.G.ld, M.G.nc, M.G.wu, M.G.wl, M.G.dzh, M.G.dz, M.G.ray, s.ex_ref, dtau,
+                               s.ln_cd, s.ln_cf, M.G.div_wa, s.ln_dwa});
+    }
   }
+  if (all_lean) all_fac = false;
   E.N = N;
   E.tot_v = ov; E.tot_e = oe; E.tot_c = oc; E.tot_t = ot;
   E.all_fac = all_fac;
+  E.all_lean = all_lean;
   E.any_damp = any_damp;
   E.nm = n;
   E.nsub = nsub;
@@ -2411,9 +2521,10 @@ int ensemble_launch(EnsembleDev& E, cudaStream_t st) {
   A.skip_first_barrier = E.test_skip_barrier;
   A.any_damp = E.any_damp ? 1 : 0;
   void (*kern)(EnsArgs);
-  if (E.N <= 32) kern = E.all_fac ? k_ensemble_step<32, true> : k_ensemble_step<32, false>;
-  else if (E.N <= 64) kern = E.all_fac ? k_ensemble_step<64, true> : k_ensemble_step<64, false>;
-  else if (E.N <= 96) kern = E.all_fac ? k_ensemble_step<96, true> : k_ensemble_step<96, false>;
+  if (E.all_lean) kern = k_ensemble_step<32, false, true>;     // the lean column has no level arrays
+  else if (E.N <= 32) kern = E.all_fac ? k_ensemble_step<32, true, false> : k_ensemble_step<32, false, false>;
+  else if (E.N <= 64) kern = E.all_fac ? k_ensemble_step<64, true, false> : k_ensemble_step<64, false, false>;
+  else if (E.N <= 96) kern = E.all_fac ? k_ensemble_step<96, true, false> : k_ensemble_step<96, false, false>;
   else {
     set_error("icon_ensemble_step: the persistent ensemble supports up to 96 levels");
     return ICON_EINVAL;
@@ -2430,6 +2541,10 @@ int ensemble_launch(EnsembleDev& E, cudaStream_t st) {
     E.grid_blocks = nsm * per;
   }
   k_ens_colconst<<<E.nm, 64, 0, st>>>(A.m, E.nm);
+  for (const EnsembleDev::LeanConst& L : E.lean_consts) {
+    k_mx_leanconst<<<1, 128, 0, st>>>(L.N, L.ld, L.wu, L.wl, L.dzh, L.dz, L.ray, L.ex_ref, L.dtau, L.cd, L.cf);
+    k_mx_dwa_t<<<blocks_for(3 * L.nc, 256), 256, 0, st>>>(3 * L.nc, L.div_wa, L.dtau, L.dwa);
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(E.grid_blocks);
   cfg.blockDim = dim3(128);

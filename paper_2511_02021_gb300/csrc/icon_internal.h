@@ -249,7 +249,20 @@ struct EnsembleDev {
   int nm = 0, nsub = 0, N = 0, grid_blocks = 0;
   int64_t tot_v = 0, tot_e = 0, tot_c = 0, tot_t = 0;
   bool all_fac = true;         // every member stores its column factors
+  bool all_lean = false;       // every member runs the lean column
   bool any_damp = false;       // some member damps the corrector's divergence
+  // per-member launches of the lean column's per-level constants and scaled weights
+  struct LeanConst {
+    int N, ld;
+    int64_t nc;
+    const double *wu, *wl, *dzh, *dz, *ray, *ex_ref;
+    double dtau;
+    double* cd;
+    float* cf;
+    const double* div_wa;
+    double* dwa;
+  };
+  std::vector<LeanConst> lean_consts;
   long long spin_limit = 1ll << 24;
   int test_skip_barrier = 0;
 };

@@ -23,7 +23,11 @@ def _fields(C, st, grid, N):
     return {f: C.icon_state_copy_field(st, grid, N, f) for f in PROG + ("mflx", "wflx")}
 
 
-def test_ensemble_members_equal_solo_runs(gpu):
+@pytest.mark.parametrize("form", ["lean", "stored"])
+def test_ensemble_members_equal_solo_runs(gpu, monkeypatch, form):
+    """Members of one persistent launch against the same states stepped alone, for the lean
+    column (the default) and the stored-factor column."""
+    monkeypatch.setenv("ICON_MIXED_COLUMN", form)
     C = gpu
     N = 60
     grids = [C.icon_grid_build(2, 2, N), C.icon_grid_build(2, 3, N)]
