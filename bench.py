@@ -745,6 +745,12 @@ def ensemble_leg(gpu, hbm_peak, rank, world, steps, warmup):
             arr = (C.ctypes.c_double * len(dts))(*dts)
             ms_b = timed(lambda: C._check(C._lib.icon_ensemble_step(ens, arr, nsub, steps)))
             clk = clk.stop() if clk else None
+            # after the timed region: one step with the phase timer (block 0 stamps the
+            # global timer at every grid barrier), the breakdown of the persistent launch
+            pms, pcnt = C.icon_ensemble_step_profile(ens, dts, nsub)
+            phases = {C.icon_ensemble_phase_name(k): {"ms_per_step": round(float(pms[k]), 3),
+                                                      "barriers_per_step": int(pcnt[k])}
+                      for k in range(C.ICON_ENS_PHASE_COUNT) if pcnt[k]}
         finally:
             C.icon_ensemble_free(ens)
             for st in sts:
@@ -788,7 +794,8 @@ def ensemble_leg(gpu, hbm_peak, rank, world, steps, warmup):
             "roofline": roof, "clocks": clk, "hbm_roofline": step_hbm_roofline(value_b, 1, hbm_peak),
             "sequential": {"value": value_s, "unit": UNIT, "ms_per_step": ms_s / steps,
                            "gpu_launches_per_step": launches_seq},
-            "batched_speedup_vs_sequential": value_b / value_s}
+            "batched_speedup_vs_sequential": value_b / value_s,
+            "phases": phases}
 
 
 def run_single(args, wl, rank, world, local_rank):

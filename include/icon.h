@@ -474,6 +474,38 @@ int icon_ensemble_step(icon_ensemble* ens, const double* dt_per_member, int nsub
 #define ICON_ENS_TEST_SKIP_BARRIER 2
 int icon_ensemble_set_option(icon_ensemble* ens, int option, long long value);
 
+/* Phases of the persistent ensemble step, in the order they run (each a work list over
+ * all members ended by a grid barrier; the damping phases only when a member damps,
+ * the corrector-update phase only with stored column factors). */
+#define ICON_ENS_PH_ZERO 0          /* zero the step-mean fluxes */
+#define ICON_ENS_PH_VERTEX 1        /* vertex curl and w at vertices */
+#define ICON_ENS_PH_EDGE_DIAG 2     /* tangential velocity */
+#define ICON_ENS_PH_CELL_KE 3       /* cell kinetic energy */
+#define ICON_ENS_PH_EDGE_TEND 4     /* vn tendency and update, edge fluxes */
+#define ICON_ENS_PH_DD_DIV 5        /* divergence damping: cell divergence */
+#define ICON_ENS_PH_DD_LAP 6        /* divergence damping: its Laplacian */
+#define ICON_ENS_PH_DD_EDGE 7       /* divergence damping: edge update (not in the lean form) */
+#define ICON_ENS_PH_GATHER 8        /* column inputs gathered from the edges */
+#define ICON_ENS_PH_COLUMN 9        /* vertically implicit column solve */
+#define ICON_ENS_PH_CORR_UPDATE 10  /* corrector update with stored factors */
+#define ICON_ENS_PH_DIFF_VERTEX 11  /* diffusion: vertex and cell terms */
+#define ICON_ENS_PH_DIFF_EDGE 12    /* diffusion: edge update */
+#define ICON_ENS_PH_DIFF_THETA 13   /* diffusion: theta_v and Exner */
+#define ICON_ENS_PHASE_COUNT 14
+
+/* Advance every member by ONE step as icon_ensemble_step does, launched outside the
+ * graph with a phase timer: block 0 of the persistent kernel reads the GPU's global
+ * timer as it leaves each grid barrier. Adds each phase's wall time (ms, from the
+ * previous barrier to the one that closes it; the last phase up to the kernel's end
+ * measured with CUDA events) to ms_per_phase[kind] and 1 per barrier to
+ * count_per_phase[kind] (host arrays of ICON_ENS_PHASE_COUNT entries, accumulated, not
+ * cleared). Waits; errors as icon_ensemble_step. */
+int icon_ensemble_step_profile(icon_ensemble* ens, const double* dt_per_member, int nsubsteps, double* ms_per_phase,
+                               int* count_per_phase);
+
+/* Name of ensemble phase i (0 <= i < ICON_ENS_PHASE_COUNT), or NULL. */
+const char* icon_ensemble_phase_name(int phase);
+
 void icon_ensemble_free(icon_ensemble* ens);
 
 #ifdef __cplusplus

@@ -85,6 +85,8 @@ def _load():
         "icon_ensemble_create": (I, [ctypes.POINTER(P), I, ctypes.POINTER(P)]),
         "icon_ensemble_step": (I, [P, ctypes.POINTER(D), I, I]), "icon_ensemble_free": (None, [P]),
         "icon_ensemble_set_option": (I, [P, I, ctypes.c_longlong]),
+        "icon_ensemble_step_profile": (I, [P, ctypes.POINTER(D), I, ctypes.POINTER(D), ctypes.POINTER(I)]),
+        "icon_ensemble_phase_name": (ctypes.c_char_p, [I]),
         "icon_state_tiling": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "icon_state_set_tiling": (I, [P, I, I, I]),
         "icon_state_set_option": (I, [P, I, D]),
@@ -302,6 +304,24 @@ def icon_ensemble_step(ens, dts, nsubsteps, nsteps):
 
 
 ICON_ENS_SPIN_LIMIT, ICON_ENS_TEST_SKIP_BARRIER = 1, 2
+ICON_ENS_PHASE_COUNT = 14
+
+
+def icon_ensemble_step_profile(ens, dts, nsubsteps, ms=None, counts=None):
+    """One ensemble step with the phase timer; returns the accumulated (ms per phase,
+    barriers per phase) arrays."""
+    if ms is None:
+        ms = np.zeros(ICON_ENS_PHASE_COUNT)
+        counts = np.zeros(ICON_ENS_PHASE_COUNT, dtype=np.int32)
+    arr = (ctypes.c_double * len(dts))(*dts)
+    _check(_lib.icon_ensemble_step_profile(ens, arr, nsubsteps, ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                           counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+    return ms, counts
+
+
+def icon_ensemble_phase_name(phase):
+    n = _lib.icon_ensemble_phase_name(phase)
+    return n.decode() if n else None
 # mixed-precision stencil kinds that take a tile
 KIND_MX_VERTEX, KIND_MX_EDGE, KIND_MX_CELL_KE, KIND_MX_EDGE_TEND, KIND_MX_COLUMN_PREP, KIND_MX_DIFF_VERTEX = \
     10, 11, 12, 13, 15, 16

@@ -299,6 +299,7 @@ int alloc_state(icon_state* st, int precision, bool topo) {
       s.ln_cd = A.get_n<double>(8 * (size_t)ld);
       s.ln_cf = A.get_n<float>(8 * (size_t)ld);
       s.ln_dwa = A.get_n<double>(3 * (size_t)nc);
+      s.ln_cw32 = A.get_n<float>(4 * (size_t)nc);
       int hd = 0;
       for (int h = 0; h <= grid->vert.N; ++h)
         if (grid->vert.rayleigh[h] > 0.0) hd = h + 1;
@@ -844,6 +845,8 @@ struct icon_ensemble {
   bool prepared = false;
   cudaGraphExec_t graph = nullptr;
   cudaStream_t capture_stream = nullptr;
+  unsigned long long* prof = nullptr;   // phase stamps of icon_ensemble_step_profile
+  int prof_cap = 0;
 };
 
 extern "C" {
@@ -1027,6 +1030,98 @@ int icon_ensemble_step(icon_ensemble* ens, const double* dt_per_member, int nsub
     ICON_CUDA(cudaStreamSynchronize(stream));
     set_error("icon_ensemble_step: a grid-barrier wait ran out; the members' states are not valid");
     return ICON_ETIMEOUT;
+  }
+  return worst;
+}
+
+static const char* kEnsPhaseNames[ICON_ENS_PHASE_COUNT] = {
+    "zero", "vertex", "edge_diag", "cell_ke", "edge_tend", "dd_div", "dd_lap",
+    "dd_edge", "gather", "column", "corr_update", "diff_vertex", "diff_edge", "diff_theta"};
+
+const char* icon_ensemble_phase_name(int phase) {
+  if (phase < 0 || phase >= ICON_ENS_PHASE_COUNT) return nullptr;
+  return kEnsPhaseNames[phase];
+}
+
+int icon_ensemble_step_profile(icon_ensemble* ens, const double* dt_per_member, int nsubsteps, double* ms_per_phase,
+                               int* count_per_phase) {
+  if (!ens || !dt_per_member || !ms_per_phase || !count_per_phase || nsubsteps < 1 || nsubsteps > 64) {
+    set_error("icon_ensemble_step_profile: bad arguments");
+    return ICON_EINVAL;
+  }
+  const int n = (int)ens->members.size();
+  for (int i = 0; i < n; ++i)
+    if (!(dt_per_member[i] > 0.0)) { set_error("icon_ensemble_step_profile: dt of member %d must be > 0", i); return ICON_EINVAL; }
+  std::vector<double> dts(dt_per_member, dt_per_member + n);
+  if (!ens->prepared || dts != ens->dts || nsubsteps != ens->nsub) {
+    int rc = ensemble_prepare(ens->E, ens->members.data(), n, dts.data(), nsubsteps);
+    if (rc != ICON_OK) return rc;
+    ens->prepared = true;
+    ens->dts = dts;
+    ens->nsub = nsubsteps;
+    if (ens->graph) {
+      cudaGraphExecDestroy(ens->graph);
+      ens->graph = nullptr;
+    }
+  }
+  // barriers per step: 1 + nsub x 2 stages x (at most 10) + 2, and the start and end stamps
+  const int cap = 8 + 20 * nsubsteps;
+  if (!ens->prof || ens->prof_cap < cap) {
+    ens->prof = ens->E.arena.get_n<unsigned long long>(2 * (size_t)cap);
+    if (!ens->prof) { set_error("icon_ensemble_step_profile: out of device memory"); return ICON_ENOMEM; }
+    ens->prof_cap = cap;
+  }
+  cudaStream_t stream = current_stream();
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ICON_CUDA(cudaEventCreate(&e0));
+  ICON_CUDA(cudaEventCreate(&e1));
+  ICON_CUDA(cudaMemsetAsync(ens->prof, 0, sizeof(unsigned long long) * 2 * cap, stream));
+  ICON_CUDA(cudaMemsetAsync(ens->E.bar, 0, 16 * sizeof(unsigned), stream));
+  ICON_CUDA(cudaEventRecord(e0, stream));
+  int rc = ensemble_launch(ens->E, stream, ens->prof, cap);
+  ICON_CUDA(cudaEventRecord(e1, stream));
+  std::vector<unsigned long long> h(2 * (size_t)cap);
+  unsigned bar_status = 0;
+  ICON_CUDA(cudaMemcpyAsync(h.data(), ens->prof, sizeof(unsigned long long) * h.size(), cudaMemcpyDeviceToHost, stream));
+  ICON_CUDA(cudaMemcpyAsync(&bar_status, ens->E.bar + 8, sizeof(unsigned), cudaMemcpyDeviceToHost, stream));
+  ICON_CUDA(cudaStreamSynchronize(stream));
+  float total = 0.f;
+  cudaEventElapsedTime(&total, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != ICON_OK) return rc;
+  if (bar_status & 2u) {
+    ICON_CUDA(cudaMemsetAsync(ens->E.bar, 0, 16 * sizeof(unsigned), stream));
+    ICON_CUDA(cudaStreamSynchronize(stream));
+    set_error("icon_ensemble_step_profile: a grid-barrier wait ran out; the members' states are not valid");
+    return ICON_ETIMEOUT;
+  }
+  // stamps: (kind, ns) pairs, the first the start (kind ICON_ENS_PHASE_COUNT), the last
+  // block 0's end of the final phase
+  int ns = 0;
+  while (ns < cap && h[2 * ns + 1] != 0) ++ns;
+  double used = 0.0;
+  for (int i = 1; i < ns; ++i) {
+    const int kind = (int)h[2 * i];
+    const double ms = (double)(h[2 * i + 1] - h[2 * i - 1]) * 1e-6;
+    if (i == ns - 1) break;                            // the last phase: closed below
+    if (kind >= 0 && kind < ICON_ENS_PHASE_COUNT) {
+      ms_per_phase[kind] += ms;
+      count_per_phase[kind] += 1;
+      used += ms;
+    }
+  }
+  if (ns >= 2) {
+    const int kind = (int)h[2 * (ns - 1)];
+    if (kind >= 0 && kind < ICON_ENS_PHASE_COUNT) {
+      ms_per_phase[kind] += total - used > 0.0 ? total - used : 0.0;
+      count_per_phase[kind] += 1;
+    }
+  }
+  int worst = ICON_OK;
+  for (int i = 0; i < n; ++i) {
+    int r = sync_status(ens->members[i], stream);
+    if (r != ICON_OK) worst = r;
   }
   return worst;
 }

@@ -1270,6 +1270,7 @@ struct MxLeanArgs {
   const double* cd;                        // per-level constants (FP64)
   const float* cf;                         // per-level constants (FP32)
   const double* dwa_t;                     // [Nc][3] dtau s l / A_c (FP64)
+  const float4* cw32;                      // [Nc] FP32 dtau s l / A_c of the three edges, dtau / A_c
   unsigned* status;
   double dtau, inv_nsub;
   int hdamp;                               // half levels h < hdamp are Rayleigh-damped
@@ -1321,8 +1322,10 @@ __device__ inline void mx_lean_gather_body(const MxGeo& G, const MxLeanArgs& a, 
       if (c >= nc) break;
       const int64_t o = c * ld;
       int64_t E[3];
-      float sg[3], kw[3], dw32[3];
+      float sg[3], kw[3];
       double dwt[3];
+      const float4 cw = a.cw32[c];
+      const float dw32[3] = {cw.x, cw.y, cw.z};
       int64_t Ca[3], Cb[3];                  // DDF: the edges' two cells (row offsets)
       float sc[3], le[3];
       bool own[3];
@@ -1332,7 +1335,6 @@ __device__ inline void mx_lean_gather_body(const MxGeo& G, const MxLeanArgs& a, 
         sg[s] = G.s_ce32[3 * c + s];
         kw[s] = G.kin_w32[3 * c + s];
         if (CORR) dwt[s] = a.dwa_t[3 * c + s];
-        else dw32[s] = (float)a.dwa_t[3 * c + s];
         if (DDF) {
           const int ca = G.e2c[2 * e], cb = G.e2c[2 * e + 1];
           Ca[s] = (int64_t)ca * ld;
@@ -1342,7 +1344,7 @@ __device__ inline void mx_lean_gather_body(const MxGeo& G, const MxLeanArgs& a, 
           own[s] = ca == c;
         }
       }
-      const float ta = dtau32 * (float)G.inv_Ac[c];
+      const float ta = cw.w;
       const int k = k0 + lane;
       if (k < N) {
         float F[3], Gt[3];
@@ -1744,6 +1746,7 @@ MxLeanArgs lean_args(StateDev& s, bool corr, double dtau, int nsub) {
   la.cd = s.ln_cd;
   la.cf = s.ln_cf;
   la.dwa_t = s.ln_dwa;
+  la.cw32 = reinterpret_cast<const float4*>(s.ln_cw32);
   la.status = s.status;
   la.dtau = dtau;
   la.inv_nsub = 1.0 / nsub;
@@ -1756,9 +1759,22 @@ MxLeanArgs lean_args(StateDev& s, bool corr, double dtau, int nsub) {
   return la;
 }
 
-__global__ void k_mx_dwa_t(int64_t n3, const double* __restrict__ div_wa, double dtau, double* __restrict__ out) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n3) out[i] = dtau * div_wa[i];
+// the gather's per-cell weights for one dtau: FP64 dtau s l / A_c of the three edges, and
+// their FP32 roundings with the FP32 dtau / A_c (formed as the product of the two FP32
+// roundings), so that the gather's inner loop converts nothing
+__global__ void k_mx_dwa_t(int64_t nc, const double* __restrict__ div_wa, const double* __restrict__ inv_Ac,
+                           double dtau, double* __restrict__ out, float* __restrict__ out32) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  float4 f;
+  float* fp = &f.x;
+  for (int s = 0; s < 3; ++s) {
+    const double v = dtau * div_wa[3 * c + s];
+    out[3 * c + s] = v;
+    fp[s] = (float)v;
+  }
+  f.w = (float)dtau * (float)inv_Ac[c];
+  reinterpret_cast<float4*>(out32)[c] = f;
 }
 
 // ---------------------------------------------------------------- launch helpers with tile choices
@@ -1950,7 +1966,7 @@ void enqueue_step_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream
   const bool lean = s.ln_B != nullptr;
   if (lean) {
     k_mx_leanconst<<<1, 128, 0, stream>>>(G.N, G.ld, G.wu, G.wl, G.dzh, G.dz, G.ray, s.ex_ref, dtau, s.ln_cd, s.ln_cf);
-    k_mx_dwa_t<<<blocks_for(3 * nc, 256), 256, 0, stream>>>(3 * nc, G.div_wa, dtau, s.ln_dwa);
+    k_mx_dwa_t<<<blocks_for(nc, 256), 256, 0, stream>>>(nc, G.div_wa, G.inv_Ac, dtau, s.ln_dwa, s.ln_cw32);
   }
   auto tile = [&](int kind) { return st->tile[kind].lanes ? st->tile[kind] : TileChoice{32, 256}; };
   for (int it = 0; it < nsub; ++it) {
@@ -2169,7 +2185,15 @@ struct EnsArgs {
   long long spin_limit;
   int skip_first_barrier;       // test hook: block 0 does not arrive at the first barrier
   int any_damp;                 // some member damps: the corrector runs the damping phases
+  unsigned long long* prof;     // if set: (phase kind, global ns) after every barrier, by block 0
+  int prof_max;                 // entries (pairs) prof holds
 };
+
+__device__ inline unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 __device__ inline int find_member(const int64_t* off, int nm, int64_t item) {
   int lo = 0, hi = nm - 1;
@@ -2196,6 +2220,40 @@ __device__ inline void warp_items(const int64_t* off, int nm, int64_t tot, int64
         next = m + 1 < nm ? off[m + 1] : tot;
       }
       f(m, i - off[m]);
+    }
+  }
+}
+
+// the same work list taken two items at a time: when both items of a pair belong to one
+// member, the two half-warps take one each with 16 lanes over the levels (f16(m, first item
+// of the pair)); a pair that straddles a member boundary is taken by the whole warp, one
+// item after the other (f32(m, item))
+template <int K, typename F16, typename F32>
+__device__ inline void warp_pairs(const int64_t* off, int nm, int64_t tot, int64_t gwarp, int64_t nwarps, F16 f16,
+                                  F32 f32) {
+  static_assert(K % 2 == 0, "pairs");
+  for (int64_t i0 = gwarp * K; i0 < tot; i0 += nwarps * K) {
+    int m = find_member(off, nm, i0);
+    int64_t next = m + 1 < nm ? off[m + 1] : tot;
+    for (int j = 0; j < K; j += 2) {
+      const int64_t i = i0 + j;
+      if (i >= tot) break;
+      while (i >= next) {
+        ++m;
+        next = m + 1 < nm ? off[m + 1] : tot;
+      }
+      if (i + 1 < next) {
+        f16(m, i - off[m]);
+      } else {
+        f32(m, i - off[m]);
+        if (i + 1 < tot) {
+          while (i + 1 >= next) {
+            ++m;
+            next = m + 1 < nm ? off[m + 1] : tot;
+          }
+          f32(m, i + 1 - off[m]);
+        }
+      }
     }
   }
 }
@@ -2238,16 +2296,80 @@ __device__ bool grid_barrier(const EnsArgs& A, bool skip) {
 
 constexpr int kChunk = 4;   // consecutive work items per warp
 
+// Each warp copies its current member's geometry and phase arguments into shared memory
+// when the member changes. Read from the global member table, every field would be
+// reloaded after each store of a phase (a global store may alias the table); read from
+// shared memory they cannot alias, as the kernel parameters of the per-state kernels
+// cannot. (Keeping a phase out of line, with registers of its own, measured slower: the
+// call saves and restores the caller's registers.)
+union MemberArgs {
+  MxEdgeArgs ea;
+  MxLeanArgs la;
+};
+static_assert(sizeof(MxGeo) % 8 == 0 && sizeof(MxEdgeArgs) % 8 == 0 && sizeof(MxLeanArgs) % 8 == 0,
+              "member structs are copied in 8-byte words");
+__shared__ MxGeo s_ens_geo[4];
+__shared__ MemberArgs s_ens_arg[4];
+
+struct SlotCache {
+  const MemberDev* mt;
+  int geo_m = -1, arg_m = -1;
+  __device__ explicit SlotCache(const MemberDev* t) : mt(t) {}
+  __device__ static void copy(void* dst, const void* src, int bytes) {
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    for (int i = lane; i < bytes / 8; i += 32)
+      static_cast<unsigned long long*>(dst)[i] = static_cast<const unsigned long long*>(src)[i];
+    __syncwarp();
+  }
+  __device__ const MxGeo& geo(int m) {
+    MxGeo& g = s_ens_geo[threadIdx.x >> 5];
+    if (m != geo_m) {
+      copy(&g, &mt[m].G, sizeof(MxGeo));
+      geo_m = m;
+    }
+    return g;
+  }
+  __device__ const MxEdgeArgs& edge(int m, int stage) {
+    MxEdgeArgs& e = s_ens_arg[threadIdx.x >> 5].ea;
+    if (m != arg_m) {
+      copy(&e, &mt[m].ea[stage], sizeof(MxEdgeArgs));
+      arg_m = m;
+    }
+    return e;
+  }
+  __device__ const MxLeanArgs& lean(int m, int stage) {
+    MxLeanArgs& l = s_ens_arg[threadIdx.x >> 5].la;
+    if (m != arg_m) {
+      copy(&l, &mt[m].la[stage], sizeof(MxLeanArgs));
+      arg_m = m;
+    }
+    return l;
+  }
+};
+
+// shared tiles of the persistent kernel: the lean form needs only the lean gather tile and
+// the column's shadow transposes (8-level chunks; 4-level chunks, which would leave the
+// stencil phases more L1, measured 13 % slower in the column and no faster elsewhere); the
+// stored-factor forms need the gather and corrector-update tiles
+constexpr int kEnsLeanCH = 8;
+template <bool LEAN>
+union EnsTiles {
+  GatherTile<16> g;
+  UpdTile u;
+  LeanGatherTile<16> lg;
+  LeanTile<8> lt[4];
+};
+template <>
+union EnsTiles<true> {
+  LeanGatherTile<16> lg;
+  LeanTile<kEnsLeanCH> lt[4];
+};
+
 template <int NMAX, bool ALLFAC, bool LEAN, int MINB = 8>
 __global__ void __launch_bounds__(128, MINB) k_ensemble_step(EnsArgs A) {
   __shared__ int64_t s_off_v[64], s_off_e[64], s_off_c[64], s_off_t[64];
-  __shared__ union {
-    GatherTile<16> g;
-    UpdTile u;
-    LeanGatherTile<16> lg;
-    LeanTile<8> lt[4];
-  } tiles;
-  GatherTile<16>& tileT = tiles.g;
+  __shared__ EnsTiles<LEAN> tiles;
   for (int i = threadIdx.x; i < A.nm; i += blockDim.x) {
     s_off_v[i] = A.m[i].off_v;
     s_off_e[i] = A.m[i].off_e;
@@ -2261,11 +2383,31 @@ __global__ void __launch_bounds__(128, MINB) k_ensemble_step(EnsArgs A) {
   const int64_t gwarp = gtid >> 5;
   const int lane = threadIdx.x & 31;
   bool first = true;
-  auto sync = [&]() {
+  // phase timer (icon_ensemble_step_profile): block 0 stamps the global timer at the start
+  // and as it leaves each barrier, with the kind of the phase that barrier closes
+  const bool stamps = A.prof != nullptr && blockIdx.x == 0 && threadIdx.x == 0;
+  int nstamp = 0;
+  auto stamp = [&](int kind) {
+    if (stamps && nstamp < A.prof_max) {
+      A.prof[2 * nstamp] = (unsigned long long)kind;
+      A.prof[2 * nstamp + 1] = global_ns();
+      ++nstamp;
+    }
+  };
+  auto sync = [&](int kind) {
     const bool skip = first && A.skip_first_barrier && blockIdx.x == 0;
     first = false;
-    return grid_barrier(A, skip);
+    const bool ok = grid_barrier(A, skip);
+    stamp(kind);
+    return ok;
   };
+  stamp(ICON_ENS_PHASE_COUNT);                       // the start
+
+  SlotCache sc(A.m);
+  auto geo = [&](int m) -> const MxGeo& { return sc.geo(m); };
+  auto edge_args_of = [&](int m, int stage) -> const MxEdgeArgs& { return sc.edge(m, stage); };
+  auto lean_args_of = [&](int m, int stage) -> const MxLeanArgs& { return sc.lean(m, stage); };
+  int& arg_m = sc.arg_m;
 
   // phase 0: zero the accumulators
   for (int m = 0; m < A.nm; ++m) {
@@ -2274,102 +2416,129 @@ __global__ void __launch_bounds__(128, MINB) k_ensemble_step(EnsArgs A) {
     for (int64_t i = gtid; i < ne; i += nthreads) M.mflx[i] = 0.0;
     for (int64_t i = gtid; i < nh; i += nthreads) M.wflx[i] = 0.0;
   }
-  if (!sync()) return;
+  if (!sync(ICON_ENS_PH_ZERO)) return;
   for (int it = 0; it < A.nsub; ++it) {
     for (int stage = 0; stage < 2; ++stage) {
-      warp_items<kChunk>(s_off_v, A.nm, A.tot_v, gwarp, nwarps, [&](int m, int64_t j) {
-        const MemberDev& M = A.m[m];
-        mx_vertex_item<32>(M.G, M.ea[stage].vn, M.ea[stage].w, M.zeta32, M.wv32, j, lane);
-      });
-      if (!sync()) return;
-      warp_items<kChunk>(s_off_e, A.nm, A.tot_e, gwarp, nwarps, [&](int m, int64_t j) {
-        const MemberDev& M = A.m[m];
-        mx_edge_diag_item<32>(M.G, M.ea[stage].vn, M.vt32, j, lane);
-      });
-      if (!sync()) return;
-      warp_items<kChunk>(s_off_c, A.nm, A.tot_c, gwarp, nwarps, [&](int m, int64_t j) {
-        const MemberDev& M = A.m[m];
-        mx_cell_ke_item<32>(M.G, M.ea[stage].vn, M.vt32, M.Kc32, j, lane);
-      });
-      if (!sync()) return;
-      warp_items<kChunk>(s_off_e, A.nm, A.tot_e, gwarp, nwarps, [&](int m, int64_t j) {
-        const MemberDev& M = A.m[m];
-        mx_edge_tend_item<32>(M.G, M.ea[stage], j, lane);
-      });
-      if (!sync()) return;
+      // the stencil phases take two entities per warp (16 lanes over the levels each), as
+      // the per-state kernels' tuned tiles do
+      warp_pairs<kChunk>(
+          s_off_v, A.nm, A.tot_v, gwarp, nwarps,
+          [&](int m, int64_t j) {
+            const MemberDev& M = A.m[m];
+            mx_vertex_item<16>(geo(m), M.ea[stage].vn, M.ea[stage].w, M.zeta32, M.wv32, j + (lane >> 4), lane & 15);
+          },
+          [&](int m, int64_t j) {
+            const MemberDev& M = A.m[m];
+            mx_vertex_item<32>(geo(m), M.ea[stage].vn, M.ea[stage].w, M.zeta32, M.wv32, j, lane);
+          });
+      if (!sync(ICON_ENS_PH_VERTEX)) return;
+      warp_pairs<kChunk>(
+          s_off_e, A.nm, A.tot_e, gwarp, nwarps,
+          [&](int m, int64_t j) {
+            const MemberDev& M = A.m[m];
+            mx_edge_diag_item<16>(geo(m), M.ea[stage].vn, M.vt32, j + (lane >> 4), lane & 15);
+          },
+          [&](int m, int64_t j) {
+            const MemberDev& M = A.m[m];
+            mx_edge_diag_item<32>(geo(m), M.ea[stage].vn, M.vt32, j, lane);
+          });
+      if (!sync(ICON_ENS_PH_EDGE_DIAG)) return;
+      warp_pairs<kChunk>(
+          s_off_c, A.nm, A.tot_c, gwarp, nwarps,
+          [&](int m, int64_t j) {
+            const MemberDev& M = A.m[m];
+            mx_cell_ke_item<16>(geo(m), M.ea[stage].vn, M.vt32, M.Kc32, j + (lane >> 4), lane & 15);
+          },
+          [&](int m, int64_t j) {
+            const MemberDev& M = A.m[m];
+            mx_cell_ke_item<32>(geo(m), M.ea[stage].vn, M.vt32, M.Kc32, j, lane);
+          });
+      if (!sync(ICON_ENS_PH_CELL_KE)) return;
+      arg_m = -1;
+      warp_pairs<kChunk>(
+          s_off_e, A.nm, A.tot_e, gwarp, nwarps,
+          [&](int m, int64_t j) { mx_edge_tend_item<16>(geo(m), edge_args_of(m, stage), j + (lane >> 4), lane & 15); },
+          [&](int m, int64_t j) { mx_edge_tend_item<32>(geo(m), edge_args_of(m, stage), j, lane); });
+      if (!sync(ICON_ENS_PH_EDGE_TEND)) return;
       if (stage == 1 && A.any_damp) {
         // divergence damping of vn^{n+1}: cell divergence (into Kc32), its Laplacian (into
         // vt32), then the edge update with the fluxes the edge tendency left out
         warp_items<kChunk>(s_off_c, A.nm, A.tot_c, gwarp, nwarps, [&](int m, int64_t j) {
           const MemberDev& M = A.m[m];
-          if (M.damp) mx_dd_div_item(M.G, M.dd.vn, M.Kc32, j, lane);
+          if (M.damp) mx_dd_div_item(geo(m), M.dd.vn, M.Kc32, j, lane);
         });
-        if (!sync()) return;
+        if (!sync(ICON_ENS_PH_DD_DIV)) return;
         warp_items<kChunk>(s_off_c, A.nm, A.tot_c, gwarp, nwarps, [&](int m, int64_t j) {
           const MemberDev& M = A.m[m];
-          if (M.damp) mx_dd_lap_item(M.G, M.Kc32, M.vt32, j, lane);
+          if (M.damp) mx_dd_lap_item(geo(m), M.Kc32, M.vt32, j, lane);
         });
-        if (!sync()) return;
+        if (!sync(ICON_ENS_PH_DD_LAP)) return;
         if (!LEAN) {     // the lean column's gather forms the damped fluxes itself
           warp_items<kChunk>(s_off_e, A.nm, A.tot_e, gwarp, nwarps, [&](int m, int64_t j) {
             const MemberDev& M = A.m[m];
             if (M.damp) mx_dd_edge_item(M.G, M.dd, j, lane);
           });
-          if (!sync()) return;
+          if (!sync(ICON_ENS_PH_DD_EDGE)) return;
         }
       }
       // column-input gather: one 32-cell tile per block at a time (members without
       // stored factors have no tiles)
+      arg_m = -1;
       for (int64_t t = blockIdx.x; t < A.tot_t; t += gridDim.x) {
         const int m = find_member(s_off_t, A.nm, t);
         const MemberDev& M = A.m[m];
         const int64_t c0 = (t - M.off_t) * kGatherCells;
-        if (LEAN) {
-          if (stage == 0) mx_lean_gather_body<16, false>(M.G, M.la[0], c0, tiles.lg);
-          else if (M.damp) mx_lean_gather_body<16, true, true>(M.G, M.la[1], c0, tiles.lg);
-          else mx_lean_gather_body<16, true>(M.G, M.la[1], c0, tiles.lg);
+        if constexpr (LEAN) {
+          const MxGeo& G = geo(m);
+          const MxLeanArgs& la = lean_args_of(m, stage);
+          if (stage == 0) mx_lean_gather_body<16, false>(G, la, c0, tiles.lg);
+          else if (M.damp) mx_lean_gather_body<16, true, true>(G, la, c0, tiles.lg);
+          else mx_lean_gather_body<16, true>(G, la, c0, tiles.lg);
         } else {
-          if (stage == 0) mx_gather_tile_body<16, false>(M.G, M.ca[0], c0, tileT);
-          else mx_gather_tile_body<16, true>(M.G, M.ca[1], c0, tileT);
+          if (stage == 0) mx_gather_tile_body<16, false>(M.G, M.ca[0], c0, tiles.g);
+          else mx_gather_tile_body<16, true>(M.G, M.ca[1], c0, tiles.g);
         }
       }
-      if (!sync()) return;
-      if (LEAN) {
+      if (!sync(ICON_ENS_PH_GATHER)) return;
+      if constexpr (LEAN) {
         // lean column: one warp per 32-column tile, both sweeps and the updates in one pass
+        arg_m = -1;
         for (int64_t t = gwarp; t < A.tot_t; t += nwarps) {
           const int m = find_member(s_off_t, A.nm, t);
           const MemberDev& M = A.m[m];
           const int64_t c0 = (t - M.off_t) * kGatherCells;
-          LeanTile<8>& lt = tiles.lt[threadIdx.x >> 5];
-          if (stage == 0) mx_lean_column_item<false, 2, 8>(M.G, M.la[0], c0 + lane, c0, lane, lt);
-          else mx_lean_column_item<true, 2, 8>(M.G, M.la[1], c0 + lane, c0, lane, lt);
+          LeanTile<kEnsLeanCH>& lt = tiles.lt[threadIdx.x >> 5];
+          const MxGeo& G = geo(m);
+          const MxLeanArgs& la = lean_args_of(m, stage);
+          if (stage == 0) mx_lean_column_item<false, 2, kEnsLeanCH>(G, la, c0 + lane, c0, lane, lt);
+          else mx_lean_column_item<true, 2, kEnsLeanCH>(G, la, c0 + lane, c0, lane, lt);
         }
-        if (!sync()) return;
-        continue;
-      }
-      for (int64_t i = gtid; i < A.tot_c; i += nthreads) {
-        const int m = find_member(s_off_c, A.nm, i);
-        const MemberDev& M = A.m[m];
-        if (ALLFAC) {
-          if (stage == 0) mx_column_fac_item<NMAX, false>(M.G, M.ca[0], i - M.off_c);
-          else mx_corr_solve_item(M.G, M.ca[1], i - M.off_c);
-        } else {
-          if (stage == 0) mx_column_any<NMAX, false>(M.G, M.ca[0], i - M.off_c);
-          else mx_column_any<NMAX, true>(M.G, M.ca[1], i - M.off_c);
-        }
-      }
-      if (ALLFAC && stage == 1) {
-        // corrector updates: element-parallel 32-cell tiles (the member's tile list)
-        if (!sync()) return;
-        static_assert(kUpdCells == kGatherCells, "the corrector update reuses the gather tile list");
-        for (int64_t t = blockIdx.x; t < A.tot_t; t += gridDim.x) {
-          const int m = find_member(s_off_t, A.nm, t);
+        if (!sync(ICON_ENS_PH_COLUMN)) return;
+      } else {
+        for (int64_t i = gtid; i < A.tot_c; i += nthreads) {
+          const int m = find_member(s_off_c, A.nm, i);
           const MemberDev& M = A.m[m];
-          if (!mx_corr_update_tile(M.G, M.ca[1], (t - M.off_t) * kUpdCells, tiles.u)) atomicOr(M.ca[1].status, 1u);
-          __syncthreads();
+          if (ALLFAC) {
+            if (stage == 0) mx_column_fac_item<NMAX, false>(M.G, M.ca[0], i - M.off_c);
+            else mx_corr_solve_item(M.G, M.ca[1], i - M.off_c);
+          } else {
+            if (stage == 0) mx_column_any<NMAX, false>(M.G, M.ca[0], i - M.off_c);
+            else mx_column_any<NMAX, true>(M.G, M.ca[1], i - M.off_c);
+          }
         }
+        if (ALLFAC && stage == 1) {
+          // corrector updates: element-parallel 32-cell tiles (the member's tile list)
+          if (!sync(ICON_ENS_PH_COLUMN)) return;
+          static_assert(kUpdCells == kGatherCells, "the corrector update reuses the gather tile list");
+          for (int64_t t = blockIdx.x; t < A.tot_t; t += gridDim.x) {
+            const int m = find_member(s_off_t, A.nm, t);
+            const MemberDev& M = A.m[m];
+            if (!mx_corr_update_tile(M.G, M.ca[1], (t - M.off_t) * kUpdCells, tiles.u)) atomicOr(M.ca[1].status, 1u);
+            __syncthreads();
+          }
+        }
+        if (!sync(ALLFAC && stage == 1 ? ICON_ENS_PH_CORR_UPDATE : ICON_ENS_PH_COLUMN)) return;
       }
-      if (!sync()) return;
     }
   }
   // diffusion
@@ -2385,18 +2554,19 @@ __global__ void __launch_bounds__(128, MINB) k_ensemble_step(EnsArgs A) {
       mx_diff_div_item<32>(M.G, M.vn32, M.Kc32, j - M.off_c, lane);
     }
   }
-  if (!sync()) return;
+  if (!sync(ICON_ENS_PH_DIFF_VERTEX)) return;
   warp_items<kChunk>(s_off_e, A.nm, A.tot_e, gwarp, nwarps, [&](int m, int64_t j) {
     const MemberDev& M = A.m[m];
     mx_diff_edge_item<32>(M.G, M.vn32, M.uvx32, M.uvy32, M.uvz32, M.zeta32, M.Kc32, M.thv32, M.vt32, (float)M.dt,
                           j, lane);
   });
-  if (!sync()) return;
+  if (!sync(ICON_ENS_PH_DIFF_EDGE)) return;
   for (int64_t i = gtid; i < A.tot_c; i += nthreads) {
     const int m = find_member(s_off_c, A.nm, i);
     const MemberDev& M = A.m[m];
     mx_diff_theta_item(M.G, M.vt32, M.thv, M.ex, M.thv32, M.exp32, (float)M.dt, i - M.off_c);
   }
+  stamp(ICON_ENS_PH_DIFF_THETA);                     // block 0's own end of the last phase
 }
 
 __global__ void k_ens_colconst(const MemberDev* m, int nm) {
@@ -2488,7 +2658,7 @@ int ensemble_prepare(EnsembleDev& E, icon_state* const* members, int n, const do
         la.dd_out = s.vn32; la.mflx = s.mflx; la.dd_scale = M.dd.scale; la.dd_upwind = 0;
       }
       E.lean_consts.push_back({M.G.N, M.G.ld, M.G.nc, M.G.wu, M.G.wl, M.G.dzh, M.G.dz, M.G.ray, s.ex_ref, dtau,
-                               s.ln_cd, s.ln_cf, M.G.div_wa, s.ln_dwa});
+                               s.ln_cd, s.ln_cf, M.G.div_wa, M.G.inv_Ac, s.ln_dwa, s.ln_cw32});
     }
   }
   if (all_lean) all_fac = false;
@@ -2515,8 +2685,10 @@ int ensemble_prepare(EnsembleDev& E, icon_state* const* members, int n, const do
   return ICON_OK;
 }
 
-int ensemble_launch(EnsembleDev& E, cudaStream_t st) {
+int ensemble_launch(EnsembleDev& E, cudaStream_t st, unsigned long long* prof, int prof_max) {
   EnsArgs A;
+  A.prof = prof;
+  A.prof_max = prof_max;
   A.m = static_cast<const MemberDev*>(E.members);
   A.nm = E.nm;
   A.nsub = E.nsub;
@@ -2528,9 +2700,10 @@ int ensemble_launch(EnsembleDev& E, cudaStream_t st) {
   A.any_damp = E.any_damp ? 1 : 0;
   void (*kern)(EnsArgs);
   // The lean form keeps 8 CTAs per SM (64 registers, a few hundred bytes of spills): on a
-  // 64-member R2B4/R2B5 ensemble it measured 276 ms per step against 285, 315 and 380 ms
-  // with 6, 5 and 4 CTAs per SM (80, 96 and 120 registers, no spills), since the grid
-  // barriers between phases wait on the slowest CTA and more resident warps hide that.
+  // 64-member R2B4/R2B5 ensemble it measured faster than 7, 6, 5 and 4 CTAs per SM (72 to
+  // 120 registers, fewer or no spills) in every phase but the edge tendency, which gains
+  // nothing from the extra registers; the grid barriers wait on the slowest CTA and more
+  // resident warps hide that.
   if (E.all_lean)      // the lean column has no level arrays
     kern = k_ensemble_step<32, false, true, 8>;
   else if (E.N <= 32) kern = E.all_fac ? k_ensemble_step<32, true, false> : k_ensemble_step<32, false, false>;
@@ -2541,9 +2714,18 @@ int ensemble_launch(EnsembleDev& E, cudaStream_t st) {
     return ICON_EINVAL;
   }
   if (E.grid_blocks == 0) {
-    int dev = 0, nsm = 0, per = 0;
+    int dev = 0, nsm = 0, per = 0, smem_sm = 0;
     ICON_CUDA(cudaGetDevice(&dev));
     ICON_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    ICON_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    // ask for no more shared memory than 8 resident blocks take (with the 1 KB the
+    // system reserves per block): the rest of the SM's unified memory stays L1 cache for
+    // the stencil phases
+    cudaFuncAttributes fa;
+    ICON_CUDA(cudaFuncGetAttributes(&fa, kern));
+    const double need = 8.0 * ((double)fa.sharedSizeBytes + 1024.0);
+    const int pct = smem_sm > 0 ? (int)std::ceil(100.0 * need / smem_sm) : 100;
+    ICON_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, pct < 100 ? pct : 100));
     ICON_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 128, 0));
     if (per < 1) {
       set_error("icon_ensemble_step: the persistent kernel does not fit on an SM");
@@ -2554,7 +2736,7 @@ int ensemble_launch(EnsembleDev& E, cudaStream_t st) {
   k_ens_colconst<<<E.nm, 64, 0, st>>>(A.m, E.nm);
   for (const EnsembleDev::LeanConst& L : E.lean_consts) {
     k_mx_leanconst<<<1, 128, 0, st>>>(L.N, L.ld, L.wu, L.wl, L.dzh, L.dz, L.ray, L.ex_ref, L.dtau, L.cd, L.cf);
-    k_mx_dwa_t<<<blocks_for(3 * L.nc, 256), 256, 0, st>>>(3 * L.nc, L.div_wa, L.dtau, L.dwa);
+    k_mx_dwa_t<<<blocks_for(L.nc, 256), 256, 0, st>>>(L.nc, L.div_wa, L.inv_Ac, L.dtau, L.dwa, L.cw32);
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(E.grid_blocks);

@@ -207,6 +207,7 @@ struct StateDev {
   double* ln_dr64 = nullptr;
   float *ln_dt32 = nullptr, *ln_aw32 = nullptr, *ln_cp = nullptr, *ln_cf = nullptr;
   double *ln_B = nullptr, *ln_dp = nullptr, *ln_cd = nullptr, *ln_dwa = nullptr;
+  float* ln_cw32 = nullptr;   // per cell: FP32 dtau s l / A_c of its three edges, then dtau / A_c
   int ln_hdamp = 0;           // half levels h < ln_hdamp lie in the Rayleigh layer
   // mass reduction partials and the device status word
   double *mass_part = nullptr;
@@ -259,15 +260,16 @@ struct EnsembleDev {
     double dtau;
     double* cd;
     float* cf;
-    const double* div_wa;
+    const double *div_wa, *inv_Ac;
     double* dwa;
+    float* cw32;
   };
   std::vector<LeanConst> lean_consts;
   long long spin_limit = 1ll << 24;
   int test_skip_barrier = 0;
 };
 int ensemble_prepare(EnsembleDev& E, icon_state* const* members, int n, const double* dts, int nsub);
-int ensemble_launch(EnsembleDev& E, cudaStream_t st);
+int ensemble_launch(EnsembleDev& E, cudaStream_t st, unsigned long long* prof = nullptr, int prof_max = 0);
 void autotune_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream);
 // the stored-factor column parts of a mixed state (api.cu); false if they do not fit
 bool alloc_mixed_factors(icon_state* st);

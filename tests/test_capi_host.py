@@ -38,6 +38,10 @@ def test_host_argument_checks(built_lib):
     assert lib.icon_dycore_step(None, 1.0, 1) == C.ICON_EINVAL
     assert lib.icon_global_mass(None, None) == C.ICON_EINVAL
     assert lib.icon_ensemble_create(None, 0, ctypes.byref(h)) == C.ICON_EINVAL
+    assert lib.icon_ensemble_step_profile(None, None, 5, None, None) == C.ICON_EINVAL
+    names = [C.icon_ensemble_phase_name(k) for k in range(C.ICON_ENS_PHASE_COUNT)]
+    assert len(set(names)) == C.ICON_ENS_PHASE_COUNT and None not in names
+    assert C.icon_ensemble_phase_name(-1) is None and C.icon_ensemble_phase_name(C.ICON_ENS_PHASE_COUNT) is None
     n = ctypes.c_int()
     assert lib.icon_state_add_tracers(None, 1) == C.ICON_EINVAL
     assert lib.icon_state_set_option(None, 1, 0.0) == C.ICON_EINVAL
@@ -72,3 +76,16 @@ def test_case_params_layout_matches_the_header(tmp_path):
     out = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
     assert out[0] == ctypes.sizeof(C.CaseParams)
     assert out[1:] == [getattr(C.CaseParams, f).offset for f in fields]
+
+
+def test_binding_constants_match_the_header():
+    """Every ICON_* integer constant of the binding equals the header's #define or enum value."""
+    import re
+    from paper_2511_02021_gb300 import capi as C
+    text = open(os.path.join(ROOT, "include", "icon.h")).read()
+    defs = {m.group(1): int(m.group(2)) for m in re.finditer(r"^#define (ICON_\w+) (-?\d+)\b", text, re.M)}
+    defs.update({m.group(1): int(m.group(2)) for m in re.finditer(r"^\s+(ICON_\w+) = (-?\d+),", text, re.M)})
+    shared = [n for n in defs if hasattr(C, n)]
+    assert {"ICON_KIND_COUNT", "ICON_ENS_PHASE_COUNT", "ICON_OK", "ICON_EINVAL"} <= set(shared)
+    for n in shared:
+        assert getattr(C, n) == defs[n], n

@@ -167,3 +167,43 @@ def test_failing_allocator_gives_enomem_without_leaks(gpu):
         assert live == {}                                  # every block handed out was returned
     finally:
         P.use_torch_allocator(0)
+
+
+def test_ensemble_phase_profile(gpu):
+    """The phase-timed step advances the members exactly as a plain ensemble step (same
+    kernel, same work lists), reports every phase the step runs with one barrier per
+    phase and substep stage, and its phase times add up to the launch."""
+    C = gpu
+    N, nsub = 30, 5
+    grids = [C.icon_grid_build(2, 2, N), C.icon_grid_build(2, 3, N)]
+    spec = [(0, 0, 300.0), (1, 1, 150.0)]
+    dts = [dt for _, _, dt in spec]
+    a = [C.icon_state_init_ex(grids[g], 4, C.ICON_CASE_MEMBER, precision=C.ICON_MIXED, member=m) for g, m, _ in spec]
+    b = [C.icon_state_init_ex(grids[g], 4, C.ICON_CASE_MEMBER, precision=C.ICON_MIXED, member=m) for g, m, _ in spec]
+    ea, eb = C.icon_ensemble_create(a), C.icon_ensemble_create(b)
+    try:
+        C.icon_ensemble_step(ea, dts, nsub, 1)
+        ms, cnt = C.icon_ensemble_step_profile(eb, dts, nsub)
+        for (g, _, _), sa, sb in zip(spec, a, b):
+            for f in PROG:
+                assert np.array_equal(C.icon_state_copy_field(sa, grids[g], N, f),
+                                      C.icon_state_copy_field(sb, grids[g], N, f)), f
+        names = [C.icon_ensemble_phase_name(k) for k in range(C.ICON_ENS_PHASE_COUNT)]
+        got = {names[k]: int(cnt[k]) for k in range(C.ICON_ENS_PHASE_COUNT) if cnt[k]}
+        # lean column with damping (the defaults): the damping's edge update is in the gather
+        per_stage = {"vertex": 2, "edge_diag": 2, "cell_ke": 2, "edge_tend": 2, "gather": 2, "column": 2}
+        want = {k: v * nsub for k, v in per_stage.items()}
+        want.update(zero=1, dd_div=nsub, dd_lap=nsub, diff_vertex=1, diff_edge=1, diff_theta=1)
+        assert got == want
+        assert np.all(ms >= 0.0) and ms.sum() > 0.0
+        assert C.icon_ensemble_phase_name(C.ICON_ENS_PHASE_COUNT) is None
+        # a second profiled step accumulates
+        ms2, cnt2 = C.icon_ensemble_step_profile(eb, dts, nsub, ms.copy(), cnt.copy())
+        assert np.array_equal(cnt2, 2 * cnt) and ms2.sum() > ms.sum()
+    finally:
+        C.icon_ensemble_free(ea)
+        C.icon_ensemble_free(eb)
+        for s in a + b:
+            C.icon_state_free(s)
+        for g in grids:
+            C.icon_grid_free(g)
