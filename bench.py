@@ -69,19 +69,27 @@ def peaks():
 # beside it.
 FP64_INSTR_DERIVED = 152 * 2 * 2.07e9
 # FP64 instructions per cell-level of one launch of the FP64 column solve (rows + Thomas +
-# update), averaged over predictor and corrector, counted from the kernel source (a fused
-# multiply-add is one, the Newton-Raphson reciprocal three): rows 56, Thomas 9, update 11/15.
-COLUMN_FP64_OPS = 73
+# update), averaged over predictor and corrector, as ncu counts them executed at R2B5/90
+# (sm__thread_inst_executed_pipe_fp64_pred_on.sum over cell-levels): predictor 47.9 + 8.9 +
+# 14.0 = 70.8 (it forms and factors the tridiagonal matrix of S^n), corrector 37.9 + 3.9 +
+# 17.0 = 58.8 (it substitutes with the predictor's factors).
+COLUMN_FP64_OPS = 64.8
 # FP64 instructions per cell-level of the mixed column, one launch averaged over the
 # predictor and the corrector (the corrector's kernels include the FP64 divergence of the
 # FP32 mass fluxes): see MX_OPS below, set from the kernels the state runs
 MX_OPS = {"stored": 36, "recompute": 56}
 # FP64 instructions per cell-level of the tracer transport of one tracer
 TRACER_FP64_OPS = 77
-# DRAM bytes per launch of a kernel kind measured by ncu on the current kernels (None where
-# the kernel changed after the counters were taken)
+# DRAM bytes per launch of a kernel kind measured by ncu on the current kernels (absent where
+# the kernel changed after the counters were taken), mean of the predictor and corrector
+# launches. Captured at R2B5/90 (the full sizes hold too much memory for a multi-pass capture)
+# and scaled by cell-levels: every column does the same work, so the traffic grows in
+# proportion. FP64 column 2.407 GB per launch at R2B5/90; lean mixed column 1.085 GB.
 NCU_TRAFFIC = {
-    ("R2B6-L90-jet-fp64", "column_solve"): 10.60e9,
+    ("R2B6-L90-jet-fp64", "column_solve"): 2.407e9 * 4,
+    ("R2B6-L90-jet-fp64", "mx_lean_column"): 1.085e9 * 4,
+    ("R2B8-L90-jet-mixed", "mx_lean_column"): 1.085e9 * 64,
+    ("R2B9-L60-jet-mixed", "mx_lean_column"): 1.085e9 * 256 * 60 / 90,
 }
 
 

@@ -246,7 +246,7 @@ int alloc_state(icon_state* st, int precision, bool topo) {
     s.wflx = A.get_n<double>(C);
     s.colconst = A.get_n<double>(8 * (size_t)ld);
     double** col[] = {&s.col_lo, &s.col_di, &s.col_up, &s.col_rh, &s.col_rx,
-                      &s.col_tx, &s.col_px, &s.col_gm, &s.col_ri, &s.col_mm};
+                      &s.col_tx, &s.col_px, &s.col_gm, &s.col_ri, &s.col_mm, &s.col_ws, &s.col_gc};
     for (double** p : col) *p = A.get_n<double>(C);
     s.vn = A.get_n<double>(E); s.vn_s = A.get_n<double>(E);
     s.Avn0 = A.get_n<double>(E); s.Aw0 = A.get_n<double>(C);

@@ -342,12 +342,13 @@ __global__ void __launch_bounds__(256, 4) k_dd_edge(Geo64 G, DDArgs a) {
 //   k_col_rows   one warp per cell, lanes over levels: everything that is parallel
 //                over the levels (half-level interpolants, horizontal divergences,
 //                explicit predictors, the linearised state equation, the w predictor
-//                and the tridiagonal row of every interior half level). Rows go out
+//                and, in the predictor, the tridiagonal row of every interior half
+//                level, which depends on S^n only and serves both stages). Rows go out
 //                level-major for the solve; the operands of the final update stay in
 //                the cell's own rows.
 //   k_col_thomas one thread per column: the Thomas recurrence on level-major rows
-//                (coalesced across the warp), Rayleigh damping; the solution w
-//                overwrites the sub-diagonal.
+//                (coalesced across the warp; the corrector substitutes with the
+//                predictor's factors), Rayleigh damping; the solution w goes to ws.
 //   k_col_update one warp per cell, lanes over levels: the implicit parts of rho,
 //                Theta and pi, theta_v = Theta / rho, the step-mean vertical mass flux.
 // Only the recurrence is sequential in the level; keeping it apart lets the rest run
@@ -358,7 +359,9 @@ struct ColArgs {
   const double *F, *G, *a_e;               // edge fluxes and w-advection edge terms
   double* Aw0;                             // stored (predictor) or read (corrector)
   double *lo, *di, *up, *rh;               // tridiagonal rows, level-major [h][Nc], h = 1..N-1
+  double* ws;                              // the damped solution w^{n+1}, level-major [h][Nc]
   double *rx, *tx, *px, *gm;               // rho*, Theta*, pi* (explicit parts), gamma: [c][ld]
+  double* gc;                              // (Rd/cvd) pi / Theta of S^n: [c][ld]
   double *ri, *mm;                         // half-level rho and rho theta_v of S^n: [c][ld]
   double *rho_o, *thv_o, *ex_o, *w_o;      // S* or S^{n+1} (may alias S^n)
   double* wflx;
@@ -440,16 +443,25 @@ __global__ void __launch_bounds__(256, 4) k_col_rows(Geo64 G, ColArgs a) {
         rx = (rho - dtau * Dr) - dt1 * (ri * wk - ri1 * w1);
         tx = (Th - hdtau * Dt2) - dt1 * (M * wk - M1 * w1);
       }
-      const double g = (rcv * ex) * recip64(Th);
+      // the state-equation factor of S^n: formed by the predictor, read back by the corrector
+      double g;
+      if (!a.corrector) {
+        g = (rcv * ex) * recip64(Th);
+        a.gc[o + k] = g;
+      } else {
+        g = a.gc[o + k];
+      }
       px = ex + g * (tx - Th);
-      if constexpr (TOPO) gam = g * (dtau * kBeta * G.t_inv_dz_c[o + k]);
-      else gam = g * cc[C_DTBDZ * ld + k];
       a.rx[o + k] = rx;
       a.tx[o + k] = tx;
       a.px[o + k] = px;
-      a.gm[o + k] = gam;
+      if (!a.corrector) {
+        if constexpr (TOPO) gam = g * (dtau * kBeta * G.t_inv_dz_c[o + k]);
+        else gam = g * cc[C_DTBDZ * ld + k];
+        a.gm[o + k] = gam;
+      }
     }
-    if (hv && lane < 31) {
+    if (hv && lane < 31 && !a.corrector) {
       a.ri[o + k] = ri;
       a.mm[o + k] = M;
     }
@@ -482,10 +494,12 @@ __global__ void __launch_bounds__(256, 4) k_col_rows(Geo64 G, ColArgs a) {
         aa = cc[C_CA * ld + h] * th_ic;
       }
       const int64_t i = (int64_t)h * nc + c;
-      const double P = aa * gam_m, Q = aa * gam;
-      a.lo[i] = -P * M_m;
-      a.di[i] = fma(P + Q, M, 1.0);
-      a.up[i] = -Q * M1;
+      if (!a.corrector) {
+        const double P = aa * gam_m, Q = aa * gam;
+        a.lo[i] = -P * M_m;
+        a.di[i] = fma(P + Q, M, 1.0);
+        a.up[i] = -Q * M1;
+      }
       a.rh[i] = w_x - aa * (px_m - px);
     }
     gam_c = __shfl_sync(0xffffffffu, gam, 30);
@@ -495,7 +509,12 @@ __global__ void __launch_bounds__(256, 4) k_col_rows(Geo64 G, ColArgs a) {
 }
 
 // Thomas recurrence per column on the level-major rows; the next row is loaded before
-// the current one is stored so that its loads overlap the recurrence
+// the current one is stored so that its loads overlap the recurrence. The matrix depends on
+// S^n only (rho_ic, theta_ic and the state-equation factor of the substep's start), so it is
+// the same in both stages: the predictor factors it, keeping the sub-diagonal, storing
+// 1 / pivot over the diagonal and up / pivot over the super-diagonal, and the corrector only
+// substitutes its own right-hand side (the same operations on the same values as a second
+// factorisation, so the results are unchanged). The damped solution goes to ws.
 __global__ void __launch_bounds__(128) k_col_thomas(Geo64 G, ColArgs a) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= G.nc) return;
@@ -503,33 +522,50 @@ __global__ void __launch_bounds__(128) k_col_thomas(Geo64 G, ColArgs a) {
   if (N < 2) return;
   const int64_t nc = G.nc;
   const double* __restrict__ cc = G.cc;
-  double* __restrict__ lo = a.lo;
-  const double* __restrict__ di = a.di;
+  const double* __restrict__ lo = a.lo;
+  double* __restrict__ di = a.di;
   double* __restrict__ up = a.up;
   double* __restrict__ rh = a.rh;
-  double cp = 0.0, dp = 0.0;
-  double l = lo[nc + c], d = di[nc + c], u = up[nc + c], r = rh[nc + c];
-  for (int h = 1; h < N; ++h) {
-    double ln = 0.0, dn = 0.0, un = 0.0, rn = 0.0;
-    if (h + 1 < N) {
-      const int64_t j = (int64_t)(h + 1) * nc + c;
-      ln = lo[j]; dn = di[j]; un = up[j]; rn = rh[j];
+  double* __restrict__ ws = a.ws;
+  double dp = 0.0;
+  if (!a.corrector) {
+    double cp = 0.0;
+    double l = lo[nc + c], d = di[nc + c], u = up[nc + c], r = rh[nc + c];
+    for (int h = 1; h < N; ++h) {
+      double ln = 0.0, dn = 0.0, un = 0.0, rn = 0.0;
+      if (h + 1 < N) {
+        const int64_t j = (int64_t)(h + 1) * nc + c;
+        ln = lo[j]; dn = di[j]; un = up[j]; rn = rh[j];
+      }
+      const double q = recip64(h == 1 ? d : d - l * cp);
+      cp = u * q;
+      dp = (h == 1 ? r : r - l * dp) * q;
+      const int64_t i = (int64_t)h * nc + c;
+      di[i] = q;
+      up[i] = cp;
+      rh[i] = dp;
+      l = ln; d = dn; u = un; r = rn;
     }
-    const double q = recip64(h == 1 ? d : d - l * cp);
-    cp = u * q;
-    dp = (h == 1 ? r : r - l * dp) * q;
-    const int64_t i = (int64_t)h * nc + c;
-    up[i] = cp;
-    rh[i] = dp;
-    l = ln; d = dn; u = un; r = rn;
+  } else {
+    double l = lo[nc + c], q = di[nc + c], r = rh[nc + c];
+    for (int h = 1; h < N; ++h) {
+      double ln = 0.0, qn = 0.0, rn = 0.0;
+      if (h + 1 < N) {
+        const int64_t j = (int64_t)(h + 1) * nc + c;
+        ln = lo[j]; qn = di[j]; rn = rh[j];
+      }
+      dp = (h == 1 ? r : r - l * dp) * q;
+      rh[(int64_t)h * nc + c] = dp;
+      l = ln; q = qn; r = rn;
+    }
   }
-  // back substitution; the damped solution replaces the sub-diagonal
+  // back substitution
   double x = dp;
-  lo[(int64_t)(N - 1) * nc + c] = x * cc[C_DAMP * ld + N - 1];
+  ws[(int64_t)(N - 1) * nc + c] = x * cc[C_DAMP * ld + N - 1];
   for (int h = N - 2; h >= 1; --h) {
     const int64_t i = (int64_t)h * nc + c;
     x = rh[i] - up[i] * x;
-    lo[i] = x * cc[C_DAMP * ld + h];
+    ws[i] = x * cc[C_DAMP * ld + h];
   }
 }
 
@@ -546,7 +582,7 @@ __global__ void __launch_bounds__(256) k_col_update(Geo64 G, ColArgs a) {
   for (int base = 0; base < N; base += 31) {
     const int k = base + lane;
     // w^{n+1} (damped) at half level k; zero at the top and the bottom
-    const double wn = (k >= 1 && k < N) ? a.lo[(int64_t)k * nc + c] : 0.0;
+    const double wn = (k >= 1 && k < N) ? a.ws[(int64_t)k * nc + c] : 0.0;
     const double ri = k <= N ? a.ri[o + k] : 0.0;
     const double M = k <= N ? a.mm[o + k] : 0.0;
     const double wn1 = __shfl_down_sync(0xffffffffu, wn, 1);
@@ -842,9 +878,9 @@ void fp64_step_stage(icon_state* st, double dt, int nsub, bool corr, cudaStream_
   ca.w_stage = w_st;
   ca.F = s.F; ca.G = s.G; ca.a_e = s.a_e;
   ca.Aw0 = s.Aw0;
-  ca.lo = s.col_lo; ca.di = s.col_di; ca.up = s.col_up; ca.rh = s.col_rh;
+  ca.lo = s.col_lo; ca.di = s.col_di; ca.up = s.col_up; ca.rh = s.col_rh; ca.ws = s.col_ws;
   ca.rx = s.col_rx; ca.tx = s.col_tx; ca.px = s.col_px; ca.gm = s.col_gm;
-  ca.ri = s.col_ri; ca.mm = s.col_mm;
+  ca.ri = s.col_ri; ca.mm = s.col_mm; ca.gc = s.col_gc;
   ca.rho_o = corr ? s.rho : s.rho_s;
   ca.thv_o = corr ? s.thv : s.thv_s;
   ca.ex_o = corr ? s.ex : s.ex_s;

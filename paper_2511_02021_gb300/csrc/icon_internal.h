@@ -187,7 +187,7 @@ struct StateDev {
   // FP64 column scratch: tridiagonal rows level-major [h][Nc], update operands [c][ld]
   double *col_lo = nullptr, *col_di = nullptr, *col_up = nullptr, *col_rh = nullptr;
   double *col_rx = nullptr, *col_tx = nullptr, *col_px = nullptr, *col_gm = nullptr;
-  double *col_ri = nullptr, *col_mm = nullptr;
+  double *col_ri = nullptr, *col_mm = nullptr, *col_ws = nullptr, *col_gc = nullptr;
   double* colconst = nullptr;
   // tracers (mixing ratios, FP64 [t][Nc][ld]) and their transport scratch
   int ntr = 0;
