@@ -310,8 +310,11 @@ int icon_dycore_step_profile(icon_state* state, double dt, int nsubsteps, double
 
 /* Self-test of internal device helpers that replace hardware operations: the
  * FP32 <-> FP64 conversions done on the integer pipe are compared bit for bit with
- * the hardware conversions on n random inputs each (finite normals, zeros, exact
- * halfway cases), and the Newton-Raphson FP64 reciprocal of the column solves is
+ * the hardware conversions on n random inputs each (finite normals up to the largest
+ * binary32 exponent, zeros, exact halfway cases), checked outside the binary32 normal
+ * range against their documented mapping (signed zero below, signed infinity above,
+ * NaN included; binary32 subnormals to a signed zero), and the Newton-Raphson FP64
+ * reciprocal of the column solves is
  * compared with the IEEE division on n random operands (within 1 ulp for 1/x,
  * 2 ulps for a * (1/x)). *failures receives the number of mismatches (0 expected).
  * Allocates 4 bytes with cudaMalloc (not the registered allocator). Waits. */

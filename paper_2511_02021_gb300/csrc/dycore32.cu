@@ -1561,6 +1561,8 @@ __device__ inline void mx_lean_column_item(const MxGeo& G, const MxLeanArgs& a, 
       thv_u = LMV(a.thv, k - 1);
       ex_u = LMV(a.ex, k - 1);
     }
+    // the FP32 roundings of level k are formed again rather than carried from the level
+    // above: carried, the two extra live values spill at this kernel's 48 registers
     const float rho_kf = f64_to_f32(rho_k), thv_kf = f64_to_f32(thv_k);
     float ri_k, M_k;
     if (k == 0) {
@@ -2104,7 +2106,7 @@ __global__ void k_selftest_conv(int64_t n, unsigned* fails) {
   // binary64 in the binary32 normal range; every 4th value sits exactly halfway
   const uint64_t r2 = st_mix(r);
   uint64_t bits = r2 & 0x800fffffffffffffull;
-  const unsigned ee = 897u + (unsigned)((r2 >> 52) % 253u);
+  const unsigned ee = 897u + (unsigned)((r2 >> 52) % 254u);   // up to the largest binary32 exponent
   bits |= (uint64_t)ee << 52;
   if ((i & 3) == 0) bits = (bits & ~0x1fffffffull) | 0x10000000ull;
   const double d = __longlong_as_double((long long)bits);
@@ -2114,6 +2116,19 @@ __global__ void k_selftest_conv(int64_t n, unsigned* fails) {
     if (__double_as_longlong(f32_to_f64(-0.0f)) != __double_as_longlong(-0.0)) atomicAdd(fails, 1u);
     if (__float_as_uint(f64_to_f32(0.0)) != 0u) atomicAdd(fails, 1u);
   }
+  // outside the binary32 normal range, the documented mapping: binary64 below it to a signed
+  // zero, above it (infinities and NaNs included) to a signed infinity, binary32 subnormals
+  // to a signed zero
+  const uint64_t r5 = st_mix(r2 + 1);
+  const uint64_t sg = r5 & 0x8000000000000000ull, man = r5 & 0x000fffffffffffffull;
+  const uint64_t elow = (r5 >> 52) % 897u, ehigh = 1151u + (r5 >> 40) % 897u;
+  const unsigned s32 = (unsigned)(sg >> 32);
+  if (__float_as_uint(f64_to_f32(__longlong_as_double((long long)(sg | (elow << 52) | man)))) != s32)
+    atomicAdd(fails, 1u);
+  if (__float_as_uint(f64_to_f32(__longlong_as_double((long long)(sg | (ehigh << 52) | man)))) != (s32 | 0x7f800000u))
+    atomicAdd(fails, 1u);
+  const unsigned us = s32 | ((unsigned)(r5 >> 8) & 0x007fffffu);
+  if (__double_as_longlong(f32_to_f64(__uint_as_float(us))) != (long long)((uint64_t)s32 << 32)) atomicAdd(fails, 1u);
   // Newton-Raphson reciprocal: within one ulp of the IEEE quotient 1/x, and a * recip64(b)
   // within two ulps of a / b, for x, b of either sign with exponents in [-120, 120]
   const uint64_t r3 = st_mix(r2 ^ 0xD1B54A32D192ED03ull);
