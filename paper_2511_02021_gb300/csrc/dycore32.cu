@@ -1357,7 +1357,7 @@ __device__ inline void mx_lean_gather_body(const MxGeo& G, const MxLeanArgs& a, 
             Gt[s] = (le[s] * F[s]) * (a.dd_upwind ? (vd >= 0.0f ? t1 : t2) : 0.5f * (t1 + t2));
             if (own[s]) {
               a.dd_out[E[s] + k] = vd;
-              a.mflx[E[s] + k] += f32_to_f64(F[s]) * a.inv_nsub;
+              a.mflx[E[s] + k] += (double)F[s] * a.inv_nsub;
             }
           }
         } else {
@@ -1366,7 +1366,9 @@ __device__ inline void mx_lean_gather_body(const MxGeo& G, const MxLeanArgs& a, 
             Gt[s] = a.gth[E[s] + k];
           }
         }
-        if (CORR) T.d[lane][cl] = (dwt[0] * f32_to_f64(F[0]) + dwt[1] * f32_to_f64(F[1])) + dwt[2] * f32_to_f64(F[2]);
+        // the hardware conversion here: the gather leaves the FP64 pipe half idle, and the
+        // integer-pipe form costs more issue slots (measured 6.0 against 5.6 ms per step)
+        if (CORR) T.d[lane][cl] = (dwt[0] * (double)F[0] + dwt[1] * (double)F[1]) + dwt[2] * (double)F[2];
         else T.f[3][lane][cl] = (dw32[0] * F[0] + dw32[1] * F[1]) + dw32[2] * F[2];
         T.f[0][lane][cl] = (sg[0] * Gt[0] + sg[1] * Gt[1] + sg[2] * Gt[2]) * ta;
       }
