@@ -447,12 +447,16 @@ void icon_domain_free(icon_domain* domain);
 
 /* ---------------------------------------------------------------- ensemble */
 
-/* Stencil tile of a kernel kind (ICON_KIND_* below) of a mixed-precision state:
- * lanes per entity (32 = one entity per warp, 16 = two) and threads per block. The
- * autotuner picks them on the first step (timing every candidate on the state's
- * data; cached per grid size, level count and GPU, and in the file named by the
- * environment variable ICON_TUNE_CACHE if set). set_tiling forces a tile
- * (lanes 0 restores automatic choice); results do not depend on the tile. */
+/* Tile of a kernel kind (the kind numbers of icon_kernel_kind_name) of a mixed-precision
+ * state. Stencil kinds (10, 11, 12, 13, 15, 16): lanes per entity (32 = one entity per
+ * warp, 16 = two, 8 = four) and threads per block (64, 128, 256 or 512). The lean column
+ * (24): its launch shape, lanes = the unroll factor of its two sweeps and block = the
+ * resident 128-thread blocks per SM its registers are held to, one of (2, 10), (2, 8),
+ * (2, 12), (2, 6). The autotuner picks them on the first step (timing every candidate on
+ * the state's data, in the order of the step; cached per grid size, level count and GPU,
+ * and in the file named by the environment variable ICON_TUNE_CACHE if set). set_tiling
+ * forces a tile (lanes 0 restores automatic choice; ICON_EINVAL for any other value
+ * outside these sets); results do not depend on the tile. */
 int icon_state_tiling(const icon_state* state, int kind, int* lanes, int* block);
 int icon_state_set_tiling(icon_state* state, int kind, int lanes, int block);
 

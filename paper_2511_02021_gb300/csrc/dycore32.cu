@@ -39,6 +39,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include "icon_internal.h"
 #include "fastconv.h"
 #include "recip64.h"
@@ -173,7 +174,8 @@ __device__ inline void mx_edge_tend_item(const MxGeo& G, const MxEdgeArgs& a, in
   const float* __restrict__ thv = a.thv;
   const float* __restrict__ exq = a.exp;
   const float* __restrict__ rho = a.rho;
-  const unsigned seg = LPE == 32 ? 0xffffffffu : (0xffffu << (threadIdx.x & 16));
+  static_assert(LPE == 8 || LPE == 16 || LPE == 32, "lane groups of 8, 16 or 32");
+  const unsigned seg = LPE == 32 ? 0xffffffffu : (((1u << LPE) - 1u) << (threadIdx.x & (32 - LPE)));
 #pragma unroll 2   // two windows' loads in flight (the kernel is bound by load latency)
   for (int base = 0; base <= N; base += LPE - 1) {
     const int h = base + lane;
@@ -1652,13 +1654,31 @@ __global__ void __launch_bounds__(THREADS, MINB) k_mx_lean_column(MxGeo G, MxLea
   mx_lean_column_item<CORR, U, CH>(G, a, c0 + lane, c0, lane, T[warp]);
 }
 
-// launch shape (measured at R2B6/90 over eight shapes): blocks of four warps held to 48
-// registers so that ten blocks (40 warps) share an SM, 8-level transpose chunks, sweeps
-// unrolled by two: the kernel waits on memory latency and gains from occupancy (12.2 ms per
-// R2B6/90 step against 16.9 ms with 64-thread blocks at 94 registers)
+// launch shapes of the lean column, one thread per column in blocks of four warps: the tile's
+// "lanes" is the unroll factor of the two sweeps and its "block" the resident blocks per SM
+// the registers are held to (6: 80 registers, 8: 64, 10: 48, 12: 40). Only the register cap
+// varies among the candidates: it leaves the arithmetic as it is, while another unroll factor
+// changes which multiply-adds the compiler fuses and with them the FP32 roundings (measured:
+// unroll 1 or 4 moves vn by 1e-7 relative after one step), and a tuner choosing by timing
+// must not change results. The default (unrolled by two, 10 blocks) measured fastest at
+// R2B6/90 over eight shapes (12.2 ms per step against 16.9 ms with 64-thread blocks at 94
+// registers): the kernel waits on memory latency and gains from occupancy.
+const TileChoice kLeanShapes[] = {{2, 10}, {2, 8}, {2, 12}, {2, 6}};
+const TileChoice kLeanDefault = {2, 10};
+
+bool lean_shape_ok(const TileChoice& t) {
+  for (const TileChoice& c : kLeanShapes)
+    if (c.lanes == t.lanes && c.block == t.block) return true;
+  return false;
+}
+
 template <bool CORR>
-void launch_lean_column(const MxGeo& G, const MxLeanArgs& a, cudaStream_t st) {
-  k_mx_lean_column<CORR, 2, 8, 128, 10><<<blocks_for(G.nc, 128), 128, 0, st>>>(G, a);
+void launch_lean_column(const MxGeo& G, const MxLeanArgs& a, const TileChoice& t, cudaStream_t st) {
+  const unsigned nb = blocks_for(G.nc, 128);
+  if (t.block == 8) k_mx_lean_column<CORR, 2, 8, 128, 8><<<nb, 128, 0, st>>>(G, a);
+  else if (t.block == 12) k_mx_lean_column<CORR, 2, 8, 128, 12><<<nb, 128, 0, st>>>(G, a);
+  else if (t.block == 6) k_mx_lean_column<CORR, 2, 8, 128, 6><<<nb, 128, 0, st>>>(G, a);
+  else k_mx_lean_column<CORR, 2, 8, 128, 10><<<nb, 128, 0, st>>>(G, a);
 }
 
 MxGeo make_mx_geo(const icon_grid* grid, const StateDev& s) {
@@ -1787,59 +1807,74 @@ unsigned item_blocks(int64_t n, int lpe, int block) {
   return (unsigned)((n + per_block - 1) / per_block);
 }
 
+// the lane count of a tile as a compile-time constant (8, 16 or 32 lanes per entity)
+template <typename F>
+void with_lanes(int lanes, F f) {
+  if (lanes == 8) f(std::integral_constant<int, 8>{});
+  else if (lanes == 16) f(std::integral_constant<int, 16>{});
+  else f(std::integral_constant<int, 32>{});
+}
+
 void launch_kind(int kind, const TileChoice& t, const MxGeo& G, StateDev& s, const MxEdgeArgs& ea,
                  const MxColArgs& ca, float dt, cudaStream_t st) {
-  const bool l16 = t.lanes == 16;
   const int B = t.block;
   switch (kind) {
     case K_MX_VERTEX:
-      if (l16) k_mx_vertex<16><<<item_blocks(G.nv, 16, B), B, 0, st>>>(G, ea.vn, ea.w, s.zeta32, s.wv32);
-      else k_mx_vertex<32><<<item_blocks(G.nv, 32, B), B, 0, st>>>(G, ea.vn, ea.w, s.zeta32, s.wv32);
+      with_lanes(t.lanes, [&](auto L) {
+        constexpr int LPE = decltype(L)::value;
+        k_mx_vertex<LPE><<<item_blocks(G.nv, LPE, B), B, 0, st>>>(G, ea.vn, ea.w, s.zeta32, s.wv32);
+      });
       break;
     case K_MX_EDGE:
-      if (l16) k_mx_edge_diag<16><<<item_blocks(G.ne, 16, B), B, 0, st>>>(G, ea.vn, s.vt32);
-      else k_mx_edge_diag<32><<<item_blocks(G.ne, 32, B), B, 0, st>>>(G, ea.vn, s.vt32);
+      with_lanes(t.lanes, [&](auto L) {
+        constexpr int LPE = decltype(L)::value;
+        k_mx_edge_diag<LPE><<<item_blocks(G.ne, LPE, B), B, 0, st>>>(G, ea.vn, s.vt32);
+      });
       break;
     case K_MX_CELL_KE:
-      if (l16) k_mx_cell_ke<16><<<item_blocks(G.nc, 16, B), B, 0, st>>>(G, ea.vn, s.vt32, s.Kc32);
-      else k_mx_cell_ke<32><<<item_blocks(G.nc, 32, B), B, 0, st>>>(G, ea.vn, s.vt32, s.Kc32);
+      with_lanes(t.lanes, [&](auto L) {
+        constexpr int LPE = decltype(L)::value;
+        k_mx_cell_ke<LPE><<<item_blocks(G.nc, LPE, B), B, 0, st>>>(G, ea.vn, s.vt32, s.Kc32);
+      });
       break;
     case K_MX_EDGE_TEND:
-      if (s.topo.on) {
-        if (l16) k_mx_edge_tend<16, true><<<item_blocks(G.ne, 16, B), B, 0, st>>>(G, ea);
-        else k_mx_edge_tend<32, true><<<item_blocks(G.ne, 32, B), B, 0, st>>>(G, ea);
-      } else {
-        if (l16) k_mx_edge_tend<16><<<item_blocks(G.ne, 16, B), B, 0, st>>>(G, ea);
-        else k_mx_edge_tend<32><<<item_blocks(G.ne, 32, B), B, 0, st>>>(G, ea);
-      }
+      with_lanes(t.lanes, [&](auto L) {
+        constexpr int LPE = decltype(L)::value;
+        if (s.topo.on) k_mx_edge_tend<LPE, true><<<item_blocks(G.ne, LPE, B), B, 0, st>>>(G, ea);
+        else k_mx_edge_tend<LPE><<<item_blocks(G.ne, LPE, B), B, 0, st>>>(G, ea);
+      });
       break;
     case K_MX_DIFF_VERTEX:
-      if (l16)
-        k_mx_diff_vertex<16><<<item_blocks(G.nv + G.nc, 16, B), B, 0, st>>>(G, s.vn32, s.uvx32, s.uvy32, s.uvz32,
-                                                                         s.zeta32, s.Kc32);
-      else
-        k_mx_diff_vertex<32><<<item_blocks(G.nv + G.nc, 32, B), B, 0, st>>>(G, s.vn32, s.uvx32, s.uvy32, s.uvz32,
-                                                                         s.zeta32, s.Kc32);
+      with_lanes(t.lanes, [&](auto L) {
+        constexpr int LPE = decltype(L)::value;
+        k_mx_diff_vertex<LPE><<<item_blocks(G.nv + G.nc, LPE, B), B, 0, st>>>(G, s.vn32, s.uvx32, s.uvy32, s.uvz32,
+                                                                              s.zeta32, s.Kc32);
+      });
       break;
     case K_MX_COLUMN_PREP: {   // the predictor's gather (the corrector's only differs in the Aw0 average)
       const unsigned nb = (unsigned)((G.nc + 31) / 32);
-      if (s.ln_B) {
-        const MxLeanArgs la = lean_args(s, false, (double)ea.dtau, 1);
-        if (l16) k_mx_lean_gather<16, false><<<nb, B, 0, st>>>(G, la);
-        else k_mx_lean_gather<32, false><<<nb, B, 0, st>>>(G, la);
-      } else {
-        if (l16) k_mx_gather_tile<16, false><<<nb, B, 0, st>>>(G, ca);
-        else k_mx_gather_tile<32, false><<<nb, B, 0, st>>>(G, ca);
-      }
+      with_lanes(t.lanes, [&](auto L) {
+        constexpr int LPE = decltype(L)::value;
+        if (s.ln_B) {
+          const MxLeanArgs la = lean_args(s, false, (double)ea.dtau, 1);
+          k_mx_lean_gather<LPE, false><<<nb, B, 0, st>>>(G, la);
+        } else {
+          k_mx_gather_tile<LPE, false><<<nb, B, 0, st>>>(G, ca);
+        }
+      });
+      break;
+    }
+    case K_MX_LEAN: {          // the predictor's lean column (writes only the stage's scratch and S*)
+      const MxLeanArgs la = lean_args(s, false, (double)ea.dtau, 1);
+      launch_lean_column<false>(G, la, t, st);
       break;
     }
     case K_MX_DIFF_EDGE:
-      if (l16)
-        k_mx_diff_edge<16><<<item_blocks(G.ne, 16, B), B, 0, st>>>(G, s.vn32, s.uvx32, s.uvy32, s.uvz32, s.zeta32,
-                                                                s.Kc32, s.thv32, s.vt32, dt);
-      else
-        k_mx_diff_edge<32><<<item_blocks(G.ne, 32, B), B, 0, st>>>(G, s.vn32, s.uvx32, s.uvy32, s.uvz32, s.zeta32,
-                                                                s.Kc32, s.thv32, s.vt32, dt);
+      with_lanes(t.lanes, [&](auto L) {
+        constexpr int LPE = decltype(L)::value;
+        k_mx_diff_edge<LPE><<<item_blocks(G.ne, LPE, B), B, 0, st>>>(G, s.vn32, s.uvx32, s.uvy32, s.uvz32, s.zeta32,
+                                                                     s.Kc32, s.thv32, s.vt32, dt);
+      });
       break;
     default: break;
   }
@@ -1869,12 +1904,18 @@ void launch_mx_column(const MxGeo& G, const MxColArgs& a, bool topo, cudaStream_
 }
 
 // ---------------------------------------------------------------- autotuner
-// Candidate tiles over (entity, level): 32 lanes per entity (one entity per warp)
-// or 16 (two per warp), blocks of 128, 256 or 512 threads. Each stencil kind is timed
-// on the state's own data (three launches per candidate, CUDA events) and the fastest
-// kept. Choices are cached per (kind, grid size, levels, GPU) in the process and, if
-// the environment variable ICON_TUNE_CACHE names a file, in that file.
-const int kTunedKinds[] = {K_MX_VERTEX, K_MX_EDGE, K_MX_CELL_KE, K_MX_EDGE_TEND, K_MX_COLUMN_PREP, K_MX_DIFF_VERTEX};
+// Candidate tiles over (entity, level): 32 lanes per entity (one entity per warp), 16
+// (two per warp) or 8 (four per warp), blocks of 64, 128, 256 or 512 threads: twelve per
+// stencil kind. The lean column (one thread per column) chooses among its precompiled
+// launch shapes (kLeanShapes). Each kind is timed on the state's own data (three launches
+// per candidate after one untimed, CUDA events) and the fastest kept, in the order of the
+// step, so that every trial reads inputs its predecessors formed. Choices are cached per
+// (kind, grid size, levels, GPU) in the process and, if the environment variable
+// ICON_TUNE_CACHE names a file, in that file.
+const int kTunedKinds[] = {K_MX_VERTEX, K_MX_EDGE, K_MX_CELL_KE, K_MX_EDGE_TEND, K_MX_COLUMN_PREP, K_MX_LEAN,
+                           K_MX_DIFF_VERTEX};
+const int kTileLanes[] = {32, 16, 8};
+const int kTileBlocks[] = {128, 256, 512, 64};
 std::mutex g_tune_mu;
 std::map<std::string, TileChoice> g_tune_cache;
 bool g_tune_file_loaded = false;
@@ -1914,6 +1955,8 @@ void save_tune_entry(const std::string& key, const TileChoice& t) {
 
 }  // namespace
 
+bool lean_column_shape_ok(int unroll, int blocks_per_sm) { return lean_shape_ok(TileChoice{unroll, blocks_per_sm}); }
+
 void autotune_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream) {
   StateDev& s = st->s;
   const MxGeo G = make_mx_geo(st->grid, s);
@@ -1921,40 +1964,56 @@ void autotune_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream) {
   // the predictor's arguments: every tuned kernel then writes only scratch or S* buffers
   const MxEdgeArgs ea = edge_args(s, false, dtau, nsub);
   const MxColArgs ca = col_args(s, false, dtau, nsub);
+  const bool lean = s.ln_B != nullptr;
+  if (lean) {
+    // the lean gather's weights and the column's per-level constants for this dtau, so that
+    // the gather and column trials compute on valid inputs
+    k_mx_leanconst<<<1, 128, 0, stream>>>(G.N, G.ld, G.wu, G.wl, G.dzh, G.dz, G.ray, s.ex_ref, dtau, s.ln_cd, s.ln_cf);
+    k_mx_dwa_t<<<blocks_for(G.nc, 256), 256, 0, stream>>>(G.nc, G.div_wa, G.inv_Ac, dtau, s.ln_dwa, s.ln_cw32);
+  }
   std::lock_guard<std::mutex> lk(g_tune_mu);
   load_tune_file();
   for (int kind : kTunedKinds) {
     if (st->tile[kind].lanes != 0 && st->tile_forced[kind]) continue;
-    if (kind == K_MX_COLUMN_PREP && !s.fac64 && !s.ln_B) continue;
+    if (kind == K_MX_COLUMN_PREP && !s.fac64 && !lean) continue;
+    if (kind == K_MX_LEAN && !lean) continue;
     const std::string key = tune_key(kind, G);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
       st->tile[kind] = it->second;
       continue;
     }
+    std::vector<TileChoice> cands;
+    if (kind == K_MX_LEAN) {
+      for (const TileChoice& c : kLeanShapes) cands.push_back(c);
+    } else {
+      for (int lanes : kTileLanes)
+        for (int block : kTileBlocks) cands.push_back(TileChoice{lanes, block});
+    }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    TileChoice bestc{32, 256};
-    for (int lanes : {32, 16})
-      for (int block : {128, 256, 512}) {
-        const TileChoice t{lanes, block};
-        launch_kind(kind, t, G, s, ea, ca, (float)dt, stream);     // warm
-        cudaEventRecord(e0, stream);
-        for (int r = 0; r < 3; ++r) launch_kind(kind, t, G, s, ea, ca, (float)dt, stream);
-        cudaEventRecord(e1, stream);
-        cudaEventSynchronize(e1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) { best = ms; bestc = t; }
-      }
+    TileChoice bestc = cands[0];
+    for (const TileChoice& t : cands) {
+      launch_kind(kind, t, G, s, ea, ca, (float)dt, stream);     // warm
+      cudaEventRecord(e0, stream);
+      for (int r = 0; r < 3; ++r) launch_kind(kind, t, G, s, ea, ca, (float)dt, stream);
+      cudaEventRecord(e1, stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; bestc = t; }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     st->tile[kind] = bestc;
     g_tune_cache[key] = bestc;
     save_tune_entry(key, bestc);
   }
+  // a trial that met a non-finite value would have flagged the state; the step that
+  // follows checks it again
+  cudaMemsetAsync(s.status, 0, sizeof(unsigned), stream);
   st->tuned = true;
 }
 
@@ -2023,17 +2082,18 @@ void enqueue_step_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream
         prof_begin(stream, K_MX_LEAN_GATHER);
         if (corr && fused) {
           launch_lean_gather_dd(G, la, stream);
-        } else if (corr) {
-          if (t.lanes == 16) k_mx_lean_gather<16, true><<<nb, t.block, 0, stream>>>(G, la);
-          else k_mx_lean_gather<32, true><<<nb, t.block, 0, stream>>>(G, la);
         } else {
-          if (t.lanes == 16) k_mx_lean_gather<16, false><<<nb, t.block, 0, stream>>>(G, la);
-          else k_mx_lean_gather<32, false><<<nb, t.block, 0, stream>>>(G, la);
+          with_lanes(t.lanes, [&](auto L) {
+            constexpr int LPE = decltype(L)::value;
+            if (corr) k_mx_lean_gather<LPE, true><<<nb, t.block, 0, stream>>>(G, la);
+            else k_mx_lean_gather<LPE, false><<<nb, t.block, 0, stream>>>(G, la);
+          });
         }
         prof_end(stream);
         prof_begin(stream, K_MX_LEAN);
-        if (corr) launch_lean_column<true>(G, la, stream);
-        else launch_lean_column<false>(G, la, stream);
+        const TileChoice tc = st->tile[K_MX_LEAN].lanes ? st->tile[K_MX_LEAN] : kLeanDefault;
+        if (corr) launch_lean_column<true>(G, la, tc, stream);
+        else launch_lean_column<false>(G, la, tc, stream);
         prof_end(stream);
         continue;
       }
@@ -2041,13 +2101,11 @@ void enqueue_step_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream
         const TileChoice t = tile(K_MX_COLUMN_PREP);
         const unsigned nb = (unsigned)((nc + 31) / 32);
         prof_begin(stream, K_MX_COLUMN_PREP);
-        if (corr) {
-          if (t.lanes == 16) k_mx_gather_tile<16, true><<<nb, t.block, 0, stream>>>(G, ca);
-          else k_mx_gather_tile<32, true><<<nb, t.block, 0, stream>>>(G, ca);
-        } else {
-          if (t.lanes == 16) k_mx_gather_tile<16, false><<<nb, t.block, 0, stream>>>(G, ca);
-          else k_mx_gather_tile<32, false><<<nb, t.block, 0, stream>>>(G, ca);
-        }
+        with_lanes(t.lanes, [&](auto L) {
+          constexpr int LPE = decltype(L)::value;
+          if (corr) k_mx_gather_tile<LPE, true><<<nb, t.block, 0, stream>>>(G, ca);
+          else k_mx_gather_tile<LPE, false><<<nb, t.block, 0, stream>>>(G, ca);
+        });
         prof_end(stream);
       }
       prof_begin(stream, K_MX_COLUMN);

@@ -271,6 +271,8 @@ struct EnsembleDev {
 int ensemble_prepare(EnsembleDev& E, icon_state* const* members, int n, const double* dts, int nsub);
 int ensemble_launch(EnsembleDev& E, cudaStream_t st, unsigned long long* prof = nullptr, int prof_max = 0);
 void autotune_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream);
+// a launch shape (sweep unroll, resident blocks per SM) the lean mixed column is built with
+bool lean_column_shape_ok(int unroll, int blocks_per_sm);
 // the stored-factor column parts of a mixed state (api.cu); false if they do not fit
 bool alloc_mixed_factors(icon_state* st);
 int selftest_conversions(int64_t n, unsigned* host_fails);

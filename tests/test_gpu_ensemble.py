@@ -63,6 +63,9 @@ def test_ensemble_members_equal_solo_runs(gpu, monkeypatch, form):
 
 
 def test_results_do_not_depend_on_tiles(gpu):
+    """Every stencil tile (8, 16 or 32 lanes per entity, 64 to 512 threads per block) and
+    every launch shape of the lean column (registers held for 6 to 12 blocks per SM) gives
+    bit-identical results; the autotuner's choices lie in the candidate sets."""
     C = gpu
     N = 40
     grid = C.icon_grid_build(2, 3, N)
@@ -70,20 +73,34 @@ def test_results_do_not_depend_on_tiles(gpu):
              C.KIND_MX_DIFF_VERTEX]
     out = []
     try:
-        for lanes, block in ((32, 128), (16, 512), (0, 0)):
+        for (lanes, block), shape in (((32, 128), (2, 10)), ((16, 512), (2, 12)), ((8, 64), (2, 6)),
+                                      ((16, 256), (2, 8)), ((0, 0), (0, 0))):
             st = C.icon_state_init_ex(grid, 9, C.ICON_CASE_JET, noise_K=0.1, precision=C.ICON_MIXED)
             for k in kinds:
                 C.icon_state_set_tiling(st, k, lanes, block)
+            C.icon_state_set_tiling(st, C.KIND_MX_LEAN, *shape)
             C.icon_dycore_step(st, 150.0, 5)
             tiles = [C.icon_state_tiling(st, k) for k in kinds]
             if lanes:
                 assert all(t == (lanes, block) for t in tiles)
+                assert C.icon_state_tiling(st, C.KIND_MX_LEAN) == shape
             else:        # chosen by the autotuner
-                assert all(t[0] in (16, 32) and t[1] in (128, 256, 512) for t in tiles)
+                assert all(t[0] in (8, 16, 32) and t[1] in (64, 128, 256, 512) for t in tiles), tiles
+                assert C.icon_state_tiling(st, C.KIND_MX_LEAN) in C.LEAN_SHAPES
             out.append(_fields(C, st, grid, N))
             C.icon_state_free(st)
-        for f in out[0]:
-            assert np.array_equal(out[0][f], out[1][f]) and np.array_equal(out[0][f], out[2][f]), f
+        for o in out[1:]:
+            for f in out[0]:
+                assert np.array_equal(out[0][f], o[f]), f
+        st = C.icon_state_init_ex(grid, 9, C.ICON_CASE_JET, precision=C.ICON_MIXED)
+        try:
+            for kind, lanes, block in ((C.KIND_MX_VERTEX, 4, 128), (C.KIND_MX_VERTEX, 16, 96),
+                                       (C.KIND_MX_LEAN, 1, 10), (C.KIND_MX_LEAN, 2, 9)):
+                with pytest.raises(C.IconError) as ei:
+                    C.icon_state_set_tiling(st, kind, lanes, block)
+                assert ei.value.status == C.ICON_EINVAL
+        finally:
+            C.icon_state_free(st)
     finally:
         C.icon_grid_free(grid)
 
