@@ -130,7 +130,8 @@ typedef struct {
    * and topo_radius_m >= 1e4, else ICON_EINVAL. Tracers of a state with topography are
    * transported with these fluxes on its own levels; such states join no ensemble. A
    * mixed-precision state with topography forms the metric terms in FP32 with its other
-   * stencils and its column always recomputes its factors (no stored-factor form). */
+   * stencils and runs the lean column with each cell's own spacings and the contravariant
+   * vertical velocity (or, if asked, the recomputing column; no stored-factor form). */
   double topo_height_m;
   double topo_radius_m;
 } icon_case_params;
@@ -194,11 +195,13 @@ void icon_grid_free(icon_grid* grid);
 int icon_state_init(const icon_grid* grid, uint64_t seed, int case_id, icon_state** out);
 
 /* As icon_state_init with explicit parameters (params may be NULL).
- * A mixed-precision state stores the parts of the column system that the predictor
- * and corrector share (17 level-major FP64 fields per cell) when they take at most a
- * quarter of the device memory, and otherwise recomputes them in both stages. If the
- * environment variable ICON_MIXED_RECOMPUTE is "1" when the state is created, it
- * recomputes regardless (for testing the second form on small grids). */
+ * A mixed-precision state runs the lean column (FP32 rows and factors, FP64 hydrostatic
+ * base, substitution and updates; 6 level-major scratch fields per cell) unless the
+ * environment variable ICON_MIXED_COLUMN names another form when the state is created:
+ * "stored" (the parts of the column system the two stages share, 17 level-major FP64
+ * fields per cell, stored by the predictor when they take at most a quarter of the device
+ * memory; flat levels only) or "recompute" (both stages form them; also selected by
+ * ICON_MIXED_RECOMPUTE=1). The forms agree within the mixed-precision bounds. */
 int icon_state_init_ex(const icon_grid* grid, uint64_t seed, int case_id,
                        const icon_case_params* params, icon_state** out);
 

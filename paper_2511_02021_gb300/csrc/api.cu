@@ -279,16 +279,17 @@ int alloc_state(icon_state* st, int precision, bool topo) {
     // the column form: ICON_MIXED_COLUMN = "lean" (default), "stored" (the frozen parts of the
     // column system stored by the predictor for the corrector, when they take at most a
     // quarter of the device memory) or "recompute" (both stages compute them; also selected
-    // by ICON_MIXED_RECOMPUTE=1); on terrain-following levels the column always recomputes
-    // them (the stored forms freeze the explicit vertical fluxes, which there carry each
-    // stage's own contravariant correction)
+    // by ICON_MIXED_RECOMPUTE=1). On terrain-following levels the lean column runs with the
+    // cells' own tables (its stored base depends on S^n only; the explicit vertical fluxes,
+    // which carry each stage's own contravariant correction, are formed in each stage); the
+    // stored form is flat-only (it freezes those fluxes)
     const char* form = getenv("ICON_MIXED_COLUMN");
     const char* force_recompute = getenv("ICON_MIXED_RECOMPUTE");
     bool recompute = force_recompute && force_recompute[0] == '1' && force_recompute[1] == '\0';
     bool stored = false;
     if (form && strcmp(form, "recompute") == 0) recompute = true;
     if (form && strcmp(form, "stored") == 0) stored = true;
-    if (!topo && !recompute && !stored) {
+    if (!recompute && !stored) {
       const size_t H = (size_t)nc * (ld0 + 1);
       s.ln_dr64 = A.get_n<double>(H);
       s.ln_dt32 = A.get_n<float>(H);

@@ -1285,6 +1285,12 @@ struct MxLeanArgs {
   double* mflx;
   float dd_scale;
   int dd_upwind;
+  // terrain-following levels (TOPO instances): the column's per-cell tables, level-major
+  // [k][Nc] (upper interpolation weight, 1/dz, 1/dzh, reference Exner), the stage's
+  // contravariant correction wcc at half levels ([Nc][ld]); for the gather w - wcc and 1/dzh
+  // ([Nc][ld]) and the layer thickness at edges ([Ne][ld])
+  const double *t_wu_lm, *t_idz_lm, *t_idzh_lm, *t_exref_lm;
+  const float *t_wcc, *t_wcon, *t_inv_dzh, *t_dz_e;
 };
 
 // per-warp shadow transpose: CH levels of 32 columns (16 in the per-state kernel, 8 in the
@@ -1302,7 +1308,10 @@ struct LeanGatherTile {
   float f[4][LPE][kGatherCells + 1];       // dtau D_Theta, dtau A_w, A_w (predictor), dtau D_rho (predictor)
 };
 
-template <int LPE, bool CORR, bool DDF = false>
+// TOPO (terrain-following levels): the damped fluxes through the edges' layer thickness, the
+// vertical advection of w with w - wcc and the cell's own 1/dzh; the divergences stay per unit
+// thickness here and the column scales them by the cell's 1/dz
+template <int LPE, bool CORR, bool DDF = false, bool TOPO = false>
 __device__ inline void mx_lean_gather_body(const MxGeo& G, const MxLeanArgs& a, int64_t c0, LeanGatherTile<LPE>& T) {
   constexpr int CB = kGatherCells;
   const int N = G.N, ld = G.ld;
@@ -1355,6 +1364,7 @@ __device__ inline void mx_lean_gather_body(const MxGeo& G, const MxLeanArgs& a, 
           for (int s = 0; s < 3; ++s) {
             const float vd = a.dd_vn[E[s] + k] - sc[s] * (a.dd_L[Cb[s] + k] - a.dd_L[Ca[s] + k]);
             F[s] = 0.5f * (a.dd_rho[Ca[s] + k] + a.dd_rho[Cb[s] + k]) * vd;
+            if constexpr (TOPO) F[s] *= a.t_dz_e[E[s] + k];
             const float t1 = a.dd_thv[Ca[s] + k], t2 = a.dd_thv[Cb[s] + k];
             Gt[s] = (le[s] * F[s]) * (a.dd_upwind ? (vd >= 0.0f ? t1 : t2) : 0.5f * (t1 + t2));
             if (own[s]) {
@@ -1376,8 +1386,11 @@ __device__ inline void mx_lean_gather_body(const MxGeo& G, const MxLeanArgs& a, 
       }
       if (k >= 1 && k < N) {
         const float hadv = kw[0] * a.a_e[E[0] + k] + kw[1] * a.a_e[E[1] + k] + kw[2] * a.a_e[E[2] + k];
-        const float ws = a.w_stage[o + k];
-        float Aw = -hadv - ws * (a.w_stage[o + k - 1] - a.w_stage[o + k + 1]) * G.inv_dz2_32[k];
+        float Aw;
+        if constexpr (TOPO)
+          Aw = -hadv - a.t_wcon[o + k] * (a.w_stage[o + k - 1] - a.w_stage[o + k + 1]) * (0.5f * a.t_inv_dzh[o + k]);
+        else
+          Aw = -hadv - a.w_stage[o + k] * (a.w_stage[o + k - 1] - a.w_stage[o + k + 1]) * G.inv_dz2_32[k];
         if (CORR) Aw = 0.5f * (T.f[2][lane][cl] + Aw);
         else T.f[2][lane][cl] = Aw;
         T.f[1][lane][cl] = dtau32 * Aw;
@@ -1401,17 +1414,18 @@ __device__ inline void mx_lean_gather_body(const MxGeo& G, const MxLeanArgs& a, 
   }
 }
 
-template <int LPE, bool CORR, bool DDF = false>
+template <int LPE, bool CORR, bool DDF = false, bool TOPO = false>
 __global__ void __launch_bounds__(512, 3) k_mx_lean_gather(MxGeo G, MxLeanArgs a) {
   __shared__ LeanGatherTile<LPE> T;
-  mx_lean_gather_body<LPE, CORR, DDF>(G, a, (int64_t)blockIdx.x * kGatherCells, T);
+  mx_lean_gather_body<LPE, CORR, DDF, TOPO>(G, a, (int64_t)blockIdx.x * kGatherCells, T);
 }
 
 // the corrector's gather with the damping fused in (32 lanes per cell, 256-thread blocks: the
 // fastest of six tiles measured at R2B6/90, within 13 % of one another)
-void launch_lean_gather_dd(const MxGeo& G, const MxLeanArgs& a, cudaStream_t st) {
+void launch_lean_gather_dd(const MxGeo& G, const MxLeanArgs& a, bool topo, cudaStream_t st) {
   const unsigned nb = (unsigned)((G.nc + kGatherCells - 1) / kGatherCells);
-  k_mx_lean_gather<32, true, true><<<nb, 256, 0, st>>>(G, a);
+  if (topo) k_mx_lean_gather<32, true, true, true><<<nb, 256, 0, st>>>(G, a);
+  else k_mx_lean_gather<32, true, true><<<nb, 256, 0, st>>>(G, a);
 }
 
 // write the finished chunk [k0, k0 + CH) of the warp's 32 columns (first cell c0): CH lanes
@@ -1439,7 +1453,12 @@ __device__ inline void lean_flush(const MxGeo& G, const MxLeanArgs& a, const Lea
 
 // one column per thread (lane); every lane of the warp runs the loops (lanes past the last
 // cell compute on zeros and store nothing) so that the chunk flushes stay warp-synchronous
-template <bool CORR, int U, int CH>
+// TOPO (terrain-following levels): each cell's interpolation weights, 1/dz and 1/dzh and
+// reference Exner (level-major tables) in place of the per-level constants, the contravariant
+// (1 - beta) w - wcc in the explicit vertical fluxes (zero at the lid and the ground), the
+// gathered divergences scaled by the cell's 1/dz, and the stage's terrain-following w at the
+// ground
+template <bool CORR, int U, int CH, bool TOPO = false>
 __device__ inline void mx_lean_column_item(const MxGeo& G, const MxLeanArgs& a, int64_t c, int64_t c0, int lane,
                                            LeanTile<CH>& T) {
   const int N = G.N, ld = G.ld;
@@ -1455,7 +1474,7 @@ __device__ inline void mx_lean_column_item(const MxGeo& G, const MxLeanArgs& a, 
   double thv1 = 0.0, ex1 = 0.0, ex2 = 0.0;          // full levels j-1 and j-2 (FP64)
   float rho1f = 0.f, thv1f = 0.f;
   double ti1 = 0.0;                                  // theta_ic at half level j-1 (FP64)
-  float ti1f = 0.f, M1 = 0.f, M2 = 0.f, w1f = 0.f;   // half level j-1 (and j-2 for M)
+  float ti1f = 0.f, M1 = 0.f, M2 = 0.f, xv1 = 0.f;   // half level j-1 (and j-2 for M)
   double w1 = 0.0;
   float gam2 = 0.f, dpe2 = 0.f;                      // full level j-2
   float cp_prev = 0.f;
@@ -1480,6 +1499,16 @@ __device__ inline void mx_lean_column_item(const MxGeo& G, const MxLeanArgs& a, 
       ti = thv1;
       rif = rho1f;
       tif = thv1f;
+    } else if constexpr (TOPO) {
+      const double wu = LMV(a.t_wu_lm, j);
+      const float wuf = f64_to_f32(wu);
+      rif = wuf * rho1f + (1.0f - wuf) * rhof;
+      if (!CORR) {
+        ti = wu * thv1 + (1.0 - wu) * thv;
+        tif = f64_to_f32(ti);
+      } else {
+        tif = wuf * thv1f + (1.0f - wuf) * thvf;
+      }
     } else {
       rif = cf[LF_WU * ld + j] * rho1f + cf[LF_WL * ld + j] * rhof;
       if (!CORR) {
@@ -1492,22 +1521,46 @@ __device__ inline void mx_lean_column_item(const MxGeo& G, const MxLeanArgs& a, 
     const float Mh = rif * tif;
     const double wh = (j == 0 || j == N) ? 0.0 : LMV(a.w, j);
     const float whf = f64_to_f32(wh);
+    // the explicit vertical velocity through half level j: w on flat levels (the factor
+    // 1 - beta is in the level constant), (1 - beta) w - wcc on terrain-following ones
+    float xvj = whf;
+    if constexpr (TOPO) xvj = (j == 0 || j == N) ? 0.0f : (float)(1.0 - kBeta) * whf - a.t_wcc[cc * ld + j];
     float gam1 = 0.f, dpe1 = 0.f;
     if (j >= 1) {
       const int k = j - 1;
-      const float dthe = -LMV(a.dt32, k) - cf[LF_DT1 * ld + k] * (M1 * w1f - Mh * whf);
+      float dtk = LMV(a.dt32, k), dt1, dtb;
+      if constexpr (TOPO) {
+        const double idz = LMV(a.t_idz_lm, k);
+        dtk *= f64_to_f32(idz);
+        dt1 = f64_to_f32(dtau * idz);
+        dtb = f64_to_f32(dtau * kBeta * idz);
+      } else {
+        dt1 = cf[LF_DT1 * ld + k];
+        dtb = cf[LF_DTB * ld + k];
+      }
+      const float dthe = -dtk - dt1 * (M1 * xv1 - Mh * xvj);
       const float g = kRcvF * (f64_to_f32(ex1) / (rho1f * thv1f));
-      gam1 = g * cf[LF_DTB * ld + k];
+      gam1 = g * dtb;
       dpe1 = g * dthe;
       if (k >= 1) {
         const int h = k;
-        const float aa = cf[LF_CA * ld + h] * ti1f;
+        double cpdzh;                                    // cpd / dzh of half level h
+        float ca;
+        if constexpr (TOPO) {
+          const double idzh = LMV(a.t_idzh_lm, h);
+          cpdzh = kCpd * idzh;
+          ca = f64_to_f32(dtau * kBeta * kCpd * idzh);
+        } else {
+          cpdzh = cd[LD_CPDZH * ld + h];
+          ca = cf[LF_CA * ld + h];
+        }
+        const float aa = ca * ti1f;
         const float lo = -aa * gam2 * M2;
         const float di = 1.0f + aa * (gam2 + gam1) * M1;
         const float up = -aa * gam1 * Mh;
         double B;
         if (!CORR) {
-          B = w1 - dtau * fma(cd[LD_CPDZH * ld + h] * ti1, ex2 - ex1, kGrav);
+          B = w1 - dtau * fma(cpdzh * ti1, ex2 - ex1, kGrav);
           if (act) LMV(a.B, h) = B;
         } else {
           B = LMV(a.B, h);
@@ -1529,7 +1582,7 @@ __device__ inline void mx_lean_column_item(const MxGeo& G, const MxLeanArgs& a, 
     M2 = M1;
     M1 = Mh;
     w1 = wh;
-    w1f = whf;
+    xv1 = xvj;
     ti1 = ti;
     ti1f = tif;
     ex2 = ex1;
@@ -1545,7 +1598,7 @@ __device__ inline void mx_lean_column_item(const MxGeo& G, const MxLeanArgs& a, 
   double x_next = 0.0, wn_next = 0.0;                // half level k+1: undamped, damped
   float wnf_next = 0.f;
   // half level k+1 quantities carried upward
-  float ri_next = 0.f, M_next = 0.f, wf_next = 0.f;  // at k+1 (w of S^n)
+  float ri_next = 0.f, M_next = 0.f, xv_next = 0.f;  // at k+1 (explicit vertical velocity of S^n)
   float fflux_next = 0.f;                            // corrector: vertical mass flux at k+1
   // full level k (current) and k-1 (next), FP64 and FP32
   double rho_k = act ? LMV(a.rho, N - 1) : 0.0, thv_k = act ? LMV(a.thv, N - 1) : 0.0;
@@ -1572,11 +1625,17 @@ __device__ inline void mx_lean_column_item(const MxGeo& G, const MxLeanArgs& a, 
     if (k == 0) {
       ri_k = rho_kf;
       M_k = rho_kf * thv_kf;
+    } else if constexpr (TOPO) {
+      const float wuf = f64_to_f32(LMV(a.t_wu_lm, k));
+      ri_k = wuf * f64_to_f32(rho_u) + (1.0f - wuf) * rho_kf;
+      M_k = ri_k * (wuf * f64_to_f32(thv_u) + (1.0f - wuf) * thv_kf);
     } else {
       ri_k = cf[LF_WU * ld + k] * f64_to_f32(rho_u) + cf[LF_WL * ld + k] * rho_kf;
       M_k = ri_k * (cf[LF_WU * ld + k] * f64_to_f32(thv_u) + cf[LF_WL * ld + k] * thv_kf);
     }
     const float wf_k = k >= 1 ? f64_to_f32(LMV(a.w, k)) : 0.0f;
+    float xv_k = wf_k;
+    if constexpr (TOPO) xv_k = k >= 1 ? (float)(1.0 - kBeta) * wf_k - a.t_wcc[o + k] : 0.0f;
     // back substitution at half level k
     double x = 0.0, wn = 0.0;
     if (k >= 1) {
@@ -1585,24 +1644,45 @@ __device__ inline void mx_lean_column_item(const MxGeo& G, const MxLeanArgs& a, 
     }
     const float wnf = f64_to_f32(wn);
     // full level k
-    const float dtb = cf[LF_DTB * ld + k], dt1 = cf[LF_DT1 * ld + k];
-    const float dthe = -LMV(a.dt32, k) - dt1 * (M_k * wf_k - M_next * wf_next);
+    float dtb, dt1, dtk = LMV(a.dt32, k);
+    double idz = 0.0, exref;
+    if constexpr (TOPO) {
+      idz = LMV(a.t_idz_lm, k);
+      dtk *= f64_to_f32(idz);
+      dt1 = f64_to_f32(dtau * idz);
+      dtb = f64_to_f32(dtau * kBeta * idz);
+      exref = LMV(a.t_exref_lm, k);
+    } else {
+      dtb = cf[LF_DTB * ld + k];
+      dt1 = cf[LF_DT1 * ld + k];
+      exref = cd[LD_EXREF * ld + k];
+    }
+    const float dthe = -dtk - dt1 * (M_k * xv_k - M_next * xv_next);
     const float g = kRcvF * (f64_to_f32(ex_k) / (rho_kf * thv_kf));
     const float q = M_k * wnf - M_next * wnf_next;
     const float dTh = dthe - dtb * q;                // Theta increment
     const float dex = g * dthe - g * dtb * q;        // Exner increment (linearised state equation)
     float s_rho, s_thv, s_exp;
     if (!CORR) {
-      const float drho = -LMV(a.dr32, k) - dt1 * (ri_k * wf_k - ri_next * wf_next) -
-                         dtb * (ri_k * wnf - ri_next * wnf_next);
+      float drk = LMV(a.dr32, k);
+      if constexpr (TOPO) drk *= f64_to_f32(idz);
+      const float drho = -drk - dt1 * (ri_k * xv_k - ri_next * xv_next) - dtb * (ri_k * wnf - ri_next * wnf_next);
       s_rho = rho_kf + drho;
       s_thv = thv_kf + (dTh - drho * thv_kf) / s_rho;
-      s_exp = f64_to_f32(ex_k - cd[LD_EXREF * ld + k]) + dex;
+      s_exp = f64_to_f32(ex_k - exref) + dex;
       ok = ok && isfinite(s_thv) && isfinite(s_exp) && isfinite(wnf);
     } else {
-      // vertical mass flux through half level k of the step: rho_ic ((1 - beta) w^n + beta w^{n+1})
-      const float fk = ri_k * ((float)(1.0 - kBeta) * wf_k + (float)kBeta * wnf);
-      const double t = fma(cd[LD_IDZ * ld + k], f32_to_f64(fk) - f32_to_f64(fflux_next), LMV(a.dr64, k));
+      // vertical mass flux through half level k of the step: rho_ic ((1 - beta) w^n + beta w^{n+1}),
+      // less rho_ic wcc on terrain-following levels
+      double t;
+      float fk;
+      if constexpr (TOPO) {
+        fk = ri_k * (xv_k + (float)kBeta * wnf);
+        t = fma(dtau * idz, f32_to_f64(fk) - f32_to_f64(fflux_next), LMV(a.dr64, k) * idz);
+      } else {
+        fk = ri_k * ((float)(1.0 - kBeta) * wf_k + (float)kBeta * wnf);
+        t = fma(cd[LD_IDZ * ld + k], f32_to_f64(fk) - f32_to_f64(fflux_next), LMV(a.dr64, k));
+      }
       const double rho_n = rho_k - t;
       const float rho_nf = f64_to_f32(rho_n);
       const double thv_n = thv_k + f32_to_f64((dTh + f64_to_f32(t) * thv_kf) / rho_nf);
@@ -1616,7 +1696,7 @@ __device__ inline void mx_lean_column_item(const MxGeo& G, const MxLeanArgs& a, 
       }
       s_rho = rho_nf;
       s_thv = f64_to_f32(thv_n);
-      s_exp = f64_to_f32(ex_n - cd[LD_EXREF * ld + k]);
+      s_exp = f64_to_f32(ex_n - exref);
       ok = ok && finite64(thv_n) && finite64(ex_n) && finite64(wn);
       fflux_next = fk;
     }
@@ -1631,27 +1711,33 @@ __device__ inline void mx_lean_column_item(const MxGeo& G, const MxLeanArgs& a, 
     wnf_next = wnf;
     ri_next = ri_k;
     M_next = M_k;
-    wf_next = wf_k;
+    xv_next = xv_k;
     rho_k = rho_u;
     thv_k = thv_u;
     ex_k = ex_u;
   }
   (void)wn_next;
   if (act) {
-    a.w32[o + N] = 0.0f;
-    if (CORR) LMV(a.w, N) = 0.0;                     // the ground (w^n there is 0 already)
+    if constexpr (TOPO) {                            // the ground: the stage's terrain-following w
+      const float wg = a.t_wcc[o + N];
+      a.w32[o + N] = wg;
+      if (CORR) LMV(a.w, N) = f32_to_f64(wg);
+    } else {
+      a.w32[o + N] = 0.0f;
+      if (CORR) LMV(a.w, N) = 0.0;                   // the ground (w^n there is 0 already)
+    }
   }
   if (!ok && act) atomicOr(a.status, 1u);
 #undef LMV
 }
 
-template <bool CORR, int U, int CH, int THREADS, int MINB>
+template <bool CORR, int U, int CH, int THREADS, int MINB, bool TOPO = false>
 __global__ void __launch_bounds__(THREADS, MINB) k_mx_lean_column(MxGeo G, MxLeanArgs a) {
   __shared__ LeanTile<CH> T[THREADS / 32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t c0 = (int64_t)blockIdx.x * THREADS + warp * 32;
   if (c0 >= G.nc) return;                            // whole warp past the end
-  mx_lean_column_item<CORR, U, CH>(G, a, c0 + lane, c0, lane, T[warp]);
+  mx_lean_column_item<CORR, U, CH, TOPO>(G, a, c0 + lane, c0, lane, T[warp]);
 }
 
 // launch shapes of the lean column, one thread per column in blocks of four warps: the tile's
@@ -1672,13 +1758,19 @@ bool lean_shape_ok(const TileChoice& t) {
   return false;
 }
 
-template <bool CORR>
-void launch_lean_column(const MxGeo& G, const MxLeanArgs& a, const TileChoice& t, cudaStream_t st) {
+template <bool CORR, bool TOPO = false>
+void launch_lean_column_as(const MxGeo& G, const MxLeanArgs& a, const TileChoice& t, cudaStream_t st) {
   const unsigned nb = blocks_for(G.nc, 128);
-  if (t.block == 8) k_mx_lean_column<CORR, 2, 8, 128, 8><<<nb, 128, 0, st>>>(G, a);
-  else if (t.block == 12) k_mx_lean_column<CORR, 2, 8, 128, 12><<<nb, 128, 0, st>>>(G, a);
-  else if (t.block == 6) k_mx_lean_column<CORR, 2, 8, 128, 6><<<nb, 128, 0, st>>>(G, a);
-  else k_mx_lean_column<CORR, 2, 8, 128, 10><<<nb, 128, 0, st>>>(G, a);
+  if (t.block == 8) k_mx_lean_column<CORR, 2, 8, 128, 8, TOPO><<<nb, 128, 0, st>>>(G, a);
+  else if (t.block == 12) k_mx_lean_column<CORR, 2, 8, 128, 12, TOPO><<<nb, 128, 0, st>>>(G, a);
+  else if (t.block == 6) k_mx_lean_column<CORR, 2, 8, 128, 6, TOPO><<<nb, 128, 0, st>>>(G, a);
+  else k_mx_lean_column<CORR, 2, 8, 128, 10, TOPO><<<nb, 128, 0, st>>>(G, a);
+}
+
+template <bool CORR>
+void launch_lean_column(const MxGeo& G, const MxLeanArgs& a, const TileChoice& t, bool topo, cudaStream_t st) {
+  if (topo) launch_lean_column_as<CORR, true>(G, a, t, st);
+  else launch_lean_column_as<CORR, false>(G, a, t, st);
 }
 
 MxGeo make_mx_geo(const icon_grid* grid, const StateDev& s) {
@@ -1780,6 +1872,9 @@ MxLeanArgs lean_args(StateDev& s, bool corr, double dtau, int nsub) {
   la.mflx = s.mflx;
   la.dd_scale = 0.0f;
   la.dd_upwind = 0;
+  const TopoDev& T = s.topo;
+  la.t_wu_lm = T.wu_lm; la.t_idz_lm = T.idz_lm; la.t_idzh_lm = T.idzh_lm; la.t_exref_lm = T.exref_lm;
+  la.t_wcc = T.wcc32; la.t_wcon = T.wcon32; la.t_inv_dzh = T.inv_dzh_c32; la.t_dz_e = T.dz_e32;
   return la;
 }
 
@@ -1857,7 +1952,8 @@ void launch_kind(int kind, const TileChoice& t, const MxGeo& G, StateDev& s, con
         constexpr int LPE = decltype(L)::value;
         if (s.ln_B) {
           const MxLeanArgs la = lean_args(s, false, (double)ea.dtau, 1);
-          k_mx_lean_gather<LPE, false><<<nb, B, 0, st>>>(G, la);
+          if (s.topo.on) k_mx_lean_gather<LPE, false, false, true><<<nb, B, 0, st>>>(G, la);
+          else k_mx_lean_gather<LPE, false><<<nb, B, 0, st>>>(G, la);
         } else {
           k_mx_gather_tile<LPE, false><<<nb, B, 0, st>>>(G, ca);
         }
@@ -1866,7 +1962,7 @@ void launch_kind(int kind, const TileChoice& t, const MxGeo& G, StateDev& s, con
     }
     case K_MX_LEAN: {          // the predictor's lean column (writes only the stage's scratch and S*)
       const MxLeanArgs la = lean_args(s, false, (double)ea.dtau, 1);
-      launch_lean_column<false>(G, la, t, st);
+      launch_lean_column<false>(G, la, t, s.topo.on, st);
       break;
     }
     case K_MX_DIFF_EDGE:
@@ -2081,19 +2177,24 @@ void enqueue_step_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream
         const unsigned nb = (unsigned)((nc + 31) / 32);
         prof_begin(stream, K_MX_LEAN_GATHER);
         if (corr && fused) {
-          launch_lean_gather_dd(G, la, stream);
+          launch_lean_gather_dd(G, la, s.topo.on, stream);
         } else {
           with_lanes(t.lanes, [&](auto L) {
             constexpr int LPE = decltype(L)::value;
-            if (corr) k_mx_lean_gather<LPE, true><<<nb, t.block, 0, stream>>>(G, la);
-            else k_mx_lean_gather<LPE, false><<<nb, t.block, 0, stream>>>(G, la);
+            if (s.topo.on) {
+              if (corr) k_mx_lean_gather<LPE, true, false, true><<<nb, t.block, 0, stream>>>(G, la);
+              else k_mx_lean_gather<LPE, false, false, true><<<nb, t.block, 0, stream>>>(G, la);
+            } else {
+              if (corr) k_mx_lean_gather<LPE, true><<<nb, t.block, 0, stream>>>(G, la);
+              else k_mx_lean_gather<LPE, false><<<nb, t.block, 0, stream>>>(G, la);
+            }
           });
         }
         prof_end(stream);
         prof_begin(stream, K_MX_LEAN);
         const TileChoice tc = st->tile[K_MX_LEAN].lanes ? st->tile[K_MX_LEAN] : kLeanDefault;
-        if (corr) launch_lean_column<true>(G, la, tc, stream);
-        else launch_lean_column<false>(G, la, tc, stream);
+        if (corr) launch_lean_column<true>(G, la, tc, s.topo.on, stream);
+        else launch_lean_column<false>(G, la, tc, s.topo.on, stream);
         prof_end(stream);
         continue;
       }

@@ -148,11 +148,14 @@ def test_tracer_over_terrain_vs_oracle(gpu):
 
 
 # ------------------------------------------------------------------ mixed precision
+@pytest.mark.parametrize("form", ["lean", "recompute"])
 @pytest.mark.parametrize("bis,nlev,case,dt", [(2, 20, 2, 300.0), (3, 30, 3, 200.0)])
-def test_mixed_terrain_one_step_vs_oracle(gpu, bis, nlev, case, dt):
-    """The mixed form on terrain-following levels (FP32 stencils and metric terms, FP64
-    column with each cell's spacings) against the FP64 oracle, with the mixed form's
+def test_mixed_terrain_one_step_vs_oracle(gpu, monkeypatch, bis, nlev, case, dt, form):
+    """The mixed form on terrain-following levels (FP32 stencils and metric terms; the lean
+    column with each cell's spacings and the contravariant vertical velocity, the default,
+    or the recomputing FP64 column) against the FP64 oracle, with the mixed form's
     tolerances."""
+    monkeypatch.setenv("ICON_MIXED_COLUMN", form)
     gi, go, m0, m1 = run_gpu(gpu, bis, nlev, 8, case, dt, 5, 1, precision=1)
     oi, oo, _, _ = run_oracle(bis, nlev, 8, case, dt, 5, 1)
     for f in ("rho", "theta_v", "exner"):
