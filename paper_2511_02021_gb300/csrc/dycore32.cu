@@ -1576,7 +1576,7 @@ __device__ inline void mx_lean_column_item(const MxGeo& G, const MxLeanArgs& a, 
         dtb = cf[LF_DTB * ld + k];
       }
       const float dthe = -dtk - dt1 * (M1 * xv1 - Mh * xvj);
-      const float g = kRcvF * (f64_to_f32(ex1) / (rho1f * thv1f));
+      const float g = kRcvF * __fdividef(f64_to_f32(ex1), rho1f * thv1f);
       gam1 = g * dtb;
       dpe1 = g * dthe;
       if (k >= 1) {
@@ -1603,7 +1603,7 @@ __device__ inline void mx_lean_column_item(const MxGeo& G, const MxLeanArgs& a, 
           B = LMV(a.B, h);
         }
         const float inc = LMV(a.aw32, h) - aa * (dpe2 - dpe1);
-        const float piv = 1.0f / (di - lo * cp_prev);
+        const float piv = __fdividef(1.0f, di - lo * cp_prev);
         const float cpv = up * piv;
         const double dpv = (B + f32_to_f64(inc) - f32_to_f64(lo) * dp_prev) * f32_to_f64(piv);
         if (act) {
@@ -1695,7 +1695,7 @@ __device__ inline void mx_lean_column_item(const MxGeo& G, const MxLeanArgs& a, 
       exref = cd[LD_EXREF * ld + k];
     }
     const float dthe = -dtk - dt1 * (M_k * xv_k - M_next * xv_next);
-    const float g = kRcvF * (f64_to_f32(ex_k) / (rho_kf * thv_kf));
+    const float g = kRcvF * __fdividef(f64_to_f32(ex_k), rho_kf * thv_kf);
     const float q = M_k * wnf - M_next * wnf_next;
     const float dTh = dthe - dtb * q;                // Theta increment
     const float dex = g * dthe - g * dtb * q;        // Exner increment (linearised state equation)
@@ -1705,7 +1705,7 @@ __device__ inline void mx_lean_column_item(const MxGeo& G, const MxLeanArgs& a, 
       if constexpr (TOPO) drk *= f64_to_f32(idz);
       const float drho = -drk - dt1 * (ri_k * xv_k - ri_next * xv_next) - dtb * (ri_k * wnf - ri_next * wnf_next);
       s_rho = rho_kf + drho;
-      s_thv = thv_kf + (dTh - drho * thv_kf) / s_rho;
+      s_thv = thv_kf + __fdividef(dTh - drho * thv_kf, s_rho);
       s_exp = f64_to_f32(ex_k - exref) + dex;
       ok = ok && isfinite(s_thv) && isfinite(s_exp) && isfinite(wnf);
     } else {
@@ -1722,7 +1722,7 @@ __device__ inline void mx_lean_column_item(const MxGeo& G, const MxLeanArgs& a, 
       }
       const double rho_n = rho_k - t;
       const float rho_nf = f64_to_f32(rho_n);
-      const double thv_n = thv_k + f32_to_f64((dTh + f64_to_f32(t) * thv_kf) / rho_nf);
+      const double thv_n = thv_k + f32_to_f64(__fdividef(dTh + f64_to_f32(t) * thv_kf, rho_nf));
       const double ex_n = ex_k + f32_to_f64(dex);
       if (act) {
         LMV(a.wflx, k) = fma(f32_to_f64(fk), a.inv_nsub, LMV(a.wflx, k));
