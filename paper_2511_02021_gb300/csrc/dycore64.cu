@@ -751,7 +751,7 @@ __global__ void __launch_bounds__(256) k_diff_theta(Geo64 G, const double* __res
     for (int s = 0; s < 3; ++s) acc += sg[s] * thflx[E[s] + k];
     const double dth = dtA * acc;
     const double th = thv[c * ld + k];
-    ex[c * ld + k] = ex[c * ld + k] * (1.0 + (kRd / kCvd) * dth / th);
+    ex[c * ld + k] = ex[c * ld + k] * (1.0 + ((kRd / kCvd) * dth) * recip64(th));
     thv[c * ld + k] = th + dth;
   }
 }
