@@ -354,6 +354,12 @@ int record_graph(icon_state* st, double dt, int nsub) {
     st->graph = nullptr;
   }
   if (!st->capture_stream) ICON_CUDA(cudaStreamCreateWithFlags(&st->capture_stream, cudaStreamNonBlocking));
+  const char* ov = getenv("ICON_STEP_OVERLAP");
+  if (st->s.precision == ICON_MIXED && !st->s.topo.on && !st->side_stream && !(ov && ov[0] == '0')) {
+    ICON_CUDA(cudaStreamCreateWithFlags(&st->side_stream, cudaStreamNonBlocking));
+    ICON_CUDA(cudaEventCreateWithFlags(&st->fork_ev, cudaEventDisableTiming));
+    ICON_CUDA(cudaEventCreateWithFlags(&st->join_ev, cudaEventDisableTiming));
+  }
   cudaGraph_t g = nullptr;
   ICON_CUDA(cudaStreamBeginCapture(st->capture_stream, cudaStreamCaptureModeThreadLocal));
   Prof* saved = t_prof;
@@ -836,6 +842,9 @@ void icon_state_free(icon_state* st) {
   cudaDeviceSynchronize();
   if (st->graph) cudaGraphExecDestroy(st->graph);
   if (st->capture_stream) cudaStreamDestroy(st->capture_stream);
+  if (st->side_stream) cudaStreamDestroy(st->side_stream);
+  if (st->fork_ev) cudaEventDestroy(st->fork_ev);
+  if (st->join_ev) cudaEventDestroy(st->join_ev);
   if (st->done) cudaEventDestroy(st->done);
   st->arena.release();
   delete st;

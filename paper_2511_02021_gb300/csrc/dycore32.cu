@@ -2165,6 +2165,28 @@ void enqueue_step_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream
     k_mx_dwa_t<<<blocks_for(nc, 256), 256, 0, stream>>>(nc, G.div_wa, G.inv_Ac, dtau, s.ln_dwa, s.ln_cw32);
   }
   auto tile = [&](int kind) { return st->tile[kind].lanes ? st->tile[kind] : TileChoice{32, 256}; };
+  // The next stage's edge diagnostics (vt) and cell kinetic energy read only that stage's vn,
+  // final once this stage's edge tendency (predictor) or damped gather (corrector) has run,
+  // and write vt32 and Kc32, which neither this stage's gather nor its column reads. While a
+  // step on flat levels is recorded into its graph they go on a second branch beside the
+  // column, whose last wave of blocks leaves part of the SMs idle; the branch is joined before
+  // the next stage's edge tendency. Eager (profiled) steps keep one stream. (Measured: R2B6/90
+  // 29.5 -> 28.7 ms per step; over terrain, and for the FP64 step, the branch measured slower or
+  // equal and is not used.)
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(stream, &cs);
+  const bool overlap = lean && !s.topo.on && st->side_stream && cs == cudaStreamCaptureStatusActive;
+  bool diag_ahead = false;                 // this stage's vt32 and Kc32 are on the branch
+  auto fork_diag = [&](bool next_corr) {
+    const MxEdgeArgs en = edge_args(s, next_corr, dtau, nsub);
+    cudaEventRecord(st->fork_ev, stream);
+    cudaStreamWaitEvent(st->side_stream, st->fork_ev, 0);
+    launch_kind(K_MX_EDGE, tile(K_MX_EDGE), G, s, en, col_args(s, next_corr, dtau, nsub), (float)dt, st->side_stream);
+    launch_kind(K_MX_CELL_KE, tile(K_MX_CELL_KE), G, s, en, col_args(s, next_corr, dtau, nsub), (float)dt,
+                st->side_stream);
+    cudaEventRecord(st->join_ev, st->side_stream);
+    diag_ahead = true;
+  };
   for (int it = 0; it < nsub; ++it) {
     for (int stage = 0; stage < 2; ++stage) {
       const bool corr = stage == 1;
@@ -2180,6 +2202,11 @@ void enqueue_step_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream
       ead.upwind_theta = st->upwind_theta ? 1 : 0;
       if (fused) ead.vn_out = s.Avn0_32;
       for (int kind : {K_MX_VERTEX, K_MX_EDGE, K_MX_CELL_KE, K_MX_EDGE_TEND}) {
+        if (diag_ahead && (kind == K_MX_EDGE || kind == K_MX_CELL_KE)) continue;
+        if (diag_ahead && kind == K_MX_EDGE_TEND) {
+          cudaStreamWaitEvent(stream, st->join_ev, 0);
+          diag_ahead = false;
+        }
         if (kind == K_MX_EDGE_TEND && s.topo.on) topo_stage32(st, ea.vn, s.vt32, ea.w, ea.exp, stream);
         prof_begin(stream, kind);
         launch_kind(kind, tile(kind), G, s, ead, ca, (float)dt, stream);
@@ -2228,6 +2255,7 @@ void enqueue_step_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream
           });
         }
         prof_end(stream);
+        if (overlap && (!corr || it + 1 < nsub)) fork_diag(!corr);
         prof_begin(stream, K_MX_LEAN);
         const TileChoice tc = st->tile[K_MX_LEAN].lanes ? st->tile[K_MX_LEAN] : kLeanDefault;
         if (corr) launch_lean_column<true>(G, la, tc, s.topo.on, stream);

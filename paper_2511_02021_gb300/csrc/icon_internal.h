@@ -230,6 +230,10 @@ struct icon_state {
   cudaStream_t capture_stream = nullptr;
   cudaStream_t graph_stream = nullptr;
   cudaEvent_t done = nullptr;
+  // second branch of the recorded mixed step on flat levels (the next stage's edge
+  // diagnostics beside the column); not created when ICON_STEP_OVERLAP=0
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   // stencil tiles (mixed mode): chosen by the autotuner unless forced
   icon::TileChoice tile[ICON_KIND_COUNT] = {};
   bool tile_forced[ICON_KIND_COUNT] = {};
