@@ -212,9 +212,9 @@ int icon_state_init_ex(const icon_grid* grid, uint64_t seed, int case_id,
  * the state's tracers, if any, are then transported with them, and the options set
  * with icon_state_set_option apply. The first call for a given (dt, nsubsteps)
  * records a CUDA graph of the step (again after an option or tracers are added);
- * later calls replay it. In the graph of a mixed-precision step on flat levels, each
- * stage's edge diagnostics and cell kinetic energy run on a second branch beside the
- * previous stage's column (same kernels on the same inputs, so the results are the same;
+ * later calls replay it. In the graph of a mixed-precision step on flat levels of a grid
+ * of at least 327,680 cells (R2B6), each stage's edge diagnostics and cell kinetic energy
+ * run on a second branch beside the previous stage's column (same kernels on the same inputs, so the results are the same;
  * the environment variable ICON_STEP_OVERLAP=0 at the first recording keeps one branch).
  * Waits for completion and returns ICON_ENONFINITE if a non-finite value was produced.
  * dt > 0, 1 <= nsubsteps <= 64.

@@ -2170,12 +2170,16 @@ void enqueue_step_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream
   // and write vt32 and Kc32, which neither this stage's gather nor its column reads. While a
   // step on flat levels is recorded into its graph they go on a second branch beside the
   // column, whose last wave of blocks leaves part of the SMs idle; the branch is joined before
-  // the next stage's edge tendency. Eager (profiled) steps keep one stream. (Measured: R2B6/90
-  // 29.5 -> 28.7 ms per step; over terrain, and for the FP64 step, the branch measured slower or
-  // equal and is not used.)
+  // the next stage's edge tendency. Eager (profiled) steps keep one stream. Measured: R2B6/90
+  // 29.5 -> 28.7 ms per step, R2B8/90 439.7 -> 438.5 ms; on coarser grids the joins cost about
+  // what the branch saves (64 states of R2B4/60 and R2B5/60 stepped one after another: 270 ->
+  // 285 ms), over terrain and for the FP64 step the branch measured slower or equal: it is
+  // recorded for flat mixed states of at least kBranchMinCells cells (R2B6) only.
+  constexpr int64_t kBranchMinCells = 327680;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(stream, &cs);
-  const bool overlap = lean && !s.topo.on && st->side_stream && cs == cudaStreamCaptureStatusActive;
+  const bool overlap = lean && !s.topo.on && nc >= kBranchMinCells && st->side_stream &&
+                       cs == cudaStreamCaptureStatusActive;
   bool diag_ahead = false;                 // this stage's vt32 and Kc32 are on the branch
   auto fork_diag = [&](bool next_corr) {
     const MxEdgeArgs en = edge_args(s, next_corr, dtau, nsub);

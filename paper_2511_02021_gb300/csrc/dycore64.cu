@@ -173,6 +173,7 @@ struct EdgeArgs {
   double *F, *G, *a_e, *mflx;
   double dtau, inv_nsub;
   double hinv_nsub;                        // inv_nsub / 2 (set on the host)
+  double hdtau;                            // dtau / 2 (set on the host)
   int corrector;
   int skip_flux;                           // fluxes formed after divergence damping instead
   int upwind_theta;                        // heat flux with the upwind theta_v (option)
@@ -204,6 +205,9 @@ __global__ void __launch_bounds__(256, 4) k_edge_tend(Geo64 G, EdgeArgs a) {
   // these constants (and the column's divergence weights), exact scalings by powers of two
   const double hcide = 0.5 * (kCpd * ide);
   const double hcsne = TOPO ? 0.5 * (kCpd * G.t_sn[e]) : 0.0;
+  // flat levels: the pressure-gradient term enters vn through one multiply-add with
+  // -dtau cpd / (2 d_e), and the advective part through dtau (predictor) or dtau / 2
+  const double ndhcide = -(a.dtau * hcide);
   const double hinv_nsub = a.hinv_nsub;
   const double* __restrict__ vn = a.vn + eo;
   const double* __restrict__ vt = a.vt + eo;
@@ -248,19 +252,24 @@ __global__ void __launch_bounds__(256, 4) k_edge_tend(Geo64 G, EdgeArgs a) {
       const double A = fma(-((sw + sw_up) * (vie - vie_up)), TOPO ? G.t_qinv_dz_e[eo + k] : G.qinv_dz[k], T);
       const double t1 = a.thv[c1 + k], t2 = a.thv[c2 + k];
       const double th_s = t1 + t2;                     // 2 theta_e
-      double pg;
+      double vnew;
       if (TOPO) {
         const double corr = (hcsne * G.t_bf[k]) * (G.t_hdpdz[c1 + k] + G.t_hdpdz[c2 + k]);
-        pg = th_s * fma(G.t_ep[c2 + k] - G.t_ep[c1 + k], hcide, -corr);
+        const double pg = th_s * fma(G.t_ep[c2 + k] - G.t_ep[c1 + k], hcide, -corr);
+        if (a.corrector) {
+          vnew = fma(dtau, fma(0.5, a.Avn0[eo + k] + A, -pg), a.vn_base[eo + k]);
+        } else {
+          vnew = fma(dtau, A - pg, a.vn_base[eo + k]);
+          a.Avn0[eo + k] = A;
+        }
       } else {
-        pg = th_s * ((a.ex[c2 + k] - a.ex[c1 + k]) * hcide);
-      }
-      double vnew;
-      if (a.corrector) {
-        vnew = fma(dtau, fma(0.5, a.Avn0[eo + k] + A, -pg), a.vn_base[eo + k]);
-      } else {
-        vnew = fma(dtau, A - pg, a.vn_base[eo + k]);
-        a.Avn0[eo + k] = A;
+        const double tdx = th_s * (a.ex[c2 + k] - a.ex[c1 + k]);
+        if (a.corrector) {
+          vnew = fma(ndhcide, tdx, fma(a.hdtau, a.Avn0[eo + k] + A, a.vn_base[eo + k]));
+        } else {
+          vnew = fma(ndhcide, tdx, fma(dtau, A, a.vn_base[eo + k]));
+          a.Avn0[eo + k] = A;
+        }
       }
       a.vn_out[eo + k] = vnew;
       if (a.skip_flux) continue;
@@ -846,6 +855,7 @@ void fp64_step_stage(icon_state* st, double dt, int nsub, bool corr, cudaStream_
   ea.F = s.F; ea.G = s.G; ea.a_e = s.a_e; ea.mflx = s.mflx;
   ea.dtau = dtau; ea.inv_nsub = 1.0 / nsub; ea.corrector = corr;
   ea.hinv_nsub = 0.5 / nsub;
+  ea.hdtau = 0.5 * dtau;
   const bool damp = corr && st->divdamp4 > 0.0;
   ea.skip_flux = damp ? 1 : 0;
   ea.upwind_theta = st->upwind_theta ? 1 : 0;

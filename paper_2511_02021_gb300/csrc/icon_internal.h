@@ -230,8 +230,8 @@ struct icon_state {
   cudaStream_t capture_stream = nullptr;
   cudaStream_t graph_stream = nullptr;
   cudaEvent_t done = nullptr;
-  // second branch of the recorded mixed step on flat levels (the next stage's edge
-  // diagnostics beside the column); not created when ICON_STEP_OVERLAP=0
+  // second branch of the recorded mixed step on flat levels of R2B6 and finer grids (the next
+  // stage's edge diagnostics beside the column); not created when ICON_STEP_OVERLAP=0
   cudaStream_t side_stream = nullptr;
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   // stencil tiles (mixed mode): chosen by the autotuner unless forced
