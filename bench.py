@@ -144,7 +144,7 @@ def kernel_model(kind, wl, mx_ops):
         "edge_vt_ke": (b * 3 * ne * N, ne * N * 8),
         "cell_ke": (b * (ne + nc) * N, nc * N * 3),
         "edge_tendency_flux": (b * (ne * N * 6.5 + nc * N * 4 + nv * N + nc * H + nv * H + ne * H),
-                               ne * N * 23 + ne * H * 11),
+                               ne * N * 22 + ne * H * 11),
         "column_solve": (b * (nc * N * 8 + ne * N * 2 + ne * H + nc * H * 2.5), nc * N * COLUMN_FP64_OPS),
         "diff_vertex": (b * (ne * N + 4 * nv * N), nv * N * 25),
         "diff_div": (b * (ne + nc) * N, nc * N * 7),
