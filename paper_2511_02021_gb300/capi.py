@@ -327,7 +327,7 @@ KIND_MX_VERTEX, KIND_MX_EDGE, KIND_MX_CELL_KE, KIND_MX_EDGE_TEND, KIND_MX_COLUMN
     10, 11, 12, 13, 15, 16
 # the lean mixed column: its tile is a launch shape (sweep unroll, resident blocks per SM)
 KIND_MX_LEAN = 24
-LEAN_SHAPES = ((2, 10), (2, 8), (2, 12), (2, 6))
+LEAN_SHAPES = ((2, 9), (2, 10), (2, 8), (2, 12), (2, 6))
 
 
 def icon_ensemble_set_option(ens, option, value):

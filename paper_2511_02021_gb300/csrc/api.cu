@@ -813,7 +813,7 @@ int icon_state_set_tiling(icon_state* st, int kind, int lanes, int block) {
   if (!st || kind < 0 || kind >= ICON_KIND_COUNT) { set_error("icon_state_set_tiling: bad argument"); return ICON_EINVAL; }
   if (lanes != 0 && kind == K_MX_LEAN) {
     if (!lean_column_shape_ok(lanes, block)) {
-      set_error("icon_state_set_tiling: the lean column takes (unroll, blocks per SM) (2, 10), (2, 8), (2, 12) or (2, 6)");
+      set_error("icon_state_set_tiling: the lean column takes (unroll, blocks per SM) (2, 9), (2, 10), (2, 8), (2, 12) or (2, 6)");
       return ICON_EINVAL;
     }
   } else if (lanes != 0 && ((lanes != 8 && lanes != 16 && lanes != 32) ||

@@ -1779,15 +1779,16 @@ __global__ void __launch_bounds__(THREADS, MINB) k_mx_lean_column(MxGeo G, MxLea
 
 // launch shapes of the lean column, one thread per column in blocks of four warps: the tile's
 // "lanes" is the unroll factor of the two sweeps and its "block" the resident blocks per SM
-// the registers are held to (6: 80 registers, 8: 64, 10: 48, 12: 40). Only the register cap
-// varies among the candidates: it leaves the arithmetic as it is, while another unroll factor
+// the registers are held to (6: 80 registers, 8: 64, 9: 56, 10: 48, 12: 40). Only the register
+// cap varies among the candidates: it leaves the arithmetic as it is, while another unroll factor
 // changes which multiply-adds the compiler fuses and with them the FP32 roundings (measured:
 // unroll 1 or 4 moves vn by 1e-7 relative after one step), and a tuner choosing by timing
-// must not change results. The default (unrolled by two, 10 blocks) measured fastest at
-// R2B6/90 over eight shapes (12.2 ms per step against 16.9 ms with 64-thread blocks at 94
-// registers): the kernel waits on memory latency and gains from occupancy.
-const TileChoice kLeanShapes[] = {{2, 10}, {2, 8}, {2, 12}, {2, 6}};
-const TileChoice kLeanDefault = {2, 10};
+// must not change results. The kernel waits on memory latency and gains from occupancy (12.2 ms
+// per R2B6/90 step at 10 blocks against 16.9 ms with 64-thread blocks at 94 registers); the
+// default, 9 blocks (36 warps per SM, 56 registers, no spills), measured 11.21 against 11.68 ms
+// at 10 blocks (48 registers, spilling in the corrector) and 161.3 against 162.4 ms at R2B8/90.
+const TileChoice kLeanShapes[] = {{2, 9}, {2, 10}, {2, 8}, {2, 12}, {2, 6}};
+const TileChoice kLeanDefault = {2, 9};
 
 bool lean_shape_ok(const TileChoice& t) {
   for (const TileChoice& c : kLeanShapes)
@@ -1799,9 +1800,10 @@ template <bool CORR, bool TOPO = false>
 void launch_lean_column_as(const MxGeo& G, const MxLeanArgs& a, const TileChoice& t, cudaStream_t st) {
   const unsigned nb = blocks_for(G.nc, 128);
   if (t.block == 8) k_mx_lean_column<CORR, 2, 8, 128, 8, TOPO><<<nb, 128, 0, st>>>(G, a);
+  else if (t.block == 10) k_mx_lean_column<CORR, 2, 8, 128, 10, TOPO><<<nb, 128, 0, st>>>(G, a);
   else if (t.block == 12) k_mx_lean_column<CORR, 2, 8, 128, 12, TOPO><<<nb, 128, 0, st>>>(G, a);
   else if (t.block == 6) k_mx_lean_column<CORR, 2, 8, 128, 6, TOPO><<<nb, 128, 0, st>>>(G, a);
-  else k_mx_lean_column<CORR, 2, 8, 128, 10, TOPO><<<nb, 128, 0, st>>>(G, a);
+  else k_mx_lean_column<CORR, 2, 8, 128, 9, TOPO><<<nb, 128, 0, st>>>(G, a);
 }
 
 template <bool CORR>

@@ -74,7 +74,7 @@ def test_results_do_not_depend_on_tiles(gpu):
     out = []
     try:
         for (lanes, block), shape in (((32, 128), (2, 10)), ((16, 512), (2, 12)), ((8, 64), (2, 6)),
-                                      ((16, 256), (2, 8)), ((0, 0), (0, 0))):
+                                      ((16, 256), (2, 8)), ((8, 128), (2, 9)), ((0, 0), (0, 0))):
             st = C.icon_state_init_ex(grid, 9, C.ICON_CASE_JET, noise_K=0.1, precision=C.ICON_MIXED)
             for k in kinds:
                 C.icon_state_set_tiling(st, k, lanes, block)
@@ -95,7 +95,7 @@ def test_results_do_not_depend_on_tiles(gpu):
         st = C.icon_state_init_ex(grid, 9, C.ICON_CASE_JET, precision=C.ICON_MIXED)
         try:
             for kind, lanes, block in ((C.KIND_MX_VERTEX, 4, 128), (C.KIND_MX_VERTEX, 16, 96),
-                                       (C.KIND_MX_LEAN, 1, 10), (C.KIND_MX_LEAN, 2, 9)):
+                                       (C.KIND_MX_LEAN, 1, 10), (C.KIND_MX_LEAN, 2, 7)):
                 with pytest.raises(C.IconError) as ei:
                     C.icon_state_set_tiling(st, kind, lanes, block)
                 assert ei.value.status == C.ICON_EINVAL
