@@ -459,8 +459,10 @@ void icon_domain_free(icon_domain* domain);
  * warp, 16 = two, 8 = four) and threads per block (64, 128, 256 or 512). The lean column
  * (24): its launch shape, lanes = the unroll factor of its two sweeps and block = the
  * resident 128-thread blocks per SM its registers are held to, one of (2, 9), (2, 10),
- * (2, 8), (2, 12), (2, 6). The autotuner picks them on the first step (timing every candidate on
- * the state's data, in the order of the step; cached per grid size, level count and GPU,
+ * (2, 8), (2, 12), (2, 6); a tuned shape applies to the predictor's column, the
+ * corrector's keeps (2, 9) unless a shape is forced. The autotuner picks them on the
+ * first step (timing every candidate on the state's data, in the order of the step;
+ * cached per grid size, level count and GPU,
  * and in the file named by the environment variable ICON_TUNE_CACHE if set). set_tiling
  * forces a tile (lanes 0 restores automatic choice; ICON_EINVAL for any other value
  * outside these sets); results do not depend on the tile. */

@@ -2263,8 +2263,12 @@ void enqueue_step_mixed(icon_state* st, double dt, int nsub, cudaStream_t stream
         prof_end(stream);
         if (overlap && (!corr || it + 1 < nsub)) fork_diag(!corr);
         prof_begin(stream, K_MX_LEAN);
+        // the autotuner times the predictor's column (the corrector updates S^n in place and
+        // cannot be run again on the state); the corrector, whose extra live values spill at
+        // 48 registers, keeps the default shape (56 registers, no spills) unless one is forced
         const TileChoice tc = st->tile[K_MX_LEAN].lanes ? st->tile[K_MX_LEAN] : kLeanDefault;
-        if (corr) launch_lean_column<true>(G, la, tc, s.topo.on, stream);
+        const TileChoice tcc = st->tile_forced[K_MX_LEAN] ? tc : kLeanDefault;
+        if (corr) launch_lean_column<true>(G, la, tcc, s.topo.on, stream);
         else launch_lean_column<false>(G, la, tc, s.topo.on, stream);
         prof_end(stream);
         continue;
