@@ -84,12 +84,13 @@ TRACER_FP64_OPS = 77
 # the kernel changed after the counters were taken), mean of the predictor and corrector
 # launches. Captured at R2B5/90 (the full sizes hold too much memory for a multi-pass capture)
 # and scaled by cell-levels: every column does the same work, so the traffic grows in
-# proportion. FP64 column 2.407 GB per launch at R2B5/90; lean mixed column 1.085 GB.
+# proportion. FP64 column 2.407 GB per launch at R2B5/90; lean mixed column 1.081 GB (its
+# default shape, 9 blocks per SM in both stages).
 NCU_TRAFFIC = {
     ("R2B6-L90-jet-fp64", "column_solve"): 2.407e9 * 4,
-    ("R2B6-L90-jet-fp64", "mx_lean_column"): 1.085e9 * 4,
-    ("R2B8-L90-jet-mixed", "mx_lean_column"): 1.085e9 * 64,
-    ("R2B9-L60-jet-mixed", "mx_lean_column"): 1.085e9 * 256 * 60 / 90,
+    ("R2B6-L90-jet-fp64", "mx_lean_column"): 1.081e9 * 4,
+    ("R2B8-L90-jet-mixed", "mx_lean_column"): 1.081e9 * 64,
+    ("R2B9-L60-jet-mixed", "mx_lean_column"): 1.081e9 * 256 * 60 / 90,
 }
 
 
