@@ -89,3 +89,16 @@ def test_binding_constants_match_the_header():
     assert {"ICON_KIND_COUNT", "ICON_ENS_PHASE_COUNT", "ICON_OK", "ICON_EINVAL"} <= set(shared)
     for n in shared:
         assert getattr(C, n) == defs[n], n
+
+
+def test_every_environment_switch_is_documented():
+    """Each environment variable the library reads is described in the header a user reads."""
+    csrc = os.path.join(ROOT, "paper_2511_02021_gb300", "csrc")
+    names = set()
+    for f in os.listdir(csrc):
+        if f.endswith((".cu", ".h")):
+            names |= set(re.findall(r'getenv\("([A-Z0-9_]+)"\)', open(os.path.join(csrc, f)).read()))
+    assert {"ICON_MIXED_COLUMN", "ICON_TUNE_CACHE", "ICON_STEP_OVERLAP"} <= names
+    header = open(os.path.join(ROOT, "include", "icon.h")).read()
+    for n in sorted(names):
+        assert n in header, n
