@@ -261,7 +261,7 @@ def test_vertical_advection_of_the_terrain_oracle_over_flat_ground():
 @pytest.mark.parametrize("old,new,which", [
     ("- wbar * (vn_ie[:, :N] - vn_ie[:, 1:])", "+ wbar * (vn_ie[:, :N] - vn_ie[:, 1:])", 0),
     ("- w[:, 1:N] * (w[:, 0:N - 1]", "+ w[:, 1:N] * (w[:, 0:N - 1]", 1),
-    # the single-interval denominator printed in the survey's O7 (the centred difference spans two)
+    # a denominator over one level interval while the centred difference of w spans two
     ("(v.z_h[0:N - 1] - v.z_h[2:N + 1])", "(v.z_f[0:N - 1] - v.z_f[1:N])", 1),
 ])
 def test_planted_vertical_advection_mistakes_fail(old, new, which):
